@@ -1,0 +1,208 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the benchmark.
+
+This module holds no arithmetic of the method itself (no forces, CVs, network
+passes or integrator): it only draws parameters and starting geometries from a
+seed, so that the GPU path and the FP64 oracle see byte-identical inputs.
+
+The paper's workloads (solvated chignolin with 18 backbone torsions, a 4 x
+[300]^4 residual ensemble, 12 walkers; the HfO2 Deep-Potential system) are not
+available, so bead chains in implicit solvent stand in for them:
+
+* force field (reduced units, kT = 1, mass = 1): harmonic bonds k = 100,
+  r0 = 1; harmonic angles k = 20, theta0 = 110 deg; three-term dihedrals
+  sum_n k_n (1 + cos(n phi - delta_n)) with k_n ~ U(0, 2), delta_n ~ U(0, 2 pi)
+  per dihedral; Lennard-Jones eps = 1, sigma = 1, cutoff 2.5, 1-2 and 1-3
+  pairs excluded;
+* CVs: C evenly spaced backbone-like torsions i_j = floor((j + 1/2)(N - 3)/C)
+  over beads (i_j, i_j+1, i_j+2, i_j+3) -- the stand-in for the phi/psi
+  torsions of "torsion" mode (Sec. "CV selection", Table 2);
+* ensemble: M tanh MLPs D -> H x L -> 1 (Sec. "Training phase": numb_models,
+  neurons), Glorot-uniform weights; biases are drawn U(-0.2, 0.2) rather than
+  zero so that a dropped bias term shows up in every parity test;
+* starting chains: self-avoiding random chains built bead by bead from the
+  bond length, bond angle and a uniform random dihedral, rejecting placements
+  closer than 0.9 to any non-excluded earlier bead.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "SystemParams", "EnsembleParams", "make_system", "make_chains",
+    "make_ensemble", "make_label_targets", "ensemble_param_count",
+    "WORKLOADS", "workload",
+]
+
+_TAG_SYSTEM, _TAG_CHAIN, _TAG_ENS, _TAG_LABEL = 11, 23, 37, 41
+
+
+def _rng(seed: int, tag: int) -> np.random.Generator:
+    return np.random.default_rng([int(seed), int(tag)])
+
+
+@dataclass
+class SystemParams:
+    n_beads: int
+    n_cv: int
+    seed: int
+    mass: float = 1.0
+    kT: float = 1.0
+    dt: float = 0.005
+    gamma: float = 1.0
+    bond_k: float = 100.0
+    bond_r0: float = 1.0
+    angle_k: float = 20.0
+    angle_theta0: float = math.radians(110.0)
+    lj_eps: float = 1.0
+    lj_sigma: float = 1.0
+    lj_rc: float = 2.5
+    output_freq: int = 50
+    dihedral_k: np.ndarray = field(default=None, repr=False)      # [N-3][3] f64
+    dihedral_delta: np.ndarray = field(default=None, repr=False)  # [N-3][3] f64
+    cv_atoms: np.ndarray = field(default=None, repr=False)        # [C][4] int32
+
+
+@dataclass
+class EnsembleParams:
+    n_models: int
+    n_in: int
+    n_layers: int
+    width: int
+    resnet: bool
+    weights: np.ndarray = field(repr=False)  # [M][P] float32, packed per model
+    trust_lo: float = 2.0
+    trust_hi: float = 3.0
+
+
+def evenly_spaced_cvs(n_beads: int, n_cv: int) -> np.ndarray:
+    """C torsion quadruples spread evenly along the chain."""
+    if n_beads < 4 or n_cv < 1:
+        raise ValueError("need n_beads >= 4 and n_cv >= 1")
+    nd = n_beads - 3
+    first = np.floor((np.arange(n_cv) + 0.5) * nd / n_cv).astype(np.int64)
+    return (first[:, None] + np.arange(4)[None, :]).astype(np.int32)
+
+
+def make_system(n_beads: int, n_cv: int, seed: int, **overrides) -> SystemParams:
+    sp = SystemParams(n_beads=n_beads, n_cv=n_cv, seed=seed, **overrides)
+    g = _rng(seed, _TAG_SYSTEM)
+    nd = n_beads - 3
+    sp.dihedral_k = g.uniform(0.0, 2.0, size=(nd, 3))
+    sp.dihedral_delta = g.uniform(0.0, 2.0 * math.pi, size=(nd, 3))
+    sp.cv_atoms = evenly_spaced_cvs(n_beads, n_cv)
+    return sp
+
+
+def _place_next(a, b, c, bond, theta, phi):
+    """Place a bead at distance `bond` from c, angle `theta` at c (b-c-new)
+    and dihedral `phi` for (a, b, c, new).  Vectorised over rows."""
+    bc = c - b
+    bc /= np.linalg.norm(bc, axis=-1, keepdims=True)
+    n = np.cross(b - a, bc)
+    n /= np.linalg.norm(n, axis=-1, keepdims=True)
+    m = np.cross(n, bc)
+    d2 = np.stack([-bond * np.cos(theta) * np.ones_like(phi),
+                   bond * np.sin(theta) * np.cos(phi),
+                   bond * np.sin(theta) * np.sin(phi)], axis=-1)
+    return c + d2[:, :1] * bc + d2[:, 1:2] * m + d2[:, 2:3] * n
+
+
+def _grow(n, N, r0, th, g, min_dist, max_tries):
+    """Grow n chains; returns positions and a mask of chains that got trapped."""
+    x = np.zeros((n, N, 3), dtype=np.float64)
+    x[:, 1, 0] = r0
+    if N > 2:
+        x[:, 2, 0] = r0 - r0 * math.cos(th)
+        x[:, 2, 1] = r0 * math.sin(th)
+    alive = np.ones(n, dtype=bool)
+    for i in range(3, N):
+        todo = np.flatnonzero(alive)
+        for _ in range(max_tries):
+            phi = g.uniform(-math.pi, math.pi, size=todo.size)
+            cand = _place_next(x[todo, i - 3], x[todo, i - 2], x[todo, i - 1], r0, th, phi)
+            d = np.linalg.norm(x[todo, : i - 2] - cand[:, None, :], axis=-1)
+            ok = (d >= min_dist).all(axis=1)
+            x[todo[ok], i] = cand[ok]
+            todo = todo[~ok]
+            if todo.size == 0:
+                break
+        alive[todo] = False
+    return x, alive
+
+
+def make_chains(n_walkers: int, sp: SystemParams, seed: int,
+                min_dist: float = 0.9, max_tries: int = 200) -> np.ndarray:
+    """Self-avoiding starting chains, float32 [W][N][3], centred at the origin.
+
+    Chains that get trapped while growing are regrown from scratch."""
+    N = sp.n_beads
+    g = _rng(seed, _TAG_CHAIN)
+    x = np.zeros((n_walkers, N, 3), dtype=np.float64)
+    need = np.arange(n_walkers)
+    for _ in range(100):
+        xs, ok = _grow(need.size, N, sp.bond_r0, sp.angle_theta0, g, min_dist, max_tries)
+        x[need[ok]] = xs[ok]
+        need = need[~ok]
+        if need.size == 0:
+            break
+    if need.size:
+        raise RuntimeError("chain growth kept getting trapped")
+    # a random overall orientation per walker (QR of a Gaussian matrix), centred
+    q, r = np.linalg.qr(g.standard_normal((n_walkers, 3, 3)))
+    q = q * np.sign(np.diagonal(r, axis1=1, axis2=2))[:, None, :]
+    x = np.einsum("wij,wnj->wni", q, x)
+    x -= x.mean(axis=1, keepdims=True)
+    return np.ascontiguousarray(x.astype(np.float32))
+
+
+def ensemble_param_count(n_in: int, n_layers: int, width: int) -> int:
+    """Floats per packed model: W1[H][D], b1[H], (W_l[H][H], b_l[H]) for
+    l = 2..L, w_out[H], b_out."""
+    H = width
+    return H * n_in + H + (n_layers - 1) * (H * H + H) + H + 1
+
+
+def make_ensemble(n_models: int, n_in: int, n_layers: int, width: int, seed: int,
+                  resnet: bool = False, trust_lo: float = 2.0,
+                  trust_hi: float = 3.0, bias_scale: float = 0.2) -> EnsembleParams:
+    g = _rng(seed, _TAG_ENS)
+    P = ensemble_param_count(n_in, n_layers, width)
+    out = np.empty((n_models, P), dtype=np.float32)
+    for m in range(n_models):
+        parts = []
+        fan_in = n_in
+        for _ in range(n_layers):
+            a = math.sqrt(6.0 / (fan_in + width))
+            parts.append(g.uniform(-a, a, size=(width, fan_in)).ravel())
+            parts.append(g.uniform(-bias_scale, bias_scale, size=width))
+            fan_in = width
+        a = math.sqrt(6.0 / (width + 1))
+        parts.append(g.uniform(-a, a, size=width))
+        parts.append(g.uniform(-bias_scale, bias_scale, size=1))
+        out[m] = np.concatenate(parts).astype(np.float32)
+    return EnsembleParams(n_models, n_in, n_layers, width, resnet, out, trust_lo, trust_hi)
+
+
+def make_label_targets(n_runs: int, n_cv: int, seed: int) -> np.ndarray:
+    """Restraint centres s0, uniform on the torus [-pi, pi)^C, float64 [R][C]."""
+    g = _rng(seed, _TAG_LABEL)
+    return g.uniform(-math.pi, math.pi, size=(n_runs, n_cv))
+
+
+# Workload recipes (chain length, CV count, ensemble shape, batch) -------------
+WORKLOADS = {
+    "tiny_n22": dict(n_beads=22, n_cv=2, n_models=4, n_layers=3, width=64,
+                     n_walkers=16, n_steps=2000, n_label_runs=16,
+                     label_steps=1000, kappa=50.0),
+    "chain_n200_w1024": dict(n_beads=200, n_cv=20, n_models=4, n_layers=4,
+                             width=256, n_walkers=1024, n_steps=10000),
+    "chain_n100_w8192": dict(n_beads=100, n_cv=32, n_models=8, n_layers=4,
+                             width=512, n_walkers=8192, n_steps=10000),
+}
+
+
+def workload(name: str) -> dict:
+    return dict(WORKLOADS[name])
