@@ -1,0 +1,243 @@
+/*
+ * rid.h -- C ABI of librid, a GB300 (sm_103a) implementation of the
+ * Reinforced Dynamics (RiD) biased / restrained Langevin MD step run over many
+ * walkers at once (RiD-kit, arXiv 2408.14070).
+ *
+ * Conventions for every entry point
+ *   - Return value: an rid_status code.  On failure rid_last_error() returns a
+ *     one-line message for the calling thread; no output is written unless
+ *     the call returns RID_OK (results may be partially written on
+ *     RID_ERR_NONFINITE, see below).
+ *   - Arrays are dense, C order, in the element type named.  Positions and
+ *     velocities are [walker][bead][xyz] float32.
+ *   - `mem` says where ALL array arguments of that call live: RID_MEM_HOST
+ *     (pageable or pinned host memory) or RID_MEM_DEVICE (device memory of
+ *     the current CUDA device).  The library never keeps a caller pointer
+ *     after the call returns (rid_submit is the one exception, see there).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Synchronous
+ *     calls enqueue their work on it and return after it has completed.
+ *   - The caller owns every array it passes.  The library owns the device
+ *     copies of parameters and the resident walker state it allocates.
+ *   - Units are reduced (kT, mass, length as given); angles are radians.
+ *   - Objects are not thread-safe: one thread at a time per rid_system.
+ */
+#ifndef RID_H
+#define RID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RID_API __attribute__((visibility("default")))
+#else
+#define RID_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RID_OK = 0,
+    RID_ERR_ARG = 1,        /* invalid argument (NULL, size, range)         */
+    RID_ERR_OOM = 2,        /* device allocation failed / budget exceeded    */
+    RID_ERR_CUDA = 3,       /* a CUDA runtime call failed                    */
+    RID_ERR_NONFINITE = 4,  /* NaN/Inf appeared in positions or forces       */
+    RID_ERR_TIMEOUT = 5,    /* a bounded wait expired                        */
+    RID_NOT_READY = 6,      /* rid_poll: job not finished yet                */
+    RID_ERR_STATE = 7,      /* call not valid in the object's current state  */
+    RID_ERR_CANCELLED = 8   /* job was cancelled                              */
+} rid_status;
+
+enum { RID_MEM_HOST = 0, RID_MEM_DEVICE = 1 };
+
+/* Arithmetic of the ensemble MLP.  Forces, CVs and the integrator are always
+ * FP32; label running sums and energy reductions are FP64. */
+enum { RID_PREC_FP32 = 0, RID_PREC_BF16 = 1 };
+
+/* CV force applied in rid_eval_forces. */
+enum { RID_BIAS_NONE = 0, RID_BIAS_ENSEMBLE = 1, RID_BIAS_RESTRAINT = 2 };
+
+/*
+ * A bead chain in implicit solvent (the stand-in for the paper's GROMACS
+ * systems, Sec. "Exploration phase"), its torsion CVs (Sec. "CV selection",
+ * torsion mode, periodic) and Langevin parameters.
+ *   U = sum_bonds k_b/2 (r - r0)^2 + sum_angles k_a/2 (theta - theta0)^2
+ *     + sum_dihedrals sum_{n=1..3} k_n (1 + cos(n phi - delta_n))
+ *     + sum_{|i-j|>=3, r^2 < rc^2} [4 eps ((sig/r)^12 - (sig/r)^6) - U(rc)]
+ * The LJ inclusion test r^2 < rc^2 is taken in FP32 without fused
+ * multiply-add.  Torsions use the IUPAC sign convention on [-pi, pi).
+ */
+typedef struct {
+    int32_t n_beads;              /* N, 4 <= N <= 4096                          */
+    int32_t n_cv;                 /* C, 1 <= C <= 128                           */
+    int32_t output_freq;          /* trace stride in steps (>= 1)               */
+    int32_t reserved0;            /* must be 0                                  */
+    double mass, kT, dt, gamma;   /* bead mass, thermal energy, step, friction  */
+    uint64_t seed;                /* Philox4x32-10 key                          */
+    double bond_k, bond_r0;
+    double angle_k, angle_theta0;
+    double lj_eps, lj_sigma, lj_rc;
+    const double* dihedral_k;     /* host [N-3][3]: k_1..k_3 per dihedral       */
+    const double* dihedral_delta; /* host [N-3][3]: delta_1..delta_3            */
+    const int32_t* cv_atoms;      /* host [C][4]: bead indices of each torsion  */
+} rid_system_desc;
+
+/*
+ * Ensemble of M MLPs s -> A_i(s) (Sec. "Training phase": numb_models,
+ * neurons, resnet).  Input u = (cos s_0, sin s_0, cos s_1, sin s_1, ...),
+ * D = 2C; L hidden tanh layers of width H (residual h_l = h_{l-1} + tanh(.)
+ * for l >= 2 when resnet != 0); scalar linear output.
+ * Packed FP32 weights per model, models back to back:
+ *   W_1[H][D], b_1[H], (W_l[H][H], b_l[H]) for l = 2..L, w_out[H], b_out[1].
+ * Bias (Sec. "Development of the protocol"): U_bias = -Abar (the inverted
+ * predicted PMF), applied with the switch sigma(eps) of the model deviation
+ * eps = sqrt((1/M) sum_i |dA_i/ds - Fbar|^2):
+ *   sigma = 1 (eps < trust_lo), 0 (eps >= trust_hi),
+ *           (1 + cos(pi (eps - trust_lo)/(trust_hi - trust_lo)))/2 between
+ * (trust_lvl_1 / trust_lvl_2, Sec. "Overall workflow setting"); CV force
+ * F_s = sigma(eps) Fbar with Fbar = (1/M) sum_i dA_i/ds.
+ */
+typedef struct {
+    int32_t n_models;             /* M, 1..16                                   */
+    int32_t n_in;                 /* D, must equal 2 * n_cv                     */
+    int32_t n_layers;             /* L, 1..8                                    */
+    int32_t width;                /* H, multiple of 32, 32..512                 */
+    int32_t resnet;               /* 0 / 1                                      */
+    int32_t precision;            /* RID_PREC_*                                 */
+    double trust_lo, trust_hi;    /* trust_lo < trust_hi                        */
+    const float* weights;         /* host [M][P], copied by the call            */
+} rid_ensemble_desc;
+
+typedef struct rid_system rid_system;
+
+/* Library identity and diagnostics. */
+RID_API int rid_version(void);                       /* 10000 * major + 100 * minor   */
+RID_API const char* rid_status_string(int status);
+RID_API const char* rid_last_error(void);            /* thread-local, never NULL      */
+
+/* Create a system on the current CUDA device.  Copies every array of desc.
+ * Errors: RID_ERR_ARG (bad sizes / indices), RID_ERR_OOM, RID_ERR_CUDA. */
+RID_API int rid_create_system(const rid_system_desc* desc, rid_system** out);
+/* Release the system and all device memory it owns (NULL is accepted). */
+RID_API int rid_destroy_system(rid_system* sys);
+
+/* Set (or replace) the ensemble used by biased exploration.  Copies the
+ * weights to device-resident FP32 (and BF16 for RID_PREC_BF16) tiles.
+ * Errors: RID_ERR_ARG (shape mismatch with the system's C), RID_ERR_OOM. */
+RID_API int rid_set_ensemble(rid_system* sys, const rid_ensemble_desc* desc);
+
+/*
+ * Biased exploration (Sec. "Exploration phase"): W walkers, n_steps BAOAB
+ * Langevin steps each (one force evaluation per step), starting at global
+ * step index step0 (the Philox counter; step0 + n_steps <= 2^32).  Without an
+ * ensemble the run is unbiased MD.
+ *   x0      [W][N][3]        starting positions
+ *   v0      [W][N][3]|NULL   starting velocities; NULL draws Maxwell-Boltzmann
+ *                            velocities from Philox stream 1 at step0
+ *   cv_out  [W][T][C]|NULL   CVs after steps output_freq, 2 output_freq, ...
+ *                            (T = n_steps / output_freq)
+ *   eps_out [W][T]|NULL      model deviation at the same steps
+ *   energy_out [W][T][3]|NULL  float64 (U_ff, -Abar, kinetic) at those steps
+ *   x_out, v_out [W][N][3]|NULL  final state
+ * Noise: counter (bead, walker, step, 0), key = seed; u = (word + 1/2) 2^-32;
+ * Box-Muller on words (0,1) -> xi_x, xi_y and (2,3) -> xi_z.
+ * Errors: RID_ERR_ARG, RID_ERR_OOM, RID_ERR_CUDA, RID_ERR_NONFINITE (the run
+ * completed but some walker produced NaN/Inf; outputs are written).
+ */
+RID_API int rid_explore(rid_system* sys, int32_t n_walkers, const float* x0, const float* v0,
+                uint64_t step0, int64_t n_steps, float* cv_out, float* eps_out,
+                double* energy_out, float* x_out, float* v_out, int32_t mem, void* stream);
+
+/*
+ * Restrained-MD labelling (Sec. "Labeling phase", restrained method): R runs,
+ * each with harmonic restraints U_r = sum_j kappa_j/2 wrap(s_j - s0_j)^2 on
+ * every CV and no ensemble bias.  After n_equil steps every step contributes
+ * d = wrap(s - s0) (wrap onto [-pi, pi)) to FP64 running sums on the device.
+ *   s0, kappa [R][C] float64     restraint centres and force constants
+ *   mf_out    [R][C] float64     mean force -kappa <d>
+ *   se_out    [R][C] float64     standard error from n_blocks equal blocks:
+ *                                kappa std_{ddof=1}(block means)/sqrt(B);
+ *                                sample k of K goes to block floor(k B / K)
+ *   std_out   [R][C] float64     population std of kappa d
+ * Requires 2 <= n_blocks <= 256 and n_steps - n_equil >= n_blocks.
+ */
+RID_API int rid_label(rid_system* sys, int32_t n_runs, const float* x0, const float* v0,
+              const double* s0, const double* kappa, uint64_t step0, int64_t n_steps,
+              int64_t n_equil, int32_t n_blocks, double* mf_out, double* se_out, double* std_out,
+              float* x_out, float* v_out, int32_t mem, void* stream);
+
+/*
+ * One force evaluation at given positions (no integration), through the same
+ * kernels as a step.  bias = RID_BIAS_*; s0/kappa [W][C] are read only for
+ * RID_BIAS_RESTRAINT.
+ *   f_out [W][N][3] float32   total force (force field + CV force)
+ *   s_out [W][C], eps_out [W], abar_out [W], grad_out [M][W][C] (dA_i/ds),
+ *   all float32 and optional (NULL).
+ */
+RID_API int rid_eval_forces(rid_system* sys, int32_t n_walkers, const float* x, int32_t bias,
+                    const double* s0, const double* kappa, float* f_out, float* s_out,
+                    float* eps_out, float* abar_out, float* grad_out, int32_t mem, void* stream);
+
+/*
+ * LJ pair inclusion of the force kernel, as a bit mask: bit (j & 31) of word
+ * [w][i][j >> 5] is set iff the pair (i, j) interacts (|i-j| >= 3 and FP32
+ * r^2 < rc^2).  mask_out [W][N][ceil(N/32)] uint32.
+ */
+RID_API int rid_pair_mask(rid_system* sys, int32_t n_walkers, const float* x, uint32_t* mask_out,
+                  int32_t mem, void* stream);
+
+/*
+ * The integrator's random numbers for n given counters (bead, walker, step,
+ * stream) under key `seed`: the Philox4x32-10 words (out_words [n][4] uint32)
+ * and the three normals built from them (out_normals [n][3] float32).
+ */
+RID_API int rid_philox(int64_t n, const uint32_t* counters, uint64_t seed, uint32_t* out_words,
+               float* out_normals, int32_t mem, void* stream);
+
+
+/*
+ * Resident walkers.  rid_explore is load + advance + read in one call; these
+ * three let a caller keep the walker state on the device across calls (the
+ * state lives in the system object; one walker set per system).
+ *
+ * rid_walkers_load: copy W walkers in (v0 NULL: Maxwell-Boltzmann draw at
+ *   step0), set the global step counter to step0 and evaluate the forces at
+ *   x0.  Synchronous.
+ * rid_walkers_advance: n_steps biased (or, without an ensemble, unbiased)
+ *   BAOAB steps from the resident state; traces as in rid_explore with
+ *   T = n_steps / output_freq counted from the start of this call.  With
+ *   mem = RID_MEM_DEVICE (or no trace outputs) the call only enqueues work on
+ *   `stream` and returns; with host trace outputs it waits for completion.
+ *   Non-finite results are reported by the next rid_walkers_read.
+ * rid_walkers_read: wait for `stream`, copy positions / velocities out (either
+ *   may be NULL), return the next global step index in *step_next (may be
+ *   NULL), and report RID_ERR_NONFINITE if any walker went non-finite since
+ *   the last load.
+ */
+RID_API int rid_walkers_load(rid_system* sys, int32_t n_walkers, const float* x0, const float* v0,
+                             uint64_t step0, int32_t mem, void* stream);
+RID_API int rid_walkers_advance(rid_system* sys, int64_t n_steps, float* cv_out, float* eps_out,
+                                double* energy_out, int32_t mem, void* stream);
+RID_API int rid_walkers_read(rid_system* sys, float* x_out, float* v_out, uint64_t* step_next,
+                             int32_t mem, void* stream);
+
+/*
+ * Kernel timing for this system: while enabled, every kernel the system
+ * launches is bracketed by CUDA events on its launch stream.  Enabling resets
+ * the record.  rid_profile_read waits for the recorded events and returns, per
+ * kernel name (in first-launch order, at most max_kernels), the summed
+ * device time in milliseconds and the launch count; names_out receives
+ * max_kernels slots of 48 bytes (NUL-terminated).  *n_kernels is the number
+ * of distinct kernels recorded.  rid_launch_count returns the number of
+ * kernels this system has launched since it was created.
+ */
+RID_API int rid_profile_enable(rid_system* sys, int32_t enable);
+RID_API int rid_profile_read(rid_system* sys, int32_t max_kernels, char* names_out, double* total_ms,
+                             int64_t* launches, int32_t* n_kernels);
+RID_API int64_t rid_launch_count(rid_system* sys);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RID_H */

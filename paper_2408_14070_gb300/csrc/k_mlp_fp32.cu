@@ -1,0 +1,198 @@
+// k_mlp_fp32.cu -- plain FP32 (SIMT) ensemble MLP: forward pass and
+// reverse-mode input gradient for every member on a tile of 32 walkers.
+//
+// Grid (ceil(W/32), M), 128 threads.  Each warp owns 8 walkers, each lane a
+// stripe of neurons n = nb + lane + 32 kk (kk < 8), so a thread keeps an
+// 8 x 8 register tile.  Activations live in shared memory transposed as
+// [neuron][walker] rows of 36 floats (32 walkers + 4 pad: 16-byte aligned
+// rows whose float4 stores by 8 consecutive lanes hit distinct banks).
+// Weights stream from L2 through the read-only path, coalesced along the
+// output neuron (forward reads W^T [in][out], backward reads W [out][in]).
+// tanh(z_l) of every layer is kept in a global scratch [M][tile][L][32][H]
+// (L2-resident at the sizes used) for the backward pass:
+//   g_L = w_out,  delta_l = g_l * (1 - tanh^2 z_l),
+//   g_{l-1} = W_l^T delta_l (+ g_l for a residual layer),
+//   dA/ds_j = -sin s_j g_0[2j] + cos s_j g_0[2j+1].
+#include "rid_internal.cuh"
+
+namespace {
+
+constexpr int TW = 32;    // walkers per CTA
+constexpr int ROW = 36;   // shared row stride in floats
+constexpr int NT = 128;   // threads per CTA
+
+// acc[i][kk] += sum_k in[k][8 warp + i] * Wg[k * ldw + nb + lane + 32 kk]
+__device__ __forceinline__ void tile_gemm(const float* __restrict__ in, int K, const float* __restrict__ Wg, int ldw,
+                                          int N, int nb, int warp, int lane, float (&acc)[8][8]) {
+    bool ok[8];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) ok[kk] = nb + lane + 32 * kk < N;
+    const float* wp = Wg + nb + lane;
+#pragma unroll 2
+    for (int k = 0; k < K; ++k) {
+        const float4 a0 = *reinterpret_cast<const float4*>(in + k * ROW + 8 * warp);
+        const float4 a1 = *reinterpret_cast<const float4*>(in + k * ROW + 8 * warp + 4);
+        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        float wv[8];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) wv[kk] = ok[kk] ? __ldg(wp + (size_t)k * ldw + 32 * kk) : 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) acc[i][kk] = fmaf(a[i], wv[kk], acc[i][kk]);
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_mlp_fp32(EnsDev E, StateDev st, int W, int C) {
+    extern __shared__ __align__(16) float sm[];
+    const int D = E.D, L = E.L, H = E.H, M = E.M;
+    const int Kmax = H > D ? H : D;
+    float* bufA = sm;
+    float* bufB = bufA + Kmax * ROW;
+    float* ubuf = bufB + Kmax * ROW;
+    const int m = blockIdx.y, tile = blockIdx.x, ntiles = gridDim.x;
+    const int w0 = tile * TW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float* Wm = E.W + (size_t)m * E.wstride;
+    const float* WTm = E.WT + (size_t)m * E.wstride;
+    float* hs = st.hs + ((size_t)m * ntiles + tile) * (size_t)L * TW * H;
+
+    for (int idx = threadIdx.x; idx < D * TW; idx += NT) {
+        const int wl = idx / D, k = idx - wl * D;
+        ubuf[k * ROW + wl] = (w0 + wl < W) ? st.u[(size_t)(w0 + wl) * D + k] : 0.0f;
+    }
+    __syncthreads();
+
+    // ---------------- forward
+    const float* in = ubuf;
+    float* out = bufA;
+    for (int l = 0; l < L; ++l) {
+        const int K = l == 0 ? D : H;
+        const float* Wt = WTm + E.loff[l];
+        const float* bias = E.b + ((size_t)m * L + l) * H;
+        for (int nb = 0; nb < H; nb += 256) {
+            float acc[8][8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) acc[i][kk] = 0.0f;
+            tile_gemm(in, K, Wt, H, H, nb, warp, lane, acc);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const int n = nb + lane + 32 * kk;
+                if (n < H) {
+                    const float bn = bias[n];
+                    float h[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float t = tanhf(acc[i][kk] + bn);
+                        hs[((size_t)l * TW + 8 * warp + i) * H + n] = t;
+                        h[i] = (E.resnet && l > 0) ? t + in[n * ROW + 8 * warp + i] : t;
+                    }
+                    *reinterpret_cast<float4*>(out + n * ROW + 8 * warp) = make_float4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<float4*>(out + n * ROW + 8 * warp + 4) = make_float4(h[4], h[5], h[6], h[7]);
+                }
+            }
+        }
+        __syncthreads();
+        in = out;
+        out = (out == bufA) ? bufB : bufA;
+    }
+    // value A = w_out . h_L + b_out
+    {
+        const float* wo = E.wout + (size_t)m * H;
+        float part[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int n = lane; n < H; n += 32) {
+            const float wn = wo[n];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) part[i] = fmaf(wn, in[n * ROW + 8 * warp + i], part[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part[i] += __shfl_xor_sync(0xffffffffu, part[i], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int wg = w0 + 8 * warp + i;
+                if (wg < W) st.Aval[(size_t)m * W + wg] = part[i] + E.bout[m];
+            }
+        }
+    }
+    // ---------------- backward: G holds g_l, Dl holds delta_l
+    float* G = (in == bufA) ? bufB : bufA;   // free buffer
+    float* Dl = (float*)in;                  // h_L no longer needed
+    {
+        const float* wo = E.wout + (size_t)m * H;
+        for (int idx = threadIdx.x; idx < H * TW; idx += NT) {
+            const int n = idx / TW, wl = idx - n * TW;
+            G[n * ROW + wl] = wo[n];
+        }
+    }
+    __syncthreads();
+    for (int l = L - 1; l >= 0; --l) {
+        const int K = H, Nout = l == 0 ? D : H;
+        // delta_l = g_l * (1 - t_l^2)
+        for (int idx = threadIdx.x; idx < H * TW; idx += NT) {
+            const int wl = idx / H, n = idx - wl * H;
+            const float t = hs[((size_t)l * TW + wl) * H + n];
+            Dl[n * ROW + wl] = G[n * ROW + wl] * (1.0f - t * t);
+        }
+        __syncthreads();
+        const float* Wl = Wm + E.loff[l];   // [H][fin] row-major = [K][Nout]
+        const bool res = E.resnet && l > 0;
+        float accs[8][8];
+        for (int nb = 0; nb < Nout; nb += 256) {
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const int n = nb + lane + 32 * kk;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) accs[i][kk] = (res && n < Nout) ? G[n * ROW + 8 * warp + i] : 0.0f;
+            }
+            tile_gemm(Dl, K, Wl, Nout, Nout, nb, warp, lane, accs);
+            __syncthreads();   // every thread has read G for its initial values
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const int n = nb + lane + 32 * kk;
+                if (n < Nout) {
+                    *reinterpret_cast<float4*>(G + n * ROW + 8 * warp) =
+                        make_float4(accs[0][kk], accs[1][kk], accs[2][kk], accs[3][kk]);
+                    *reinterpret_cast<float4*>(G + n * ROW + 8 * warp + 4) =
+                        make_float4(accs[4][kk], accs[5][kk], accs[6][kk], accs[7][kk]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // dA/ds_j = -sin s_j g0[2j] + cos s_j g0[2j+1]
+    for (int idx = threadIdx.x; idx < C * TW; idx += NT) {
+        const int wl = idx / C, j = idx - wl * C;
+        const int wg = w0 + wl;
+        if (wg < W) {
+            const float cs = ubuf[(2 * j) * ROW + wl], sn = ubuf[(2 * j + 1) * ROW + wl];
+            const float g = -sn * G[(2 * j) * ROW + wl] + cs * G[(2 * j + 1) * ROW + wl];
+            st.gradA[((size_t)m * W + wg) * C + j] = g;
+        }
+    }
+    (void)M;
+}
+
+}  // namespace
+
+size_t rid_mlp_fp32_scratch_floats(int W, int M, int L, int H) {
+    const size_t ntiles = (size_t)(W + TW - 1) / TW;
+    return (size_t)M * ntiles * L * TW * H;
+}
+
+void rid_launch_mlp_fp32(const EnsDev& E, StateDev st, int W, int C, cudaStream_t s) {
+    const int Kmax = E.H > E.D ? E.H : E.D;
+    const size_t sm = sizeof(float) * ((size_t)2 * Kmax * ROW + (size_t)E.D * ROW);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    dim3 grid((W + TW - 1) / TW, E.M);
+    k_mlp_fp32<<<grid, NT, sm, s>>>(E, st, W, C);
+}

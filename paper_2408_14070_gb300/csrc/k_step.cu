@@ -1,0 +1,488 @@
+// k_step.cu -- per-walker kernels of the RiD Langevin step on sm_103a.
+//
+// One CTA owns one walker (bead chain) for the whole evaluation: the chain's
+// positions are staged once in shared memory and every force term reads them
+// from there.  All sums are taken in a fixed order, so results are
+// bit-reproducible run to run.
+//
+//   k_force_cv  : [B A O A of BAOAB] + force field (bonds, angles, dihedrals,
+//                 all-pairs Lennard-Jones) + torsion CVs and their Jacobians
+//   k_finish    : CV force (ensemble bias with the trust-level switch, or a
+//                 harmonic restraint with FP64 label sums) chain-ruled to the
+//                 beads + the closing B half-kick + trace output
+#include <math.h>
+
+#include "rid_internal.cuh"
+
+namespace {
+
+
+__global__ void k_pack(const float* __restrict__ src, float4* __restrict__ dst, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = make_float4(src[3 * i], src[3 * i + 1], src[3 * i + 2], 0.0f);
+}
+
+__global__ void k_unpack(const float4* __restrict__ src, float* __restrict__ dst, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const float4 a = src[i];
+        dst[3 * i] = a.x;
+        dst[3 * i + 1] = a.y;
+        dst[3 * i + 2] = a.z;
+    }
+}
+
+// Maxwell-Boltzmann velocities: Philox stream 1 at counter (bead, walker, step0, 1).
+__global__ void k_mb(SysDev S, StateDev st, int W, uint32_t step0) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)W * S.N) return;
+    const int w = (int)(idx / S.N), i = (int)(idx % S.N);
+    const float3 z = rid_normals3(rid_philox(make_uint4(i, w, step0, 1u), S.key0, S.key1));
+    st.v[idx] = make_float4(S.sd_mb * z.x, S.sd_mb * z.y, S.sd_mb * z.z, 0.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Bonded terms, gathered per bead (each term is evaluated by every bead it
+// touches, which keeps the sums ordered and needs no atomics).
+
+// Force on p from the harmonic bond p-q.
+__device__ __forceinline__ float3 bond_force(const SysDev& S, float3 p, float3 q) {
+    const float3 d = q - p;
+    const float r = sqrtf(dot3(d, d));
+    return (S.kb * (r - S.r0) / r) * d;
+}
+
+// Harmonic angle a-c-b (vertex c): forces on a, c, b.
+__device__ __forceinline__ void angle_forces(const SysDev& S, float3 pa, float3 pc, float3 pb, float3& fa,
+                                             float3& fc, float3& fb) {
+    const float3 a = pa - pc, b = pb - pc;
+    const float3 axb = cross3(a, b);
+    const float cr = sqrtf(dot3(axb, axb)), dp = dot3(a, b);
+    const float th = atan2f(cr, dp);
+    const float dU = S.ka * (th - S.th0);
+    const float ia = 1.0f / cr;
+    const float3 ga = ia * ((dp / dot3(a, a)) * a - b);   // d theta / d a
+    const float3 gb = ia * ((dp / dot3(b, b)) * b - a);   // d theta / d b
+    fa = (-dU) * ga;
+    fb = (-dU) * gb;
+    fc = dU * (ga + gb);
+}
+
+// Dihedral k (beads k..k+3): -dU/dphi and the torsion gradient.
+__device__ __forceinline__ float dihedral_mdU(const SysDev& S, int k, float phi) {
+    const float* p = S.dih + 6 * k;
+    float m = 0.0f;
+#pragma unroll
+    for (int n = 1; n <= 3; ++n) m = fmaf((float)n * p[n - 1], sinf((float)n * phi - p[2 + n]), m);
+    return m;   // -dU/dphi = sum_n n k_n sin(n phi - delta_n)
+}
+
+__device__ __forceinline__ float dihedral_energy(const SysDev& S, int k, float phi) {
+    const float* p = S.dih + 6 * k;
+    float e = 0.0f;
+#pragma unroll
+    for (int n = 1; n <= 3; ++n) e += p[n - 1] * (1.0f + cosf((float)n * phi - p[2 + n]));
+    return e;
+}
+
+__device__ float3 bonded_force_on(const SysDev& S, const float4* xs, int i) {
+    const int N = S.N;
+    const float3 xi = f3(xs[i]);
+    float3 f = make_float3(0.f, 0.f, 0.f);
+    if (i > 0) f = f + bond_force(S, xi, f3(xs[i - 1]));
+    if (i + 1 < N) f = f + bond_force(S, xi, f3(xs[i + 1]));
+    float3 fa, fc, fb;
+    if (i + 2 < N) { angle_forces(S, xi, f3(xs[i + 1]), f3(xs[i + 2]), fa, fc, fb); f = f + fa; }
+    if (i >= 1 && i + 1 < N) { angle_forces(S, f3(xs[i - 1]), xi, f3(xs[i + 1]), fa, fc, fb); f = f + fc; }
+    if (i >= 2) { angle_forces(S, f3(xs[i - 2]), f3(xs[i - 1]), xi, fa, fc, fb); f = f + fb; }
+    const int d0 = i - 3 > 0 ? i - 3 : 0;
+    const int d1 = i < N - 4 ? i : N - 4;
+    for (int k = d0; k <= d1; ++k) {
+        float3 g[4];
+        const float phi = rid_torsion(f3(xs[k]), f3(xs[k + 1]), f3(xs[k + 2]), f3(xs[k + 3]), g);
+        const int q = i - k;   // select without a dynamic index (keeps g in registers)
+        const float3 gq = q == 0 ? g[0] : (q == 1 ? g[1] : (q == 2 ? g[2] : g[3]));
+        f = f + dihedral_mdU(S, k, phi) * gq;
+    }
+    return f;
+}
+
+// Energy of the bonded terms that start at bead i (bond i,i+1; angle i..i+2;
+// dihedral i..i+3), so that every term is counted once.
+__device__ double bonded_energy_from(const SysDev& S, const float4* xs, int i) {
+    const int N = S.N;
+    double e = 0.0;
+    const float3 xi = f3(xs[i]);
+    if (i + 1 < N) {
+        const float3 d = f3(xs[i + 1]) - xi;
+        const float dr = sqrtf(dot3(d, d)) - S.r0;
+        e += 0.5 * S.kb * (double)dr * dr;
+    }
+    if (i + 2 < N) {
+        const float3 a = xi - f3(xs[i + 1]), b = f3(xs[i + 2]) - f3(xs[i + 1]);
+        const float3 axb = cross3(a, b);
+        const float dth = atan2f(sqrtf(dot3(axb, axb)), dot3(a, b)) - S.th0;
+        e += 0.5 * S.ka * (double)dth * dth;
+    }
+    if (i + 3 < N) {
+        const float phi = rid_torsion(xi, f3(xs[i + 1]), f3(xs[i + 2]), f3(xs[i + 3]), nullptr);
+        e += dihedral_energy(S, i, phi);
+    }
+    return e;
+}
+
+// Pair inclusion: |i-j| >= 3 and r^2 < rc^2 with r^2 formed in FP32 without
+// fused multiply-add, ((dx dx + dy dy) + dz dz).
+__device__ __forceinline__ float pair_r2(float3 d) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(d.x, d.x), __fmul_rn(d.y, d.y)), __fmul_rn(d.z, d.z));
+}
+
+// Lennard-Jones force on bead i from every other bead (both orders of each
+// pair are evaluated, one per owning thread).
+template <bool ENERGY>
+__device__ __forceinline__ float3 lj_force_on(const SysDev& S, const float4* xs, int i, double& e) {
+    const float3 xi = f3(xs[i]);
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    float el = 0.f;
+    const int N = S.N;
+#pragma unroll 4
+    for (int j = 0; j < N; ++j) {
+        const float4 xj = xs[j];
+        const float3 d = make_float3(xj.x - xi.x, xj.y - xi.y, xj.z - xi.z);
+        const float r2 = pair_r2(d);
+        const bool inc = (r2 < S.rc2) && (j - i > 2 || i - j > 2);
+        const float inv = __fdividef(1.0f, r2);
+        const float sr2 = S.sig2 * inv;
+        const float sr6 = sr2 * sr2 * sr2;
+        float c = S.lj_eps24 * inv * sr6 * (2.0f * sr6 - 1.0f);
+        c = inc ? c : 0.0f;
+        fx = fmaf(-c, d.x, fx);
+        fy = fmaf(-c, d.y, fy);
+        fz = fmaf(-c, d.z, fz);
+        if (ENERGY) el += inc ? (S.lj_eps4 * sr6 * (sr6 - 1.0f) - S.urc) : 0.0f;
+    }
+    if (ENERGY) e += 0.5 * (double)el;
+    return make_float3(fx, fy, fz);
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum_ordered(T v, T* red) {
+    // fixed-shape tree: warp shuffles, then warp 0 over the warp partials
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    T r = 0;
+    if (warp == 0) {
+        r = lane < nw ? red[lane] : (T)0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;   // valid in warp 0
+}
+
+// ---------------------------------------------------------------------------
+template <bool INTEGRATE, bool ENERGY>
+__global__ void __launch_bounds__(256) k_force_cv(SysDev S, StateDev st, uint32_t step) {
+    extern __shared__ float4 xs[];
+    __shared__ double red[32];
+    const int w = blockIdx.x, N = S.N, C = S.C;
+    const long long base = (long long)w * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        float4 x = st.x[base + i];
+        if (INTEGRATE) {
+            float4 v = st.v[base + i];
+            const float4 f = st.f[base + i];
+            const float kick = S.half_dt * S.inv_mass;
+            v.x = fmaf(kick, f.x, v.x);             // B
+            v.y = fmaf(kick, f.y, v.y);
+            v.z = fmaf(kick, f.z, v.z);
+            x.x = fmaf(S.half_dt, v.x, x.x);        // A
+            x.y = fmaf(S.half_dt, v.y, x.y);
+            x.z = fmaf(S.half_dt, v.z, x.z);
+            if (S.c2 != 0.0f) {                     // O
+                const float3 z = rid_normals3(rid_philox(make_uint4(i, w, step, 0u), S.key0, S.key1));
+                v.x = fmaf(S.c1, v.x, S.c2 * z.x);
+                v.y = fmaf(S.c1, v.y, S.c2 * z.y);
+                v.z = fmaf(S.c1, v.z, S.c2 * z.z);
+            }
+            x.x = fmaf(S.half_dt, v.x, x.x);        // A
+            x.y = fmaf(S.half_dt, v.y, x.y);
+            x.z = fmaf(S.half_dt, v.z, x.z);
+            st.x[base + i] = x;
+            st.v[base + i] = v;
+        }
+        xs[i] = x;
+    }
+    __syncthreads();
+    double e = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const float3 fb = bonded_force_on(S, xs, i);
+        const float3 fl = lj_force_on<ENERGY>(S, xs, i, e);
+        st.fff[base + i] = make_float4(fb.x + fl.x, fb.y + fl.y, fb.z + fl.z, 0.0f);
+        if (ENERGY) e += bonded_energy_from(S, xs, i);
+    }
+    for (int j = threadIdx.x; j < C; j += blockDim.x) {
+        const int4 q = S.cv[j];
+        float3 g[4];
+        const float s = rid_torsion(f3(xs[q.x]), f3(xs[q.y]), f3(xs[q.z]), f3(xs[q.w]), g);
+        const long long o = (long long)w * C + j;
+        st.s[o] = s;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) st.J[o * 4 + a] = make_float4(g[a].x, g[a].y, g[a].z, 0.0f);
+        float sn, cs;
+        sincosf(s, &sn, &cs);
+        st.u[(long long)w * 2 * C + 2 * j] = cs;
+        st.u[(long long)w * 2 * C + 2 * j + 1] = sn;
+    }
+    if (ENERGY) {
+        const double tot = block_sum_ordered<double>(e, red);
+        if (threadIdx.x == 0) st.eff[w] = tot;
+    }
+}
+
+// Pair-inclusion bit mask of the force kernel's LJ loop.
+__global__ void __launch_bounds__(256) k_pair_mask(SysDev S, StateDev st, uint32_t* __restrict__ mask) {
+    extern __shared__ float4 xs[];
+    const int w = blockIdx.x, N = S.N, nw = (N + 31) >> 5;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) xs[i] = st.x[(long long)w * N + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const float3 xi = f3(xs[i]);
+        for (int jw = 0; jw < nw; ++jw) {
+            uint32_t bits = 0;
+            for (int b = 0; b < 32; ++b) {
+                const int j = jw * 32 + b;
+                if (j >= N) break;
+                const float4 xj = xs[j];
+                const float r2 = pair_r2(make_float3(xj.x - xi.x, xj.y - xi.y, xj.z - xi.z));
+                if ((r2 < S.rc2) && (j - i > 2 || i - j > 2)) bits |= 1u << b;
+            }
+            mask[((long long)w * N + i) * nw + jw] = bits;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Closing half of the step.  MODE: 0 no CV force, 1 ensemble bias, 2 restraint.
+template <int MODE, bool KICK, bool ENERGY>
+__global__ void __launch_bounds__(256) k_finish(SysDev S, StateDev st, EnsDev E, LabelDev lab, long long t,
+                                                int slot, float* __restrict__ cv_out,
+                                                float* __restrict__ eps_out, double* __restrict__ energy_out,
+                                                long long T) {
+    __shared__ float Fs[RID_MAX_CV];
+    __shared__ float s_eps, s_abar;
+    __shared__ double red[32];
+    const int w = blockIdx.x, N = S.N, C = S.C, W = st.W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (MODE == 1) {
+        if (warp == 0) {
+            const float invM = 1.0f / (float)E.M;
+            float d2 = 0.0f;
+            for (int j = lane; j < C; j += 32) {
+                float fb = 0.0f;
+                for (int m = 0; m < E.M; ++m) fb += st.gradA[((long long)m * W + w) * C + j];
+                fb *= invM;
+                for (int m = 0; m < E.M; ++m) {
+                    const float d = st.gradA[((long long)m * W + w) * C + j] - fb;
+                    d2 = fmaf(d, d, d2);
+                }
+                Fs[j] = fb;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+            const float eps = sqrtf(d2 * invM);
+            float sig;
+            if (eps < E.e0) sig = 1.0f;
+            else if (eps >= E.e1) sig = 0.0f;
+            else sig = 0.5f * (1.0f + cospif((eps - E.e0) / (E.e1 - E.e0)));
+            __syncwarp();
+            for (int j = lane; j < C; j += 32) Fs[j] *= sig;
+            if (lane == 0) {
+                float ab = 0.0f;
+                for (int m = 0; m < E.M; ++m) ab += st.Aval[(long long)m * W + w];
+                s_abar = ab * invM;
+                s_eps = eps;
+                st.eps[w] = eps;
+            }
+        }
+    } else if (MODE == 2) {
+        const bool sample = KICK && t >= lab.n_equil;
+        long long b = 0;
+        if (sample) b = ((t - lab.n_equil) * lab.B) / lab.K;
+        for (int j = threadIdx.x; j < C; j += blockDim.x) {
+            const long long o = (long long)w * C + j;
+            const double d = rid_wrapd((double)st.s[o] - lab.s0[o]);
+            Fs[j] = (float)(-lab.kappa[o] * d);
+            if (sample) {
+                lab.sum[o] += d;
+                lab.sum2[o] = fma(d, d, lab.sum2[o]);
+                lab.bsum[o * lab.B + b] += d;
+            }
+        }
+        if (threadIdx.x == 0) { s_eps = 0.0f; s_abar = 0.0f; }
+    } else {
+        for (int j = threadIdx.x; j < C; j += blockDim.x) Fs[j] = 0.0f;
+        if (threadIdx.x == 0) { s_eps = 0.0f; s_abar = 0.0f; }
+    }
+    __syncthreads();
+    const long long base = (long long)w * N;
+    const float kick = S.half_dt * S.inv_mass;
+    double ke = 0.0;
+    int bad = 0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        float4 f = st.fff[base + i];
+        for (int e = S.acv_off[i]; e < S.acv_off[i + 1]; ++e) {
+            const int2 ja = S.acv[e];
+            const float4 g = st.J[((long long)w * C + ja.x) * 4 + ja.y];
+            const float fs = Fs[ja.x];
+            f.x = fmaf(fs, g.x, f.x);
+            f.y = fmaf(fs, g.y, f.y);
+            f.z = fmaf(fs, g.z, f.z);
+        }
+        st.f[base + i] = f;
+        bad |= !(isfinite(f.x) && isfinite(f.y) && isfinite(f.z));
+        if (KICK) {
+            float4 v = st.v[base + i];
+            v.x = fmaf(kick, f.x, v.x);
+            v.y = fmaf(kick, f.y, v.y);
+            v.z = fmaf(kick, f.z, v.z);
+            st.v[base + i] = v;
+            bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z));
+            if (ENERGY) ke += 0.5 / (double)S.inv_mass * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+        }
+    }
+    if (bad) st.flags[w] = 1;
+    if (slot >= 0) {
+        if (cv_out)
+            for (int j = threadIdx.x; j < C; j += blockDim.x)
+                cv_out[((long long)w * T + slot) * C + j] = st.s[(long long)w * C + j];
+        if (eps_out && threadIdx.x == 0) eps_out[(long long)w * T + slot] = s_eps;
+    }
+    if (ENERGY) {
+        const double kt = block_sum_ordered<double>(ke, red);
+        if (threadIdx.x == 0 && slot >= 0 && energy_out) {
+            double* e = energy_out + ((long long)w * T + slot) * 3;
+            e[0] = st.eff[w];
+            e[1] = (MODE == 1) ? -(double)s_abar : 0.0;
+            e[2] = kt;
+        }
+    }
+}
+
+__global__ void k_label_final(LabelDev lab, int W, int C, double* __restrict__ mf, double* __restrict__ se,
+                              double* __restrict__ sd) {
+    const long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= (long long)W * C) return;
+    const double K = (double)lab.K, kap = lab.kappa[o];
+    const double mean = lab.sum[o] / K;
+    double var = lab.sum2[o] / K - mean * mean;
+    if (var < 0) var = 0;
+    const int B = lab.B;
+    double bm_mean = 0.0;
+    for (int b = 0; b < B; ++b) {
+        const long long lo = (b * lab.K + B - 1) / B, hi = ((b + 1) * lab.K + B - 1) / B;
+        bm_mean += lab.bsum[o * B + b] / (double)(hi - lo) / B;
+    }
+    double ss = 0.0;
+    for (int b = 0; b < B; ++b) {
+        const long long lo = (b * lab.K + B - 1) / B, hi = ((b + 1) * lab.K + B - 1) / B;
+        const double d = lab.bsum[o * B + b] / (double)(hi - lo) - bm_mean;
+        ss += d * d;
+    }
+    mf[o] = -kap * mean;
+    se[o] = kap * sqrt(ss / (B - 1) / B);
+    sd[o] = kap * sqrt(var);
+}
+
+__global__ void k_philox(long long n, const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t k1,
+                         uint32_t* __restrict__ words, float* __restrict__ normals) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+    const uint4 o = rid_philox(c, k0, k1);
+    if (words) {
+        words[4 * i] = o.x;
+        words[4 * i + 1] = o.y;
+        words[4 * i + 2] = o.z;
+        words[4 * i + 3] = o.w;
+    }
+    if (normals) {
+        const float3 z = rid_normals3(o);
+        normals[3 * i] = z.x;
+        normals[3 * i + 1] = z.y;
+        normals[3 * i + 2] = z.z;
+    }
+}
+
+inline int chain_threads(int N) {
+    int t = ((N + 31) / 32) * 32;
+    return t > 256 ? 256 : (t < 32 ? 32 : t);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+void rid_launch_pack(const float* src, float4* dst, long long n, cudaStream_t s) {
+    if (n > 0) k_pack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
+}
+void rid_launch_unpack(const float4* src, float* dst, long long n, cudaStream_t s) {
+    if (n > 0) k_unpack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
+}
+void rid_launch_mb(const SysDev& S, StateDev st, int W, uint32_t step0, cudaStream_t s) {
+    const long long n = (long long)W * S.N;
+    if (n > 0) k_mb<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S, st, W, step0);
+}
+void rid_launch_force_cv(const SysDev& S, StateDev st, int W, bool integrate, bool energy, uint32_t step,
+                         cudaStream_t s) {
+    const int th = chain_threads(S.N);
+    const size_t sm = sizeof(float4) * (size_t)S.N;
+    if (integrate) {
+        if (energy) k_force_cv<true, true><<<W, th, sm, s>>>(S, st, step);
+        else k_force_cv<true, false><<<W, th, sm, s>>>(S, st, step);
+    } else {
+        if (energy) k_force_cv<false, true><<<W, th, sm, s>>>(S, st, step);
+        else k_force_cv<false, false><<<W, th, sm, s>>>(S, st, step);
+    }
+}
+void rid_launch_pair_mask(const SysDev& S, StateDev st, int W, uint32_t* mask, cudaStream_t s) {
+    k_pair_mask<<<W, chain_threads(S.N), sizeof(float4) * (size_t)S.N, s>>>(S, st, mask);
+}
+
+template <int MODE>
+static void launch_finish_mode(const SysDev& S, StateDev st, const EnsDev& E, const LabelDev& L, int W, bool kick,
+                               bool energy, long long t, int slot, float* cv, float* eps, double* en, long long T,
+                               cudaStream_t s) {
+    const int th = chain_threads(S.N);
+    if (kick) {
+        if (energy) k_finish<MODE, true, true><<<W, th, 0, s>>>(S, st, E, L, t, slot, cv, eps, en, T);
+        else k_finish<MODE, true, false><<<W, th, 0, s>>>(S, st, E, L, t, slot, cv, eps, en, T);
+    } else {
+        k_finish<MODE, false, false><<<W, th, 0, s>>>(S, st, E, L, t, slot, cv, eps, en, T);
+    }
+}
+
+void rid_launch_finish(const SysDev& S, StateDev st, const EnsDev* E, const LabelDev* lab, int W, int mode,
+                       bool kick, long long t, int slot, float* cv_out, float* eps_out, double* energy_out,
+                       long long T, cudaStream_t s) {
+    EnsDev e{};
+    LabelDev l{};
+    if (E) e = *E;
+    if (lab) l = *lab;
+    const bool energy = energy_out != nullptr && slot >= 0;
+    if (mode == 1) launch_finish_mode<1>(S, st, e, l, W, kick, energy, t, slot, cv_out, eps_out, energy_out, T, s);
+    else if (mode == 2) launch_finish_mode<2>(S, st, e, l, W, kick, energy, t, slot, cv_out, eps_out, energy_out, T, s);
+    else launch_finish_mode<0>(S, st, e, l, W, kick, energy, t, slot, cv_out, eps_out, energy_out, T, s);
+}
+
+void rid_launch_label_final(const LabelDev& lab, int W, int C, double* mf, double* se, double* sd, cudaStream_t s) {
+    const long long n = (long long)W * C;
+    if (n > 0) k_label_final<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(lab, W, C, mf, se, sd);
+}
+
+void rid_launch_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* words, float* normals,
+                       cudaStream_t s) {
+    if (n > 0) k_philox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, ctr, k0, k1, words, normals);
+}

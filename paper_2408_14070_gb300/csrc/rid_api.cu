@@ -1,0 +1,741 @@
+// rid_api.cu -- host side of librid: argument checking, device-resident
+// system / ensemble / walker state, and the step loop that drives the kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rid_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// errors
+static thread_local std::string g_err = "";
+
+static int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? RID_ERR_OOM : RID_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+    } while (0)
+
+#define TRY(expr)                       \
+    do {                                \
+        int r_ = (expr);                \
+        if (r_ != RID_OK) return r_;    \
+    } while (0)
+
+// A grow-only device buffer.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t n) {
+        if (n <= bytes) return RID_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        if (n == 0) return RID_OK;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            return fail(RID_ERR_OOM, "cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
+        }
+        bytes = n;
+        return RID_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct rid_system {
+    rid_system_desc desc{};
+    SysDev S{};
+    int device = 0;
+    DevBuf d_dih, d_cv, d_acv_off, d_acv;
+    // ensemble
+    bool has_ens = false;
+    EnsDev E{};
+    int precision = RID_PREC_FP32;
+    DevBuf d_W, d_WT, d_b, d_wout, d_bout;
+    // state
+    int cap = 0;
+    DevBuf x, v, f, fff, s, J, u, gradA, Aval, eps, hs, eff, flags;
+    // label
+    DevBuf lsum, lsum2, lbsum, ls0, lkap;
+    // staging for host I/O and traces
+    DevBuf io0, io1, tr_cv, tr_eps, tr_en, out_mf, out_se, out_sd;
+    // resident walker session
+    int W_act = 0;
+    uint64_t step_next = 0;
+    bool loaded = false;
+    // kernel timing
+    bool prof_on = false;
+    std::vector<std::string> prof_names;
+    struct Rec { int id; cudaEvent_t a, b; };
+    std::vector<Rec> prof_recs;
+    long long launches = 0;
+};
+
+// Run one kernel launcher, bracketed by events while profiling is enabled.
+template <typename F>
+static int timed_launch(rid_system* sys, const char* name, cudaStream_t st, F&& launch) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (sys->prof_on) {
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        CK(cudaEventRecord(a, st));
+    }
+    launch();
+    ++sys->launches;
+    if (sys->prof_on) {
+        CK(cudaEventRecord(b, st));
+        int id = -1;
+        for (size_t i = 0; i < sys->prof_names.size(); ++i)
+            if (sys->prof_names[i] == name) id = (int)i;
+        if (id < 0) { id = (int)sys->prof_names.size(); sys->prof_names.push_back(name); }
+        sys->prof_recs.push_back({id, a, b});
+    }
+    return RID_OK;
+}
+
+static int check_device(rid_system* sys) {
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != sys->device) return fail(RID_ERR_STATE, "system was created on device %d, current device is %d", sys->device, dev);
+    return RID_OK;
+}
+
+static StateDev state_view(rid_system* sys) {
+    StateDev st{};
+    st.W = sys->cap;
+    st.x = sys->x.as<float4>();
+    st.v = sys->v.as<float4>();
+    st.f = sys->f.as<float4>();
+    st.fff = sys->fff.as<float4>();
+    st.s = sys->s.as<float>();
+    st.J = sys->J.as<float4>();
+    st.u = sys->u.as<float>();
+    st.gradA = sys->gradA.as<float>();
+    st.Aval = sys->Aval.as<float>();
+    st.eps = sys->eps.as<float>();
+    st.hs = sys->hs.as<float>();
+    st.eff = sys->eff.as<double>();
+    st.flags = sys->flags.as<int>();
+    return st;
+}
+
+// The kernels index per-walker arrays by the walker count of the current call
+// (StateDev.W is set to it), so capacity only bounds the allocation.
+static int ensure_state(rid_system* sys, int W) {
+    const int N = sys->S.N, C = sys->S.C;
+    const size_t nb = (size_t)W * N, nc = (size_t)W * C;
+    TRY(sys->x.ensure(nb * sizeof(float4)));
+    TRY(sys->v.ensure(nb * sizeof(float4)));
+    TRY(sys->f.ensure(nb * sizeof(float4)));
+    TRY(sys->fff.ensure(nb * sizeof(float4)));
+    TRY(sys->s.ensure(nc * sizeof(float)));
+    TRY(sys->J.ensure(nc * 4 * sizeof(float4)));
+    TRY(sys->u.ensure(nc * 2 * sizeof(float)));
+    TRY(sys->eps.ensure((size_t)W * sizeof(float)));
+    TRY(sys->eff.ensure((size_t)W * sizeof(double)));
+    TRY(sys->flags.ensure((size_t)W * sizeof(int)));
+    if (sys->has_ens) {
+        const EnsDev& E = sys->E;
+        TRY(sys->gradA.ensure((size_t)E.M * nc * sizeof(float)));
+        TRY(sys->Aval.ensure((size_t)E.M * W * sizeof(float)));
+        TRY(sys->hs.ensure(rid_mlp_fp32_scratch_floats(W, E.M, E.L, E.H) * sizeof(float)));
+    }
+    if (W > sys->cap) sys->cap = W;
+    return RID_OK;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" int rid_version(void) { return 100; }
+
+extern "C" const char* rid_status_string(int s) {
+    switch (s) {
+        case RID_OK: return "ok";
+        case RID_ERR_ARG: return "invalid argument";
+        case RID_ERR_OOM: return "out of device memory";
+        case RID_ERR_CUDA: return "CUDA error";
+        case RID_ERR_NONFINITE: return "non-finite positions or forces";
+        case RID_ERR_TIMEOUT: return "timeout";
+        case RID_NOT_READY: return "not ready";
+        case RID_ERR_STATE: return "invalid state";
+        case RID_ERR_CANCELLED: return "cancelled";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* rid_last_error(void) { return g_err.c_str(); }
+
+static void destroy_all(rid_system* sys) {
+    DevBuf* bufs[] = {&sys->d_dih, &sys->d_cv, &sys->d_acv_off, &sys->d_acv, &sys->d_W, &sys->d_WT, &sys->d_b,
+                      &sys->d_wout, &sys->d_bout, &sys->x, &sys->v, &sys->f, &sys->fff, &sys->s, &sys->J,
+                      &sys->u, &sys->gradA, &sys->Aval, &sys->eps, &sys->hs, &sys->eff, &sys->flags,
+                      &sys->lsum, &sys->lsum2, &sys->lbsum, &sys->ls0, &sys->lkap, &sys->io0, &sys->io1,
+                      &sys->tr_cv, &sys->tr_eps, &sys->tr_en, &sys->out_mf, &sys->out_se, &sys->out_sd};
+    for (DevBuf* b : bufs) b->release();
+    for (auto& r : sys->prof_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    sys->prof_recs.clear();
+}
+
+extern "C" int rid_create_system(const rid_system_desc* d, rid_system** out) {
+    if (!d || !out) return fail(RID_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    const int N = d->n_beads, C = d->n_cv;
+    if (N < 4 || N > RID_MAX_BEADS) return fail(RID_ERR_ARG, "n_beads=%d outside [4, %d]", N, RID_MAX_BEADS);
+    if (C < 1 || C > RID_MAX_CV) return fail(RID_ERR_ARG, "n_cv=%d outside [1, %d]", C, RID_MAX_CV);
+    if (d->output_freq < 1) return fail(RID_ERR_ARG, "output_freq must be >= 1");
+    if (d->reserved0 != 0) return fail(RID_ERR_ARG, "reserved0 must be 0");
+    if (!(d->mass > 0) || !(d->kT >= 0) || !(d->dt > 0) || !(d->gamma >= 0))
+        return fail(RID_ERR_ARG, "need mass > 0, kT >= 0, dt > 0, gamma >= 0");
+    if (!(d->lj_rc > 0) || !(d->lj_sigma > 0)) return fail(RID_ERR_ARG, "need lj_rc > 0, lj_sigma > 0");
+    if (!d->dihedral_k || !d->dihedral_delta || !d->cv_atoms) return fail(RID_ERR_ARG, "NULL parameter array");
+    for (int j = 0; j < C; ++j) {
+        for (int a = 0; a < 4; ++a) {
+            const int q = d->cv_atoms[4 * j + a];
+            if (q < 0 || q >= N) return fail(RID_ERR_ARG, "cv_atoms[%d][%d]=%d outside [0, %d)", j, a, q, N);
+        }
+        const int* q = d->cv_atoms + 4 * j;
+        if (q[0] == q[1] || q[1] == q[2] || q[2] == q[3] || q[0] == q[2] || q[1] == q[3] || q[0] == q[3])
+            return fail(RID_ERR_ARG, "cv %d has repeated beads", j);
+    }
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    rid_system* sys = new rid_system();
+    sys->device = dev;
+    sys->desc = *d;
+    sys->desc.dihedral_k = nullptr;
+    sys->desc.dihedral_delta = nullptr;
+    sys->desc.cv_atoms = nullptr;
+    SysDev& S = sys->S;
+    S.N = N;
+    S.C = C;
+    S.output_freq = d->output_freq;
+    S.inv_mass = (float)(1.0 / d->mass);
+    S.half_dt = (float)(0.5 * d->dt);
+    const double c1 = std::exp(-d->gamma * d->dt);
+    S.c1 = (float)c1;
+    S.c2 = (float)std::sqrt((1.0 - c1 * c1) * d->kT / d->mass);
+    S.sd_mb = (float)std::sqrt(d->kT / d->mass);
+    S.kb = (float)d->bond_k;
+    S.r0 = (float)d->bond_r0;
+    S.ka = (float)d->angle_k;
+    S.th0 = (float)d->angle_theta0;
+    S.lj_eps24 = (float)(24.0 * d->lj_eps);
+    S.lj_eps4 = (float)(4.0 * d->lj_eps);
+    S.sig2 = (float)(d->lj_sigma * d->lj_sigma);
+    S.rc2 = (float)(d->lj_rc * d->lj_rc);
+    {
+        const double sr6 = std::pow(d->lj_sigma / d->lj_rc, 6.0);
+        S.urc = (float)(4.0 * d->lj_eps * (sr6 * sr6 - sr6));
+    }
+    S.key0 = (uint32_t)d->seed;
+    S.key1 = (uint32_t)(d->seed >> 32);
+    // parameters
+    std::vector<float> dih((size_t)(N - 3) * 6);
+    for (int k = 0; k < N - 3; ++k)
+        for (int n = 0; n < 3; ++n) {
+            dih[6 * k + n] = (float)d->dihedral_k[3 * k + n];
+            dih[6 * k + 3 + n] = (float)d->dihedral_delta[3 * k + n];
+        }
+    std::vector<int> off(N + 1, 0);
+    for (int j = 0; j < C; ++j)
+        for (int a = 0; a < 4; ++a) off[d->cv_atoms[4 * j + a] + 1]++;
+    for (int i = 0; i < N; ++i) off[i + 1] += off[i];
+    std::vector<int2> acv(4 * C);
+    {
+        std::vector<int> fill(off.begin(), off.end() - 1);
+        for (int j = 0; j < C; ++j)
+            for (int a = 0; a < 4; ++a) acv[fill[d->cv_atoms[4 * j + a]]++] = make_int2(j, a);
+    }
+    int r = RID_OK;
+    if ((r = sys->d_dih.ensure(dih.size() * sizeof(float))) || (r = sys->d_cv.ensure(C * sizeof(int4))) ||
+        (r = sys->d_acv_off.ensure((N + 1) * sizeof(int))) || (r = sys->d_acv.ensure(4 * C * sizeof(int2)))) {
+        destroy_all(sys);
+        delete sys;
+        return r;
+    }
+    cudaError_t e = cudaMemcpy(sys->d_dih.p, dih.data(), dih.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(sys->d_cv.p, d->cv_atoms, C * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(sys->d_acv_off.p, off.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(sys->d_acv.p, acv.data(), 4 * C * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        destroy_all(sys);
+        delete sys;
+        return fail(RID_ERR_CUDA, "parameter upload failed: %s", cudaGetErrorString(e));
+    }
+    S.dih = sys->d_dih.as<float>();
+    S.cv = sys->d_cv.as<int4>();
+    S.acv_off = sys->d_acv_off.as<int>();
+    S.acv = sys->d_acv.as<int2>();
+    *out = sys;
+    return RID_OK;
+}
+
+extern "C" int rid_destroy_system(rid_system* sys) {
+    if (!sys) return RID_OK;
+    destroy_all(sys);
+    delete sys;
+    return RID_OK;
+}
+
+extern "C" int rid_set_ensemble(rid_system* sys, const rid_ensemble_desc* d) {
+    if (!sys || !d || !d->weights) return fail(RID_ERR_ARG, "NULL argument");
+    TRY(check_device(sys));
+    const int M = d->n_models, D = d->n_in, L = d->n_layers, H = d->width;
+    if (M < 1 || M > RID_MAX_MODELS) return fail(RID_ERR_ARG, "n_models=%d outside [1, %d]", M, RID_MAX_MODELS);
+    if (D != 2 * sys->S.C) return fail(RID_ERR_ARG, "n_in=%d must equal 2 * n_cv = %d", D, 2 * sys->S.C);
+    if (L < 1 || L > RID_MAX_LAYERS) return fail(RID_ERR_ARG, "n_layers=%d outside [1, %d]", L, RID_MAX_LAYERS);
+    if (H < 32 || H > RID_MAX_WIDTH || H % 32) return fail(RID_ERR_ARG, "width=%d must be a multiple of 32 in [32, %d]", H, RID_MAX_WIDTH);
+    if (d->precision != RID_PREC_FP32 && d->precision != RID_PREC_BF16)
+        return fail(RID_ERR_ARG, "unknown precision %d", d->precision);
+    if (!(d->trust_lo < d->trust_hi)) return fail(RID_ERR_ARG, "need trust_lo < trust_hi");
+    const long long P = (long long)H * D + H + (long long)(L - 1) * ((long long)H * H + H) + H + 1;
+    // split the packed layout into W (row-major [H][fin]), W^T, biases, w_out, b_out
+    long long wst = (long long)H * D + (long long)(L - 1) * H * H;
+    std::vector<float> W((size_t)M * wst), WT((size_t)M * wst), b((size_t)M * L * H), wo((size_t)M * H), bo(M);
+    long long loff[RID_MAX_LAYERS] = {0};
+    for (int l = 1; l < L; ++l) loff[l] = loff[l - 1] + (long long)H * (l == 1 ? D : H);
+    for (int m = 0; m < M; ++m) {
+        const float* p = d->weights + (size_t)m * P;
+        for (int l = 0; l < L; ++l) {
+            const int fin = l == 0 ? D : H;
+            float* Wm = W.data() + (size_t)m * wst + loff[l];
+            float* WTm = WT.data() + (size_t)m * wst + loff[l];
+            for (int o = 0; o < H; ++o)
+                for (int i = 0; i < fin; ++i) {
+                    const float val = p[(size_t)o * fin + i];
+                    if (!std::isfinite(val)) return fail(RID_ERR_ARG, "non-finite weight in model %d", m);
+                    Wm[(size_t)o * fin + i] = val;
+                    WTm[(size_t)i * H + o] = val;
+                }
+            p += (size_t)H * fin;
+            for (int o = 0; o < H; ++o) b[((size_t)m * L + l) * H + o] = p[o];
+            p += H;
+        }
+        for (int o = 0; o < H; ++o) wo[(size_t)m * H + o] = p[o];
+        bo[m] = p[H];
+    }
+    TRY(sys->d_W.ensure(W.size() * sizeof(float)));
+    TRY(sys->d_WT.ensure(WT.size() * sizeof(float)));
+    TRY(sys->d_b.ensure(b.size() * sizeof(float)));
+    TRY(sys->d_wout.ensure(wo.size() * sizeof(float)));
+    TRY(sys->d_bout.ensure(bo.size() * sizeof(float)));
+    CK(cudaMemcpy(sys->d_W.p, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sys->d_WT.p, WT.data(), WT.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sys->d_b.p, b.data(), b.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sys->d_wout.p, wo.data(), wo.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sys->d_bout.p, bo.data(), bo.size() * sizeof(float), cudaMemcpyHostToDevice));
+    EnsDev& E = sys->E;
+    E.M = M; E.D = D; E.L = L; E.H = H; E.resnet = d->resnet ? 1 : 0;
+    E.e0 = (float)d->trust_lo;
+    E.e1 = (float)d->trust_hi;
+    E.W = sys->d_W.as<float>();
+    E.WT = sys->d_WT.as<float>();
+    E.b = sys->d_b.as<float>();
+    E.wout = sys->d_wout.as<float>();
+    E.bout = sys->d_bout.as<float>();
+    E.wstride = wst;
+    for (int l = 0; l < RID_MAX_LAYERS; ++l) E.loff[l] = loff[l];
+    sys->precision = d->precision;
+    sys->has_ens = true;
+    // re-size the ensemble scratch for the current capacity
+    if (sys->cap > 0) {
+        const int cap = sys->cap;
+        sys->cap = 0;
+        TRY(ensure_state(sys, cap));
+    }
+    return RID_OK;
+}
+
+// ---------------------------------------------------------------------------
+// I/O helpers: bring [W][N][3] float arrays in / out of the float4 state.
+static int load_xyz(rid_system* sys, const float* src, float4* dst, long long n, int mem, cudaStream_t st) {
+    const float* dsrc = src;
+    if (mem == RID_MEM_HOST) {
+        TRY(sys->io0.ensure((size_t)n * 3 * sizeof(float)));
+        CK(cudaMemcpyAsync(sys->io0.p, src, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, st));
+        dsrc = sys->io0.as<float>();
+    }
+    rid_launch_pack(dsrc, dst, n, st);
+    CK(cudaGetLastError());
+    return RID_OK;
+}
+
+static int store_xyz(rid_system* sys, const float4* src, float* dst, long long n, int mem, cudaStream_t st) {
+    if (!dst) return RID_OK;
+    float* ddst = dst;
+    if (mem == RID_MEM_HOST) {
+        TRY(sys->io1.ensure((size_t)n * 3 * sizeof(float)));
+        ddst = sys->io1.as<float>();
+    }
+    rid_launch_unpack(src, ddst, n, st);
+    CK(cudaGetLastError());
+    if (mem == RID_MEM_HOST) CK(cudaMemcpyAsync(dst, ddst, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost, st));
+    return RID_OK;
+}
+
+static int fetch_flags(rid_system* sys, int W, cudaStream_t st, bool* any) {
+    std::vector<int> h(W);
+    CK(cudaMemcpyAsync(h.data(), sys->flags.p, (size_t)W * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *any = false;
+    for (int i = 0; i < W; ++i) *any |= h[i] != 0;
+    return RID_OK;
+}
+
+// One force evaluation at the current positions (optionally preceded by the
+// B-A-O-A half of a step) and the closing kernel.
+static int evaluate(rid_system* sys, int W, bool integrate, uint32_t step, int mode, const LabelDev* lab, bool kick,
+                    long long t, int slot, float* cv, float* eps, double* en, long long T, cudaStream_t st) {
+    StateDev sd = state_view(sys);
+    sd.W = W;
+    const bool energy = en != nullptr && slot >= 0;
+    TRY(timed_launch(sys, "k_force_cv", st, [&] { rid_launch_force_cv(sys->S, sd, W, integrate, energy, step, st); }));
+    if (mode == 1) TRY(timed_launch(sys, "k_mlp_fp32", st, [&] { rid_launch_mlp_fp32(sys->E, sd, W, sys->S.C, st); }));
+    TRY(timed_launch(sys, "k_finish", st, [&] {
+        rid_launch_finish(sys->S, sd, mode == 1 ? &sys->E : nullptr, lab, W, mode, kick, t, slot, cv, eps, en, T, st);
+    }));
+    CK(cudaGetLastError());
+    return RID_OK;
+}
+
+// --- resident walker session ------------------------------------------------
+static int do_load(rid_system* sys, int W, const float* x0, const float* v0, uint64_t step0, int mem, cudaStream_t st) {
+    if (W < 1) return fail(RID_ERR_ARG, "n_walkers=%d must be >= 1", W);
+    if (!x0) return fail(RID_ERR_ARG, "NULL x0");
+    if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "mem must be RID_MEM_HOST or RID_MEM_DEVICE");
+    if (step0 > (1ull << 32)) return fail(RID_ERR_ARG, "step0 exceeds 2^32");
+    if ((long long)W * sys->S.N > (1ll << 31)) return fail(RID_ERR_ARG, "n_walkers * n_beads too large");
+    TRY(check_device(sys));
+    TRY(ensure_state(sys, W));
+    const long long nb = (long long)W * sys->S.N;
+    StateDev sd = state_view(sys);
+    TRY(load_xyz(sys, x0, sd.x, nb, mem, st));
+    ++sys->launches;
+    if (v0) { TRY(load_xyz(sys, v0, sd.v, nb, mem, st)); ++sys->launches; }
+    else { rid_launch_mb(sys->S, sd, W, (uint32_t)step0, st); ++sys->launches; }
+    CK(cudaMemsetAsync(sys->flags.p, 0, (size_t)W * sizeof(int), st));
+    TRY(evaluate(sys, W, false, 0, sys->has_ens ? 1 : 0, nullptr, false, -1, -1, nullptr, nullptr, nullptr, 0, st));
+    sys->W_act = W;
+    sys->step_next = step0;
+    sys->loaded = true;
+    return RID_OK;
+}
+
+static int do_advance(rid_system* sys, int64_t n_steps, float* cv_out, float* eps_out, double* energy_out, int mem,
+                      cudaStream_t st) {
+    if (!sys->loaded) return fail(RID_ERR_STATE, "no walkers loaded");
+    if (n_steps < 0) return fail(RID_ERR_ARG, "n_steps < 0");
+    if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "mem must be RID_MEM_HOST or RID_MEM_DEVICE");
+    if (sys->step_next + (uint64_t)n_steps > (1ull << 32)) return fail(RID_ERR_ARG, "step counter would exceed 2^32");
+    TRY(check_device(sys));
+    const int W = sys->W_act, C = sys->S.C, of = sys->S.output_freq;
+    const long long T = n_steps / of;
+    const int mode = sys->has_ens ? 1 : 0;
+    float* dcv = cv_out;
+    float* deps = eps_out;
+    double* den = energy_out;
+    if (mem == RID_MEM_HOST) {
+        if (cv_out) { TRY(sys->tr_cv.ensure((size_t)W * T * C * sizeof(float))); dcv = sys->tr_cv.as<float>(); }
+        if (eps_out) { TRY(sys->tr_eps.ensure((size_t)W * T * sizeof(float))); deps = sys->tr_eps.as<float>(); }
+        if (energy_out) { TRY(sys->tr_en.ensure((size_t)W * T * 3 * sizeof(double))); den = sys->tr_en.as<double>(); }
+    }
+    for (long long t = 0; t < n_steps; ++t) {
+        const int slot = ((t + 1) % of == 0) ? (int)((t + 1) / of - 1) : -1;
+        TRY(evaluate(sys, W, true, (uint32_t)(sys->step_next + t), mode, nullptr, true, t, slot, dcv, deps, den, T, st));
+    }
+    sys->step_next += (uint64_t)n_steps;
+    if (mem == RID_MEM_HOST && T > 0 && (cv_out || eps_out || energy_out)) {
+        if (cv_out) CK(cudaMemcpyAsync(cv_out, dcv, (size_t)W * T * C * sizeof(float), cudaMemcpyDeviceToHost, st));
+        if (eps_out) CK(cudaMemcpyAsync(eps_out, deps, (size_t)W * T * sizeof(float), cudaMemcpyDeviceToHost, st));
+        if (energy_out) CK(cudaMemcpyAsync(energy_out, den, (size_t)W * T * 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return RID_OK;
+}
+
+static int do_read(rid_system* sys, float* x_out, float* v_out, uint64_t* step_next, int mem, cudaStream_t st) {
+    if (!sys->loaded) return fail(RID_ERR_STATE, "no walkers loaded");
+    if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "mem must be RID_MEM_HOST or RID_MEM_DEVICE");
+    TRY(check_device(sys));
+    const int W = sys->W_act;
+    const long long nb = (long long)W * sys->S.N;
+    StateDev sd = state_view(sys);
+    if (x_out) { TRY(store_xyz(sys, sd.x, x_out, nb, mem, st)); ++sys->launches; }
+    if (v_out) { TRY(store_xyz(sys, sd.v, v_out, nb, mem, st)); ++sys->launches; }
+    if (step_next) *step_next = sys->step_next;
+    bool bad = false;
+    TRY(fetch_flags(sys, W, st, &bad));
+    if (bad) return fail(RID_ERR_NONFINITE, "non-finite force or velocity in at least one walker");
+    return RID_OK;
+}
+
+extern "C" int rid_walkers_load(rid_system* sys, int32_t W, const float* x0, const float* v0, uint64_t step0,
+                                int32_t mem, void* stream) {
+    if (!sys) return fail(RID_ERR_ARG, "NULL system");
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(do_load(sys, W, x0, v0, step0, mem, st));
+    CK(cudaStreamSynchronize(st));
+    return RID_OK;
+}
+
+extern "C" int rid_walkers_advance(rid_system* sys, int64_t n_steps, float* cv_out, float* eps_out,
+                                   double* energy_out, int32_t mem, void* stream) {
+    if (!sys) return fail(RID_ERR_ARG, "NULL system");
+    return do_advance(sys, n_steps, cv_out, eps_out, energy_out, mem, (cudaStream_t)stream);
+}
+
+extern "C" int rid_walkers_read(rid_system* sys, float* x_out, float* v_out, uint64_t* step_next, int32_t mem,
+                                void* stream) {
+    if (!sys) return fail(RID_ERR_ARG, "NULL system");
+    return do_read(sys, x_out, v_out, step_next, mem, (cudaStream_t)stream);
+}
+
+extern "C" int rid_profile_enable(rid_system* sys, int32_t enable) {
+    if (!sys) return fail(RID_ERR_ARG, "NULL system");
+    for (auto& r : sys->prof_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    sys->prof_recs.clear();
+    sys->prof_names.clear();
+    sys->prof_on = enable != 0;
+    return RID_OK;
+}
+
+extern "C" int rid_profile_read(rid_system* sys, int32_t max_kernels, char* names_out, double* total_ms,
+                                int64_t* launches, int32_t* n_kernels) {
+    if (!sys || max_kernels < 0 || (max_kernels > 0 && (!names_out || !total_ms || !launches)))
+        return fail(RID_ERR_ARG, "bad arguments");
+    const int K = (int)sys->prof_names.size();
+    std::vector<double> ms(K, 0.0);
+    std::vector<long long> cnt(K, 0);
+    for (auto& r : sys->prof_recs) {
+        CK(cudaEventSynchronize(r.b));
+        float e = 0.f;
+        CK(cudaEventElapsedTime(&e, r.a, r.b));
+        ms[r.id] += e;
+        cnt[r.id] += 1;
+    }
+    for (int k = 0; k < K && k < max_kernels; ++k) {
+        std::snprintf(names_out + 48 * k, 48, "%s", sys->prof_names[k].c_str());
+        total_ms[k] = ms[k];
+        launches[k] = cnt[k];
+    }
+    if (n_kernels) *n_kernels = K;
+    return RID_OK;
+}
+
+extern "C" int64_t rid_launch_count(rid_system* sys) { return sys ? sys->launches : -1; }
+
+extern "C" int rid_explore(rid_system* sys, int32_t W, const float* x0, const float* v0, uint64_t step0,
+                           int64_t n_steps, float* cv_out, float* eps_out, double* energy_out, float* x_out,
+                           float* v_out, int32_t mem, void* stream) {
+    if (!sys || !x0) return fail(RID_ERR_ARG, "NULL argument");
+    if (n_steps < 0) return fail(RID_ERR_ARG, "n_steps < 0");
+    if (step0 + (uint64_t)n_steps > (1ull << 32)) return fail(RID_ERR_ARG, "step0 + n_steps exceeds 2^32");
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(do_load(sys, W, x0, v0, step0, mem, st));
+    TRY(do_advance(sys, n_steps, cv_out, eps_out, energy_out, mem, st));
+    return do_read(sys, x_out, v_out, nullptr, mem, st);
+}
+
+extern "C" int rid_label(rid_system* sys, int32_t R, const float* x0, const float* v0, const double* s0,
+                         const double* kappa, uint64_t step0, int64_t n_steps, int64_t n_equil, int32_t n_blocks,
+                         double* mf_out, double* se_out, double* std_out, float* x_out, float* v_out, int32_t mem,
+                         void* stream) {
+    if (!sys || !x0 || !s0 || !kappa || !mf_out || !se_out || !std_out) return fail(RID_ERR_ARG, "NULL argument");
+    if (R < 1) return fail(RID_ERR_ARG, "n_runs=%d must be >= 1", R);
+    if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "mem must be RID_MEM_HOST or RID_MEM_DEVICE");
+    if (n_blocks < 2 || n_blocks > RID_MAX_BLOCKS) return fail(RID_ERR_ARG, "n_blocks=%d outside [2, %d]", n_blocks, RID_MAX_BLOCKS);
+    if (n_equil < 0 || n_steps - n_equil < n_blocks) return fail(RID_ERR_ARG, "need 0 <= n_equil and n_steps - n_equil >= n_blocks");
+    if (step0 + (uint64_t)n_steps > (1ull << 32)) return fail(RID_ERR_ARG, "step0 + n_steps exceeds 2^32");
+    TRY(check_device(sys));
+    sys->loaded = false;   // these calls reuse the resident walker buffers
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(ensure_state(sys, R));
+    const int N = sys->S.N, C = sys->S.C;
+    const long long nb = (long long)R * N, nc = (long long)R * C;
+    TRY(sys->lsum.ensure(nc * sizeof(double)));
+    TRY(sys->lsum2.ensure(nc * sizeof(double)));
+    TRY(sys->lbsum.ensure(nc * n_blocks * sizeof(double)));
+    TRY(sys->ls0.ensure(nc * sizeof(double)));
+    TRY(sys->lkap.ensure(nc * sizeof(double)));
+    const cudaMemcpyKind k = mem == RID_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(sys->ls0.p, s0, nc * sizeof(double), k, st));
+    CK(cudaMemcpyAsync(sys->lkap.p, kappa, nc * sizeof(double), k, st));
+    CK(cudaMemsetAsync(sys->lsum.p, 0, nc * sizeof(double), st));
+    CK(cudaMemsetAsync(sys->lsum2.p, 0, nc * sizeof(double), st));
+    CK(cudaMemsetAsync(sys->lbsum.p, 0, nc * n_blocks * sizeof(double), st));
+    LabelDev lab{};
+    lab.s0 = sys->ls0.as<double>();
+    lab.kappa = sys->lkap.as<double>();
+    lab.sum = sys->lsum.as<double>();
+    lab.sum2 = sys->lsum2.as<double>();
+    lab.bsum = sys->lbsum.as<double>();
+    lab.B = n_blocks;
+    lab.n_equil = n_equil;
+    lab.K = n_steps - n_equil;
+    StateDev sd = state_view(sys);
+    TRY(load_xyz(sys, x0, sd.x, nb, mem, st));
+    if (v0) TRY(load_xyz(sys, v0, sd.v, nb, mem, st));
+    else rid_launch_mb(sys->S, sd, R, (uint32_t)step0, st);
+    CK(cudaMemsetAsync(sys->flags.p, 0, (size_t)R * sizeof(int), st));
+    TRY(evaluate(sys, R, false, 0, 2, &lab, false, -1, -1, nullptr, nullptr, nullptr, 0, st));
+    for (long long t = 0; t < n_steps; ++t)
+        TRY(evaluate(sys, R, true, (uint32_t)(step0 + t), 2, &lab, true, t, -1, nullptr, nullptr, nullptr, 0, st));
+    double *dmf = mf_out, *dse = se_out, *dsd = std_out;
+    if (mem == RID_MEM_HOST) {
+        TRY(sys->out_mf.ensure(nc * sizeof(double)));
+        TRY(sys->out_se.ensure(nc * sizeof(double)));
+        TRY(sys->out_sd.ensure(nc * sizeof(double)));
+        dmf = sys->out_mf.as<double>();
+        dse = sys->out_se.as<double>();
+        dsd = sys->out_sd.as<double>();
+    }
+    rid_launch_label_final(lab, R, C, dmf, dse, dsd, st);
+    CK(cudaGetLastError());
+    TRY(store_xyz(sys, sd.x, x_out, nb, mem, st));
+    TRY(store_xyz(sys, sd.v, v_out, nb, mem, st));
+    if (mem == RID_MEM_HOST) {
+        CK(cudaMemcpyAsync(mf_out, dmf, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(se_out, dse, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(std_out, dsd, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    bool bad = false;
+    TRY(fetch_flags(sys, R, st, &bad));
+    if (bad) return fail(RID_ERR_NONFINITE, "non-finite force or velocity in at least one run");
+    return RID_OK;
+}
+
+extern "C" int rid_eval_forces(rid_system* sys, int32_t W, const float* x, int32_t bias, const double* s0,
+                               const double* kappa, float* f_out, float* s_out, float* eps_out, float* abar_out,
+                               float* grad_out, int32_t mem, void* stream) {
+    if (!sys || !x) return fail(RID_ERR_ARG, "NULL argument");
+    if (W < 1) return fail(RID_ERR_ARG, "n_walkers must be >= 1");
+    if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "bad mem");
+    if (bias < 0 || bias > 2) return fail(RID_ERR_ARG, "bias must be RID_BIAS_*");
+    if (bias == RID_BIAS_ENSEMBLE && !sys->has_ens) return fail(RID_ERR_STATE, "no ensemble set");
+    if (bias == RID_BIAS_RESTRAINT && (!s0 || !kappa)) return fail(RID_ERR_ARG, "restraint needs s0 and kappa");
+    if ((eps_out || abar_out || grad_out) && bias != RID_BIAS_ENSEMBLE)
+        return fail(RID_ERR_ARG, "eps/abar/grad outputs need bias = RID_BIAS_ENSEMBLE");
+    TRY(check_device(sys));
+    sys->loaded = false;   // these calls reuse the resident walker buffers
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(ensure_state(sys, W));
+    const int N = sys->S.N, C = sys->S.C;
+    const long long nb = (long long)W * N, nc = (long long)W * C;
+    LabelDev lab{};
+    if (bias == RID_BIAS_RESTRAINT) {
+        TRY(sys->ls0.ensure(nc * sizeof(double)));
+        TRY(sys->lkap.ensure(nc * sizeof(double)));
+        const cudaMemcpyKind k = mem == RID_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        CK(cudaMemcpyAsync(sys->ls0.p, s0, nc * sizeof(double), k, st));
+        CK(cudaMemcpyAsync(sys->lkap.p, kappa, nc * sizeof(double), k, st));
+        lab.s0 = sys->ls0.as<double>();
+        lab.kappa = sys->lkap.as<double>();
+        lab.B = 1;
+        lab.K = 1;
+    }
+    StateDev sd = state_view(sys);
+    TRY(load_xyz(sys, x, sd.x, nb, mem, st));
+    CK(cudaMemsetAsync(sys->flags.p, 0, (size_t)W * sizeof(int), st));
+    TRY(evaluate(sys, W, false, 0, bias, bias == 2 ? &lab : nullptr, false, -1, -1, nullptr, nullptr, nullptr, 0, st));
+    TRY(store_xyz(sys, sd.f, f_out, nb, mem, st));
+    const cudaMemcpyKind ko = mem == RID_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (s_out) CK(cudaMemcpyAsync(s_out, sd.s, nc * sizeof(float), ko, st));
+    if (eps_out) CK(cudaMemcpyAsync(eps_out, sd.eps, (size_t)W * sizeof(float), ko, st));
+    if (bias == RID_BIAS_ENSEMBLE) {
+        const int M = sys->E.M;
+        // the per-walker rows of Aval / gradA are laid out for the call's W
+        if (grad_out) CK(cudaMemcpyAsync(grad_out, sd.gradA, (size_t)M * nc * sizeof(float), ko, st));
+        if (abar_out) {
+            std::vector<float> a((size_t)M * W);
+            CK(cudaMemcpyAsync(a.data(), sd.Aval, a.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            std::vector<float> ab(W, 0.0f);
+            for (int w = 0; w < W; ++w) {
+                float acc = 0.0f;
+                for (int m = 0; m < M; ++m) acc += a[(size_t)m * W + w];
+                ab[w] = acc / (float)M;
+            }
+            CK(cudaMemcpyAsync(abar_out, ab.data(), W * sizeof(float),
+                               mem == RID_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice, st));
+        }
+    }
+    CK(cudaStreamSynchronize(st));
+    return RID_OK;
+}
+
+extern "C" int rid_pair_mask(rid_system* sys, int32_t W, const float* x, uint32_t* mask_out, int32_t mem,
+                             void* stream) {
+    if (!sys || !x || !mask_out) return fail(RID_ERR_ARG, "NULL argument");
+    if (W < 1) return fail(RID_ERR_ARG, "n_walkers must be >= 1");
+    if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "bad mem");
+    TRY(check_device(sys));
+    sys->loaded = false;   // these calls reuse the resident walker buffers
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(ensure_state(sys, W));
+    const int N = sys->S.N;
+    const long long nb = (long long)W * N, nw = (N + 31) / 32;
+    StateDev sd = state_view(sys);
+    TRY(load_xyz(sys, x, sd.x, nb, mem, st));
+    uint32_t* dm = mask_out;
+    if (mem == RID_MEM_HOST) {
+        TRY(sys->io1.ensure((size_t)nb * nw * sizeof(uint32_t)));
+        dm = sys->io1.as<uint32_t>();
+    }
+    rid_launch_pair_mask(sys->S, sd, W, dm, st);
+    CK(cudaGetLastError());
+    if (mem == RID_MEM_HOST) CK(cudaMemcpyAsync(mask_out, dm, (size_t)nb * nw * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return RID_OK;
+}
+
+extern "C" int rid_philox(int64_t n, const uint32_t* counters, uint64_t seed, uint32_t* out_words,
+                          float* out_normals, int32_t mem, void* stream) {
+    if (n < 0 || (n > 0 && !counters)) return fail(RID_ERR_ARG, "bad counters");
+    if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "bad mem");
+    if (n == 0) return RID_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t* dc = counters;
+    uint32_t* dw = out_words;
+    float* dn = out_normals;
+    void* tmp = nullptr;
+    if (mem == RID_MEM_HOST) {
+        const size_t bytes = (size_t)n * (16 + 16 + 12);
+        CK(cudaMalloc(&tmp, bytes));
+        char* b = (char*)tmp;
+        CK(cudaMemcpyAsync(b, counters, (size_t)n * 16, cudaMemcpyHostToDevice, st));
+        dc = (const uint32_t*)b;
+        dw = out_words ? (uint32_t*)(b + (size_t)n * 16) : nullptr;
+        dn = out_normals ? (float*)(b + (size_t)n * 32) : nullptr;
+    }
+    rid_launch_philox(n, dc, (uint32_t)seed, (uint32_t)(seed >> 32), dw, dn, st);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && mem == RID_MEM_HOST) {
+        if (out_words) e = cudaMemcpyAsync(out_words, dw, (size_t)n * 16, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && out_normals) e = cudaMemcpyAsync(out_normals, dn, (size_t)n * 12, cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return fail(RID_ERR_CUDA, "rid_philox: %s", cudaGetErrorString(e));
+    return RID_OK;
+}

@@ -1,0 +1,169 @@
+// rid_internal.cuh -- device-side data layout and shared device helpers of
+// librid.  Included by every .cu file of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rid.h"
+
+#define RID_MAX_LAYERS 8
+#define RID_MAX_MODELS 16
+#define RID_MAX_CV 128
+#define RID_MAX_BEADS 4096
+#define RID_MAX_WIDTH 512
+#define RID_MAX_BLOCKS 256
+
+// --------------------------------------------------------------------------
+// Parameters of one bead-chain system, passed by value to kernels.
+struct SysDev {
+    int N, C, output_freq;
+    float inv_mass, half_dt, c1, c2, sd_mb;   // c1 = e^{-gamma dt}, c2 = sqrt((1-c1^2) kT/m)
+    float kb, r0, ka, th0;
+    float lj_eps24, lj_eps4, sig2, rc2, urc; // urc: U_LJ(rc) shift
+    uint32_t key0, key1;
+    const float* dih;        // [N-3][6]: k_1, k_2, k_3, delta_1, delta_2, delta_3
+    const int4* cv;          // [C] bead quadruples
+    const int* acv_off;      // [N+1] CSR offsets: CV slots touching each bead
+    const int2* acv;         // (cv index, slot 0..3), ordered by cv index
+};
+
+// Ensemble weights on the device, FP32 (plain path).
+struct EnsDev {
+    int M, D, L, H, resnet;
+    float e0, e1;
+    const float* W;          // per model, per layer: row-major [H][fin]
+    const float* WT;         // per model, per layer: row-major [fin][H]
+    const float* b;          // [M][L][H]
+    const float* wout;       // [M][H]
+    const float* bout;       // [M]
+    long long wstride;       // floats per model in W / WT
+    long long loff[RID_MAX_LAYERS];  // offset of layer l within a model
+};
+
+// Resident walker state (capacity W walkers).
+struct StateDev {
+    int W;
+    float4* x;      // [W][N] positions (w unused)
+    float4* v;      // [W][N] velocities
+    float4* f;      // [W][N] total force of the last evaluation
+    float4* fff;    // [W][N] force-field part of the current evaluation
+    float* s;       // [W][C] CVs
+    float4* J;      // [W][C][4] dCV/dx for the four beads
+    float* u;       // [W][D] MLP input (cos, sin) FP32
+    float* gradA;   // [M][W][C] member CV gradients
+    float* Aval;    // [M][W] member values
+    float* eps;     // [W] model deviation of the current evaluation
+    float* hs;      // MLP activation scratch
+    double* eff;    // [W] force-field energy (energy mode)
+    int* flags;     // [W] non-finite flags
+};
+
+// Label (restrained MD) accumulators.
+struct LabelDev {
+    const double* s0;     // [W][C]
+    const double* kappa;  // [W][C]
+    double* sum;          // [W][C]
+    double* sum2;         // [W][C]
+    double* bsum;         // [W][C][B]
+    int B;
+    long long n_equil, K; // K = samples = n_steps - n_equil
+};
+
+// --------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 products
+// on words 0 and 2, mixed with words 1, 3 and the key, key bumped by the Weyl
+// constants after each round.
+__device__ __forceinline__ uint4 rid_philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// -2 ln u for u = (x + 1/2) 2^-32, accurate in FP32 over the whole range:
+// for x >= 2^31 it works from 1 - u = (~x + 1/2) 2^-32 through log1p.
+__device__ __forceinline__ float rid_m2logu(uint32_t x) {
+    if (x < 0x80000000u) {
+        const float u = fmaf(__uint2float_rn(x), 0x1p-32f, 0x1p-33f);
+        return -2.0f * logf(u);
+    }
+    const float om = fmaf(__uint2float_rn(~x), 0x1p-32f, 0x1p-33f);
+    return -2.0f * log1pf(-om);
+}
+
+// Three standard normals from one counter: Box-Muller on words (0,1) and (2,3).
+__device__ __forceinline__ float3 rid_normals3(uint4 w) {
+    const float r0 = sqrtf(rid_m2logu(w.x));
+    const float r1 = sqrtf(rid_m2logu(w.z));
+    float s0, c0, s1, c1;
+    sincospif(fmaf(__uint2float_rn(w.y), 0x1p-31f, 0x1p-32f), &s0, &c0);
+    sincospif(fmaf(__uint2float_rn(w.w), 0x1p-31f, 0x1p-32f), &s1, &c1);
+    (void)s1;
+    return make_float3(r0 * c0, r0 * s0, r1 * c1);
+}
+
+// --------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// Torsion angle (IUPAC sign, [-pi, pi)) and optionally its gradient w.r.t.
+// the four points.  With F = p0-p1, G = p1-p2, H = p3-p2, A = F x G and
+// B = H x G:  phi = atan2(-|G| F.B, A.B), and (Blondel & Karplus 1996)
+//   dphi/dp0 = -|G|/A^2 A,  dphi/dp3 = |G|/B^2 B,
+//   dphi/dp1 = (|G|/A^2 + F.G/(A^2|G|)) A - H.G/(B^2|G|) B,
+//   dphi/dp2 = (H.G/(B^2|G|) - |G|/B^2) B - F.G/(A^2|G|) A.
+__device__ __forceinline__ float rid_torsion(float3 p0, float3 p1, float3 p2, float3 p3, float3* g) {
+    const float3 F = p0 - p1, G = p1 - p2, H = p3 - p2;
+    const float3 A = cross3(F, G), B = cross3(H, G);
+    const float lG = sqrtf(dot3(G, G));
+    float phi = atan2f(-lG * dot3(F, B), dot3(A, B));
+    if (phi >= 3.14159265358979f) phi -= 6.28318530717959f;
+    if (g) {
+        const float A2 = dot3(A, A), B2 = dot3(B, B);
+        const float ia = lG / A2, ib = lG / B2;
+        const float ca = dot3(F, G) / (A2 * lG), cb = dot3(H, G) / (B2 * lG);
+        g[0] = (-ia) * A;
+        g[3] = ib * B;
+        g[1] = (ia + ca) * A - cb * B;
+        g[2] = (cb - ib) * B - ca * A;
+    }
+    return phi;
+}
+
+// wrap onto [-pi, pi): d - 2 pi floor(d / 2 pi + 1/2)
+__device__ __forceinline__ float rid_wrapf(float d) {
+    return d - 6.28318530717959f * floorf(d * 0.159154943091895f + 0.5f);
+}
+__device__ __forceinline__ double rid_wrapd(double d) {
+    return d - 6.283185307179586 * floor(d * 0.15915494309189535 + 0.5);
+}
+
+// --------------------------------------------------------------------------
+// Host-side kernel launchers (defined in the .cu files).
+void rid_launch_pack(const float* src, float4* dst, long long n, cudaStream_t st);
+void rid_launch_unpack(const float4* src, float* dst, long long n, cudaStream_t st);
+void rid_launch_mb(const SysDev& S, StateDev st, int W, uint32_t step0, cudaStream_t s);
+void rid_launch_force_cv(const SysDev& S, StateDev st, int W, bool integrate, bool energy,
+                         uint32_t step, cudaStream_t s);
+void rid_launch_pair_mask(const SysDev& S, StateDev st, int W, uint32_t* mask, cudaStream_t s);
+void rid_launch_finish(const SysDev& S, StateDev st, const EnsDev* E, const LabelDev* lab, int W,
+                       int mode, bool kick, long long t, int slot, float* cv_out, float* eps_out,
+                       double* energy_out, long long T, cudaStream_t s);
+void rid_launch_label_final(const LabelDev& lab, int W, int C, double* mf, double* se, double* sd,
+                            cudaStream_t s);
+void rid_launch_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* words,
+                       float* normals, cudaStream_t s);
+void rid_launch_mlp_fp32(const EnsDev& E, StateDev st, int W, int C, cudaStream_t s);
+size_t rid_mlp_fp32_scratch_floats(int W, int M, int L, int H);

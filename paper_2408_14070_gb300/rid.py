@@ -1,0 +1,288 @@
+"""Python binding of librid (ctypes).  Argument marshalling only: every step
+of the computation runs in the library's CUDA kernels.
+
+Arrays may be numpy arrays (host memory) or CUDA torch tensors (device
+memory); all arrays of one call must live on the same side.  The binding
+raises ``RidError`` carrying the library's status code and message.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librid.so")
+
+RID_OK, RID_ERR_ARG, RID_ERR_OOM, RID_ERR_CUDA, RID_ERR_NONFINITE = 0, 1, 2, 3, 4
+RID_ERR_TIMEOUT, RID_NOT_READY, RID_ERR_STATE, RID_ERR_CANCELLED = 5, 6, 7, 8
+RID_MEM_HOST, RID_MEM_DEVICE = 0, 1
+RID_PREC_FP32, RID_PREC_BF16 = 0, 1
+RID_BIAS_NONE, RID_BIAS_ENSEMBLE, RID_BIAS_RESTRAINT = 0, 1, 2
+
+# every exported symbol of include/rid.h
+EXPORTS = ("rid_version", "rid_status_string", "rid_last_error", "rid_create_system", "rid_destroy_system",
+           "rid_set_ensemble", "rid_explore", "rid_label", "rid_eval_forces", "rid_pair_mask", "rid_philox",
+           "rid_walkers_load", "rid_walkers_advance", "rid_walkers_read", "rid_profile_enable",
+           "rid_profile_read", "rid_launch_count")
+
+
+class RidError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class SystemDesc(C.Structure):
+    _fields_ = [("n_beads", C.c_int32), ("n_cv", C.c_int32), ("output_freq", C.c_int32), ("reserved0", C.c_int32),
+                ("mass", C.c_double), ("kT", C.c_double), ("dt", C.c_double), ("gamma", C.c_double),
+                ("seed", C.c_uint64), ("bond_k", C.c_double), ("bond_r0", C.c_double), ("angle_k", C.c_double),
+                ("angle_theta0", C.c_double), ("lj_eps", C.c_double), ("lj_sigma", C.c_double),
+                ("lj_rc", C.c_double), ("dihedral_k", C.POINTER(C.c_double)),
+                ("dihedral_delta", C.POINTER(C.c_double)), ("cv_atoms", C.POINTER(C.c_int32))]
+
+
+class EnsembleDesc(C.Structure):
+    _fields_ = [("n_models", C.c_int32), ("n_in", C.c_int32), ("n_layers", C.c_int32), ("width", C.c_int32),
+                ("resnet", C.c_int32), ("precision", C.c_int32), ("trust_lo", C.c_double),
+                ("trust_hi", C.c_double), ("weights", C.POINTER(C.c_float))]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load librid.so; raises if the CUDA library has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"librid.so not found at {LIB_PATH}: run paper_2408_14070_gb300.build.build() first")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+    L.rid_version.restype = C.c_int
+    L.rid_status_string.restype = C.c_char_p
+    L.rid_status_string.argtypes = [C.c_int]
+    L.rid_last_error.restype = C.c_char_p
+    L.rid_create_system.argtypes = [C.POINTER(SystemDesc), C.POINTER(vp)]
+    L.rid_destroy_system.argtypes = [vp]
+    L.rid_set_ensemble.argtypes = [vp, C.POINTER(EnsembleDesc)]
+    L.rid_explore.argtypes = [vp, i32, vp, vp, u64, i64, vp, vp, vp, vp, vp, i32, vp]
+    L.rid_label.argtypes = [vp, i32, vp, vp, vp, vp, u64, i64, i64, i32, vp, vp, vp, vp, vp, i32, vp]
+    L.rid_eval_forces.argtypes = [vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, i32, vp]
+    L.rid_pair_mask.argtypes = [vp, i32, vp, vp, i32, vp]
+    L.rid_philox.argtypes = [i64, vp, u64, vp, vp, i32, vp]
+    L.rid_walkers_load.argtypes = [vp, i32, vp, vp, u64, i32, vp]
+    L.rid_walkers_advance.argtypes = [vp, i64, vp, vp, vp, i32, vp]
+    L.rid_walkers_read.argtypes = [vp, vp, vp, C.POINTER(u64), i32, vp]
+    L.rid_profile_enable.argtypes = [vp, i32]
+    L.rid_profile_read.argtypes = [vp, i32, C.c_char_p, C.POINTER(C.c_double), C.POINTER(i64), C.POINTER(i32)]
+    L.rid_launch_count.argtypes = [vp]
+    L.rid_launch_count.restype = i64
+    for name in EXPORTS:
+        getattr(L, name).restype = getattr(L, name).restype or C.c_int
+    _lib = L
+    return L
+
+
+def _check(code: int):
+    if code != RID_OK:
+        raise RidError(code, lib().rid_last_error().decode())
+
+
+# ---------------------------------------------------------------------------
+class _Args:
+    """Collects array pointers of one call and checks they share a memory side."""
+
+    def __init__(self):
+        self.mem = None
+        self.keep = []
+
+    def ptr(self, a, dtype, shape=None, writable=False):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):          # torch tensor
+            import torch
+            want = {np.float32: torch.float32, np.float64: torch.float64, np.uint32: torch.uint32,
+                    np.int32: torch.int32}[dtype]
+            if a.dtype != want:
+                raise TypeError(f"expected {want}, got {a.dtype}")
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            side = RID_MEM_DEVICE if a.is_cuda else RID_MEM_HOST
+            if shape is not None and a.numel() != int(np.prod(shape)):
+                raise ValueError(f"expected {int(np.prod(shape))} elements, got {a.numel()}")
+            p = a.data_ptr()
+        else:
+            if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+                raise TypeError(f"expected a C-contiguous numpy array of {np.dtype(dtype)}")
+            if writable and not a.flags.writeable:
+                raise ValueError("output array is read-only")
+            if shape is not None and a.size != int(np.prod(shape)):
+                raise ValueError(f"expected {int(np.prod(shape))} elements, got {a.size}")
+            side = RID_MEM_HOST
+            p = a.ctypes.data
+        if self.mem is None:
+            self.mem = side
+        elif self.mem != side:
+            raise ValueError("all arrays of a call must be on the same side (host or device)")
+        self.keep.append(a)
+        return C.c_void_p(p)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+# ---------------------------------------------------------------------------
+class System:
+    """A bead-chain system on the current CUDA device (wraps rid_system*)."""
+
+    def __init__(self, sp):
+        L = lib()
+        self.sp = sp
+        self.N, self.C = int(sp.n_beads), int(sp.n_cv)
+        self._dk = np.ascontiguousarray(sp.dihedral_k, dtype=np.float64)
+        self._dd = np.ascontiguousarray(sp.dihedral_delta, dtype=np.float64)
+        self._cv = np.ascontiguousarray(sp.cv_atoms, dtype=np.int32)
+        d = SystemDesc(self.N, self.C, int(sp.output_freq), 0, sp.mass, sp.kT, sp.dt, sp.gamma, int(sp.seed),
+                       sp.bond_k, sp.bond_r0, sp.angle_k, sp.angle_theta0, sp.lj_eps, sp.lj_sigma, sp.lj_rc,
+                       self._dk.ctypes.data_as(C.POINTER(C.c_double)),
+                       self._dd.ctypes.data_as(C.POINTER(C.c_double)),
+                       self._cv.ctypes.data_as(C.POINTER(C.c_int32)))
+        h = C.c_void_p()
+        _check(L.rid_create_system(C.byref(d), C.byref(h)))
+        self.h = h
+        self.M = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rid_destroy_system(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_ensemble(self, ens, precision=RID_PREC_FP32):
+        w = np.ascontiguousarray(ens.weights, dtype=np.float32)
+        d = EnsembleDesc(ens.n_models, ens.n_in, ens.n_layers, ens.width, int(ens.resnet), int(precision),
+                         float(ens.trust_lo), float(ens.trust_hi), w.ctypes.data_as(C.POINTER(C.c_float)))
+        _check(lib().rid_set_ensemble(self.h, C.byref(d)))
+        self.M = ens.n_models
+
+    def explore(self, x0, n_steps, v0=None, step0=0, cv_out=None, eps_out=None, energy_out=None, x_out=None,
+                v_out=None, stream=None):
+        W = int(x0.shape[0])
+        a = _Args()
+        px = a.ptr(x0, np.float32, (W, self.N, 3))
+        pv = a.ptr(v0, np.float32, (W, self.N, 3))
+        T = n_steps // self.sp.output_freq
+        pc = a.ptr(cv_out, np.float32, (W, T, self.C), True)
+        pe = a.ptr(eps_out, np.float32, (W, T), True)
+        pen = a.ptr(energy_out, np.float64, (W, T, 3), True)
+        pxo = a.ptr(x_out, np.float32, (W, self.N, 3), True)
+        pvo = a.ptr(v_out, np.float32, (W, self.N, 3), True)
+        _check(lib().rid_explore(self.h, W, px, pv, C.c_uint64(step0), C.c_int64(n_steps), pc, pe, pen, pxo, pvo,
+                                 a.mem, _stream_ptr(stream)))
+
+    def label(self, x0, s0, kappa, n_steps, n_equil, n_blocks, mf_out, se_out, std_out, v0=None, step0=0,
+              x_out=None, v_out=None, stream=None):
+        R = int(x0.shape[0])
+        a = _Args()
+        args = [a.ptr(x0, np.float32, (R, self.N, 3)), a.ptr(v0, np.float32, (R, self.N, 3)),
+                a.ptr(s0, np.float64, (R, self.C)), a.ptr(kappa, np.float64, (R, self.C))]
+        outs = [a.ptr(mf_out, np.float64, (R, self.C), True), a.ptr(se_out, np.float64, (R, self.C), True),
+                a.ptr(std_out, np.float64, (R, self.C), True), a.ptr(x_out, np.float32, (R, self.N, 3), True),
+                a.ptr(v_out, np.float32, (R, self.N, 3), True)]
+        _check(lib().rid_label(self.h, R, *args, C.c_uint64(step0), C.c_int64(n_steps), C.c_int64(n_equil),
+                               int(n_blocks), *outs, a.mem, _stream_ptr(stream)))
+
+    def eval_forces(self, x, bias=RID_BIAS_NONE, s0=None, kappa=None, f_out=None, s_out=None, eps_out=None,
+                    abar_out=None, grad_out=None, stream=None):
+        W = int(x.shape[0])
+        a = _Args()
+        px = a.ptr(x, np.float32, (W, self.N, 3))
+        ps0 = a.ptr(s0, np.float64, (W, self.C))
+        pk = a.ptr(kappa, np.float64, (W, self.C))
+        outs = [a.ptr(f_out, np.float32, (W, self.N, 3), True), a.ptr(s_out, np.float32, (W, self.C), True),
+                a.ptr(eps_out, np.float32, (W,), True), a.ptr(abar_out, np.float32, (W,), True),
+                a.ptr(grad_out, np.float32, (max(self.M, 1), W, self.C), True)]
+        _check(lib().rid_eval_forces(self.h, W, px, int(bias), ps0, pk, *outs, a.mem, _stream_ptr(stream)))
+
+    # resident walkers -------------------------------------------------------
+    def walkers_load(self, x0, v0=None, step0=0, stream=None):
+        W = int(x0.shape[0])
+        a = _Args()
+        px = a.ptr(x0, np.float32, (W, self.N, 3))
+        pv = a.ptr(v0, np.float32, (W, self.N, 3))
+        _check(lib().rid_walkers_load(self.h, W, px, pv, C.c_uint64(step0), a.mem, _stream_ptr(stream)))
+        self.W = W
+
+    def walkers_advance(self, n_steps, cv_out=None, eps_out=None, energy_out=None, stream=None, mem=None):
+        a = _Args()
+        T = n_steps // self.sp.output_freq
+        pc = a.ptr(cv_out, np.float32, (self.W, T, self.C), True)
+        pe = a.ptr(eps_out, np.float32, (self.W, T), True)
+        pen = a.ptr(energy_out, np.float64, (self.W, T, 3), True)
+        m = a.mem if a.mem is not None else (RID_MEM_DEVICE if mem is None else mem)
+        _check(lib().rid_walkers_advance(self.h, C.c_int64(n_steps), pc, pe, pen, m, _stream_ptr(stream)))
+
+    def walkers_read(self, x_out=None, v_out=None, stream=None, mem=None):
+        a = _Args()
+        px = a.ptr(x_out, np.float32, (self.W, self.N, 3), True)
+        pv = a.ptr(v_out, np.float32, (self.W, self.N, 3), True)
+        nxt = C.c_uint64(0)
+        m = a.mem if a.mem is not None else (RID_MEM_HOST if mem is None else mem)
+        _check(lib().rid_walkers_read(self.h, px, pv, C.byref(nxt), m, _stream_ptr(stream)))
+        return nxt.value
+
+    # kernel timing ------------------------------------------------------------
+    def profile_enable(self, on=True):
+        _check(lib().rid_profile_enable(self.h, int(bool(on))))
+
+    def profile_read(self, max_kernels=16):
+        names = C.create_string_buffer(48 * max_kernels)
+        ms = (C.c_double * max_kernels)()
+        cnt = (C.c_int64 * max_kernels)()
+        nk = C.c_int32(0)
+        _check(lib().rid_profile_read(self.h, max_kernels, names, ms, cnt, C.byref(nk)))
+        out = {}
+        for k in range(min(nk.value, max_kernels)):
+            nm = names.raw[48 * k:48 * (k + 1)].split(b"\0", 1)[0].decode()
+            out[nm] = (ms[k], int(cnt[k]))
+        return out
+
+    def launch_count(self):
+        return int(lib().rid_launch_count(self.h))
+
+    def pair_mask(self, x, mask_out, stream=None):
+        W = int(x.shape[0])
+        a = _Args()
+        px = a.ptr(x, np.float32, (W, self.N, 3))
+        pm = a.ptr(mask_out, np.uint32, (W, self.N, (self.N + 31) // 32), True)
+        _check(lib().rid_pair_mask(self.h, W, px, pm, a.mem, _stream_ptr(stream)))
+
+
+def philox(counters, seed, words_out=None, normals_out=None, stream=None):
+    n = int(counters.shape[0])
+    a = _Args()
+    pc = a.ptr(counters, np.uint32, (n, 4))
+    pw = a.ptr(words_out, np.uint32, (n, 4), True)
+    pn = a.ptr(normals_out, np.float32, (n, 3), True)
+    _check(lib().rid_philox(C.c_int64(n), pc, C.c_uint64(int(seed)), pw, pn, a.mem, _stream_ptr(stream)))
+
+
+def version() -> int:
+    return lib().rid_version()
