@@ -302,7 +302,8 @@ __global__ void __launch_bounds__(256) k_finish(SysDev S, StateDev st, EnsDev E,
             for (int j = lane; j < C; j += 32) Fs[j] *= sig;
             if (lane == 0) {
                 float ab = 0.0f;
-                for (int m = 0; m < E.M; ++m) ab += st.Aval[(long long)m * W + w];
+                for (int m = 0; m < E.M; ++m)
+                    for (int q = 0; q < E.aslices; ++q) ab += st.Aval[((long long)m * E.aslices + q) * W + w];
                 s_abar = ab * invM;
                 s_eps = eps;
                 st.eps[w] = eps;

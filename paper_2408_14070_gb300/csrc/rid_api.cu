@@ -7,7 +7,12 @@
 #include <string>
 #include <vector>
 
+#include <cstdlib>
+
+#include <cudaTypedefs.h>
+
 #include "rid_internal.cuh"
+#include "rid_tc.cuh"
 
 // ---------------------------------------------------------------------------
 // errors
@@ -64,6 +69,18 @@ struct DevBuf {
     template <typename T> T* as() const { return static_cast<T*>(p); }
 };
 
+// One cluster-size variant of the pre-tiled BF16 weights and its tensor maps.
+struct TcVariant {
+    bool ok = false;
+    int CS = 1, ck = 64, stages = 0, Kmax = 0, tmem_cols = 0;
+    unsigned stage_bytes = 0;
+    long long member_rows = 0;
+    long long grow[2 * RID_MAX_LAYERS] = {0};
+    int gN[2 * RID_MAX_LAYERS] = {0}, gK[2 * RID_MAX_LAYERS] = {0};
+    DevBuf blob;
+    CUtensorMap big{}, small{};
+};
+
 struct rid_system {
     rid_system_desc desc{};
     SysDev S{};
@@ -74,6 +91,10 @@ struct rid_system {
     EnsDev E{};
     int precision = RID_PREC_FP32;
     DevBuf d_W, d_WT, d_b, d_wout, d_bout;
+    TcVariant tcv[3];          // cluster sizes 1, 2, 4
+    int Dp = 0;
+    DevBuf tsave, d_err;
+    int last_cs = 1;
     // state
     int cap = 0;
     DevBuf x, v, f, fff, s, J, u, gradA, Aval, eps, hs, eff, flags;
@@ -160,7 +181,13 @@ static int ensure_state(rid_system* sys, int W) {
         const EnsDev& E = sys->E;
         TRY(sys->gradA.ensure((size_t)E.M * nc * sizeof(float)));
         TRY(sys->Aval.ensure((size_t)E.M * W * sizeof(float)));
-        TRY(sys->hs.ensure(rid_mlp_fp32_scratch_floats(W, E.M, E.L, E.H) * sizeof(float)));
+        TRY(sys->Aval.ensure((size_t)E.M * 4 * W * sizeof(float)));
+        if (sys->precision == RID_PREC_FP32) {
+            TRY(sys->hs.ensure(rid_mlp_fp32_scratch_floats(W, E.M, E.L, E.H) * sizeof(float)));
+        } else {
+            const size_t ntiles = (size_t)(W + 127) / 128;
+            TRY(sys->tsave.ensure((size_t)E.M * ntiles * E.L * 128 * E.H * sizeof(__nv_bfloat16)));
+        }
     }
     if (W > sys->cap) sys->cap = W;
     return RID_OK;
@@ -193,6 +220,9 @@ static void destroy_all(rid_system* sys) {
                       &sys->lsum, &sys->lsum2, &sys->lbsum, &sys->ls0, &sys->lkap, &sys->io0, &sys->io1,
                       &sys->tr_cv, &sys->tr_eps, &sys->tr_en, &sys->out_mf, &sys->out_se, &sys->out_sd};
     for (DevBuf* b : bufs) b->release();
+    for (auto& v : sys->tcv) v.blob.release();
+    sys->tsave.release();
+    sys->d_err.release();
     for (auto& r : sys->prof_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     sys->prof_recs.clear();
 }
@@ -298,6 +328,120 @@ extern "C" int rid_destroy_system(rid_system* sys) {
     return RID_OK;
 }
 
+// ---------------------------------------------------------------------------
+// BF16 tensor-core path: weight images and tensor maps.
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+static uint16_t f2bf(float f) {   // round to nearest even
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return (uint16_t)(u >> 16);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+static int build_tc_variant(rid_system* sys, const std::vector<float>& W, long long wst, const long long* loff,
+                            int CS, TcVariant& V) {
+    const EnsDev& E = sys->E;
+    const int M = E.M, D = E.D, L = E.L, H = E.H, Dp = sys->Dp, G = 2 * L;
+    V.ok = false;
+    V.CS = CS;
+    V.ck = H > 256 ? 32 : (H % 64 == 0 ? 64 : 32);
+    V.Kmax = H > Dp ? H : Dp;
+    int nsmax = 0;
+    long long rows = 0;
+    for (int g = 0; g < G; ++g) {
+        const bool fwd = g < L;
+        const int l = fwd ? g : G - 1 - g;
+        V.gN[g] = fwd ? H : (l == 0 ? Dp : H);
+        V.gK[g] = fwd ? (l == 0 ? Dp : H) : H;
+        const int ns = V.gN[g] / CS;
+        if (V.gN[g] % (16 * CS) || ns > (CS == 1 ? 512 : 256) || V.gK[g] % V.ck) return RID_OK;   // unsupported
+        if (ns > nsmax) nsmax = ns;
+        V.grow[g] = rows;
+        rows += (long long)V.gN[g] * V.gK[g] / 64;
+    }
+    V.member_rows = rows;
+    V.stage_bytes = (unsigned)nsmax * V.ck * 2u;
+    const size_t abytes = 128u * (size_t)V.Kmax * 2u * (CS > 1 ? 2 : 1);
+    const size_t budget = 220u * 1024u;
+    if (abytes + 2 * (size_t)V.stage_bytes > budget) return RID_OK;
+    V.stages = (int)((budget - abytes) / V.stage_bytes);
+    if (V.stages > TC_MAX_STAGES) V.stages = TC_MAX_STAGES;
+    V.tmem_cols = 32;
+    while (V.tmem_cols < nsmax) V.tmem_cols *= 2;
+    // pre-tiled image
+    std::vector<uint16_t> img((size_t)M * rows * 64, 0);
+    for (int m = 0; m < M; ++m)
+        for (int g = 0; g < G; ++g) {
+            const bool fwd = g < L;
+            const int l = fwd ? g : G - 1 - g;
+            const int fin = l == 0 ? D : H;
+            const float* Wl = W.data() + (size_t)m * wst + loff[l];   // [H][fin]
+            const int N = V.gN[g], K = V.gK[g], ns = N / CS, ck = V.ck;
+            for (int c = 0; c < K / ck; ++c)
+                for (int q = 0; q < CS; ++q) {
+                    const size_t base = ((size_t)m * rows + V.grow[g] + (size_t)(c * CS + q) * (ns * ck / 64)) * 64;
+                    for (int kb = 0; kb < ck / 8; ++kb)
+                        for (int rg = 0; rg < ns / 8; ++rg)
+                            for (int r = 0; r < 8; ++r)
+                                for (int kc = 0; kc < 8; ++kc) {
+                                    const int n = q * ns + rg * 8 + r, k = c * ck + kb * 8 + kc;
+                                    float val = 0.0f;
+                                    if (fwd) { if (k < fin) val = Wl[(size_t)n * fin + k]; }
+                                    else if (n < fin) val = Wl[(size_t)k * fin + n];
+                                    img[base + (((size_t)kb * (ns / 8) + rg) * 8 + r) * 8 + kc] = f2bf(val);
+                                }
+                }
+        }
+    TRY(V.blob.ensure(img.size() * 2));
+    CK(cudaMemcpy(V.blob.p, img.data(), img.size() * 2, cudaMemcpyHostToDevice));
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return fail(RID_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[2] = {64, (cuuint64_t)M * rows};
+    const cuuint64_t strides[1] = {128};
+    const cuuint32_t estr[2] = {1, 1};
+    const cuuint32_t box_big[2] = {64, 64}, box_small[2] = {64, 8};
+    CUresult r1 = enc(&V.big, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, V.blob.p, dims, strides, box_big, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r2 = enc(&V.small, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, V.blob.p, dims, strides, box_small, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) return fail(RID_ERR_CUDA, "tensor map encoding failed (%d, %d)", (int)r1, (int)r2);
+    V.ok = true;
+    return RID_OK;
+}
+
+// Cluster size for a launch: RID_MLP_CLUSTER (1, 2, 4) if set and available,
+// else the smallest that gives at least ~120 CTAs.
+static int pick_cluster(rid_system* sys, int W) {
+    const int ntiles = (W + 127) / 128, M = sys->E.M;
+    const char* env = std::getenv("RID_MLP_CLUSTER");
+    if (env) {
+        const int want = std::atoi(env);
+        for (int i = 0; i < 3; ++i)
+            if (sys->tcv[i].ok && sys->tcv[i].CS == want) return i;
+    }
+    int best = -1;
+    for (int i = 0; i < 3; ++i) {
+        if (!sys->tcv[i].ok) continue;
+        best = i;
+        if (ntiles * M * sys->tcv[i].CS >= 120) return i;
+    }
+    return best;
+}
+
 extern "C" int rid_set_ensemble(rid_system* sys, const rid_ensemble_desc* d) {
     if (!sys || !d || !d->weights) return fail(RID_ERR_ARG, "NULL argument");
     TRY(check_device(sys));
@@ -309,6 +453,8 @@ extern "C" int rid_set_ensemble(rid_system* sys, const rid_ensemble_desc* d) {
     if (d->precision != RID_PREC_FP32 && d->precision != RID_PREC_BF16)
         return fail(RID_ERR_ARG, "unknown precision %d", d->precision);
     if (!(d->trust_lo < d->trust_hi)) return fail(RID_ERR_ARG, "need trust_lo < trust_hi");
+    if (d->precision == RID_PREC_BF16 && d->resnet)
+        return fail(RID_ERR_ARG, "resnet ensembles run with RID_PREC_FP32 only");
     const long long P = (long long)H * D + H + (long long)(L - 1) * ((long long)H * H + H) + H + 1;
     // split the packed layout into W (row-major [H][fin]), W^T, biases, w_out, b_out
     long long wst = (long long)H * D + (long long)(L - 1) * H * H;
@@ -358,6 +504,19 @@ extern "C" int rid_set_ensemble(rid_system* sys, const rid_ensemble_desc* d) {
     for (int l = 0; l < RID_MAX_LAYERS; ++l) E.loff[l] = loff[l];
     sys->precision = d->precision;
     sys->has_ens = true;
+    E.aslices = 1;
+    if (d->precision == RID_PREC_BF16) {
+        sys->Dp = (D + 63) / 64 * 64;
+        const int css[3] = {1, 2, 4};
+        bool any = false;
+        for (int i = 0; i < 3; ++i) {
+            TRY(build_tc_variant(sys, W, wst, loff, css[i], sys->tcv[i]));
+            any |= sys->tcv[i].ok;
+        }
+        if (!any) return fail(RID_ERR_ARG, "no tensor-core tiling fits width=%d, n_in=%d", H, D);
+        TRY(sys->d_err.ensure(sizeof(int)));
+        CK(cudaMemset(sys->d_err.p, 0, sizeof(int)));
+    }
     // re-size the ensemble scratch for the current capacity
     if (sys->cap > 0) {
         const int cap = sys->cap;
@@ -400,6 +559,14 @@ static int fetch_flags(rid_system* sys, int W, cudaStream_t st, bool* any) {
     CK(cudaStreamSynchronize(st));
     *any = false;
     for (int i = 0; i < W; ++i) *any |= h[i] != 0;
+    if (sys->d_err.p) {
+        int e = 0;
+        CK(cudaMemcpy(&e, sys->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) {
+            cudaMemset(sys->d_err.p, 0, sizeof(int));
+            return fail(RID_ERR_TIMEOUT, "tensor-core MLP kernel: a bounded wait expired (code %d)", e);
+        }
+    }
     return RID_OK;
 }
 
@@ -411,9 +578,28 @@ static int evaluate(rid_system* sys, int W, bool integrate, uint32_t step, int m
     sd.W = W;
     const bool energy = en != nullptr && slot >= 0;
     TRY(timed_launch(sys, "k_force_cv", st, [&] { rid_launch_force_cv(sys->S, sd, W, integrate, energy, step, st); }));
-    if (mode == 1) TRY(timed_launch(sys, "k_mlp_fp32", st, [&] { rid_launch_mlp_fp32(sys->E, sd, W, sys->S.C, st); }));
+    EnsDev E = sys->E;
+    if (mode == 1 && sys->precision == RID_PREC_BF16) {
+        const int vi = pick_cluster(sys, W);
+        const TcVariant& V = sys->tcv[vi];
+        TcArgs P{};
+        P.W = W; P.C = sys->S.C; P.D = E.D; P.Dp = sys->Dp; P.L = E.L; P.H = E.H; P.M = E.M;
+        P.CS = V.CS; P.ck = V.ck; P.stages = V.stages; P.Kmax = V.Kmax; P.ntiles = (W + 127) / 128;
+        P.tmem_cols = V.tmem_cols; P.stage_bytes = V.stage_bytes;
+        P.u = sd.u; P.bias = E.b; P.wout = E.wout; P.bout = E.bout;
+        P.tsave = sys->tsave.as<__nv_bfloat16>(); P.gradA = sd.gradA; P.Apart = sd.Aval; P.err = sys->d_err.as<int>();
+        P.member_rows = V.member_rows;
+        for (int g = 0; g < 2 * E.L; ++g) { P.grow[g] = V.grow[g]; P.gN[g] = V.gN[g]; P.gK[g] = V.gK[g]; }
+        cudaError_t le = cudaSuccess;
+        TRY(timed_launch(sys, "k_mlp_tc", st, [&] { le = rid_launch_mlp_tc(P, V.big, V.small, st); }));
+        if (le != cudaSuccess) return fail(RID_ERR_CUDA, "k_mlp_tc launch: %s", cudaGetErrorString(le));
+        E.aslices = V.CS;
+        sys->last_cs = V.CS;
+    } else if (mode == 1) {
+        TRY(timed_launch(sys, "k_mlp_fp32", st, [&] { rid_launch_mlp_fp32(E, sd, W, sys->S.C, st); }));
+    }
     TRY(timed_launch(sys, "k_finish", st, [&] {
-        rid_launch_finish(sys->S, sd, mode == 1 ? &sys->E : nullptr, lab, W, mode, kick, t, slot, cv, eps, en, T, st);
+        rid_launch_finish(sys->S, sd, mode == 1 ? &E : nullptr, lab, W, mode, kick, t, slot, cv, eps, en, T, st);
     }));
     CK(cudaGetLastError());
     return RID_OK;
@@ -667,13 +853,15 @@ extern "C" int rid_eval_forces(rid_system* sys, int32_t W, const float* x, int32
         // the per-walker rows of Aval / gradA are laid out for the call's W
         if (grad_out) CK(cudaMemcpyAsync(grad_out, sd.gradA, (size_t)M * nc * sizeof(float), ko, st));
         if (abar_out) {
-            std::vector<float> a((size_t)M * W);
+            const int ns = sys->precision == RID_PREC_BF16 ? sys->last_cs : 1;
+            std::vector<float> a((size_t)M * ns * W);
             CK(cudaMemcpyAsync(a.data(), sd.Aval, a.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             std::vector<float> ab(W, 0.0f);
             for (int w = 0; w < W; ++w) {
                 float acc = 0.0f;
-                for (int m = 0; m < M; ++m) acc += a[(size_t)m * W + w];
+                for (int m = 0; m < M; ++m)
+                    for (int q = 0; q < ns; ++q) acc += a[((size_t)m * ns + q) * W + w];
                 ab[w] = acc / (float)M;
             }
             CK(cudaMemcpyAsync(abar_out, ab.data(), W * sizeof(float),

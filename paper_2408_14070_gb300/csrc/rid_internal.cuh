@@ -31,6 +31,7 @@ struct SysDev {
 // Ensemble weights on the device, FP32 (plain path).
 struct EnsDev {
     int M, D, L, H, resnet;
+    int aslices;             // member values come as [M][aslices][W] partial sums
     float e0, e1;
     const float* W;          // per model, per layer: row-major [H][fin]
     const float* WT;         // per model, per layer: row-major [fin][H]

@@ -1,0 +1,144 @@
+"""GPU parity of the BF16 tensor-core ensemble path (tcgen05 + TMA) against
+the FP64 oracle.
+
+Tolerance (derived from the arithmetic, BF16 operands with FP32
+accumulation): weights and activations are rounded to BF16 (unit roundoff
+u = 2^-9) before each of the 2L GEMMs, and tanh uses the hardware
+approximation (relative error ~2^-11).  Each GEMM adds a relative error of a
+few u in the normwise sense, so after 2L = 8 GEMMs the member gradients carry
+~1e-2; the test bound is 3e-2 normwise per walker (member gradients, mean
+force) and 5e-2 on the model deviation eps (a difference of gradients).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2408_14070_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 3e-2
+EPS_TOL = 5e-2
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_2408_14070_gb300 import build, rid
+    build.build()
+    return rid
+
+
+@pytest.fixture
+def cluster():
+    old = os.environ.get("RID_MLP_CLUSTER")
+
+    def set_(v):
+        if v is None:
+            os.environ.pop("RID_MLP_CLUSTER", None)
+        else:
+            os.environ["RID_MLP_CLUSTER"] = str(v)
+    yield set_
+    set_(old)
+
+
+def normwise(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def run_eval(R, sp, ens, x, prec):
+    W = x.shape[0]
+    f = np.zeros((W, sp.n_beads, 3), np.float32)
+    eps = np.zeros(W, np.float32)
+    abar = np.zeros(W, np.float32)
+    g = np.zeros((ens.n_models, W, sp.n_cv), np.float32)
+    with R.System(sp) as sys:
+        sys.set_ensemble(ens, precision=prec)
+        sys.eval_forces(x, R.RID_BIAS_ENSEMBLE, f_out=f, eps_out=eps, abar_out=abar, grad_out=g)
+    return f, eps, abar, g
+
+
+@pytest.mark.parametrize("cs", [1, 2, 4])
+@pytest.mark.parametrize("n,C,W,M,L,H,seed", [
+    (200, 20, 300, 4, 4, 256, 1),      # the benchmark shape, ragged walker count
+    (22, 2, 16, 4, 3, 64, 2),          # tiny chain: D = 4 padded to 64
+    (60, 9, 130, 3, 2, 96, 3),         # width not a multiple of 64 (K-chunks of 32)
+])
+def test_bf16_member_gradients_eps_and_values(R, orc, cluster, cs, n, C, W, M, L, H, seed):
+    cluster(cs)
+    sp = I.make_system(n, C, seed)
+    x = I.make_chains(W, sp, seed)
+    ens = I.make_ensemble(M, 2 * C, L, H, seed, trust_lo=1e9, trust_hi=2e9)
+    f, eps, abar, g = run_eval(R, sp, ens, x, R.RID_PREC_BF16)
+    sample = sorted(set([0, 1, W // 2, W - 1] + list(range(0, W, max(1, W // 12)))))
+    for w in sample:
+        xd = x[w].astype(np.float64)
+        r = orc.total(sp, xd, ens=ens)
+        e = orc.ensemble(ens, r["s"])
+        for m in range(M):
+            assert normwise(g[m, w], e["gradA"][m]) < GRAD_TOL, (w, m)
+        assert abs(eps[w] - e["eps"]) <= EPS_TOL * abs(e["eps"]) + 1e-4
+        assert abs(abar[w] - e["Abar"]) <= GRAD_TOL * (abs(e["Abar"]) + 0.1)
+        fb = f[w] - orc.total(sp, xd)["f"]          # the CV (bias) part of the force
+        rb = r["f"] - orc.total(sp, xd)["f"]
+        assert normwise(fb, rb) < GRAD_TOL, w
+
+
+def test_bf16_width512_eight_members(R, orc, cluster):
+    """The precision-sweep shape (64 -> 512 x 4 -> 1, 8 members) on a sample."""
+    cluster(None)
+    sp = I.make_system(100, 32, 4)
+    W = 150
+    x = I.make_chains(W, sp, 4)
+    ens = I.make_ensemble(8, 64, 4, 512, 4, trust_lo=1e9, trust_hi=2e9)
+    f, eps, abar, g = run_eval(R, sp, ens, x, R.RID_PREC_BF16)
+    for w in [0, 77, 128, 149]:
+        e = orc.ensemble(ens, orc.cvs(sp, x[w].astype(np.float64))[0])
+        for m in range(8):
+            assert normwise(g[m, w], e["gradA"][m]) < GRAD_TOL
+        assert abs(eps[w] - e["eps"]) <= EPS_TOL * abs(e["eps"]) + 1e-4
+
+
+def test_bf16_cluster_sizes_agree_and_runs_are_deterministic(R, cluster):
+    sp = I.make_system(200, 20, 5)
+    x = I.make_chains(256, sp, 5)
+    ens = I.make_ensemble(4, 40, 4, 256, 5)
+    outs = {}
+    for cs in (1, 2, 4):
+        cluster(cs)
+        outs[cs] = run_eval(R, sp, ens, x, R.RID_PREC_BF16)
+    again = run_eval(R, sp, ens, x, R.RID_PREC_BF16)
+    assert all(np.array_equal(a, b) for a, b in zip(outs[4], again))
+    for cs in (1, 2):
+        # same products in the same K order: gradients agree to rounding
+        assert normwise(outs[cs][3], outs[4][3]) < 1e-5
+
+
+def test_bf16_switching_and_trajectory(R, orc, cluster):
+    cluster(None)
+    sp = I.make_system(200, 20, 6, output_freq=1)
+    W = 8
+    x0 = I.make_chains(W, sp, 6)
+    ens = I.make_ensemble(4, 40, 4, 256, 6)
+    eps_r = np.array([orc.ensemble(ens, orc.cvs(sp, xi.astype(np.float64))[0])["eps"] for xi in x0])
+    ens.trust_lo, ens.trust_hi = float(np.percentile(eps_r, 25)), float(np.percentile(eps_r, 75))
+    steps = 20
+    xo = np.zeros_like(x0)
+    eps = np.zeros((W, steps), np.float32)
+    with R.System(sp) as sys:
+        sys.set_ensemble(ens, precision=R.RID_PREC_BF16)
+        sys.explore(x0, steps, eps_out=eps, x_out=xo)
+    ref = orc.explore(sp, x0, steps, ens=ens)
+    # BF16 bias forces perturb the trajectory by ~1e-2 of the bias force, dt^2 scaled
+    assert np.all(np.abs(xo - ref["x"]) <= 1e-3 * (np.abs(ref["x"]) + 1))
+    assert np.all(np.abs(eps - ref["eps"]) <= EPS_TOL * np.abs(ref["eps"]) + 1e-3)
+
+
+def test_bf16_rejects_resnet(R):
+    sp = I.make_system(22, 2, 1)
+    ens = I.make_ensemble(4, 4, 3, 64, 1, resnet=True)
+    with R.System(sp) as sys:
+        with pytest.raises(R.RidError) as e:
+            sys.set_ensemble(ens, precision=R.RID_PREC_BF16)
+        assert e.value.code == R.RID_ERR_ARG
+        sys.set_ensemble(ens, precision=R.RID_PREC_FP32)
