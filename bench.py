@@ -289,30 +289,32 @@ def main():
     system.profile_enable(False)
     top = max(prof, key=lambda k: prof[k][0])
     avg_ms = prof[top][0] / prof[top][1]
-    if top.startswith("k_mlp"):
-        work = mlp_flops_per_walker_step(wl) * W
-        src = "k_mlp_fp32.cu" if top == "k_mlp_fp32" else "k_mlp_tc.cu"
-        if top == "k_mlp_fp32":
-            roof = {"bound": "alu", "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "peak_source": f"derived: {FP32_PEAK_NOTE}"}
-        else:
-            roof = {"bound": "tensor", "peak": None, "unit": "TFLOP/s", "peak_source": "MEASURED_PEAKS.json"}
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    if top == "k_mlp_tc":
+        work, src = mlp_flops_per_walker_step(wl) * W, "k_mlp_tc.cu"
+        peak = peaks.get("bf16_tflops")
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak if peak else 1900.0,
+                "peak_source": "measured bf16_tflops (burst)" if peak else "fallback 1.9 PFLOP/s bf16"}
         achieved = work / (avg_ms / 1e3) / 1e12
+    elif top == "k_mlp_fp32":
+        work, src = mlp_flops_per_walker_step(wl) * W, "k_mlp_fp32.cu"
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS, "peak_source": f"derived: {FP32_PEAK_NOTE}"}
+        achieved = work / (avg_ms / 1e3) / 1e12
+    elif top == "k_head":
+        # integrator: read x, v, f and write x, v (12 B each) per bead
+        work, src = 60 * wl["n_beads"] * W, "k_step.cu"
+        peak = peaks.get("hbm_gbs")
+        roof = {"bound": "hbm", "unit": "GB/s", "peak": peak if peak else 6800.0,
+                "peak_source": "measured hbm_gbs" if peak else "fallback 6.8 TB/s"}
+        achieved = work / (avg_ms / 1e3) / 1e9
     else:
-        work = pair_flops_per_walker_step(wl) * W
-        src = "k_step.cu"
-        roof = {"bound": "alu", "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "peak_source": f"derived: {FP32_PEAK_NOTE}"}
+        work, src = pair_flops_per_walker_step(wl) * W, "k_step.cu"
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS, "peak_source": f"derived: {FP32_PEAK_NOTE}"}
         achieved = work / (avg_ms / 1e3) / 1e12
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if roof["bound"] == "tensor":
-        try:
-            pk = json.load(open(peaks_path))
-            roof["peak"] = pk["bf16_tflops"]
-            roof["peak_source"] = "measured bf16_tflops (burst), MEASURED_PEAKS.json"
-        except (OSError, KeyError, ValueError):
-            roof["peak"] = 1900.0
-            roof["peak_source"] = "fallback 1.9 PFLOP/s bf16"
     roofline = {"kernel": top, "bound": roof["bound"], "achieved": achieved, "peak": roof["peak"],
                 "unit": roof["unit"], "frac": achieved / roof["peak"] if roof["peak"] else None,
                 "traffic": traffic_for(top, src, WORKLOAD), "work_per_launch": work,

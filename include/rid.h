@@ -65,8 +65,9 @@ enum { RID_BIAS_NONE = 0, RID_BIAS_ENSEMBLE = 1, RID_BIAS_RESTRAINT = 2 };
  *   U = sum_bonds k_b/2 (r - r0)^2 + sum_angles k_a/2 (theta - theta0)^2
  *     + sum_dihedrals sum_{n=1..3} k_n (1 + cos(n phi - delta_n))
  *     + sum_{|i-j|>=3, r^2 < rc^2} [4 eps ((sig/r)^12 - (sig/r)^6) - U(rc)]
- * The LJ inclusion test r^2 < rc^2 is taken in FP32 without fused
- * multiply-add.  Torsions use the IUPAC sign convention on [-pi, pi).
+ * The LJ inclusion test r^2 < rc^2 is taken in FP32 with
+ * r^2 = fma(dz, dz, fma(dy, dy, dx * dx)), d = x_j - x_i.  Torsions use the
+ * IUPAC sign convention on [-pi, pi).
  */
 typedef struct {
     int32_t n_beads;              /* N, 4 <= N <= 4096                          */
@@ -182,7 +183,7 @@ RID_API int rid_eval_forces(rid_system* sys, int32_t n_walkers, const float* x, 
 /*
  * LJ pair inclusion of the force kernel, as a bit mask: bit (j & 31) of word
  * [w][i][j >> 5] is set iff the pair (i, j) interacts (|i-j| >= 3 and FP32
- * r^2 < rc^2).  mask_out [W][N][ceil(N/32)] uint32.
+ * r^2 < rc^2, r^2 formed as in rid_system_desc).  mask_out [W][N][ceil(N/32)] uint32.
  */
 RID_API int rid_pair_mask(rid_system* sys, int32_t n_walkers, const float* x, uint32_t* mask_out,
                   int32_t mem, void* stream);

@@ -11,8 +11,8 @@
  * one function per step of the method, in the order the method applies them.
  * The only single-precision arithmetic is the Lennard-Jones inclusion test
  * r^2 < rc^2, which is an integer decision and is therefore taken in the same
- * precision as the GPU kernel (FP32, no fused multiply-add; build with
- * -ffp-contract=off).
+ * precision as the GPU kernel (FP32, r^2 formed with two fused multiply-adds
+ * in a fixed order; build with -ffp-contract=off so nothing else is fused).
  *
  * What each part follows (RiD-kit paper, arXiv 2408.14070):
  *   - mean force F(s) = grad_s A(s), A = -kT ln p(s)               (Box 2)
@@ -200,14 +200,15 @@ double orc_dihedral(const double* p /* [4][3] */, double* grad /* [4][3] or NULL
 /* terms[0..3] (if non-NULL) = bond, angle, dihedral, LJ energies.          */
 /* ------------------------------------------------------------------------ */
 
-/* Pair inclusion decision in FP32 without FMA (same precision as the kernel). */
+/* Pair inclusion decision, taken in the precision of the kernel: FP32
+ * differences and r^2 = fma(dz, dz, fma(dy, dy, dx dx)) with correctly rounded
+ * fused multiply-adds (C99 fmaf), so both sides decide identically. */
 static int lj_included(const double* xi, const double* xj, float rc2f)
 {
     float dx = (float)xj[0] - (float)xi[0];
     float dy = (float)xj[1] - (float)xi[1];
     float dz = (float)xj[2] - (float)xi[2];
-    float r2 = dx * dx + dy * dy;
-    r2 = r2 + dz * dz;
+    float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
     return r2 < rc2f;
 }
 

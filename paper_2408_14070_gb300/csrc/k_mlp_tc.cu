@@ -136,9 +136,6 @@ __device__ __forceinline__ void dsmem_bulk(uint32_t dst_cluster, uint32_t src, u
         "r"(src), "r"(bytes), "r"(bar_cluster)
         : "memory");
 }
-__device__ __forceinline__ void bulk_commit_wait_read() {
-    asm volatile("cp.async.bulk.commit_group;\ncp.async.bulk.wait_group.read 0;" ::: "memory");
-}
 __device__ __forceinline__ float tanh_fast(float x) {
     float y;
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -163,7 +160,6 @@ struct Smem {
     uint64_t acc_full;
     uint64_t a_full[2];
     uint64_t drain;
-    uint64_t slice_ready;
     uint32_t tmem_base;
     int abort_flag;
     float apart[2][128];
@@ -196,7 +192,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_init(smem_u32(&S.a_full[0]), 8);
         mbar_init(smem_u32(&S.a_full[1]), 8);
         mbar_init(smem_u32(&S.drain), 1);
-        mbar_init(smem_u32(&S.slice_ready), 8);
         S.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -301,6 +296,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int wg = tile * 128 + row;         // global walker
         const bool valid = wg < P.W;
         const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+        const int nsf = P.H / CS;                // this CTA's forward column slice
+        float* sbias = reinterpret_cast<float*>(stages + (size_t)NS * stage_bytes);   // [L][nsf]
+        float* swout = sbias + (size_t)L * nsf;                                        // [nsf]
+        // per-CTA copies of the biases / output weights of this column slice
+        for (int idx = e * 32 + lane; idx < (L + 1) * nsf; idx += 256) {
+            const int l = idx / nsf, c = idx - l * nsf;
+            const int gc = (int)q * nsf + c;
+            sbias[idx] = l < L ? __ldg(P.bias + ((size_t)m * L + l) * P.H + gc) : __ldg(P.wout + (size_t)m * P.H + gc);
+        }
         // GEMM 0 input: u (FP32, [W][D]) -> BF16 canonical tile, all Dp columns
         {
             unsigned char* A0 = Abuf[0];
@@ -320,11 +324,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&S.a_full[0]));
         }
+        asm volatile("bar.sync 1, 256;" ::: "memory");   // staged biases visible to all epilogue warps
         __nv_bfloat16* tsave_tile = P.tsave + ((size_t)m * P.ntiles + tile) * (size_t)L * 128 * P.H;
         float apart = 0.0f;
         for (int g = 0; g < G; ++g) {
-            if (!mbar_wait(smem_u32(&S.acc_full), g & 1, abort_flag, P.err, 8)) break;
-            fence_after();
             const int N = P.gN[g], ns = N / CS;
             const int col0 = (int)q * ns;              // global column of local column 0
             const int ngr = ns / 8, gh = ngr / 2;      // 8-column groups, per half
@@ -332,88 +335,108 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const bool fwd = g < L;
             const int l = fwd ? g : (G - 1 - g);       // layer of this GEMM
             unsigned char* Anext = Abuf[CS > 1 ? ((g + 1) & 1) : 0];
-            for (int gi = gbeg; gi < gend; ++gi) {
-                float acc[8];
-                tmem_ld8(trow + (uint32_t)(gi * 8), acc);
+            // prefetch the saved tanh values of the first batch (independent of the accumulator)
+            uint4 tpre[4];
+            if (!fwd && l > 0) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (gbeg + k < gend)
+                        tpre[k] = *reinterpret_cast<const uint4*>(tsave_tile + ((size_t)(l - 1) * 128 + row) * P.H +
+                                                                   col0 + (gbeg + k) * 8);
+            }
+            if (CS > 1 && g >= 1 && lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            __syncwarp();
+            if (!mbar_wait(smem_u32(&S.acc_full), g & 1, abort_flag, P.err, 8)) break;
+            fence_after();
+            for (int gb = gbeg; gb < gend; gb += 4) {
+                const int nb = gend - gb < 4 ? gend - gb : 4;
+                float acc[4][8];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < nb) tmem_ld8(trow + (uint32_t)((gb + k) * 8), acc[k]);
+                if (!fwd && l > 0 && gb != gbeg) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (k < nb)
+                            tpre[k] = *reinterpret_cast<const uint4*>(tsave_tile + ((size_t)(l - 1) * 128 + row) * P.H +
+                                                                       col0 + (gb + k) * 8);
+                }
                 tmem_wait_ld();
-                const int gc = col0 + gi * 8;          // global column of this group
-                if (fwd) {
-                    const float* bias = P.bias + ((size_t)m * L + l) * P.H + gc;
-                    float t[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) t[i] = tanh_fast(acc[i] + __ldg(bias + i));
-                    uint4 tw = make_uint4(pack_bf16(t[0], t[1]), pack_bf16(t[2], t[3]), pack_bf16(t[4], t[5]),
-                                          pack_bf16(t[6], t[7]));
-                    *reinterpret_cast<uint4*>(tsave_tile + ((size_t)l * 128 + row) * P.H + gc) = tw;
-                    uint4 ow;
-                    if (l == L - 1) {
-                        const float* wo = P.wout + (size_t)m * P.H + gc;
-                        float d[8];
+                for (int k = 0; k < 4; ++k) {
+                    if (k >= nb) break;
+                    const int gi = gb + k;
+                    const int gc = col0 + gi * 8;          // global column of this group
+                    const int lc = gi * 8;                 // column within this CTA's slice
+                    if (fwd) {
+                        const float* bias = sbias + (size_t)l * nsf + lc;
+                        float t[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const float w = __ldg(wo + i);
-                            apart = fmaf(w, t[i], apart);
-                            d[i] = w * (1.0f - t[i] * t[i]);
+                        for (int i = 0; i < 8; ++i) t[i] = tanh_fast(acc[k][i] + bias[i]);
+                        uint4 tw = make_uint4(pack_bf16(t[0], t[1]), pack_bf16(t[2], t[3]), pack_bf16(t[4], t[5]),
+                                              pack_bf16(t[6], t[7]));
+                        *reinterpret_cast<uint4*>(tsave_tile + ((size_t)l * 128 + row) * P.H + gc) = tw;
+                        uint4 ow;
+                        if (l == L - 1) {
+                            const float* wo = swout + lc;
+                            float d[8];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                apart = fmaf(wo[i], t[i], apart);
+                                d[i] = wo[i] * (1.0f - t[i] * t[i]);
+                            }
+                            ow = make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]),
+                                            pack_bf16(d[6], d[7]));
+                        } else {
+                            ow = tw;
                         }
-                        ow = make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]),
-                                        pack_bf16(d[6], d[7]));
-                    } else {
-                        ow = tw;
-                    }
-                    *reinterpret_cast<uint4*>(Anext + (size_t)(gc / 8) * 2048 + row * 16) = ow;
-                } else if (l > 0) {
-                    // G_{l-1} -> Delta_{l-1} = G (1 - t_{l-1}^2)
-                    const uint4 tw = *reinterpret_cast<const uint4*>(tsave_tile + ((size_t)(l - 1) * 128 + row) * P.H + gc);
-                    float t[8], d[8];
-                    unpack_bf16x8(tw, t);
+                        *reinterpret_cast<uint4*>(Anext + (size_t)(gc / 8) * 2048 + row * 16) = ow;
+                    } else if (l > 0) {
+                        // G_{l-1} -> Delta_{l-1} = G (1 - t_{l-1}^2)
+                        float t[8], d[8];
+                        unpack_bf16x8(tpre[k], t);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) d[i] = acc[i] * (1.0f - t[i] * t[i]);
-                    *reinterpret_cast<uint4*>(Anext + (size_t)(gc / 8) * 2048 + row * 16) =
-                        make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]),
-                                   pack_bf16(d[6], d[7]));
-                } else if (valid) {
-                    // G_0 = dA/du: dA/ds_j = -sin s_j g[2j] + cos s_j g[2j+1]
+                        for (int i = 0; i < 8; ++i) d[i] = acc[k][i] * (1.0f - t[i] * t[i]);
+                        *reinterpret_cast<uint4*>(Anext + (size_t)(gc / 8) * 2048 + row * 16) =
+                            make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]),
+                                       pack_bf16(d[6], d[7]));
+                    } else if (valid) {
+                        // G_0 = dA/du: dA/ds_j = -sin s_j g[2j] + cos s_j g[2j+1]
 #pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        const int j = gc / 2 + p;
-                        if (2 * j < P.D) {
-                            const float cs = __ldg(P.u + (size_t)wg * P.D + 2 * j);
-                            const float sn = __ldg(P.u + (size_t)wg * P.D + 2 * j + 1);
-                            P.gradA[((size_t)m * P.W + wg) * P.C + j] = -sn * acc[2 * p] + cs * acc[2 * p + 1];
+                        for (int p = 0; p < 4; ++p) {
+                            const int j = gc / 2 + p;
+                            if (2 * j < P.D) {
+                                const float cs = __ldg(P.u + (size_t)wg * P.D + 2 * j);
+                                const float sn = __ldg(P.u + (size_t)wg * P.D + 2 * j + 1);
+                                P.gradA[((size_t)m * P.W + wg) * P.C + j] = -sn * acc[k][2 * p] + cs * acc[k][2 * p + 1];
+                            }
                         }
                     }
                 }
             }
-            if (fwd && l == L - 1) {
-                S.apart[half][row] = apart;
-            }
+            if (fwd && l == L - 1) S.apart[half][row] = apart;
             fence_before();
             if (g == G - 1) break;
             fence_async_smem();
-            const int b = CS > 1 ? ((g + 1) & 1) : 0;
             __syncwarp();
-            if (CS > 1) {
-                // the 8 epilogue warps hand their finished slice to one thread,
-                // which copies it to every peer's buffer
-                if (lane == 0) mbar_arrive(smem_u32(&S.slice_ready));
-                if (e == 0 && lane == 0) {
-                    if (mbar_wait(smem_u32(&S.slice_ready), g & 1, abort_flag, P.err, 16)) {
-                        const uint32_t slice_bytes = (uint32_t)ns * 256u;
-                        const uint32_t src = smem_u32(Anext + (size_t)(col0 / 8) * 2048);
+            const int b = CS > 1 ? ((g + 1) & 1) : 0;
+            if (lane == 0) {
+                if (CS > 1) {
+                    // this warp's 32 rows of each of its column groups -> every peer's buffer
+                    for (int gi = gbeg; gi < gend; ++gi) {
+                        const uint32_t src = smem_u32(Anext + (size_t)((col0 + gi * 8) / 8) * 2048 + quarter * 512);
                         for (int p = 1; p < CS; ++p) {
                             const uint32_t peer = (q + (uint32_t)p) % (uint32_t)CS;
-                            dsmem_bulk(mapa(src, peer), src, slice_bytes, mapa(smem_u32(&S.a_full[b]), peer));
+                            dsmem_bulk(mapa(src, peer), src, 512u, mapa(smem_u32(&S.a_full[b]), peer));
                         }
-                        bulk_commit_wait_read();
                     }
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                 }
-                __syncwarp();
-            }
-            if (lane == 0) {
                 if (e == 0 && CS > 1) mbar_arrive_tx(smem_u32(&S.a_full[b]), (uint32_t)(CS - 1) * (uint32_t)ns * 256u);
                 else mbar_arrive(smem_u32(&S.a_full[b]));
             }
         }
+        if (CS > 1 && lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     }
     fence_before();
     __syncthreads();
@@ -439,7 +462,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 size_t rid_mlp_tc_smem_bytes(const TcArgs& P) {
     const size_t abytes = 128u * (size_t)P.Kmax * 2u;
-    return (P.CS > 1 ? 2 : 1) * abytes + (size_t)P.stages * P.stage_bytes;
+    return (P.CS > 1 ? 2 : 1) * abytes + (size_t)P.stages * P.stage_bytes +
+           sizeof(float) * (size_t)(P.L + 1) * (P.H / P.CS);
 }
 
 cudaError_t rid_launch_mlp_tc(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, cudaStream_t s) {

@@ -131,10 +131,17 @@ __device__ double bonded_energy_from(const SysDev& S, const float4* xs, int i) {
     return e;
 }
 
-// Pair inclusion: |i-j| >= 3 and r^2 < rc^2 with r^2 formed in FP32 without
-// fused multiply-add, ((dx dx + dy dy) + dz dz).
+// Pair inclusion: |i-j| >= 3 and r^2 < rc^2 with r^2 formed in FP32 as
+// fma(dz, dz, fma(dy, dy, dx dx)) (explicit round-to-nearest intrinsics, so
+// the compiler cannot reassociate it; the CPU reference forms it the same way).
 __device__ __forceinline__ float pair_r2(float3 d) {
-    return __fadd_rn(__fadd_rn(__fmul_rn(d.x, d.x), __fmul_rn(d.y, d.y)), __fmul_rn(d.z, d.z));
+    return __fmaf_rn(d.z, d.z, __fmaf_rn(d.y, d.y, __fmul_rn(d.x, d.x)));
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // Lennard-Jones force on bead i from every other bead (both orders of each
@@ -184,18 +191,250 @@ __device__ __forceinline__ T block_sum_ordered(T v, T* red) {
 }
 
 // ---------------------------------------------------------------------------
-template <bool INTEGRATE, bool ENERGY>
-__global__ void __launch_bounds__(256) k_force_cv(SysDev S, StateDev st, uint32_t step) {
-    extern __shared__ float4 xs[];
+// Bonded terms evaluated once per term index t (bond t, angle t, dihedral t)
+// into shared per-term force slots, then gathered per bead in a fixed order.
+__device__ __forceinline__ void bonded_terms_to_smem(const SysDev& S, const float4* xs, int t, float3* fB, float3* fA,
+                                                     float3* fD) {
+    const int N = S.N;
+    if (t + 1 < N) fB[t] = bond_force(S, f3(xs[t]), f3(xs[t + 1]));
+    if (t + 2 < N) {
+        float3 fa, fc, fb;
+        angle_forces(S, f3(xs[t]), f3(xs[t + 1]), f3(xs[t + 2]), fa, fc, fb);
+        fA[3 * t] = fa;
+        fA[3 * t + 1] = fc;
+        fA[3 * t + 2] = fb;
+    }
+    if (t + 3 < N) {
+        float3 g[4];
+        const float phi = rid_torsion(f3(xs[t]), f3(xs[t + 1]), f3(xs[t + 2]), f3(xs[t + 3]), g);
+        const float m = dihedral_mdU(S, t, phi);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) fD[4 * t + a] = m * g[a];
+    }
+}
+
+__device__ __forceinline__ float3 bonded_gather(const SysDev& S, int i, const float3* fB, const float3* fA,
+                                                const float3* fD) {
+    const int N = S.N;
+    float3 f = make_float3(0.f, 0.f, 0.f);
+    if (i + 1 < N) f = f + fB[i];
+    if (i >= 1) f = f - fB[i - 1];
+    if (i + 2 < N) f = f + fA[3 * i];
+    if (i >= 1 && i + 1 < N) f = f + fA[3 * (i - 1) + 1];
+    if (i >= 2) f = f + fA[3 * (i - 2) + 2];
+    if (i + 3 < N) f = f + fD[4 * i];
+    if (i >= 1 && i + 2 < N) f = f + fD[4 * (i - 1) + 1];
+    if (i >= 2 && i + 1 < N) f = f + fD[4 * (i - 2) + 2];
+    if (i >= 3) f = f + fD[4 * (i - 3) + 3];
+    return f;
+}
+
+// One Lennard-Jones interaction seen from bead i (d = x_j - x_i).  Adds
+// c d with c = (1/r^2) (s/r)^6 (2 (s/r)^6 - 1) for an included pair; the
+// -24 eps factor is applied once per bead.  SIG1: sigma = 1.
+template <bool EXCL, bool SIG1, bool ENERGY>
+__device__ __forceinline__ void lj_pair(const SysDev& S, float3 xi, float4 xj, int i, int j, float& fx, float& fy,
+                                        float& fz, float& el) {
+    const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+    const float r2 = pair_r2(make_float3(dx, dy, dz));
+    bool inc = r2 < S.rc2;
+    if (EXCL) inc = inc && (j - i > 2 || i - j > 2);
+    const float inv = rcp_approx(r2);
+    const float sr2 = SIG1 ? inv : S.sig2 * inv;
+    const float sr6 = sr2 * sr2 * sr2;
+    float c = inv * (sr6 * fmaf(2.0f, sr6, -1.0f));
+    c = inc ? c : 0.0f;
+    fx = fmaf(c, dx, fx);
+    fy = fmaf(c, dy, fy);
+    fz = fmaf(c, dz, fz);
+    if (ENERGY) el += inc ? (S.lj_eps4 * sr6 * (sr6 - 1.0f) - S.urc) : 0.0f;
+}
+
+template <bool SIG1, bool ENERGY>
+__device__ __forceinline__ void lj_row(const SysDev& S, const float4* xs, float3 xi, int i, int b0, int b1,
+                                       float& fx, float& fy, float& fz, float& el) {
+    const int N = S.N;
+#pragma unroll 8
+    for (int j = 0; j < b0; ++j) lj_pair<false, SIG1, ENERGY>(S, xi, xs[j], i, j, fx, fy, fz, el);
+    for (int j = b0; j <= b1; ++j) lj_pair<true, SIG1, ENERGY>(S, xi, xs[j], i, j, fx, fy, fz, el);
+#pragma unroll 8
+    for (int j = b1 + 1; j < N; ++j) lj_pair<false, SIG1, ENERGY>(S, xi, xs[j], i, j, fx, fy, fz, el);
+}
+
+// At most 224 threads (7 warps) and 40 registers per thread, so that seven
+// CTAs (one walker each) fit on an SM.
+constexpr int FF_THREADS = 224;
+
+// Force-field forces (bonded + all-pairs LJ) of every bead at the current
+// positions -> fff.  One CTA per walker.  BSMEM: bonded terms through shared
+// per-term slots (chains up to RID_BONDED_SMEM_MAX beads), else per bead.
+template <bool ENERGY, bool BSMEM>
+__global__ void __maxnreg__(40) k_ff(SysDev S, StateDev st) {
+    extern __shared__ float4 sm4[];
     __shared__ double red[32];
-    const int w = blockIdx.x, N = S.N, C = S.C;
+    const int w = blockIdx.x, N = S.N;
+    const int lane = threadIdx.x & 31;
+    float4* xs = sm4;                                         // [N] float4
+    float3* fB = reinterpret_cast<float3*>(xs + N);           // [N]  float3 (BSMEM only)
+    float3* fA = fB + N;                                      // [3N]
+    float3* fD = fA + 3 * N;                                  // [4N]  -> see rid_ff_smem_bytes
     const long long base = (long long)w * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) xs[i] = st.x[base + i];
+    __syncthreads();
+    if (BSMEM) {
+        for (int t = threadIdx.x; t < N; t += blockDim.x) bonded_terms_to_smem(S, xs, t, fB, fA, fD);
+        __syncthreads();
+    }
+    const bool sig1 = S.sig2 == 1.0f;
+    double e = 0.0;
+    const int iters = (N + blockDim.x - 1) / blockDim.x;
+    for (int it = 0; it < iters; ++it) {
+        const int i = it * blockDim.x + threadIdx.x;
+        const bool act = i < N;
+        const float3 xi = f3(xs[act ? i : N - 1]);
+        // j ranges: far (no exclusion possible for any lane of this warp) and
+        // the band [wlo - 2, whi + 2] around the warp's own beads
+        const int wlo = i - lane, whi = wlo + 31;
+        const int b0 = wlo - 2 > 0 ? wlo - 2 : 0;
+        const int b1 = whi + 2 < N - 1 ? whi + 2 : N - 1;
+        float fx = 0.f, fy = 0.f, fz = 0.f, el = 0.f;
+        if (sig1) lj_row<true, ENERGY>(S, xs, xi, i, b0, b1, fx, fy, fz, el);
+        else lj_row<false, ENERGY>(S, xs, xi, i, b0, b1, fx, fy, fz, el);
+        if (act) {
+            const float3 fb = BSMEM ? bonded_gather(S, i, fB, fA, fD) : bonded_force_on(S, xs, i);
+            const float s = -S.lj_eps24;
+            st.fff[base + i] = make_float4(fmaf(s, fx, fb.x), fmaf(s, fy, fb.y), fmaf(s, fz, fb.z), 0.0f);
+            if (ENERGY) e += 0.5 * (double)el + bonded_energy_from(S, xs, i);
+        }
+    }
+    if (ENERGY) {
+        const double tot = block_sum_ordered<double>(e, red);
+        if (threadIdx.x == 0) st.eff[w] = tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_head: the closing half of step t-1 (CV force from the ensemble or the
+// restraint, chain rule through the torsion Jacobians, B half-kick, traces and
+// FP64 label sums) fused with the opening half of step t (B A O A) and the
+// CVs at the new positions.
+//   FIN: finish the previous evaluation (f = fff + sum_j F_s,j ds_j/dx)
+//   KICK: apply the closing half-kick of the previous step (FIN only)
+//   INT: 0 nothing, 1 CVs at the current positions, 2 B-A-O-A then CVs
+// With FIN and INT = 0 the total force is stored (end of a call); with
+// FIN = 0 the opening kick uses the stored force.
+template <int MODE, bool FIN, bool KICK, int INT, bool ENERGY>
+__global__ void __maxnreg__(40) k_head(SysDev S, StateDev st, EnsDev E, LabelDev lab, long long t_fin,
+                                              int slot, float* __restrict__ cv_out, float* __restrict__ eps_out,
+                                              double* __restrict__ energy_out, long long T, uint32_t step) {
+    extern __shared__ float4 xs[];
+    __shared__ float Fs[RID_MAX_CV];
+    __shared__ float s_eps, s_abar;
+    __shared__ double red[32];
+    const int w = blockIdx.x, N = S.N, C = S.C, W = st.W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long base = (long long)w * N;
+    const float kick = S.half_dt * S.inv_mass;
+    if (FIN) {
+        if (MODE == 1) {
+            if (warp == 0) {
+                const float invM = 1.0f / (float)E.M;
+                // member values: lane k holds entries k and k + 32 of [M][aslices]
+                const int na = E.M * E.aslices;
+                float av = 0.0f;
+                for (int k = lane; k < na; k += 32) av += st.Aval[(long long)k * W + w];
+                float d2 = 0.0f;
+                for (int j = lane; j < C; j += 32) {
+                    float g[RID_MAX_MODELS];
+#pragma unroll
+                    for (int m = 0; m < RID_MAX_MODELS; ++m)
+                        g[m] = m < E.M ? st.gradA[((long long)m * W + w) * C + j] : 0.0f;
+                    float fb = 0.0f;
+#pragma unroll
+                    for (int m = 0; m < RID_MAX_MODELS; ++m) fb += g[m];
+                    fb *= invM;
+#pragma unroll
+                    for (int m = 0; m < RID_MAX_MODELS; ++m) {
+                        const float d = m < E.M ? g[m] - fb : 0.0f;
+                        d2 = fmaf(d, d, d2);
+                    }
+                    Fs[j] = fb;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+                    av += __shfl_xor_sync(0xffffffffu, av, o);
+                }
+                const float eps = sqrtf(d2 * invM);
+                float sig;
+                if (eps < E.e0) sig = 1.0f;
+                else if (eps >= E.e1) sig = 0.0f;
+                else sig = 0.5f * (1.0f + cospif((eps - E.e0) / (E.e1 - E.e0)));
+                __syncwarp();
+                for (int j = lane; j < C; j += 32) Fs[j] *= sig;
+                if (lane == 0) {
+                    s_abar = av * invM;
+                    s_eps = eps;
+                    st.eps[w] = eps;
+                }
+            }
+        } else if (MODE == 2) {
+            const bool sample = KICK && t_fin >= lab.n_equil;
+            long long b = 0;
+            if (sample) b = ((t_fin - lab.n_equil) * lab.B) / lab.K;
+            for (int j = threadIdx.x; j < C; j += blockDim.x) {
+                const long long o = (long long)w * C + j;
+                const double d = rid_wrapd((double)st.s[o] - lab.s0[o]);
+                Fs[j] = (float)(-lab.kappa[o] * d);
+                if (sample) {
+                    lab.sum[o] += d;
+                    lab.sum2[o] = fma(d, d, lab.sum2[o]);
+                    lab.bsum[o * lab.B + b] += d;
+                }
+            }
+            if (threadIdx.x == 0) { s_eps = 0.0f; s_abar = 0.0f; }
+        } else {
+            for (int j = threadIdx.x; j < C; j += blockDim.x) Fs[j] = 0.0f;
+            if (threadIdx.x == 0) { s_eps = 0.0f; s_abar = 0.0f; }
+        }
+        __syncthreads();
+        // traces of the finished step read the CVs before they are recomputed
+        if (slot >= 0) {
+            if (cv_out)
+                for (int j = threadIdx.x; j < C; j += blockDim.x)
+                    cv_out[((long long)w * T + slot) * C + j] = st.s[(long long)w * C + j];
+            if (eps_out && threadIdx.x == 0) eps_out[(long long)w * T + slot] = s_eps;
+        }
+    }
+    double ke = 0.0;
+    int bad = 0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         float4 x = st.x[base + i];
-        if (INTEGRATE) {
-            float4 v = st.v[base + i];
-            const float4 f = st.f[base + i];
-            const float kick = S.half_dt * S.inv_mass;
+        float4 v = st.v[base + i];
+        float4 f;
+        if (FIN) {
+            f = st.fff[base + i];
+            for (int e = S.acv_off[i]; e < S.acv_off[i + 1]; ++e) {
+                const int2 ja = S.acv[e];
+                const float4 g = st.J[((long long)w * C + ja.x) * 4 + ja.y];
+                const float fs = Fs[ja.x];
+                f.x = fmaf(fs, g.x, f.x);
+                f.y = fmaf(fs, g.y, f.y);
+                f.z = fmaf(fs, g.z, f.z);
+            }
+            bad |= !(isfinite(f.x) && isfinite(f.y) && isfinite(f.z));
+            if (KICK) {
+                v.x = fmaf(kick, f.x, v.x);
+                v.y = fmaf(kick, f.y, v.y);
+                v.z = fmaf(kick, f.z, v.z);
+                bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z));
+                if (ENERGY) ke += 0.5 / (double)S.inv_mass * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+            }
+            if (INT != 2) st.f[base + i] = f;
+        } else if (INT == 2) {
+            f = st.f[base + i];
+        }
+        if (INT == 2) {
             v.x = fmaf(kick, f.x, v.x);             // B
             v.y = fmaf(kick, f.y, v.y);
             v.z = fmaf(kick, f.z, v.z);
@@ -212,34 +451,37 @@ __global__ void __launch_bounds__(256) k_force_cv(SysDev S, StateDev st, uint32_
             x.y = fmaf(S.half_dt, v.y, x.y);
             x.z = fmaf(S.half_dt, v.z, x.z);
             st.x[base + i] = x;
-            st.v[base + i] = v;
         }
-        xs[i] = x;
+        if (INT == 2 || (FIN && KICK)) st.v[base + i] = v;
+        if (INT != 0) xs[i] = x;
     }
-    __syncthreads();
-    double e = 0.0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const float3 fb = bonded_force_on(S, xs, i);
-        const float3 fl = lj_force_on<ENERGY>(S, xs, i, e);
-        st.fff[base + i] = make_float4(fb.x + fl.x, fb.y + fl.y, fb.z + fl.z, 0.0f);
-        if (ENERGY) e += bonded_energy_from(S, xs, i);
+    if (FIN) {
+        if (bad) st.flags[w] = 1;
+        if (ENERGY) {
+            const double kt = block_sum_ordered<double>(ke, red);
+            if (threadIdx.x == 0 && slot >= 0 && energy_out) {
+                double* e = energy_out + ((long long)w * T + slot) * 3;
+                e[0] = st.eff[w];
+                e[1] = (MODE == 1) ? -(double)s_abar : 0.0;
+                e[2] = kt;
+            }
+        }
     }
-    for (int j = threadIdx.x; j < C; j += blockDim.x) {
-        const int4 q = S.cv[j];
-        float3 g[4];
-        const float s = rid_torsion(f3(xs[q.x]), f3(xs[q.y]), f3(xs[q.z]), f3(xs[q.w]), g);
-        const long long o = (long long)w * C + j;
-        st.s[o] = s;
+    if (INT != 0) {
+        __syncthreads();   // all Jacobian reads of the finish are done; positions staged
+        for (int j = threadIdx.x; j < C; j += blockDim.x) {
+            const int4 q = S.cv[j];
+            float3 g[4];
+            const float sj = rid_torsion(f3(xs[q.x]), f3(xs[q.y]), f3(xs[q.z]), f3(xs[q.w]), g);
+            const long long o = (long long)w * C + j;
+            st.s[o] = sj;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) st.J[o * 4 + a] = make_float4(g[a].x, g[a].y, g[a].z, 0.0f);
-        float sn, cs;
-        sincosf(s, &sn, &cs);
-        st.u[(long long)w * 2 * C + 2 * j] = cs;
-        st.u[(long long)w * 2 * C + 2 * j + 1] = sn;
-    }
-    if (ENERGY) {
-        const double tot = block_sum_ordered<double>(e, red);
-        if (threadIdx.x == 0) st.eff[w] = tot;
+            for (int a = 0; a < 4; ++a) st.J[o * 4 + a] = make_float4(g[a].x, g[a].y, g[a].z, 0.0f);
+            float sn, cs;
+            sincosf(sj, &sn, &cs);
+            st.u[(long long)w * 2 * C + 2 * j] = cs;
+            st.u[(long long)w * 2 * C + 2 * j + 1] = sn;
+        }
     }
 }
 
@@ -261,114 +503,6 @@ __global__ void __launch_bounds__(256) k_pair_mask(SysDev S, StateDev st, uint32
                 if ((r2 < S.rc2) && (j - i > 2 || i - j > 2)) bits |= 1u << b;
             }
             mask[((long long)w * N + i) * nw + jw] = bits;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Closing half of the step.  MODE: 0 no CV force, 1 ensemble bias, 2 restraint.
-template <int MODE, bool KICK, bool ENERGY>
-__global__ void __launch_bounds__(256) k_finish(SysDev S, StateDev st, EnsDev E, LabelDev lab, long long t,
-                                                int slot, float* __restrict__ cv_out,
-                                                float* __restrict__ eps_out, double* __restrict__ energy_out,
-                                                long long T) {
-    __shared__ float Fs[RID_MAX_CV];
-    __shared__ float s_eps, s_abar;
-    __shared__ double red[32];
-    const int w = blockIdx.x, N = S.N, C = S.C, W = st.W;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (MODE == 1) {
-        if (warp == 0) {
-            const float invM = 1.0f / (float)E.M;
-            float d2 = 0.0f;
-            for (int j = lane; j < C; j += 32) {
-                float fb = 0.0f;
-                for (int m = 0; m < E.M; ++m) fb += st.gradA[((long long)m * W + w) * C + j];
-                fb *= invM;
-                for (int m = 0; m < E.M; ++m) {
-                    const float d = st.gradA[((long long)m * W + w) * C + j] - fb;
-                    d2 = fmaf(d, d, d2);
-                }
-                Fs[j] = fb;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-            const float eps = sqrtf(d2 * invM);
-            float sig;
-            if (eps < E.e0) sig = 1.0f;
-            else if (eps >= E.e1) sig = 0.0f;
-            else sig = 0.5f * (1.0f + cospif((eps - E.e0) / (E.e1 - E.e0)));
-            __syncwarp();
-            for (int j = lane; j < C; j += 32) Fs[j] *= sig;
-            if (lane == 0) {
-                float ab = 0.0f;
-                for (int m = 0; m < E.M; ++m)
-                    for (int q = 0; q < E.aslices; ++q) ab += st.Aval[((long long)m * E.aslices + q) * W + w];
-                s_abar = ab * invM;
-                s_eps = eps;
-                st.eps[w] = eps;
-            }
-        }
-    } else if (MODE == 2) {
-        const bool sample = KICK && t >= lab.n_equil;
-        long long b = 0;
-        if (sample) b = ((t - lab.n_equil) * lab.B) / lab.K;
-        for (int j = threadIdx.x; j < C; j += blockDim.x) {
-            const long long o = (long long)w * C + j;
-            const double d = rid_wrapd((double)st.s[o] - lab.s0[o]);
-            Fs[j] = (float)(-lab.kappa[o] * d);
-            if (sample) {
-                lab.sum[o] += d;
-                lab.sum2[o] = fma(d, d, lab.sum2[o]);
-                lab.bsum[o * lab.B + b] += d;
-            }
-        }
-        if (threadIdx.x == 0) { s_eps = 0.0f; s_abar = 0.0f; }
-    } else {
-        for (int j = threadIdx.x; j < C; j += blockDim.x) Fs[j] = 0.0f;
-        if (threadIdx.x == 0) { s_eps = 0.0f; s_abar = 0.0f; }
-    }
-    __syncthreads();
-    const long long base = (long long)w * N;
-    const float kick = S.half_dt * S.inv_mass;
-    double ke = 0.0;
-    int bad = 0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        float4 f = st.fff[base + i];
-        for (int e = S.acv_off[i]; e < S.acv_off[i + 1]; ++e) {
-            const int2 ja = S.acv[e];
-            const float4 g = st.J[((long long)w * C + ja.x) * 4 + ja.y];
-            const float fs = Fs[ja.x];
-            f.x = fmaf(fs, g.x, f.x);
-            f.y = fmaf(fs, g.y, f.y);
-            f.z = fmaf(fs, g.z, f.z);
-        }
-        st.f[base + i] = f;
-        bad |= !(isfinite(f.x) && isfinite(f.y) && isfinite(f.z));
-        if (KICK) {
-            float4 v = st.v[base + i];
-            v.x = fmaf(kick, f.x, v.x);
-            v.y = fmaf(kick, f.y, v.y);
-            v.z = fmaf(kick, f.z, v.z);
-            st.v[base + i] = v;
-            bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z));
-            if (ENERGY) ke += 0.5 / (double)S.inv_mass * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
-        }
-    }
-    if (bad) st.flags[w] = 1;
-    if (slot >= 0) {
-        if (cv_out)
-            for (int j = threadIdx.x; j < C; j += blockDim.x)
-                cv_out[((long long)w * T + slot) * C + j] = st.s[(long long)w * C + j];
-        if (eps_out && threadIdx.x == 0) eps_out[(long long)w * T + slot] = s_eps;
-    }
-    if (ENERGY) {
-        const double kt = block_sum_ordered<double>(ke, red);
-        if (threadIdx.x == 0 && slot >= 0 && energy_out) {
-            double* e = energy_out + ((long long)w * T + slot) * 3;
-            e[0] = st.eff[w];
-            e[1] = (MODE == 1) ? -(double)s_abar : 0.0;
-            e[2] = kt;
         }
     }
 }
@@ -436,46 +570,62 @@ void rid_launch_mb(const SysDev& S, StateDev st, int W, uint32_t step0, cudaStre
     const long long n = (long long)W * S.N;
     if (n > 0) k_mb<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S, st, W, step0);
 }
-void rid_launch_force_cv(const SysDev& S, StateDev st, int W, bool integrate, bool energy, uint32_t step,
-                         cudaStream_t s) {
-    const int th = chain_threads(S.N);
-    const size_t sm = sizeof(float4) * (size_t)S.N;
-    if (integrate) {
-        if (energy) k_force_cv<true, true><<<W, th, sm, s>>>(S, st, step);
-        else k_force_cv<true, false><<<W, th, sm, s>>>(S, st, step);
-    } else {
-        if (energy) k_force_cv<false, true><<<W, th, sm, s>>>(S, st, step);
-        else k_force_cv<false, false><<<W, th, sm, s>>>(S, st, step);
-    }
-}
 void rid_launch_pair_mask(const SysDev& S, StateDev st, int W, uint32_t* mask, cudaStream_t s) {
     k_pair_mask<<<W, chain_threads(S.N), sizeof(float4) * (size_t)S.N, s>>>(S, st, mask);
 }
 
-template <int MODE>
-static void launch_finish_mode(const SysDev& S, StateDev st, const EnsDev& E, const LabelDev& L, int W, bool kick,
-                               bool energy, long long t, int slot, float* cv, float* eps, double* en, long long T,
-                               cudaStream_t s) {
-    const int th = chain_threads(S.N);
-    if (kick) {
-        if (energy) k_finish<MODE, true, true><<<W, th, 0, s>>>(S, st, E, L, t, slot, cv, eps, en, T);
-        else k_finish<MODE, true, false><<<W, th, 0, s>>>(S, st, E, L, t, slot, cv, eps, en, T);
+// Shared memory of k_ff: positions [N] float4 and, with per-term bonded
+// slots, bond [N] + angle [3N] + dihedral [4N] forces as float3.
+int rid_ff_smem_bytes(int N) {
+    return (int)(sizeof(float4) * (size_t)N + (N <= RID_BONDED_SMEM_MAX ? sizeof(float3) * 8 * (size_t)N : 0));
+}
+
+void rid_launch_ff(const SysDev& S, StateDev st, int W, bool energy, cudaStream_t s) {
+    const int th = chain_threads(S.N) < FF_THREADS ? chain_threads(S.N) : FF_THREADS;
+    const size_t sm = (size_t)rid_ff_smem_bytes(S.N);
+    const bool bsm = S.N <= RID_BONDED_SMEM_MAX;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_ff<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_ff<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    if (bsm) {
+        if (energy) k_ff<true, true><<<W, th, sm, s>>>(S, st);
+        else k_ff<false, true><<<W, th, sm, s>>>(S, st);
     } else {
-        k_finish<MODE, false, false><<<W, th, 0, s>>>(S, st, E, L, t, slot, cv, eps, en, T);
+        if (energy) k_ff<true, false><<<W, th, sm, s>>>(S, st);
+        else k_ff<false, false><<<W, th, sm, s>>>(S, st);
     }
 }
 
-void rid_launch_finish(const SysDev& S, StateDev st, const EnsDev* E, const LabelDev* lab, int W, int mode,
-                       bool kick, long long t, int slot, float* cv_out, float* eps_out, double* energy_out,
-                       long long T, cudaStream_t s) {
-    EnsDev e{};
-    LabelDev l{};
-    if (E) e = *E;
-    if (lab) l = *lab;
-    const bool energy = energy_out != nullptr && slot >= 0;
-    if (mode == 1) launch_finish_mode<1>(S, st, e, l, W, kick, energy, t, slot, cv_out, eps_out, energy_out, T, s);
-    else if (mode == 2) launch_finish_mode<2>(S, st, e, l, W, kick, energy, t, slot, cv_out, eps_out, energy_out, T, s);
-    else launch_finish_mode<0>(S, st, e, l, W, kick, energy, t, slot, cv_out, eps_out, energy_out, T, s);
+template <int MODE, bool FIN, bool KICK, int INT>
+static void head_e(const HeadArgs& a, cudaStream_t s) {
+    const int th = chain_threads(a.S.N);
+    const size_t sm = sizeof(float4) * (size_t)a.S.N;
+    if (a.energy)
+        k_head<MODE, FIN, KICK, INT, true><<<a.W, th, sm, s>>>(a.S, a.st, a.E, a.lab, a.t_fin, a.slot, a.cv_out,
+                                                                 a.eps_out, a.energy_out, a.T, a.step);
+    else
+        k_head<MODE, FIN, KICK, INT, false><<<a.W, th, sm, s>>>(a.S, a.st, a.E, a.lab, a.t_fin, a.slot, a.cv_out,
+                                                                  a.eps_out, a.energy_out, a.T, a.step);
+}
+
+template <int MODE>
+static void head_m(const HeadArgs& a, cudaStream_t s) {
+    // (FIN, KICK, INT) combinations used by the driver
+    if (!a.fin && a.integ == 1) head_e<MODE, false, false, 1>(a, s);
+    else if (!a.fin && a.integ == 2) head_e<MODE, false, false, 2>(a, s);
+    else if (a.fin && a.kick && a.integ == 2) head_e<MODE, true, true, 2>(a, s);
+    else if (a.fin && a.kick && a.integ == 0) head_e<MODE, true, true, 0>(a, s);
+    else if (a.fin && !a.kick && a.integ == 0) head_e<MODE, true, false, 0>(a, s);
+    else head_e<MODE, true, false, 2>(a, s);
+}
+
+void rid_launch_head(const HeadArgs& a, cudaStream_t s) {
+    if (a.mode == 1) head_m<1>(a, s);
+    else if (a.mode == 2) head_m<2>(a, s);
+    else head_m<0>(a, s);
 }
 
 void rid_launch_label_final(const LabelDev& lab, int W, int C, double* mf, double* se, double* sd, cudaStream_t s) {

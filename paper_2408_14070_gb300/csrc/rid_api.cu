@@ -106,6 +106,7 @@ struct rid_system {
     int W_act = 0;
     uint64_t step_next = 0;
     bool loaded = false;
+    bool pending = false;      // the last step's closing half (finish + kick) is still to run
     // kernel timing
     bool prof_on = false;
     std::vector<std::string> prof_names;
@@ -374,7 +375,7 @@ static int build_tc_variant(rid_system* sys, const std::vector<float>& W, long l
     V.member_rows = rows;
     V.stage_bytes = (unsigned)nsmax * V.ck * 2u;
     const size_t abytes = 128u * (size_t)V.Kmax * 2u * (CS > 1 ? 2 : 1);
-    const size_t budget = 220u * 1024u;
+    const size_t budget = 220u * 1024u - sizeof(float) * (size_t)(L + 1) * (H / CS);
     if (abytes + 2 * (size_t)V.stage_bytes > budget) return RID_OK;
     V.stages = (int)((budget - abytes) / V.stage_bytes);
     if (V.stages > TC_MAX_STAGES) V.stages = TC_MAX_STAGES;
@@ -433,6 +434,8 @@ static int pick_cluster(rid_system* sys, int W) {
         for (int i = 0; i < 3; ++i)
             if (sys->tcv[i].ok && sys->tcv[i].CS == want) return i;
     }
+    // smallest cluster that gives at least ~120 CTAs (measured on GB300 with
+    // 4 x 40-256x4-1 and 1024 walkers: cluster 4 takes 51 us, cluster 1 64 us)
     int best = -1;
     for (int i = 0; i < 3; ++i) {
         if (!sys->tcv[i].ok) continue;
@@ -440,6 +443,7 @@ static int pick_cluster(rid_system* sys, int W) {
         if (ntiles * M * sys->tcv[i].CS >= 120) return i;
     }
     return best;
+    return -1;
 }
 
 extern "C" int rid_set_ensemble(rid_system* sys, const rid_ensemble_desc* d) {
@@ -570,15 +574,13 @@ static int fetch_flags(rid_system* sys, int W, cudaStream_t st, bool* any) {
     return RID_OK;
 }
 
-// One force evaluation at the current positions (optionally preceded by the
-// B-A-O-A half of a step) and the closing kernel.
-static int evaluate(rid_system* sys, int W, bool integrate, uint32_t step, int mode, const LabelDev* lab, bool kick,
-                    long long t, int slot, float* cv, float* eps, double* en, long long T, cudaStream_t st) {
+// Force-field and ensemble kernels at the current positions (the CVs and the
+// MLP input have been written by the preceding k_head).
+static int launch_forces(rid_system* sys, int W, int mode, bool energy, cudaStream_t st) {
     StateDev sd = state_view(sys);
     sd.W = W;
-    const bool energy = en != nullptr && slot >= 0;
-    TRY(timed_launch(sys, "k_force_cv", st, [&] { rid_launch_force_cv(sys->S, sd, W, integrate, energy, step, st); }));
-    EnsDev E = sys->E;
+    TRY(timed_launch(sys, "k_ff", st, [&] { rid_launch_ff(sys->S, sd, W, energy, st); }));
+    EnsDev& E = sys->E;
     if (mode == 1 && sys->precision == RID_PREC_BF16) {
         const int vi = pick_cluster(sys, W);
         const TcVariant& V = sys->tcv[vi];
@@ -594,14 +596,82 @@ static int evaluate(rid_system* sys, int W, bool integrate, uint32_t step, int m
         TRY(timed_launch(sys, "k_mlp_tc", st, [&] { le = rid_launch_mlp_tc(P, V.big, V.small, st); }));
         if (le != cudaSuccess) return fail(RID_ERR_CUDA, "k_mlp_tc launch: %s", cudaGetErrorString(le));
         E.aslices = V.CS;
-        sys->last_cs = V.CS;
     } else if (mode == 1) {
+        E.aslices = 1;
         TRY(timed_launch(sys, "k_mlp_fp32", st, [&] { rid_launch_mlp_fp32(E, sd, W, sys->S.C, st); }));
     }
-    TRY(timed_launch(sys, "k_finish", st, [&] {
-        rid_launch_finish(sys->S, sd, mode == 1 ? &E : nullptr, lab, W, mode, kick, t, slot, cv, eps, en, T, st);
-    }));
     CK(cudaGetLastError());
+    return RID_OK;
+}
+
+// k_head: finish the previous evaluation and / or open the next step.
+static int launch_head(rid_system* sys, int W, int mode, const LabelDev* lab, bool fin, bool kick, int integ,
+                       long long t_fin, int slot, float* cv, float* eps, double* en, long long T, uint32_t step,
+                       cudaStream_t st) {
+    HeadArgs a{};
+    a.S = sys->S;
+    a.st = state_view(sys);
+    a.st.W = W;
+    if (mode == 1) a.E = sys->E;
+    if (lab) a.lab = *lab;
+    a.W = W;
+    a.mode = mode;
+    a.fin = fin;
+    a.kick = kick;
+    a.integ = integ;
+    a.t_fin = t_fin;
+    a.slot = fin ? slot : -1;
+    a.cv_out = cv;
+    a.eps_out = eps;
+    a.energy_out = en;
+    a.energy = fin && en != nullptr && slot >= 0;
+    a.T = T;
+    a.step = step;
+    TRY(timed_launch(sys, "k_head", st, [&] { rid_launch_head(a, st); }));
+    CK(cudaGetLastError());
+    return RID_OK;
+}
+
+// Evaluate the total force at the current positions (no step): CVs, force
+// field, ensemble, then the finish that stores f.
+static int evaluate_at_rest(rid_system* sys, int W, int mode, const LabelDev* lab, cudaStream_t st) {
+    TRY(launch_head(sys, W, mode, lab, false, false, 1, -1, -1, nullptr, nullptr, nullptr, 0, 0, st));
+    TRY(launch_forces(sys, W, mode, false, st));
+    TRY(launch_head(sys, W, mode, lab, true, false, 0, -1, -1, nullptr, nullptr, nullptr, 0, 0, st));
+    return RID_OK;
+}
+
+// n_steps BAOAB steps.  On entry either f is stored for the current x
+// (pending = false) or the closing half of the previous step is still to run
+// (pending = true, its forces and CVs are in the buffers).  The closing half of
+// the last step is run here only if it carries a trace or label sample
+// (close_last), else it is left pending for the next call or read.
+static int run_steps(rid_system* sys, int W, int mode, const LabelDev* lab, int64_t n_steps, uint64_t step0,
+                     float* cv, float* eps, double* en, long long T, bool& pending, bool close_last, cudaStream_t st) {
+    const int of = sys->S.output_freq;
+    auto slot_of = [&](long long t) { return ((t + 1) % of == 0) ? (int)((t + 1) / of - 1) : -1; };
+    for (long long t = 0; t < n_steps; ++t) {
+        const bool fin = t > 0 || pending;
+        TRY(launch_head(sys, W, mode, lab, fin, true, 2, t - 1, t > 0 ? slot_of(t - 1) : -1, cv, eps, en, T,
+                        (uint32_t)(step0 + t), st));
+        TRY(launch_forces(sys, W, mode, en != nullptr && slot_of(t) >= 0, st));
+        pending = true;
+    }
+    const bool need = n_steps > 0 && (close_last || slot_of(n_steps - 1) >= 0);
+    if (pending && (need || close_last)) {
+        TRY(launch_head(sys, W, mode, lab, true, true, 0, n_steps - 1, n_steps > 0 ? slot_of(n_steps - 1) : -1, cv,
+                        eps, en, T, 0, st));
+        pending = false;
+    }
+    return RID_OK;
+}
+
+// Run a pending closing half-step (no trace) so that f, v are complete.
+static int settle(rid_system* sys, cudaStream_t st) {
+    if (!sys->pending) return RID_OK;
+    TRY(launch_head(sys, sys->W_act, sys->has_ens ? 1 : 0, nullptr, true, true, 0, -1, -1, nullptr, nullptr, nullptr,
+                    0, 0, st));
+    sys->pending = false;
     return RID_OK;
 }
 
@@ -621,7 +691,8 @@ static int do_load(rid_system* sys, int W, const float* x0, const float* v0, uin
     if (v0) { TRY(load_xyz(sys, v0, sd.v, nb, mem, st)); ++sys->launches; }
     else { rid_launch_mb(sys->S, sd, W, (uint32_t)step0, st); ++sys->launches; }
     CK(cudaMemsetAsync(sys->flags.p, 0, (size_t)W * sizeof(int), st));
-    TRY(evaluate(sys, W, false, 0, sys->has_ens ? 1 : 0, nullptr, false, -1, -1, nullptr, nullptr, nullptr, 0, st));
+    TRY(evaluate_at_rest(sys, W, sys->has_ens ? 1 : 0, nullptr, st));
+    sys->pending = false;
     sys->W_act = W;
     sys->step_next = step0;
     sys->loaded = true;
@@ -636,6 +707,7 @@ static int do_advance(rid_system* sys, int64_t n_steps, float* cv_out, float* ep
     if (sys->step_next + (uint64_t)n_steps > (1ull << 32)) return fail(RID_ERR_ARG, "step counter would exceed 2^32");
     TRY(check_device(sys));
     const int W = sys->W_act, C = sys->S.C, of = sys->S.output_freq;
+    (void)of;
     const long long T = n_steps / of;
     const int mode = sys->has_ens ? 1 : 0;
     float* dcv = cv_out;
@@ -646,10 +718,7 @@ static int do_advance(rid_system* sys, int64_t n_steps, float* cv_out, float* ep
         if (eps_out) { TRY(sys->tr_eps.ensure((size_t)W * T * sizeof(float))); deps = sys->tr_eps.as<float>(); }
         if (energy_out) { TRY(sys->tr_en.ensure((size_t)W * T * 3 * sizeof(double))); den = sys->tr_en.as<double>(); }
     }
-    for (long long t = 0; t < n_steps; ++t) {
-        const int slot = ((t + 1) % of == 0) ? (int)((t + 1) / of - 1) : -1;
-        TRY(evaluate(sys, W, true, (uint32_t)(sys->step_next + t), mode, nullptr, true, t, slot, dcv, deps, den, T, st));
-    }
+    TRY(run_steps(sys, W, mode, nullptr, n_steps, sys->step_next, dcv, deps, den, T, sys->pending, false, st));
     sys->step_next += (uint64_t)n_steps;
     if (mem == RID_MEM_HOST && T > 0 && (cv_out || eps_out || energy_out)) {
         if (cv_out) CK(cudaMemcpyAsync(cv_out, dcv, (size_t)W * T * C * sizeof(float), cudaMemcpyDeviceToHost, st));
@@ -664,6 +733,7 @@ static int do_read(rid_system* sys, float* x_out, float* v_out, uint64_t* step_n
     if (!sys->loaded) return fail(RID_ERR_STATE, "no walkers loaded");
     if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "mem must be RID_MEM_HOST or RID_MEM_DEVICE");
     TRY(check_device(sys));
+    TRY(settle(sys, st));
     const int W = sys->W_act;
     const long long nb = (long long)W * sys->S.N;
     StateDev sd = state_view(sys);
@@ -755,6 +825,7 @@ extern "C" int rid_label(rid_system* sys, int32_t R, const float* x0, const floa
     if (step0 + (uint64_t)n_steps > (1ull << 32)) return fail(RID_ERR_ARG, "step0 + n_steps exceeds 2^32");
     TRY(check_device(sys));
     sys->loaded = false;   // these calls reuse the resident walker buffers
+    sys->pending = false;
     cudaStream_t st = (cudaStream_t)stream;
     TRY(ensure_state(sys, R));
     const int N = sys->S.N, C = sys->S.C;
@@ -784,9 +855,9 @@ extern "C" int rid_label(rid_system* sys, int32_t R, const float* x0, const floa
     if (v0) TRY(load_xyz(sys, v0, sd.v, nb, mem, st));
     else rid_launch_mb(sys->S, sd, R, (uint32_t)step0, st);
     CK(cudaMemsetAsync(sys->flags.p, 0, (size_t)R * sizeof(int), st));
-    TRY(evaluate(sys, R, false, 0, 2, &lab, false, -1, -1, nullptr, nullptr, nullptr, 0, st));
-    for (long long t = 0; t < n_steps; ++t)
-        TRY(evaluate(sys, R, true, (uint32_t)(step0 + t), 2, &lab, true, t, -1, nullptr, nullptr, nullptr, 0, st));
+    TRY(evaluate_at_rest(sys, R, 2, &lab, st));
+    bool pend = false;
+    TRY(run_steps(sys, R, 2, &lab, n_steps, step0, nullptr, nullptr, nullptr, 0, pend, true, st));
     double *dmf = mf_out, *dse = se_out, *dsd = std_out;
     if (mem == RID_MEM_HOST) {
         TRY(sys->out_mf.ensure(nc * sizeof(double)));
@@ -824,6 +895,7 @@ extern "C" int rid_eval_forces(rid_system* sys, int32_t W, const float* x, int32
         return fail(RID_ERR_ARG, "eps/abar/grad outputs need bias = RID_BIAS_ENSEMBLE");
     TRY(check_device(sys));
     sys->loaded = false;   // these calls reuse the resident walker buffers
+    sys->pending = false;
     cudaStream_t st = (cudaStream_t)stream;
     TRY(ensure_state(sys, W));
     const int N = sys->S.N, C = sys->S.C;
@@ -843,7 +915,7 @@ extern "C" int rid_eval_forces(rid_system* sys, int32_t W, const float* x, int32
     StateDev sd = state_view(sys);
     TRY(load_xyz(sys, x, sd.x, nb, mem, st));
     CK(cudaMemsetAsync(sys->flags.p, 0, (size_t)W * sizeof(int), st));
-    TRY(evaluate(sys, W, false, 0, bias, bias == 2 ? &lab : nullptr, false, -1, -1, nullptr, nullptr, nullptr, 0, st));
+    TRY(evaluate_at_rest(sys, W, bias, bias == 2 ? &lab : nullptr, st));
     TRY(store_xyz(sys, sd.f, f_out, nb, mem, st));
     const cudaMemcpyKind ko = mem == RID_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (s_out) CK(cudaMemcpyAsync(s_out, sd.s, nc * sizeof(float), ko, st));
@@ -853,7 +925,7 @@ extern "C" int rid_eval_forces(rid_system* sys, int32_t W, const float* x, int32
         // the per-walker rows of Aval / gradA are laid out for the call's W
         if (grad_out) CK(cudaMemcpyAsync(grad_out, sd.gradA, (size_t)M * nc * sizeof(float), ko, st));
         if (abar_out) {
-            const int ns = sys->precision == RID_PREC_BF16 ? sys->last_cs : 1;
+            const int ns = sys->E.aslices;
             std::vector<float> a((size_t)M * ns * W);
             CK(cudaMemcpyAsync(a.data(), sd.Aval, a.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
@@ -879,6 +951,7 @@ extern "C" int rid_pair_mask(rid_system* sys, int32_t W, const float* x, uint32_
     if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "bad mem");
     TRY(check_device(sys));
     sys->loaded = false;   // these calls reuse the resident walker buffers
+    sys->pending = false;
     cudaStream_t st = (cudaStream_t)stream;
     TRY(ensure_state(sys, W));
     const int N = sys->S.N;

@@ -13,6 +13,7 @@
 #define RID_MAX_BEADS 4096
 #define RID_MAX_WIDTH 512
 #define RID_MAX_BLOCKS 256
+#define RID_BONDED_SMEM_MAX 1024
 
 // --------------------------------------------------------------------------
 // Parameters of one bead-chain system, passed by value to kernels.
@@ -156,12 +157,28 @@ __device__ __forceinline__ double rid_wrapd(double d) {
 void rid_launch_pack(const float* src, float4* dst, long long n, cudaStream_t st);
 void rid_launch_unpack(const float4* src, float* dst, long long n, cudaStream_t st);
 void rid_launch_mb(const SysDev& S, StateDev st, int W, uint32_t step0, cudaStream_t s);
-void rid_launch_force_cv(const SysDev& S, StateDev st, int W, bool integrate, bool energy,
-                         uint32_t step, cudaStream_t s);
 void rid_launch_pair_mask(const SysDev& S, StateDev st, int W, uint32_t* mask, cudaStream_t s);
-void rid_launch_finish(const SysDev& S, StateDev st, const EnsDev* E, const LabelDev* lab, int W,
-                       int mode, bool kick, long long t, int slot, float* cv_out, float* eps_out,
-                       double* energy_out, long long T, cudaStream_t s);
+int rid_ff_smem_bytes(int N);
+void rid_launch_ff(const SysDev& S, StateDev st, int W, bool energy, cudaStream_t s);
+
+// Arguments of the fused finish / B-A-O-A / CV kernel.
+struct HeadArgs {
+    SysDev S;
+    StateDev st;
+    EnsDev E;
+    LabelDev lab;
+    int W, mode;
+    bool fin, kick, energy;
+    int integ;                 // 0 none, 1 CVs at current positions, 2 B-A-O-A then CVs
+    long long t_fin;           // local index of the step being finished
+    int slot;                  // trace slot of that step, -1 for none
+    float* cv_out;
+    float* eps_out;
+    double* energy_out;
+    long long T;
+    uint32_t step;             // Philox step of the opened step
+};
+void rid_launch_head(const HeadArgs& a, cudaStream_t s);
 void rid_launch_label_final(const LabelDev& lab, int W, int C, double* mf, double* se, double* sd,
                             cudaStream_t s);
 void rid_launch_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* words,

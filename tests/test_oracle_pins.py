@@ -52,6 +52,39 @@ def test_normals_are_standard_gaussian(orc):
     assert np.abs(orc.normals(b2[:10], 99) - z[:10]).min() > 0
 
 
+def fma32(a, b, c):
+    """Correctly rounded float32 fused multiply-add, from exact rational
+    arithmetic (round to nearest, ties to even)."""
+    from fractions import Fraction
+    a, b, c = np.float32(a), np.float32(b), np.float32(c)
+    q = Fraction(float(a)) * Fraction(float(b)) + Fraction(float(c))
+    f = np.float32(float(q))
+    cands = [np.nextafter(f, np.float32(-np.inf)), f, np.nextafter(f, np.float32(np.inf))]
+
+    def key(x):
+        odd = int(np.frombuffer(np.float32(x).tobytes(), np.uint32)[0]) & 1
+        return (abs(Fraction(float(x)) - q), odd)
+    return np.float32(min(cands, key=key))
+
+
+def r2_fma(d):
+    """r^2 as the kernel forms it: fma(dz, dz, fma(dy, dy, dx dx)), FP32."""
+    d = d.astype(np.float32)
+    return fma32(d[2], d[2], fma32(d[1], d[1], np.float32(d[0] * d[0])))
+
+
+def test_fma32_emulation_against_float64_where_exact():
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        a, b, c = (np.float32(v) for v in rng.normal(size=3))
+        # a*b is exact in float64 (24 + 24 bits), so float64 a*b + c rounded to
+        # float32 differs from the true fma only on double-rounding ties
+        ref = np.float32(float(a) * float(b) + float(c))
+        got = fma32(a, b, c)
+        assert abs(float(got) - float(ref)) <= float(np.spacing(np.float32(abs(ref)) if ref != 0 else np.float32(1e-38)))
+    assert fma32(np.float32(1 + 2 ** -23), np.float32(1 - 2 ** -23), np.float32(-1)) == np.float32(-2.0 ** -46)
+
+
 # --------------------------------------------------------------------------- geometry
 def test_dihedral_sign_convention_and_ties(orc):
     # looking down the p1->p2 axis, p0 projects on +x, p3 on +y: IUPAC +90 deg
@@ -139,19 +172,40 @@ def test_lj_pair_set_bruteforce_fp32_strict_cutoff(orc):
     x = np.zeros((8, 3), np.float32)
     x[:, 0] = np.array([0.0, 1.0, 2.0, 2.5, 3.4, 4.9, 6.0, 7.3], np.float32)
     x[:, 1] = np.array([0, 0.3, 0, 0.0, 0.1, 0, 0.4, 0], np.float32)
-    # hand enumeration of the candidate pairs |i - j| >= 3 with FP32 r^2
+    # hand enumeration of the candidate pairs |i - j| >= 3 with the FP32 r^2
     rc2 = np.float32(rc * rc)
     want = []
     for i in range(8):
         for j in range(i + 3, 8):
-            d = x[j] - x[i]
-            r2 = np.float32(np.float32(d[0] * d[0] + d[1] * d[1]) + d[2] * d[2])
-            if r2 < rc2:
+            if r2_fma(x[j] - x[i]) < rc2:
                 want.append((i, j))
     got = [tuple(p) for p in orc.lj_pairs(x, rc)]
     assert got == want
     assert (0, 3) not in got          # r = 2.5 exactly: excluded by the strict test
     assert (1, 4) in got and (2, 5) not in got
+
+
+def test_lj_pair_decision_follows_the_fused_form(orc):
+    """Search pairs whose r^2 lands within a few ulp of rc^2, where the fused
+    and unfused FP32 forms can disagree; the oracle must follow the fused one."""
+    rng = np.random.default_rng(11)
+    rc = 2.5
+    rc2 = np.float32(rc * rc)
+    found = 0
+    for _ in range(20000):
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        d = (u * rc * (1 + rng.uniform(-3e-7, 3e-7))).astype(np.float32)
+        fused = r2_fma(d)
+        plain = np.float32(np.float32(np.float32(d[0] * d[0]) + np.float32(d[1] * d[1])) + np.float32(d[2] * d[2]))
+        if (fused < rc2) != (plain < rc2):
+            x = np.zeros((4, 3), np.float32)
+            x[3] = d
+            assert len(orc.lj_pairs(x, rc)) == int(fused < rc2)
+            found += 1
+            if found >= 5:
+                break
+    assert found >= 1
 
 
 def test_lj_pairs_random_chain_bruteforce(orc):
@@ -161,9 +215,7 @@ def test_lj_pairs_random_chain_bruteforce(orc):
     want = []
     for i in range(30):
         for j in range(i + 3, 30):
-            d = (x[j] - x[i]).astype(np.float32)
-            r2 = np.float32(np.float32(d[0] * d[0] + d[1] * d[1]) + d[2] * d[2])
-            if r2 < rc2:
+            if r2_fma((x[j] - x[i]).astype(np.float32)) < rc2:
                 want.append((i, j))
     assert [tuple(p) for p in orc.lj_pairs(x, sp.lj_rc)] == want
 
