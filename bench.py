@@ -213,15 +213,12 @@ def main():
     ap.add_argument("--cpu-walkers", type=int, default=1024)
     ap.add_argument("--cpu-steps", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mlp-cluster", type=int, default=0, help="force the tensor-core MLP cluster size (1, 2, 4)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
         return
 
-    if args.mlp_cluster:
-        os.environ["RID_MLP_CLUSTER"] = str(args.mlp_cluster)
     import torch
     world, rank, local = dist_setup(args)
     torch.cuda.set_device(local)

@@ -1,26 +1,33 @@
 // k_mlp_tc.cu -- BF16 ensemble MLP on the 5th-generation tensor cores
 // (tcgen05.mma, accumulators in TMEM, weights streamed by tensor TMA).
 //
-// Work unit: one tile of 128 walkers x one ensemble member, split over a
-// cluster of CS CTAs (CS = 1, 2 or 4); CTA rank q computes output neurons
-// [q N/CS, (q+1) N/CS) of every layer.  For each member the chain of 2L GEMMs
+// Work unit: one CTA = one tile of 128 walkers x one ensemble member.  The
+// chain of 2L GEMMs
 //   forward  l = 0..L-1 :  Z_l = H_{l-1} W_l^T      (128 x H,   K = D' or H)
 //   backward l = L-1..0 :  G_{l-1} = Delta_l W_l     (128 x fin, K = H)
-// runs with the activation tile (A operand, BF16, canonical no-swizzle
-// K-major layout) in shared memory and the weight slice (B operand) streamed
-// in K-chunks through a ring of TMA stages.  Epilogues (8 warps) read the
-// FP32 accumulator from TMEM, apply bias + tanh (forward) or the tanh
-// derivative (backward), write the next A operand, and for CS > 1 copy their
-// column slice to every peer CTA's A buffer with DSMEM bulk copies.
+// runs with the activation tile (A operand, BF16) resident in shared memory
+// and the weights (B operand) streamed in 64-wide K-chunks through a ring of
+// TMA stages.  Both operands use the 128-byte swizzled K-major layout: rows of
+// 128 bytes (64 BF16 along K), the 16-byte chunk c of row r stored at chunk
+// c ^ (r mod 8), 8-row groups 1024 bytes apart.  The weights are swizzled on
+// the host, so the TMA copies them as plain bytes.
+//
+// Epilogues (16 warps) read the FP32 accumulator from TMEM and write the next
+// A operand chunk by chunk (64 columns); each chunk is released to the MMA
+// issuer through its own mbarrier, and the accumulator is double buffered in
+// TMEM, so the next GEMM's MMAs start on chunk 0 while later chunks of the
+// current epilogue are still being written.
 //   g_L = w_out, Delta_l = g_l * (1 - tanh^2 z_l), g_{l-1} = W_l^T Delta_l,
 //   dA/ds_j = -sin s_j g_0[2j] + cos s_j g_0[2j+1].
-// tanh(z_l) is kept as BF16 in a global scratch for the backward pass.
+// tanh(z_l) is kept as BF16 in a global scratch for the backward pass (laid
+// out so that a warp's 32 rows move one contiguous 512-byte line), and a
+// backward epilogue loads its part of it before waiting for the accumulator.
 //
-// Warp roles (320 threads): warp 0 = TMA producer, warp 1 = TMEM allocator +
-// MMA issuer, warps 2..9 = epilogue (two warps per TMEM lane quarter, each
-// with half of the columns).  Every wait is bounded in time; a wait that
-// expires sets an error word, drains the copies and MMAs already issued and
-// returns.
+// Warp roles (576 threads): warp 0 = TMA producer, warp 1 = TMEM allocator +
+// MMA issuer, warps 2..17 = epilogue: warp w reads TMEM lane quarter w mod 4
+// (rows 32 (w mod 4) ..) and, inside every 64-column chunk, the 16 columns
+// 16 ((w - 2) / 4) ...  Every wait is bounded in time; a wait that expires
+// sets an error word, drains what was issued and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -29,8 +36,9 @@
 
 namespace {
 
-constexpr int NTHREADS = 320;
 constexpr int EPI_WARP0 = 2;
+constexpr int EPI_WARPS = 16;                       // 4 per TMEM lane quarter
+constexpr int NTHREADS = 32 * (EPI_WARP0 + EPI_WARPS);
 constexpr unsigned long long WAIT_NS = 1000000000ull;   // 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -75,11 +83,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile 
     }
 }
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    // tcgen05 shared-memory matrix descriptor, no swizzle, K-major operand:
-    // start >> 4 | LBO >> 4 << 16 | SBO >> 4 << 32 | version 1 << 46
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+// tcgen05 shared-memory matrix descriptor for a K-major operand in the
+// 128-byte swizzled layout: start >> 4, leading byte offset 16 (unused for
+// this layout), stride byte offset 1024 (between 8-row groups), version 1 at
+// bit 46, layout type 2 (128-byte swizzle) at bits 61-63.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
 }
 __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
     // kind::f16 instruction descriptor: D F32 (bit 4), A BF16 (bits 7-9 = 1),
@@ -116,34 +126,20 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
         : "memory");
 }
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ uint32_t mapa(uint32_t a, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ void dsmem_bulk(uint32_t dst_cluster, uint32_t src, uint32_t bytes, uint32_t bar_cluster) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst_cluster),
-        "r"(src), "r"(bytes), "r"(bar_cluster)
-        : "memory");
-}
-__device__ __forceinline__ float tanh_fast(float x) {
-    float y;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+// tanh of two values rounded to BF16, result packed as BF16x2 (the operand
+// and scratch format); hardware approximation with BF16 output precision.
+__device__ __forceinline__ uint32_t tanh_bf16x2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    uint32_t x = *reinterpret_cast<uint32_t*>(&h), y;
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(x));
     return y;
 }
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ uint4 pack8(const float (&v)[8]) {
+    return make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
 }
 __device__ __forceinline__ void unpack_bf16x8(uint4 w, float (&v)[8]) {
     const uint32_t u[4] = {w.x, w.y, w.z, w.w};
@@ -153,34 +149,49 @@ __device__ __forceinline__ void unpack_bf16x8(uint4 w, float (&v)[8]) {
         v[2 * i + 1] = __uint_as_float(u[i] & 0xFFFF0000u);
     }
 }
+// Element offset of (layer l, row, 8-column group starting at col) in a
+// tile's saved-tanh scratch [L][H/8][128][8]: the 32 rows of a warp touch one
+// contiguous 512-byte line.
+__device__ __forceinline__ size_t ts_off(int l, int row, int col, int H) {
+    return (((size_t)l * (H / 8) + (col >> 3)) * 128 + row) * 8;
+}
+// Byte offset of (row, column col; col a multiple of 8) in the 128-row
+// swizzled A tile: 64-column atoms of 128 rows x 128 bytes.
+__device__ __forceinline__ uint32_t a_off(int row, int col) {
+    const int atom = col >> 6, ch = (col >> 3) & 7;
+    return (uint32_t)atom * (128u * 128u) + (uint32_t)row * 128u + (uint32_t)((ch ^ (row & 7)) << 4);
+}
 
 struct Smem {
     uint64_t full[TC_MAX_STAGES];
     uint64_t empty[TC_MAX_STAGES];
-    uint64_t acc_full;
-    uint64_t a_full[2];
+    uint64_t acc_full[2];
+    uint64_t acc_empty[2];
+    uint64_t a_chunk[TC_MAX_KCHUNKS];
     uint64_t drain;
     uint32_t tmem_base;
     int abort_flag;
-    float apart[2][128];
+    float apart[4][128];
 };
 
-__global__ void __launch_bounds__(NTHREADS, 1)
+// 18 warps spread 5/5/4/4 over the four schedulers, each with 16K registers:
+// at most 96 registers per thread
+__global__ void __maxnreg__(96)
     k_mlp_tc(const __grid_constant__ TcArgs P, const __grid_constant__ CUtensorMap map_big,
              const __grid_constant__ CUtensorMap map_small) {
-    extern __shared__ __align__(1024) unsigned char dsm[];
+    extern __shared__ __align__(1024) unsigned char dsm_raw[];
+    // swizzled tiles need 1024-byte aligned atoms
+    unsigned char* dsm =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
     __shared__ Smem S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int CS = P.CS;
-    const uint32_t q = CS > 1 ? cluster_rank() : 0u;
-    const int tile = blockIdx.x / CS, m = blockIdx.y;
+    const int tile = blockIdx.x, m = blockIdx.y;
     const int L = P.L, G = 2 * L;
-    const int Kmax = P.Kmax;
-    const uint32_t abytes = 128u * (uint32_t)Kmax * 2u;
-    unsigned char* Abuf[2] = {dsm, dsm + (CS > 1 ? abytes : 0u)};
-    unsigned char* stages = dsm + (CS > 1 ? 2u : 1u) * abytes;
+    unsigned char* Abuf = dsm;                                     // [Kpmax/64][128 rows][128 B]
+    unsigned char* stages = dsm + (size_t)P.Kpmax * 256u;          // 128 rows x 2 B per column
     const uint32_t stage_bytes = P.stage_bytes;
     const int NS = P.stages;
+    const int NACC = P.nacc;
     volatile int* abort_flag = &S.abort_flag;
 
     if (threadIdx.x == 0) {
@@ -188,9 +199,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(smem_u32(&S.full[s]), 1);
             mbar_init(smem_u32(&S.empty[s]), 1);
         }
-        mbar_init(smem_u32(&S.acc_full), 1);
-        mbar_init(smem_u32(&S.a_full[0]), 8);
-        mbar_init(smem_u32(&S.a_full[1]), 8);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&S.acc_full[b]), 1);
+            mbar_init(smem_u32(&S.acc_empty[b]), EPI_WARPS);
+        }
+        for (int j = 0; j < TC_MAX_KCHUNKS; ++j) mbar_init(smem_u32(&S.a_chunk[j]), EPI_WARPS);
         mbar_init(smem_u32(&S.drain), 1);
         S.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -202,8 +215,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     fence_before();
-    if (CS > 1) cluster_sync();
-    else __syncthreads();
+    __syncthreads();
     fence_after();
     const uint32_t tmem = S.tmem_base;
 
@@ -215,26 +227,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int s = 0; s < NS; ++s) last_it[s] = -1;
             bool ok = true;
             for (int g = 0; g < G && ok; ++g) {
-                const int N = P.gN[g], K = P.gK[g], ns = N / CS;
-                const int nch = K / P.ck;
-                const uint32_t bytes = (uint32_t)ns * P.ck * 2u;
-                const int rows = (int)(bytes / 128u);
-                for (int c = 0; c < nch; ++c, ++it) {
-                    const int s = it % NS;
-                    if (!mbar_wait(smem_u32(&S.empty[s]), ((it / NS) & 1) ^ 1, abort_flag, P.err, 1)) { ok = false; break; }
-                    mbar_arrive_tx(smem_u32(&S.full[s]), bytes);
-                    last_it[s] = it;
-                    const long long row0 = (long long)m * P.member_rows + P.grow[g] + (long long)(c * CS + (int)q) * rows;
-                    uint32_t dst = smem_u32(stages + (size_t)s * stage_bytes);
-                    int r = 0;
-                    for (; r + 64 <= rows; r += 64, dst += 8192u)
-                        tma_load_2d(dst, &map_big, 0, (int)(row0 + r), smem_u32(&S.full[s]));
-                    for (; r < rows; r += 8, dst += 1024u)
-                        tma_load_2d(dst, &map_small, 0, (int)(row0 + r), smem_u32(&S.full[s]));
-                }
+                const int N = P.gN[g], nch = P.gKp[g] / 64;
+                for (int c = 0; c < nch && ok; ++c)
+                    for (int n0 = 0; n0 < N; n0 += 256, ++it) {
+                        const int rows = N - n0 < 256 ? N - n0 : 256;
+                        const int s = it % NS;
+                        if (!mbar_wait(smem_u32(&S.empty[s]), ((it / NS) & 1) ^ 1, abort_flag, P.err, 1)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_tx(smem_u32(&S.full[s]), (uint32_t)rows * 128u);
+                        last_it[s] = it;
+                        const long long row0 = (long long)m * P.member_rows + P.grow[g] + (long long)c * N + n0;
+                        uint32_t dst = smem_u32(stages + (size_t)s * stage_bytes);
+                        int r = 0;
+                        for (; r + 64 <= rows; r += 64, dst += 8192u)
+                            tma_load_2d(dst, &map_big, 0, (int)(row0 + r), smem_u32(&S.full[s]));
+                        for (; r < rows; r += 8, dst += 1024u)
+                            tma_load_2d(dst, &map_small, 0, (int)(row0 + r), smem_u32(&S.full[s]));
+                    }
             }
             if (!ok) {
-                // let the loads already issued land before the CTA can exit
+                // the loads already issued land before the CTA can exit
                 for (int s = 0; s < NS; ++s)
                     if (last_it[s] >= 0) {
                         const unsigned long long t0 = gtimer();
@@ -247,159 +261,161 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) {
             int it = 0;
             bool ok = true;
-            int issued = 0;
+            uint32_t cpar = 0;   // phase bit of every a_chunk[] barrier
             for (int g = 0; g < G && ok; ++g) {
-                const int N = P.gN[g], K = P.gK[g], ns = N / CS;
-                const int nch = K / P.ck;
-                const int b = CS > 1 ? (g & 1) : 0;
-                const uint32_t apar = CS > 1 ? ((g >> 1) & 1) : (g & 1);
-                if (!mbar_wait(smem_u32(&S.a_full[b]), apar, abort_flag, P.err, 2)) { ok = false; break; }
-                fence_after();
-                const uint32_t abase = smem_u32(Abuf[b]);
-                const uint32_t id = idesc_bf16(128, ns < 256 ? ns : 256);
-                for (int c = 0; c < nch; ++c, ++it) {
-                    const int s = it % NS;
-                    if (!mbar_wait(smem_u32(&S.full[s]), (it / NS) & 1, abort_flag, P.err, 4)) { ok = false; break; }
-                    fence_after();
-                    const uint32_t bbase = smem_u32(stages + (size_t)s * stage_bytes);
-                    for (int kk = 0; kk < P.ck / 16; ++kk) {
-                        const int k0 = c * P.ck + kk * 16;   // first K index of this MMA
-                        // A: k-block stride 128 rows x 16 B = 2048 B, 8-row group stride 128 B
-                        const uint64_t ad = smem_desc(abase + (uint32_t)(k0 / 8) * 2048u, 2048u, 128u);
-                        // B slice: k-block stride ns/8 x 128 B, 8-row group stride 128 B
-                        for (int n0 = 0; n0 < ns; n0 += 256) {
-                            // rows n0.. of the slice start n0/8 row groups (128 B each) further
-                            const uint64_t bd = smem_desc(bbase + (uint32_t)(kk * 2) * (uint32_t)ns * 16u +
-                                                              (uint32_t)(n0 / 8) * 128u,
-                                                          (uint32_t)ns * 16u, 128u);
-                            mma_bf16(tmem + (uint32_t)n0, ad, bd, ns - n0 >= 256 ? id : idesc_bf16(128, ns - n0),
-                                     (c | kk) != 0);
-                            ++issued;
-                        }
-                    }
-                    mma_commit(smem_u32(&S.empty[s]));
+                const int N = P.gN[g], nch = P.gKp[g] / 64;
+                const int b = g % NACC;
+                const uint32_t dacc = tmem + (uint32_t)(b * P.acc_cols);
+                if (g >= NACC &&
+                    !mbar_wait(smem_u32(&S.acc_empty[b]), ((g / NACC) - 1) & 1, abort_flag, P.err, 2)) {
+                    ok = false;
+                    break;
                 }
-                if (ok) mma_commit(smem_u32(&S.acc_full));
+                for (int c = 0; c < nch && ok; ++c) {
+                    if (!mbar_wait(smem_u32(&S.a_chunk[c]), (cpar >> c) & 1u, abort_flag, P.err, 4)) {
+                        ok = false;
+                        break;
+                    }
+                    cpar ^= 1u << c;
+                    fence_after();
+                    const uint32_t a_atom = smem_u32(Abuf) + (uint32_t)c * (128u * 128u);
+                    for (int n0 = 0; n0 < N; n0 += 256, ++it) {
+                        const int rows = N - n0 < 256 ? N - n0 : 256;
+                        const int s = it % NS;
+                        if (!mbar_wait(smem_u32(&S.full[s]), (it / NS) & 1, abort_flag, P.err, 4)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint32_t b_atom = smem_u32(stages + (size_t)s * stage_bytes);
+                        const uint32_t id = idesc_bf16(128, rows);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)   // K = 16 per MMA: 32 bytes into the 128-byte rows
+                            mma_bf16(dacc + (uint32_t)n0, desc_sw128(a_atom + 32u * kk),
+                                     desc_sw128(b_atom + 32u * kk), id, (c | kk) != 0);
+                        mma_commit(smem_u32(&S.empty[s]));
+                    }
+                }
+                if (ok) mma_commit(smem_u32(&S.acc_full[b]));
             }
             // every MMA issued has completed before TMEM can be released
             mma_commit(smem_u32(&S.drain));
             const unsigned long long t0 = gtimer();
             while (!mbar_try(smem_u32(&S.drain), 0) && gtimer() - t0 < WAIT_NS) {}
-            (void)issued;
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int e = warp - EPI_WARP0;          // 0..7
+        const int e = warp - EPI_WARP0;          // 0..15
         const int quarter = warp & 3;            // TMEM lane quarter this warp may access
-        const int half = e >> 2;                 // column half
+        const int sub = e >> 2;                  // 16-column slice of every 64-column chunk
         const int row = quarter * 32 + lane;     // walker within the tile
         const int wg = tile * 128 + row;         // global walker
         const bool valid = wg < P.W;
         const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
-        const int nsf = P.H / CS;                // this CTA's forward column slice
-        float* sbias = reinterpret_cast<float*>(stages + (size_t)NS * stage_bytes);   // [L][nsf]
-        float* swout = sbias + (size_t)L * nsf;                                        // [nsf]
-        // per-CTA copies of the biases / output weights of this column slice
-        for (int idx = e * 32 + lane; idx < (L + 1) * nsf; idx += 256) {
-            const int l = idx / nsf, c = idx - l * nsf;
-            const int gc = (int)q * nsf + c;
-            sbias[idx] = l < L ? __ldg(P.bias + ((size_t)m * L + l) * P.H + gc) : __ldg(P.wout + (size_t)m * P.H + gc);
-        }
-        // GEMM 0 input: u (FP32, [W][D]) -> BF16 canonical tile, all Dp columns
+        const int H = P.H;
+        const int ET = 32 * EPI_WARPS;
+        // GEMM 0 input first: u (FP32, [W][D]) -> BF16, chunk by chunk (zeros past D)
         {
-            unsigned char* A0 = Abuf[0];
-            const int ngroups = P.Dp / 8;
-            for (int kb = half; kb < ngroups; kb += 2) {
-                float v[8];
+            const int nch0 = P.gKp[0] / 64;
+            for (int c = 0; c < nch0; ++c) {
+                for (int k8 = 0; k8 < 2; ++k8) {
+                    const int col = c * 64 + sub * 16 + k8 * 8;
+                    float v[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int k = kb * 8 + i;
-                    v[i] = (valid && k < P.D) ? __ldg(P.u + (size_t)wg * P.D + k) : 0.0f;
+                    for (int i = 0; i < 8; ++i) {
+                        const int k = col + i;
+                        v[i] = (valid && k < P.D) ? __ldg(P.u + (size_t)wg * P.D + k) : 0.0f;
+                    }
+                    *reinterpret_cast<uint4*>(Abuf + a_off(row, col)) = pack8(v);
                 }
-                uint4 w4 = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
-                                      pack_bf16(v[6], v[7]));
-                *reinterpret_cast<uint4*>(A0 + (size_t)kb * 2048 + row * 16) = w4;
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&S.a_chunk[c]));
             }
-            fence_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&S.a_full[0]));
         }
-        asm volatile("bar.sync 1, 256;" ::: "memory");   // staged biases visible to all epilogue warps
-        __nv_bfloat16* tsave_tile = P.tsave + ((size_t)m * P.ntiles + tile) * (size_t)L * 128 * P.H;
+        float* sbias = reinterpret_cast<float*>(stages + (size_t)NS * stage_bytes);   // [L][H]
+        float* swout = sbias + (size_t)L * H;                                          // [H]
+        for (int idx = e * 32 + lane; idx < (L + 1) * H; idx += ET) {
+            const int l = idx / H, c = idx - l * H;
+            sbias[idx] = l < L ? __ldg(P.bias + ((size_t)m * L + l) * H + c) : __ldg(P.wout + (size_t)m * H + c);
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(ET) : "memory");   // all epilogue warps, before any bounded wait
+        __nv_bfloat16* tsave_tile = P.tsave + ((size_t)m * P.ntiles + tile) * (size_t)L * 128 * H;
         float apart = 0.0f;
         for (int g = 0; g < G; ++g) {
-            const int N = P.gN[g], ns = N / CS;
-            const int col0 = (int)q * ns;              // global column of local column 0
-            const int ngr = ns / 8, gh = ngr / 2;      // 8-column groups, per half
-            const int gbeg = half * gh, gend = gbeg + gh;
+            const int N = P.gN[g], nch = (N + 63) / 64;
             const bool fwd = g < L;
             const int l = fwd ? g : (G - 1 - g);       // layer of this GEMM
-            unsigned char* Anext = Abuf[CS > 1 ? ((g + 1) & 1) : 0];
-            // prefetch the saved tanh values of the first batch (independent of the accumulator)
-            uint4 tpre[4];
+            const int b = g % NACC;
+            // saved tanh of layer l-1 for this warp's columns, loaded before the wait
+            constexpr int PREF = 2;                    // chunks prefetched; later ones load in place
+            uint4 tall[PREF][2];
             if (!fwd && l > 0) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (gbeg + k < gend)
-                        tpre[k] = *reinterpret_cast<const uint4*>(tsave_tile + ((size_t)(l - 1) * 128 + row) * P.H +
-                                                                   col0 + (gbeg + k) * 8);
+                for (int c = 0; c < PREF; ++c)
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int col = c * 64 + sub * 16 + k * 8;
+                        if (c < nch && col < N)
+                            tall[c][k] = *reinterpret_cast<const uint4*>(tsave_tile + ts_off(l - 1, row, col, H));
+                    }
             }
-            if (CS > 1 && g >= 1 && lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-            __syncwarp();
-            if (!mbar_wait(smem_u32(&S.acc_full), g & 1, abort_flag, P.err, 8)) break;
+            if (!mbar_wait(smem_u32(&S.acc_full[b]), (g / NACC) & 1, abort_flag, P.err, 8)) break;
             fence_after();
-            for (int gb = gbeg; gb < gend; gb += 4) {
-                const int nb = gend - gb < 4 ? gend - gb : 4;
-                float acc[4][8];
+            const uint32_t tacc = trow + (uint32_t)(b * P.acc_cols);
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (k < nb) tmem_ld8(trow + (uint32_t)((gb + k) * 8), acc[k]);
-                if (!fwd && l > 0 && gb != gbeg) {
+            for (int c = 0; c < TC_MAX_KCHUNKS; ++c) {
+                if (c >= nch) break;
+                const int col0 = c * 64 + sub * 16;    // first of this warp's 16 columns
+                const int left = N - col0;
+                const int ng = left <= 0 ? 0 : (left >= 16 ? 2 : 1);   // 8-column groups
+                uint4 tcur[2];
+                if (!fwd && l > 0) {
+                    if (c < PREF) {
+                        tcur[0] = tall[c < PREF ? c : 0][0];
+                        tcur[1] = tall[c < PREF ? c : 0][1];
+                    } else {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (k < nb)
-                            tpre[k] = *reinterpret_cast<const uint4*>(tsave_tile + ((size_t)(l - 1) * 128 + row) * P.H +
-                                                                       col0 + (gb + k) * 8);
+                        for (int k = 0; k < 2; ++k)
+                            if (k < ng) tcur[k] = *reinterpret_cast<const uint4*>(tsave_tile + ts_off(l - 1, row, col0 + k * 8, H));
+                    }
                 }
+                float acc[2][8];
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    if (k < ng) tmem_ld8(tacc + (uint32_t)(col0 + k * 8), acc[k]);
                 tmem_wait_ld();
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (k >= nb) break;
-                    const int gi = gb + k;
-                    const int gc = col0 + gi * 8;          // global column of this group
-                    const int lc = gi * 8;                 // column within this CTA's slice
+                for (int k = 0; k < 2; ++k) {
+                    if (k >= ng) break;
+                    const int gc = col0 + k * 8;
                     if (fwd) {
-                        const float* bias = sbias + (size_t)l * nsf + lc;
-                        float t[8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) t[i] = tanh_fast(acc[k][i] + bias[i]);
-                        uint4 tw = make_uint4(pack_bf16(t[0], t[1]), pack_bf16(t[2], t[3]), pack_bf16(t[4], t[5]),
-                                              pack_bf16(t[6], t[7]));
-                        *reinterpret_cast<uint4*>(tsave_tile + ((size_t)l * 128 + row) * P.H + gc) = tw;
-                        uint4 ow;
+                        const float* bias = sbias + (size_t)l * H + gc;
+                        const uint4 tw = make_uint4(tanh_bf16x2(acc[k][0] + bias[0], acc[k][1] + bias[1]),
+                                                    tanh_bf16x2(acc[k][2] + bias[2], acc[k][3] + bias[3]),
+                                                    tanh_bf16x2(acc[k][4] + bias[4], acc[k][5] + bias[5]),
+                                                    tanh_bf16x2(acc[k][6] + bias[6], acc[k][7] + bias[7]));
+                        *reinterpret_cast<uint4*>(tsave_tile + ts_off(l, row, gc, H)) = tw;
                         if (l == L - 1) {
-                            const float* wo = swout + lc;
-                            float d[8];
+                            float t[8], d[8];
+                            unpack_bf16x8(tw, t);
+                            const float* wo = swout + gc;
 #pragma unroll
                             for (int i = 0; i < 8; ++i) {
                                 apart = fmaf(wo[i], t[i], apart);
                                 d[i] = wo[i] * (1.0f - t[i] * t[i]);
                             }
-                            ow = make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]),
-                                            pack_bf16(d[6], d[7]));
+                            *reinterpret_cast<uint4*>(Abuf + a_off(row, gc)) = pack8(d);
                         } else {
-                            ow = tw;
+                            *reinterpret_cast<uint4*>(Abuf + a_off(row, gc)) = tw;
                         }
-                        *reinterpret_cast<uint4*>(Anext + (size_t)(gc / 8) * 2048 + row * 16) = ow;
                     } else if (l > 0) {
                         // G_{l-1} -> Delta_{l-1} = G (1 - t_{l-1}^2)
                         float t[8], d[8];
-                        unpack_bf16x8(tpre[k], t);
+                        unpack_bf16x8(tcur[k], t);
 #pragma unroll
                         for (int i = 0; i < 8; ++i) d[i] = acc[k][i] * (1.0f - t[i] * t[i]);
-                        *reinterpret_cast<uint4*>(Anext + (size_t)(gc / 8) * 2048 + row * 16) =
-                            make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]),
-                                       pack_bf16(d[6], d[7]));
+                        *reinterpret_cast<uint4*>(Abuf + a_off(row, gc)) = pack8(d);
                     } else if (valid) {
                         // G_0 = dA/du: dA/ds_j = -sin s_j g[2j] + cos s_j g[2j+1]
 #pragma unroll
@@ -413,78 +429,53 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                     }
                 }
-            }
-            if (fwd && l == L - 1) S.apart[half][row] = apart;
-            fence_before();
-            if (g == G - 1) break;
-            fence_async_smem();
-            __syncwarp();
-            const int b = CS > 1 ? ((g + 1) & 1) : 0;
-            if (lane == 0) {
-                if (CS > 1) {
-                    // this warp's 32 rows of each of its column groups -> every peer's buffer
-                    for (int gi = gbeg; gi < gend; ++gi) {
-                        const uint32_t src = smem_u32(Anext + (size_t)((col0 + gi * 8) / 8) * 2048 + quarter * 512);
-                        for (int p = 1; p < CS; ++p) {
-                            const uint32_t peer = (q + (uint32_t)p) % (uint32_t)CS;
-                            dsmem_bulk(mapa(src, peer), src, 512u, mapa(smem_u32(&S.a_full[b]), peer));
-                        }
-                    }
-                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                if (g < G - 1) {
+                    // columns past N inside the last chunk are K padding of the next GEMM: zero
+                    for (int k = ng; k < 2; ++k)
+                        *reinterpret_cast<uint4*>(Abuf + a_off(row, col0 + k * 8)) = make_uint4(0, 0, 0, 0);
+                    // chunk c of the next GEMM's A operand is complete (this warp's part)
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&S.a_chunk[c]));
                 }
-                if (e == 0 && CS > 1) mbar_arrive_tx(smem_u32(&S.a_full[b]), (uint32_t)(CS - 1) * (uint32_t)ns * 256u);
-                else mbar_arrive(smem_u32(&S.a_full[b]));
             }
+            if (fwd && l == L - 1) S.apart[sub][row] = apart;
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&S.acc_empty[b]));
         }
-        if (CS > 1 && lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     }
     fence_before();
     __syncthreads();
-    // member value A = w_out . h_L + b_out (this CTA's column slice)
+    // member value A = w_out . h_L + b_out
     if (warp >= EPI_WARP0 && warp < EPI_WARP0 + 4) {
         const int row = (warp & 3) * 32 + lane;
         const int wg = tile * 128 + row;
-        if (wg < P.W && !S.abort_flag) {
-            float a = S.apart[0][row] + S.apart[1][row];
-            if (q == 0) a += __ldg(P.bout + m);
-            P.Apart[((size_t)m * CS + q) * P.W + wg] = a;
-        }
+        if (wg < P.W && !S.abort_flag)
+            P.Apart[(size_t)m * P.W + wg] =
+                (S.apart[0][row] + S.apart[1][row]) + (S.apart[2][row] + S.apart[3][row]) + __ldg(P.bout + m);
     }
     if (warp == 1) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)P.tmem_cols)
                      : "memory");
     }
-    if (CS > 1) cluster_sync();
 }
 
 }  // namespace
 
 size_t rid_mlp_tc_smem_bytes(const TcArgs& P) {
-    const size_t abytes = 128u * (size_t)P.Kmax * 2u;
-    return (P.CS > 1 ? 2 : 1) * abytes + (size_t)P.stages * P.stage_bytes +
-           sizeof(float) * (size_t)(P.L + 1) * (P.H / P.CS);
+    return 1024 + (size_t)P.Kpmax * 256u + (size_t)P.stages * P.stage_bytes + sizeof(float) * (size_t)(P.L + 1) * P.H;
 }
 
 cudaError_t rid_launch_mlp_tc(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, cudaStream_t s) {
     const size_t smem = rid_mlp_tc_smem_bytes(P);
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (P.CS > 1) {
-        e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        attr = smem;
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(P.ntiles * P.CS, P.M, 1);
-    cfg.blockDim = dim3(NTHREADS, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = P.CS;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_mlp_tc, P, big, small);
+    k_mlp_tc<<<dim3(P.ntiles, P.M, 1), NTHREADS, smem, s>>>(P, big, small);
+    return cudaGetLastError();
 }

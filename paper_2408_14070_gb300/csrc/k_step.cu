@@ -269,7 +269,7 @@ constexpr int FF_THREADS = 224;
 // positions -> fff.  One CTA per walker.  BSMEM: bonded terms through shared
 // per-term slots (chains up to RID_BONDED_SMEM_MAX beads), else per bead.
 template <bool ENERGY, bool BSMEM>
-__global__ void __maxnreg__(40) k_ff(SysDev S, StateDev st) {
+__global__ void __maxnreg__(32) k_ff(SysDev S, StateDev st) {
     extern __shared__ float4 sm4[];
     __shared__ double red[32];
     const int w = blockIdx.x, N = S.N;

@@ -69,14 +69,14 @@ struct DevBuf {
     template <typename T> T* as() const { return static_cast<T*>(p); }
 };
 
-// One cluster-size variant of the pre-tiled BF16 weights and its tensor maps.
+// The pre-swizzled BF16 weight image and its tensor maps.
 struct TcVariant {
     bool ok = false;
-    int CS = 1, ck = 64, stages = 0, Kmax = 0, tmem_cols = 0;
+    int stages = 0, Kpmax = 0, tmem_cols = 0, nacc = 1, acc_cols = 0;
     unsigned stage_bytes = 0;
     long long member_rows = 0;
     long long grow[2 * RID_MAX_LAYERS] = {0};
-    int gN[2 * RID_MAX_LAYERS] = {0}, gK[2 * RID_MAX_LAYERS] = {0};
+    int gN[2 * RID_MAX_LAYERS] = {0}, gKp[2 * RID_MAX_LAYERS] = {0};
     DevBuf blob;
     CUtensorMap big{}, small{};
 };
@@ -91,10 +91,9 @@ struct rid_system {
     EnsDev E{};
     int precision = RID_PREC_FP32;
     DevBuf d_W, d_WT, d_b, d_wout, d_bout;
-    TcVariant tcv[3];          // cluster sizes 1, 2, 4
+    TcVariant tcv;
     int Dp = 0;
     DevBuf tsave, d_err;
-    int last_cs = 1;
     // state
     int cap = 0;
     DevBuf x, v, f, fff, s, J, u, gradA, Aval, eps, hs, eff, flags;
@@ -182,7 +181,7 @@ static int ensure_state(rid_system* sys, int W) {
         const EnsDev& E = sys->E;
         TRY(sys->gradA.ensure((size_t)E.M * nc * sizeof(float)));
         TRY(sys->Aval.ensure((size_t)E.M * W * sizeof(float)));
-        TRY(sys->Aval.ensure((size_t)E.M * 4 * W * sizeof(float)));
+        TRY(sys->Aval.ensure((size_t)E.M * W * sizeof(float)));
         if (sys->precision == RID_PREC_FP32) {
             TRY(sys->hs.ensure(rid_mlp_fp32_scratch_floats(W, E.M, E.L, E.H) * sizeof(float)));
         } else {
@@ -221,7 +220,7 @@ static void destroy_all(rid_system* sys) {
                       &sys->lsum, &sys->lsum2, &sys->lbsum, &sys->ls0, &sys->lkap, &sys->io0, &sys->io1,
                       &sys->tr_cv, &sys->tr_eps, &sys->tr_en, &sys->out_mf, &sys->out_se, &sys->out_sd};
     for (DevBuf* b : bufs) b->release();
-    for (auto& v : sys->tcv) v.blob.release();
+    sys->tcv.blob.release();
     sys->tsave.release();
     sys->d_err.release();
     for (auto& r : sys->prof_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -352,36 +351,37 @@ static uint16_t f2bf(float f) {   // round to nearest even
 }
 
 static int build_tc_variant(rid_system* sys, const std::vector<float>& W, long long wst, const long long* loff,
-                            int CS, TcVariant& V) {
+                            TcVariant& V) {
     const EnsDev& E = sys->E;
     const int M = E.M, D = E.D, L = E.L, H = E.H, Dp = sys->Dp, G = 2 * L;
     V.ok = false;
-    V.CS = CS;
-    V.ck = H > 256 ? 32 : (H % 64 == 0 ? 64 : 32);
-    V.Kmax = H > Dp ? H : Dp;
-    int nsmax = 0;
+    int nmax = 0, kpmax = 0;
     long long rows = 0;
     for (int g = 0; g < G; ++g) {
         const bool fwd = g < L;
         const int l = fwd ? g : G - 1 - g;
         V.gN[g] = fwd ? H : (l == 0 ? Dp : H);
-        V.gK[g] = fwd ? (l == 0 ? Dp : H) : H;
-        const int ns = V.gN[g] / CS;
-        if (V.gN[g] % (16 * CS) || ns > (CS == 1 ? 512 : 256) || V.gK[g] % V.ck) return RID_OK;   // unsupported
-        if (ns > nsmax) nsmax = ns;
+        V.gKp[g] = (((fwd ? (l == 0 ? Dp : H) : H) + 63) / 64) * 64;
+        if (V.gN[g] > nmax) nmax = V.gN[g];
+        if (V.gKp[g] > kpmax) kpmax = V.gKp[g];
         V.grow[g] = rows;
-        rows += (long long)V.gN[g] * V.gK[g] / 64;
+        rows += (long long)(V.gKp[g] / 64) * V.gN[g];
     }
+    if (kpmax / 64 > TC_MAX_KCHUNKS) return fail(RID_ERR_ARG, "tensor-core path: K up to %d", 64 * TC_MAX_KCHUNKS);
+    V.Kpmax = kpmax;
     V.member_rows = rows;
-    V.stage_bytes = (unsigned)nsmax * V.ck * 2u;
-    const size_t abytes = 128u * (size_t)V.Kmax * 2u * (CS > 1 ? 2 : 1);
-    const size_t budget = 220u * 1024u - sizeof(float) * (size_t)(L + 1) * (H / CS);
-    if (abytes + 2 * (size_t)V.stage_bytes > budget) return RID_OK;
-    V.stages = (int)((budget - abytes) / V.stage_bytes);
+    V.stage_bytes = (unsigned)(nmax < 256 ? nmax : 256) * 128u;
+    const size_t fixed = 1024 + (size_t)kpmax * 256u + sizeof(float) * (size_t)(L + 1) * H;
+    const size_t budget = 225u * 1024u;
+    if (fixed + 2 * (size_t)V.stage_bytes > budget)
+        return fail(RID_ERR_ARG, "tensor-core path: tile too large for shared memory");
+    V.stages = (int)((budget - fixed) / V.stage_bytes);
     if (V.stages > TC_MAX_STAGES) V.stages = TC_MAX_STAGES;
+    V.acc_cols = (nmax + 31) / 32 * 32;
+    V.nacc = 2 * V.acc_cols <= 512 ? 2 : 1;
     V.tmem_cols = 32;
-    while (V.tmem_cols < nsmax) V.tmem_cols *= 2;
-    // pre-tiled image
+    while (V.tmem_cols < V.nacc * V.acc_cols) V.tmem_cols *= 2;
+    // pre-swizzled image: per GEMM, per 64-column K-chunk, N rows of 128 bytes
     std::vector<uint16_t> img((size_t)M * rows * 64, 0);
     for (int m = 0; m < M; ++m)
         for (int g = 0; g < G; ++g) {
@@ -389,21 +389,19 @@ static int build_tc_variant(rid_system* sys, const std::vector<float>& W, long l
             const int l = fwd ? g : G - 1 - g;
             const int fin = l == 0 ? D : H;
             const float* Wl = W.data() + (size_t)m * wst + loff[l];   // [H][fin]
-            const int N = V.gN[g], K = V.gK[g], ns = N / CS, ck = V.ck;
-            for (int c = 0; c < K / ck; ++c)
-                for (int q = 0; q < CS; ++q) {
-                    const size_t base = ((size_t)m * rows + V.grow[g] + (size_t)(c * CS + q) * (ns * ck / 64)) * 64;
-                    for (int kb = 0; kb < ck / 8; ++kb)
-                        for (int rg = 0; rg < ns / 8; ++rg)
-                            for (int r = 0; r < 8; ++r)
-                                for (int kc = 0; kc < 8; ++kc) {
-                                    const int n = q * ns + rg * 8 + r, k = c * ck + kb * 8 + kc;
-                                    float val = 0.0f;
-                                    if (fwd) { if (k < fin) val = Wl[(size_t)n * fin + k]; }
-                                    else if (n < fin) val = Wl[(size_t)k * fin + n];
-                                    img[base + (((size_t)kb * (ns / 8) + rg) * 8 + r) * 8 + kc] = f2bf(val);
-                                }
-                }
+            const int N = V.gN[g];
+            for (int c = 0; c < V.gKp[g] / 64; ++c) {
+                const size_t base = ((size_t)m * rows + V.grow[g] + (size_t)c * N) * 64;
+                for (int n = 0; n < N; ++n)
+                    for (int kl = 0; kl < 64; ++kl) {
+                        const int k = c * 64 + kl;
+                        float val = 0.0f;
+                        if (fwd) { if (k < fin) val = Wl[(size_t)n * fin + k]; }      // W_l[n][k]
+                        else if (n < fin && k < H) val = Wl[(size_t)k * fin + n];     // W_l^T[n][k]
+                        const int j = (kl >> 3) ^ (n & 7);
+                        img[base + (size_t)n * 64 + j * 8 + (kl & 7)] = f2bf(val);
+                    }
+            }
         }
     TRY(V.blob.ensure(img.size() * 2));
     CK(cudaMemcpy(V.blob.p, img.data(), img.size() * 2, cudaMemcpyHostToDevice));
@@ -419,31 +417,10 @@ static int build_tc_variant(rid_system* sys, const std::vector<float>& W, long l
     CUresult r2 = enc(&V.small, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, V.blob.p, dims, strides, box_small, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) return fail(RID_ERR_CUDA, "tensor map encoding failed (%d, %d)", (int)r1, (int)r2);
+    if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS)
+        return fail(RID_ERR_CUDA, "tensor map encoding failed (%d, %d)", (int)r1, (int)r2);
     V.ok = true;
     return RID_OK;
-}
-
-// Cluster size for a launch: RID_MLP_CLUSTER (1, 2, 4) if set and available,
-// else the smallest that gives at least ~120 CTAs.
-static int pick_cluster(rid_system* sys, int W) {
-    const int ntiles = (W + 127) / 128, M = sys->E.M;
-    const char* env = std::getenv("RID_MLP_CLUSTER");
-    if (env) {
-        const int want = std::atoi(env);
-        for (int i = 0; i < 3; ++i)
-            if (sys->tcv[i].ok && sys->tcv[i].CS == want) return i;
-    }
-    // smallest cluster that gives at least ~120 CTAs (measured on GB300 with
-    // 4 x 40-256x4-1 and 1024 walkers: cluster 4 takes 51 us, cluster 1 64 us)
-    int best = -1;
-    for (int i = 0; i < 3; ++i) {
-        if (!sys->tcv[i].ok) continue;
-        best = i;
-        if (ntiles * M * sys->tcv[i].CS >= 120) return i;
-    }
-    return best;
-    return -1;
 }
 
 extern "C" int rid_set_ensemble(rid_system* sys, const rid_ensemble_desc* d) {
@@ -511,13 +488,7 @@ extern "C" int rid_set_ensemble(rid_system* sys, const rid_ensemble_desc* d) {
     E.aslices = 1;
     if (d->precision == RID_PREC_BF16) {
         sys->Dp = (D + 63) / 64 * 64;
-        const int css[3] = {1, 2, 4};
-        bool any = false;
-        for (int i = 0; i < 3; ++i) {
-            TRY(build_tc_variant(sys, W, wst, loff, css[i], sys->tcv[i]));
-            any |= sys->tcv[i].ok;
-        }
-        if (!any) return fail(RID_ERR_ARG, "no tensor-core tiling fits width=%d, n_in=%d", H, D);
+        TRY(build_tc_variant(sys, W, wst, loff, sys->tcv));
         TRY(sys->d_err.ensure(sizeof(int)));
         CK(cudaMemset(sys->d_err.p, 0, sizeof(int)));
     }
@@ -582,20 +553,19 @@ static int launch_forces(rid_system* sys, int W, int mode, bool energy, cudaStre
     TRY(timed_launch(sys, "k_ff", st, [&] { rid_launch_ff(sys->S, sd, W, energy, st); }));
     EnsDev& E = sys->E;
     if (mode == 1 && sys->precision == RID_PREC_BF16) {
-        const int vi = pick_cluster(sys, W);
-        const TcVariant& V = sys->tcv[vi];
+        const TcVariant& V = sys->tcv;
         TcArgs P{};
         P.W = W; P.C = sys->S.C; P.D = E.D; P.Dp = sys->Dp; P.L = E.L; P.H = E.H; P.M = E.M;
-        P.CS = V.CS; P.ck = V.ck; P.stages = V.stages; P.Kmax = V.Kmax; P.ntiles = (W + 127) / 128;
-        P.tmem_cols = V.tmem_cols; P.stage_bytes = V.stage_bytes;
+        P.stages = V.stages; P.Kpmax = V.Kpmax; P.ntiles = (W + 127) / 128;
+        P.tmem_cols = V.tmem_cols; P.nacc = V.nacc; P.acc_cols = V.acc_cols; P.stage_bytes = V.stage_bytes;
         P.u = sd.u; P.bias = E.b; P.wout = E.wout; P.bout = E.bout;
         P.tsave = sys->tsave.as<__nv_bfloat16>(); P.gradA = sd.gradA; P.Apart = sd.Aval; P.err = sys->d_err.as<int>();
         P.member_rows = V.member_rows;
-        for (int g = 0; g < 2 * E.L; ++g) { P.grow[g] = V.grow[g]; P.gN[g] = V.gN[g]; P.gK[g] = V.gK[g]; }
+        for (int g = 0; g < 2 * E.L; ++g) { P.grow[g] = V.grow[g]; P.gN[g] = V.gN[g]; P.gKp[g] = V.gKp[g]; }
         cudaError_t le = cudaSuccess;
         TRY(timed_launch(sys, "k_mlp_tc", st, [&] { le = rid_launch_mlp_tc(P, V.big, V.small, st); }));
         if (le != cudaSuccess) return fail(RID_ERR_CUDA, "k_mlp_tc launch: %s", cudaGetErrorString(le));
-        E.aslices = V.CS;
+        E.aslices = 1;
     } else if (mode == 1) {
         E.aslices = 1;
         TRY(timed_launch(sys, "k_mlp_fp32", st, [&] { rid_launch_mlp_fp32(E, sd, W, sys->S.C, st); }));

@@ -8,15 +8,16 @@
 #include "rid_internal.cuh"
 
 #define TC_MAX_STAGES 8
+#define TC_MAX_KCHUNKS 8   // 64-wide K-chunks of the widest GEMM (K <= 512)
 
-// Weight images: for every member, GEMM g (forward layers 0..L-1, then
-// backward layers L-1..0), K-chunk c and cluster rank q, the B-operand slice
-// rows [q N_g/CS, (q+1) N_g/CS) x columns [c ck, (c+1) ck) stored exactly as
-// the canonical no-swizzle K-major shared-memory layout: 8-row x 16-byte core
-// matrices, k-block-major ([ck/8][rows/8][8][8] BF16).  Offsets are in rows of
-// 128 bytes (the tensor map's inner box).
+// Weight image, per member: for GEMM g (forward layers 0..L-1, then backward
+// layers L-1..0) and K-chunk c (64 columns), the B operand rows [0, N_g) x
+// columns [64 c, 64 c + 64) as rows of 128 bytes in the 128-byte swizzled
+// layout (16-byte chunk j of row n at position j ^ (n mod 8)), zero padded
+// beyond K_g.  Offsets are counted in those 128-byte rows.
 struct TcArgs {
-    int W, C, D, Dp, L, H, M, CS, ck, stages, Kmax, ntiles, tmem_cols;
+    int W, C, D, Dp, L, H, M;
+    int stages, Kpmax, ntiles, tmem_cols, nacc, acc_cols;
     unsigned stage_bytes;
     const float* u;          // [W][D] MLP input (cos, sin), FP32
     const float* bias;       // [M][L][H]
@@ -24,11 +25,11 @@ struct TcArgs {
     const float* bout;       // [M]
     __nv_bfloat16* tsave;    // [M][ntiles][L][128][H] tanh(z_l), BF16
     float* gradA;            // [M][W][C]
-    float* Apart;            // [M][CS][W] member value, per column slice
+    float* Apart;            // [M][W] member value
     int* err;                // error word (bounded-wait expiry codes)
     long long member_rows;   // 128-byte rows per member image
-    long long grow[2 * RID_MAX_LAYERS];   // first row of GEMM g within a member image
-    int gN[2 * RID_MAX_LAYERS], gK[2 * RID_MAX_LAYERS];
+    long long grow[2 * RID_MAX_LAYERS];          // first row of GEMM g within a member image
+    int gN[2 * RID_MAX_LAYERS], gKp[2 * RID_MAX_LAYERS];   // N and K padded to 64
 };
 
 size_t rid_mlp_tc_smem_bytes(const TcArgs& P);

@@ -9,8 +9,6 @@ few u in the normwise sense, so after 2L = 8 GEMMs the member gradients carry
 ~1e-2; the test bound is 3e-2 normwise per walker (member gradients, mean
 force) and 5e-2 on the model deviation eps (a difference of gradients).
 """
-import os
-
 import numpy as np
 import pytest
 
@@ -29,19 +27,6 @@ def R():
     return rid
 
 
-@pytest.fixture
-def cluster():
-    old = os.environ.get("RID_MLP_CLUSTER")
-
-    def set_(v):
-        if v is None:
-            os.environ.pop("RID_MLP_CLUSTER", None)
-        else:
-            os.environ["RID_MLP_CLUSTER"] = str(v)
-    yield set_
-    set_(old)
-
-
 def normwise(a, b):
     return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30)
 
@@ -58,14 +43,14 @@ def run_eval(R, sp, ens, x, prec):
     return f, eps, abar, g
 
 
-@pytest.mark.parametrize("cs", [1, 2, 4])
 @pytest.mark.parametrize("n,C,W,M,L,H,seed", [
     (200, 20, 300, 4, 4, 256, 1),      # the benchmark shape, ragged walker count
     (22, 2, 16, 4, 3, 64, 2),          # tiny chain: D = 4 padded to 64
-    (60, 9, 130, 3, 2, 96, 3),         # width not a multiple of 64 (K-chunks of 32)
+    (60, 9, 130, 3, 2, 96, 3),         # width not a multiple of 64 (partial K-chunks)
+    (80, 16, 200, 4, 3, 160, 7),       # width 160: three chunks, the last half full
+    (150, 64, 129, 2, 2, 64, 8),       # 128 inputs (two input chunks) wider than the hidden layers
 ])
-def test_bf16_member_gradients_eps_and_values(R, orc, cluster, cs, n, C, W, M, L, H, seed):
-    cluster(cs)
+def test_bf16_member_gradients_eps_and_values(R, orc, n, C, W, M, L, H, seed):
     sp = I.make_system(n, C, seed)
     x = I.make_chains(W, sp, seed)
     ens = I.make_ensemble(M, 2 * C, L, H, seed, trust_lo=1e9, trust_hi=2e9)
@@ -84,9 +69,9 @@ def test_bf16_member_gradients_eps_and_values(R, orc, cluster, cs, n, C, W, M, L
         assert normwise(fb, rb) < GRAD_TOL, w
 
 
-def test_bf16_width512_eight_members(R, orc, cluster):
-    """The precision-sweep shape (64 -> 512 x 4 -> 1, 8 members) on a sample."""
-    cluster(None)
+def test_bf16_width512_eight_members(R, orc):
+    """The precision-sweep shape (64 -> 512 x 4 -> 1, 8 members) on a sample:
+    one accumulator (512 TMEM columns) and two 256-row weight halves per chunk."""
     sp = I.make_system(100, 32, 4)
     W = 150
     x = I.make_chains(W, sp, 4)
@@ -99,23 +84,19 @@ def test_bf16_width512_eight_members(R, orc, cluster):
         assert abs(eps[w] - e["eps"]) <= EPS_TOL * abs(e["eps"]) + 1e-4
 
 
-def test_bf16_cluster_sizes_agree_and_runs_are_deterministic(R, cluster):
+def test_bf16_runs_are_deterministic_and_close_to_fp32(R):
     sp = I.make_system(200, 20, 5)
     x = I.make_chains(256, sp, 5)
     ens = I.make_ensemble(4, 40, 4, 256, 5)
-    outs = {}
-    for cs in (1, 2, 4):
-        cluster(cs)
-        outs[cs] = run_eval(R, sp, ens, x, R.RID_PREC_BF16)
-    again = run_eval(R, sp, ens, x, R.RID_PREC_BF16)
-    assert all(np.array_equal(a, b) for a, b in zip(outs[4], again))
-    for cs in (1, 2):
-        # same products in the same K order: gradients agree to rounding
-        assert normwise(outs[cs][3], outs[4][3]) < 1e-5
+    a = run_eval(R, sp, ens, x, R.RID_PREC_BF16)
+    b = run_eval(R, sp, ens, x, R.RID_PREC_BF16)
+    assert all(np.array_equal(u, v) for u, v in zip(a, b))
+    c = run_eval(R, sp, ens, x, R.RID_PREC_FP32)
+    for w in range(0, 256, 17):
+        assert normwise(a[3][:, w], c[3][:, w]) < GRAD_TOL
 
 
-def test_bf16_switching_and_trajectory(R, orc, cluster):
-    cluster(None)
+def test_bf16_switching_and_trajectory(R, orc):
     sp = I.make_system(200, 20, 6, output_freq=1)
     W = 8
     x0 = I.make_chains(W, sp, 6)
