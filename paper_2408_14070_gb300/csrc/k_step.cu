@@ -323,10 +323,14 @@ __global__ void __maxnreg__(32) k_ff(SysDev S, StateDev st) {
 //   INT: 0 nothing, 1 CVs at the current positions, 2 B-A-O-A then CVs
 // With FIN and INT = 0 the total force is stored (end of a call); with
 // FIN = 0 the opening kick uses the stored force.
+constexpr int HEAD_THREADS = 128;  // four warps per walker, seven CTAs per SM: the grid is resident at once
+constexpr int HEAD_BEADS = 2;      // beads per thread per batch, loaded before they are needed
+
 template <int MODE, bool FIN, bool KICK, int INT, bool ENERGY>
-__global__ void __maxnreg__(40) k_head(SysDev S, StateDev st, EnsDev E, LabelDev lab, long long t_fin,
-                                              int slot, float* __restrict__ cv_out, float* __restrict__ eps_out,
-                                              double* __restrict__ energy_out, long long T, uint32_t step) {
+__global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st, EnsDev E, LabelDev lab, long long t_fin,
+                                                        int slot, float* __restrict__ cv_out,
+                                                        float* __restrict__ eps_out, double* __restrict__ energy_out,
+                                                        long long T, uint32_t step) {
     extern __shared__ float4 xs[];
     __shared__ float Fs[RID_MAX_CV];
     __shared__ float s_eps, s_abar;
@@ -335,6 +339,24 @@ __global__ void __maxnreg__(40) k_head(SysDev S, StateDev st, EnsDev E, LabelDev
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long base = (long long)w * N;
     const float kick = S.half_dt * S.inv_mass;
+    constexpr int BATCH = HEAD_THREADS * HEAD_BEADS;
+    // bead data of the first batch (and its Langevin noise) is loaded / drawn
+    // before the ensemble reduction, so the two overlap
+    float3 px[HEAD_BEADS], pv[HEAD_BEADS], pf[HEAD_BEADS], pz[HEAD_BEADS];
+    auto load_batch = [&](int b0) {
+#pragma unroll
+        for (int k = 0; k < HEAD_BEADS; ++k) {
+            const int i = b0 + k * HEAD_THREADS + threadIdx.x;
+            if (i < N) {
+                px[k] = f3(st.x[base + i]);
+                pv[k] = f3(st.v[base + i]);
+                if (FIN) pf[k] = f3(st.fff[base + i]);
+                else if (INT == 2) pf[k] = f3(st.f[base + i]);
+                if (INT == 2 && S.c2 != 0.0f) pz[k] = rid_normals3(rid_philox(make_uint4(i, w, step, 0u), S.key0, S.key1));
+            }
+        }
+    };
+    load_batch(0);
     if (FIN) {
         if (MODE == 1) {
             if (warp == 0) {
@@ -345,17 +367,11 @@ __global__ void __maxnreg__(40) k_head(SysDev S, StateDev st, EnsDev E, LabelDev
                 for (int k = lane; k < na; k += 32) av += st.Aval[(long long)k * W + w];
                 float d2 = 0.0f;
                 for (int j = lane; j < C; j += 32) {
-                    float g[RID_MAX_MODELS];
-#pragma unroll
-                    for (int m = 0; m < RID_MAX_MODELS; ++m)
-                        g[m] = m < E.M ? st.gradA[((long long)m * W + w) * C + j] : 0.0f;
                     float fb = 0.0f;
-#pragma unroll
-                    for (int m = 0; m < RID_MAX_MODELS; ++m) fb += g[m];
+                    for (int m = 0; m < E.M; ++m) fb += st.gradA[((long long)m * W + w) * C + j];
                     fb *= invM;
-#pragma unroll
-                    for (int m = 0; m < RID_MAX_MODELS; ++m) {
-                        const float d = m < E.M ? g[m] - fb : 0.0f;
+                    for (int m = 0; m < E.M; ++m) {
+                        const float d = st.gradA[((long long)m * W + w) * C + j] - fb;
                         d2 = fmaf(d, d, d2);
                     }
                     Fs[j] = fb;
@@ -408,52 +424,56 @@ __global__ void __maxnreg__(40) k_head(SysDev S, StateDev st, EnsDev E, LabelDev
     }
     double ke = 0.0;
     int bad = 0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        float4 x = st.x[base + i];
-        float4 v = st.v[base + i];
-        float4 f;
-        if (FIN) {
-            f = st.fff[base + i];
-            for (int e = S.acv_off[i]; e < S.acv_off[i + 1]; ++e) {
-                const int2 ja = S.acv[e];
-                const float4 g = st.J[((long long)w * C + ja.x) * 4 + ja.y];
-                const float fs = Fs[ja.x];
-                f.x = fmaf(fs, g.x, f.x);
-                f.y = fmaf(fs, g.y, f.y);
-                f.z = fmaf(fs, g.z, f.z);
+    for (int b0 = 0; b0 < N; b0 += BATCH) {
+        if (b0 > 0) load_batch(b0);
+#pragma unroll
+        for (int k = 0; k < HEAD_BEADS; ++k) {
+            const int i = b0 + k * HEAD_THREADS + threadIdx.x;
+            if (i >= N) break;
+            float4 x = make_float4(px[k].x, px[k].y, px[k].z, 0.f);
+            float4 v = make_float4(pv[k].x, pv[k].y, pv[k].z, 0.f);
+            float4 f = make_float4(pf[k].x, pf[k].y, pf[k].z, 0.f);
+            if (FIN) {
+                for (int e = S.acv_off[i]; e < S.acv_off[i + 1]; ++e) {
+                    const int2 ja = S.acv[e];
+                    const float4 g = st.J[((long long)w * C + ja.x) * 4 + ja.y];
+                    const float fs = Fs[ja.x];
+                    f.x = fmaf(fs, g.x, f.x);
+                    f.y = fmaf(fs, g.y, f.y);
+                    f.z = fmaf(fs, g.z, f.z);
+                }
+                bad |= !(isfinite(f.x) && isfinite(f.y) && isfinite(f.z));
+                if (KICK) {
+                    v.x = fmaf(kick, f.x, v.x);
+                    v.y = fmaf(kick, f.y, v.y);
+                    v.z = fmaf(kick, f.z, v.z);
+                    bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z));
+                    if (ENERGY)
+                        ke += 0.5 / (double)S.inv_mass * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+                }
+                if (INT != 2) st.f[base + i] = f;
             }
-            bad |= !(isfinite(f.x) && isfinite(f.y) && isfinite(f.z));
-            if (KICK) {
-                v.x = fmaf(kick, f.x, v.x);
+            if (INT == 2) {
+                v.x = fmaf(kick, f.x, v.x);             // B
                 v.y = fmaf(kick, f.y, v.y);
                 v.z = fmaf(kick, f.z, v.z);
-                bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z));
-                if (ENERGY) ke += 0.5 / (double)S.inv_mass * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+                x.x = fmaf(S.half_dt, v.x, x.x);        // A
+                x.y = fmaf(S.half_dt, v.y, x.y);
+                x.z = fmaf(S.half_dt, v.z, x.z);
+                if (S.c2 != 0.0f) {                     // O
+                    const float3 z = pz[k];
+                    v.x = fmaf(S.c1, v.x, S.c2 * z.x);
+                    v.y = fmaf(S.c1, v.y, S.c2 * z.y);
+                    v.z = fmaf(S.c1, v.z, S.c2 * z.z);
+                }
+                x.x = fmaf(S.half_dt, v.x, x.x);        // A
+                x.y = fmaf(S.half_dt, v.y, x.y);
+                x.z = fmaf(S.half_dt, v.z, x.z);
+                st.x[base + i] = x;
             }
-            if (INT != 2) st.f[base + i] = f;
-        } else if (INT == 2) {
-            f = st.f[base + i];
+            if (INT == 2 || (FIN && KICK)) st.v[base + i] = v;
+            if (INT != 0) xs[i] = x;
         }
-        if (INT == 2) {
-            v.x = fmaf(kick, f.x, v.x);             // B
-            v.y = fmaf(kick, f.y, v.y);
-            v.z = fmaf(kick, f.z, v.z);
-            x.x = fmaf(S.half_dt, v.x, x.x);        // A
-            x.y = fmaf(S.half_dt, v.y, x.y);
-            x.z = fmaf(S.half_dt, v.z, x.z);
-            if (S.c2 != 0.0f) {                     // O
-                const float3 z = rid_normals3(rid_philox(make_uint4(i, w, step, 0u), S.key0, S.key1));
-                v.x = fmaf(S.c1, v.x, S.c2 * z.x);
-                v.y = fmaf(S.c1, v.y, S.c2 * z.y);
-                v.z = fmaf(S.c1, v.z, S.c2 * z.z);
-            }
-            x.x = fmaf(S.half_dt, v.x, x.x);        // A
-            x.y = fmaf(S.half_dt, v.y, x.y);
-            x.z = fmaf(S.half_dt, v.z, x.z);
-            st.x[base + i] = x;
-        }
-        if (INT == 2 || (FIN && KICK)) st.v[base + i] = v;
-        if (INT != 0) xs[i] = x;
     }
     if (FIN) {
         if (bad) st.flags[w] = 1;
@@ -601,7 +621,7 @@ void rid_launch_ff(const SysDev& S, StateDev st, int W, bool energy, cudaStream_
 
 template <int MODE, bool FIN, bool KICK, int INT>
 static void head_e(const HeadArgs& a, cudaStream_t s) {
-    const int th = chain_threads(a.S.N);
+    const int th = HEAD_THREADS;
     const size_t sm = sizeof(float4) * (size_t)a.S.N;
     if (a.energy)
         k_head<MODE, FIN, KICK, INT, true><<<a.W, th, sm, s>>>(a.S, a.st, a.E, a.lab, a.t_fin, a.slot, a.cv_out,

@@ -106,6 +106,9 @@ struct rid_system {
     uint64_t step_next = 0;
     bool loaded = false;
     bool pending = false;      // the last step's closing half (finish + kick) is still to run
+    // the force field runs on a side stream, concurrently with the ensemble kernel
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // kernel timing
     bool prof_on = false;
     std::vector<std::string> prof_names;
@@ -225,6 +228,11 @@ static void destroy_all(rid_system* sys) {
     sys->d_err.release();
     for (auto& r : sys->prof_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     sys->prof_recs.clear();
+    if (sys->ev_fork) cudaEventDestroy(sys->ev_fork);
+    if (sys->ev_join) cudaEventDestroy(sys->ev_join);
+    if (sys->side) cudaStreamDestroy(sys->side);
+    sys->ev_fork = sys->ev_join = nullptr;
+    sys->side = nullptr;
 }
 
 extern "C" int rid_create_system(const rid_system_desc* d, rid_system** out) {
@@ -545,12 +553,46 @@ static int fetch_flags(rid_system* sys, int W, cudaStream_t st, bool* any) {
     return RID_OK;
 }
 
+static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_t st);
+
+// Side stream (lowest priority) and fork / join events, created on first use.
+static int ensure_side(rid_system* sys) {
+    if (sys->side) return RID_OK;
+    int lo = 0, hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CK(cudaStreamCreateWithPriority(&sys->side, cudaStreamNonBlocking, lo));
+    CK(cudaEventCreateWithFlags(&sys->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&sys->ev_join, cudaEventDisableTiming));
+    return RID_OK;
+}
+
 // Force-field and ensemble kernels at the current positions (the CVs and the
-// MLP input have been written by the preceding k_head).
+// MLP input have been written by the preceding k_head).  Both depend only on
+// the positions: the ensemble kernel (a few CTAs that each need most of an
+// SM's shared memory) is launched first on the caller's stream so that it is
+// dispatched as soon as k_head ends, and the force field runs concurrently on
+// a side stream over the remaining SMs; the caller's stream then waits for it.
 static int launch_forces(rid_system* sys, int W, int mode, bool energy, cudaStream_t st) {
     StateDev sd = state_view(sys);
     sd.W = W;
-    TRY(timed_launch(sys, "k_ff", st, [&] { rid_launch_ff(sys->S, sd, W, energy, st); }));
+    if (mode != 1) {
+        TRY(timed_launch(sys, "k_ff", st, [&] { rid_launch_ff(sys->S, sd, W, energy, st); }));
+        CK(cudaGetLastError());
+        return RID_OK;
+    }
+    TRY(ensure_side(sys));
+    CK(cudaEventRecord(sys->ev_fork, st));
+    CK(cudaStreamWaitEvent(sys->side, sys->ev_fork, 0));
+    TRY(launch_mlp(sys, W, mode, sd, st));
+    cudaStream_t fs = sys->side;
+    TRY(timed_launch(sys, "k_ff", fs, [&] { rid_launch_ff(sys->S, sd, W, energy, fs); }));
+    CK(cudaEventRecord(sys->ev_join, fs));
+    CK(cudaStreamWaitEvent(st, sys->ev_join, 0));
+    CK(cudaGetLastError());
+    return RID_OK;
+}
+
+static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_t st) {
     EnsDev& E = sys->E;
     if (mode == 1 && sys->precision == RID_PREC_BF16) {
         const TcVariant& V = sys->tcv;
@@ -570,7 +612,6 @@ static int launch_forces(rid_system* sys, int W, int mode, bool energy, cudaStre
         E.aslices = 1;
         TRY(timed_launch(sys, "k_mlp_fp32", st, [&] { rid_launch_mlp_fp32(E, sd, W, sys->S.C, st); }));
     }
-    CK(cudaGetLastError());
     return RID_OK;
 }
 
