@@ -238,6 +238,38 @@ RID_API int rid_profile_read(rid_system* sys, int32_t max_kernels, char* names_o
                              int64_t* launches, int32_t* n_kernels);
 RID_API int64_t rid_launch_count(rid_system* sys);
 
+/*
+ * Ensemble member gradients with no device allocation.  The paper has no
+ * counterpart: this is a library facility for callers that cannot allocate
+ * device memory (a framework that owns all device memory through its own pool,
+ * code between the start and end of a stream capture that must not allocate,
+ * an embedding that forbids allocation after start-up).
+ *
+ * For P points s [P][C] (device, float32, radians) and the packed ensemble
+ * `weights` [M][Pw] (device, float32, the layout of rid_ensemble_desc.weights,
+ * D = 2C inputs (cos s_j, sin s_j)) it writes
+ *   grad_out  [M][P][C] float32 (device)        dA_i/ds at every point
+ *   value_out [M][P]    float32 (device) | NULL A_i at every point
+ * with the arithmetic of the RID_PREC_FP32 ensemble kernel.  All arrays belong
+ * to the caller; the call enqueues one kernel on `stream` and returns.
+ *
+ * Scratch: the hidden activations kept for the reverse pass live in one
+ * static 8 MiB device array per device, so M * ceil(P/32) * 32 * L * H must
+ * not exceed 2^21 floats (e.g. P = 1024, M = 4, L = 4, H = 128); larger
+ * requests return RID_ERR_ARG without launching.  The array keeps the last
+ * call's contents; nothing in it needs to start at zero (every entry read is
+ * written earlier by the same kernel).  Calls that overlap in time on one
+ * device (two streams, or two threads) share the array and race: serialise
+ * them.  The first call on a device (with that device current) looks up the
+ * array's address with cudaGetSymbolAddress and sets the kernel's shared
+ * memory limit; make that first call before any stream capture.
+ * Errors: RID_ERR_ARG (NULL array, sizes outside the limits of
+ * rid_ensemble_desc, scratch too small), RID_ERR_CUDA.
+ */
+RID_API int rid_ensemble_grad_noalloc(int32_t n_points, int32_t n_cv, const float* s, int32_t n_models,
+                                      int32_t n_layers, int32_t width, int32_t resnet, const float* weights,
+                                      float* grad_out, float* value_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -185,3 +185,5 @@ void rid_launch_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k
                        float* normals, cudaStream_t s);
 void rid_launch_mlp_fp32(const EnsDev& E, StateDev st, int W, int C, cudaStream_t s);
 size_t rid_mlp_fp32_scratch_floats(int W, int M, int L, int H);
+// Set the calling thread's rid_last_error message; returns code.
+int rid_fail(int code, const char* fmt, ...);

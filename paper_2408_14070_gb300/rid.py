@@ -25,7 +25,7 @@ RID_BIAS_NONE, RID_BIAS_ENSEMBLE, RID_BIAS_RESTRAINT = 0, 1, 2
 EXPORTS = ("rid_version", "rid_status_string", "rid_last_error", "rid_create_system", "rid_destroy_system",
            "rid_set_ensemble", "rid_explore", "rid_label", "rid_eval_forces", "rid_pair_mask", "rid_philox",
            "rid_walkers_load", "rid_walkers_advance", "rid_walkers_read", "rid_profile_enable",
-           "rid_profile_read", "rid_launch_count")
+           "rid_profile_read", "rid_launch_count", "rid_ensemble_grad_noalloc")
 
 
 class RidError(RuntimeError):
@@ -79,6 +79,7 @@ def lib() -> C.CDLL:
     L.rid_profile_enable.argtypes = [vp, i32]
     L.rid_profile_read.argtypes = [vp, i32, C.c_char_p, C.POINTER(C.c_double), C.POINTER(i64), C.POINTER(i32)]
     L.rid_launch_count.argtypes = [vp]
+    L.rid_ensemble_grad_noalloc.argtypes = [i32, i32, vp, i32, i32, i32, i32, vp, vp, vp, vp]
     L.rid_launch_count.restype = i64
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype or C.c_int
@@ -282,6 +283,23 @@ def philox(counters, seed, words_out=None, normals_out=None, stream=None):
     pw = a.ptr(words_out, np.uint32, (n, 4), True)
     pn = a.ptr(normals_out, np.float32, (n, 3), True)
     _check(lib().rid_philox(C.c_int64(n), pc, C.c_uint64(int(seed)), pw, pn, a.mem, _stream_ptr(stream)))
+
+
+def ensemble_grad_noalloc(s, weights, n_models, n_layers, width, grad_out, value_out=None, resnet=False,
+                          stream=None):
+    """Member gradients dA_i/ds [M][P][C] at device points s [P][C] with the
+    packed device weights [M][Pw], using only the library's static scratch."""
+    P, Cn = int(s.shape[0]), int(s.shape[1])
+    M = int(n_models)
+    a = _Args()
+    ps = a.ptr(s, np.float32, (P, Cn))
+    pw = a.ptr(weights, np.float32)
+    pg = a.ptr(grad_out, np.float32, (M, P, Cn), True)
+    pv = a.ptr(value_out, np.float32, (M, P), True)
+    if a.mem != RID_MEM_DEVICE:
+        raise ValueError("ensemble_grad_noalloc takes device tensors only")
+    _check(lib().rid_ensemble_grad_noalloc(P, Cn, ps, M, int(n_layers), int(width), int(bool(resnet)), pw, pg, pv,
+                                           _stream_ptr(stream)))
 
 
 def version() -> int:
