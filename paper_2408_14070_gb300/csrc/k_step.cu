@@ -250,56 +250,126 @@ __device__ __forceinline__ void lj_pair(const SysDev& S, float3 xi, float4 xj, i
     if (ENERGY) el += inc ? (S.lj_eps4 * sr6 * (sr6 - 1.0f) - S.urc) : 0.0f;
 }
 
+// Pair culling by bounding boxes.  Beads are grouped in clusters of 8
+// consecutive beads; a warp (32 consecutive i beads) visits only the clusters
+// whose box gap to the warp's own box is inside the cutoff.  The gap is formed
+// with the same FP32 subtractions and the same fused r^2 as the pair test, and
+// rounding is monotonic, so every pair of a skipped cluster has r^2 >= gap^2
+// >= rc^2: it is one the pair test would exclude, and skipping it changes no
+// result (an excluded pair adds exactly +0).
+constexpr int LJ_CLUSTER = 8;
+constexpr int LJ_MAX_MASK_WORDS = (RID_MAX_BEADS / LJ_CLUSTER + 31) / 32;
+
+template <bool EXCL, bool SIG1, bool ENERGY>
+__device__ __forceinline__ void lj_cluster(const SysDev& S, const float4* xj, float3 xi, int i, int j0, float& fx,
+                                           float& fy, float& fz, float& el) {
+#pragma unroll
+    for (int k = 0; k < LJ_CLUSTER; ++k) lj_pair<EXCL, SIG1, ENERGY>(S, xi, xj[k], i, j0 + k, fx, fy, fz, el);
+}
+
+// Walk the kept clusters of one warp in increasing order; clusters that meet
+// the band [b0, b1] around the warp's beads test the |i - j| > 2 exclusion.
 template <bool SIG1, bool ENERGY>
-__device__ __forceinline__ void lj_row(const SysDev& S, const float4* xs, float3 xi, int i, int b0, int b1,
-                                       float& fx, float& fy, float& fz, float& el) {
-    const int N = S.N;
-#pragma unroll 8
-    for (int j = 0; j < b0; ++j) lj_pair<false, SIG1, ENERGY>(S, xi, xs[j], i, j, fx, fy, fz, el);
-    for (int j = b0; j <= b1; ++j) lj_pair<true, SIG1, ENERGY>(S, xi, xs[j], i, j, fx, fy, fz, el);
-#pragma unroll 8
-    for (int j = b1 + 1; j < N; ++j) lj_pair<false, SIG1, ENERGY>(S, xi, xs[j], i, j, fx, fy, fz, el);
+__device__ __forceinline__ void lj_row_culled(const SysDev& S, const float4* xs, const unsigned* keep, int nwords,
+                                              float3 xi, int i, int cb0, int cb1, float& fx, float& fy, float& fz,
+                                              float& el) {
+    for (int q = 0; q < nwords; ++q) {
+        unsigned m = keep[q];
+        while (m) {
+            const int c = 32 * q + __ffs(m) - 1;
+            m &= m - 1;
+            const int j0 = LJ_CLUSTER * c;
+            if (c >= cb0 && c <= cb1) lj_cluster<true, SIG1, ENERGY>(S, xs + j0, xi, i, j0, fx, fy, fz, el);
+            else lj_cluster<false, SIG1, ENERGY>(S, xs + j0, xi, i, j0, fx, fy, fz, el);
+        }
+    }
 }
 
 // At most 224 threads (7 warps) and 40 registers per thread, so that seven
 // CTAs (one walker each) fit on an SM.
 constexpr int FF_THREADS = 224;
 
-// Force-field forces (bonded + all-pairs LJ) of every bead at the current
-// positions -> fff.  One CTA per walker.  BSMEM: bonded terms through shared
-// per-term slots (chains up to RID_BONDED_SMEM_MAX beads), else per bead.
+// Force-field forces (bonded + all-pairs LJ, culled by cluster boxes) of
+// every bead at the current positions -> fff.  One CTA per walker.  BSMEM:
+// bonded terms through shared per-term slots (chains up to
+// RID_BONDED_SMEM_MAX beads), else per bead.
 template <bool ENERGY, bool BSMEM>
 __global__ void __maxnreg__(32) k_ff(SysDev S, StateDev st) {
     extern __shared__ float4 sm4[];
     __shared__ double red[32];
+    __shared__ unsigned keep_s[FF_THREADS / 32][LJ_MAX_MASK_WORDS];
     const int w = blockIdx.x, N = S.N;
-    const int lane = threadIdx.x & 31;
-    float4* xs = sm4;                                         // [N] float4
-    float3* fB = reinterpret_cast<float3*>(xs + N);           // [N]  float3 (BSMEM only)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nclus = (N + LJ_CLUSTER - 1) / LJ_CLUSTER, N8 = nclus * LJ_CLUSTER;
+    const int nwords = (nclus + 31) / 32;
+    float4* xs = sm4;                                         // [N8] float4, far-away padding beyond N
+    float4* cbox = xs + N8;                                   // [nclus] x (lo, hi)
+    float3* fB = reinterpret_cast<float3*>(cbox + 2 * nclus); // [N]  float3 (BSMEM only)
     float3* fA = fB + N;                                      // [3N]
     float3* fD = fA + 3 * N;                                  // [4N]  -> see rid_ff_smem_bytes
     const long long base = (long long)w * N;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) xs[i] = st.x[base + i];
+    for (int i = threadIdx.x; i < N8; i += blockDim.x)
+        xs[i] = i < N ? st.x[base + i] : make_float4(1.0e30f, 1.0e30f, 1.0e30f, 0.0f);
     __syncthreads();
+    for (int c = threadIdx.x; c < nclus; c += blockDim.x) {
+        const int j1 = min(LJ_CLUSTER * (c + 1), N);
+        float4 lo = xs[LJ_CLUSTER * c], hi = lo;
+        for (int j = LJ_CLUSTER * c + 1; j < j1; ++j) {
+            const float4 p = xs[j];
+            lo.x = fminf(lo.x, p.x); lo.y = fminf(lo.y, p.y); lo.z = fminf(lo.z, p.z);
+            hi.x = fmaxf(hi.x, p.x); hi.y = fmaxf(hi.y, p.y); hi.z = fmaxf(hi.z, p.z);
+        }
+        cbox[2 * c] = lo;
+        cbox[2 * c + 1] = hi;
+    }
     if (BSMEM) {
         for (int t = threadIdx.x; t < N; t += blockDim.x) bonded_terms_to_smem(S, xs, t, fB, fA, fD);
-        __syncthreads();
     }
+    __syncthreads();
     const bool sig1 = S.sig2 == 1.0f;
     double e = 0.0;
     const int iters = (N + blockDim.x - 1) / blockDim.x;
     for (int it = 0; it < iters; ++it) {
         const int i = it * blockDim.x + threadIdx.x;
+        const int wlo = i - lane, whi = wlo + 31;
+        if (wlo >= N) break;                                  // warp-uniform: no bead of this warp
         const bool act = i < N;
         const float3 xi = f3(xs[act ? i : N - 1]);
-        // j ranges: far (no exclusion possible for any lane of this warp) and
-        // the band [wlo - 2, whi + 2] around the warp's own beads
-        const int wlo = i - lane, whi = wlo + 31;
+        // the warp's box (lanes past N repeat bead N - 1, which is in the warp)
+        float3 ilo = xi, ihi = xi;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ilo.x = fminf(ilo.x, __shfl_xor_sync(0xffffffffu, ilo.x, o));
+            ilo.y = fminf(ilo.y, __shfl_xor_sync(0xffffffffu, ilo.y, o));
+            ilo.z = fminf(ilo.z, __shfl_xor_sync(0xffffffffu, ilo.z, o));
+            ihi.x = fmaxf(ihi.x, __shfl_xor_sync(0xffffffffu, ihi.x, o));
+            ihi.y = fmaxf(ihi.y, __shfl_xor_sync(0xffffffffu, ihi.y, o));
+            ihi.z = fmaxf(ihi.z, __shfl_xor_sync(0xffffffffu, ihi.z, o));
+        }
+        for (int q = 0; q < nwords; ++q) {
+            const int c = 32 * q + lane;
+            bool kp = false;
+            if (c < nclus) {
+                const float4 lo = cbox[2 * c], hi = cbox[2 * c + 1];
+                const float gx = fmaxf(0.0f, fmaxf(lo.x - ihi.x, ilo.x - hi.x));
+                const float gy = fmaxf(0.0f, fmaxf(lo.y - ihi.y, ilo.y - hi.y));
+                const float gz = fmaxf(0.0f, fmaxf(lo.z - ihi.z, ilo.z - hi.z));
+                kp = !(pair_r2(make_float3(gx, gy, gz)) >= S.rc2);
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, kp);
+            if (lane == 0) keep_s[warp][q] = b;
+        }
+        __syncwarp();
         const int b0 = wlo - 2 > 0 ? wlo - 2 : 0;
         const int b1 = whi + 2 < N - 1 ? whi + 2 : N - 1;
         float fx = 0.f, fy = 0.f, fz = 0.f, el = 0.f;
-        if (sig1) lj_row<true, ENERGY>(S, xs, xi, i, b0, b1, fx, fy, fz, el);
-        else lj_row<false, ENERGY>(S, xs, xi, i, b0, b1, fx, fy, fz, el);
+        if (sig1)
+            lj_row_culled<true, ENERGY>(S, xs, keep_s[warp], nwords, xi, i, b0 / LJ_CLUSTER, b1 / LJ_CLUSTER, fx, fy,
+                                        fz, el);
+        else
+            lj_row_culled<false, ENERGY>(S, xs, keep_s[warp], nwords, xi, i, b0 / LJ_CLUSTER, b1 / LJ_CLUSTER, fx,
+                                         fy, fz, el);
+        __syncwarp();                                         // keep_s is rewritten by the next iteration
         if (act) {
             const float3 fb = BSMEM ? bonded_gather(S, i, fB, fA, fD) : bonded_force_on(S, xs, i);
             const float s = -S.lj_eps24;
@@ -591,13 +661,21 @@ void rid_launch_mb(const SysDev& S, StateDev st, int W, uint32_t step0, cudaStre
     if (n > 0) k_mb<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S, st, W, step0);
 }
 void rid_launch_pair_mask(const SysDev& S, StateDev st, int W, uint32_t* mask, cudaStream_t s) {
+    static bool attr = false;   // positions of up to RID_MAX_BEADS beads exceed the default 48 KB
+    if (!attr) {
+        cudaFuncSetAttribute(k_pair_mask, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
     k_pair_mask<<<W, chain_threads(S.N), sizeof(float4) * (size_t)S.N, s>>>(S, st, mask);
 }
 
-// Shared memory of k_ff: positions [N] float4 and, with per-term bonded
+// Shared memory of k_ff: positions [N8] float4 (N8 = N rounded up to the
+// 8-bead cluster), cluster boxes [N8 / 8][2] float4 and, with per-term bonded
 // slots, bond [N] + angle [3N] + dihedral [4N] forces as float3.
 int rid_ff_smem_bytes(int N) {
-    return (int)(sizeof(float4) * (size_t)N + (N <= RID_BONDED_SMEM_MAX ? sizeof(float3) * 8 * (size_t)N : 0));
+    const size_t nclus = (size_t)(N + LJ_CLUSTER - 1) / LJ_CLUSTER;
+    return (int)(sizeof(float4) * (nclus * LJ_CLUSTER + 2 * nclus) +
+                 (N <= RID_BONDED_SMEM_MAX ? sizeof(float3) * 8 * (size_t)N : 0));
 }
 
 void rid_launch_ff(const SysDev& S, StateDev st, int W, bool energy, cudaStream_t s) {
@@ -608,6 +686,8 @@ void rid_launch_ff(const SysDev& S, StateDev st, int W, bool energy, cudaStream_
     if (!attr) {
         cudaFuncSetAttribute(k_ff<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(k_ff<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_ff<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_ff<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
     if (bsm) {
@@ -623,6 +703,14 @@ template <int MODE, bool FIN, bool KICK, int INT>
 static void head_e(const HeadArgs& a, cudaStream_t s) {
     const int th = HEAD_THREADS;
     const size_t sm = sizeof(float4) * (size_t)a.S.N;
+    static bool attr = false;   // positions of up to RID_MAX_BEADS beads exceed the default 48 KB
+    if (!attr) {
+        cudaFuncSetAttribute(k_head<MODE, FIN, KICK, INT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             sizeof(float4) * RID_MAX_BEADS);
+        cudaFuncSetAttribute(k_head<MODE, FIN, KICK, INT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             sizeof(float4) * RID_MAX_BEADS);
+        attr = true;
+    }
     if (a.energy)
         k_head<MODE, FIN, KICK, INT, true><<<a.W, th, sm, s>>>(a.S, a.st, a.E, a.lab, a.t_fin, a.slot, a.cv_out,
                                                                  a.eps_out, a.energy_out, a.T, a.step);

@@ -111,10 +111,18 @@ def test_pair_inclusion_bit_exact(R, orc, n, W, seed):
 
 
 # ------------------------------------------------------------------ forces
-@pytest.mark.parametrize("n,C,W,seed", [(22, 2, 16, 1), (200, 20, 40, 2), (61, 9, 33, 4), (4, 1, 3, 5)])
-def test_force_field_and_cvs(R, orc, n, C, W, seed):
+@pytest.mark.parametrize("n,C,W,seed,squeeze", [
+    (22, 2, 16, 1, False), (200, 20, 40, 2, False), (61, 9, 33, 4, False), (4, 1, 3, 5, False),
+    (200, 20, 12, 6, True),        # compressed walkers: many pairs and cluster boxes near the cutoff
+    (257, 9, 5, 7, False),         # two passes of the bead loop, last warp holds one bead
+    (1500, 16, 3, 8, False),       # beyond the shared-memory bonded slots, warps past the last bead
+    (4096, 64, 2, 9, False),       # largest chain
+])
+def test_force_field_and_cvs(R, orc, n, C, W, seed, squeeze):
     sp = I.make_system(n, C, seed)
     x = I.make_chains(W, sp, seed)
+    if squeeze:
+        x[1::2] *= np.float32(0.83)
     f = np.zeros((W, n, 3), np.float32)
     s = np.zeros((W, C), np.float32)
     with R.System(sp) as sys:
@@ -193,7 +201,8 @@ def test_device_pointer_path_matches_host_path(R, orc):
 
 
 # ------------------------------------------------------------------ dynamics
-@pytest.mark.parametrize("n,C,W,H,seed", [(22, 2, 16, 64, 1), (200, 20, 8, 256, 2), (45, 6, 35, 64, 9)])
+@pytest.mark.parametrize("n,C,W,H,seed", [(22, 2, 16, 64, 1), (200, 20, 8, 256, 2), (45, 6, 35, 64, 9),
+                                          (300, 12, 3, 64, 10)])   # two batches of the integrator loop
 def test_twenty_step_biased_trajectories(R, orc, n, C, W, H, seed):
     sp = I.make_system(n, C, seed, output_freq=1)
     x0 = I.make_chains(W, sp, seed)
