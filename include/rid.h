@@ -239,6 +239,59 @@ RID_API int rid_profile_read(rid_system* sys, int32_t max_kernels, char* names_o
 RID_API int64_t rid_launch_count(rid_system* sys);
 
 /*
+ * Server: one device memory pool of a fixed HBM budget, from which batched
+ * label runs (rid_label_batch) take their device memory.  The pool is
+ * allocated once by rid_server_create on the current device; every later call
+ * must be made with that device current.  Not thread-safe: one thread at a
+ * time per server.
+ * Errors: RID_ERR_ARG (budget below 1 MiB), RID_ERR_OOM (the budget cannot be
+ * allocated), RID_ERR_CUDA.
+ */
+typedef struct rid_server rid_server;
+RID_API int rid_server_create(uint64_t hbm_budget_bytes, rid_server** out);
+RID_API int rid_server_destroy(rid_server* srv);   /* NULL is accepted */
+
+/* One restrained labeling job of a batch.  Every field means what the
+ * argument of the same name means for rid_label; `sys` is the job's chain,
+ * force field, CVs and integrator (any number of jobs may share a system). */
+typedef struct {
+    rid_system* sys;
+    int32_t n_runs;             /* R >= 1                                        */
+    int32_t n_blocks;           /* 2..256, n_steps - n_equil >= n_blocks         */
+    const float* x0;            /* [R][N][3]                                      */
+    const float* v0;            /* [R][N][3] | NULL (Maxwell-Boltzmann at step0)  */
+    const double* s0;           /* [R][C]                                         */
+    const double* kappa;        /* [R][C]                                         */
+    uint64_t step0;
+    int64_t n_steps, n_equil;
+    double* mf_out;             /* [R][C]                                         */
+    double* se_out;             /* [R][C]                                         */
+    double* std_out;            /* [R][C]                                         */
+    float* x_out;               /* [R][N][3] | NULL                               */
+    float* v_out;               /* [R][N][3] | NULL                               */
+} rid_label_job;
+
+/*
+ * Batched restrained labeling (Sec. "Labeling phase", restrained method):
+ * every run of every job in ONE persistent kernel launch that keeps each
+ * chain resident in shared memory for all of its steps.  Jobs may differ in
+ * chain length, CV count, restraints and step counts.  Each job's outputs are
+ * bit-identical to rid_label on the same inputs.
+ *   threads     CTA size of the persistent kernel: 128, 256 or 512, or 0 to
+ *               pick it by timing the batch itself for a few steps (the
+ *               choice is cached per batch shape on the server)
+ *   status_out  [n_jobs] | NULL: per job RID_OK or RID_ERR_NONFINITE
+ * `mem` applies to every array of every job.  Synchronous.  The jobs' device
+ * memory comes from the server pool and is released before the call returns.
+ * Errors: RID_ERR_ARG (a job violates a rid_label limit, or its chain needs
+ * more than 220 KB of shared memory: about 4000 beads), RID_ERR_OOM (the batch
+ * does not fit the server's budget), RID_ERR_STATE (wrong device),
+ * RID_ERR_CUDA, RID_ERR_NONFINITE (some job went non-finite; outputs written).
+ */
+RID_API int rid_label_batch(rid_server* srv, const rid_label_job* jobs, int32_t n_jobs, int32_t threads,
+                            int32_t* status_out, int32_t mem, void* stream);
+
+/*
  * Ensemble member gradients with no device allocation.  The paper has no
  * counterpart: this is a library facility for callers that cannot allocate
  * device memory (a framework that owns all device memory through its own pool,

@@ -128,6 +128,10 @@ struct rid_system {
     long long launches = 0;
 };
 
+// Accessors for the batch / server code in other translation units.
+const SysDev* rid_sys_dev(const rid_system* sys) { return &sys->S; }
+int rid_sys_device(const rid_system* sys) { return sys->device; }
+
 // Run one kernel launcher, bracketed by events while profiling is enabled.
 template <typename F>
 static int timed_launch(rid_system* sys, const char* name, cudaStream_t st, F&& launch) {

@@ -187,3 +187,6 @@ void rid_launch_mlp_fp32(const EnsDev& E, StateDev st, int W, int C, cudaStream_
 size_t rid_mlp_fp32_scratch_floats(int W, int M, int L, int H);
 // Set the calling thread's rid_last_error message; returns code.
 int rid_fail(int code, const char* fmt, ...);
+// Device description and device ordinal of a system (defined with rid_system).
+const SysDev* rid_sys_dev(const rid_system* sys);
+int rid_sys_device(const rid_system* sys);

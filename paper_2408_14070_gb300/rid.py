@@ -25,7 +25,8 @@ RID_BIAS_NONE, RID_BIAS_ENSEMBLE, RID_BIAS_RESTRAINT = 0, 1, 2
 EXPORTS = ("rid_version", "rid_status_string", "rid_last_error", "rid_create_system", "rid_destroy_system",
            "rid_set_ensemble", "rid_explore", "rid_label", "rid_eval_forces", "rid_pair_mask", "rid_philox",
            "rid_walkers_load", "rid_walkers_advance", "rid_walkers_read", "rid_profile_enable",
-           "rid_profile_read", "rid_launch_count", "rid_ensemble_grad_noalloc")
+           "rid_profile_read", "rid_launch_count", "rid_ensemble_grad_noalloc", "rid_server_create",
+           "rid_server_destroy", "rid_label_batch")
 
 
 class RidError(RuntimeError):
@@ -47,6 +48,13 @@ class EnsembleDesc(C.Structure):
     _fields_ = [("n_models", C.c_int32), ("n_in", C.c_int32), ("n_layers", C.c_int32), ("width", C.c_int32),
                 ("resnet", C.c_int32), ("precision", C.c_int32), ("trust_lo", C.c_double),
                 ("trust_hi", C.c_double), ("weights", C.POINTER(C.c_float))]
+
+
+class LabelJob(C.Structure):
+    _fields_ = [("sys", C.c_void_p), ("n_runs", C.c_int32), ("n_blocks", C.c_int32), ("x0", C.c_void_p),
+                ("v0", C.c_void_p), ("s0", C.c_void_p), ("kappa", C.c_void_p), ("step0", C.c_uint64),
+                ("n_steps", C.c_int64), ("n_equil", C.c_int64), ("mf_out", C.c_void_p), ("se_out", C.c_void_p),
+                ("std_out", C.c_void_p), ("x_out", C.c_void_p), ("v_out", C.c_void_p)]
 
 
 _lib = None
@@ -80,6 +88,9 @@ def lib() -> C.CDLL:
     L.rid_profile_read.argtypes = [vp, i32, C.c_char_p, C.POINTER(C.c_double), C.POINTER(i64), C.POINTER(i32)]
     L.rid_launch_count.argtypes = [vp]
     L.rid_ensemble_grad_noalloc.argtypes = [i32, i32, vp, i32, i32, i32, i32, vp, vp, vp, vp]
+    L.rid_server_create.argtypes = [u64, C.POINTER(vp)]
+    L.rid_server_destroy.argtypes = [vp]
+    L.rid_label_batch.argtypes = [vp, C.POINTER(LabelJob), i32, i32, C.POINTER(i32), i32, vp]
     L.rid_launch_count.restype = i64
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype or C.c_int
@@ -283,6 +294,57 @@ def philox(counters, seed, words_out=None, normals_out=None, stream=None):
     pw = a.ptr(words_out, np.uint32, (n, 4), True)
     pn = a.ptr(normals_out, np.float32, (n, 3), True)
     _check(lib().rid_philox(C.c_int64(n), pc, C.c_uint64(int(seed)), pw, pn, a.mem, _stream_ptr(stream)))
+
+
+class Server:
+    """A budgeted device memory pool for batched label runs (wraps rid_server*)."""
+
+    def __init__(self, hbm_budget_bytes):
+        h = C.c_void_p()
+        _check(lib().rid_server_create(C.c_uint64(int(hbm_budget_bytes)), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rid_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def label_batch(self, jobs, threads=0, stream=None, raise_nonfinite=True):
+        """jobs: list of dicts with keys system, x0, s0, kappa, n_steps, n_equil,
+        n_blocks, mf, se, std and optionally v0, step0, x_out, v_out.  Returns
+        the per-job status list."""
+        a = _Args()
+        arr = (LabelJob * max(1, len(jobs)))()
+        for k, j in enumerate(jobs):
+            sysobj = j["system"]
+            R = int(j["x0"].shape[0])
+            N, Cn = sysobj.N, sysobj.C
+            arr[k] = LabelJob(sysobj.h.value, R, int(j["n_blocks"]),
+                              a.ptr(j["x0"], np.float32, (R, N, 3)), a.ptr(j.get("v0"), np.float32, (R, N, 3)),
+                              a.ptr(j["s0"], np.float64, (R, Cn)), a.ptr(j["kappa"], np.float64, (R, Cn)),
+                              int(j.get("step0", 0)), int(j["n_steps"]), int(j["n_equil"]),
+                              a.ptr(j["mf"], np.float64, (R, Cn), True), a.ptr(j["se"], np.float64, (R, Cn), True),
+                              a.ptr(j["std"], np.float64, (R, Cn), True),
+                              a.ptr(j.get("x_out"), np.float32, (R, N, 3), True),
+                              a.ptr(j.get("v_out"), np.float32, (R, N, 3), True))
+        status = (C.c_int32 * max(1, len(jobs)))()
+        mem = a.mem if a.mem is not None else RID_MEM_HOST
+        rc = lib().rid_label_batch(self.h, arr, len(jobs), int(threads), status, mem, _stream_ptr(stream))
+        if rc != RID_OK and not (rc == RID_ERR_NONFINITE and not raise_nonfinite):
+            _check(rc)
+        return [int(status[k]) for k in range(len(jobs))]
 
 
 def ensemble_grad_noalloc(s, weights, n_models, n_layers, width, grad_out, value_out=None, resnet=False,
