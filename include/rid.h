@@ -239,11 +239,13 @@ RID_API int rid_profile_read(rid_system* sys, int32_t max_kernels, char* names_o
 RID_API int64_t rid_launch_count(rid_system* sys);
 
 /*
- * Server: one device memory pool of a fixed HBM budget, from which batched
- * label runs (rid_label_batch) take their device memory.  The pool is
- * allocated once by rid_server_create on the current device; every later call
- * must be made with that device current.  Not thread-safe: one thread at a
- * time per server.
+ * Server: device memory of a fixed HBM budget, from which batched label runs
+ * (rid_label_batch) and the request loop (rid_submit / rid_poll) take their
+ * device memory.  Memory is allocated in segments, on demand, up to the
+ * budget, on the device current at rid_server_create; every later call must
+ * be made with that device current.  rid_submit and rid_poll may be called
+ * from any thread; rid_label_batch and rid_server_destroy from one thread at
+ * a time.  rid_server_destroy waits for every submitted job to finish.
  * Errors: RID_ERR_ARG (budget below 1 MiB), RID_ERR_OOM (the budget cannot be
  * allocated), RID_ERR_CUDA.
  */
@@ -290,6 +292,76 @@ typedef struct {
  */
 RID_API int rid_label_batch(rid_server* srv, const rid_label_job* jobs, int32_t n_jobs, int32_t threads,
                             int32_t* status_out, int32_t mem, void* stream);
+
+/*
+ * Request loop (continuous batching).  rid_submit queues a labeling or an
+ * exploration job and returns at once; a worker thread of the server admits
+ * queued jobs in arrival order as soon as their device memory fits the
+ * budget, and runs every admitted job concurrently:
+ *   - label jobs advance together, in ticks of the persistent kernel
+ *     (rid_label_batch's kernel); each tick gives every active job a number
+ *     of steps sized to its chain length, and jobs that arrive meanwhile join
+ *     the next tick;
+ *   - exploration jobs run on their own stream as captured CUDA graphs of a
+ *     chunk of steps, replayed until the job is done (one graph per job).
+ * A job's results are the same bits as rid_label / rid_explore on the same
+ * inputs, alone or in any mix.
+ * Memory: label jobs take their arrays from the server pool; an exploration
+ * job's system holds its own device state, which the server counts against
+ * the same budget (the bytes of its walker state and ensemble scratch) while
+ * the job runs.
+ */
+enum { RID_JOB_LABEL = 1, RID_JOB_EXPLORE = 2 };
+
+typedef struct {
+    int32_t kind;             /* RID_JOB_LABEL or RID_JOB_EXPLORE                         */
+    int32_t n_walkers;        /* label runs R, or exploration walkers W                    */
+    rid_system* sys;          /* the job's chain; for exploration also its ensemble.  An
+                                 exploration job uses the system's resident walker state:
+                                 exploration jobs on one system run one after another,
+                                 and the caller must not use the system until rid_poll
+                                 reports the job final                                  */
+    const float* x0;          /* host [W][N][3], copied by rid_submit                      */
+    const float* v0;          /* host [W][N][3] | NULL (Maxwell-Boltzmann at step0)        */
+    uint64_t step0;
+    int64_t n_steps;
+    /* labeling (see rid_label) */
+    const double* s0;         /* host [R][C], copied                                       */
+    const double* kappa;      /* host [R][C], copied                                       */
+    int64_t n_equil;
+    int32_t n_blocks;
+    double* mf_out;           /* host [R][C]                                              */
+    double* se_out;
+    double* std_out;
+    /* exploration (see rid_explore) */
+    float* cv_out;            /* host [W][T][C] | NULL                                     */
+    float* eps_out;           /* host [W][T] | NULL                                        */
+    /* both */
+    float* x_out;             /* host [W][N][3] | NULL                                     */
+    float* v_out;             /* host [W][N][3] | NULL                                     */
+} rid_request;
+
+/* Times in milliseconds since the server was created. */
+typedef struct {
+    int32_t status;           /* RID_NOT_READY or the job's final status                  */
+    int32_t kind;
+    double t_submit_ms;
+    double t_start_ms;        /* admitted (device memory granted), -1 while queued         */
+    double t_end_ms;          /* results written, -1 while running                         */
+} rid_job_info;
+
+/* Queue a job.  Output arrays must stay valid until rid_poll reports the job
+ * final.  Errors (nothing queued): RID_ERR_ARG (a rid_label / rid_explore
+ * limit, host arrays only), RID_ERR_STATE (system on another device),
+ * RID_ERR_OOM (the job alone exceeds the budget). */
+RID_API int rid_submit(rid_server* srv, const rid_request* req, uint64_t* job_id);
+/* Non-blocking: RID_NOT_READY while the job is queued or running, else its
+ * final status (RID_OK, RID_ERR_NONFINITE with outputs written, RID_ERR_CUDA,
+ * ...), after which the id is forgotten.  info (may be NULL) is filled in
+ * either case.  Unknown id: RID_ERR_ARG. */
+RID_API int rid_poll(rid_server* srv, uint64_t job_id, rid_job_info* info);
+/* Jobs queued and running, and device bytes granted to running jobs. */
+RID_API int rid_server_load(rid_server* srv, int32_t* queued, int32_t* running, uint64_t* bytes_in_use);
 
 /*
  * Ensemble member gradients with no device allocation.  The paper has no

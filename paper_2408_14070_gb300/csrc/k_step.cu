@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long base = (long long)w * N;
     const float kick = S.half_dt * S.inv_mass;
+    const uint32_t stp = step + ((INT == 2 && st.stepbase) ? *st.stepbase : 0u);
     constexpr int BATCH = HEAD_THREADS * HEAD_BEADS;
     // bead data of the first batch (and its Langevin noise) is loaded / drawn
     // before the ensemble reduction, so the two overlap
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
                 pv[k] = f3(st.v[base + i]);
                 if (FIN) pf[k] = f3(st.fff[base + i]);
                 else if (INT == 2) pf[k] = f3(st.f[base + i]);
-                if (INT == 2 && S.c2 != 0.0f) pz[k] = rid_normals3(rid_philox(make_uint4(i, w, step, 0u), S.key0, S.key1));
+                if (INT == 2 && S.c2 != 0.0f) pz[k] = rid_normals3(rid_philox(make_uint4(i, w, stp, 0u), S.key0, S.key1));
             }
         }
     };
@@ -348,6 +349,10 @@ __global__ void k_philox(long long n, const uint32_t* __restrict__ ctr, uint32_t
     }
 }
 
+__global__ void k_add_u32(uint32_t* p, uint32_t d) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *p += d;
+}
+
 inline int chain_threads(int N) {
     int t = ((N + 31) / 32) * 32;
     return t > 256 ? 256 : (t < 32 ? 32 : t);
@@ -441,6 +446,8 @@ void rid_launch_head(const HeadArgs& a, cudaStream_t s) {
     else if (a.mode == 2) head_m<2>(a, s);
     else head_m<0>(a, s);
 }
+
+void rid_launch_add_u32(uint32_t* p, uint32_t d, cudaStream_t s) { k_add_u32<<<1, 32, 0, s>>>(p, d); }
 
 void rid_launch_label_final(const LabelDev& lab, int W, int C, double* mf, double* se, double* sd, cudaStream_t s) {
     const long long n = (long long)W * C;

@@ -117,6 +117,9 @@ struct rid_system {
     uint64_t step_next = 0;
     bool loaded = false;
     bool pending = false;      // the last step's closing half (finish + kick) is still to run
+    // graph replay: the Philox step index is read from a device base
+    DevBuf d_stepbase;
+    bool graph_mode = false;
     // the force field runs on a side stream, concurrently with the ensemble kernel
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -177,6 +180,7 @@ static StateDev state_view(rid_system* sys) {
     st.hs = sys->hs.as<float>();
     st.eff = sys->eff.as<double>();
     st.flags = sys->flags.as<int>();
+    st.stepbase = sys->graph_mode ? sys->d_stepbase.as<uint32_t>() : nullptr;
     return st;
 }
 
@@ -770,6 +774,87 @@ static int do_read(rid_system* sys, float* x_out, float* v_out, uint64_t* step_n
     TRY(fetch_flags(sys, W, st, &bad));
     if (bad) return fail(RID_ERR_NONFINITE, "non-finite force or velocity in at least one walker");
     return RID_OK;
+}
+
+// --- operations for the request loop (rid_server.cu) ------------------------
+int rid_sys_load(rid_system* sys, int W, const float* x0, const float* v0, uint64_t step0, cudaStream_t st) {
+    TRY(do_load(sys, W, x0, v0, step0, RID_MEM_HOST, st));
+    TRY(sys->d_stepbase.ensure(sizeof(uint32_t)));
+    CK(cudaMemsetAsync(sys->d_stepbase.p, 0, sizeof(uint32_t), st));
+    rid_launch_add_u32(sys->d_stepbase.as<uint32_t>(), (uint32_t)step0, st);
+    CK(cudaGetLastError());
+    return RID_OK;
+}
+
+int rid_sys_graph_advance(rid_system* sys, int64_t n_steps, float* dcv, float* deps, cudaStream_t st,
+                          cudaGraphExec_t* out) {
+    if (!sys->loaded) return fail(RID_ERR_STATE, "no walkers loaded");
+    const int of = sys->S.output_freq;
+    if (n_steps < 1 || n_steps % of) return fail(RID_ERR_ARG, "graph chunk must be a positive multiple of output_freq");
+    if (sys->prof_on) return fail(RID_ERR_STATE, "kernel profiling is on");
+    if (!sys->d_stepbase.p) return fail(RID_ERR_STATE, "walkers were not loaded for graph replay");
+    TRY(check_device(sys));
+    TRY(ensure_side(sys));
+    TRY(settle(sys, st));
+    const int W = sys->W_act, mode = sys->has_ens ? 1 : 0;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    sys->graph_mode = true;
+    bool pend = false;
+    int rc = run_steps(sys, W, mode, nullptr, n_steps, 0, dcv, deps, nullptr, n_steps / of, pend, false, st);
+    if (rc == RID_OK) rid_launch_add_u32(sys->d_stepbase.as<uint32_t>(), (uint32_t)n_steps, st);
+    sys->graph_mode = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc != RID_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(RID_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
+    const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return fail(RID_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+    sys->pending = pend;
+    return RID_OK;
+}
+
+int rid_sys_advance(rid_system* sys, int64_t n_steps, float* dcv, float* deps, cudaStream_t st) {
+    if (!sys->loaded) return fail(RID_ERR_STATE, "no walkers loaded");
+    TRY(check_device(sys));
+    const int W = sys->W_act, mode = sys->has_ens ? 1 : 0, of = sys->S.output_freq;
+    TRY(ensure_side(sys));
+    sys->graph_mode = true;   // Philox step = device base + t, as in the replayed graph
+    const int rc = run_steps(sys, W, mode, nullptr, n_steps, 0, dcv, deps, nullptr, n_steps / of, sys->pending,
+                             false, st);
+    sys->graph_mode = false;
+    TRY(rc);
+    rid_launch_add_u32(sys->d_stepbase.as<uint32_t>(), (uint32_t)n_steps, st);
+    CK(cudaGetLastError());
+    return RID_OK;
+}
+
+int rid_sys_read_async(rid_system* sys, float* dx, float* dv, cudaStream_t st) {
+    if (!sys->loaded) return fail(RID_ERR_STATE, "no walkers loaded");
+    TRY(settle(sys, st));
+    const long long nb = (long long)sys->W_act * sys->S.N;
+    StateDev sd = state_view(sys);
+    if (dx) rid_launch_unpack(sd.x, dx, nb, st);
+    if (dv) rid_launch_unpack(sd.v, dv, nb, st);
+    CK(cudaGetLastError());
+    return RID_OK;
+}
+
+int rid_sys_flags(rid_system* sys, cudaStream_t st, bool* any_bad) { return fetch_flags(sys, sys->W_act, st, any_bad); }
+
+size_t rid_sys_footprint(const rid_system* sys, int W) {
+    const size_t N = sys->S.N, C = sys->S.C, nb = (size_t)W * N, nc = (size_t)W * C;
+    size_t b = 4 * 16 * nb + nc * (4 + 64 + 8) + (size_t)W * (4 + 8 + 4) + 2 * 12 * nb;
+    if (sys->has_ens) {
+        const EnsDev& E = sys->E;
+        b += (size_t)E.M * nc * 4 + (size_t)E.M * W * 4;
+        if (sys->precision == RID_PREC_FP32) b += rid_mlp_fp32_scratch_floats(W, E.M, E.L, E.H) * 4;
+        else b += (size_t)E.M * ((W + 127) / 128) * E.L * 128 * E.H * 2;
+    }
+    return b;
 }
 
 extern "C" int rid_walkers_load(rid_system* sys, int32_t W, const float* x0, const float* v0, uint64_t step0,

@@ -59,6 +59,7 @@ struct StateDev {
     float* hs;      // MLP activation scratch
     double* eff;    // [W] force-field energy (energy mode)
     int* flags;     // [W] non-finite flags
+    const uint32_t* stepbase;   // device base added to the Philox step index (graph replay), or NULL
 };
 
 // Label (restrained MD) accumulators.
@@ -179,6 +180,7 @@ struct HeadArgs {
     uint32_t step;             // Philox step of the opened step
 };
 void rid_launch_head(const HeadArgs& a, cudaStream_t s);
+void rid_launch_add_u32(uint32_t* p, uint32_t d, cudaStream_t s);
 void rid_launch_label_final(const LabelDev& lab, int W, int C, double* mf, double* se, double* sd,
                             cudaStream_t s);
 void rid_launch_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* words,
@@ -190,3 +192,21 @@ int rid_fail(int code, const char* fmt, ...);
 // Device description and device ordinal of a system (defined with rid_system).
 const SysDev* rid_sys_dev(const rid_system* sys);
 int rid_sys_device(const rid_system* sys);
+// Resident-walker operations used by the request loop (all enqueue on st).
+//   load: W walkers from host arrays (v0 NULL: Maxwell-Boltzmann), force at x0,
+//     Philox step base = step0.
+//   graph_advance: capture n_steps biased steps (n_steps a multiple of the
+//     output frequency) with device traces dcv [W][T][C], deps [W][T] as a
+//     graph whose Philox step index is read from the device base, which the
+//     graph advances by n_steps at its end; the graph can be replayed.
+//   advance: the same steps launched directly (for a remainder chunk).
+//   read_async: unpack x, v (either may be NULL) into device xyz arrays.
+//   flags: whether any walker went non-finite since the load (synchronises st).
+int rid_sys_load(rid_system* sys, int W, const float* x0, const float* v0, uint64_t step0, cudaStream_t st);
+int rid_sys_graph_advance(rid_system* sys, int64_t n_steps, float* dcv, float* deps, cudaStream_t st,
+                          cudaGraphExec_t* out);
+int rid_sys_advance(rid_system* sys, int64_t n_steps, float* dcv, float* deps, cudaStream_t st);
+int rid_sys_read_async(rid_system* sys, float* dx, float* dv, cudaStream_t st);
+int rid_sys_flags(rid_system* sys, cudaStream_t st, bool* any_bad);
+// Device bytes a system holds for W walkers with its current ensemble.
+size_t rid_sys_footprint(const rid_system* sys, int W);

@@ -1,12 +1,23 @@
-// rid_server.cu -- the server object: a budgeted device memory pool, pinned
-// staging, and batched restrained labeling through the persistent kernel
-// k_label_fused (one launch for any number of uneven jobs), with a timing
-// autotuner for the kernel's CTA size.
+// rid_server.cu -- the server object: device memory of a fixed budget
+// (segments allocated on demand, first-fit inside each segment), pinned
+// staging, batched restrained labeling through the persistent kernel
+// k_label_fused (one launch for any number of uneven jobs) with a timing
+// autotuner for its CTA size, and the request loop (rid_submit / rid_poll):
+// a worker thread that admits jobs by device footprint and runs label jobs in
+// ticks of the persistent kernel and exploration jobs as replayed CUDA graphs.
 #include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdint>
 #include <cstring>
+#include <deque>
 #include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "rid_batch.cuh"
@@ -32,33 +43,12 @@ constexpr size_t LF_SMEM_LIMIT = 220 * 1024;
 
 inline size_t align_up(size_t n) { return (n + POOL_ALIGN - 1) & ~(POOL_ALIGN - 1); }
 
-// First-fit allocator over one device allocation of the server's budget.
-// Free blocks are kept by offset and merged with their neighbours on release.
-class Pool {
+// First-fit allocator over a range of offsets.  Free blocks are kept by
+// offset and merged with their neighbours on release.
+class OffsetAlloc {
   public:
-    int init(size_t bytes) {
-        cudaError_t e = cudaMalloc(&base_, bytes);
-        if (e != cudaSuccess) {
-            base_ = nullptr;
-            cudaGetLastError();
-            return rid_fail(RID_ERR_OOM, "rid_server_create: cudaMalloc(%zu) failed: %s", bytes,
-                            cudaGetErrorString(e));
-        }
-        cap_ = bytes;
-        free_.clear();
-        free_[0] = bytes;
-        used_ = 0;
-        return RID_OK;
-    }
-    void release() {
-        if (base_) cudaFree(base_);
-        base_ = nullptr;
-        free_.clear();
-        cap_ = used_ = 0;
-    }
-    // Offset of n bytes (256-byte aligned), or SIZE_MAX if no block fits.
+    explicit OffsetAlloc(size_t bytes) { free_[0] = bytes; }
     size_t alloc(size_t n) {
-        n = align_up(n ? n : 1);
         for (auto it = free_.begin(); it != free_.end(); ++it) {
             if (it->second < n) continue;
             const size_t off = it->first, rest = it->second - n;
@@ -70,7 +60,6 @@ class Pool {
         return SIZE_MAX;
     }
     void free(size_t off, size_t n) {
-        n = align_up(n ? n : 1);
         used_ -= n;
         auto it = free_.emplace(off, n).first;
         auto nx = std::next(it);
@@ -86,14 +75,96 @@ class Pool {
             }
         }
     }
-    char* base() const { return static_cast<char*>(base_); }
     size_t used() const { return used_; }
-    size_t capacity() const { return cap_; }
 
   private:
-    void* base_ = nullptr;
-    size_t cap_ = 0, used_ = 0;
     std::map<size_t, size_t> free_;
+    size_t used_ = 0;
+};
+
+// Device memory of the server: segments of at least seg_bytes, allocated on
+// demand while the segments plus the reservations of exploration jobs (whose
+// systems hold their own device memory) stay within the budget.  Empty
+// segments are kept until trim() (cudaFree synchronises the device).
+class SegPool {
+  public:
+    void init(size_t budget) {
+        budget_ = budget;
+        seg_bytes_ = std::min<size_t>(budget, (size_t)64 << 20);
+    }
+    // Device pointer to n bytes (256-byte aligned), or nullptr if it does not
+    // fit the budget now (or cudaMalloc failed).
+    void* alloc(size_t n) {
+        n = align_up(n ? n : 1);
+        for (auto& sg : segs_) {
+            const size_t off = sg->a.alloc(n);
+            if (off != SIZE_MAX) return sg->base + off;
+        }
+        const size_t sz = std::max(seg_bytes_, n);
+        if (seg_total_ + reserved_ + sz > budget_) {
+            trim();
+            if (seg_total_ + reserved_ + sz > budget_) return nullptr;
+        }
+        void* p = nullptr;
+        if (cudaMalloc(&p, sz) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        segs_.emplace_back(new Seg{static_cast<char*>(p), sz, OffsetAlloc(sz)});
+        seg_total_ += sz;
+        return segs_.back()->base + segs_.back()->a.alloc(n);
+    }
+    void free(void* p, size_t n) {
+        if (!p) return;
+        n = align_up(n ? n : 1);
+        char* c = static_cast<char*>(p);
+        for (auto& sg : segs_)
+            if (c >= sg->base && c < sg->base + sg->bytes) {
+                sg->a.free((size_t)(c - sg->base), n);
+                return;
+            }
+    }
+    bool reserve(size_t n) {
+        if (seg_total_ + reserved_ + n > budget_) {
+            trim();
+            if (seg_total_ + reserved_ + n > budget_) return false;
+        }
+        reserved_ += n;
+        return true;
+    }
+    void unreserve(size_t n) { reserved_ -= n; }
+    void trim() {
+        for (size_t i = 0; i < segs_.size();) {
+            if (segs_[i]->a.used() == 0) {
+                cudaFree(segs_[i]->base);
+                seg_total_ -= segs_[i]->bytes;
+                segs_.erase(segs_.begin() + i);
+            } else {
+                ++i;
+            }
+        }
+    }
+    void release() {
+        for (auto& sg : segs_) cudaFree(sg->base);
+        segs_.clear();
+        seg_total_ = 0;
+    }
+    size_t budget() const { return budget_; }
+    size_t in_use() const {
+        size_t u = reserved_;
+        for (auto& sg : segs_) u += sg->a.used();
+        return u;
+    }
+    size_t held() const { return seg_total_ + reserved_; }
+
+  private:
+    struct Seg {
+        char* base;
+        size_t bytes;
+        OffsetAlloc a;
+    };
+    std::vector<std::unique_ptr<Seg>> segs_;
+    size_t budget_ = 0, seg_bytes_ = 0, seg_total_ = 0, reserved_ = 0;
 };
 
 // Grow-only pinned host buffer.
@@ -157,32 +228,114 @@ JobLayout job_layout(int R, int N, int C, int B) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+namespace {
+
+// One queued or running job of the request loop.
+struct SJob {
+    uint64_t id = 0;
+    rid_request rq{};
+    int W = 0, N = 0, C = 0, of = 1;
+    long long T = 0;                     // exploration trace slots
+    std::vector<float> x0, v0;
+    std::vector<double> s0, kappa;
+    size_t foot = 0;                     // bytes counted against the budget
+    double t_submit = 0, t_start = -1, t_end = -1;
+    int status = RID_NOT_READY;
+    // label: one pool region = job arrays | input staging | output staging
+    char* region = nullptr;
+    JobLayout lay{};
+    size_t in_off = 0, in_bytes = 0, out_off = 0, out_bytes = 0;
+    FusedJob fj{};
+    bool staged = false;
+    long long t_done = 0, t_next = 0;
+    // exploration
+    int slot = -1, phase = 0;            // phase 1: chunk in flight, 2: final read in flight
+    cudaGraphExec_t gexec = nullptr;
+    long long chunk = 0, done = 0, cur = 0;
+    char* dbuf = nullptr;                // pool: chunk traces, then final x / v
+    size_t dbuf_bytes = 0;
+};
+
+struct ESlot {                           // stream of one running exploration job
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    Pinned pin;
+    SJob* job = nullptr;
+};
+
+constexpr int N_ESLOTS = 16;
+
+size_t label_io_in(const SJob& j) { return align_up(12 * (size_t)j.W * j.N * (j.v0.empty() ? 1 : 2) + 16 * (size_t)j.W * j.C); }
+size_t label_io_out(const SJob& j) {
+    return align_up(24 * (size_t)j.W * j.C + 4 * (size_t)j.W +
+                    12 * (size_t)j.W * j.N * ((j.rq.x_out ? 1 : 0) + (j.rq.v_out ? 1 : 0)));
+}
+long long explore_chunk(int of, long long n_steps) {
+    long long c = ((256 + of - 1) / of) * of;
+    return std::max<long long>(of, std::min(c, (n_steps / of) * of));
+}
+size_t explore_dbuf(const SJob& j) {
+    const size_t tc = (size_t)(explore_chunk(j.of, j.rq.n_steps) / j.of);
+    return align_up(std::max((size_t)j.W * tc * (j.C + 1) * 4, (size_t)j.W * j.N * 24));
+}
+
+}  // namespace
+
 struct rid_server {
     int device = 0, n_sm = 0;
-    Pool pool;
-    Pinned pin_in, pin_out, pin_meta;
-    void* d_meta = nullptr;       // job table, items, descriptors, counter (grow-only, outside the budget)
+    SegPool pool;
+    std::mutex pool_mu;                  // pool and tuner cache: batch call and worker
+    Pinned pin_in, pin_out, pin_meta;    // batch call staging
+    void* d_meta = nullptr;              // batch call tables (grow-only, outside the budget)
     size_t d_meta_bytes = 0;
-    std::map<long long, int> tuned;   // batch-shape key -> CTA size
+    std::map<long long, int> tuned;      // batch-shape key -> CTA size
     int last_threads = 0;
+    // request loop
+    std::chrono::steady_clock::time_point t0;
+    std::mutex mu;                       // queue, job records
+    std::condition_variable cv;
+    std::deque<SJob*> queue;
+    std::unordered_map<uint64_t, std::unique_ptr<SJob>> jobs;
+    uint64_t next_id = 1;
+    int running = 0;
+    bool stop = false;
+    std::thread worker;
+    // worker-owned
+    cudaStream_t lst = nullptr;
+    cudaEvent_t lev = nullptr, le0 = nullptr;
+    std::vector<SJob*> labels;           // admitted label jobs
+    std::vector<SJob*> tick;             // jobs of the tick in flight
+    bool tick_busy = false;
+    double tick_target_ms = 4.0, cost = 3.0e-5;   // ms per step per N^1.5, refined after every tick
+    double tick_pred = 0.0;
+    Pinned lmeta_h, lio_h;
+    void* lmeta_d = nullptr;
+    size_t lmeta_d_bytes = 0;
+    ESlot es[N_ESLOTS];
 };
 
 namespace {
 
-int ensure_meta(rid_server* srv, size_t n) {
-    if (n <= srv->d_meta_bytes) return RID_OK;
-    if (srv->d_meta) cudaFree(srv->d_meta);
-    srv->d_meta = nullptr;
-    srv->d_meta_bytes = 0;
-    cudaError_t e = cudaMalloc(&srv->d_meta, n);
+double now_ms(const rid_server* srv) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - srv->t0).count();
+}
+
+int ensure_dev(void** p, size_t* have, size_t n) {
+    if (n <= *have) return RID_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    cudaError_t e = cudaMalloc(p, n);
     if (e != cudaSuccess) {
-        srv->d_meta = nullptr;
+        *p = nullptr;
         cudaGetLastError();
-        return rid_fail(RID_ERR_OOM, "cudaMalloc(%zu) for batch tables failed", n);
+        return rid_fail(RID_ERR_OOM, "cudaMalloc(%zu) for server tables failed", n);
     }
-    srv->d_meta_bytes = n;
+    *have = n;
     return RID_OK;
 }
+
+int ensure_meta(rid_server* srv, size_t n) { return ensure_dev(&srv->d_meta, &srv->d_meta_bytes, n); }
 
 int check_server_device(rid_server* srv) {
     int dev = -1;
@@ -192,26 +345,28 @@ int check_server_device(rid_server* srv) {
     return RID_OK;
 }
 
-// Validation shared by the batch call: the limits of rid_label plus the
-// persistent kernel's shared-memory limit.
-int check_label_job(const rid_label_job& j, int idx, int device) {
-    if (!j.sys || !j.x0 || !j.s0 || !j.kappa || !j.mf_out || !j.se_out || !j.std_out)
-        return rid_fail(RID_ERR_ARG, "job %d: NULL argument", idx);
-    if (rid_sys_device(j.sys) != device)
-        return rid_fail(RID_ERR_STATE, "job %d: system lives on device %d, server on %d", idx, rid_sys_device(j.sys),
+// The limits of rid_label plus the persistent kernel's shared-memory limit.
+int check_label_args(rid_system* sys, int R, int B, uint64_t step0, int64_t n_steps, int64_t n_equil, int idx,
+                     int device) {
+    if (rid_sys_device(sys) != device)
+        return rid_fail(RID_ERR_STATE, "job %d: system lives on device %d, server on %d", idx, rid_sys_device(sys),
                         device);
-    if (j.n_runs < 1) return rid_fail(RID_ERR_ARG, "job %d: n_runs=%d must be >= 1", idx, j.n_runs);
-    if (j.n_blocks < 2 || j.n_blocks > RID_MAX_BLOCKS)
-        return rid_fail(RID_ERR_ARG, "job %d: n_blocks=%d outside [2, %d]", idx, j.n_blocks, RID_MAX_BLOCKS);
-    if (j.n_equil < 0 || j.n_steps - j.n_equil < j.n_blocks)
+    if (R < 1) return rid_fail(RID_ERR_ARG, "job %d: n_runs=%d must be >= 1", idx, R);
+    if (B < 2 || B > RID_MAX_BLOCKS) return rid_fail(RID_ERR_ARG, "job %d: n_blocks=%d outside [2, %d]", idx, B, RID_MAX_BLOCKS);
+    if (n_equil < 0 || n_steps - n_equil < B)
         return rid_fail(RID_ERR_ARG, "job %d: need 0 <= n_equil and n_steps - n_equil >= n_blocks", idx);
-    if (j.step0 + (uint64_t)j.n_steps > (1ull << 32))
-        return rid_fail(RID_ERR_ARG, "job %d: step0 + n_steps exceeds 2^32", idx);
-    const SysDev* S = rid_sys_dev(j.sys);
+    if (step0 + (uint64_t)n_steps > (1ull << 32)) return rid_fail(RID_ERR_ARG, "job %d: step0 + n_steps exceeds 2^32", idx);
+    const SysDev* S = rid_sys_dev(sys);
     if (rid_label_fused_smem(S->N, S->C, 0) > LF_SMEM_LIMIT)
         return rid_fail(RID_ERR_ARG, "job %d: a chain of %d beads and %d CVs needs %zu bytes of shared memory (> %zu)",
                         idx, S->N, S->C, rid_label_fused_smem(S->N, S->C, 0), LF_SMEM_LIMIT);
     return RID_OK;
+}
+
+int check_label_job(const rid_label_job& j, int idx, int device) {
+    if (!j.sys || !j.x0 || !j.s0 || !j.kappa || !j.mf_out || !j.se_out || !j.std_out)
+        return rid_fail(RID_ERR_ARG, "job %d: NULL argument", idx);
+    return check_label_args(j.sys, j.n_runs, j.n_blocks, j.step0, j.n_steps, j.n_equil, idx, device);
 }
 
 long long shape_key(int n_items, int maxN) {
@@ -221,6 +376,433 @@ long long shape_key(int n_items, int maxN) {
     return (long long)a * 64 + b;
 }
 
+// Fill the device pointers of a label job placed at `b`.
+void place_label_job(FusedJob& J, char* b, const JobLayout& L, const SysDev& S, int R, int B, int64_t n_steps,
+                     int64_t n_equil, uint64_t step0, bool mb) {
+    memset(&J, 0, sizeof(J));
+    J.S = S;
+    J.x = reinterpret_cast<float4*>(b + L.x);
+    J.v = reinterpret_cast<float4*>(b + L.v);
+    J.f = reinterpret_cast<float4*>(b + L.f);
+    J.s0 = reinterpret_cast<const double*>(b + L.s0);
+    J.kappa = reinterpret_cast<const double*>(b + L.kappa);
+    J.mf = reinterpret_cast<double*>(b + L.mf);
+    J.se = reinterpret_cast<double*>(b + L.se);
+    J.sd = reinterpret_cast<double*>(b + L.sd);
+    J.sum = reinterpret_cast<double*>(b + L.sum);
+    J.sum2 = reinterpret_cast<double*>(b + L.sum2);
+    J.bsum = reinterpret_cast<double*>(b + L.bsum);
+    J.flags = reinterpret_cast<int*>(b + L.flags);
+    J.R = R;
+    J.B = B;
+    J.n_steps = n_steps;
+    J.n_equil = n_equil;
+    J.K = n_steps - n_equil;
+    J.t0 = 0;
+    J.t1 = n_steps;
+    J.step0 = (uint32_t)step0;
+    J.init = 1;
+    J.mb = mb ? 1 : 0;
+}
+
+// Descriptors that move a label job's inputs from `src` (staging laid out as
+// x0 | v0? | s0 | kappa, or caller device arrays) into its arrays and zero its
+// accumulators.
+void label_in_descs(std::vector<CopyDesc>& d, const FusedJob& J, const JobLayout& L, char* region, const void* x0,
+                    const void* v0, const void* s0, const void* kappa) {
+    const long long nb = (long long)J.R * J.S.N, nc = (long long)J.R * J.S.C;
+    d.push_back({x0, J.x, nb, 0});
+    if (v0) d.push_back({v0, J.v, nb, 0});
+    d.push_back({s0, (void*)J.s0, nc, 2});
+    d.push_back({kappa, (void*)J.kappa, nc, 2});
+    d.push_back({nullptr, region + L.sum, (long long)(L.zero_bytes / 4), 4});
+}
+
+// Descriptors that move a label job's results into `dst` laid out as
+// mf | se | sd | flags | x? | v?.
+void label_out_descs(std::vector<CopyDesc>& d, const FusedJob& J, char* dst, bool xo, bool vo) {
+    const long long nb = (long long)J.R * J.S.N, nc = (long long)J.R * J.S.C;
+    d.push_back({J.mf, dst, nc, 2});
+    d.push_back({J.se, dst + 8 * nc, nc, 2});
+    d.push_back({J.sd, dst + 16 * nc, nc, 2});
+    d.push_back({J.flags, dst + 24 * nc, J.R, 3});
+    char* q = dst + 24 * nc + 4 * J.R;
+    if (xo) {
+        d.push_back({J.x, q, nb, 1});
+        q += 12 * nb;
+    }
+    if (vo) d.push_back({J.v, q, nb, 1});
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// The request loop.
+namespace {
+
+void finish_job(rid_server* srv, SJob* j, int status) {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    j->status = status;
+    j->t_end = now_ms(srv);
+    --srv->running;
+    srv->cv.notify_all();
+}
+
+// Admission of the job at the head of the queue: device memory within the
+// budget (and for exploration a free stream slot and an idle system).
+bool try_admit(rid_server* srv, SJob* j) {
+    std::lock_guard<std::mutex> lk(srv->pool_mu);
+    if (j->rq.kind == RID_JOB_LABEL) {
+        void* p = srv->pool.alloc(j->foot);
+        if (!p) return false;
+        j->region = static_cast<char*>(p);
+        return true;
+    }
+    int slot = -1;
+    for (int k = 0; k < N_ESLOTS; ++k) {
+        if (srv->es[k].job && srv->es[k].job->rq.sys == j->rq.sys) return false;   // system busy
+        if (!srv->es[k].job && slot < 0) slot = k;
+    }
+    if (slot < 0) return false;
+    const size_t sys_bytes = j->foot - j->dbuf_bytes;
+    if (!srv->pool.reserve(sys_bytes)) return false;
+    void* p = srv->pool.alloc(j->dbuf_bytes);
+    if (!p) {
+        srv->pool.unreserve(sys_bytes);
+        return false;
+    }
+    j->dbuf = static_cast<char*>(p);
+    j->slot = slot;
+    srv->es[slot].job = j;
+    return true;
+}
+
+void release_job_memory(rid_server* srv, SJob* j) {
+    std::lock_guard<std::mutex> lk(srv->pool_mu);
+    if (j->rq.kind == RID_JOB_LABEL) {
+        srv->pool.free(j->region, j->foot);
+        j->region = nullptr;
+    } else {
+        srv->pool.free(j->dbuf, j->dbuf_bytes);
+        srv->pool.unreserve(j->foot - j->dbuf_bytes);
+        j->dbuf = nullptr;
+        srv->es[j->slot].job = nullptr;
+    }
+}
+
+// ---- exploration jobs
+int explore_launch_chunk(rid_server* srv, SJob* j) {
+    ESlot& e = srv->es[j->slot];
+    rid_system* sys = j->rq.sys;
+    j->cur = std::min(j->chunk, j->rq.n_steps - j->done);
+    float* dcv = reinterpret_cast<float*>(j->dbuf);
+    const long long tc = j->cur / j->of;
+    float* deps = dcv + (size_t)j->W * tc * j->C;
+    if (j->gexec && j->cur == j->chunk) {
+        SCK(cudaGraphLaunch(j->gexec, e.st));
+    } else {
+        STRY(rid_sys_advance(sys, j->cur, dcv, deps, e.st));
+    }
+    if (tc > 0 && (j->rq.cv_out || j->rq.eps_out)) {
+        const size_t bytes = (size_t)j->W * tc * (j->C + 1) * 4;
+        STRY(e.pin.ensure(bytes));
+        SCK(cudaMemcpyAsync(e.pin.p, j->dbuf, bytes, cudaMemcpyDeviceToHost, e.st));
+    }
+    SCK(cudaEventRecord(e.ev, e.st));
+    j->phase = 1;
+    return RID_OK;
+}
+
+int explore_start(rid_server* srv, SJob* j) {
+    ESlot& e = srv->es[j->slot];
+    rid_system* sys = j->rq.sys;
+    STRY(rid_sys_load(sys, j->W, j->x0.data(), j->v0.empty() ? nullptr : j->v0.data(), j->rq.step0, e.st));
+    j->chunk = explore_chunk(j->of, j->rq.n_steps);
+    if (j->rq.n_steps >= j->chunk) {
+        float* dcv = reinterpret_cast<float*>(j->dbuf);
+        float* deps = dcv + (size_t)j->W * (j->chunk / j->of) * j->C;
+        STRY(rid_sys_graph_advance(sys, j->chunk, dcv, deps, e.st, &j->gexec));
+    }
+    return explore_launch_chunk(srv, j);
+}
+
+// Returns true when the job made progress.
+bool explore_progress(rid_server* srv, SJob* j) {
+    ESlot& e = srv->es[j->slot];
+    const cudaError_t q = cudaEventQuery(e.ev);
+    if (q == cudaErrorNotReady) return false;
+    int rc = RID_OK;
+    if (q != cudaSuccess) rc = rid_fail(RID_ERR_CUDA, "exploration job: %s", cudaGetErrorString(q));
+    if (rc == RID_OK && j->phase == 1) {
+        const long long tc = j->cur / j->of, s0 = j->done / j->of;
+        const float* pc = static_cast<const float*>(e.pin.p);
+        const float* pe = pc + (size_t)j->W * tc * j->C;
+        for (int w = 0; w < j->W && tc > 0; ++w) {
+            if (j->rq.cv_out)
+                memcpy(j->rq.cv_out + ((size_t)w * j->T + s0) * j->C, pc + (size_t)w * tc * j->C, 4 * tc * j->C);
+            if (j->rq.eps_out) memcpy(j->rq.eps_out + (size_t)w * j->T + s0, pe + (size_t)w * tc, 4 * tc);
+        }
+        j->done += j->cur;
+        if (j->done < j->rq.n_steps) {
+            rc = explore_launch_chunk(srv, j);
+            if (rc == RID_OK) return true;
+        } else {
+            float* dx = reinterpret_cast<float*>(j->dbuf);
+            float* dv = dx + (size_t)j->W * j->N * 3;
+            rc = rid_sys_read_async(j->rq.sys, dx, dv, e.st);
+            if (rc == RID_OK) rc = e.pin.ensure((size_t)j->W * j->N * 24);
+            if (rc == RID_OK && cudaMemcpyAsync(e.pin.p, j->dbuf, (size_t)j->W * j->N * 24, cudaMemcpyDeviceToHost,
+                                                e.st) != cudaSuccess)
+                rc = rid_fail(RID_ERR_CUDA, "exploration job: copy of the final state failed");
+            if (rc == RID_OK && cudaEventRecord(e.ev, e.st) != cudaSuccess) rc = rid_fail(RID_ERR_CUDA, "event record");
+            if (rc == RID_OK) {
+                j->phase = 2;
+                return true;
+            }
+        }
+    } else if (rc == RID_OK && j->phase == 2) {
+        const size_t nb3 = (size_t)j->W * j->N * 3;
+        const float* p = static_cast<const float*>(e.pin.p);
+        if (j->rq.x_out) memcpy(j->rq.x_out, p, 4 * nb3);
+        if (j->rq.v_out) memcpy(j->rq.v_out, p + nb3, 4 * nb3);
+        bool bad = false;
+        rc = rid_sys_flags(j->rq.sys, e.st, &bad);
+        if (rc == RID_OK && bad) rc = RID_ERR_NONFINITE;
+    }
+    // final (done, or failed)
+    cudaStreamSynchronize(e.st);
+    if (j->gexec) cudaGraphExecDestroy(j->gexec);
+    j->gexec = nullptr;
+    release_job_memory(srv, j);
+    finish_job(srv, j, rc);
+    return true;
+}
+
+// ---- label jobs: one tick of the persistent kernel over every admitted job
+int label_tick_launch(rid_server* srv) {
+    std::vector<SJob*> act;
+    for (SJob* j : srv->labels) act.push_back(j);
+    if (act.empty()) return RID_OK;
+    cudaStream_t st = srv->lst;
+    // steps per job: about tick_target_ms of work for the job's chain length
+    std::vector<FusedJob> fj(act.size());
+    std::vector<CopyDesc> din, dout;
+    std::vector<FusedItem> items;
+    size_t in_h = 0, out_h = 0;
+    double pred = 0.0;
+    int maxN = 0;
+    size_t smem = 0;
+    for (size_t k = 0; k < act.size(); ++k) {
+        SJob* j = act[k];
+        const double per = srv->cost * std::pow((double)j->N, 1.5);
+        long long steps = (long long)(srv->tick_target_ms / per);
+        steps = std::max<long long>(8, steps);
+        steps = std::min<long long>(steps, j->rq.n_steps - j->t_done);
+        FusedJob J = j->fj;
+        J.t0 = j->t_done;
+        J.t1 = j->t_done + steps;
+        J.init = j->t_done == 0 ? 1 : 0;
+        j->t_next = J.t1;
+        fj[k] = J;
+        pred = std::max(pred, per * steps);
+        maxN = std::max(maxN, j->N);
+        smem = std::max(smem, rid_label_fused_smem(j->N, j->C, 0));
+        for (int r = 0; r < j->W; ++r) items.push_back({(int)k, r});
+        if (!j->staged) {
+            char* src = j->region + j->in_off;
+            const size_t nb = (size_t)j->W * j->N;
+            const char* x0 = src;
+            const char* v0 = j->v0.empty() ? nullptr : src + 12 * nb;
+            const char* s0 = src + 12 * nb * (j->v0.empty() ? 1 : 2);
+            label_in_descs(din, J, j->lay, j->region, x0, v0, s0, s0 + 8 * (size_t)j->W * j->C);
+            in_h += j->in_bytes;
+        }
+        if (J.t1 == j->rq.n_steps) {
+            label_out_descs(dout, J, j->region + j->out_off, j->rq.x_out != nullptr, j->rq.v_out != nullptr);
+            out_h += j->out_bytes;
+        }
+    }
+    std::stable_sort(items.begin(), items.end(), [&](const FusedItem& a, const FusedItem& b) {
+        return (fj[a.job].t1 - fj[a.job].t0) * (double)fj[a.job].S.N * fj[a.job].S.N >
+               (fj[b.job].t1 - fj[b.job].t0) * (double)fj[b.job].S.N * fj[b.job].S.N;
+    });
+    // host staging of new inputs, then the tables
+    STRY(srv->lio_h.ensure(std::max(in_h, out_h) + 256));
+    const size_t o_items = align_up(sizeof(FusedJob) * fj.size());
+    const size_t o_din = align_up(o_items + sizeof(FusedItem) * items.size());
+    const size_t o_dout = align_up(o_din + sizeof(CopyDesc) * din.size());
+    const size_t o_cnt = align_up(o_dout + sizeof(CopyDesc) * dout.size());
+    const size_t meta = o_cnt + 256;
+    STRY(srv->lmeta_h.ensure(meta));
+    STRY(ensure_dev(&srv->lmeta_d, &srv->lmeta_d_bytes, meta));
+    char* hm = srv->lmeta_h.c();
+    char* dm = static_cast<char*>(srv->lmeta_d);
+    memcpy(hm, fj.data(), sizeof(FusedJob) * fj.size());
+    memcpy(hm + o_items, items.data(), sizeof(FusedItem) * items.size());
+    if (!din.empty()) memcpy(hm + o_din, din.data(), sizeof(CopyDesc) * din.size());
+    if (!dout.empty()) memcpy(hm + o_dout, dout.data(), sizeof(CopyDesc) * dout.size());
+    SCK(cudaMemcpyAsync(dm, hm, o_cnt, cudaMemcpyHostToDevice, st));
+    size_t ho = 0;
+    for (SJob* j : act) {
+        if (j->staged) continue;
+        char* p = srv->lio_h.c() + ho;
+        const size_t nb = (size_t)j->W * j->N, nc = (size_t)j->W * j->C;
+        size_t o = 0;
+        memcpy(p + o, j->x0.data(), 12 * nb);
+        o += 12 * nb;
+        if (!j->v0.empty()) {
+            memcpy(p + o, j->v0.data(), 12 * nb);
+            o += 12 * nb;
+        }
+        memcpy(p + o, j->s0.data(), 8 * nc);
+        o += 8 * nc;
+        memcpy(p + o, j->kappa.data(), 8 * nc);
+        SCK(cudaMemcpyAsync(j->region + j->in_off, p, j->in_bytes, cudaMemcpyHostToDevice, st));
+        ho += j->in_bytes;
+        j->staged = true;
+    }
+    if (!din.empty()) rid_launch_copy_descs(reinterpret_cast<const CopyDesc*>(dm + o_din), (int)din.size(), st);
+    FusedArgs A{};
+    A.jobs = reinterpret_cast<const FusedJob*>(dm);
+    A.items = reinterpret_cast<const FusedItem*>(dm + o_items);
+    A.n_items = (int)items.size();
+    A.next = reinterpret_cast<int*>(dm + o_cnt);
+    int nt = 256;
+    {
+        std::lock_guard<std::mutex> lk(srv->pool_mu);
+        auto hit = srv->tuned.find(shape_key((int)items.size(), maxN));
+        if (hit != srv->tuned.end()) nt = hit->second;
+    }
+    if (rid_label_fused_occupancy(nt, smem) < 1) nt = 128;
+    const int occ = std::max(1, rid_label_fused_occupancy(nt, smem));
+    const int grid = (int)std::min<long long>((long long)items.size(), (long long)occ * srv->n_sm);
+    SCK(cudaMemsetAsync(A.next, 0, sizeof(int), st));
+    SCK(cudaEventRecord(srv->le0, st));
+    SCK(rid_launch_label_fused(A, nt, grid, smem, st));
+    if (!dout.empty()) rid_launch_copy_descs(reinterpret_cast<const CopyDesc*>(dm + o_dout), (int)dout.size(), st);
+    SCK(cudaEventRecord(srv->lev, st));
+    ho = 0;
+    for (size_t k = 0; k < act.size(); ++k) {
+        SJob* j = act[k];
+        if (j->t_next != j->rq.n_steps) continue;
+        SCK(cudaMemcpyAsync(srv->lio_h.c() + ho, j->region + j->out_off, j->out_bytes, cudaMemcpyDeviceToHost, st));
+        ho += j->out_bytes;
+    }
+    SCK(cudaEventRecord(srv->lev, st));
+    srv->tick = act;
+    srv->tick_pred = pred;
+    srv->tick_busy = true;
+    return RID_OK;
+}
+
+bool label_tick_progress(rid_server* srv) {
+    if (!srv->tick_busy) return false;
+    const cudaError_t q = cudaEventQuery(srv->lev);
+    if (q == cudaErrorNotReady) return false;
+    srv->tick_busy = false;
+    int rc = q == cudaSuccess ? RID_OK : rid_fail(RID_ERR_CUDA, "label tick: %s", cudaGetErrorString(q));
+    // refine the cost model from the kernel's time (its longest item sets it)
+    float ms = 0.f;
+    if (rc == RID_OK && cudaEventElapsedTime(&ms, srv->le0, srv->lev) == cudaSuccess && srv->tick_pred > 0.0) {
+        const double ratio = ms / srv->tick_pred;
+        srv->cost *= std::min(4.0, std::max(0.25, 0.5 + 0.5 * ratio));
+    }
+    size_t ho = 0;
+    std::vector<SJob*> keep;
+    for (SJob* j : srv->labels) {
+        if (rc != RID_OK) {
+            release_job_memory(srv, j);
+            finish_job(srv, j, rc);
+            continue;
+        }
+        j->t_done = j->t_next;
+        if (j->t_done < j->rq.n_steps) {
+            keep.push_back(j);
+            continue;
+        }
+        const char* p = srv->lio_h.c() + ho;
+        ho += j->out_bytes;
+        const size_t nb = (size_t)j->W * j->N, nc = (size_t)j->W * j->C;
+        memcpy(j->rq.mf_out, p, 8 * nc);
+        memcpy(j->rq.se_out, p + 8 * nc, 8 * nc);
+        memcpy(j->rq.std_out, p + 16 * nc, 8 * nc);
+        const int* fl = reinterpret_cast<const int*>(p + 24 * nc);
+        bool bad = false;
+        for (int r = 0; r < j->W; ++r) bad |= fl[r] != 0;
+        const char* q2 = p + 24 * nc + 4 * (size_t)j->W;
+        if (j->rq.x_out) {
+            memcpy(j->rq.x_out, q2, 12 * nb);
+            q2 += 12 * nb;
+        }
+        if (j->rq.v_out) memcpy(j->rq.v_out, q2, 12 * nb);
+        release_job_memory(srv, j);
+        finish_job(srv, j, bad ? RID_ERR_NONFINITE : RID_OK);
+    }
+    srv->labels.swap(keep);
+    srv->tick.clear();
+    return true;
+}
+
+void worker_main(rid_server* srv) {
+    cudaSetDevice(srv->device);
+    for (;;) {
+        std::vector<SJob*> admitted;
+        {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            for (;;) {
+                const bool busy = srv->running > 0;
+                if (srv->stop && srv->queue.empty() && !busy) return;
+                if (!srv->queue.empty() || busy) break;
+                srv->cv.wait(lk);
+            }
+            while (!srv->queue.empty()) {
+                SJob* j = srv->queue.front();
+                if (!try_admit(srv, j)) break;
+                srv->queue.pop_front();
+                ++srv->running;
+                j->t_start = now_ms(srv);
+                admitted.push_back(j);
+            }
+        }
+        bool moved = !admitted.empty();
+        for (SJob* j : admitted) {
+            if (j->rq.kind == RID_JOB_LABEL) {
+                place_label_job(j->fj, j->region, j->lay, *rid_sys_dev(j->rq.sys), j->W, j->rq.n_blocks,
+                                j->rq.n_steps, j->rq.n_equil, j->rq.step0, j->v0.empty());
+                srv->labels.push_back(j);
+            } else {
+                const int rc = explore_start(srv, j);
+                if (rc != RID_OK) {
+                    cudaStreamSynchronize(srv->es[j->slot].st);
+                    if (j->gexec) cudaGraphExecDestroy(j->gexec);
+                    j->gexec = nullptr;
+                    release_job_memory(srv, j);
+                    finish_job(srv, j, rc);
+                }
+            }
+        }
+        moved |= label_tick_progress(srv);
+        if (!srv->tick_busy && !srv->labels.empty()) {
+            const int rc = label_tick_launch(srv);
+            if (rc != RID_OK) {
+                cudaStreamSynchronize(srv->lst);
+                for (SJob* j : srv->labels) {
+                    release_job_memory(srv, j);
+                    finish_job(srv, j, rc);
+                }
+                srv->labels.clear();
+            }
+            moved = true;
+        }
+        for (int k = 0; k < N_ESLOTS; ++k)
+            if (srv->es[k].job) moved |= explore_progress(srv, srv->es[k].job);
+        if (!moved) {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            srv->cv.wait_for(lk, std::chrono::microseconds(100));
+        }
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -228,31 +810,137 @@ extern "C" int rid_server_create(uint64_t budget, rid_server** out) {
     if (!out) return rid_fail(RID_ERR_ARG, "NULL out");
     *out = nullptr;
     if (budget < (1u << 20)) return rid_fail(RID_ERR_ARG, "hbm_budget_bytes=%llu below 1 MiB", (unsigned long long)budget);
-    rid_server* srv = new rid_server();
+    std::unique_ptr<rid_server> srv(new rid_server());
+    srv->t0 = std::chrono::steady_clock::now();
     cudaError_t e = cudaGetDevice(&srv->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&srv->n_sm, cudaDevAttrMultiProcessorCount, srv->device);
-    if (e != cudaSuccess) {
-        delete srv;
-        return rid_fail(RID_ERR_CUDA, "rid_server_create: %s", cudaGetErrorString(e));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&srv->lst, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&srv->lev);
+    if (e == cudaSuccess) e = cudaEventCreate(&srv->le0);
+    for (int k = 0; k < N_ESLOTS && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&srv->es[k].st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&srv->es[k].ev, cudaEventDisableTiming);
     }
-    const int rc = srv->pool.init((size_t)budget);
-    if (rc != RID_OK) {
-        delete srv;
-        return rc;
-    }
-    *out = srv;
+    if (e != cudaSuccess) return rid_fail(RID_ERR_CUDA, "rid_server_create: %s", cudaGetErrorString(e));
+    srv->pool.init((size_t)budget);
+    rid_server* p = srv.release();
+    p->worker = std::thread(worker_main, p);
+    *out = p;
     return RID_OK;
 }
 
 extern "C" int rid_server_destroy(rid_server* srv) {
     if (!srv) return RID_OK;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+    }
+    srv->cv.notify_all();
+    if (srv->worker.joinable()) srv->worker.join();
     cudaDeviceSynchronize();
     srv->pool.release();
     srv->pin_in.release();
     srv->pin_out.release();
     srv->pin_meta.release();
+    srv->lmeta_h.release();
+    srv->lio_h.release();
     if (srv->d_meta) cudaFree(srv->d_meta);
+    if (srv->lmeta_d) cudaFree(srv->lmeta_d);
+    for (int k = 0; k < N_ESLOTS; ++k) {
+        srv->es[k].pin.release();
+        if (srv->es[k].ev) cudaEventDestroy(srv->es[k].ev);
+        if (srv->es[k].st) cudaStreamDestroy(srv->es[k].st);
+    }
+    if (srv->lev) cudaEventDestroy(srv->lev);
+    if (srv->le0) cudaEventDestroy(srv->le0);
+    if (srv->lst) cudaStreamDestroy(srv->lst);
     delete srv;
+    return RID_OK;
+}
+
+extern "C" int rid_submit(rid_server* srv, const rid_request* req, uint64_t* job_id) {
+    if (!srv || !req || !job_id) return rid_fail(RID_ERR_ARG, "NULL argument");
+    const rid_request& q = *req;
+    if (q.kind != RID_JOB_LABEL && q.kind != RID_JOB_EXPLORE) return rid_fail(RID_ERR_ARG, "kind=%d is not a job kind", q.kind);
+    if (!q.sys || !q.x0) return rid_fail(RID_ERR_ARG, "NULL sys or x0");
+    if (q.n_walkers < 1) return rid_fail(RID_ERR_ARG, "n_walkers=%d must be >= 1", q.n_walkers);
+    if (q.n_steps < 1) return rid_fail(RID_ERR_ARG, "n_steps must be >= 1");
+    const SysDev* S = rid_sys_dev(q.sys);
+    std::unique_ptr<SJob> j(new SJob());
+    j->rq = q;
+    j->W = q.n_walkers;
+    j->N = S->N;
+    j->C = S->C;
+    j->of = S->output_freq > 0 ? S->output_freq : 1;
+    const size_t nb = (size_t)j->W * j->N, nc = (size_t)j->W * j->C;
+    if (q.kind == RID_JOB_LABEL) {
+        if (!q.s0 || !q.kappa || !q.mf_out || !q.se_out || !q.std_out) return rid_fail(RID_ERR_ARG, "label job: NULL argument");
+        STRY(check_label_args(q.sys, q.n_walkers, q.n_blocks, q.step0, q.n_steps, q.n_equil, 0, srv->device));
+    } else {
+        if (rid_sys_device(q.sys) != srv->device) return rid_fail(RID_ERR_STATE, "system lives on another device");
+        if (q.step0 + (uint64_t)q.n_steps > (1ull << 32)) return rid_fail(RID_ERR_ARG, "step0 + n_steps exceeds 2^32");
+        j->T = q.n_steps / j->of;
+    }
+    j->x0.assign(q.x0, q.x0 + 3 * nb);
+    if (q.v0) j->v0.assign(q.v0, q.v0 + 3 * nb);
+    if (q.kind == RID_JOB_LABEL) {
+        j->s0.assign(q.s0, q.s0 + nc);
+        j->kappa.assign(q.kappa, q.kappa + nc);
+        j->lay = job_layout(j->W, j->N, j->C, q.n_blocks);
+        j->in_off = j->lay.bytes;
+        j->in_bytes = label_io_in(*j);
+        j->out_off = j->in_off + j->in_bytes;
+        j->out_bytes = label_io_out(*j);
+        j->foot = j->out_off + j->out_bytes;
+    } else {
+        j->dbuf_bytes = explore_dbuf(*j);
+        j->foot = rid_sys_footprint(q.sys, j->W) + j->dbuf_bytes;
+    }
+    if (j->foot > srv->pool.budget())
+        return rid_fail(RID_ERR_OOM, "job needs %zu bytes, more than the server's budget of %zu", j->foot,
+                        srv->pool.budget());
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->stop) return rid_fail(RID_ERR_STATE, "server is shutting down");
+    j->id = srv->next_id++;
+    j->t_submit = now_ms(srv);
+    *job_id = j->id;
+    SJob* raw = j.get();
+    srv->jobs[j->id] = std::move(j);
+    srv->queue.push_back(raw);
+    srv->cv.notify_all();
+    return RID_OK;
+}
+
+extern "C" int rid_poll(rid_server* srv, uint64_t job_id, rid_job_info* info) {
+    if (!srv) return rid_fail(RID_ERR_ARG, "NULL server");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->jobs.find(job_id);
+    if (it == srv->jobs.end()) return rid_fail(RID_ERR_ARG, "unknown job id %llu", (unsigned long long)job_id);
+    SJob* j = it->second.get();
+    if (info) {
+        info->status = j->status;
+        info->kind = j->rq.kind;
+        info->t_submit_ms = j->t_submit;
+        info->t_start_ms = j->t_start;
+        info->t_end_ms = j->t_end;
+    }
+    const int st = j->status;
+    if (st == RID_NOT_READY) return RID_NOT_READY;
+    // rid_fail keeps a message for this thread only for the failing statuses
+    if (st != RID_OK) rid_fail(st, "job %llu finished with status %d", (unsigned long long)job_id, st);
+    srv->jobs.erase(it);
+    return st;
+}
+
+extern "C" int rid_server_load(rid_server* srv, int32_t* queued, int32_t* running, uint64_t* bytes_in_use) {
+    if (!srv) return rid_fail(RID_ERR_ARG, "NULL server");
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (queued) *queued = (int32_t)srv->queue.size();
+        if (running) *running = srv->running;
+    }
+    std::lock_guard<std::mutex> lk(srv->pool_mu);
+    if (bytes_in_use) *bytes_in_use = srv->pool.in_use();
     return RID_OK;
 }
 
@@ -266,12 +954,13 @@ extern "C" int rid_label_batch(rid_server* srv, const rid_label_job* jobs, int32
     if (n_jobs == 0) return RID_OK;
     STRY(check_server_device(srv));
     for (int k = 0; k < n_jobs; ++k) STRY(check_label_job(jobs[k], k, srv->device));
+    std::lock_guard<std::mutex> pool_lock(srv->pool_mu);
     cudaStream_t st = (cudaStream_t)stream;
     const bool host = mem == RID_MEM_HOST;
 
     // ---- device regions: one per job, plus the input / output staging
     std::vector<JobLayout> lay(n_jobs);
-    std::vector<size_t> off(n_jobs, SIZE_MAX);
+    std::vector<char*> off(n_jobs, nullptr);
     size_t in_bytes = 0, out_bytes = 0;
     std::vector<size_t> in_off(n_jobs), out_off(n_jobs);
     int maxN = 0;
@@ -291,30 +980,30 @@ extern "C" int rid_label_batch(rid_server* srv, const rid_label_job* jobs, int32
         n_items += j.n_runs;
     }
     if (n_items > (1 << 30)) return rid_fail(RID_ERR_ARG, "too many runs in one batch");
-    size_t stage_in = SIZE_MAX, stage_out = SIZE_MAX;
+    char* stage_in = nullptr;
+    char* stage_out = nullptr;
     auto release = [&]() {
         for (int k = 0; k < n_jobs; ++k)
-            if (off[k] != SIZE_MAX) srv->pool.free(off[k], lay[k].bytes);
-        if (stage_in != SIZE_MAX) srv->pool.free(stage_in, in_bytes);
-        if (stage_out != SIZE_MAX) srv->pool.free(stage_out, out_bytes);
+            if (off[k]) srv->pool.free(off[k], lay[k].bytes);
+        if (stage_in) srv->pool.free(stage_in, in_bytes);
+        if (stage_out) srv->pool.free(stage_out, out_bytes);
     };
     for (int k = 0; k < n_jobs; ++k) {
-        off[k] = srv->pool.alloc(lay[k].bytes);
-        if (off[k] == SIZE_MAX) {
+        off[k] = static_cast<char*>(srv->pool.alloc(lay[k].bytes));
+        if (!off[k]) {
             release();
             return rid_fail(RID_ERR_OOM, "batch does not fit the server's HBM budget (%zu of %zu bytes in use)",
-                            srv->pool.used(), srv->pool.capacity());
+                            srv->pool.in_use(), srv->pool.budget());
         }
     }
     if (host) {
-        stage_in = srv->pool.alloc(in_bytes);
-        stage_out = srv->pool.alloc(out_bytes);
-        if (stage_in == SIZE_MAX || stage_out == SIZE_MAX) {
+        stage_in = static_cast<char*>(srv->pool.alloc(in_bytes));
+        stage_out = static_cast<char*>(srv->pool.alloc(out_bytes));
+        if (!stage_in || !stage_out) {
             release();
             return rid_fail(RID_ERR_OOM, "batch staging does not fit the server's HBM budget");
         }
     }
-    char* pb = srv->pool.base();
 
     // ---- host-side tables
     std::vector<FusedJob> fj(n_jobs);
@@ -324,7 +1013,7 @@ extern "C" int rid_label_batch(rid_server* srv, const rid_label_job* jobs, int32
         const SysDev* S = rid_sys_dev(j.sys);
         const int R = j.n_runs, N = S->N, C = S->C;
         const size_t nb = (size_t)R * N, nc = (size_t)R * C;
-        char* b = pb + off[k];
+        char* b = off[k];
         const JobLayout& L = lay[k];
         FusedJob& J = fj[k];
         memset(&J, 0, sizeof(J));
@@ -352,7 +1041,7 @@ extern "C" int rid_label_batch(rid_server* srv, const rid_label_job* jobs, int32
         J.init = 1;
         J.mb = j.v0 ? 0 : 1;
         // inputs: caller arrays (device) or staging (host) -> pool
-        const char* src = host ? pb + stage_in + in_off[k] : nullptr;
+        const char* src = host ? stage_in + in_off[k] : nullptr;
         size_t so = 0;
         auto in = [&](const void* user, size_t bytes) -> const void* {
             if (!host) return user;
@@ -366,7 +1055,7 @@ extern "C" int rid_label_batch(rid_server* srv, const rid_label_job* jobs, int32
         din.push_back({in(j.kappa, 8 * nc), (void*)J.kappa, (long long)nc, 2});
         din.push_back({nullptr, b + L.sum, (long long)(L.zero_bytes / 4), 4});
         // outputs: pool -> caller arrays (device) or staging (host)
-        char* dst = host ? pb + stage_out + out_off[k] : nullptr;
+        char* dst = host ? stage_out + out_off[k] : nullptr;
         size_t doff = 0;
         auto outp = [&](void* user, size_t bytes) -> void* {
             if (!host) return user;
@@ -456,7 +1145,7 @@ extern "C" int rid_label_batch(rid_server* srv, const rid_label_job* jobs, int32
 
     int rc = [&]() -> int {
         SCK(cudaMemcpyAsync(dm, hm, o_cnt, cudaMemcpyHostToDevice, st));
-        if (host) SCK(cudaMemcpyAsync(pb + stage_in, srv->pin_in.p, in_bytes, cudaMemcpyHostToDevice, st));
+        if (host) SCK(cudaMemcpyAsync(stage_in, srv->pin_in.p, in_bytes, cudaMemcpyHostToDevice, st));
         FusedArgs A{};
         A.jobs = reinterpret_cast<const FusedJob*>(dm + o_jobs);
         A.items = reinterpret_cast<const FusedItem*>(dm + o_items);
@@ -521,7 +1210,7 @@ extern "C" int rid_label_batch(rid_server* srv, const rid_label_job* jobs, int32
         STRY(run(nt));
         rid_launch_copy_descs(reinterpret_cast<const CopyDesc*>(dm + o_dout), (int)(dout.size() + dflags.size()), st);
         SCK(cudaGetLastError());
-        if (host) SCK(cudaMemcpyAsync(srv->pin_out.p, pb + stage_out, out_bytes, cudaMemcpyDeviceToHost, st));
+        if (host) SCK(cudaMemcpyAsync(srv->pin_out.p, stage_out, out_bytes, cudaMemcpyDeviceToHost, st));
         else SCK(cudaMemcpyAsync(hm + o_flags, dm + o_flags, 4 * n_flag_words, cudaMemcpyDeviceToHost, st));
         SCK(cudaStreamSynchronize(st));
         return RID_OK;

@@ -26,7 +26,9 @@ EXPORTS = ("rid_version", "rid_status_string", "rid_last_error", "rid_create_sys
            "rid_set_ensemble", "rid_explore", "rid_label", "rid_eval_forces", "rid_pair_mask", "rid_philox",
            "rid_walkers_load", "rid_walkers_advance", "rid_walkers_read", "rid_profile_enable",
            "rid_profile_read", "rid_launch_count", "rid_ensemble_grad_noalloc", "rid_server_create",
-           "rid_server_destroy", "rid_label_batch")
+           "rid_server_destroy", "rid_label_batch", "rid_submit", "rid_poll", "rid_server_load")
+RID_NOT_READY = 6
+RID_JOB_LABEL, RID_JOB_EXPLORE = 1, 2
 
 
 class RidError(RuntimeError):
@@ -55,6 +57,19 @@ class LabelJob(C.Structure):
                 ("v0", C.c_void_p), ("s0", C.c_void_p), ("kappa", C.c_void_p), ("step0", C.c_uint64),
                 ("n_steps", C.c_int64), ("n_equil", C.c_int64), ("mf_out", C.c_void_p), ("se_out", C.c_void_p),
                 ("std_out", C.c_void_p), ("x_out", C.c_void_p), ("v_out", C.c_void_p)]
+
+
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_walkers", C.c_int32), ("sys", C.c_void_p), ("x0", C.c_void_p),
+                ("v0", C.c_void_p), ("step0", C.c_uint64), ("n_steps", C.c_int64), ("s0", C.c_void_p),
+                ("kappa", C.c_void_p), ("n_equil", C.c_int64), ("n_blocks", C.c_int32), ("mf_out", C.c_void_p),
+                ("se_out", C.c_void_p), ("std_out", C.c_void_p), ("cv_out", C.c_void_p), ("eps_out", C.c_void_p),
+                ("x_out", C.c_void_p), ("v_out", C.c_void_p)]
+
+
+class JobInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("kind", C.c_int32), ("t_submit_ms", C.c_double),
+                ("t_start_ms", C.c_double), ("t_end_ms", C.c_double)]
 
 
 _lib = None
@@ -91,6 +106,9 @@ def lib() -> C.CDLL:
     L.rid_server_create.argtypes = [u64, C.POINTER(vp)]
     L.rid_server_destroy.argtypes = [vp]
     L.rid_label_batch.argtypes = [vp, C.POINTER(LabelJob), i32, i32, C.POINTER(i32), i32, vp]
+    L.rid_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(u64)]
+    L.rid_poll.argtypes = [vp, u64, C.POINTER(JobInfo)]
+    L.rid_server_load.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(u64)]
     L.rid_launch_count.restype = i64
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype or C.c_int
@@ -345,6 +363,78 @@ class Server:
         if rc != RID_OK and not (rc == RID_ERR_NONFINITE and not raise_nonfinite):
             _check(rc)
         return [int(status[k]) for k in range(len(jobs))]
+
+    # request loop ------------------------------------------------------------
+    def _submit(self, rq, keep):
+        jid = C.c_uint64()
+        _check(lib().rid_submit(self.h, C.byref(rq), C.byref(jid)))
+        if not hasattr(self, "_live"):
+            self._live = {}
+        self._live[jid.value] = keep          # output arrays stay alive until the job is final
+        return jid.value
+
+    def submit_label(self, system, x0, s0, kappa, n_steps, n_equil, n_blocks, mf, se, std, v0=None, step0=0,
+                     x_out=None, v_out=None):
+        R = int(x0.shape[0])
+        N, Cn = system.N, system.C
+        a = _Args()
+        rq = Request(RID_JOB_LABEL, R, system.h.value, a.ptr(x0, np.float32, (R, N, 3)),
+                     a.ptr(v0, np.float32, (R, N, 3)), int(step0), int(n_steps), a.ptr(s0, np.float64, (R, Cn)),
+                     a.ptr(kappa, np.float64, (R, Cn)), int(n_equil), int(n_blocks),
+                     a.ptr(mf, np.float64, (R, Cn), True), a.ptr(se, np.float64, (R, Cn), True),
+                     a.ptr(std, np.float64, (R, Cn), True), None, None,
+                     a.ptr(x_out, np.float32, (R, N, 3), True), a.ptr(v_out, np.float32, (R, N, 3), True))
+        if a.mem != RID_MEM_HOST:
+            raise ValueError("requests take host arrays only")
+        return self._submit(rq, a.keep)
+
+    def submit_explore(self, system, x0, n_steps, v0=None, step0=0, cv_out=None, eps_out=None, x_out=None,
+                       v_out=None):
+        W = int(x0.shape[0])
+        N, Cn = system.N, system.C
+        T = int(n_steps) // system.sp.output_freq
+        a = _Args()
+        rq = Request(RID_JOB_EXPLORE, W, system.h.value, a.ptr(x0, np.float32, (W, N, 3)),
+                     a.ptr(v0, np.float32, (W, N, 3)), int(step0), int(n_steps), None, None, 0, 0, None, None, None,
+                     a.ptr(cv_out, np.float32, (W, T, Cn), True), a.ptr(eps_out, np.float32, (W, T), True),
+                     a.ptr(x_out, np.float32, (W, N, 3), True), a.ptr(v_out, np.float32, (W, N, 3), True))
+        if a.mem != RID_MEM_HOST:
+            raise ValueError("requests take host arrays only")
+        return self._submit(rq, a.keep)
+
+    def poll(self, job_id):
+        """(status, info dict); status RID_NOT_READY while queued or running."""
+        info = JobInfo()
+        rc = lib().rid_poll(self.h, C.c_uint64(job_id), C.byref(info))
+        if rc == RID_ERR_ARG and info.kind == 0:
+            _check(rc)
+        d = dict(status=int(info.status), kind=int(info.kind), t_submit_ms=info.t_submit_ms,
+                 t_start_ms=info.t_start_ms, t_end_ms=info.t_end_ms)
+        if rc != RID_NOT_READY:
+            getattr(self, "_live", {}).pop(job_id, None)
+        return int(rc), d
+
+    def wait(self, job_ids, timeout=600.0, sleep=0.0005):
+        """Poll until every job is final; returns {id: (status, info)}."""
+        import time
+        left, out = set(job_ids), {}
+        t_end = time.time() + timeout
+        while left:
+            for jid in list(left):
+                st, info = self.poll(jid)
+                if st != RID_NOT_READY:
+                    out[jid] = (st, info)
+                    left.discard(jid)
+            if left:
+                if time.time() > t_end:
+                    raise TimeoutError(f"{len(left)} jobs not final after {timeout} s")
+                time.sleep(sleep)
+        return out
+
+    def load(self):
+        q, r, b = C.c_int32(), C.c_int32(), C.c_uint64()
+        _check(lib().rid_server_load(self.h, C.byref(q), C.byref(r), C.byref(b)))
+        return int(q.value), int(r.value), int(b.value)
 
 
 def ensemble_grad_noalloc(s, weights, n_models, n_layers, width, grad_out, value_out=None, resnet=False,
