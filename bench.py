@@ -11,6 +11,12 @@ with CUDA events on the stream the kernels run on.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
                   [--impl ours|reference]
 
+Two more legs on rank 0 (N = 1) go into the same JSON line: "batching"
+(512 uneven restrained labeling jobs in one persistent launch against the
+plain per-job path) and "serving" (a Poisson stream of mixed labeling /
+exploration requests through rid_submit / rid_poll: throughput and p50 / p99
+latency, against the plain FP32 per-job path on the first requests).
+
 --impl reference times the FP64 CPU oracle on the host cores (a bounded
 sample of the same workload per step).  Under torchrun every rank runs its
 own 1024 walkers (weak scaling, no collective on the data path).
@@ -161,6 +167,189 @@ def cpu_baseline(sp, x0, ens, walkers, steps):
                       f"force evaluation per walker), {dt:.1f} s"}
 
 
+def chain_pools(lengths, walkers, seed):
+    """Starting chains grown once per chain length: {N: [walkers][N][3]}."""
+    pools = {}
+    for N in sorted(set(int(n) for n in lengths)):
+        pools[N] = I.make_chains(walkers, I.make_system(N, 1, seed + N), seed + N)
+    return pools
+
+
+def targets_near_start(rid, system, x0, rng, spread=0.3):
+    """Restraint centres near the CVs of the starting configuration (labeling
+    restrains selected configurations at their own CV values), perturbed."""
+    s = np.zeros((x0.shape[0], system.C), np.float32)
+    system.eval_forces(x0, rid.RID_BIAS_NONE, s_out=s)
+    return s.astype(np.float64) + rng.uniform(-spread, spread, size=s.shape)
+
+
+def run_batching(rid, n_jobs, n_steps, plain_jobs, seed=3):
+    """Uneven restrained labeling jobs (one run each) in one persistent launch
+    (rid_label_batch, CTA size autotuned), against the plain FP32 per-job path
+    (rid_label, one job after another) on an evenly spaced sample of the jobs."""
+    specs = I.label_batch_jobs(n_jobs, seed, n_steps=n_steps)
+    rng = np.random.default_rng(seed)
+    pools = chain_pools([j["n_beads"] for j in specs], max(1, max(
+        sum(1 for j in specs if j["n_beads"] == n) for n in set(j["n_beads"] for j in specs))), seed)
+    used = {}
+    jobs = []
+    for j in specs:
+        sp = I.make_system(j["n_beads"], j["n_cv"], j["seed"])
+        system = rid.System(sp)
+        k = used.get(j["n_beads"], 0)
+        used[j["n_beads"]] = k + 1
+        x0 = np.ascontiguousarray(pools[j["n_beads"]][k:k + 1])
+        s0 = targets_near_start(rid, system, x0, rng)
+        C = j["n_cv"]
+        jobs.append(dict(system=system, x0=x0, s0=s0, kappa=np.ascontiguousarray(j["kappa"][None, :]),
+                         n_steps=j["n_steps"], n_equil=j["n_steps"] // 10, n_blocks=20,
+                         mf=np.zeros((1, C)), se=np.zeros((1, C)), std=np.zeros((1, C))))
+    wsteps = sum(j["n_steps"] for j in jobs)
+    srv = rid.Server(8 << 30)
+    srv.label_batch(jobs, threads=0, raise_nonfinite=False)              # autotune + warm
+    t0 = time.perf_counter()
+    st = srv.label_batch(jobs, threads=0, raise_nonfinite=False)
+    dt = time.perf_counter() - t0
+    srv.close()
+    order = sorted(range(len(jobs)), key=lambda k: jobs[k]["system"].N)
+    sample = [order[int(i)] for i in np.linspace(0, len(order) - 1, min(plain_jobs, len(order)))]
+    t_plain, ws_plain = 0.0, 0
+    for k in sample:
+        j = jobs[k]
+        C = j["system"].C
+        mf, se, sd = np.zeros((1, C)), np.zeros((1, C)), np.zeros((1, C))
+        t1 = time.perf_counter()
+        try:
+            j["system"].label(j["x0"], j["s0"], j["kappa"], j["n_steps"], j["n_equil"], j["n_blocks"], mf, se, sd)
+        except rid.RidError:
+            pass
+        t_plain += time.perf_counter() - t1
+        ws_plain += j["n_steps"]
+    for j in jobs:
+        j["system"].close()
+    Ns = [j["system"].N for j in jobs]
+    return {"workload": f"{n_jobs} restrained labeling jobs, 1 run x {n_steps} steps each, chain length "
+                        f"log-uniform {min(Ns)}-{max(Ns)} beads, 4-40 torsion CVs, kappa 50-500, "
+                        f"restraint centres near the starting CVs",
+            "value": wsteps / dt, "unit": "walker-steps/s", "wall_s": dt, "kernel_launches": 1,
+            "timed": "one rid_label_batch call from host arrays (uploads, the persistent kernel, downloads); "
+                     "a first call picked the CTA size",
+            "nonfinite_jobs": int(sum(1 for x in st if x != rid.RID_OK)),
+            "plain_per_job": {"value": ws_plain / t_plain, "unit": "walker-steps/s", "jobs": len(sample),
+                              "path": "rid_label per job (per-step kernels, FP32), jobs run one after another"},
+            "speedup_vs_plain": (wsteps / dt) / (ws_plain / t_plain)}
+
+
+def run_serving(rid, n_req, rate, plain_req, seed=5):
+    """Poisson stream of mixed labeling / exploration requests through the
+    request loop (BF16 ensembles), and the first plain_req requests of the
+    same stream through the plain FP32 per-job path in arrival order."""
+    reqs = I.serving_requests(n_req, rate, seed)
+    pools = chain_pools([r["n_beads"] for r in reqs], 12, seed)
+    rng = np.random.default_rng(seed)
+
+    def build_req(r, prec):
+        sp = I.make_system(r["n_beads"], r["n_cv"], r["seed"], output_freq=10)
+        system = rid.System(sp)
+        W, N, C = r["walkers"], r["n_beads"], r["n_cv"]
+        d = dict(r, system=system)
+        if r["kind"] == "label":
+            k = r["seed"] % pools[N].shape[0]
+            d["x0"] = np.ascontiguousarray(pools[N][k:k + 1])
+            d["s0"] = targets_near_start(rid, system, d["x0"], rng)
+            d["kappa_a"] = np.ascontiguousarray(r["kappa"][None, :])
+            d["mf"], d["se"], d["std"] = (np.zeros((1, C)) for _ in range(3))
+        else:
+            ens = I.make_ensemble(r["n_models"], 2 * C, r["n_layers"], r["width"], r["seed"])
+            system.set_ensemble(ens, precision=prec)
+            d["x0"] = np.ascontiguousarray(pools[N][:W])
+            T = r["n_steps"] // 10
+            d["cv"], d["eps"] = np.zeros((W, T, C), np.float32), np.zeros((W, T), np.float32)
+        return d
+
+    served = [build_req(r, rid.RID_PREC_BF16) for r in reqs]
+    srv = rid.Server(16 << 30)
+    out, pending = {}, {}
+    t0 = time.perf_counter()
+    k = 0
+    while k < len(served) or pending:
+        now = time.perf_counter() - t0
+        while k < len(served) and served[k]["t"] <= now:
+            d = served[k]
+            if d["kind"] == "label":
+                jid = srv.submit_label(d["system"], d["x0"], d["s0"], d["kappa_a"], d["n_steps"], d["n_steps"] // 10,
+                                       20, d["mf"], d["se"], d["std"])
+            else:
+                jid = srv.submit_explore(d["system"], d["x0"], d["n_steps"], cv_out=d["cv"], eps_out=d["eps"])
+            pending[jid] = k
+            k += 1
+        for jid in list(pending):
+            st, info = srv.poll(jid)
+            if st != rid.RID_NOT_READY:
+                out[pending.pop(jid)] = (st, info)
+        time.sleep(0.0002)
+    srv.close()
+    lat = {"label": [], "explore": []}
+    wsteps = 0
+    t_first = min(i["t_submit_ms"] for _, i in out.values())
+    t_last = max(i["t_end_ms"] for _, i in out.values())
+    for idx, (st, info) in out.items():
+        r = served[idx]
+        lat[r["kind"]].append(info["t_end_ms"] - info["t_submit_ms"])
+        wsteps += r["walkers"] * r["n_steps"]
+    for d in served:
+        d["system"].close()
+
+    # plain FP32 per-job path on the first plain_req requests, in arrival order
+    plain = [build_req(r, rid.RID_PREC_FP32) for r in reqs[:plain_req]]
+    lat_p = {"label": [], "explore": []}
+    t0 = time.perf_counter()
+    busy_until = 0.0
+    for d in plain:
+        now = time.perf_counter() - t0
+        if now < d["t"]:
+            time.sleep(d["t"] - now)
+        try:
+            if d["kind"] == "label":
+                d["system"].label(d["x0"], d["s0"], d["kappa_a"], d["n_steps"], d["n_steps"] // 10, 20, d["mf"],
+                                  d["se"], d["std"])
+            else:
+                d["system"].explore(d["x0"], d["n_steps"], cv_out=d["cv"], eps_out=d["eps"])
+        except rid.RidError:
+            pass
+        lat_p[d["kind"]].append(1e3 * (time.perf_counter() - t0 - d["t"]))
+    for d in plain:
+        d["system"].close()
+    served_first = {"label": [], "explore": []}
+    for idx in range(min(plain_req, len(served))):
+        st, info = out[idx]
+        served_first[served[idx]["kind"]].append(info["t_end_ms"] - info["t_submit_ms"])
+
+    def pct(v, q):
+        return float(np.percentile(v, q)) if v else None
+
+    return {"workload": f"{n_req} requests, Poisson arrivals at {rate:g}/s, 70% labeling (1 run) / 30% exploration "
+                        f"(12 walkers), chains log-uniform 20-2000 beads, 2-64 torsion CVs, 500-5000 steps, "
+                        f"ensembles 4 x (64-512 wide, 4 layers)",
+            "throughput": wsteps / ((t_last - t_first) / 1e3), "unit": "walker-steps/s",
+            "requests_per_s": len(out) / ((t_last - t_first) / 1e3),
+            "label_latency_ms": {"p50": pct(lat["label"], 50), "p99": pct(lat["label"], 99), "n": len(lat["label"])},
+            "explore_latency_ms": {"p50": pct(lat["explore"], 50), "p99": pct(lat["explore"], 99),
+                                   "n": len(lat["explore"])},
+            "nonfinite": int(sum(1 for st, _ in out.values() if st == rid.RID_ERR_NONFINITE)),
+            "failed": int(sum(1 for st, _ in out.values() if st not in (rid.RID_OK, rid.RID_ERR_NONFINITE))),
+            "mlp_precision": "bf16",
+            "plain_per_job": {"requests": len(plain), "path": "rid_label / rid_explore per request in arrival "
+                                                              "order, FP32 ensembles, one at a time",
+                              "label_latency_ms": {"p50": pct(lat_p["label"], 50), "p99": pct(lat_p["label"], 99)},
+                              "explore_latency_ms": {"p50": pct(lat_p["explore"], 50),
+                                                     "p99": pct(lat_p["explore"], 99)},
+                              "served_same_requests_label_latency_ms": {"p50": pct(served_first["label"], 50),
+                                                                        "p99": pct(served_first["label"], 99)},
+                              "served_same_requests_explore_latency_ms": {"p50": pct(served_first["explore"], 50),
+                                                                          "p99": pct(served_first["explore"], 99)}}}
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -213,6 +402,14 @@ def main():
     ap.add_argument("--cpu-walkers", type=int, default=1024)
     ap.add_argument("--cpu-steps", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-jobs", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=2000)
+    ap.add_argument("--batch-plain-jobs", type=int, default=24)
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-plain-requests", type=int, default=24)
+    ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -365,6 +562,10 @@ def main():
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sp, x0, ens, args.cpu_walkers, args.cpu_steps)
+    if rank == 0 and world == 1 and not args.no_batching:
+        out["batching"] = run_batching(rid, args.batch_jobs, args.batch_steps, args.batch_plain_jobs)
+    if rank == 0 and world == 1 and not args.no_serving:
+        out["serving"] = run_serving(rid, args.serve_requests, args.serve_rate, args.serve_plain_requests)
     if rank == 0:
         print(json.dumps(out))
     system.close()

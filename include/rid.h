@@ -297,7 +297,9 @@ RID_API int rid_label_batch(rid_server* srv, const rid_label_job* jobs, int32_t 
  * Request loop (continuous batching).  rid_submit queues a labeling or an
  * exploration job and returns at once; a worker thread of the server admits
  * queued jobs in arrival order as soon as their device memory fits the
- * budget, and runs every admitted job concurrently:
+ * budget (a job that does not fit holds back the jobs behind it; an
+ * exploration job waiting for one of the 16 exploration streams or for its
+ * system does not), and runs every admitted job concurrently:
  *   - label jobs advance together, in ticks of the persistent kernel
  *     (rid_label_batch's kernel); each tick gives every active job a number
  *     of steps sized to its chain length, and jobs that arrive meanwhile join

@@ -405,9 +405,8 @@ void place_label_job(FusedJob& J, char* b, const JobLayout& L, const SysDev& S, 
     J.mb = mb ? 1 : 0;
 }
 
-// Descriptors that move a label job's inputs from `src` (staging laid out as
-// x0 | v0? | s0 | kappa, or caller device arrays) into its arrays and zero its
-// accumulators.
+// Descriptors that move a label job's inputs (from staging or from caller
+// device arrays) into its arrays and zero its accumulators.
 void label_in_descs(std::vector<CopyDesc>& d, const FusedJob& J, const JobLayout& L, char* region, const void* x0,
                     const void* v0, const void* s0, const void* kappa) {
     const long long nb = (long long)J.R * J.S.N, nc = (long long)J.R * J.S.C;
@@ -448,33 +447,33 @@ void finish_job(rid_server* srv, SJob* j, int status) {
     srv->cv.notify_all();
 }
 
-// Admission of the job at the head of the queue: device memory within the
-// budget (and for exploration a free stream slot and an idle system).
-bool try_admit(rid_server* srv, SJob* j) {
+// Admission of a queued job: 0 admitted, 1 no device memory within the budget
+// now, 2 waiting for a stream slot or for its system to become idle.
+int try_admit(rid_server* srv, SJob* j) {
     std::lock_guard<std::mutex> lk(srv->pool_mu);
     if (j->rq.kind == RID_JOB_LABEL) {
         void* p = srv->pool.alloc(j->foot);
-        if (!p) return false;
+        if (!p) return 1;
         j->region = static_cast<char*>(p);
-        return true;
+        return 0;
     }
     int slot = -1;
     for (int k = 0; k < N_ESLOTS; ++k) {
-        if (srv->es[k].job && srv->es[k].job->rq.sys == j->rq.sys) return false;   // system busy
+        if (srv->es[k].job && srv->es[k].job->rq.sys == j->rq.sys) return 2;   // system busy
         if (!srv->es[k].job && slot < 0) slot = k;
     }
-    if (slot < 0) return false;
+    if (slot < 0) return 2;
     const size_t sys_bytes = j->foot - j->dbuf_bytes;
-    if (!srv->pool.reserve(sys_bytes)) return false;
+    if (!srv->pool.reserve(sys_bytes)) return 1;
     void* p = srv->pool.alloc(j->dbuf_bytes);
     if (!p) {
         srv->pool.unreserve(sys_bytes);
-        return false;
+        return 1;
     }
     j->dbuf = static_cast<char*>(p);
     j->slot = slot;
     srv->es[slot].job = j;
-    return true;
+    return 0;
 }
 
 void release_job_memory(rid_server* srv, SJob* j) {
@@ -609,12 +608,12 @@ int label_tick_launch(rid_server* srv) {
         smem = std::max(smem, rid_label_fused_smem(j->N, j->C, 0));
         for (int r = 0; r < j->W; ++r) items.push_back({(int)k, r});
         if (!j->staged) {
+            // staging order s0 | kappa | x0 | v0: the doubles first, so every array stays aligned
             char* src = j->region + j->in_off;
-            const size_t nb = (size_t)j->W * j->N;
-            const char* x0 = src;
-            const char* v0 = j->v0.empty() ? nullptr : src + 12 * nb;
-            const char* s0 = src + 12 * nb * (j->v0.empty() ? 1 : 2);
-            label_in_descs(din, J, j->lay, j->region, x0, v0, s0, s0 + 8 * (size_t)j->W * j->C);
+            const size_t nb = (size_t)j->W * j->N, nc = (size_t)j->W * j->C;
+            const char* x0 = src + 16 * nc;
+            const char* v0 = j->v0.empty() ? nullptr : x0 + 12 * nb;
+            label_in_descs(din, J, j->lay, j->region, x0, v0, src, src + 8 * nc);
             in_h += j->in_bytes;
         }
         if (J.t1 == j->rq.n_steps) {
@@ -648,15 +647,13 @@ int label_tick_launch(rid_server* srv) {
         char* p = srv->lio_h.c() + ho;
         const size_t nb = (size_t)j->W * j->N, nc = (size_t)j->W * j->C;
         size_t o = 0;
-        memcpy(p + o, j->x0.data(), 12 * nb);
-        o += 12 * nb;
-        if (!j->v0.empty()) {
-            memcpy(p + o, j->v0.data(), 12 * nb);
-            o += 12 * nb;
-        }
         memcpy(p + o, j->s0.data(), 8 * nc);
         o += 8 * nc;
         memcpy(p + o, j->kappa.data(), 8 * nc);
+        o += 8 * nc;
+        memcpy(p + o, j->x0.data(), 12 * nb);
+        o += 12 * nb;
+        if (!j->v0.empty()) memcpy(p + o, j->v0.data(), 12 * nb);
         SCK(cudaMemcpyAsync(j->region + j->in_off, p, j->in_bytes, cudaMemcpyHostToDevice, st));
         ho += j->in_bytes;
         j->staged = true;
@@ -755,10 +752,17 @@ void worker_main(rid_server* srv) {
                 if (!srv->queue.empty() || busy) break;
                 srv->cv.wait(lk);
             }
-            while (!srv->queue.empty()) {
-                SJob* j = srv->queue.front();
-                if (!try_admit(srv, j)) break;
-                srv->queue.pop_front();
+            // arrival order; a job short of memory stops admission (so large jobs
+            // are not starved), one waiting for a slot or its system is passed over
+            for (auto it = srv->queue.begin(); it != srv->queue.end();) {
+                SJob* j = *it;
+                const int a = try_admit(srv, j);
+                if (a == 1) break;
+                if (a == 2) {
+                    ++it;
+                    continue;
+                }
+                it = srv->queue.erase(it);
                 ++srv->running;
                 j->t_start = now_ms(srv);
                 admitted.push_back(j);
@@ -1049,10 +1053,11 @@ extern "C" int rid_label_batch(rid_server* srv, const rid_label_job* jobs, int32
             so += bytes;
             return at;
         };
-        din.push_back({in(j.x0, 12 * nb), J.x, (long long)nb, 0});
-        if (j.v0) din.push_back({in(j.v0, 12 * nb), J.v, (long long)nb, 0});
+        // staging order: the doubles first, so every array stays aligned
         din.push_back({in(j.s0, 8 * nc), (void*)J.s0, (long long)nc, 2});
         din.push_back({in(j.kappa, 8 * nc), (void*)J.kappa, (long long)nc, 2});
+        din.push_back({in(j.x0, 12 * nb), J.x, (long long)nb, 0});
+        if (j.v0) din.push_back({in(j.v0, 12 * nb), J.v, (long long)nb, 0});
         din.push_back({nullptr, b + L.sum, (long long)(L.zero_bytes / 4), 4});
         // outputs: pool -> caller arrays (device) or staging (host)
         char* dst = host ? stage_out + out_off[k] : nullptr;
@@ -1131,15 +1136,13 @@ extern "C" int rid_label_batch(rid_server* srv, const rid_label_job* jobs, int32
             const SysDev* S = rid_sys_dev(j.sys);
             const size_t nb = (size_t)j.n_runs * S->N, nc = (size_t)j.n_runs * S->C;
             char* p = srv->pin_in.c() + in_off[k];
-            memcpy(p, j.x0, 12 * nb);
-            p += 12 * nb;
-            if (j.v0) {
-                memcpy(p, j.v0, 12 * nb);
-                p += 12 * nb;
-            }
             memcpy(p, j.s0, 8 * nc);
             p += 8 * nc;
             memcpy(p, j.kappa, 8 * nc);
+            p += 8 * nc;
+            memcpy(p, j.x0, 12 * nb);
+            p += 12 * nb;
+            if (j.v0) memcpy(p, j.v0, 12 * nb);
         }
     }
 

@@ -33,10 +33,10 @@ import numpy as np
 __all__ = [
     "SystemParams", "EnsembleParams", "make_system", "make_chains",
     "make_ensemble", "make_label_targets", "ensemble_param_count",
-    "WORKLOADS", "workload",
+    "WORKLOADS", "workload", "chain_length_buckets", "label_batch_jobs", "serving_requests",
 ]
 
-_TAG_SYSTEM, _TAG_CHAIN, _TAG_ENS, _TAG_LABEL = 11, 23, 37, 41
+_TAG_SYSTEM, _TAG_CHAIN, _TAG_ENS, _TAG_LABEL, _TAG_MIX = 11, 23, 37, 41, 53
 
 
 def _rng(seed: int, tag: int) -> np.random.Generator:
@@ -206,3 +206,62 @@ WORKLOADS = {
 
 def workload(name: str) -> dict:
     return dict(WORKLOADS[name])
+
+
+# --------------------------------------------------------------------------
+# Job mixes for batched labeling and for the request stream.  Chain lengths
+# are drawn log-uniformly and snapped to a fixed set of bucket lengths, so that
+# starting chains can be grown once per bucket for many jobs.
+
+def chain_length_buckets(lo: int, hi: int, n: int = 24) -> np.ndarray:
+    return np.unique(np.round(np.geomspace(lo, hi, n)).astype(int))
+
+
+def _snap(x: np.ndarray, buckets: np.ndarray) -> np.ndarray:
+    lx, lb = np.log(x), np.log(buckets.astype(np.float64))
+    return buckets[np.abs(lx[:, None] - lb[None, :]).argmin(axis=1)]
+
+
+def label_batch_jobs(n_jobs: int, seed: int, n_lo: int = 50, n_hi: int = 500, cv_lo: int = 4, cv_hi: int = 40,
+                     kappa_lo: float = 50.0, kappa_hi: float = 500.0, width_lo: int = 128, width_hi: int = 512,
+                     n_steps: int = 2000) -> list:
+    """Uneven restrained labeling jobs, one run each: chain length log-uniform
+    in [n_lo, n_hi] (snapped to buckets), CV count uniform in [cv_lo, cv_hi],
+    per-CV kappa uniform in [kappa_lo, kappa_hi], an ensemble width uniform in
+    [width_lo, width_hi] (multiples of 32; labeling runs do not use it)."""
+    g = _rng(seed, _TAG_MIX)
+    b = chain_length_buckets(n_lo, n_hi)
+    N = _snap(np.exp(g.uniform(math.log(n_lo), math.log(n_hi), size=n_jobs)), b)
+    out = []
+    for k in range(n_jobs):
+        C = int(min(g.integers(cv_lo, cv_hi + 1), N[k] - 3))
+        out.append(dict(n_beads=int(N[k]), n_cv=C, seed=int(g.integers(1, 2 ** 31)),
+                        kappa=g.uniform(kappa_lo, kappa_hi, size=C),
+                        width=int(32 * g.integers(width_lo // 32, width_hi // 32 + 1)), n_steps=n_steps))
+    return out
+
+
+def serving_requests(n_req: int, rate: float, seed: int, p_label: float = 0.7, n_lo: int = 20, n_hi: int = 2000,
+                     cv_lo: int = 2, cv_hi: int = 64, steps_lo: int = 500, steps_hi: int = 5000,
+                     width_lo: int = 64, width_hi: int = 512, explore_walkers: int = 12,
+                     kappa_lo: float = 50.0, kappa_hi: float = 500.0) -> list:
+    """A Poisson stream of mixed requests: arrival times with exponential gaps
+    of mean 1/rate; a labeling request (one run) with probability p_label,
+    else an exploration request with `explore_walkers` walkers; chain length
+    log-uniform in [n_lo, n_hi] (snapped to buckets), CV count uniform in
+    [cv_lo, cv_hi], step count uniform in [steps_lo, steps_hi], ensemble of
+    4 members of width uniform in [width_lo, width_hi] (multiples of 32) with
+    4 hidden layers."""
+    g = _rng(seed, _TAG_MIX + 1)
+    t = np.cumsum(g.exponential(1.0 / rate, size=n_req))
+    b = chain_length_buckets(n_lo, n_hi)
+    N = _snap(np.exp(g.uniform(math.log(n_lo), math.log(n_hi), size=n_req)), b)
+    out = []
+    for k in range(n_req):
+        label = bool(g.uniform() < p_label)
+        C = int(min(g.integers(cv_lo, cv_hi + 1), N[k] - 3))
+        out.append(dict(t=float(t[k]), kind="label" if label else "explore", n_beads=int(N[k]), n_cv=C,
+                        walkers=1 if label else explore_walkers, n_steps=int(g.integers(steps_lo, steps_hi + 1)),
+                        width=int(32 * g.integers(width_lo // 32, width_hi // 32 + 1)), n_layers=4, n_models=4,
+                        kappa=g.uniform(kappa_lo, kappa_hi, size=C), seed=int(g.integers(1, 2 ** 31))))
+    return out

@@ -50,7 +50,8 @@ def uneven_jobs(R):
             make_job(R, 61, 9, 2, 90, 2, mb=True, step0=1000),
             make_job(R, 200, 20, 1, 60, 3, blocks=4),
             make_job(R, 130, 40, 2, 75, 4, n_equil=0),
-            make_job(R, 257, 12, 1, 40, 5, blocks=2)]
+            make_job(R, 257, 12, 1, 40, 5, blocks=2),
+            make_job(R, 51, 7, 1, 60, 9, mb=True)]       # odd bead count, no v0: staging offsets not multiples of 8
 
 
 @pytest.mark.parametrize("threads", [128, 256, 512, 0])

@@ -94,6 +94,7 @@ def mixed_specs(R):
         Spec(R, "label", 61, 9, 2, 900, 5),
         Spec(R, "explore", 22, 2, 16, 333, 6, prec=R.RID_PREC_FP32),  # graph chunks + a remainder chunk
         Spec(R, "label", 300, 12, 1, 120, 7),
+        Spec(R, "label", 51, 7, 1, 100, 8),                            # odd bead count, no v0
     ]
 
 
