@@ -11,7 +11,9 @@ with CUDA events on the stream the kernels run on.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
                   [--impl ours|reference]
 
-Two more legs on rank 0 (N = 1) go into the same JSON line: "batching"
+Three more legs on rank 0 (N = 1) go into the same JSON line: "precision"
+(the 8192-walker precision sweep: FP32 / BF16 throughput, BF16 deviation,
+NVE drift), "batching"
 (512 uneven restrained labeling jobs in one persistent launch against the
 plain per-job path) and "serving" (a Poisson stream of mixed labeling /
 exploration requests through rid_submit / rid_poll: throughput and p50 / p99
@@ -350,6 +352,56 @@ def run_serving(rid, n_req, rate, plain_req, seed=5):
                                                                           "p99": pct(served_first["explore"], 99)}}}
 
 
+def run_precision(rid, torch, steps=10, nve_walkers=64, nve_steps=10000, seed=4):
+    """Precision sweep: 8192 walkers of a 100-bead chain, 32 torsion CVs,
+    8 x MLP 64 -> 512 x 4 -> 1.  Per ensemble precision: throughput of full
+    steps, the CV force's deviation from the FP32 path on the same positions,
+    and the NVE (gamma = 0, sigma = 1) energy drift over nve_steps steps of
+    nve_walkers walkers."""
+    wl = I.workload("chain_n100_w8192")
+    sp, x0, ens = make_inputs(wl, seed)
+    W = wl["n_walkers"]
+    ens.trust_lo, ens.trust_hi = 1e9, 2e9
+    res = {"workload": f"{W} walkers, {wl['n_beads']}-bead chain, {wl['n_cv']} torsion CVs, {wl['n_models']} x MLP "
+                       f"{2 * wl['n_cv']}-{wl['width']}x{wl['n_layers']}-1; state and MLP scratch exceed L2"}
+    xd = torch.from_numpy(x0).cuda()
+    stream = torch.cuda.current_stream()
+    grads = {}
+    for name, prec in (("fp32", rid.RID_PREC_FP32), ("bf16", rid.RID_PREC_BF16)):
+        with rid.System(sp) as system:
+            system.set_ensemble(ens, precision=prec)
+            g = torch.zeros((wl["n_models"], W, wl["n_cv"]), dtype=torch.float32, device="cuda")
+            system.eval_forces(xd, rid.RID_BIAS_ENSEMBLE, grad_out=g, stream=stream)
+            grads[name] = g.mean(dim=0).double()
+            system.walkers_load(xd, stream=stream)
+            system.walkers_advance(3, stream=stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            system.walkers_advance(steps, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            system.walkers_read()
+        # NVE drift: gamma = 0, bias on with sigma = 1 (a conservative force)
+        spn = I.make_system(wl["n_beads"], wl["n_cv"], seed, output_freq=nve_steps // 100, gamma=0.0)
+        with rid.System(spn) as system:
+            system.set_ensemble(ens, precision=prec)
+            T = nve_steps // spn.output_freq
+            en = np.zeros((nve_walkers, T, 3))
+            v0 = np.zeros((nve_walkers, wl["n_beads"], 3), np.float32)
+            system.explore(x0[:nve_walkers], nve_steps, v0=v0, energy_out=en)
+            e = en.sum(axis=2)
+            drift = np.abs(e - e[:, :1]).max(axis=1) / (3 * wl["n_beads"] * spn.kT)
+        res[name] = {"value": W * steps / (ms / 1e3), "unit": "walker-steps/s", "ms_per_step": ms / steps,
+                     "nve_drift_max_over_3NkT": float(drift.max()), "nve_drift_mean_over_3NkT": float(drift.mean()),
+                     "nve": f"{nve_walkers} walkers x {nve_steps} steps, dt = {spn.dt}, energy sampled every "
+                            f"{spn.output_freq} steps"}
+    d = (grads["bf16"] - grads["fp32"]).norm(dim=1) / grads["fp32"].norm(dim=1).clamp_min(1e-30)
+    res["bf16"]["mean_force_rel_dev_from_fp32"] = {"median": float(d.median()), "max": float(d.max())}
+    return res
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -410,6 +462,7 @@ def main():
     ap.add_argument("--serve-plain-requests", type=int, default=24)
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -564,6 +617,8 @@ def main():
         out["cpu_baseline"] = cpu_baseline(sp, x0, ens, args.cpu_walkers, args.cpu_steps)
     if rank == 0 and world == 1 and not args.no_batching:
         out["batching"] = run_batching(rid, args.batch_jobs, args.batch_steps, args.batch_plain_jobs)
+    if rank == 0 and world == 1 and not args.no_precision:
+        out["precision"] = run_precision(rid, torch)
     if rank == 0 and world == 1 and not args.no_serving:
         out["serving"] = run_serving(rid, args.serve_requests, args.serve_rate, args.serve_plain_requests)
     if rank == 0:
