@@ -12,8 +12,8 @@ with CUDA events on the stream the kernels run on.
                   [--impl ours|reference]
 
 Three more legs on rank 0 (N = 1) go into the same JSON line: "precision"
-(the 8192-walker precision sweep: FP32 / BF16 throughput, BF16 deviation,
-NVE drift), "batching"
+(the 8192-walker precision sweep: FP32 / BF16 / FP8 throughput, deviation
+from FP32, NVE drift), "batching"
 (512 uneven restrained labeling jobs in one persistent launch against the
 plain per-job path) and "serving" (a Poisson stream of mixed labeling /
 exploration requests through rid_submit / rid_poll: throughput and p50 / p99
@@ -367,7 +367,7 @@ def run_precision(rid, torch, steps=10, nve_walkers=64, nve_steps=10000, seed=4)
     xd = torch.from_numpy(x0).cuda()
     stream = torch.cuda.current_stream()
     grads = {}
-    for name, prec in (("fp32", rid.RID_PREC_FP32), ("bf16", rid.RID_PREC_BF16)):
+    for name, prec in (("fp32", rid.RID_PREC_FP32), ("bf16", rid.RID_PREC_BF16), ("fp8", rid.RID_PREC_FP8)):
         with rid.System(sp) as system:
             system.set_ensemble(ens, precision=prec)
             g = torch.zeros((wl["n_models"], W, wl["n_cv"]), dtype=torch.float32, device="cuda")
@@ -397,8 +397,10 @@ def run_precision(rid, torch, steps=10, nve_walkers=64, nve_steps=10000, seed=4)
                      "nve_drift_max_over_3NkT": float(drift.max()), "nve_drift_mean_over_3NkT": float(drift.mean()),
                      "nve": f"{nve_walkers} walkers x {nve_steps} steps, dt = {spn.dt}, energy sampled every "
                             f"{spn.output_freq} steps"}
-    d = (grads["bf16"] - grads["fp32"]).norm(dim=1) / grads["fp32"].norm(dim=1).clamp_min(1e-30)
-    res["bf16"]["mean_force_rel_dev_from_fp32"] = {"median": float(d.median()), "max": float(d.max())}
+    for name in ("bf16", "fp8"):
+        d = (grads[name] - grads["fp32"]).norm(dim=1) / grads["fp32"].norm(dim=1).clamp_min(1e-30)
+        res[name]["mean_force_rel_dev_from_fp32"] = {"median": float(d.median()), "max": float(d.max())}
+    res["fp8"]["arithmetic"] = "forward GEMMs e4m3 (weights / (amax/448) per matrix), input-gradient GEMMs BF16"
     return res
 
 

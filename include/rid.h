@@ -52,8 +52,14 @@ typedef enum {
 enum { RID_MEM_HOST = 0, RID_MEM_DEVICE = 1 };
 
 /* Arithmetic of the ensemble MLP.  Forces, CVs and the integrator are always
- * FP32; label running sums and energy reductions are FP64. */
-enum { RID_PREC_FP32 = 0, RID_PREC_BF16 = 1 };
+ * FP32; label running sums and energy reductions are FP64.
+ *   RID_PREC_FP32  FP32 SIMT, every GEMM
+ *   RID_PREC_BF16  tensor cores, BF16 operands, FP32 accumulation
+ *   RID_PREC_FP8   tensor cores: the forward GEMMs with FP8 e4m3 operands
+ *                  (weights scaled per matrix by amax/448, activations
+ *                  tanh in [-1, 1] unscaled), the input-gradient GEMMs BF16;
+ *                  FP32 accumulation throughout */
+enum { RID_PREC_FP32 = 0, RID_PREC_BF16 = 1, RID_PREC_FP8 = 2 };
 
 /* CV force applied in rid_eval_forces. */
 enum { RID_BIAS_NONE = 0, RID_BIAS_ENSEMBLE = 1, RID_BIAS_RESTRAINT = 2 };
@@ -105,7 +111,7 @@ typedef struct {
     int32_t n_layers;             /* L, 1..8                                    */
     int32_t width;                /* H, multiple of 32, 32..512                 */
     int32_t resnet;               /* 0 / 1                                      */
-    int32_t precision;            /* RID_PREC_*                                 */
+    int32_t precision;            /* RID_PREC_* (FP8 / BF16: resnet = 0 only)   */
     double trust_lo, trust_hi;    /* trust_lo < trust_hi                        */
     const float* weights;         /* host [M][P], copied by the call            */
 } rid_ensemble_desc;

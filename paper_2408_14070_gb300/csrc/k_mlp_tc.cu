@@ -1,5 +1,12 @@
-// k_mlp_tc.cu -- BF16 ensemble MLP on the 5th-generation tensor cores
+// k_mlp_tc.cu -- BF16 / FP8 ensemble MLP on the 5th-generation tensor cores
 // (tcgen05.mma, accumulators in TMEM, weights streamed by tensor TMA).
+//
+// Operands are BF16 (kind::f16) or, for the forward GEMMs of the FP8 mode,
+// e4m3 (kind::f8f6f4); the byte layout is the same for both (128-byte rows,
+// 64 BF16 or 128 FP8 columns per K-chunk, 32 bytes of K per MMA), so a GEMM's
+// operand format only changes how its A operand is written and which MMA
+// kind is issued.  FP8 weights are stored as W / s_W and the accumulator is
+// scaled back by s_W in the epilogue.
 //
 // Work unit: one CTA = one tile of 128 walkers x one ensemble member.  The
 // chain of 2L GEMMs
@@ -103,6 +110,18 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
         "l"(a), "l"(b), "r"(id), "r"(acc)
         : "memory");
 }
+__device__ __forceinline__ uint32_t idesc_e4m3(int M, int N) {
+    // kind::f8f6f4 instruction descriptor: D F32 (bit 4), A and B E4M3 (format
+    // code 0 in bits 7-9 and 10-12), K-major A and B, N >> 3 at bit 17, M >> 4 at bit 24
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_e4m3(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p; }" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -149,6 +168,17 @@ __device__ __forceinline__ void unpack_bf16x8(uint4 w, float (&v)[8]) {
         v[2 * i + 1] = __uint_as_float(u[i] & 0xFFFF0000u);
     }
 }
+// Two floats -> two FP8 e4m3 bytes, x in the low byte (round to nearest even,
+// saturating at +-448).
+__device__ __forceinline__ uint32_t pack_e4m3x2(float x, float y) {
+    uint16_t r;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(y), "f"(x));
+    return r;
+}
+__device__ __forceinline__ uint2 pack8_e4m3(const float (&v)[8]) {
+    return make_uint2(pack_e4m3x2(v[0], v[1]) | (pack_e4m3x2(v[2], v[3]) << 16),
+                      pack_e4m3x2(v[4], v[5]) | (pack_e4m3x2(v[6], v[7]) << 16));
+}
 // Element offset of (layer l, row, 8-column group starting at col) in a
 // tile's saved-tanh scratch [L][H/8][128][8]: the 32 rows of a warp touch one
 // contiguous 512-byte line.
@@ -160,6 +190,24 @@ __device__ __forceinline__ size_t ts_off(int l, int row, int col, int H) {
 __device__ __forceinline__ uint32_t a_off(int row, int col) {
     const int atom = col >> 6, ch = (col >> 3) & 7;
     return (uint32_t)atom * (128u * 128u) + (uint32_t)row * 128u + (uint32_t)((ch ^ (row & 7)) << 4);
+}
+
+// Byte offset of (row, column col; col a multiple of 8) in the FP8 A tile:
+// 128-column atoms, 16 columns per 16-byte chunk.
+__device__ __forceinline__ uint32_t a_off8(int row, int col) {
+    const int atom = col >> 7, ch = (col >> 4) & 7;
+    return (uint32_t)atom * (128u * 128u) + (uint32_t)row * 128u + (uint32_t)((ch ^ (row & 7)) << 4) +
+           (uint32_t)(col & 8);
+}
+// Eight A-operand values of one row at columns col..col+7 in the operand
+// format of the GEMM that reads them (eb bytes per element).
+__device__ __forceinline__ void store_a8(unsigned char* A, int row, int col, int eb, const float (&v)[8]) {
+    if (eb == 2) *reinterpret_cast<uint4*>(A + a_off(row, col)) = pack8(v);
+    else *reinterpret_cast<uint2*>(A + a_off8(row, col)) = pack8_e4m3(v);
+}
+__device__ __forceinline__ void zero_a8(unsigned char* A, int row, int col, int eb) {
+    if (eb == 2) *reinterpret_cast<uint4*>(A + a_off(row, col)) = make_uint4(0, 0, 0, 0);
+    else *reinterpret_cast<uint2*>(A + a_off8(row, col)) = make_uint2(0, 0);
 }
 
 struct Smem {
@@ -227,7 +275,7 @@ __global__ void __maxnreg__(96)
             for (int s = 0; s < NS; ++s) last_it[s] = -1;
             bool ok = true;
             for (int g = 0; g < G && ok; ++g) {
-                const int N = P.gN[g], nch = P.gKp[g] / 64;
+                const int N = P.gN[g], nch = P.gKp[g] * P.geb[g] / 128;
                 for (int c = 0; c < nch && ok; ++c)
                     for (int n0 = 0; n0 < N; n0 += 256, ++it) {
                         const int rows = N - n0 < 256 ? N - n0 : 256;
@@ -263,7 +311,8 @@ __global__ void __maxnreg__(96)
             bool ok = true;
             uint32_t cpar = 0;   // phase bit of every a_chunk[] barrier
             for (int g = 0; g < G && ok; ++g) {
-                const int N = P.gN[g], nch = P.gKp[g] / 64;
+                const int N = P.gN[g], nch = P.gKp[g] * P.geb[g] / 128;
+                const bool f8 = P.geb[g] == 1;
                 const int b = g % NACC;
                 const uint32_t dacc = tmem + (uint32_t)(b * P.acc_cols);
                 if (g >= NACC &&
@@ -288,11 +337,20 @@ __global__ void __maxnreg__(96)
                         }
                         fence_after();
                         const uint32_t b_atom = smem_u32(stages + (size_t)s * stage_bytes);
-                        const uint32_t id = idesc_bf16(128, rows);
+                        // K = 16 BF16 or 32 FP8 per MMA: 32 bytes into the 128-byte rows
+                        if (f8) {
+                            const uint32_t id = idesc_e4m3(128, rows);
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)   // K = 16 per MMA: 32 bytes into the 128-byte rows
-                            mma_bf16(dacc + (uint32_t)n0, desc_sw128(a_atom + 32u * kk),
-                                     desc_sw128(b_atom + 32u * kk), id, (c | kk) != 0);
+                            for (int kk = 0; kk < 4; ++kk)
+                                mma_e4m3(dacc + (uint32_t)n0, desc_sw128(a_atom + 32u * kk),
+                                         desc_sw128(b_atom + 32u * kk), id, (c | kk) != 0);
+                        } else {
+                            const uint32_t id = idesc_bf16(128, rows);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                mma_bf16(dacc + (uint32_t)n0, desc_sw128(a_atom + 32u * kk),
+                                         desc_sw128(b_atom + 32u * kk), id, (c | kk) != 0);
+                        }
                         mma_commit(smem_u32(&S.empty[s]));
                     }
                 }
@@ -314,19 +372,20 @@ __global__ void __maxnreg__(96)
         const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
         const int H = P.H;
         const int ET = 32 * EPI_WARPS;
-        // GEMM 0 input first: u (FP32, [W][D]) -> BF16, chunk by chunk (zeros past D)
+        // GEMM 0 input first: u (FP32, [W][D]) -> its operand format, chunk by
+        // chunk (zeros past D); a 128-byte chunk is 64 BF16 or 128 FP8 columns
         {
-            const int nch0 = P.gKp[0] / 64;
+            const int eb0 = P.geb[0], kc0 = 128 / eb0, nch0 = P.gKp[0] * eb0 / 128;
             for (int c = 0; c < nch0; ++c) {
-                for (int k8 = 0; k8 < 2; ++k8) {
-                    const int col = c * 64 + sub * 16 + k8 * 8;
+                for (int k8 = 0; k8 < kc0 / 32; ++k8) {
+                    const int col = c * kc0 + sub * (kc0 / 4) + k8 * 8;
                     float v[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int k = col + i;
                         v[i] = (valid && k < P.D) ? __ldg(P.u + (size_t)wg * P.D + k) : 0.0f;
                     }
-                    *reinterpret_cast<uint4*>(Abuf + a_off(row, col)) = pack8(v);
+                    store_a8(Abuf, row, col, eb0, v);
                 }
                 fence_async_smem();
                 __syncwarp();
@@ -343,8 +402,13 @@ __global__ void __maxnreg__(96)
         __nv_bfloat16* tsave_tile = P.tsave + ((size_t)m * P.ntiles + tile) * (size_t)L * 128 * H;
         float apart = 0.0f;
         for (int g = 0; g < G; ++g) {
-            const int N = P.gN[g], nch = (N + 63) / 64;
+            const int N = P.gN[g];
             const bool fwd = g < L;
+            // operand bytes of the next GEMM; with FP8 its 128-column K-chunks
+            // span two of these 64-column chunks, and its K padding is zeroed too
+            const int ebn = g + 1 < G ? P.geb[g + 1] : 2;
+            const int nch = ebn == 1 ? 2 * ((N + 127) / 128) : (N + 63) / 64;
+            const float ws = P.wscale[(size_t)m * G + g];
             const int l = fwd ? g : (G - 1 - g);       // layer of this GEMM
             const int b = g % NACC;
             // saved tanh of layer l-1 for this warp's columns, loaded before the wait
@@ -391,10 +455,12 @@ __global__ void __maxnreg__(96)
                     const int gc = col0 + k * 8;
                     if (fwd) {
                         const float* bias = sbias + (size_t)l * H + gc;
-                        const uint4 tw = make_uint4(tanh_bf16x2(acc[k][0] + bias[0], acc[k][1] + bias[1]),
-                                                    tanh_bf16x2(acc[k][2] + bias[2], acc[k][3] + bias[3]),
-                                                    tanh_bf16x2(acc[k][4] + bias[4], acc[k][5] + bias[5]),
-                                                    tanh_bf16x2(acc[k][6] + bias[6], acc[k][7] + bias[7]));
+                        // z = s_W (A W'^T) + b: the weight scale of an FP8 GEMM (1 for BF16)
+                        const uint4 tw =
+                            make_uint4(tanh_bf16x2(fmaf(acc[k][0], ws, bias[0]), fmaf(acc[k][1], ws, bias[1])),
+                                       tanh_bf16x2(fmaf(acc[k][2], ws, bias[2]), fmaf(acc[k][3], ws, bias[3])),
+                                       tanh_bf16x2(fmaf(acc[k][4], ws, bias[4]), fmaf(acc[k][5], ws, bias[5])),
+                                       tanh_bf16x2(fmaf(acc[k][6], ws, bias[6]), fmaf(acc[k][7], ws, bias[7])));
                         *reinterpret_cast<uint4*>(tsave_tile + ts_off(l, row, gc, H)) = tw;
                         if (l == L - 1) {
                             float t[8], d[8];
@@ -405,9 +471,13 @@ __global__ void __maxnreg__(96)
                                 apart = fmaf(wo[i], t[i], apart);
                                 d[i] = wo[i] * (1.0f - t[i] * t[i]);
                             }
-                            *reinterpret_cast<uint4*>(Abuf + a_off(row, gc)) = pack8(d);
-                        } else {
+                            store_a8(Abuf, row, gc, ebn, d);
+                        } else if (ebn == 2) {
                             *reinterpret_cast<uint4*>(Abuf + a_off(row, gc)) = tw;
+                        } else {
+                            float t[8];
+                            unpack_bf16x8(tw, t);
+                            store_a8(Abuf, row, gc, ebn, t);
                         }
                     } else if (l > 0) {
                         // G_{l-1} -> Delta_{l-1} = G (1 - t_{l-1}^2)
@@ -415,7 +485,7 @@ __global__ void __maxnreg__(96)
                         unpack_bf16x8(tcur[k], t);
 #pragma unroll
                         for (int i = 0; i < 8; ++i) d[i] = acc[k][i] * (1.0f - t[i] * t[i]);
-                        *reinterpret_cast<uint4*>(Abuf + a_off(row, gc)) = pack8(d);
+                        store_a8(Abuf, row, gc, ebn, d);
                     } else if (valid) {
                         // G_0 = dA/du: dA/ds_j = -sin s_j g[2j] + cos s_j g[2j+1]
 #pragma unroll
@@ -430,13 +500,15 @@ __global__ void __maxnreg__(96)
                     }
                 }
                 if (g < G - 1) {
-                    // columns past N inside the last chunk are K padding of the next GEMM: zero
-                    for (int k = ng; k < 2; ++k)
-                        *reinterpret_cast<uint4*>(Abuf + a_off(row, col0 + k * 8)) = make_uint4(0, 0, 0, 0);
-                    // chunk c of the next GEMM's A operand is complete (this warp's part)
-                    fence_async_smem();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&S.a_chunk[c]));
+                    // columns past N are K padding of the next GEMM: zero
+                    for (int k = ng; k < 2; ++k) zero_a8(Abuf, row, col0 + k * 8, ebn);
+                    // a 128-byte K-chunk of the next GEMM's A operand is complete
+                    // (this warp's part): every chunk for BF16, every second for FP8
+                    if (ebn == 2 || (c & 1)) {
+                        fence_async_smem();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&S.a_chunk[ebn == 2 ? c : (c >> 1)]));
+                    }
                 }
             }
             if (fwd && l == L - 1) S.apart[sub][row] = apart;

@@ -10,6 +10,7 @@
 #include <cstdlib>
 
 #include <cudaTypedefs.h>
+#include <algorithm>
 
 #include "rid_internal.cuh"
 #include "rid_tc.cuh"
@@ -87,8 +88,8 @@ struct TcVariant {
     unsigned stage_bytes = 0;
     long long member_rows = 0;
     long long grow[2 * RID_MAX_LAYERS] = {0};
-    int gN[2 * RID_MAX_LAYERS] = {0}, gKp[2 * RID_MAX_LAYERS] = {0};
-    DevBuf blob;
+    int gN[2 * RID_MAX_LAYERS] = {0}, gKp[2 * RID_MAX_LAYERS] = {0}, geb[2 * RID_MAX_LAYERS] = {0};
+    DevBuf blob, wscale;
     CUtensorMap big{}, small{};
 };
 
@@ -369,6 +370,27 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+// FP8 e4m3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; no
+// infinities; largest finite 448; subnormals k 2^-9): round to nearest even,
+// saturating at +-448.
+static uint8_t f2e4m3(float f) {
+    const uint8_t sgn = std::signbit(f) ? 0x80 : 0x00;
+    const double a = std::fabs((double)f);
+    if (std::isnan(f)) return sgn | 0x7F;
+    if (a >= 448.0) return sgn | 0x7E;
+    int e = 0;
+    std::frexp(a, &e);                        // a = m 2^e, m in [0.5, 1)
+    int E = e - 1;                            // a = (1 + f) 2^E for normal values
+    if (a == 0.0 || E < -6) {                 // subnormal range: multiples of 2^-9
+        const int q = (int)std::nearbyint(std::ldexp(a, 9));   // q = 8 is the smallest normal, bits 0x08
+        return sgn | (uint8_t)q;
+    }
+    int m = (int)std::nearbyint((std::ldexp(a, -E) - 1.0) * 8.0);
+    if (m == 8) { m = 0; ++E; }
+    if (E > 8 || (E == 8 && m > 6)) return sgn | 0x7E;
+    return sgn | (uint8_t)(((E + 7) << 3) | m);
+}
+
 static uint16_t f2bf(float f) {   // round to nearest even
     uint32_t u;
     std::memcpy(&u, &f, 4);
@@ -378,27 +400,29 @@ static uint16_t f2bf(float f) {   // round to nearest even
 }
 
 static int build_tc_variant(rid_system* sys, const std::vector<float>& W, long long wst, const long long* loff,
-                            TcVariant& V) {
+                            bool fp8, TcVariant& V) {
     const EnsDev& E = sys->E;
     const int M = E.M, D = E.D, L = E.L, H = E.H, Dp = sys->Dp, G = 2 * L;
     V.ok = false;
-    int nmax = 0, kpmax = 0;
+    int nmax = 0, rowbytes = 0;
     long long rows = 0;
     for (int g = 0; g < G; ++g) {
         const bool fwd = g < L;
         const int l = fwd ? g : G - 1 - g;
+        V.geb[g] = (fp8 && fwd) ? 1 : 2;
+        const int kc = 128 / V.geb[g];            // columns per 128-byte K-chunk
         V.gN[g] = fwd ? H : (l == 0 ? Dp : H);
-        V.gKp[g] = (((fwd ? (l == 0 ? Dp : H) : H) + 63) / 64) * 64;
+        V.gKp[g] = (((fwd ? (l == 0 ? D : H) : H) + kc - 1) / kc) * kc;
         if (V.gN[g] > nmax) nmax = V.gN[g];
-        if (V.gKp[g] > kpmax) kpmax = V.gKp[g];
+        if (V.gKp[g] * V.geb[g] > rowbytes) rowbytes = V.gKp[g] * V.geb[g];
         V.grow[g] = rows;
-        rows += (long long)(V.gKp[g] / 64) * V.gN[g];
+        rows += (long long)(V.gKp[g] * V.geb[g] / 128) * V.gN[g];
     }
-    if (kpmax / 64 > TC_MAX_KCHUNKS) return fail(RID_ERR_ARG, "tensor-core path: K up to %d", 64 * TC_MAX_KCHUNKS);
-    V.Kpmax = kpmax;
+    if (rowbytes / 128 > TC_MAX_KCHUNKS) return fail(RID_ERR_ARG, "tensor-core path: K up to %d", 64 * TC_MAX_KCHUNKS);
+    V.Kpmax = rowbytes / 2;
     V.member_rows = rows;
     V.stage_bytes = (unsigned)(nmax < 256 ? nmax : 256) * 128u;
-    const size_t fixed = 1024 + (size_t)kpmax * 256u + sizeof(float) * (size_t)(L + 1) * H;
+    const size_t fixed = 1024 + (size_t)V.Kpmax * 256u + sizeof(float) * (size_t)(L + 1) * H;
     const size_t budget = 225u * 1024u;
     if (fixed + 2 * (size_t)V.stage_bytes > budget)
         return fail(RID_ERR_ARG, "tensor-core path: tile too large for shared memory");
@@ -408,40 +432,58 @@ static int build_tc_variant(rid_system* sys, const std::vector<float>& W, long l
     V.nacc = 2 * V.acc_cols <= 512 ? 2 : 1;
     V.tmem_cols = 32;
     while (V.tmem_cols < V.nacc * V.acc_cols) V.tmem_cols *= 2;
-    // pre-swizzled image: per GEMM, per 64-column K-chunk, N rows of 128 bytes
-    std::vector<uint16_t> img((size_t)M * rows * 64, 0);
+    // pre-swizzled byte image: per GEMM, per 128-byte K-chunk, N rows of 128 bytes
+    std::vector<uint8_t> img((size_t)M * rows * 128, 0);
+    std::vector<float> scale((size_t)M * G, 1.0f);
     for (int m = 0; m < M; ++m)
         for (int g = 0; g < G; ++g) {
             const bool fwd = g < L;
             const int l = fwd ? g : G - 1 - g;
             const int fin = l == 0 ? D : H;
             const float* Wl = W.data() + (size_t)m * wst + loff[l];   // [H][fin]
-            const int N = V.gN[g];
-            for (int c = 0; c < V.gKp[g] / 64; ++c) {
-                const size_t base = ((size_t)m * rows + V.grow[g] + (size_t)c * N) * 64;
+            const int N = V.gN[g], eb = V.geb[g], kc = 128 / eb;
+            float s = 1.0f;
+            if (eb == 1) {
+                float amax = 0.0f;
+                for (size_t i = 0; i < (size_t)H * fin; ++i) amax = std::max(amax, std::fabs(Wl[i]));
+                s = amax > 0.0f ? amax / 448.0f : 1.0f;
+                scale[(size_t)m * G + g] = s;
+            }
+            for (int c = 0; c < V.gKp[g] / kc; ++c) {
+                const size_t base = ((size_t)m * rows + V.grow[g] + (size_t)c * N) * 128;
                 for (int n = 0; n < N; ++n)
-                    for (int kl = 0; kl < 64; ++kl) {
-                        const int k = c * 64 + kl;
+                    for (int kl = 0; kl < kc; ++kl) {
+                        const int k = c * kc + kl;
                         float val = 0.0f;
                         if (fwd) { if (k < fin) val = Wl[(size_t)n * fin + k]; }      // W_l[n][k]
                         else if (n < fin && k < H) val = Wl[(size_t)k * fin + n];     // W_l^T[n][k]
-                        const int j = (kl >> 3) ^ (n & 7);
-                        img[base + (size_t)n * 64 + j * 8 + (kl & 7)] = f2bf(val);
+                        const int byte = kl * eb;
+                        const int j = (byte >> 4) ^ (n & 7);
+                        uint8_t* dst = img.data() + base + (size_t)n * 128 + j * 16 + (byte & 15);
+                        if (eb == 1) {
+                            dst[0] = f2e4m3(val / s);
+                        } else {
+                            const uint16_t h = f2bf(val);
+                            dst[0] = (uint8_t)(h & 0xFF);
+                            dst[1] = (uint8_t)(h >> 8);
+                        }
                     }
             }
         }
-    TRY(V.blob.ensure(img.size() * 2));
-    CK(cudaMemcpy(V.blob.p, img.data(), img.size() * 2, cudaMemcpyHostToDevice));
+    TRY(V.blob.ensure(img.size()));
+    CK(cudaMemcpy(V.blob.p, img.data(), img.size(), cudaMemcpyHostToDevice));
+    TRY(V.wscale.ensure(scale.size() * sizeof(float)));
+    CK(cudaMemcpy(V.wscale.p, scale.data(), scale.size() * sizeof(float), cudaMemcpyHostToDevice));
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return fail(RID_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    const cuuint64_t dims[2] = {64, (cuuint64_t)M * rows};
+    const cuuint64_t dims[2] = {128, (cuuint64_t)M * rows};
     const cuuint64_t strides[1] = {128};
     const cuuint32_t estr[2] = {1, 1};
-    const cuuint32_t box_big[2] = {64, 64}, box_small[2] = {64, 8};
-    CUresult r1 = enc(&V.big, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, V.blob.p, dims, strides, box_big, estr,
+    const cuuint32_t box_big[2] = {128, 64}, box_small[2] = {128, 8};
+    CUresult r1 = enc(&V.big, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, V.blob.p, dims, strides, box_big, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    CUresult r2 = enc(&V.small, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, V.blob.p, dims, strides, box_small, estr,
+    CUresult r2 = enc(&V.small, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, V.blob.p, dims, strides, box_small, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS)
@@ -458,10 +500,10 @@ extern "C" int rid_set_ensemble(rid_system* sys, const rid_ensemble_desc* d) {
     if (D != 2 * sys->S.C) return fail(RID_ERR_ARG, "n_in=%d must equal 2 * n_cv = %d", D, 2 * sys->S.C);
     if (L < 1 || L > RID_MAX_LAYERS) return fail(RID_ERR_ARG, "n_layers=%d outside [1, %d]", L, RID_MAX_LAYERS);
     if (H < 32 || H > RID_MAX_WIDTH || H % 32) return fail(RID_ERR_ARG, "width=%d must be a multiple of 32 in [32, %d]", H, RID_MAX_WIDTH);
-    if (d->precision != RID_PREC_FP32 && d->precision != RID_PREC_BF16)
+    if (d->precision != RID_PREC_FP32 && d->precision != RID_PREC_BF16 && d->precision != RID_PREC_FP8)
         return fail(RID_ERR_ARG, "unknown precision %d", d->precision);
     if (!(d->trust_lo < d->trust_hi)) return fail(RID_ERR_ARG, "need trust_lo < trust_hi");
-    if (d->precision == RID_PREC_BF16 && d->resnet)
+    if (d->precision != RID_PREC_FP32 && d->resnet)
         return fail(RID_ERR_ARG, "resnet ensembles run with RID_PREC_FP32 only");
     const long long P = (long long)H * D + H + (long long)(L - 1) * ((long long)H * H + H) + H + 1;
     // split the packed layout into W (row-major [H][fin]), W^T, biases, w_out, b_out
@@ -513,9 +555,9 @@ extern "C" int rid_set_ensemble(rid_system* sys, const rid_ensemble_desc* d) {
     sys->precision = d->precision;
     sys->has_ens = true;
     E.aslices = 1;
-    if (d->precision == RID_PREC_BF16) {
+    if (d->precision != RID_PREC_FP32) {
         sys->Dp = (D + 63) / 64 * 64;
-        TRY(build_tc_variant(sys, W, wst, loff, sys->tcv));
+        TRY(build_tc_variant(sys, W, wst, loff, d->precision == RID_PREC_FP8, sys->tcv));
         TRY(sys->d_err.ensure(sizeof(int)));
         CK(cudaMemset(sys->d_err.p, 0, sizeof(int)));
     }
@@ -613,7 +655,7 @@ static int launch_forces(rid_system* sys, int W, int mode, bool energy, cudaStre
 
 static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_t st) {
     EnsDev& E = sys->E;
-    if (mode == 1 && sys->precision == RID_PREC_BF16) {
+    if (mode == 1 && sys->precision != RID_PREC_FP32) {
         const TcVariant& V = sys->tcv;
         TcArgs P{};
         P.W = W; P.C = sys->S.C; P.D = E.D; P.Dp = sys->Dp; P.L = E.L; P.H = E.H; P.M = E.M;
@@ -622,7 +664,13 @@ static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_
         P.u = sd.u; P.bias = E.b; P.wout = E.wout; P.bout = E.bout;
         P.tsave = sys->tsave.as<__nv_bfloat16>(); P.gradA = sd.gradA; P.Apart = sd.Aval; P.err = sys->d_err.as<int>();
         P.member_rows = V.member_rows;
-        for (int g = 0; g < 2 * E.L; ++g) { P.grow[g] = V.grow[g]; P.gN[g] = V.gN[g]; P.gKp[g] = V.gKp[g]; }
+        for (int g = 0; g < 2 * E.L; ++g) {
+            P.grow[g] = V.grow[g];
+            P.gN[g] = V.gN[g];
+            P.gKp[g] = V.gKp[g];
+            P.geb[g] = V.geb[g];
+        }
+        P.wscale = V.wscale.as<float>();
         cudaError_t le = cudaSuccess;
         TRY(timed_launch(sys, "k_mlp_tc", st, [&] { le = rid_launch_mlp_tc(P, V.big, V.small, st); }));
         if (le != cudaSuccess) return fail(RID_ERR_CUDA, "k_mlp_tc launch: %s", cudaGetErrorString(le));

@@ -8,16 +8,18 @@
 #include "rid_internal.cuh"
 
 #define TC_MAX_STAGES 8
-#define TC_MAX_KCHUNKS 8   // 64-wide K-chunks of the widest GEMM (K <= 512)
+#define TC_MAX_KCHUNKS 8   // 128-byte K-chunks of the widest GEMM (K <= 512 BF16)
 
 // Weight image, per member: for GEMM g (forward layers 0..L-1, then backward
-// layers L-1..0) and K-chunk c (64 columns), the B operand rows [0, N_g) x
-// columns [64 c, 64 c + 64) as rows of 128 bytes in the 128-byte swizzled
-// layout (16-byte chunk j of row n at position j ^ (n mod 8)), zero padded
-// beyond K_g.  Offsets are counted in those 128-byte rows.
+// layers L-1..0) and K-chunk c (128 bytes of K: 64 BF16 or 128 FP8 e4m3
+// columns), the B operand rows [0, N_g) x that column range as rows of 128
+// bytes in the 128-byte swizzled layout (16-byte chunk j of row n at position
+// j ^ (n mod 8)), zero padded beyond K_g.  Offsets are counted in those
+// 128-byte rows.  FP8 matrices hold W / s with s = amax|W| / 448 per member
+// and matrix.
 struct TcArgs {
     int W, C, D, Dp, L, H, M;
-    int stages, Kpmax, ntiles, tmem_cols, nacc, acc_cols;
+    int stages, Kpmax, ntiles, tmem_cols, nacc, acc_cols;   // Kpmax: A-tile row bytes / 2
     unsigned stage_bytes;
     const float* u;          // [W][D] MLP input (cos, sin), FP32
     const float* bias;       // [M][L][H]
@@ -29,7 +31,9 @@ struct TcArgs {
     int* err;                // error word (bounded-wait expiry codes)
     long long member_rows;   // 128-byte rows per member image
     long long grow[2 * RID_MAX_LAYERS];          // first row of GEMM g within a member image
-    int gN[2 * RID_MAX_LAYERS], gKp[2 * RID_MAX_LAYERS];   // N and K padded to 64
+    int gN[2 * RID_MAX_LAYERS], gKp[2 * RID_MAX_LAYERS];   // N, and K padded to a 128-byte chunk
+    int geb[2 * RID_MAX_LAYERS];                           // operand bytes per element: 2 BF16, 1 FP8 e4m3
+    const float* wscale;     // [M][2L] weight scale of every GEMM (1 for BF16)
 };
 
 size_t rid_mlp_tc_smem_bytes(const TcArgs& P);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "librid.so")
 RID_OK, RID_ERR_ARG, RID_ERR_OOM, RID_ERR_CUDA, RID_ERR_NONFINITE = 0, 1, 2, 3, 4
 RID_ERR_TIMEOUT, RID_NOT_READY, RID_ERR_STATE, RID_ERR_CANCELLED = 5, 6, 7, 8
 RID_MEM_HOST, RID_MEM_DEVICE = 0, 1
-RID_PREC_FP32, RID_PREC_BF16 = 0, 1
+RID_PREC_FP32, RID_PREC_BF16, RID_PREC_FP8 = 0, 1, 2
 RID_BIAS_NONE, RID_BIAS_ENSEMBLE, RID_BIAS_RESTRAINT = 0, 1, 2
 
 # every exported symbol of include/rid.h

@@ -119,7 +119,47 @@ def test_bf16_rejects_resnet(R):
     sp = I.make_system(22, 2, 1)
     ens = I.make_ensemble(4, 4, 3, 64, 1, resnet=True)
     with R.System(sp) as sys:
-        with pytest.raises(R.RidError) as e:
-            sys.set_ensemble(ens, precision=R.RID_PREC_BF16)
-        assert e.value.code == R.RID_ERR_ARG
+        for prec in (R.RID_PREC_BF16, R.RID_PREC_FP8):
+            with pytest.raises(R.RidError) as e:
+                sys.set_ensemble(ens, precision=prec)
+            assert e.value.code == R.RID_ERR_ARG
         sys.set_ensemble(ens, precision=R.RID_PREC_FP32)
+
+
+@pytest.mark.parametrize("n,C,W,M,L,H,seed", [
+    (200, 20, 300, 4, 4, 256, 1),      # the benchmark shape
+    (60, 9, 130, 3, 2, 96, 3),         # width 96: the FP8 K-chunk (128 columns) is partly padding
+    (80, 16, 200, 4, 3, 160, 7),       # width 160: two FP8 K-chunks, the second partly padding
+    (150, 64, 129, 2, 2, 64, 8),       # 128 inputs (one FP8 chunk), width 64 (half a chunk)
+])
+def test_fp8_mean_force_and_eps(R, orc, n, C, W, M, L, H, seed):
+    """FP8 e4m3 forward GEMMs (BF16 input gradient): mean force within 6e-2
+    and eps within 5e-2 of the oracle (host emulation: about 2e-2)."""
+    sp = I.make_system(n, C, seed)
+    x = I.make_chains(W, sp, seed)
+    ens = I.make_ensemble(M, 2 * C, L, H, seed, trust_lo=1e9, trust_hi=2e9)
+    f, eps, abar, g = run_eval(R, sp, ens, x, R.RID_PREC_FP8)
+    worst_f = worst_e = 0.0
+    for w in sorted(set([0, 1, W // 2, W - 1] + list(range(0, W, max(1, W // 12))))):
+        e = orc.ensemble(ens, orc.cvs(sp, x[w].astype(np.float64))[0])
+        fbar = g[:, w].astype(np.float64).mean(axis=0)
+        worst_f = max(worst_f, normwise(fbar, e["gradA"].mean(axis=0)))
+        worst_e = max(worst_e, abs(eps[w] - e["eps"]) / e["eps"])
+    print(f"\n[fp8 {n},{C},{H}] mean force {worst_f:.2e} eps {worst_e:.2e}")
+    assert worst_f < 6e-2 and worst_e < 5e-2
+
+
+def test_fp8_trajectory_is_deterministic(R):
+    sp = I.make_system(100, 16, 9, output_freq=5)
+    x0 = I.make_chains(40, sp, 9)
+    ens = I.make_ensemble(4, 32, 3, 128, 9)
+    outs = []
+    for _ in range(2):
+        xo = np.zeros_like(x0)
+        eps = np.zeros((40, 4), np.float32)
+        with R.System(sp) as sysobj:
+            sysobj.set_ensemble(ens, precision=R.RID_PREC_FP8)
+            sysobj.explore(x0, 20, eps_out=eps, x_out=xo)
+        outs.append((xo, eps))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert np.all(np.isfinite(outs[0][0]))
