@@ -404,6 +404,26 @@ def run_precision(rid, torch, steps=10, nve_walkers=64, nve_steps=10000, seed=4)
     return res
 
 
+def rank_seed(rank):
+    """Every rank runs its own walkers: seed of the inputs of `rank`."""
+    return 1 + rank
+
+
+def max_over_ranks(pg, x, device):
+    """Largest x over all ranks (the job's time is its slowest rank's)."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(walkers_per_rank, world, steps, seconds):
+    """Walker-steps of all ranks per second of the slowest rank."""
+    return walkers_per_rank * world * steps / seconds
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -489,7 +509,7 @@ def main():
 
     wl = I.workload(WORKLOAD)
     W = wl["n_walkers"]
-    sp, x0, ens = make_inputs(wl, seed=1 + rank)
+    sp, x0, ens = make_inputs(wl, seed=rank_seed(rank))
     prec = rid.RID_PREC_BF16 if args.precision == "bf16" else rid.RID_PREC_FP32
     stream = torch.cuda.current_stream()
     system = rid.System(sp)
@@ -520,13 +540,9 @@ def main():
     if pg:
         pg.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
-    if pg:
-        t = torch.tensor([tot_ms], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(pg, sum(step_ms), "cuda")
     system.walkers_read()   # raises on non-finite state
-    value = W * world * args.steps / (tot_ms / 1e3)
+    value = whole_job_rate(W, world, args.steps, tot_ms / 1e3)
 
     # ---- per-kernel timing over the same kind of region (dominant kernel roofline)
     system.profile_enable(True)
@@ -594,12 +610,8 @@ def main():
         hx, ox = ox, hx
         hv, ov = ov, hv
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": W * world * md * args.e2e_calls / e2e_s, "unit": "walker-steps/s",
+    e2e_s = max_over_ranks(pg, time.perf_counter() - t0, "cuda")
+    e2e = {"value": whole_job_rate(W, world, md * args.e2e_calls, e2e_s), "unit": "walker-steps/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "step": f"one rid_explore call from pinned host buffers: {md} MD steps of all walkers, "
                    f"initial force evaluation, CV/eps trace every {sp.output_freq} steps, final x and v"}
