@@ -125,11 +125,13 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
                                                         int slot, float* __restrict__ cv_out,
                                                         float* __restrict__ eps_out, double* __restrict__ energy_out,
                                                         long long T, uint32_t step) {
-    extern __shared__ float4 xs[];
+    extern __shared__ float4 xs[];                     // [N] positions, then (FIN) [4C] Jacobian rows, [4C] slots
     __shared__ float Fs[RID_MAX_CV];
     __shared__ float s_eps, s_abar;
     __shared__ double red[32];
     const int w = blockIdx.x, N = S.N, C = S.C, W = st.W;
+    float4* Jsm = xs + N;                                   // this walker's torsion Jacobians [C][4]
+    int2* acv_s = reinterpret_cast<int2*>(Jsm + 4 * C);     // (cv, slot) list of the chain rule
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long base = (long long)w * N;
     const float kick = S.half_dt * S.inv_mass;
@@ -138,6 +140,7 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
     // bead data of the first batch (and its Langevin noise) is loaded / drawn
     // before the ensemble reduction, so the two overlap
     float3 px[HEAD_BEADS], pv[HEAD_BEADS], pf[HEAD_BEADS], pz[HEAD_BEADS];
+    int a0[HEAD_BEADS], a1[HEAD_BEADS];                    // chain-rule list range of each bead
     auto load_batch = [&](int b0) {
 #pragma unroll
         for (int k = 0; k < HEAD_BEADS; ++k) {
@@ -145,7 +148,11 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
             if (i < N) {
                 px[k] = f3(st.x[base + i]);
                 pv[k] = f3(st.v[base + i]);
-                if (FIN) pf[k] = f3(st.fff[base + i]);
+                if (FIN) {
+                    pf[k] = f3(st.fff[base + i]);
+                    a0[k] = __ldg(S.acv_off + i);
+                    a1[k] = __ldg(S.acv_off + i + 1);
+                }
                 else if (INT == 2) pf[k] = f3(st.f[base + i]);
                 if (INT == 2 && S.c2 != 0.0f) pz[k] = rid_normals3(rid_philox(make_uint4(i, w, stp, 0u), S.key0, S.key1));
             }
@@ -153,6 +160,12 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
     };
     load_batch(0);
     if (FIN) {
+        // the Jacobians of the finished evaluation and the chain-rule list go to
+        // shared memory while the CV force is formed
+        for (int k = threadIdx.x; k < 4 * C; k += blockDim.x) {
+            Jsm[k] = st.J[(long long)w * C * 4 + k];
+            acv_s[k] = __ldg(S.acv + k);
+        }
         if (MODE == 1) {
             if (warp == 0) {
                 const float invM = 1.0f / (float)E.M;
@@ -229,9 +242,9 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
             float4 v = make_float4(pv[k].x, pv[k].y, pv[k].z, 0.f);
             float4 f = make_float4(pf[k].x, pf[k].y, pf[k].z, 0.f);
             if (FIN) {
-                for (int e = S.acv_off[i]; e < S.acv_off[i + 1]; ++e) {
-                    const int2 ja = S.acv[e];
-                    const float4 g = st.J[((long long)w * C + ja.x) * 4 + ja.y];
+                for (int e = a0[k]; e < a1[k]; ++e) {
+                    const int2 ja = acv_s[e];
+                    const float4 g = Jsm[ja.x * 4 + ja.y];
                     const float fs = Fs[ja.x];
                     f.x = fmaf(fs, g.x, f.x);
                     f.y = fmaf(fs, g.y, f.y);
@@ -413,13 +426,12 @@ void rid_launch_ff(const SysDev& S, StateDev st, int W, bool energy, cudaStream_
 template <int MODE, bool FIN, bool KICK, int INT>
 static void head_e(const HeadArgs& a, cudaStream_t s) {
     const int th = HEAD_THREADS;
-    const size_t sm = sizeof(float4) * (size_t)a.S.N;
+    const size_t sm = sizeof(float4) * (size_t)a.S.N + (FIN ? (sizeof(float4) + sizeof(int2)) * 4 * (size_t)a.S.C : 0);
     static bool attr = false;   // positions of up to RID_MAX_BEADS beads exceed the default 48 KB
     if (!attr) {
-        cudaFuncSetAttribute(k_head<MODE, FIN, KICK, INT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             sizeof(float4) * RID_MAX_BEADS);
-        cudaFuncSetAttribute(k_head<MODE, FIN, KICK, INT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             sizeof(float4) * RID_MAX_BEADS);
+        const int mx = (int)(sizeof(float4) * RID_MAX_BEADS + (sizeof(float4) + sizeof(int2)) * 4 * RID_MAX_CV);
+        cudaFuncSetAttribute(k_head<MODE, FIN, KICK, INT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_head<MODE, FIN, KICK, INT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         attr = true;
     }
     if (a.energy)
