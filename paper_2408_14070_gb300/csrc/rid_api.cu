@@ -85,6 +85,7 @@ struct DevBuf {
 struct TcVariant {
     bool ok = false;
     int stages = 0, Kpmax = 0, tmem_cols = 0, nacc = 1, acc_cols = 0;
+    int max_stages = 0, tuned_W = -1;   // weight-stage depth: chosen by timing at each new walker count
     unsigned stage_bytes = 0;
     long long member_rows = 0;
     long long grow[2 * RID_MAX_LAYERS] = {0};
@@ -428,6 +429,8 @@ static int build_tc_variant(rid_system* sys, const std::vector<float>& W, long l
         return fail(RID_ERR_ARG, "tensor-core path: tile too large for shared memory");
     V.stages = (int)((budget - fixed) / V.stage_bytes);
     if (V.stages > TC_MAX_STAGES) V.stages = TC_MAX_STAGES;
+    V.max_stages = V.stages;
+    V.tuned_W = -1;
     V.acc_cols = (nmax + 31) / 32 * 32;
     V.nacc = 2 * V.acc_cols <= 512 ? 2 : 1;
     V.tmem_cols = 32;
@@ -653,6 +656,46 @@ static int launch_forces(rid_system* sys, int W, int mode, bool energy, cudaStre
     return RID_OK;
 }
 
+// Autotuner of the tensor-core kernel's weight pipeline: at the first
+// evaluation with a new walker count, time the kernel with 2, 3, 4, ... up
+// to the largest stage ring that fits shared memory (three launches each,
+// after one warm-up) and keep the fastest.  Results do not depend on the
+// choice.  Skipped while the stream is being captured.
+static int tune_tc_stages(rid_system* sys, TcArgs P, cudaStream_t st) {
+    TcVariant& V = sys->tcv;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone || V.max_stages <= 2) {
+        V.tuned_W = P.W;
+        return RID_OK;
+    }
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    float best = 1e30f;
+    int pick = V.max_stages;
+    for (int ns = 2; ns <= V.max_stages; ++ns) {
+        P.stages = ns;
+        CK(rid_launch_mlp_tc(P, V.big, V.small, st));
+        CK(cudaEventRecord(a, st));
+        for (int r = 0; r < 3; ++r) CK(rid_launch_mlp_tc(P, V.big, V.small, st));
+        CK(cudaEventRecord(b, st));
+        CK(cudaEventSynchronize(b));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best * 0.98f) {        // prefer fewer stages unless clearly slower
+            best = ms;
+            pick = ns;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    V.stages = pick;
+    V.tuned_W = P.W;
+    sys->launches += 4 * (V.max_stages - 1);
+    return RID_OK;
+}
+
 static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_t st) {
     EnsDev& E = sys->E;
     if (mode == 1 && sys->precision != RID_PREC_FP32) {
@@ -672,6 +715,8 @@ static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_
         }
         P.wscale = V.wscale.as<float>();
         cudaError_t le = cudaSuccess;
+        if (V.tuned_W != W) TRY(tune_tc_stages(sys, P, st));
+        P.stages = V.stages;
         TRY(timed_launch(sys, "k_mlp_tc", st, [&] { le = rid_launch_mlp_tc(P, V.big, V.small, st); }));
         if (le != cudaSuccess) return fail(RID_ERR_CUDA, "k_mlp_tc launch: %s", cudaGetErrorString(le));
         E.aslices = 1;
