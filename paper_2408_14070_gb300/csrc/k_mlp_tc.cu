@@ -224,6 +224,10 @@ struct Smem {
 
 // 18 warps spread 5/5/4/4 over the four schedulers, each with 16K registers:
 // at most 96 registers per thread
+// F8: the forward GEMMs take FP8 e4m3 operands (the input-gradient GEMMs
+// stay BF16); the BF16 instantiation has every operand format fixed at
+// compile time.
+template <bool F8>
 __global__ void __maxnreg__(96)
     k_mlp_tc(const __grid_constant__ TcArgs P, const __grid_constant__ CUtensorMap map_big,
              const __grid_constant__ CUtensorMap map_small) {
@@ -275,7 +279,7 @@ __global__ void __maxnreg__(96)
             for (int s = 0; s < NS; ++s) last_it[s] = -1;
             bool ok = true;
             for (int g = 0; g < G && ok; ++g) {
-                const int N = P.gN[g], nch = P.gKp[g] * P.geb[g] / 128;
+                const int N = P.gN[g], nch = P.gKp[g] * (F8 ? P.geb[g] : 2) / 128;
                 for (int c = 0; c < nch && ok; ++c)
                     for (int n0 = 0; n0 < N; n0 += 256, ++it) {
                         const int rows = N - n0 < 256 ? N - n0 : 256;
@@ -311,8 +315,8 @@ __global__ void __maxnreg__(96)
             bool ok = true;
             uint32_t cpar = 0;   // phase bit of every a_chunk[] barrier
             for (int g = 0; g < G && ok; ++g) {
-                const int N = P.gN[g], nch = P.gKp[g] * P.geb[g] / 128;
-                const bool f8 = P.geb[g] == 1;
+                const int N = P.gN[g], nch = P.gKp[g] * (F8 ? P.geb[g] : 2) / 128;
+                const bool f8 = F8 && P.geb[g] == 1;
                 const int b = g % NACC;
                 const uint32_t dacc = tmem + (uint32_t)(b * P.acc_cols);
                 if (g >= NACC &&
@@ -375,7 +379,7 @@ __global__ void __maxnreg__(96)
         // GEMM 0 input first: u (FP32, [W][D]) -> its operand format, chunk by
         // chunk (zeros past D); a 128-byte chunk is 64 BF16 or 128 FP8 columns
         {
-            const int eb0 = P.geb[0], kc0 = 128 / eb0, nch0 = P.gKp[0] * eb0 / 128;
+            const int eb0 = F8 ? P.geb[0] : 2, kc0 = 128 / eb0, nch0 = P.gKp[0] * eb0 / 128;
             for (int c = 0; c < nch0; ++c) {
                 for (int k8 = 0; k8 < kc0 / 32; ++k8) {
                     const int col = c * kc0 + sub * (kc0 / 4) + k8 * 8;
@@ -406,9 +410,9 @@ __global__ void __maxnreg__(96)
             const bool fwd = g < L;
             // operand bytes of the next GEMM; with FP8 its 128-column K-chunks
             // span two of these 64-column chunks, and its K padding is zeroed too
-            const int ebn = g + 1 < G ? P.geb[g + 1] : 2;
+            const int ebn = (F8 && g + 1 < G) ? P.geb[g + 1] : 2;
             const int nch = ebn == 1 ? 2 * ((N + 127) / 128) : (N + 63) / 64;
-            const float ws = P.wscale[(size_t)m * G + g];
+            const float ws = F8 ? P.wscale[(size_t)m * G + g] : 1.0f;
             const int l = fwd ? g : (G - 1 - g);       // layer of this GEMM
             const int b = g % NACC;
             // saved tanh of layer l-1 for this warp's columns, loaded before the wait
@@ -457,10 +461,14 @@ __global__ void __maxnreg__(96)
                         const float* bias = sbias + (size_t)l * H + gc;
                         // z = s_W (A W'^T) + b: the weight scale of an FP8 GEMM (1 for BF16)
                         const uint4 tw =
-                            make_uint4(tanh_bf16x2(fmaf(acc[k][0], ws, bias[0]), fmaf(acc[k][1], ws, bias[1])),
-                                       tanh_bf16x2(fmaf(acc[k][2], ws, bias[2]), fmaf(acc[k][3], ws, bias[3])),
-                                       tanh_bf16x2(fmaf(acc[k][4], ws, bias[4]), fmaf(acc[k][5], ws, bias[5])),
-                                       tanh_bf16x2(fmaf(acc[k][6], ws, bias[6]), fmaf(acc[k][7], ws, bias[7])));
+                            F8 ? make_uint4(tanh_bf16x2(fmaf(acc[k][0], ws, bias[0]), fmaf(acc[k][1], ws, bias[1])),
+                                            tanh_bf16x2(fmaf(acc[k][2], ws, bias[2]), fmaf(acc[k][3], ws, bias[3])),
+                                            tanh_bf16x2(fmaf(acc[k][4], ws, bias[4]), fmaf(acc[k][5], ws, bias[5])),
+                                            tanh_bf16x2(fmaf(acc[k][6], ws, bias[6]), fmaf(acc[k][7], ws, bias[7])))
+                               : make_uint4(tanh_bf16x2(acc[k][0] + bias[0], acc[k][1] + bias[1]),
+                                            tanh_bf16x2(acc[k][2] + bias[2], acc[k][3] + bias[3]),
+                                            tanh_bf16x2(acc[k][4] + bias[4], acc[k][5] + bias[5]),
+                                            tanh_bf16x2(acc[k][6] + bias[6], acc[k][7] + bias[7]));
                         *reinterpret_cast<uint4*>(tsave_tile + ts_off(l, row, gc, H)) = tw;
                         if (l == L - 1) {
                             float t[8], d[8];
@@ -542,12 +550,15 @@ size_t rid_mlp_tc_smem_bytes(const TcArgs& P) {
 
 cudaError_t rid_launch_mlp_tc(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, cudaStream_t s) {
     const size_t smem = rid_mlp_tc_smem_bytes(P);
-    static size_t attr = 0;
-    if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool f8 = P.geb[0] == 1;
+    static size_t attr[2] = {0, 0};
+    if (smem > attr[f8]) {
+        cudaError_t e = f8 ? cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                           : cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr = smem;
+        attr[f8] = smem;
     }
-    k_mlp_tc<<<dim3(P.ntiles, P.M, 1), NTHREADS, smem, s>>>(P, big, small);
+    if (f8) k_mlp_tc<true><<<dim3(P.ntiles, P.M, 1), NTHREADS, smem, s>>>(P, big, small);
+    else k_mlp_tc<false><<<dim3(P.ntiles, P.M, 1), NTHREADS, smem, s>>>(P, big, small);
     return cudaGetLastError();
 }
