@@ -163,3 +163,28 @@ def test_fp8_trajectory_is_deterministic(R):
         outs.append((xo, eps))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     assert np.all(np.isfinite(outs[0][0]))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("n,C,W,M,L,H,seed", [
+    (300, 128, 40, 16, 8, 512, 11),    # largest ensemble: 16 members, 8 layers, width 512, 256 inputs
+    (60, 9, 1, 4, 3, 64, 12),          # a single walker (one mostly empty tile)
+    (40, 8, 129, 4, 3, 96, 13),        # one walker past a full tile
+    (4, 1, 7, 2, 1, 32, 14),           # minimal chain and network: one CV, one hidden layer of 32
+])
+def test_tensor_core_limits(R, orc, prec, n, C, W, M, L, H, seed):
+    sp = I.make_system(n, C, seed)
+    x = I.make_chains(W, sp, seed)
+    ens = I.make_ensemble(M, 2 * C, L, H, seed, trust_lo=1e9, trust_hi=2e9)
+    f, eps, abar, g = run_eval(R, sp, ens, x, R.RID_PREC_BF16 if prec == "bf16" else R.RID_PREC_FP8)
+    # the per-GEMM rounding errors add up roughly as the square root of the
+    # number of GEMMs (2L): the 4-layer bounds scaled by sqrt(L / 4) for deeper nets
+    scale = max(1.0, (L / 4) ** 0.5)
+    tol = (GRAD_TOL if prec == "bf16" else 6e-2) * scale
+    for w in sorted(set([0, W // 2, W - 1])):
+        e = orc.ensemble(ens, orc.cvs(sp, x[w].astype(np.float64))[0])
+        fbar = g[:, w].astype(np.float64).mean(axis=0)
+        ref = e["gradA"].mean(axis=0)
+        assert np.linalg.norm(fbar - ref) <= tol * np.linalg.norm(ref) + 1e-4, w
+        assert abs(eps[w] - e["eps"]) <= EPS_TOL * scale * abs(e["eps"]) + 1e-3, w
+    assert np.all(np.isfinite(f))
