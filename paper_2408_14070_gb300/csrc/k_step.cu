@@ -158,6 +158,19 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
             }
         }
     };
+    // warp 0 forms the CV force: it issues the member gradients of its first
+    // CVs (ensembles of up to 8 members) and the member values before drawing
+    // its noise, so their latency overlaps the Philox work
+    constexpr int PM = 8;
+    float gpre[PM];
+    float avpre = 0.0f;
+    const bool pre = FIN && MODE == 1 && warp == 0 && E.M <= PM;
+    if (pre) {
+        for (int k = lane; k < E.M * E.aslices; k += 32) avpre += st.Aval[(long long)k * W + w];
+#pragma unroll
+        for (int m = 0; m < PM; ++m)
+            gpre[m] = (m < E.M && lane < C) ? st.gradA[((long long)m * W + w) * C + lane] : 0.0f;
+    }
     load_batch(0);
     if (FIN) {
         // the Jacobians of the finished evaluation and the chain-rule list go to
@@ -171,16 +184,30 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
                 const float invM = 1.0f / (float)E.M;
                 // member values: lane k holds entries k and k + 32 of [M][aslices]
                 const int na = E.M * E.aslices;
-                float av = 0.0f;
-                for (int k = lane; k < na; k += 32) av += st.Aval[(long long)k * W + w];
+                float av = avpre;
+                if (!pre)
+                    for (int k = lane; k < na; k += 32) av += st.Aval[(long long)k * W + w];
                 float d2 = 0.0f;
                 for (int j = lane; j < C; j += 32) {
                     float fb = 0.0f;
-                    for (int m = 0; m < E.M; ++m) fb += st.gradA[((long long)m * W + w) * C + j];
-                    fb *= invM;
-                    for (int m = 0; m < E.M; ++m) {
-                        const float d = st.gradA[((long long)m * W + w) * C + j] - fb;
-                        d2 = fmaf(d, d, d2);
+                    if (pre && j == lane) {
+#pragma unroll
+                        for (int m = 0; m < PM; ++m)
+                            if (m < E.M) fb += gpre[m];
+                        fb *= invM;
+#pragma unroll
+                        for (int m = 0; m < PM; ++m)
+                            if (m < E.M) {
+                                const float d = gpre[m] - fb;
+                                d2 = fmaf(d, d, d2);
+                            }
+                    } else {
+                        for (int m = 0; m < E.M; ++m) fb += st.gradA[((long long)m * W + w) * C + j];
+                        fb *= invM;
+                        for (int m = 0; m < E.M; ++m) {
+                            const float d = st.gradA[((long long)m * W + w) * C + j] - fb;
+                            d2 = fmaf(d, d, d2);
+                        }
                     }
                     Fs[j] = fb;
                 }
