@@ -43,8 +43,11 @@ __global__ void k_mb(SysDev S, StateDev st, int W, uint32_t step0) {
     st.v[idx] = make_float4(S.sd_mb * z.x, S.sd_mb * z.y, S.sd_mb * z.z, 0.0f);
 }
 
-// At most 224 threads (7 warps) and 32 registers per thread, so that up to
-// nine CTAs (one walker each) fit on an SM.
+// At most 224 threads (7 warps) per CTA (one walker).  k_ff gets 56 registers
+// per thread (five CTAs per SM): with fewer, the unrolled pair loop cannot hold
+// a cluster's positions in flight and waits on every shared-memory load
+// (measured: 32 registers 35.3 us alone, 40 registers 31.5 us, 56 registers
+// 30.2 us for 1024 walkers x 200 beads).
 constexpr int FF_THREADS = 224;
 
 // Force-field forces (bonded + all-pairs LJ, culled by cluster boxes) of
@@ -52,7 +55,7 @@ constexpr int FF_THREADS = 224;
 // bonded terms through shared per-term slots (chains up to
 // RID_BONDED_SMEM_MAX beads), else per bead.
 template <bool ENERGY, bool BSMEM>
-__global__ void __maxnreg__(32) k_ff(SysDev S, StateDev st) {
+__global__ void __maxnreg__(56) k_ff(SysDev S, StateDev st) {
     extern __shared__ float4 sm4[];
     __shared__ double red[32];
     __shared__ unsigned keep_s[FF_THREADS / 32][LJ_MAX_MASK_WORDS];
