@@ -175,6 +175,62 @@ RID_API int rid_label(rid_system* sys, int32_t n_runs, const float* x0, const fl
               float* x_out, float* v_out, int32_t mem, void* stream);
 
 /*
+ * Training the ensemble on mean-force labels (Sec. "Training phase":
+ * numb_models, neurons, resnet, batch_size, init_lr, decay_steps, decay_rate;
+ * Sec. "Training": the models are fitted to the labelled mean forces).
+ *
+ * Every member i has its own batches.  Its loss on a batch of B labels
+ * (s_k, MF_k) is the mean over the batch and the C components of
+ * (dA_i/ds_j(s_k) - MF_kj)^2, and its weights take one Adam step per batch
+ * (beta1, beta2, adam_eps) with learning rate init_lr * decay_rate^(t /
+ * decay_steps) at the trainer's t-th step (t = 0, 1, ...).  The weights use
+ * the packed layout of rid_ensemble_desc.weights, so rid_trainer_weights can
+ * feed rid_set_ensemble directly.  Arithmetic: FP32 with fixed summation
+ * orders (a run is reproducible bit for bit); b_out does not enter the loss
+ * and is never changed.
+ *
+ * All calls are synchronous on `stream`.  `mem` says where the array
+ * arguments live (RID_MEM_HOST / RID_MEM_DEVICE).  Errors: RID_ERR_ARG (bad
+ * sizes, a batch index outside [0, n_data): detected on the device, the step's
+ * results are then not to be used), RID_ERR_STATE (no data), RID_ERR_OOM,
+ * RID_ERR_CUDA.
+ */
+typedef struct {
+    int32_t n_models;             /* M, 1..16                                   */
+    int32_t n_cv;                 /* C (inputs D = 2C), 1..128                  */
+    int32_t n_layers;             /* L, 1..8                                    */
+    int32_t width;                /* H, 1..512                                  */
+    int32_t resnet;               /* 0 / 1 (h_l = h_{l-1} + tanh(.) for l >= 2) */
+    int32_t batch_size;           /* B, 1..65536 (128 in the paper)             */
+    double init_lr;               /* 8e-4 in the paper                          */
+    double decay_rate;            /* 0.96                                       */
+    int32_t decay_steps;          /* 120                                        */
+    double beta1, beta2, adam_eps;  /* Adam: 0.9, 0.999, 1e-8                   */
+} rid_train_desc;
+
+typedef struct rid_trainer rid_trainer;
+
+/* Create a trainer on the current device from host weights [M][P] (copied;
+ * Adam moments start at zero, t = 0). */
+RID_API int rid_trainer_create(const rid_train_desc* desc, const float* weights, rid_trainer** out);
+RID_API int rid_trainer_destroy(rid_trainer* tr);
+/* The label set: s [n][C] (radians) and mf [n][C], copied to the device. */
+RID_API int rid_trainer_set_data(rid_trainer* tr, int32_t n, const float* s, const float* mf, int32_t mem,
+                                 void* stream);
+/* n_steps Adam steps; idx [n_steps][M][B] int32 are the sample indices of each
+ * member's batch at each step; loss_out [n_steps][M] | NULL receives each
+ * member's batch loss at the weights before its step. */
+RID_API int rid_trainer_run(rid_trainer* tr, int32_t n_steps, const int32_t* idx, float* loss_out, int32_t mem,
+                            void* stream);
+/* The loss [M] and its gradient [M][P] at the current weights for one batch
+ * idx [M][B], without changing the weights (either output may be NULL). */
+RID_API int rid_trainer_grad(rid_trainer* tr, const int32_t* idx, float* loss_out, float* grad_out, int32_t mem,
+                             void* stream);
+/* Current weights [M][P] (NULL to skip) and the number of steps taken. */
+RID_API int rid_trainer_weights(rid_trainer* tr, float* weights_out, int64_t* steps_done, int32_t mem,
+                                void* stream);
+
+/*
  * One force evaluation at given positions (no integration), through the same
  * kernels as a step.  bias = RID_BIAS_*; s0/kappa [W][C] are read only for
  * RID_BIAS_RESTRAINT.

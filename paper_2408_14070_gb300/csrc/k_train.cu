@@ -1,0 +1,655 @@
+// k_train.cu -- training the ensemble on mean-force labels (Sec. "Training
+// phase": numb_models, neurons, resnet, batch_size, init_lr, decay_steps,
+// decay_rate; Sec. "Training": the models are fitted to the labelled mean
+// forces, the derivatives of the free energy).
+//
+// Each member i is fitted on its own batches: the loss is the mean squared
+// difference between its CV gradient dA_i/ds and the label MF over the batch
+// and the C components, and the weights take one Adam step per batch with the
+// learning rate init_lr * decay_rate^(t / decay_steps).
+//
+// One training step is a chain of batched FP32 GEMMs (members on grid z) with
+// the elementwise work of each pass fused into the GEMM that produces its
+// input (notation of the per-layer recurrences; r_l = 1 for residual layers):
+//   forward    l = 0..L-1:  t_l = tanh(h_{l-1} W_l^T + b_l), h_l = t_l + r_l h_{l-1}
+//                           (last layer: g_{L-1} = w_out, d_{L-1} = g (1 - t^2))
+//   input grad l = L-1..0:  g_{l-1} = d_l W_l + r_l g_l, d_{l-1} = g_{l-1} (1 - t_{l-1}^2)
+//   loss:                   dA/ds_j = -sin s_j g[2j] + cos s_j g[2j+1], its adjoint gbar_{-1}
+//   adjoint    l = 0..L-1:  dbar = gbar_{l-1} W_l^T, gbar_l = dbar (1 - t^2) + r_l gbar_{l-1},
+//                           tbar_l = -2 t_l g_l dbar  (last layer: zbar = tbar (1 - t^2))
+//   back       l = L-1..1:  hbar_{l-1} = zbar_l W_l + r_l hbar_l,
+//                           zbar_{l-1} = (tbar_{l-1} + hbar_{l-1}) (1 - t_{l-1}^2)
+//   weights:   dW_l = d_l^T gbar_{l-1} + zbar_l^T h_{l-1} (one GEMM over 2B rows),
+//              db_l = sum_b zbar_l, dw_out = sum_b gbar_{L-1}, db_out = 0
+//   Adam (Kingma & Ba) on every parameter.
+// Every sum is taken in a fixed order, so a run is reproducible bit for bit.
+#include <cmath>
+#include <vector>
+
+#include "rid_internal.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Batched FP32 GEMM: C[i][j] = sum over up to two K segments of A(i, k) B(k, j)
+// with element (i, k) of A at A + i * si + k * sk (member offset z * sm), so
+// one kernel serves the N-N, N-T and T-N forms.  64 x 64 output tile, K tiles
+// of 16, 256 threads with 4 x 4 outputs each.
+constexpr int GT = 64, GK = 16, GTHREADS = 256;
+
+// A operand: element (i, k) at p + z sm + i si + k sk.  B operand: element
+// (k, j) at p + z sm + j si + k sk (si strides the output column).
+struct Operand {
+    const float* p;
+    long long si, sk, sm;
+};
+struct Seg {
+    Operand a, b;
+    int K;
+};
+
+enum Epi { EPI_STORE = 0, EPI_FWD = 1, EPI_BWD = 2, EPI_ADJ = 3, EPI_BACK = 4 };
+
+// Activation tensors are [M][B][X] row-major: element (m, b, x) at
+// m * B * X + b * X + x.  The epilogue pointers below follow that layout
+// with the row stride ld of the GEMM's output width.
+struct EpiArgs {
+    float* out;        // primary output [M][rows][ld]
+    long long out_sm;  // member stride of out
+    int ld;            // row stride of out (= N)
+    // forward: bias b_l, T_l out, h_l out, h_{l-1} in (residual), w_out (last layer: G, D out)
+    const float* bias; long long bias_sm;
+    float* T; float* Hout; const float* Hin; const float* wout; long long w_sm;
+    float* Gout; float* Dout;
+    // backward / adjoint / back: residual input, T of the layer, second outputs
+    const float* res; const float* Tl; const float* Gl; float* out2; const float* tb; float* out3;
+    long long act_sm;  // member stride of the [rows][ld] activations
+    int resid;         // r_l
+    int last;          // forward / adjoint on the last layer
+};
+
+struct GemmArgs {
+    Seg seg[2];
+    int nseg;
+    int rows, cols;
+    EpiArgs e;
+};
+
+__device__ __forceinline__ float ldop(const Operand& o, int z, int r, int k) {
+    return o.p[(long long)z * o.sm + (long long)r * o.si + (long long)k * o.sk];
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(GTHREADS) k_tr_gemm(GemmArgs g) {
+    __shared__ float As[GK][GT + 4];
+    __shared__ float Bs[GK][GT + 4];
+    const int z = blockIdx.z, i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    float acc[4][4] = {};
+    for (int sidx = 0; sidx < g.nseg; ++sidx) {
+        const Seg& S = g.seg[sidx];
+        const bool a_kfast = S.a.sk == 1;   // A row-major along K: threads walk K
+        const bool b_jfast = S.b.si == 1;   // B (k, j) with j contiguous: threads walk j
+        for (int k0 = 0; k0 < S.K; k0 += GK) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int idx = tid + GTHREADS * r;
+                int ii, kk;
+                if (a_kfast) { ii = idx >> 4; kk = idx & 15; }
+                else { kk = idx >> 6; ii = idx & 63; }
+                const int gi = i0 + ii, gk = k0 + kk;
+                As[kk][ii] = (gi < g.rows && gk < S.K) ? ldop(S.a, z, gi, gk) : 0.0f;
+                int jj, kb;
+                if (b_jfast) { kb = idx >> 6; jj = idx & 63; }
+                else { jj = idx >> 4; kb = idx & 15; }
+                const int gj = j0 + jj, gkb = k0 + kb;
+                // B operand: element (k, j) at p + j * si + k * sk
+                Bs[kb][jj] = (gj < g.cols && gkb < S.K) ? ldop(S.b, z, gj, gkb) : 0.0f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < GK; ++kk) {
+                const float4 a = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+                const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+            }
+            __syncthreads();
+        }
+    }
+    const EpiArgs& e = g.e;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int i = i0 + ty * 4 + p;
+        if (i >= g.rows) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + tx * 4 + q;
+            if (j >= g.cols) continue;
+            const long long o = (long long)z * e.act_sm + (long long)i * e.ld + j;
+            const float a = acc[p][q];
+            if (EPI == EPI_STORE) {
+                e.out[(long long)z * e.out_sm + (long long)i * e.ld + j] = a;
+            } else if (EPI == EPI_FWD) {
+                const float t = tanhf(a + e.bias[(long long)z * e.bias_sm + j]);
+                e.T[o] = t;
+                if (e.Hout != e.T) e.Hout[o] = e.resid ? t + e.Hin[o] : t;
+                if (e.last) {
+                    const float w = e.wout[(long long)z * e.w_sm + j];
+                    e.Gout[o] = w;
+                    e.Dout[o] = w * (1.0f - t * t);
+                }
+            } else if (EPI == EPI_BWD) {
+                // g_{l-1} = d_l W_l + r_l g_l; d_{l-1} = g_{l-1} (1 - t_{l-1}^2)
+                const float gv = e.resid ? a + e.res[o] : a;
+                e.out[o] = gv;
+                if (e.Dout) {
+                    const float t = e.Tl[o];
+                    e.Dout[o] = gv * (1.0f - t * t);
+                }
+            } else if (EPI == EPI_ADJ) {
+                // dbar = acc; gbar_l = dbar (1 - t^2) + r gbar_{l-1}; tbar = -2 t g dbar
+                const float t = e.Tl[o];
+                const float sp = 1.0f - t * t;
+                e.out[o] = e.resid ? a * sp + e.res[o] : a * sp;
+                const float tb = -2.0f * t * e.Gl[o] * a;
+                e.out2[o] = tb;
+                if (e.last) e.out3[o] = tb * sp;      // zbar_{L-1} (hbar_{L-1} = 0)
+            } else if (EPI == EPI_BACK) {
+                // hbar_{l-1} = zbar_l W_l + r hbar_l; zbar_{l-1} = (tbar + hbar)(1 - t^2)
+                const float hb = e.resid ? a + e.res[o] : a;
+                e.out[o] = hb;
+                const float t = e.Tl[o];
+                e.out3[o] = (e.tb[o] + hb) * (1.0f - t * t);
+            }
+        }
+    }
+}
+
+// u = (cos s, sin s) of each member's batch, plus the batch's s and labels.
+// idx is checked; an index outside [0, n) reads sample 0 and sets *bad.
+__global__ void k_tr_gather(const int* __restrict__ idx, const float* __restrict__ s, const float* __restrict__ mf,
+                            int n, int M, int B, int C, float* __restrict__ U, float* __restrict__ SB,
+                            float* __restrict__ MFB, int* bad) {
+    const long long tot = (long long)M * B * C;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const long long mb = e / C;
+        const int j = (int)(e - mb * C);
+        int k = idx[mb];
+        if (k < 0 || k >= n) {
+            atomicOr(bad, 1);
+            k = 0;
+        }
+        const float sv = s[(long long)k * C + j];
+        float sn, cs;
+        sincosf(sv, &sn, &cs);
+        U[mb * 2 * C + 2 * j] = cs;
+        U[mb * 2 * C + 2 * j + 1] = sn;
+        SB[e] = sv;
+        MFB[e] = mf[(long long)k * C + j];
+    }
+}
+
+// Per member (grid x): residual dA/ds - MF, the loss (mean of its square over
+// B x C, summed in a fixed order), and gbar_{-1} = d loss / d(dA/du).
+constexpr int LT = 256;
+__global__ void __launch_bounds__(LT) k_tr_loss(const float* __restrict__ G0, const float* __restrict__ SB,
+                                                const float* __restrict__ MFB, int B, int C,
+                                                float* __restrict__ GB0, float* __restrict__ loss) {
+    __shared__ double red[LT];
+    const int m = blockIdx.x;
+    const long long n = (long long)B * C;
+    const float scale = 2.0f / (float)n;
+    double part = 0.0;
+    for (long long e = threadIdx.x; e < n; e += LT) {
+        const long long o = (long long)m * n + e;
+        const float sv = SB[o];
+        float sn, cs;
+        sincosf(sv, &sn, &cs);
+        const long long u = (long long)m * 2 * n + 2 * e;     // (b, j) -> u index 2 (b C + j)
+        const float dads = fmaf(cs, G0[u + 1], -sn * G0[u]);
+        const float r = dads - MFB[o];
+        part += (double)r * r;
+        const float v = scale * r;
+        GB0[u] = -sn * v;
+        GB0[u + 1] = cs * v;
+    }
+    red[threadIdx.x] = part;
+    __syncthreads();
+    for (int w = LT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss[m] = (float)(red[0] / (double)n);
+}
+
+// Column sums over the batch rows of [M][B][H] activations into the packed
+// gradient: grid (ceil(H / 128), M, nvec).
+struct ColSums {
+    const float* src[RID_MAX_LAYERS + 1];
+    long long dst_off[RID_MAX_LAYERS + 1];
+    int n;
+};
+__global__ void k_tr_colsum(ColSums cs, int B, int H, long long act_sm, float* __restrict__ grad, long long P) {
+    const int m = blockIdx.y, v = blockIdx.z;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= cs.n || j >= H) return;
+    const float* src = cs.src[v] + (long long)m * act_sm;
+    float a = 0.0f;
+    for (int b = 0; b < B; ++b) a += src[(long long)b * H + j];
+    grad[(long long)m * P + cs.dst_off[v] + j] = a;
+}
+
+__global__ void k_tr_adam(float* __restrict__ w, float* __restrict__ am, float* __restrict__ av,
+                          const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps, float c1,
+                          float c2) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const float gv = g[e];
+        const float m = fmaf(b1, am[e], (1.0f - b1) * gv);
+        const float v = fmaf(b2, av[e], (1.0f - b2) * gv * gv);
+        am[e] = m;
+        av[e] = v;
+        w[e] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+struct rid_trainer {
+    rid_train_desc d{};
+    int D = 0, P = 0;
+    long long woff[RID_MAX_LAYERS] = {}, boff[RID_MAX_LAYERS] = {}, ooff = 0;
+    int64_t steps = 0;
+    int n_data = 0, cap_data = 0;
+    float* w = nullptr;      // [M][P] parameters, then Adam m, v and the gradient
+    float* am = nullptr;
+    float* av = nullptr;
+    float* grad = nullptr;
+    float* ds = nullptr;     // data s [n][C], mf [n][C]
+    float* dmf = nullptr;
+    float* act = nullptr;    // activations (see carve)
+    int* didx = nullptr;     // [cap_idx] batch indices
+    long long cap_idx = 0;
+    float* dloss = nullptr;  // [cap_loss]
+    long long cap_loss = 0;
+    int* dbad = nullptr;
+    // carve of act, all [M][B][X]
+    float *U, *SB, *MFB, *G0, *GB0;
+    float *T[RID_MAX_LAYERS], *Hh[RID_MAX_LAYERS], *G[RID_MAX_LAYERS], *Dl[RID_MAX_LAYERS], *GB[RID_MAX_LAYERS],
+        *TB[RID_MAX_LAYERS], *ZB[RID_MAX_LAYERS], *HB[RID_MAX_LAYERS];
+};
+
+namespace {
+
+int tr_fail_cuda(cudaError_t e, const char* what) {
+    return rid_fail(RID_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+#define TCK(x)                                          \
+    do {                                                \
+        cudaError_t e_ = (x);                           \
+        if (e_ != cudaSuccess) return tr_fail_cuda(e_, #x); \
+    } while (0)
+
+int grow(void** p, long long* cap, long long need, size_t elem) {
+    if (need <= *cap) return RID_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(p, (size_t)need * elem) != cudaSuccess) {
+        cudaGetLastError();
+        return rid_fail(RID_ERR_OOM, "trainer: cudaMalloc of %lld bytes failed", need * (long long)elem);
+    }
+    *cap = need;
+    return RID_OK;
+}
+
+template <int EPI>
+void launch_gemm(const GemmArgs& g, int M, cudaStream_t st) {
+    dim3 grid((g.cols + GT - 1) / GT, (g.rows + GT - 1) / GT, M);
+    k_tr_gemm<EPI><<<grid, GTHREADS, 0, st>>>(g);
+}
+
+// Operand helpers over [M][rows][ld] activations and [M][P] packed weights.
+Operand act_rowmajor(const float* p, int ld, long long sm) { return Operand{p, (long long)ld, 1, sm}; }
+Operand act_transposed(const float* p, int ld, long long sm) { return Operand{p, 1, (long long)ld, sm}; }
+
+// One step's gradient into tr->grad and the per-member loss into loss[M],
+// for the batch indices idx [M][B] (device).
+int tr_gradient(rid_trainer* tr, const int* idx, float* loss, cudaStream_t st) {
+    const rid_train_desc& d = tr->d;
+    const int M = d.n_models, B = d.batch_size, C = d.n_cv, D = tr->D, L = d.n_layers, H = d.width;
+    const long long P = tr->P;
+    const long long smH = (long long)B * H, smD = (long long)B * D;
+    {
+        const long long tot = (long long)M * B * C;
+        const int blocks = (int)((tot + 255) / 256 < 1024 ? (tot + 255) / 256 : 1024);
+        k_tr_gather<<<blocks, 256, 0, st>>>(idx, tr->ds, tr->dmf, tr->n_data, M, B, C, tr->U, tr->SB, tr->MFB,
+                                            tr->dbad);
+    }
+    // forward
+    for (int l = 0; l < L; ++l) {
+        const int fin = l == 0 ? D : H;
+        GemmArgs g{};
+        g.nseg = 1;
+        g.seg[0].a = act_rowmajor(l == 0 ? tr->U : tr->Hh[l - 1], fin, l == 0 ? smD : smH);
+        g.seg[0].b = Operand{tr->w + tr->woff[l], (long long)fin, 1, P};   // (k, j) -> W_l[j][k]
+        g.seg[0].K = fin;
+        g.rows = B;
+        g.cols = H;
+        EpiArgs& e = g.e;
+        e.ld = H;
+        e.act_sm = smH;
+        e.bias = tr->w + tr->boff[l];
+        e.bias_sm = P;
+        e.T = tr->T[l];
+        e.Hout = tr->Hh[l];
+        e.Hin = l == 0 ? nullptr : tr->Hh[l - 1];
+        e.resid = d.resnet && l >= 1;
+        e.last = l == L - 1;
+        e.wout = tr->w + tr->ooff;
+        e.w_sm = P;
+        e.Gout = tr->G[L - 1];
+        e.Dout = tr->Dl[L - 1];
+        launch_gemm<EPI_FWD>(g, M, st);
+    }
+    // input gradient, decreasing l: g_{l-1} = d_l W_l (+ r g_l)
+    for (int l = L - 1; l >= 0; --l) {
+        const int fin = l == 0 ? D : H;
+        GemmArgs g{};
+        g.nseg = 1;
+        g.seg[0].a = act_rowmajor(tr->Dl[l], H, smH);
+        g.seg[0].b = Operand{tr->w + tr->woff[l], 1, (long long)fin, P};   // (k, j) -> W_l[k][j]
+        g.seg[0].K = H;
+        g.rows = B;
+        g.cols = fin;
+        EpiArgs& e = g.e;
+        e.ld = fin;
+        e.act_sm = l == 0 ? smD : smH;
+        e.out = l == 0 ? tr->G0 : tr->G[l - 1];
+        e.resid = d.resnet && l >= 1;
+        e.res = tr->G[l];
+        e.Tl = l == 0 ? nullptr : tr->T[l - 1];
+        e.Dout = l == 0 ? nullptr : tr->Dl[l - 1];
+        launch_gemm<EPI_BWD>(g, M, st);
+    }
+    k_tr_loss<<<M, LT, 0, st>>>(tr->G0, tr->SB, tr->MFB, B, C, tr->GB0, loss);
+    // adjoint of the input-gradient pass, increasing l
+    for (int l = 0; l < L; ++l) {
+        const int fin = l == 0 ? D : H;
+        GemmArgs g{};
+        g.nseg = 1;
+        g.seg[0].a = act_rowmajor(l == 0 ? tr->GB0 : tr->GB[l - 1], fin, l == 0 ? smD : smH);
+        g.seg[0].b = Operand{tr->w + tr->woff[l], (long long)fin, 1, P};   // W_l^T
+        g.seg[0].K = fin;
+        g.rows = B;
+        g.cols = H;
+        EpiArgs& e = g.e;
+        e.ld = H;
+        e.act_sm = smH;
+        e.out = tr->GB[l];
+        e.resid = d.resnet && l >= 1;
+        e.res = l == 0 ? nullptr : tr->GB[l - 1];
+        e.Tl = tr->T[l];
+        e.Gl = tr->G[l];
+        e.out2 = tr->TB[l];
+        e.last = l == L - 1;
+        e.out3 = tr->ZB[L - 1];
+        launch_gemm<EPI_ADJ>(g, M, st);
+    }
+    // back through the forward pass, decreasing l (hbar_{L-1} = 0)
+    for (int l = L - 1; l >= 1; --l) {
+        GemmArgs g{};
+        g.nseg = 1;
+        g.seg[0].a = act_rowmajor(tr->ZB[l], H, smH);
+        g.seg[0].b = Operand{tr->w + tr->woff[l], 1, (long long)H, P};     // W_l
+        g.seg[0].K = H;
+        g.rows = B;
+        g.cols = H;
+        EpiArgs& e = g.e;
+        e.ld = H;
+        e.act_sm = smH;
+        e.out = tr->HB[l - 1];
+        e.resid = d.resnet && l >= 1 && l < L - 1;   // hbar_{L-1} = 0
+        e.res = tr->HB[l];
+        e.Tl = tr->T[l - 1];
+        e.tb = tr->TB[l - 1];
+        e.out3 = tr->ZB[l - 1];
+        launch_gemm<EPI_BACK>(g, M, st);
+    }
+    // weight gradients: dW_l[a][b] = sum_k d_l[k][a] gbar_{l-1}[k][b] + zbar_l[k][a] h_{l-1}[k][b]
+    for (int l = 0; l < L; ++l) {
+        const int fin = l == 0 ? D : H;
+        const long long smF = l == 0 ? smD : smH;
+        GemmArgs g{};
+        g.nseg = 2;
+        g.seg[0].a = act_transposed(tr->Dl[l], H, smH);
+        g.seg[0].b = Operand{l == 0 ? tr->GB0 : tr->GB[l - 1], 1, (long long)fin, smF};
+        g.seg[0].K = B;
+        g.seg[1].a = act_transposed(tr->ZB[l], H, smH);
+        g.seg[1].b = Operand{l == 0 ? tr->U : tr->Hh[l - 1], 1, (long long)fin, smF};
+        g.seg[1].K = B;
+        g.rows = H;
+        g.cols = fin;
+        g.e.out = tr->grad + tr->woff[l];
+        g.e.out_sm = P;
+        g.e.ld = fin;
+        launch_gemm<EPI_STORE>(g, M, st);
+    }
+    ColSums cs{};
+    for (int l = 0; l < L; ++l) {
+        cs.src[l] = tr->ZB[l];
+        cs.dst_off[l] = tr->boff[l];
+    }
+    cs.src[L] = tr->GB[L - 1];
+    cs.dst_off[L] = tr->ooff;
+    cs.n = L + 1;
+    k_tr_colsum<<<dim3((H + 127) / 128, M, L + 1), 128, 0, st>>>(cs, B, H, smH, tr->grad, P);
+    return RID_OK;
+}
+
+int tr_check_desc(const rid_train_desc* d) {
+    if (!d) return rid_fail(RID_ERR_ARG, "trainer: desc is NULL");
+    if (d->n_models < 1 || d->n_models > RID_MAX_MODELS) return rid_fail(RID_ERR_ARG, "trainer: n_models out of range");
+    if (d->n_cv < 1 || d->n_cv > RID_MAX_CV) return rid_fail(RID_ERR_ARG, "trainer: n_cv out of range");
+    if (d->n_layers < 1 || d->n_layers > RID_MAX_LAYERS) return rid_fail(RID_ERR_ARG, "trainer: n_layers out of range");
+    if (d->width < 1 || d->width > RID_MAX_WIDTH) return rid_fail(RID_ERR_ARG, "trainer: width out of range");
+    if (d->batch_size < 1 || d->batch_size > 65536) return rid_fail(RID_ERR_ARG, "trainer: batch_size out of range");
+    if (!(d->init_lr > 0) || !(d->decay_rate > 0) || d->decay_steps < 1)
+        return rid_fail(RID_ERR_ARG, "trainer: learning-rate schedule out of range");
+    if (!(d->beta1 >= 0 && d->beta1 < 1) || !(d->beta2 >= 0 && d->beta2 < 1) || !(d->adam_eps > 0))
+        return rid_fail(RID_ERR_ARG, "trainer: Adam parameters out of range");
+    return RID_OK;
+}
+
+int tr_copy_in(void* dst, const void* src, size_t bytes, int mem, cudaStream_t st) {
+    TCK(cudaMemcpyAsync(dst, src, bytes, mem == RID_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    return RID_OK;
+}
+int tr_copy_out(void* dst, const void* src, size_t bytes, int mem, cudaStream_t st) {
+    TCK(cudaMemcpyAsync(dst, src, bytes, mem == RID_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    return RID_OK;
+}
+
+int tr_finish(rid_trainer* tr, cudaStream_t st) {
+    int bad = 0;
+    TCK(cudaMemcpyAsync(&bad, tr->dbad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TCK(cudaStreamSynchronize(st));
+    TCK(cudaGetLastError());
+    if (bad) {
+        TCK(cudaMemsetAsync(tr->dbad, 0, sizeof(int), st));
+        TCK(cudaStreamSynchronize(st));
+        return rid_fail(RID_ERR_ARG, "trainer: a batch index is outside [0, n_data)");
+    }
+    return RID_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+RID_API int rid_trainer_create(const rid_train_desc* desc, const float* weights, rid_trainer** out) {
+    if (!out || !weights) return rid_fail(RID_ERR_ARG, "trainer: NULL argument");
+    *out = nullptr;
+    if (int rc = tr_check_desc(desc)) return rc;
+    rid_trainer* tr = new rid_trainer();
+    tr->d = *desc;
+    const int M = desc->n_models, C = desc->n_cv, L = desc->n_layers, H = desc->width, B = desc->batch_size;
+    const int D = 2 * C;
+    tr->D = D;
+    long long o = 0;
+    int fin = D;
+    for (int l = 0; l < L; ++l) {
+        tr->woff[l] = o;
+        o += (long long)H * fin;
+        tr->boff[l] = o;
+        o += H;
+        fin = H;
+    }
+    tr->ooff = o;
+    o += H + 1;
+    tr->P = (int)o;
+    const long long nP = (long long)M * tr->P;
+    const long long smH = (long long)B * H, smD = (long long)B * D, smC = (long long)B * C;
+    // activations: U, G0, GB0 [M][B][D]; SB, MFB [M][B][C]; per layer T, Hh (resnet), G, Dl, GB, TB, ZB, HB
+    const long long per_layer = (desc->resnet ? 8 : 7) * smH;
+    const long long nact = (long long)M * (3 * smD + 2 * smC + L * per_layer);
+    bool ok = cudaMalloc(&tr->w, sizeof(float) * 4 * nP) == cudaSuccess;
+    ok = ok && cudaMalloc(&tr->act, sizeof(float) * nact) == cudaSuccess;
+    ok = ok && cudaMalloc(&tr->dbad, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        rid_trainer_destroy(tr);
+        return rid_fail(RID_ERR_OOM, "trainer: device allocation failed");
+    }
+    tr->am = tr->w + nP;
+    tr->av = tr->am + nP;
+    tr->grad = tr->av + nP;
+    float* p = tr->act;
+    auto take = [&](long long per_member) { float* r = p; p += M * per_member; return r; };
+    tr->U = take(smD);
+    tr->G0 = take(smD);
+    tr->GB0 = take(smD);
+    tr->SB = take(smC);
+    tr->MFB = take(smC);
+    for (int l = 0; l < L; ++l) {
+        tr->T[l] = take(smH);
+        tr->Hh[l] = desc->resnet ? take(smH) : tr->T[l];
+        tr->G[l] = take(smH);
+        tr->Dl[l] = take(smH);
+        tr->GB[l] = take(smH);
+        tr->TB[l] = take(smH);
+        tr->ZB[l] = take(smH);
+        tr->HB[l] = take(smH);
+    }
+    if (cudaMemcpy(tr->w, weights, sizeof(float) * nP, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(tr->am, 0, sizeof(float) * 3 * nP) != cudaSuccess || cudaMemset(tr->act, 0, sizeof(float) * nact) != cudaSuccess ||
+        cudaMemset(tr->dbad, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        rid_trainer_destroy(tr);
+        return rid_fail(RID_ERR_CUDA, "trainer: initial copy failed");
+    }
+    *out = tr;
+    return RID_OK;
+}
+
+RID_API int rid_trainer_destroy(rid_trainer* tr) {
+    if (!tr) return RID_OK;
+    cudaFree(tr->w);
+    cudaFree(tr->act);
+    cudaFree(tr->dbad);
+    cudaFree(tr->ds);
+    cudaFree(tr->didx);
+    cudaFree(tr->dloss);
+    delete tr;
+    return RID_OK;
+}
+
+RID_API int rid_trainer_set_data(rid_trainer* tr, int32_t n, const float* s, const float* mf, int32_t mem, void* stream) {
+    if (!tr || !s || !mf || n < 1) return rid_fail(RID_ERR_ARG, "trainer: bad data arguments");
+    if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return rid_fail(RID_ERR_ARG, "trainer: bad mem");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int C = tr->d.n_cv;
+    if (n > tr->cap_data) {
+        cudaFree(tr->ds);
+        tr->ds = nullptr;
+        tr->cap_data = 0;
+        if (cudaMalloc(&tr->ds, sizeof(float) * 2 * (size_t)n * C) != cudaSuccess) {
+            cudaGetLastError();
+            return rid_fail(RID_ERR_OOM, "trainer: data allocation failed");
+        }
+        tr->cap_data = n;
+    }
+    tr->dmf = tr->ds + (size_t)tr->cap_data * C;
+    tr->n_data = n;
+    if (int rc = tr_copy_in(tr->ds, s, sizeof(float) * (size_t)n * C, mem, st)) return rc;
+    if (int rc = tr_copy_in(tr->dmf, mf, sizeof(float) * (size_t)n * C, mem, st)) return rc;
+    TCK(cudaStreamSynchronize(st));
+    return RID_OK;
+}
+
+RID_API int rid_trainer_grad(rid_trainer* tr, const int32_t* idx, float* loss_out, float* grad_out, int32_t mem,
+                             void* stream) {
+    if (!tr || !idx) return rid_fail(RID_ERR_ARG, "trainer: NULL argument");
+    if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return rid_fail(RID_ERR_ARG, "trainer: bad mem");
+    if (tr->n_data < 1) return rid_fail(RID_ERR_STATE, "trainer: no data set");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int M = tr->d.n_models, B = tr->d.batch_size;
+    if (int rc = grow((void**)&tr->didx, &tr->cap_idx, (long long)M * B, sizeof(int))) return rc;
+    if (int rc = grow((void**)&tr->dloss, &tr->cap_loss, M, sizeof(float))) return rc;
+    if (int rc = tr_copy_in(tr->didx, idx, sizeof(int) * (size_t)M * B, mem, st)) return rc;
+    if (int rc = tr_gradient(tr, tr->didx, tr->dloss, st)) return rc;
+    TCK(cudaGetLastError());
+    if (loss_out)
+        if (int rc = tr_copy_out(loss_out, tr->dloss, sizeof(float) * M, mem, st)) return rc;
+    if (grad_out)
+        if (int rc = tr_copy_out(grad_out, tr->grad, sizeof(float) * (size_t)M * tr->P, mem, st)) return rc;
+    return tr_finish(tr, st);
+}
+
+RID_API int rid_trainer_run(rid_trainer* tr, int32_t n_steps, const int32_t* idx, float* loss_out, int32_t mem,
+                            void* stream) {
+    if (!tr || !idx || n_steps < 0) return rid_fail(RID_ERR_ARG, "trainer: bad run arguments");
+    if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return rid_fail(RID_ERR_ARG, "trainer: bad mem");
+    if (tr->n_data < 1) return rid_fail(RID_ERR_STATE, "trainer: no data set");
+    if (n_steps == 0) return RID_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const rid_train_desc& d = tr->d;
+    const int M = d.n_models, B = d.batch_size;
+    const long long per = (long long)M * B;
+    if (int rc = grow((void**)&tr->didx, &tr->cap_idx, per * n_steps, sizeof(int))) return rc;
+    if (int rc = grow((void**)&tr->dloss, &tr->cap_loss, (long long)M * n_steps, sizeof(float))) return rc;
+    if (int rc = tr_copy_in(tr->didx, idx, sizeof(int) * (size_t)(per * n_steps), mem, st)) return rc;
+    const long long nP = (long long)M * tr->P;
+    const int ablocks = (int)((nP + 255) / 256 < 2048 ? (nP + 255) / 256 : 2048);
+    for (int k = 0; k < n_steps; ++k) {
+        if (int rc = tr_gradient(tr, tr->didx + per * k, tr->dloss + (long long)M * k, st)) return rc;
+        const int64_t t = tr->steps + k;
+        const double lr = d.init_lr * std::pow(d.decay_rate, (double)t / (double)d.decay_steps);
+        const double c1 = 1.0 - std::pow(d.beta1, (double)(t + 1)), c2 = 1.0 - std::pow(d.beta2, (double)(t + 1));
+        k_tr_adam<<<ablocks, 256, 0, st>>>(tr->w, tr->am, tr->av, tr->grad, nP, (float)lr, (float)d.beta1,
+                                           (float)d.beta2, (float)d.adam_eps, (float)c1, (float)c2);
+    }
+    TCK(cudaGetLastError());
+    if (loss_out)
+        if (int rc = tr_copy_out(loss_out, tr->dloss, sizeof(float) * (size_t)M * n_steps, mem, st)) return rc;
+    const int rc = tr_finish(tr, st);
+    if (rc == RID_OK) tr->steps += n_steps;
+    return rc;
+}
+
+RID_API int rid_trainer_weights(rid_trainer* tr, float* weights_out, int64_t* steps_done, int32_t mem, void* stream) {
+    if (!tr) return rid_fail(RID_ERR_ARG, "trainer: NULL argument");
+    if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return rid_fail(RID_ERR_ARG, "trainer: bad mem");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (weights_out)
+        if (int rc = tr_copy_out(weights_out, tr->w, sizeof(float) * (size_t)tr->d.n_models * tr->P, mem, st)) return rc;
+    if (steps_done) *steps_done = tr->steps;
+    TCK(cudaStreamSynchronize(st));
+    return RID_OK;
+}
+
+}  // extern "C"

@@ -26,7 +26,9 @@ EXPORTS = ("rid_version", "rid_status_string", "rid_last_error", "rid_create_sys
            "rid_set_ensemble", "rid_explore", "rid_label", "rid_eval_forces", "rid_pair_mask", "rid_philox",
            "rid_walkers_load", "rid_walkers_advance", "rid_walkers_read", "rid_profile_enable",
            "rid_profile_read", "rid_launch_count", "rid_ensemble_grad_noalloc", "rid_server_create",
-           "rid_server_destroy", "rid_label_batch", "rid_submit", "rid_poll", "rid_server_load")
+           "rid_server_destroy", "rid_label_batch", "rid_submit", "rid_poll", "rid_server_load",
+           "rid_trainer_create", "rid_trainer_destroy", "rid_trainer_set_data", "rid_trainer_run",
+           "rid_trainer_grad", "rid_trainer_weights")
 RID_NOT_READY = 6
 RID_JOB_LABEL, RID_JOB_EXPLORE = 1, 2
 
@@ -50,6 +52,13 @@ class EnsembleDesc(C.Structure):
     _fields_ = [("n_models", C.c_int32), ("n_in", C.c_int32), ("n_layers", C.c_int32), ("width", C.c_int32),
                 ("resnet", C.c_int32), ("precision", C.c_int32), ("trust_lo", C.c_double),
                 ("trust_hi", C.c_double), ("weights", C.POINTER(C.c_float))]
+
+
+class TrainDesc(C.Structure):
+    _fields_ = [("n_models", C.c_int32), ("n_cv", C.c_int32), ("n_layers", C.c_int32), ("width", C.c_int32),
+                ("resnet", C.c_int32), ("batch_size", C.c_int32), ("init_lr", C.c_double),
+                ("decay_rate", C.c_double), ("decay_steps", C.c_int32), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("adam_eps", C.c_double)]
 
 
 class LabelJob(C.Structure):
@@ -110,6 +119,12 @@ def lib() -> C.CDLL:
     L.rid_poll.argtypes = [vp, u64, C.POINTER(JobInfo)]
     L.rid_server_load.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(u64)]
     L.rid_launch_count.restype = i64
+    L.rid_trainer_create.argtypes = [C.POINTER(TrainDesc), vp, C.POINTER(vp)]
+    L.rid_trainer_destroy.argtypes = [vp]
+    L.rid_trainer_set_data.argtypes = [vp, i32, vp, vp, i32, vp]
+    L.rid_trainer_run.argtypes = [vp, i32, vp, vp, i32, vp]
+    L.rid_trainer_grad.argtypes = [vp, vp, vp, vp, i32, vp]
+    L.rid_trainer_weights.argtypes = [vp, vp, C.POINTER(i64), i32, vp]
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype or C.c_int
     _lib = L
@@ -456,3 +471,73 @@ def ensemble_grad_noalloc(s, weights, n_models, n_layers, width, grad_out, value
 
 def version() -> int:
     return lib().rid_version()
+
+
+# ---------------------------------------------------------------------------
+class Trainer:
+    """Fits an ensemble to mean-force labels on the current CUDA device (wraps
+    rid_trainer*): per member, Adam steps on the mean squared difference
+    between dA_i/ds and the labels, learning rate init_lr * decay_rate^(t /
+    decay_steps).  Weights use the packed layout of EnsembleParams.weights."""
+
+    def __init__(self, n_models, n_cv, n_layers, width, weights, batch_size=128, resnet=False, init_lr=8e-4,
+                 decay_rate=0.96, decay_steps=120, beta1=0.9, beta2=0.999, adam_eps=1e-8):
+        L = lib()
+        self.M, self.C, self.B = int(n_models), int(n_cv), int(batch_size)
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        self.P = w.size // self.M
+        d = TrainDesc(self.M, self.C, int(n_layers), int(width), int(bool(resnet)), self.B, float(init_lr),
+                      float(decay_rate), int(decay_steps), float(beta1), float(beta2), float(adam_eps))
+        h = C.c_void_p()
+        _check(L.rid_trainer_create(C.byref(d), w.ctypes.data, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rid_trainer_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_data(self, s, mf, stream=None):
+        a = _Args()
+        n = int(s.shape[0])
+        ps = a.ptr(s, np.float32, (n, self.C))
+        pm = a.ptr(mf, np.float32, (n, self.C))
+        _check(lib().rid_trainer_set_data(self.h, n, ps, pm, a.mem, _stream_ptr(stream)))
+
+    def run(self, idx, loss_out=None, stream=None):
+        """idx [n_steps][M][B] int32 batch indices; loss_out [n_steps][M] float32."""
+        a = _Args()
+        n = int(idx.shape[0])
+        pi = a.ptr(idx, np.int32, (n, self.M, self.B))
+        pl = a.ptr(loss_out, np.float32, (n, self.M), True)
+        _check(lib().rid_trainer_run(self.h, n, pi, pl, a.mem, _stream_ptr(stream)))
+
+    def grad(self, idx, loss_out=None, grad_out=None, stream=None):
+        a = _Args()
+        pi = a.ptr(idx, np.int32, (self.M, self.B))
+        pl = a.ptr(loss_out, np.float32, (self.M,), True)
+        pg = a.ptr(grad_out, np.float32, (self.M, self.P), True)
+        _check(lib().rid_trainer_grad(self.h, pi, pl, pg, a.mem, _stream_ptr(stream)))
+
+    def weights(self, out=None, stream=None):
+        """Current weights [M][P] (float32, host unless `out` is a CUDA tensor)
+        and the number of steps taken."""
+        if out is None:
+            out = np.empty((self.M, self.P), dtype=np.float32)
+        a = _Args()
+        po = a.ptr(out, np.float32, (self.M, self.P), True)
+        steps = C.c_int64(0)
+        _check(lib().rid_trainer_weights(self.h, po, C.byref(steps), a.mem, _stream_ptr(stream)))
+        return out, steps.value
