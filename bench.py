@@ -242,6 +242,61 @@ def run_batching(rid, n_jobs, n_steps, plain_jobs, seed=3):
             "speedup_vs_plain": (wsteps / dt) / (ws_plain / t_plain)}
 
 
+def train_flops_per_sample(D, L, H):
+    """Algorithmic FP32 flops of one training sample of one member: forward,
+    input gradient and its adjoint 2F each, the pass back through the forward
+    layers 2 (L - 1) H^2, and the two outer products of the weight gradient 4F,
+    with F = D H + (L - 1) H^2 multiply-adds per pass."""
+    F = D * H + (L - 1) * H * H
+    return 10 * F + 2 * (L - 1) * H * H
+
+
+def run_training(rid, torch, steps, seed=11):
+    """Ensemble training on mean-force labels (rid_trainer_run) for the
+    exploration model of the 200-bead workload: 4 members 40-256x4-1, batch
+    128 per member, labels = the CV gradient of a teacher network at points on
+    the CV torus."""
+    wl = I.workload(WORKLOAD)
+    M, C, L, H, B = wl["n_models"], wl["n_cv"], wl["n_layers"], wl["width"], 128
+    D = 2 * C
+    n = 16384
+    student = I.make_ensemble(M, D, L, H, seed)
+    teacher = I.make_ensemble(1, D, L, H, seed + 1)
+    rng = np.random.default_rng(seed)
+    s = torch.from_numpy(rng.uniform(-np.pi, np.pi, size=(n, C)).astype(np.float32)).cuda()
+    mf = torch.zeros((1, n, C), dtype=torch.float32, device="cuda")
+    tw = torch.from_numpy(teacher.weights).cuda()
+    for c0 in range(0, n, 1024):
+        rid.ensemble_grad_noalloc(s[c0:c0 + 1024], tw, 1, L, H, mf[:, c0:c0 + 1024])
+    mf = mf[0].contiguous()
+    warm = 5
+    idx = torch.from_numpy(rng.integers(0, n, size=(warm + steps, M, B)).astype(np.int32)).cuda()
+    loss = torch.zeros((warm + steps, M), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    with rid.Trainer(M, C, L, H, student.weights, batch_size=B) as tr:
+        tr.set_data(s, mf, stream=stream)
+        tr.run(idx[:warm], loss[:warm], stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tr.run(idx[warm:], loss[warm:], stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lo = loss.cpu().numpy()
+    fl = train_flops_per_sample(D, L, H) * M * B
+    achieved = fl * steps / (ms * 1e-3) / 1e12
+    return {"workload": f"{M} members {D}-{H}x{L}-1, batch {B} per member, {n} labels (teacher CV gradients)",
+            "value": M * B * steps / (ms * 1e-3), "unit": "member-samples/s", "steps": steps,
+            "ms_per_step": ms / steps, "kernel_launches_per_step": 5 * L + 3,
+            "loss_first": float(lo[:warm].mean()), "loss_last": float(lo[-20:].mean()),
+            "algorithmic_gflop_per_step": fl / 1e9,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "peak_source": FP32_PEAK_NOTE},
+            "timed": "one rid_trainer_run call of all steps (device-resident labels and batch indices), "
+                     "CUDA events on the launching stream"}
+
+
 def run_serving(rid, n_req, rate, plain_req, seed=5):
     """Poisson stream of mixed labeling / exploration requests through the
     request loop (BF16 ensembles), and the first plain_req requests of the
@@ -485,6 +540,8 @@ def main():
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-training", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=400)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -633,6 +690,8 @@ def main():
         out["batching"] = run_batching(rid, args.batch_jobs, args.batch_steps, args.batch_plain_jobs)
     if rank == 0 and world == 1 and not args.no_precision:
         out["precision"] = run_precision(rid, torch)
+    if rank == 0 and world == 1 and not args.no_training:
+        out["training"] = run_training(rid, torch, args.train_steps)
     if rank == 0 and world == 1 and not args.no_serving:
         out["serving"] = run_serving(rid, args.serve_requests, args.serve_rate, args.serve_plain_requests)
     if rank == 0:

@@ -32,10 +32,11 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // Batched FP32 GEMM: C[i][j] = sum over up to two K segments of A(i, k) B(k, j)
-// with element (i, k) of A at A + i * si + k * sk (member offset z * sm), so
-// one kernel serves the N-N, N-T and T-N forms.  64 x 64 output tile, K tiles
-// of 16, 256 threads with 4 x 4 outputs each.
-constexpr int GT = 64, GK = 16, GTHREADS = 256;
+// (member offset z * sm), so one kernel serves the N-N, N-T and T-N forms.
+// 32 x 32 output tiles (the training GEMMs have 128-row batches, so small
+// tiles are what fills the SMs), K tiles of 32, 128 threads with 2 x 4
+// outputs each.
+constexpr int GT = 32, GK = 32, GTHREADS = 128;
 
 // A operand: element (i, k) at p + z sm + i si + k sk.  B operand: element
 // (k, j) at p + z sm + j si + k sk (si strides the output column).
@@ -81,49 +82,65 @@ __device__ __forceinline__ float ldop(const Operand& o, int z, int r, int k) {
 
 template <int EPI>
 __global__ void __launch_bounds__(GTHREADS) k_tr_gemm(GemmArgs g) {
-    __shared__ float As[GK][GT + 4];
-    __shared__ float Bs[GK][GT + 4];
+    __shared__ __align__(16) float As[GK][GT + 4];
+    __shared__ __align__(16) float Bs[GK][GT + 4];
     const int z = blockIdx.z, i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    float acc[4][4] = {};
-    for (int sidx = 0; sidx < g.nseg; ++sidx) {
+    const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;   // rows 2 ty .. +1, columns 4 tx .. +3
+    float acc[2][4] = {};
+    // K tiles of both segments in one sequence; the next tile's elements are
+    // loaded into registers while the current one is multiplied
+    const int nt0 = (g.seg[0].K + GK - 1) / GK;
+    const int nt = nt0 + (g.nseg > 1 ? (g.seg[1].K + GK - 1) / GK : 0);
+    constexpr int PER = GT * GK / GTHREADS;
+    float ra[PER], rb[PER];
+    auto fetch = [&](int t) {
+        const int sidx = t < nt0 ? 0 : 1;
         const Seg& S = g.seg[sidx];
+        const int k0 = (t - (sidx ? nt0 : 0)) * GK;
         const bool a_kfast = S.a.sk == 1;   // A row-major along K: threads walk K
         const bool b_jfast = S.b.si == 1;   // B (k, j) with j contiguous: threads walk j
-        for (int k0 = 0; k0 < S.K; k0 += GK) {
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int idx = tid + GTHREADS * r;
-                int ii, kk;
-                if (a_kfast) { ii = idx >> 4; kk = idx & 15; }
-                else { kk = idx >> 6; ii = idx & 63; }
-                const int gi = i0 + ii, gk = k0 + kk;
-                As[kk][ii] = (gi < g.rows && gk < S.K) ? ldop(S.a, z, gi, gk) : 0.0f;
-                int jj, kb;
-                if (b_jfast) { kb = idx >> 6; jj = idx & 63; }
-                else { jj = idx >> 4; kb = idx & 15; }
-                const int gj = j0 + jj, gkb = k0 + kb;
-                // B operand: element (k, j) at p + j * si + k * sk
-                Bs[kb][jj] = (gj < g.cols && gkb < S.K) ? ldop(S.b, z, gj, gkb) : 0.0f;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int kk = 0; kk < GK; ++kk) {
-                const float4 a = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-                const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-                for (int p = 0; p < 4; ++p)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
-            }
-            __syncthreads();
+        for (int r = 0; r < PER; ++r) {
+            const int idx = tid + GTHREADS * r;
+            const int hi = idx >> 5, lo = idx & 31;
+            const int gi = i0 + (a_kfast ? hi : lo), gk = k0 + (a_kfast ? lo : hi);
+            ra[r] = (gi < g.rows && gk < S.K) ? ldop(S.a, z, gi, gk) : 0.0f;
+            const int gj = j0 + (b_jfast ? lo : hi), gkb = k0 + (b_jfast ? hi : lo);
+            rb[r] = (gj < g.cols && gkb < S.K) ? ldop(S.b, z, gj, gkb) : 0.0f;
         }
+    };
+    auto stash = [&](int t) {
+        const Seg& S = g.seg[t < nt0 ? 0 : 1];
+        const bool a_kfast = S.a.sk == 1, b_jfast = S.b.si == 1;
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int idx = tid + GTHREADS * r;
+            const int hi = idx >> 5, lo = idx & 31;
+            As[a_kfast ? lo : hi][a_kfast ? hi : lo] = ra[r];
+            Bs[b_jfast ? hi : lo][b_jfast ? lo : hi] = rb[r];
+        }
+    };
+    if (nt > 0) fetch(0);
+    for (int t = 0; t < nt; ++t) {
+        stash(t);
+        __syncthreads();
+        if (t + 1 < nt) fetch(t + 1);
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            const float2 a = *reinterpret_cast<const float2*>(&As[kk][ty * 2]);
+            const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+            const float av[2] = {a.x, a.y}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+        }
+        __syncthreads();
     }
     const EpiArgs& e = g.e;
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const int i = i0 + ty * 4 + p;
+    for (int p = 0; p < 2; ++p) {
+        const int i = i0 + ty * 2 + p;
         if (i >= g.rows) continue;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
