@@ -1,0 +1,103 @@
+"""FP64 CPU oracle for the MCMC dimension reduction of the trained ensemble.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests -- never by the product path.
+It shares no code with the CUDA library; the random numbers come from the
+oracle's own Philox4x32-10 / Box-Muller (``oracle.philox``, ``oracle.normals``).
+
+What it computes (Sec. "Dimension reduction phase"; Introduction, automatic
+PMF calculation): W walkers run Metropolis Monte Carlo in CV space on the
+ensemble-mean free energy Abar(s) = (1/M) sum_i A_i(s) at temperature kT, and
+the visited CVs are projected onto one histogram per CV and one 2-D histogram
+of a chosen CV pair (bins per dimension over [-pi, pi)); the projected PMF is
+-kT ln(count / total), shifted to a zero minimum.
+
+Readings (the paper names the parameters, not the move):
+  proposal  s'_c = wrap(s_c + step_size * xi_c), xi from Philox counter
+            (c // 3, walker, step, 2), normal c % 3 of the three Box-Muller
+            normals of that counter (the MD noise mapping);
+  accept    iff kT ln u + (Abar(s') - Abar(s)) < 0, u = (x + 1/2) 2^-32 from
+            word 0 of counter (0, walker, step, 3);
+  counting  after every step t >= n_burn, every walker's current state;
+  bins      floor((s + pi) / (2 pi) * bins), clamped to [0, bins - 1];
+  wrap      d - 2 pi floor(d / (2 pi) + 1/2).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import oracle
+from oracle import train as T
+
+
+def wrap(d):
+    return d - 2.0 * math.pi * np.floor(d / (2.0 * math.pi) + 0.5)
+
+
+def ensemble_mean_value(weights, D, L, H, resnet, s):
+    """Abar at points s [W][C] (float64), members' forward passes as matmuls."""
+    u = T.features(s)
+    tot = np.zeros(s.shape[0])
+    for w in np.asarray(weights, dtype=np.float64):
+        layers, w_out, b_out = T.unpack(w, D, L, H)
+        h = u
+        for l, (W, b) in enumerate(layers):
+            t = np.tanh(h @ W.T + b)
+            h = t + h if (resnet and l >= 1) else t
+        tot += h @ w_out + b_out[0]
+    return tot / len(weights)
+
+
+def proposal_normals(W, C, step, seed):
+    nk = (C + 2) // 3
+    ctr = np.array([[k, w, step, 2] for w in range(W) for k in range(nk)], dtype=np.uint32)
+    return oracle.normals(ctr, seed).reshape(W, 3 * nk)[:, :C]
+
+
+def accept_log_u(W, step, seed):
+    ctr = np.array([[0, w, step, 3] for w in range(W)], dtype=np.uint32)
+    x = oracle.philox(ctr, seed)[:, 0].astype(np.float64)
+    return np.log((x + 0.5) * 2.0 ** -32)
+
+
+def bin_index(s, bins):
+    b = np.floor((np.asarray(s, dtype=np.float64) + math.pi) / (2.0 * math.pi) * bins).astype(np.int64)
+    return np.clip(b, 0, bins - 1)
+
+
+def run(weights, C, L, H, resnet, s0, n_steps, n_burn, kT, step_size, seed, bins, pair):
+    """Returns dict(s, A, n_accepted, hist1 [C][bins], hist2 [bins][bins],
+    min_margin [W]): min_margin is each walker's smallest |kT ln u + dA| over
+    the run (how close its closest accept decision came to the threshold)."""
+    D = 2 * C
+    s = np.array(s0, dtype=np.float64)
+    W = s.shape[0]
+    A = ensemble_mean_value(weights, D, L, H, resnet, s)
+    hist1 = np.zeros((C, bins), dtype=np.int64)
+    hist2 = np.zeros((bins, bins), dtype=np.int64)
+    n_acc = 0
+    min_margin = np.full(W, np.inf)
+    for t in range(n_steps):
+        sp = wrap(s + step_size * proposal_normals(W, C, t, seed))
+        Ap = ensemble_mean_value(weights, D, L, H, resnet, sp)
+        margin = kT * accept_log_u(W, t, seed) + (Ap - A)
+        acc = margin < 0.0
+        min_margin = np.minimum(min_margin, np.abs(margin))
+        s[acc] = sp[acc]
+        A[acc] = Ap[acc]
+        n_acc += int(acc.sum())
+        if t >= n_burn:
+            b = bin_index(s, bins)
+            for c in range(C):
+                hist1[c] += np.bincount(b[:, c], minlength=bins)
+            np.add.at(hist2, (b[:, pair[0]], b[:, pair[1]]), 1)
+    return dict(s=s, A=A, n_accepted=n_acc, hist1=hist1, hist2=hist2, min_margin=min_margin)
+
+
+def projected_pmf(hist, kT):
+    """-kT ln(count / total) shifted to a zero minimum; +inf for empty bins."""
+    h = np.asarray(hist, dtype=np.float64)
+    with np.errstate(divide="ignore"):
+        f = -kT * np.log(h / h.sum())
+    return f - f[np.isfinite(f)].min()

@@ -26,165 +26,9 @@
 #include <cmath>
 #include <vector>
 
-#include "rid_internal.cuh"
+#include "rid_gemm.cuh"
 
 namespace {
-
-// ---------------------------------------------------------------------------
-// Batched FP32 GEMM: C[i][j] = sum over up to two K segments of A(i, k) B(k, j)
-// (member offset z * sm), so one kernel serves the N-N, N-T and T-N forms.
-// 32 x 32 output tiles (the training GEMMs have 128-row batches, so small
-// tiles are what fills the SMs), K tiles of 32, 128 threads with 2 x 4
-// outputs each.
-constexpr int GT = 32, GK = 32, GTHREADS = 128;
-
-// A operand: element (i, k) at p + z sm + i si + k sk.  B operand: element
-// (k, j) at p + z sm + j si + k sk (si strides the output column).
-struct Operand {
-    const float* p;
-    long long si, sk, sm;
-};
-struct Seg {
-    Operand a, b;
-    int K;
-};
-
-enum Epi { EPI_STORE = 0, EPI_FWD = 1, EPI_BWD = 2, EPI_ADJ = 3, EPI_BACK = 4 };
-
-// Activation tensors are [M][B][X] row-major: element (m, b, x) at
-// m * B * X + b * X + x.  The epilogue pointers below follow that layout
-// with the row stride ld of the GEMM's output width.
-struct EpiArgs {
-    float* out;        // primary output [M][rows][ld]
-    long long out_sm;  // member stride of out
-    int ld;            // row stride of out (= N)
-    // forward: bias b_l, T_l out, h_l out, h_{l-1} in (residual), w_out (last layer: G, D out)
-    const float* bias; long long bias_sm;
-    float* T; float* Hout; const float* Hin; const float* wout; long long w_sm;
-    float* Gout; float* Dout;
-    // backward / adjoint / back: residual input, T of the layer, second outputs
-    const float* res; const float* Tl; const float* Gl; float* out2; const float* tb; float* out3;
-    long long act_sm;  // member stride of the [rows][ld] activations
-    int resid;         // r_l
-    int last;          // forward / adjoint on the last layer
-};
-
-struct GemmArgs {
-    Seg seg[2];
-    int nseg;
-    int rows, cols;
-    EpiArgs e;
-};
-
-__device__ __forceinline__ float ldop(const Operand& o, int z, int r, int k) {
-    return o.p[(long long)z * o.sm + (long long)r * o.si + (long long)k * o.sk];
-}
-
-template <int EPI>
-__global__ void __launch_bounds__(GTHREADS) k_tr_gemm(GemmArgs g) {
-    __shared__ __align__(16) float As[GK][GT + 4];
-    __shared__ __align__(16) float Bs[GK][GT + 4];
-    const int z = blockIdx.z, i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
-    const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;   // rows 2 ty .. +1, columns 4 tx .. +3
-    float acc[2][4] = {};
-    // K tiles of both segments in one sequence; the next tile's elements are
-    // loaded into registers while the current one is multiplied
-    const int nt0 = (g.seg[0].K + GK - 1) / GK;
-    const int nt = nt0 + (g.nseg > 1 ? (g.seg[1].K + GK - 1) / GK : 0);
-    constexpr int PER = GT * GK / GTHREADS;
-    float ra[PER], rb[PER];
-    auto fetch = [&](int t) {
-        const int sidx = t < nt0 ? 0 : 1;
-        const Seg& S = g.seg[sidx];
-        const int k0 = (t - (sidx ? nt0 : 0)) * GK;
-        const bool a_kfast = S.a.sk == 1;   // A row-major along K: threads walk K
-        const bool b_jfast = S.b.si == 1;   // B (k, j) with j contiguous: threads walk j
-#pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int idx = tid + GTHREADS * r;
-            const int hi = idx >> 5, lo = idx & 31;
-            const int gi = i0 + (a_kfast ? hi : lo), gk = k0 + (a_kfast ? lo : hi);
-            ra[r] = (gi < g.rows && gk < S.K) ? ldop(S.a, z, gi, gk) : 0.0f;
-            const int gj = j0 + (b_jfast ? lo : hi), gkb = k0 + (b_jfast ? hi : lo);
-            rb[r] = (gj < g.cols && gkb < S.K) ? ldop(S.b, z, gj, gkb) : 0.0f;
-        }
-    };
-    auto stash = [&](int t) {
-        const Seg& S = g.seg[t < nt0 ? 0 : 1];
-        const bool a_kfast = S.a.sk == 1, b_jfast = S.b.si == 1;
-#pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int idx = tid + GTHREADS * r;
-            const int hi = idx >> 5, lo = idx & 31;
-            As[a_kfast ? lo : hi][a_kfast ? hi : lo] = ra[r];
-            Bs[b_jfast ? hi : lo][b_jfast ? lo : hi] = rb[r];
-        }
-    };
-    if (nt > 0) fetch(0);
-    for (int t = 0; t < nt; ++t) {
-        stash(t);
-        __syncthreads();
-        if (t + 1 < nt) fetch(t + 1);
-#pragma unroll
-        for (int kk = 0; kk < GK; ++kk) {
-            const float2 a = *reinterpret_cast<const float2*>(&As[kk][ty * 2]);
-            const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-            const float av[2] = {a.x, a.y}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-            for (int p = 0; p < 2; ++p)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
-        }
-        __syncthreads();
-    }
-    const EpiArgs& e = g.e;
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int i = i0 + ty * 2 + p;
-        if (i >= g.rows) continue;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int j = j0 + tx * 4 + q;
-            if (j >= g.cols) continue;
-            const long long o = (long long)z * e.act_sm + (long long)i * e.ld + j;
-            const float a = acc[p][q];
-            if (EPI == EPI_STORE) {
-                e.out[(long long)z * e.out_sm + (long long)i * e.ld + j] = a;
-            } else if (EPI == EPI_FWD) {
-                const float t = tanhf(a + e.bias[(long long)z * e.bias_sm + j]);
-                e.T[o] = t;
-                if (e.Hout != e.T) e.Hout[o] = e.resid ? t + e.Hin[o] : t;
-                if (e.last) {
-                    const float w = e.wout[(long long)z * e.w_sm + j];
-                    e.Gout[o] = w;
-                    e.Dout[o] = w * (1.0f - t * t);
-                }
-            } else if (EPI == EPI_BWD) {
-                // g_{l-1} = d_l W_l + r_l g_l; d_{l-1} = g_{l-1} (1 - t_{l-1}^2)
-                const float gv = e.resid ? a + e.res[o] : a;
-                e.out[o] = gv;
-                if (e.Dout) {
-                    const float t = e.Tl[o];
-                    e.Dout[o] = gv * (1.0f - t * t);
-                }
-            } else if (EPI == EPI_ADJ) {
-                // dbar = acc; gbar_l = dbar (1 - t^2) + r gbar_{l-1}; tbar = -2 t g dbar
-                const float t = e.Tl[o];
-                const float sp = 1.0f - t * t;
-                e.out[o] = e.resid ? a * sp + e.res[o] : a * sp;
-                const float tb = -2.0f * t * e.Gl[o] * a;
-                e.out2[o] = tb;
-                if (e.last) e.out3[o] = tb * sp;      // zbar_{L-1} (hbar_{L-1} = 0)
-            } else if (EPI == EPI_BACK) {
-                // hbar_{l-1} = zbar_l W_l + r hbar_l; zbar_{l-1} = (tbar + hbar)(1 - t^2)
-                const float hb = e.resid ? a + e.res[o] : a;
-                e.out[o] = hb;
-                const float t = e.Tl[o];
-                e.out3[o] = (e.tb[o] + hb) * (1.0f - t * t);
-            }
-        }
-    }
-}
 
 // u = (cos s, sin s) of each member's batch, plus the batch's s and labels.
 // idx is checked; an index outside [0, n) reads sample 0 and sets *bad.
@@ -323,16 +167,6 @@ int grow(void** p, long long* cap, long long need, size_t elem) {
     *cap = need;
     return RID_OK;
 }
-
-template <int EPI>
-void launch_gemm(const GemmArgs& g, int M, cudaStream_t st) {
-    dim3 grid((g.cols + GT - 1) / GT, (g.rows + GT - 1) / GT, M);
-    k_tr_gemm<EPI><<<grid, GTHREADS, 0, st>>>(g);
-}
-
-// Operand helpers over [M][rows][ld] activations and [M][P] packed weights.
-Operand act_rowmajor(const float* p, int ld, long long sm) { return Operand{p, (long long)ld, 1, sm}; }
-Operand act_transposed(const float* p, int ld, long long sm) { return Operand{p, 1, (long long)ld, sm}; }
 
 // One step's gradient into tr->grad and the per-member loss into loss[M],
 // for the batch indices idx [M][B] (device).

@@ -1,0 +1,98 @@
+"""Pins of the MCMC oracle (oracle/mcmc.py) against things other than itself:
+the stationary marginals of exp(-Abar / kT) integrated on a fine grid of the
+CV torus (1-D and 2-D), and the limiting cases of the Metropolis rule (a flat
+free energy accepts every move; at kT -> 0 only downhill moves are taken).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mcmc as MC
+from oracle import train as T
+
+
+def _net(D, L, H, seed, scale):
+    rng = np.random.default_rng(seed)
+    w = rng.normal(0.0, 1.0, size=(1, T.param_count(D, L, H)))
+    return w * scale
+
+
+def _exact_bin_probs(weights, C, L, H, bins, kT, sub=24):
+    # p(s) ~ exp(-Abar(s)/kT) on a (bins * sub)^C midpoint grid, summed per bin
+    n = bins * sub
+    g = -math.pi + (np.arange(n) + 0.5) * (2 * math.pi / n)
+    grids = np.meshgrid(*([g] * C), indexing="ij")
+    s = np.stack([x.ravel() for x in grids], axis=1)
+    A = MC.ensemble_mean_value(weights, 2 * C, L, H, False, s)
+    p = np.exp(-(A - A.min()) / kT).reshape([n] * C)
+    p /= p.sum()
+    for ax in range(C):
+        p = np.add.reduceat(p, np.arange(0, n, sub), axis=ax)
+    return p, A.max() - A.min()
+
+
+def test_one_cv_histogram_matches_the_stationary_marginal():
+    C, L, H, bins, kT = 1, 2, 8, 16, 1.0
+    w = _net(2 * C, L, H, 3, 0.9)
+    p, span = _exact_bin_probs(w, C, L, H, bins, kT)
+    assert span > 2.0 * kT                      # a landscape the rule must follow
+    rng = np.random.default_rng(3)
+    s0 = rng.uniform(-math.pi, math.pi, size=(200, C))
+    r = MC.run(w, C, L, H, False, s0, 600, 100, kT, 0.8, 11, bins, (0, 0))
+    h = r["hist1"][0]
+    assert h.sum() == 200 * 500
+    tv = 0.5 * np.abs(h / h.sum() - p).sum()
+    assert tv < 0.04, tv
+    # the inverted landscape is far off: the pin separates the sign of the rule
+    q, _ = _exact_bin_probs(-w, C, L, H, bins, kT)
+    assert 0.5 * np.abs(h / h.sum() - q).sum() > 0.2
+
+
+def test_two_cv_joint_histogram_matches_the_stationary_joint():
+    C, L, H, bins, kT = 2, 2, 8, 12, 1.0
+    w = _net(2 * C, L, H, 2, 0.7)
+    p, span = _exact_bin_probs(w, C, L, H, bins, kT, sub=12)
+    assert span > 2.0 * kT
+    rng = np.random.default_rng(4)
+    s0 = rng.uniform(-math.pi, math.pi, size=(400, C))
+    r = MC.run(w, C, L, H, False, s0, 500, 100, kT, 0.9, 12, bins, (0, 1))
+    h2 = r["hist2"]
+    assert h2.sum() == 400 * 400
+    tv = 0.5 * np.abs(h2 / h2.sum() - p).sum()
+    assert tv < 0.06, tv
+    # the 1-D histograms are the joint's marginals
+    np.testing.assert_array_equal(r["hist1"][0], h2.sum(axis=1))
+    np.testing.assert_array_equal(r["hist1"][1], h2.sum(axis=0))
+
+
+def test_flat_free_energy_accepts_every_move():
+    C, L, H = 3, 2, 4
+    w = np.zeros((2, T.param_count(2 * C, L, H)))
+    w[:, -1] = 1.5                                  # b_out only
+    s0 = np.zeros((16, C))
+    r = MC.run(w, C, L, H, False, s0, 20, 0, 1.0, 0.5, 5, 8, (0, 1))
+    assert r["n_accepted"] == 16 * 20
+
+
+def test_zero_temperature_takes_only_downhill_moves():
+    C, L, H = 2, 2, 6
+    w = _net(2 * C, L, H, 6, 0.8)
+    rng = np.random.default_rng(6)
+    s0 = rng.uniform(-math.pi, math.pi, size=(64, C))
+    A0 = MC.ensemble_mean_value(w, 2 * C, L, H, False, s0)
+    sp = MC.wrap(s0 + 0.7 * MC.proposal_normals(64, C, 0, 9))
+    Ap = MC.ensemble_mean_value(w, 2 * C, L, H, False, sp)
+    r = MC.run(w, C, L, H, False, s0, 1, 0, 1e-12, 0.7, 9, 8, (0, 1))
+    down = Ap < A0
+    assert r["n_accepted"] == int(down.sum())
+    np.testing.assert_allclose(r["s"][down], sp[down])
+    np.testing.assert_allclose(r["s"][~down], s0[~down])
+
+
+def test_binning_edges_and_projection():
+    b = MC.bin_index(np.array([-math.pi, -math.pi + 1e-12, 0.0, math.pi - 1e-12, math.pi]), 10)
+    np.testing.assert_array_equal(b, [0, 0, 5, 9, 9])
+    f = MC.projected_pmf(np.array([10, 0, 40, 50]), 2.0)
+    assert f[3] == 0.0 and math.isinf(f[1])
+    assert f[0] == pytest.approx(-2.0 * math.log(10 / 50))
