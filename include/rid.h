@@ -231,6 +231,48 @@ RID_API int rid_trainer_weights(rid_trainer* tr, float* weights_out, int64_t* st
                                 void* stream);
 
 /*
+ * MCMC dimension reduction (Sec. "Dimension reduction phase": numb_walkers,
+ * numb_steps, temperature, bins, proj_cv_index; Introduction, automatic PMF
+ * calculation).  W walkers run Metropolis Monte Carlo on the torus of C
+ * torsion CVs with the ensemble-mean free energy Abar(s) = (1/M) sum_i A_i(s)
+ * at temperature kT:
+ *   proposal  s' = wrap(s + step_size xi) per CV, xi = normal c % 3 of the
+ *             Box-Muller triple of Philox counter (c / 3, walker, step, 2);
+ *   accept    iff kT ln u + (Abar(s') - Abar(s)) < 0, u = (x + 1/2) 2^-32 with
+ *             x = word 0 of counter (0, walker, step, 3) (key = seed);
+ *   counting  from step n_burn on, each walker's current state after every
+ *             step goes into hist1 [C][bins] (one histogram per CV) and hist2
+ *             [bins][bins] (the pair proj_i, proj_j); bin =
+ *             floor((s + pi) / (2 pi) * bins) clamped to [0, bins - 1];
+ *   PMF       pmf = -kT ln(count / total) shifted to a zero minimum per
+ *             histogram (+inf where a bin is empty), float64.
+ * The ensemble is evaluated in FP32 (batched GEMMs).  s0 [W][C] holds the
+ * starting CVs (radians); every output may be NULL.  Synchronous on `stream`;
+ * device scratch is allocated for the call and released before it returns.
+ * Errors: RID_ERR_ARG, RID_ERR_OOM, RID_ERR_CUDA.
+ */
+typedef struct {
+    int32_t n_models;             /* M, 1..16                                   */
+    int32_t n_cv;                 /* C (inputs D = 2C), 1..128                  */
+    int32_t n_layers;             /* L, 1..8                                    */
+    int32_t width;                /* H, 1..512                                  */
+    int32_t resnet;               /* 0 / 1                                      */
+    const float* weights;         /* [M][P] packed as rid_ensemble_desc.weights,
+                                     host or device as `mem` says              */
+    int32_t n_walkers;            /* W (2000 in the paper)                      */
+    int64_t n_steps;              /* < 2^32                                     */
+    int64_t n_burn;               /* steps before counting starts               */
+    double kT;                    /* temperature in the energy unit of A        */
+    double step_size;             /* proposal standard deviation (radians)      */
+    uint64_t seed;                /* Philox key                                 */
+    int32_t bins;                 /* per CV, 1..4096 (101 in the paper)         */
+    int32_t proj_i, proj_j;       /* CV pair of the 2-D projection              */
+} rid_mcmc_desc;
+
+RID_API int rid_mcmc(const rid_mcmc_desc* desc, const float* s0, float* s_out, uint64_t* hist1, uint64_t* hist2,
+                     double* pmf1, double* pmf2, int64_t* n_accepted, int32_t mem, void* stream);
+
+/*
  * One force evaluation at given positions (no integration), through the same
  * kernels as a step.  bias = RID_BIAS_*; s0/kappa [W][C] are read only for
  * RID_BIAS_RESTRAINT.

@@ -28,7 +28,7 @@ EXPORTS = ("rid_version", "rid_status_string", "rid_last_error", "rid_create_sys
            "rid_profile_read", "rid_launch_count", "rid_ensemble_grad_noalloc", "rid_server_create",
            "rid_server_destroy", "rid_label_batch", "rid_submit", "rid_poll", "rid_server_load",
            "rid_trainer_create", "rid_trainer_destroy", "rid_trainer_set_data", "rid_trainer_run",
-           "rid_trainer_grad", "rid_trainer_weights")
+           "rid_trainer_grad", "rid_trainer_weights", "rid_mcmc")
 RID_NOT_READY = 6
 RID_JOB_LABEL, RID_JOB_EXPLORE = 1, 2
 
@@ -59,6 +59,13 @@ class TrainDesc(C.Structure):
                 ("resnet", C.c_int32), ("batch_size", C.c_int32), ("init_lr", C.c_double),
                 ("decay_rate", C.c_double), ("decay_steps", C.c_int32), ("beta1", C.c_double),
                 ("beta2", C.c_double), ("adam_eps", C.c_double)]
+
+
+class McmcDesc(C.Structure):
+    _fields_ = [("n_models", C.c_int32), ("n_cv", C.c_int32), ("n_layers", C.c_int32), ("width", C.c_int32),
+                ("resnet", C.c_int32), ("weights", C.c_void_p), ("n_walkers", C.c_int32), ("n_steps", C.c_int64),
+                ("n_burn", C.c_int64), ("kT", C.c_double), ("step_size", C.c_double), ("seed", C.c_uint64),
+                ("bins", C.c_int32), ("proj_i", C.c_int32), ("proj_j", C.c_int32)]
 
 
 class LabelJob(C.Structure):
@@ -125,6 +132,7 @@ def lib() -> C.CDLL:
     L.rid_trainer_run.argtypes = [vp, i32, vp, vp, i32, vp]
     L.rid_trainer_grad.argtypes = [vp, vp, vp, vp, i32, vp]
     L.rid_trainer_weights.argtypes = [vp, vp, C.POINTER(i64), i32, vp]
+    L.rid_mcmc.argtypes = [C.POINTER(McmcDesc), vp, vp, vp, vp, vp, vp, C.POINTER(i64), i32, vp]
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype or C.c_int
     _lib = L
@@ -150,7 +158,7 @@ class _Args:
         if hasattr(a, "data_ptr"):          # torch tensor
             import torch
             want = {np.float32: torch.float32, np.float64: torch.float64, np.uint32: torch.uint32,
-                    np.int32: torch.int32}[dtype]
+                    np.int32: torch.int32, np.uint64: torch.uint64}[dtype]
             if a.dtype != want:
                 raise TypeError(f"expected {want}, got {a.dtype}")
             if not a.is_contiguous():
@@ -541,3 +549,26 @@ class Trainer:
         steps = C.c_int64(0)
         _check(lib().rid_trainer_weights(self.h, po, C.byref(steps), a.mem, _stream_ptr(stream)))
         return out, steps.value
+
+
+def mcmc(weights, n_models, n_cv, n_layers, width, s0, n_steps, n_burn, kT, step_size, seed, bins=101,
+         pair=(0, 1), resnet=False, s_out=None, hist1=None, hist2=None, pmf1=None, pmf2=None, stream=None):
+    """MCMC dimension reduction (rid_mcmc): W = len(s0) walkers, Metropolis on
+    the ensemble-mean free energy; returns the number of accepted moves.
+    Outputs (optional, all on the side of s0): s_out [W][C] float32, hist1
+    [C][bins] and hist2 [bins][bins] uint64, pmf1 / pmf2 of the same shapes
+    float64."""
+    a = _Args()
+    W, Cn = int(s0.shape[0]), int(n_cv)
+    pw = a.ptr(weights, np.float32)
+    ps = a.ptr(s0, np.float32, (W, Cn))
+    po = a.ptr(s_out, np.float32, (W, Cn), True)
+    h1 = a.ptr(hist1, np.uint64, (Cn, bins), True)
+    h2 = a.ptr(hist2, np.uint64, (bins, bins), True)
+    f1 = a.ptr(pmf1, np.float64, (Cn, bins), True)
+    f2 = a.ptr(pmf2, np.float64, (bins, bins), True)
+    d = McmcDesc(int(n_models), Cn, int(n_layers), int(width), int(bool(resnet)), pw.value, W, int(n_steps),
+                 int(n_burn), float(kT), float(step_size), int(seed), int(bins), int(pair[0]), int(pair[1]))
+    nacc = C.c_int64(0)
+    _check(lib().rid_mcmc(C.byref(d), ps, po, h1, h2, f1, f2, C.byref(nacc), a.mem, _stream_ptr(stream)))
+    return nacc.value

@@ -1,0 +1,135 @@
+"""MCMC dimension reduction (rid_mcmc) against the FP64 MCMC oracle: walker
+trajectories step by step, exact integer counting and binning, the
+stationary 2-D marginal of a small landscape, the projected PMF, residual
+nets, host / device arguments and errors.
+
+Tolerances: both sides draw the same Philox numbers, so a walker's path is the
+same as long as every accept decision is: the FP32 free energy differs from
+the FP64 one by about 1e-6 relative, and a decision whose margin
+|kT ln u + dAbar| came within 1e-3 of zero on the oracle side may go either
+way (such walkers are excluded from the path comparison; there are few).
+Along a path, the CVs agree to 1e-4 rad (FP32 sums of up to 40 proposals).
+Bins are integer decisions taken from FP32 states; the counting test bins the
+GPU's own states with the same FP32 operations.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mcmc as MC
+from oracle import train as T
+from paper_2408_14070_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_2408_14070_gb300 import build, rid
+    build.build()
+    return rid
+
+
+def _wrapdiff(a, b):
+    d = np.asarray(a, np.float64) - np.asarray(b, np.float64)
+    return np.abs(d - 2 * math.pi * np.round(d / (2 * math.pi)))
+
+
+def _bins_f32(s, bins):
+    # floor((s + pi) * (1 / 2 pi) * bins), each operation rounded to FP32
+    t = (np.float32(s) + np.float32(math.pi)).astype(np.float32)
+    t = (t * np.float32(0.159154943091895)).astype(np.float32)
+    t = (t * np.float32(bins)).astype(np.float32)
+    return np.clip(np.floor(t).astype(np.int64), 0, bins - 1)
+
+
+@pytest.mark.parametrize("M,C,L,H,resnet,W,K", [(4, 20, 4, 256, False, 256, 30), (2, 3, 3, 40, True, 100, 40)])
+def test_trajectories_follow_the_oracle(R, M, C, L, H, resnet, W, K):
+    ens = I.make_ensemble(M, 2 * C, L, H, 31, resnet=resnet)
+    rng = np.random.default_rng(1)
+    s0 = rng.uniform(-math.pi, math.pi, size=(W, C)).astype(np.float32)
+    kT, step, seed, bins = 1.0, 0.25, 77, 101
+    s = np.zeros_like(s0)
+    nacc = R.mcmc(ens.weights, M, C, L, H, s0, K, 0, kT, step, seed, bins=bins, pair=(0, C - 1), resnet=resnet,
+                  s_out=s)
+    ref = MC.run(ens.weights, C, L, H, resnet, s0, K, 0, kT, step, seed, bins, (0, C - 1))
+    safe = ref["min_margin"] > 1e-3
+    print(f"\n[{M}x{H}x{L}] walkers with a near-threshold decision: {int((~safe).sum())} of {W}; "
+          f"accepted {nacc} (oracle {ref['n_accepted']})")
+    assert safe.mean() > 0.9
+    assert np.max(_wrapdiff(s[safe], ref["s"][safe])) < 1e-4
+    assert abs(nacc - ref["n_accepted"]) <= K * int((~safe).sum())
+    assert 0 < nacc < W * K                      # moves are taken and refused
+
+
+def test_counting_and_binning_are_exact(R):
+    M, C, L, H, W, K = 2, 5, 2, 32, 300, 7
+    ens = I.make_ensemble(M, 2 * C, L, H, 32)
+    s0 = np.random.default_rng(2).uniform(-math.pi, math.pi, size=(W, C)).astype(np.float32)
+    bins = 37
+    s = np.zeros_like(s0)
+    h1 = np.zeros((C, bins), np.uint64)
+    h2 = np.zeros((bins, bins), np.uint64)
+    f1 = np.zeros((C, bins))
+    f2 = np.zeros((bins, bins))
+    R.mcmc(ens.weights, M, C, L, H, s0, K, K - 1, 1.0, 0.6, 5, bins=bins, pair=(3, 1), s_out=s, hist1=h1, hist2=h2,
+           pmf1=f1, pmf2=f2)
+    b = _bins_f32(s, bins)                       # only the last step is counted: the final states
+    for c in range(C):
+        np.testing.assert_array_equal(h1[c], np.bincount(b[:, c], minlength=bins))
+    want2 = np.zeros((bins, bins), np.int64)
+    np.add.at(want2, (b[:, 3], b[:, 1]), 1)
+    np.testing.assert_array_equal(h2, want2)
+    for c in range(C):
+        np.testing.assert_allclose(f1[c], MC.projected_pmf(h1[c], 1.0), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(f2, MC.projected_pmf(h2, 1.0), rtol=1e-12, atol=1e-12)
+
+
+def test_joint_histogram_matches_the_stationary_marginal(R):
+    C, L, H, bins, kT = 2, 2, 8, 12, 1.0
+    rng = np.random.default_rng(2)
+    w = (rng.normal(0.0, 1.0, size=(1, T.param_count(2 * C, L, H))) * 0.7).astype(np.float32)
+    n = bins * 12
+    g = -math.pi + (np.arange(n) + 0.5) * (2 * math.pi / n)
+    gx, gy = np.meshgrid(g, g, indexing="ij")
+    A = MC.ensemble_mean_value(w, 2 * C, L, H, False, np.stack([gx.ravel(), gy.ravel()], 1))
+    p = np.exp(-(A - A.min()) / kT).reshape(n, n)
+    p = np.add.reduceat(np.add.reduceat(p, np.arange(0, n, 12), axis=0), np.arange(0, n, 12), axis=1)
+    p /= p.sum()
+    W, K, burn = 4096, 1500, 300
+    s0 = rng.uniform(-math.pi, math.pi, size=(W, C)).astype(np.float32)
+    h2 = np.zeros((bins, bins), np.uint64)
+    R.mcmc(w, 1, C, L, H, s0, K, burn, kT, 0.9, 3, bins=bins, pair=(0, 1), hist2=h2)
+    assert int(h2.sum()) == W * (K - burn)
+    tv = 0.5 * np.abs(h2 / h2.sum() - p).sum()
+    print(f"\ntotal variation against the exact joint: {tv:.4f}")
+    assert tv < 0.02, tv
+
+
+def test_device_arguments_match_host_arguments(R):
+    import torch
+    M, C, L, H, W, K = 2, 4, 2, 48, 200, 12
+    ens = I.make_ensemble(M, 2 * C, L, H, 33)
+    s0 = np.random.default_rng(3).uniform(-math.pi, math.pi, size=(W, C)).astype(np.float32)
+    sh = np.zeros_like(s0)
+    h1 = np.zeros((C, 21), np.uint64)
+    na = R.mcmc(ens.weights, M, C, L, H, s0, K, 2, 1.0, 0.4, 8, bins=21, s_out=sh, hist1=h1)
+    sd = torch.zeros((W, C), dtype=torch.float32, device="cuda")
+    hd = torch.zeros((C, 21), dtype=torch.uint64, device="cuda")
+    nd = R.mcmc(torch.from_numpy(ens.weights).cuda(), M, C, L, H, torch.from_numpy(s0).cuda(), K, 2, 1.0, 0.4, 8,
+                bins=21, s_out=sd, hist1=hd)
+    assert na == nd
+    assert np.array_equal(sh, sd.cpu().numpy())
+    assert np.array_equal(h1, hd.cpu().numpy())
+
+
+def test_errors(R):
+    ens = I.make_ensemble(1, 4, 2, 16, 34)
+    s0 = np.zeros((4, 2), np.float32)
+    with pytest.raises(R.RidError) as e:
+        R.mcmc(ens.weights, 1, 2, 2, 16, s0, 5, 0, 1.0, 0.3, 1, bins=10, pair=(0, 2))
+    assert e.value.code == R.RID_ERR_ARG
+    with pytest.raises(R.RidError) as e:
+        R.mcmc(ens.weights, 1, 2, 2, 16, s0, 5, 0, 0.0, 0.3, 1, bins=10)
+    assert e.value.code == R.RID_ERR_ARG
