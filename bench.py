@@ -297,6 +297,40 @@ def run_training(rid, torch, steps, seed=11):
                      "CUDA events on the launching stream"}
 
 
+def run_mcmc(rid, torch, steps, seed=13):
+    """MCMC dimension reduction (rid_mcmc) with the exploration model of the
+    200-bead workload: 2000 walkers (the paper's numb_walkers), 101 bins."""
+    wl = I.workload(WORKLOAD)
+    M, C, L, H = wl["n_models"], wl["n_cv"], wl["n_layers"], wl["width"]
+    D = 2 * C
+    W, bins, burn = 2000, 101, steps // 10
+    ens = I.make_ensemble(M, D, L, H, seed)
+    rng = np.random.default_rng(seed)
+    w = torch.from_numpy(ens.weights).cuda()
+    s0 = torch.from_numpy(rng.uniform(-np.pi, np.pi, size=(W, C)).astype(np.float32)).cuda()
+    h1 = torch.zeros((C, bins), dtype=torch.uint64, device="cuda")
+    f2 = torch.zeros((bins, bins), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    rid.mcmc(w, M, C, L, H, s0, 20, 0, 1.0, 0.3, seed, bins=bins, hist1=h1, pmf2=f2, stream=stream)   # warm
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    acc = rid.mcmc(w, M, C, L, H, s0, steps, burn, 1.0, 0.3, seed, bins=bins, hist1=h1, pmf2=f2, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    fl = M * 2 * (D * H + (L - 1) * H * H + H) * W        # forward GEMMs and the output layer, per step
+    achieved = fl * steps / (ms * 1e-3) / 1e12
+    return {"workload": f"{W} walkers, {M} members {D}-{H}x{L}-1, {steps} Metropolis steps ({burn} burn-in), "
+                        f"{bins} bins per CV, 2-D projection on CVs (0, 1)",
+            "value": W * steps / (ms * 1e-3), "unit": "walker-steps/s", "ms_per_step": ms / steps,
+            "acceptance": acc / (W * steps), "kernel_launches_per_step": L + 2,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "peak_source": FP32_PEAK_NOTE},
+            "timed": "one rid_mcmc call (device-resident weights and starting CVs; includes the call's "
+                     "allocation, the initial evaluation and the PMF projection), CUDA events"}
+
+
 def run_serving(rid, n_req, rate, plain_req, seed=5):
     """Poisson stream of mixed labeling / exploration requests through the
     request loop (BF16 ensembles), and the first plain_req requests of the
@@ -542,6 +576,8 @@ def main():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-training", action="store_true")
     ap.add_argument("--train-steps", type=int, default=400)
+    ap.add_argument("--no-mcmc", action="store_true")
+    ap.add_argument("--mcmc-steps", type=int, default=500)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -692,6 +728,8 @@ def main():
         out["precision"] = run_precision(rid, torch)
     if rank == 0 and world == 1 and not args.no_training:
         out["training"] = run_training(rid, torch, args.train_steps)
+    if rank == 0 and world == 1 and not args.no_mcmc:
+        out["mcmc"] = run_mcmc(rid, torch, args.mcmc_steps)
     if rank == 0 and world == 1 and not args.no_serving:
         out["serving"] = run_serving(rid, args.serve_requests, args.serve_rate, args.serve_plain_requests)
     if rank == 0:

@@ -10,10 +10,16 @@ namespace {
 
 // Batched FP32 GEMM: C[i][j] = sum over up to two K segments of A(i, k) B(k, j)
 // (member offset z * sm), so one kernel serves the N-N, N-T and T-N forms.
-// 32 x 32 output tiles (the training GEMMs have 128-row batches, so small
-// tiles are what fills the SMs), K tiles of 32, 128 threads with 2 x 4
-// outputs each.
-constexpr int GT = 32, GK = 32, GTHREADS = 128;
+// Square output tiles of TS = 32 (128 threads, 2 x 4 outputs each: the
+// training GEMMs have 128-row batches, and small tiles are what fills the SMs)
+// or TS = 64 (256 threads, 4 x 4 outputs: MCMC's thousands of walkers); K tiles
+// of 32, the next one staged in registers.  Every output sums its K terms in
+// increasing order whatever the tile, so both sizes give the same bits.
+constexpr int GK = 32;
+template <int TS> struct TileCfg {
+    static constexpr int threads = TS == 32 ? 128 : 256;
+    static constexpr int rp = TS * TS / threads / 4;   // rows per thread (4 columns each)
+};
 
 // A operand: element (i, k) at p + z sm + i si + k sk.  B operand: element
 // (k, j) at p + z sm + j si + k sk (si strides the output column).
@@ -57,18 +63,19 @@ __device__ __forceinline__ float ldop(const Operand& o, int z, int r, int k) {
     return o.p[(long long)z * o.sm + (long long)r * o.si + (long long)k * o.sk];
 }
 
-template <int EPI>
-__global__ void __launch_bounds__(GTHREADS) k_tr_gemm(GemmArgs g) {
-    __shared__ __align__(16) float As[GK][GT + 4];
-    __shared__ __align__(16) float Bs[GK][GT + 4];
-    const int z = blockIdx.z, i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
-    const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;   // rows 2 ty .. +1, columns 4 tx .. +3
-    float acc[2][4] = {};
+template <int EPI, int TS>
+__global__ void __launch_bounds__(TileCfg<TS>::threads) k_tr_gemm(GemmArgs g) {
+    constexpr int NT = TileCfg<TS>::threads, RP = TileCfg<TS>::rp;
+    __shared__ __align__(16) float As[GK][TS + 4];
+    __shared__ __align__(16) float Bs[GK][TS + 4];
+    const int z = blockIdx.z, i0 = blockIdx.y * TS, j0 = blockIdx.x * TS;
+    const int tid = threadIdx.x, tx = tid % (TS / 4), ty = tid / (TS / 4);   // rows RP ty .., columns 4 tx ..
+    float acc[RP][4] = {};
     // K tiles of both segments in one sequence; the next tile's elements are
     // loaded into registers while the current one is multiplied
     const int nt0 = (g.seg[0].K + GK - 1) / GK;
     const int nt = nt0 + (g.nseg > 1 ? (g.seg[1].K + GK - 1) / GK : 0);
-    constexpr int PER = GT * GK / GTHREADS;
+    constexpr int PER = TS * GK / NT;
     float ra[PER], rb[PER];
     auto fetch = [&](int t) {
         const int sidx = t < nt0 ? 0 : 1;
@@ -78,11 +85,12 @@ __global__ void __launch_bounds__(GTHREADS) k_tr_gemm(GemmArgs g) {
         const bool b_jfast = S.b.si == 1;   // B (k, j) with j contiguous: threads walk j
 #pragma unroll
         for (int r = 0; r < PER; ++r) {
-            const int idx = tid + GTHREADS * r;
-            const int hi = idx >> 5, lo = idx & 31;
-            const int gi = i0 + (a_kfast ? hi : lo), gk = k0 + (a_kfast ? lo : hi);
+            const int idx = tid + NT * r;
+            const int ii = a_kfast ? idx / GK : idx % TS, kk = a_kfast ? idx % GK : idx / TS;
+            const int gi = i0 + ii, gk = k0 + kk;
             ra[r] = (gi < g.rows && gk < S.K) ? ldop(S.a, z, gi, gk) : 0.0f;
-            const int gj = j0 + (b_jfast ? lo : hi), gkb = k0 + (b_jfast ? hi : lo);
+            const int jj = b_jfast ? idx % TS : idx / GK, kb = b_jfast ? idx / TS : idx % GK;
+            const int gj = j0 + jj, gkb = k0 + kb;
             rb[r] = (gj < g.cols && gkb < S.K) ? ldop(S.b, z, gj, gkb) : 0.0f;
         }
     };
@@ -91,10 +99,9 @@ __global__ void __launch_bounds__(GTHREADS) k_tr_gemm(GemmArgs g) {
         const bool a_kfast = S.a.sk == 1, b_jfast = S.b.si == 1;
 #pragma unroll
         for (int r = 0; r < PER; ++r) {
-            const int idx = tid + GTHREADS * r;
-            const int hi = idx >> 5, lo = idx & 31;
-            As[a_kfast ? lo : hi][a_kfast ? hi : lo] = ra[r];
-            Bs[b_jfast ? hi : lo][b_jfast ? lo : hi] = rb[r];
+            const int idx = tid + NT * r;
+            As[a_kfast ? idx % GK : idx / TS][a_kfast ? idx / GK : idx % TS] = ra[r];
+            Bs[b_jfast ? idx / TS : idx % GK][b_jfast ? idx % TS : idx / GK] = rb[r];
         }
     };
     if (nt > 0) fetch(0);
@@ -104,11 +111,13 @@ __global__ void __launch_bounds__(GTHREADS) k_tr_gemm(GemmArgs g) {
         if (t + 1 < nt) fetch(t + 1);
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
-            const float2 a = *reinterpret_cast<const float2*>(&As[kk][ty * 2]);
-            const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-            const float av[2] = {a.x, a.y}, bv[4] = {b.x, b.y, b.z, b.w};
+            float av[RP];
 #pragma unroll
-            for (int p = 0; p < 2; ++p)
+            for (int p = 0; p < RP; ++p) av[p] = As[kk][ty * RP + p];
+            const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+            const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int p = 0; p < RP; ++p)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
         }
@@ -116,8 +125,8 @@ __global__ void __launch_bounds__(GTHREADS) k_tr_gemm(GemmArgs g) {
     }
     const EpiArgs& e = g.e;
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int i = i0 + ty * 2 + p;
+    for (int p = 0; p < RP; ++p) {
+        const int i = i0 + ty * RP + p;
         if (i >= g.rows) continue;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -165,8 +174,13 @@ __global__ void __launch_bounds__(GTHREADS) k_tr_gemm(GemmArgs g) {
 
 template <int EPI>
 void launch_gemm(const GemmArgs& g, int M, cudaStream_t st) {
-    dim3 grid((g.cols + GT - 1) / GT, (g.rows + GT - 1) / GT, M);
-    k_tr_gemm<EPI><<<grid, GTHREADS, 0, st>>>(g);
+    if (g.rows >= 1024 && g.cols >= 64) {
+        dim3 grid((g.cols + 63) / 64, (g.rows + 63) / 64, M);
+        k_tr_gemm<EPI, 64><<<grid, TileCfg<64>::threads, 0, st>>>(g);
+    } else {
+        dim3 grid((g.cols + 31) / 32, (g.rows + 31) / 32, M);
+        k_tr_gemm<EPI, 32><<<grid, TileCfg<32>::threads, 0, st>>>(g);
+    }
 }
 
 // Operand helpers over [M][rows][ld] activations.
