@@ -273,6 +273,45 @@ RID_API int rid_mcmc(const rid_mcmc_desc* desc, const float* s0, float* s_out, u
                      double* pmf1, double* pmf2, int64_t* n_accepted, int32_t mem, void* stream);
 
 /*
+ * Selection (Sec. "Selection phase": cluster_threshold, numb_cluster_lower,
+ * numb_cluster_upper, max_selection; Sec. "Selection": explored CVs are
+ * clustered and values with high model deviation are collected by the trust
+ * levels; Sec. "CV selection": clustering weights and the angular mask).
+ *   candidates  frames f with trust_lo <= eps[f] < trust_hi (compared in
+ *               FP32), in frame order;
+ *   distance    d^2 = sum_c w_c delta_c^2, delta = cv_a - cv_b wrapped onto
+ *               [-pi, pi) for periodic CVs, FP32 with a fixed operation order;
+ *   clustering  leader algorithm in candidate order: a candidate joins the
+ *               first leader with d^2 <= t^2, else it becomes a leader (the
+ *               representative of its cluster);
+ *   adaptation  when adapt != 0 (the first iteration), t is searched from
+ *               cluster_threshold until the cluster count falls in [lower,
+ *               upper]: doubled / halved until bracketed, then geometric
+ *               bisection, at most 63 more trials;
+ *   output      selected[0 .. n_selected) = frame indices of the first
+ *               max_selection leaders; n_clusters and the threshold used.
+ * cv [n][C] and eps [n] are frames (e.g. rid_explore's traces flattened
+ * walker-major); cv, eps and selected live where `mem` says; weights and
+ * periodic are host arrays [C] (NULL: all 1 / all periodic); the scalar
+ * outputs are host pointers (NULL to skip).  Synchronous on `stream`.
+ * Errors: RID_ERR_ARG, RID_ERR_OOM, RID_ERR_CUDA.
+ */
+typedef struct {
+    int32_t n_cv;                 /* C, 1..128                                  */
+    const float* weights;         /* [C] host | NULL                            */
+    const int32_t* periodic;      /* [C] host | NULL (angular_mask)             */
+    double trust_lo, trust_hi;    /* candidate window on the model deviation    */
+    double cluster_threshold;     /* t (initial guess when adapt != 0)          */
+    int32_t numb_cluster_lower, numb_cluster_upper;
+    int32_t adapt;                /* search t into [lower, upper]               */
+    int32_t max_selection;        /* >= 0                                       */
+} rid_select_desc;
+
+RID_API int rid_select(const rid_select_desc* desc, int32_t n_frames, const float* cv, const float* eps,
+                       int32_t* selected, int32_t* n_selected, int32_t* n_clusters, double* threshold_out,
+                       int32_t mem, void* stream);
+
+/*
  * One force evaluation at given positions (no integration), through the same
  * kernels as a step.  bias = RID_BIAS_*; s0/kappa [W][C] are read only for
  * RID_BIAS_RESTRAINT.

@@ -10,7 +10,7 @@ the explored CVs are clustered, and values with high model deviation are
 collected by the trust levels; Sec. "CV selection": per-CV clustering weights
 and the angular mask).  Readings (the paper names the parameters, not the
 algorithm):
-  candidates   frames with trust_lo <= eps < trust_hi, in frame order;
+  candidates   frames with trust_lo <= eps < trust_hi (FP32), in frame order;
   distance     d(a, b)^2 = sum_c w_c delta_c^2, delta = a_c - b_c, wrapped onto
                [-pi, pi) for periodic CVs;
   clustering   the leader algorithm in candidate order: a candidate joins the
@@ -52,8 +52,10 @@ def dist2(a, b, w, periodic):
 
 
 def candidates(eps, trust_lo, trust_hi):
-    eps = np.asarray(eps, dtype=np.float64)
-    return np.nonzero((eps >= trust_lo) & (eps < trust_hi))[0]
+    """Frames with trust_lo <= eps < trust_hi, compared in FP32 (the model
+    deviations are FP32 and the window decides which frames count)."""
+    eps = np.asarray(eps, dtype=F)
+    return np.nonzero((eps >= F(trust_lo)) & (eps < F(trust_hi)))[0]
 
 
 def leaders(cv, w, periodic, t):

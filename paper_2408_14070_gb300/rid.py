@@ -28,7 +28,7 @@ EXPORTS = ("rid_version", "rid_status_string", "rid_last_error", "rid_create_sys
            "rid_profile_read", "rid_launch_count", "rid_ensemble_grad_noalloc", "rid_server_create",
            "rid_server_destroy", "rid_label_batch", "rid_submit", "rid_poll", "rid_server_load",
            "rid_trainer_create", "rid_trainer_destroy", "rid_trainer_set_data", "rid_trainer_run",
-           "rid_trainer_grad", "rid_trainer_weights", "rid_mcmc")
+           "rid_trainer_grad", "rid_trainer_weights", "rid_mcmc", "rid_select")
 RID_NOT_READY = 6
 RID_JOB_LABEL, RID_JOB_EXPLORE = 1, 2
 
@@ -66,6 +66,13 @@ class McmcDesc(C.Structure):
                 ("resnet", C.c_int32), ("weights", C.c_void_p), ("n_walkers", C.c_int32), ("n_steps", C.c_int64),
                 ("n_burn", C.c_int64), ("kT", C.c_double), ("step_size", C.c_double), ("seed", C.c_uint64),
                 ("bins", C.c_int32), ("proj_i", C.c_int32), ("proj_j", C.c_int32)]
+
+
+class SelectDesc(C.Structure):
+    _fields_ = [("n_cv", C.c_int32), ("weights", C.POINTER(C.c_float)), ("periodic", C.POINTER(C.c_int32)),
+                ("trust_lo", C.c_double), ("trust_hi", C.c_double), ("cluster_threshold", C.c_double),
+                ("numb_cluster_lower", C.c_int32), ("numb_cluster_upper", C.c_int32), ("adapt", C.c_int32),
+                ("max_selection", C.c_int32)]
 
 
 class LabelJob(C.Structure):
@@ -132,6 +139,8 @@ def lib() -> C.CDLL:
     L.rid_trainer_run.argtypes = [vp, i32, vp, vp, i32, vp]
     L.rid_trainer_grad.argtypes = [vp, vp, vp, vp, i32, vp]
     L.rid_trainer_weights.argtypes = [vp, vp, C.POINTER(i64), i32, vp]
+    L.rid_select.argtypes = [C.POINTER(SelectDesc), i32, vp, vp, vp, C.POINTER(i32), C.POINTER(i32),
+                             C.POINTER(C.c_double), i32, vp]
     L.rid_mcmc.argtypes = [C.POINTER(McmcDesc), vp, vp, vp, vp, vp, vp, C.POINTER(i64), i32, vp]
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype or C.c_int
@@ -572,3 +581,26 @@ def mcmc(weights, n_models, n_cv, n_layers, width, s0, n_steps, n_burn, kT, step
     nacc = C.c_int64(0)
     _check(lib().rid_mcmc(C.byref(d), ps, po, h1, h2, f1, f2, C.byref(nacc), a.mem, _stream_ptr(stream)))
     return nacc.value
+
+
+def select(cv, eps, trust_lo, trust_hi, threshold, lower=1, upper=1 << 30, adapt=False, max_selection=50,
+           weights=None, periodic=None, selected=None, stream=None):
+    """Selection phase (rid_select) on frames cv [n][C], eps [n]; returns
+    (selected frame indices, n_clusters, threshold).  `selected` may be a
+    preallocated int32 array / CUDA tensor of max_selection entries."""
+    n, Cn = int(cv.shape[0]), int(cv.shape[1])
+    if selected is None:
+        selected = np.zeros(max(1, max_selection), dtype=np.int32)
+    a = _Args()
+    pc = a.ptr(cv, np.float32, (n, Cn))
+    pe = a.ptr(eps, np.float32, (n,))
+    ps = a.ptr(selected, np.int32, None, True)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+    p = None if periodic is None else np.ascontiguousarray(periodic, dtype=np.int32)
+    d = SelectDesc(Cn, None if w is None else w.ctypes.data_as(C.POINTER(C.c_float)),
+                   None if p is None else p.ctypes.data_as(C.POINTER(C.c_int32)), float(trust_lo), float(trust_hi),
+                   float(threshold), int(lower), int(upper), int(bool(adapt)), int(max_selection))
+    ns, nc, thr = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
+    _check(lib().rid_select(C.byref(d), n, pc, pe, ps, C.byref(ns), C.byref(nc), C.byref(thr), a.mem,
+                            _stream_ptr(stream)))
+    return selected[:ns.value], nc.value, thr.value
