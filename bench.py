@@ -331,6 +331,33 @@ def run_mcmc(rid, torch, steps, seed=13):
                      "allocation, the initial evaluation and the PMF projection), CUDA events"}
 
 
+def run_selection(rid, torch, seed=17):
+    """Selection (rid_select) with the paper's selector config (threshold 2.6,
+    30-45 clusters, 50 selections) on the CV / model-deviation traces of
+    exploration: 1024 walkers x 100 output frames of the 200-bead system's 20
+    torsions (synthetic torus random walks of that shape), trust window [2, 3)."""
+    wl = I.workload(WORKLOAD)
+    C, W, T = wl["n_cv"], wl["n_walkers"], 100
+    rng = np.random.default_rng(seed)
+    cv = np.cumsum(rng.normal(0.0, 0.15, size=(W, T, C)), axis=1) + rng.uniform(-np.pi, np.pi, size=(W, 1, C))
+    cv = ((cv + np.pi) % (2 * np.pi) - np.pi).reshape(-1, C).astype(np.float32)
+    eps = rng.uniform(0.0, 4.0, size=W * T).astype(np.float32)
+    dcv, deps = torch.from_numpy(cv).cuda(), torch.from_numpy(eps).cuda()
+    out = torch.zeros(50, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    rid.select(dcv, deps, 2.0, 3.0, 2.6, 30, 45, True, 50, selected=out, stream=stream)     # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sel, nc, thr = rid.select(dcv, deps, 2.0, 3.0, 2.6, 30, 45, True, 50, selected=out, stream=stream)
+    dt = time.perf_counter() - t0
+    return {"workload": f"{W * T} frames ({W} walkers x {T}) of {C} torsion CVs, trust window [2, 3), "
+                        f"threshold 2.6 adapted into [30, 45] clusters, max_selection 50",
+            "value": W * T / dt, "unit": "frames/s", "wall_ms": 1e3 * dt, "clusters": nc, "threshold": thr,
+            "selected": int(sel.numel()),
+            "timed": "one rid_select call on device-resident traces (candidate compaction and every "
+                     "clustering trial of the threshold search)"}
+
+
 def run_serving(rid, n_req, rate, plain_req, seed=5):
     """Poisson stream of mixed labeling / exploration requests through the
     request loop (BF16 ensembles), and the first plain_req requests of the
@@ -577,6 +604,7 @@ def main():
     ap.add_argument("--no-training", action="store_true")
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--no-mcmc", action="store_true")
+    ap.add_argument("--no-selection", action="store_true")
     ap.add_argument("--mcmc-steps", type=int, default=500)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -728,6 +756,8 @@ def main():
         out["precision"] = run_precision(rid, torch)
     if rank == 0 and world == 1 and not args.no_training:
         out["training"] = run_training(rid, torch, args.train_steps)
+    if rank == 0 and world == 1 and not args.no_selection:
+        out["selection"] = run_selection(rid, torch)
     if rank == 0 and world == 1 and not args.no_mcmc:
         out["mcmc"] = run_mcmc(rid, torch, args.mcmc_steps)
     if rank == 0 and world == 1 and not args.no_serving:
