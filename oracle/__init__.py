@@ -80,6 +80,9 @@ def lib():
             L.orc_harmonic1d.argtypes = [C.c_double] * 8 + [C.c_uint64, C.c_int64, C.c_int64, C.c_int,
                                                             _d, _d, _d, _d]
             L.orc_label_stats.argtypes = [C.c_int64, C.c_int, C.c_int, _d, _d, _d, _d, _d]
+            L.orc_label_constrained.argtypes = sys_args + [C.c_int, _f, _f, C.c_int, _i32, _d, C.c_uint64,
+                                                           C.c_int64, C.c_int64, C.c_int, _d, _d, _d, _d, _d]
+            L.orc_label_constrained.restype = C.c_int
         return _lib
 
 
@@ -236,6 +239,27 @@ def label(sp, x0, s0, kappa, n_steps, n_equil, n_blocks=20, v0=None, step0=0, n_
     if nt < 0:
         raise ValueError("invalid label arguments")
     return dict(mf=mf, se=se, std=sd, x=xo, v=vo, threads=nt)
+
+
+def label_constrained(sp, x0, pairs, d0, n_steps, n_equil, n_blocks=20, v0=None, step0=0):
+    """Constrained-MD mean forces on distance CVs (orc_label_constrained):
+    pairs [C][2] bead indices, d0 [R][C] targets; returns dict(mf, se, std, x, v)."""
+    keep, sa = _sys(sp)
+    x0 = np.ascontiguousarray(x0, dtype=np.float32)
+    R, N = x0.shape[0], x0.shape[1]
+    v0 = None if v0 is None else np.ascontiguousarray(v0, dtype=np.float32)
+    pr = np.ascontiguousarray(pairs, dtype=np.int32)
+    Cn = pr.shape[0]
+    d0 = np.ascontiguousarray(d0, dtype=np.float64).reshape(R, Cn)
+    mf, se, sd = (np.zeros((R, Cn)) for _ in range(3))
+    xo, vo = np.zeros((R, N, 3)), np.zeros((R, N, 3))
+    rc = lib().orc_label_constrained(*sa, R, _P(x0, C.c_float), _P(v0, C.c_float), Cn, _P(pr, C.c_int32),
+                                     _P(d0, C.c_double), C.c_uint64(int(step0)), int(n_steps), int(n_equil),
+                                     int(n_blocks), _P(mf, C.c_double), _P(se, C.c_double), _P(sd, C.c_double),
+                                     _P(xo, C.c_double), _P(vo, C.c_double))
+    if rc != 0:
+        raise ValueError("orc_label_constrained: bad arguments")
+    return dict(mf=mf, se=se, std=sd, x=xo, v=vo)
 
 
 def harmonic1d(a, c, kappa, s0, n_steps, n_equil, n_blocks=20, m=1.0, kT=1.0, dt=0.01, gamma=1.0, seed=1):

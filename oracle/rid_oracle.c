@@ -786,6 +786,155 @@ int orc_label(SYS_ARGS, int R_, const float* x0, const float* v0, const double* 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Constrained-MD labels (Sec. "Labeling phase", constrained method; Box 5:   */
+/* distance CVs only).  Reading: each distance CV r_j = |x_a - x_b| (pairs   */
+/* of distinct beads, no bead in two pairs, equal masses) is held at d0_j by */
+/* BAOAB with SHAKE / RATTLE projections:                                    */
+/*   B  v += dt/2 f/m, project v;                                           */
+/*   A  x_old = x, x += dt/2 v, SHAKE x (and v), project v;                 */
+/*   O  v = c1 v + c2 xi (the noise of the unconstrained step), project v;  */
+/*   A  as above;  f = F_ff(x);  B  v += dt/2 f/m, project v.               */
+/* SHAKE for one distance: x_a -= lam r_old, x_b += lam r_old with the      */
+/* smaller root of |r' - 2 lam r_old| = d0; v gets the same change / h.     */
+/* Projection of v: the relative velocity along u = (x_a - x_b)/d0 is       */
+/* removed symmetrically.                                                    */
+/* Mean force on r_j after each step past n_equil (thermodynamic integration */
+/* along the distance, with the Jacobian r^2 of the spherical shell):        */
+/*   F_j = dU/dr - 2 kT / d0 = -(f_a - f_b) . u / 2 - 2 kT / d0,             */
+/* which equals -<lambda> of the rigid-constraint force; MF = <F>, SE from  */
+/* n_blocks blocks, std = population std of F.                              */
+/* ------------------------------------------------------------------------ */
+static void cons_shake(int C, const int32_t* pr, const double* d0, const double* xo, double* x, double* v, double h)
+{
+    for (int j = 0; j < C; ++j) {
+        const int a = pr[2 * j], b = pr[2 * j + 1];
+        double ro[3], rp[3];
+        for (int k = 0; k < 3; ++k) {
+            ro[k] = xo[3 * a + k] - xo[3 * b + k];
+            rp[k] = x[3 * a + k] - x[3 * b + k];
+        }
+        const double ro2 = ro[0] * ro[0] + ro[1] * ro[1] + ro[2] * ro[2];
+        const double rpo = rp[0] * ro[0] + rp[1] * ro[1] + rp[2] * ro[2];
+        const double rp2 = rp[0] * rp[0] + rp[1] * rp[1] + rp[2] * rp[2];
+        const double dd = rpo * rpo - ro2 * (rp2 - d0[j] * d0[j]);
+        const double lam = (rp2 - d0[j] * d0[j]) / (2.0 * (rpo + sqrt(dd > 0 ? dd : 0)));
+        for (int k = 0; k < 3; ++k) {
+            x[3 * a + k] -= lam * ro[k];
+            x[3 * b + k] += lam * ro[k];
+            v[3 * a + k] -= lam * ro[k] / h;
+            v[3 * b + k] += lam * ro[k] / h;
+        }
+    }
+}
+
+static void cons_project_v(int C, const int32_t* pr, const double* x, double* v)
+{
+    for (int j = 0; j < C; ++j) {
+        const int a = pr[2 * j], b = pr[2 * j + 1];
+        double u[3], r = 0, w = 0;
+        for (int k = 0; k < 3; ++k) {
+            u[k] = x[3 * a + k] - x[3 * b + k];
+            r += u[k] * u[k];
+        }
+        r = sqrt(r);
+        for (int k = 0; k < 3; ++k) {
+            u[k] /= r;
+            w += (v[3 * a + k] - v[3 * b + k]) * u[k];
+        }
+        w *= 0.5;
+        for (int k = 0; k < 3; ++k) {
+            v[3 * a + k] -= w * u[k];
+            v[3 * b + k] += w * u[k];
+        }
+    }
+}
+
+int orc_label_constrained(SYS_ARGS, int R_, const float* x0, const float* v0, int C, const int32_t* pairs,
+                          const double* d0 /* [R][C] */, uint64_t step0, int64_t n_steps, int64_t n_equil,
+                          int n_blocks, double* mf, double* se, double* sd, double* x_out, double* v_out)
+{
+    orc_sys S; SYS_MAKE(S);
+    const int N = S.n;
+    if (n_blocks < 2 || n_blocks > 4096 || n_steps - n_equil < n_blocks || C < 1) return -1;
+    const double m = S.mass, dt = S.dt;
+    const double c1 = exp(-S.gamma * dt), c2 = sqrt((1.0 - c1 * c1) * S.kT / m);
+    double* x = (double*)malloc(sizeof(double) * 3 * (size_t)N);
+    double* xo = (double*)malloc(sizeof(double) * 3 * (size_t)N);
+    double* v = (double*)malloc(sizeof(double) * 3 * (size_t)N);
+    double* f = (double*)malloc(sizeof(double) * 3 * (size_t)N);
+    double* smp = (double*)malloc(sizeof(double) * (size_t)C);
+    double* one = (double*)malloc(sizeof(double) * (size_t)C);
+    for (int j = 0; j < C; ++j) one[j] = 1.0;
+    for (int r = 0; r < R_; ++r) {
+        const double* dr = d0 + (size_t)r * C;
+        for (int i = 0; i < 3 * N; ++i) x[i] = x0[(size_t)r * 3 * N + i];
+        /* start on the constraint surface: each pair moved symmetrically along its own axis */
+        for (int j = 0; j < C; ++j) {
+            const int a = pairs[2 * j], b = pairs[2 * j + 1];
+            double u[3], len = 0, c[3];
+            for (int k = 0; k < 3; ++k) {
+                u[k] = x[3 * a + k] - x[3 * b + k];
+                c[k] = 0.5 * (x[3 * a + k] + x[3 * b + k]);
+                len += u[k] * u[k];
+            }
+            len = sqrt(len);
+            for (int k = 0; k < 3; ++k) {
+                x[3 * a + k] = c[k] + 0.5 * dr[j] * u[k] / len;
+                x[3 * b + k] = c[k] - 0.5 * dr[j] * u[k] / len;
+            }
+        }
+        if (v0) for (int i = 0; i < 3 * N; ++i) v[i] = v0[(size_t)r * 3 * N + i];
+        else mb_velocities(N, v, m, S.kT, S.seed, (uint32_t)r, (uint32_t)step0);
+        cons_project_v(C, pairs, x, v);
+        memset(f, 0, sizeof(double) * 3 * (size_t)N);
+        orc_ff(&S, x, f, NULL);
+        orc_stats st;
+        stats_init(&st, C, n_blocks, n_steps - n_equil);
+        for (int64_t t = 0; t < n_steps; ++t) {
+            const uint32_t step = (uint32_t)(step0 + (uint64_t)t);
+            for (int i = 0; i < 3 * N; ++i) v[i] += 0.5 * dt * f[i] / m;                  /* B */
+            cons_project_v(C, pairs, x, v);
+            memcpy(xo, x, sizeof(double) * 3 * (size_t)N);                                /* A */
+            for (int i = 0; i < 3 * N; ++i) x[i] += 0.5 * dt * v[i];
+            cons_shake(C, pairs, dr, xo, x, v, 0.5 * dt);
+            cons_project_v(C, pairs, x, v);
+            if (S.gamma > 0) {                                                            /* O */
+                for (int i = 0; i < N; ++i) {
+                    double xi[3];
+                    orc_normals3(S.seed, (uint32_t)i, (uint32_t)r, step, 0u, xi);
+                    for (int k = 0; k < 3; ++k) v[3 * i + k] = c1 * v[3 * i + k] + c2 * xi[k];
+                }
+                cons_project_v(C, pairs, x, v);
+            }
+            memcpy(xo, x, sizeof(double) * 3 * (size_t)N);                                /* A */
+            for (int i = 0; i < 3 * N; ++i) x[i] += 0.5 * dt * v[i];
+            cons_shake(C, pairs, dr, xo, x, v, 0.5 * dt);
+            cons_project_v(C, pairs, x, v);
+            memset(f, 0, sizeof(double) * 3 * (size_t)N);
+            orc_ff(&S, x, f, NULL);
+            for (int i = 0; i < 3 * N; ++i) v[i] += 0.5 * dt * f[i] / m;                  /* B */
+            cons_project_v(C, pairs, x, v);
+            if (t >= n_equil) {
+                for (int j = 0; j < C; ++j) {
+                    const int a = pairs[2 * j], b = pairs[2 * j + 1];
+                    double fu = 0;
+                    for (int k = 0; k < 3; ++k) fu += (f[3 * a + k] - f[3 * b + k]) * (x[3 * a + k] - x[3 * b + k]);
+                    const double F = -0.5 * fu / dr[j] - 2.0 * S.kT / dr[j];
+                    smp[j] = -F;              /* stats_finish returns -kappa mean: kappa = 1 */
+                }
+                stats_add(&st, t - n_equil, smp);
+            }
+        }
+        stats_finish(&st, one, mf + (size_t)r * C, se + (size_t)r * C, sd + (size_t)r * C);
+        stats_free(&st);
+        if (x_out) memcpy(x_out + (size_t)r * 3 * N, x, sizeof(double) * 3 * (size_t)N);
+        if (v_out) memcpy(v_out + (size_t)r * 3 * N, v, sizeof(double) * 3 * (size_t)N);
+    }
+    free(x); free(xo); free(v); free(f); free(smp); free(one);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* One-dimensional harmonic test systems that reuse the same integrator and */
 /* label statistics: a particle in U(x) = a/2 (x - c)^2, optionally with a   */
 /* restraint kappa/2 (x - s0)^2 on the (non-periodic) CV s = x.             */
