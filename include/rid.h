@@ -175,6 +175,28 @@ RID_API int rid_label(rid_system* sys, int32_t n_runs, const float* x0, const fl
               float* x_out, float* v_out, int32_t mem, void* stream);
 
 /*
+ * Constrained-MD labelling on distance CVs (Sec. "Labeling phase", constrained
+ * method, Box 5: distance CVs only).  For each of R runs the C distances
+ * r_j = |x_a - x_b| of `pairs` [C][2] (host int32; distinct beads, no bead in
+ * two pairs) are held at d0 [R][C] (float64, > 0) by SHAKE / RATTLE inside the
+ * BAOAB step (the system's dt, gamma, kT, mass and force field; no ensemble
+ * bias, and the system's torsion CVs play no part).  The start x0 is moved
+ * onto the constraints (each pair symmetrically along its own axis).  After
+ * n_equil steps every step samples the mean force along each distance,
+ *   F_j = -(f_a - f_b) . u_j / 2 - 2 kT / d0_j   (f: force-field forces,
+ *   u_j = (x_a - x_b) / d0_j; the free energy includes the r^2 of the shell),
+ * and mf_out / se_out / std_out [R][C] receive its mean, the standard error
+ * from n_blocks equal blocks and its population std.  Noise: counter (bead,
+ * run, step, 0); v0 NULL draws Maxwell-Boltzmann velocities at step0.
+ * Shared memory bounds the chain (about 2900 beads).  Errors: RID_ERR_ARG,
+ * RID_ERR_OOM, RID_ERR_CUDA, RID_ERR_NONFINITE.
+ */
+RID_API int rid_label_constrained(rid_system* sys, int32_t n_runs, const float* x0, const float* v0, int32_t n_cv,
+                                  const int32_t* pairs, const double* d0, uint64_t step0, int64_t n_steps,
+                                  int64_t n_equil, int32_t n_blocks, double* mf_out, double* se_out,
+                                  double* std_out, float* x_out, float* v_out, int32_t mem, void* stream);
+
+/*
  * Training the ensemble on mean-force labels (Sec. "Training phase":
  * numb_models, neurons, resnet, batch_size, init_lr, decay_steps, decay_rate;
  * Sec. "Training": the models are fitted to the labelled mean forces).

@@ -1086,6 +1086,102 @@ extern "C" int rid_label(rid_system* sys, int32_t R, const float* x0, const floa
     return RID_OK;
 }
 
+// Constrained-MD labels on distance CVs (k_label_cons.cu).  Scratch for the
+// call is allocated here and released before returning.
+extern "C" int rid_label_constrained(rid_system* sys, int32_t R, const float* x0, const float* v0, int32_t C,
+                                     const int32_t* pairs, const double* d0, uint64_t step0, int64_t n_steps,
+                                     int64_t n_equil, int32_t n_blocks, double* mf_out, double* se_out,
+                                     double* std_out, float* x_out, float* v_out, int32_t mem, void* stream) {
+    if (!sys || !x0 || !pairs || !d0 || !mf_out || !se_out || !std_out) return fail(RID_ERR_ARG, "NULL argument");
+    if (R < 1 || C < 1 || C > RID_MAX_CV) return fail(RID_ERR_ARG, "n_runs >= 1 and 1 <= n_cv <= %d required", RID_MAX_CV);
+    if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "mem must be RID_MEM_HOST or RID_MEM_DEVICE");
+    if (n_blocks < 2 || n_blocks > RID_MAX_BLOCKS) return fail(RID_ERR_ARG, "n_blocks=%d outside [2, %d]", n_blocks, RID_MAX_BLOCKS);
+    if (n_equil < 0 || n_steps - n_equil < n_blocks) return fail(RID_ERR_ARG, "need 0 <= n_equil and n_steps - n_equil >= n_blocks");
+    if (step0 + (uint64_t)n_steps > (1ull << 32)) return fail(RID_ERR_ARG, "step0 + n_steps exceeds 2^32");
+    TRY(check_device(sys));
+    const int N = sys->S.N;
+    std::vector<int> used(N, 0);
+    std::vector<int2> hp(C);
+    for (int j = 0; j < C; ++j) {
+        const int a = pairs[2 * j], b = pairs[2 * j + 1];
+        if (a < 0 || b < 0 || a >= N || b >= N || a == b) return fail(RID_ERR_ARG, "pair %d: beads out of range or equal", j);
+        if (used[a]++ || used[b]++) return fail(RID_ERR_ARG, "pair %d shares a bead with another pair", j);
+        hp[j] = make_int2(a, b);
+    }
+    const size_t smem = rid_label_cons_smem(N, C);
+    if (smem > 227 * 1024) return fail(RID_ERR_ARG, "chain of %d beads with %d CVs exceeds shared memory", N, C);
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long nb = (long long)R * N, nc = (long long)R * C;
+    const cudaMemcpyKind kin = mem == RID_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    // host d0 (double) -> device float; x0, v0 -> float4
+    std::vector<double> hd0;
+    const double* d0h = d0;
+    if (mem == RID_MEM_DEVICE) {
+        hd0.resize(nc);
+        CK(cudaMemcpyAsync(hd0.data(), d0, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        d0h = hd0.data();
+    }
+    std::vector<float> fd0(nc);
+    for (long long i = 0; i < nc; ++i) {
+        if (!(d0h[i] > 0)) return fail(RID_ERR_ARG, "d0 must be positive");
+        fd0[i] = (float)d0h[i];
+    }
+    struct Scoped {   // released on every return (cudaFree waits for the device)
+        DevBuf b;
+        ~Scoped() { b.release(); }
+    } scoped;
+    DevBuf& buf = scoped.b;
+    const size_t o_x = 0, o_v = o_x + 16 * nb, o_xo = o_v + 16 * nb, o_vo = o_xo + 16 * nb, o_io = o_vo + 16 * nb;
+    const size_t o_bs = o_io + 12 * nb, o_mf = o_bs + 8 * nc * n_blocks, o_se = o_mf + 8 * nc, o_sd = o_se + 8 * nc;
+    const size_t o_d0 = o_sd + 8 * nc, o_pr = o_d0 + ((4 * nc + 15) & ~15ll), o_bad = o_pr + ((8 * C + 15) & ~15);
+    TRY(buf.ensure(o_bad + 4 * R));
+    unsigned char* b = static_cast<unsigned char*>(buf.p);
+    float4* dx = reinterpret_cast<float4*>(b + o_x);
+    float4* dv = reinterpret_cast<float4*>(b + o_v);
+    float4* dxo = reinterpret_cast<float4*>(b + o_xo);
+    float4* dvo = reinterpret_cast<float4*>(b + o_vo);
+    float* io = reinterpret_cast<float*>(b + o_io);
+    double* bs = reinterpret_cast<double*>(b + o_bs);
+    double* dmf = reinterpret_cast<double*>(b + o_mf);
+    double* dse = reinterpret_cast<double*>(b + o_se);
+    double* dsd = reinterpret_cast<double*>(b + o_sd);
+    float* dd0 = reinterpret_cast<float*>(b + o_d0);
+    int2* dpr = reinterpret_cast<int2*>(b + o_pr);
+    int* dbad = reinterpret_cast<int*>(b + o_bad);
+    CK(cudaMemcpyAsync(io, x0, (size_t)nb * 12, kin, st));
+    rid_launch_pack(io, dx, nb, st);
+    if (v0) {
+        CK(cudaMemcpyAsync(io, v0, (size_t)nb * 12, kin, st));
+        rid_launch_pack(io, dv, nb, st);
+    }
+    CK(cudaMemcpyAsync(dd0, fd0.data(), nc * sizeof(float), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dpr, hp.data(), C * sizeof(int2), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(bs, 0, 8 * nc * n_blocks, st));
+    CK(rid_launch_label_cons(sys->S, R, C, n_blocks, n_steps, n_equil, (uint32_t)step0, (float)sys->desc.kT, dx,
+                             v0 ? dv : nullptr, dpr, dd0, bs, dmf, dse, dsd, dxo, dvo, dbad, st));
+    const cudaMemcpyKind kout = mem == RID_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(mf_out, dmf, nc * sizeof(double), kout, st));
+    CK(cudaMemcpyAsync(se_out, dse, nc * sizeof(double), kout, st));
+    CK(cudaMemcpyAsync(std_out, dsd, nc * sizeof(double), kout, st));
+    if (x_out) {
+        rid_launch_unpack(dxo, io, nb, st);
+        CK(cudaMemcpyAsync(x_out, io, (size_t)nb * 12, kout, st));
+    }
+    if (v_out) {
+        float* io2 = reinterpret_cast<float*>(b + o_x);   // x0 staging is free by now
+        rid_launch_unpack(dvo, io2, nb, st);
+        CK(cudaMemcpyAsync(v_out, io2, (size_t)nb * 12, kout, st));
+    }
+    std::vector<int> hbad(R);
+    CK(cudaMemcpyAsync(hbad.data(), dbad, R * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ++sys->launches;
+    for (int r = 0; r < R; ++r)
+        if (hbad[r]) return fail(RID_ERR_NONFINITE, "non-finite force or position in run %d", r);
+    return RID_OK;
+}
+
 extern "C" int rid_eval_forces(rid_system* sys, int32_t W, const float* x, int32_t bias, const double* s0,
                                const double* kappa, float* f_out, float* s_out, float* eps_out, float* abar_out,
                                float* grad_out, int32_t mem, void* stream) {

@@ -160,6 +160,11 @@ void rid_launch_unpack(const float4* src, float* dst, long long n, cudaStream_t 
 void rid_launch_mb(const SysDev& S, StateDev st, int W, uint32_t step0, cudaStream_t s);
 void rid_launch_pair_mask(const SysDev& S, StateDev st, int W, uint32_t* mask, cudaStream_t s);
 int rid_ff_smem_bytes(int N);
+size_t rid_label_cons_smem(int N, int C);
+cudaError_t rid_launch_label_cons(const SysDev& S, int R, int C, int B, long long n_steps, long long n_equil,
+                                  uint32_t step0, float kT, const float4* x0, const float4* v0, const int2* pairs,
+                                  const float* d0, double* bsum, double* mf, double* se, double* sd, float4* x_out,
+                                  float4* v_out, int* bad, cudaStream_t st);
 void rid_launch_ff(const SysDev& S, StateDev st, int W, bool energy, cudaStream_t s);
 
 // Arguments of the fused finish / B-A-O-A / CV kernel.

@@ -28,7 +28,8 @@ EXPORTS = ("rid_version", "rid_status_string", "rid_last_error", "rid_create_sys
            "rid_profile_read", "rid_launch_count", "rid_ensemble_grad_noalloc", "rid_server_create",
            "rid_server_destroy", "rid_label_batch", "rid_submit", "rid_poll", "rid_server_load",
            "rid_trainer_create", "rid_trainer_destroy", "rid_trainer_set_data", "rid_trainer_run",
-           "rid_trainer_grad", "rid_trainer_weights", "rid_mcmc", "rid_select")
+           "rid_trainer_grad", "rid_trainer_weights", "rid_mcmc", "rid_select",
+           "rid_label_constrained")
 RID_NOT_READY = 6
 RID_JOB_LABEL, RID_JOB_EXPLORE = 1, 2
 
@@ -139,6 +140,8 @@ def lib() -> C.CDLL:
     L.rid_trainer_run.argtypes = [vp, i32, vp, vp, i32, vp]
     L.rid_trainer_grad.argtypes = [vp, vp, vp, vp, i32, vp]
     L.rid_trainer_weights.argtypes = [vp, vp, C.POINTER(i64), i32, vp]
+    L.rid_label_constrained.argtypes = [vp, i32, vp, vp, i32, vp, vp, u64, i64, i64, i32, vp, vp, vp, vp, vp,
+                                        i32, vp]
     L.rid_select.argtypes = [C.POINTER(SelectDesc), i32, vp, vp, vp, C.POINTER(i32), C.POINTER(i32),
                              C.POINTER(C.c_double), i32, vp]
     L.rid_mcmc.argtypes = [C.POINTER(McmcDesc), vp, vp, vp, vp, vp, vp, C.POINTER(i64), i32, vp]
@@ -270,6 +273,23 @@ class System:
                 a.ptr(v_out, np.float32, (R, self.N, 3), True)]
         _check(lib().rid_label(self.h, R, *args, C.c_uint64(step0), C.c_int64(n_steps), C.c_int64(n_equil),
                                int(n_blocks), *outs, a.mem, _stream_ptr(stream)))
+
+    def label_constrained(self, x0, pairs, d0, n_steps, n_equil, n_blocks, mf_out, se_out, std_out, v0=None,
+                          step0=0, x_out=None, v_out=None, stream=None):
+        """Constrained-MD mean forces on the distances of `pairs` [C][2] held
+        at d0 [R][C] (rid_label_constrained)."""
+        R = int(x0.shape[0])
+        pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        Cn = pr.shape[0]
+        a = _Args()
+        args = [a.ptr(x0, np.float32, (R, self.N, 3)), a.ptr(v0, np.float32, (R, self.N, 3))]
+        pd0 = a.ptr(d0, np.float64, (R, Cn))
+        outs = [a.ptr(mf_out, np.float64, (R, Cn), True), a.ptr(se_out, np.float64, (R, Cn), True),
+                a.ptr(std_out, np.float64, (R, Cn), True), a.ptr(x_out, np.float32, (R, self.N, 3), True),
+                a.ptr(v_out, np.float32, (R, self.N, 3), True)]
+        _check(lib().rid_label_constrained(self.h, R, *args, Cn, pr.ctypes.data, pd0, C.c_uint64(step0),
+                                           C.c_int64(n_steps), C.c_int64(n_equil), int(n_blocks), *outs, a.mem,
+                                           _stream_ptr(stream)))
 
     def eval_forces(self, x, bias=RID_BIAS_NONE, s0=None, kappa=None, f_out=None, s_out=None, eps_out=None,
                     abar_out=None, grad_out=None, stream=None):
