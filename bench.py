@@ -358,6 +358,35 @@ def run_selection(rid, torch, seed=17):
                      "clustering trial of the threshold search)"}
 
 
+def run_constrained(rid, torch, runs=1024, steps=1000, seed=19):
+    """Constrained-MD labelling (rid_label_constrained) on the 200-bead chain:
+    `runs` runs, 10 distance CVs between beads 10 apart, each held at its
+    starting length."""
+    wl = I.workload(WORKLOAD)
+    sp = I.make_system(wl["n_beads"], wl["n_cv"], seed)
+    x0 = I.make_chains(runs, sp, seed)
+    pairs = np.array([[20 * k, 20 * k + 10] for k in range(10)], np.int32)
+    d0 = np.linalg.norm(x0[:, pairs[:, 0]] - x0[:, pairs[:, 1]], axis=-1).astype(np.float64)
+    xd, d0d = torch.from_numpy(x0).cuda(), torch.from_numpy(d0).cuda()
+    out = [torch.zeros((runs, 10), dtype=torch.float64, device="cuda") for _ in range(3)]
+    stream = torch.cuda.current_stream()
+    with rid.System(sp) as system:
+        system.label_constrained(xd[:8], pairs, d0d[:8], 50, 10, 4, *[o[:8] for o in out], stream=stream)   # warm
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        system.label_constrained(xd, pairs, d0d, steps, steps // 10, 20, *out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"workload": f"{runs} constrained runs x {steps} steps, {wl['n_beads']}-bead chain, 10 distance CVs "
+                        f"(beads 10 apart) held at their starting lengths",
+            "value": runs * steps / (ms * 1e-3), "unit": "walker-steps/s", "wall_ms": ms, "kernel_launches": 1,
+            "mean_abs_mean_force": float(out[0].abs().mean()),
+            "timed": "one rid_label_constrained call on device arrays (staging, the chain-resident kernel, "
+                     "statistics), CUDA events"}
+
+
 def run_serving(rid, n_req, rate, plain_req, seed=5):
     """Poisson stream of mixed labeling / exploration requests through the
     request loop (BF16 ensembles), and the first plain_req requests of the
@@ -605,6 +634,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--no-mcmc", action="store_true")
     ap.add_argument("--no-selection", action="store_true")
+    ap.add_argument("--no-constrained", action="store_true")
     ap.add_argument("--mcmc-steps", type=int, default=500)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -756,6 +786,8 @@ def main():
         out["precision"] = run_precision(rid, torch)
     if rank == 0 and world == 1 and not args.no_training:
         out["training"] = run_training(rid, torch, args.train_steps)
+    if rank == 0 and world == 1 and not args.no_constrained:
+        out["constrained"] = run_constrained(rid, torch)
     if rank == 0 and world == 1 and not args.no_selection:
         out["selection"] = run_selection(rid, torch)
     if rank == 0 and world == 1 and not args.no_mcmc:
