@@ -366,7 +366,7 @@ def run_constrained(rid, torch, runs=1024, steps=1000, seed=19):
     sp = I.make_system(wl["n_beads"], wl["n_cv"], seed)
     x0 = I.make_chains(runs, sp, seed)
     pairs = np.array([[20 * k, 20 * k + 10] for k in range(10)], np.int32)
-    d0 = np.linalg.norm(x0[:, pairs[:, 0]] - x0[:, pairs[:, 1]], axis=-1).astype(np.float64)
+    d0 = np.ascontiguousarray(np.linalg.norm(x0[:, pairs[:, 0]] - x0[:, pairs[:, 1]], axis=-1), dtype=np.float64)
     xd, d0d = torch.from_numpy(x0).cuda(), torch.from_numpy(d0).cuda()
     out = [torch.zeros((runs, 10), dtype=torch.float64, device="cuda") for _ in range(3)]
     stream = torch.cuda.current_stream()

@@ -72,7 +72,7 @@ def _chain_problem(runs, seed=5):
     x0 = I.make_chains(runs, sp, seed)
     pairs = np.array([[3, 9], [15, 27], [30, 34], [40, 55]], np.int32)
     cur = np.linalg.norm(x0[:, pairs[:, 0]] - x0[:, pairs[:, 1]], axis=-1)
-    d0 = (cur * np.random.default_rng(seed).uniform(0.95, 1.05, size=cur.shape)).astype(np.float64)
+    d0 = np.ascontiguousarray(cur * np.random.default_rng(seed).uniform(0.95, 1.05, size=cur.shape), dtype=np.float64)
     return sp, x0, pairs, d0
 
 
