@@ -635,6 +635,8 @@ def main():
     ap.add_argument("--no-mcmc", action="store_true")
     ap.add_argument("--no-selection", action="store_true")
     ap.add_argument("--no-constrained", action="store_true")
+    ap.add_argument("--cons-runs", type=int, default=1024)
+    ap.add_argument("--cons-steps", type=int, default=1000)
     ap.add_argument("--mcmc-steps", type=int, default=500)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -787,7 +789,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_training:
         out["training"] = run_training(rid, torch, args.train_steps)
     if rank == 0 and world == 1 and not args.no_constrained:
-        out["constrained"] = run_constrained(rid, torch)
+        out["constrained"] = run_constrained(rid, torch, args.cons_runs, args.cons_steps)
     if rank == 0 and world == 1 and not args.no_selection:
         out["selection"] = run_selection(rid, torch)
     if rank == 0 and world == 1 and not args.no_mcmc:
