@@ -224,8 +224,11 @@ extern "C" RID_API int rid_select(const rid_select_desc* d, int32_t n, const flo
     };
     double t = d->cluster_threshold;
     int count = 0;
-    bool full = true;   // the last clustering ran to the end (not stopped early)
-    if (int rc = cluster(t, 0, &count)) return rc;
+    // while searching, a clustering only needs to know whether its count passes
+    // `upper`, so it stops there; the one finally kept is completed afterwards
+    const int stop = d->adapt ? d->numb_cluster_upper : 0;
+    if (int rc = cluster(t, stop, &count)) return rc;
+    bool full = stop == 0 || count <= stop;   // the last clustering ran to the end
     if (d->adapt && hn[0] > 0) {
         const int lower = d->numb_cluster_lower, upper = d->numb_cluster_upper;
         double lo_t = 0.0, hi_t = INFINITY;
@@ -242,9 +245,9 @@ extern "C" RID_API int rid_select(const rid_select_desc* d, int32_t n, const flo
             if (int rc = cluster(t, upper, &count)) return rc;
             full = count <= upper;
         }
-        if (!full)
-            if (int rc = cluster(t, 0, &count)) return rc;
     }
+    if (!full)
+        if (int rc = cluster(t, 0, &count)) return rc;
     const int nsel = count < d->max_selection ? count : d->max_selection;
     if (nsel > 0) {
         int* dsel = mem == RID_MEM_DEVICE ? selected : dsel_buf;
