@@ -289,10 +289,24 @@ typedef struct {
     uint64_t seed;                /* Philox key                                 */
     int32_t bins;                 /* per CV, 1..4096 (101 in the paper)         */
     int32_t proj_i, proj_j;       /* CV pair of the 2-D projection              */
+    /* Path projection (the paper's "path" mode; off when path_n_nodes = 0):
+     * path collective variables of nodes p_1..p_P over the CVs path_cv,
+     * d_i = |s - p_i|^2 with wrapped differences,
+     *   s_path = sum_i i e^{-lambda d_i} / sum_i e^{-lambda d_i},
+     *   z_path = -(1/lambda) ln sum_i e^{-lambda d_i},
+     * counted into hist_path [bins][bins] over [1, P] x [path_z_lo, path_z_hi]
+     * (values clamped to the edge bins). */
+    int32_t path_n_nodes;         /* P, 0 or 2..1024                            */
+    int32_t path_n_cv;            /* CVs of the path, 1..C                      */
+    const int32_t* path_cv;       /* [path_n_cv] host                           */
+    const float* path_nodes;      /* [P][path_n_cv] host, radians               */
+    double path_lambda;           /* > 0 (path_lm in the paper)                 */
+    double path_z_lo, path_z_hi;  /* z range of hist_path                       */
 } rid_mcmc_desc;
 
 RID_API int rid_mcmc(const rid_mcmc_desc* desc, const float* s0, float* s_out, uint64_t* hist1, uint64_t* hist2,
-                     double* pmf1, double* pmf2, int64_t* n_accepted, int32_t mem, void* stream);
+                     double* pmf1, double* pmf2, uint64_t* hist_path, double* pmf_path, int64_t* n_accepted,
+                     int32_t mem, void* stream);
 
 /*
  * Selection (Sec. "Selection phase": cluster_threshold, numb_cluster_lower,

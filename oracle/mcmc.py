@@ -20,6 +20,13 @@ Readings (the paper names the parameters, not the move):
   counting  after every step t >= n_burn, every walker's current state;
   bins      floor((s + pi) / (2 pi) * bins), clamped to [0, bins - 1];
   wrap      d - 2 pi floor(d / (2 pi) + 1/2).
+The "path" projection maps a state onto the path collective variables of
+Branduardi, Gervasio and Parrinello (2007) for nodes p_1..p_P over a subset of
+the CVs (wrapped differences): with d_i = |s - p_i|^2,
+  s_path = sum_i i exp(-lambda d_i) / sum_i exp(-lambda d_i)  in [1, P],
+  z_path = -(1/lambda) ln sum_i exp(-lambda d_i),
+evaluated with the smallest d_i factored out; the (s_path, z_path) histogram
+has bins over [1, P] and over a given [z_lo, z_hi], values clamped.
 """
 from __future__ import annotations
 
@@ -66,8 +73,27 @@ def bin_index(s, bins):
     return np.clip(b, 0, bins - 1)
 
 
-def run(weights, C, L, H, resnet, s0, n_steps, n_burn, kT, step_size, seed, bins, pair):
+def path_cv(s, nodes, cvs, lam):
+    """(s_path, z_path) of points s [W][C] for path nodes [P][Cp] over the CVs `cvs`."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    d = wrap(np.asarray(s, dtype=np.float64)[:, None, list(cvs)] - nodes[None])
+    d2 = (d * d).sum(axis=-1)                          # [W][P]
+    m = d2.min(axis=1)
+    e = np.exp(-lam * (d2 - m[:, None]))
+    se = e.sum(axis=1)
+    sp = (e * np.arange(1, nodes.shape[0] + 1)).sum(axis=1) / se
+    return sp, m - np.log(se) / lam
+
+
+def path_bins(sp, z, n_nodes, z_lo, z_hi, bins):
+    bs = np.floor((np.asarray(sp) - 1.0) / (n_nodes - 1) * bins).astype(np.int64)
+    bz = np.floor((np.asarray(z) - z_lo) / (z_hi - z_lo) * bins).astype(np.int64)
+    return np.clip(bs, 0, bins - 1), np.clip(bz, 0, bins - 1)
+
+
+def run(weights, C, L, H, resnet, s0, n_steps, n_burn, kT, step_size, seed, bins, pair, path=None):
     """Returns dict(s, A, n_accepted, hist1 [C][bins], hist2 [bins][bins],
+    hist_path [bins][bins] (when path = (nodes, cvs, lam, z_lo, z_hi)),
     min_margin [W]): min_margin is each walker's smallest |kT ln u + dA| over
     the run (how close its closest accept decision came to the threshold)."""
     D = 2 * C
@@ -76,6 +102,7 @@ def run(weights, C, L, H, resnet, s0, n_steps, n_burn, kT, step_size, seed, bins
     A = ensemble_mean_value(weights, D, L, H, resnet, s)
     hist1 = np.zeros((C, bins), dtype=np.int64)
     hist2 = np.zeros((bins, bins), dtype=np.int64)
+    histp = np.zeros((bins, bins), dtype=np.int64)
     n_acc = 0
     min_margin = np.full(W, np.inf)
     for t in range(n_steps):
@@ -92,7 +119,12 @@ def run(weights, C, L, H, resnet, s0, n_steps, n_burn, kT, step_size, seed, bins
             for c in range(C):
                 hist1[c] += np.bincount(b[:, c], minlength=bins)
             np.add.at(hist2, (b[:, pair[0]], b[:, pair[1]]), 1)
-    return dict(s=s, A=A, n_accepted=n_acc, hist1=hist1, hist2=hist2, min_margin=min_margin)
+            if path is not None:
+                nodes, cvs, lam, z_lo, z_hi = path
+                sp_, z_ = path_cv(s, nodes, cvs, lam)
+                bs, bz = path_bins(sp_, z_, len(nodes), z_lo, z_hi, bins)
+                np.add.at(histp, (bs, bz), 1)
+    return dict(s=s, A=A, n_accepted=n_acc, hist1=hist1, hist2=hist2, hist_path=histp, min_margin=min_margin)
 
 
 def projected_pmf(hist, kT):

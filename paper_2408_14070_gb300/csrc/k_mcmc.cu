@@ -16,7 +16,10 @@
 //                 of every walker is counted into one histogram per CV and one
 //                 2-D histogram of a CV pair (integer atomics: exact)
 // and at the end k_mc_pmf turns the counts into -kT ln(count / total),
-// shifted to a zero minimum (+inf for empty bins).
+// shifted to a zero minimum (+inf for empty bins).  With path nodes, the warp
+// also maps each counted state onto the path collective variables (lanes over
+// the nodes, the smallest distance factored out, sums in a fixed order) and
+// counts (s_path, z_path).
 #include <cmath>
 
 #include "rid_gemm.cuh"
@@ -76,6 +79,12 @@ struct AcceptArgs {
     unsigned long long* hist1;   // [C][bins]
     unsigned long long* hist2;   // [bins][bins]
     unsigned long long* nacc;
+    // path projection (npath = 0: off)
+    int npath, Cp;
+    const int* pcv;              // [Cp]
+    const float* pnodes;         // [P][Cp]
+    float lam, z_lo, z_hi;
+    unsigned long long* histp;   // [bins][bins]
 };
 
 __global__ void k_mc_accept(AcceptArgs a) {
@@ -113,6 +122,44 @@ __global__ void k_mc_accept(AcceptArgs a) {
         for (int c = lane; c < a.C; c += 32) atomicAdd(&a.hist1[(long long)c * a.bins + mc_bin(s[c], a.bins)], 1ull);
         if (lane == 0 && a.hist2)
             atomicAdd(&a.hist2[(long long)mc_bin(s[a.pi], a.bins) * a.bins + mc_bin(s[a.pj], a.bins)], 1ull);
+        if (a.npath > 0) {
+            // d_i for the nodes of this lane, then the smallest over the warp
+            float dmin = INFINITY;
+            for (int i = lane; i < a.npath; i += 32) {
+                float d2 = 0.0f;
+                for (int c = 0; c < a.Cp; ++c) {
+                    const float d = rid_wrapf(s[a.pcv[c]] - a.pnodes[(long long)i * a.Cp + c]);
+                    d2 = fmaf(d, d, d2);
+                }
+                dmin = fminf(dmin, d2);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+            float s0 = 0.0f, s1 = 0.0f;
+            for (int i = lane; i < a.npath; i += 32) {
+                float d2 = 0.0f;
+                for (int c = 0; c < a.Cp; ++c) {
+                    const float d = rid_wrapf(s[a.pcv[c]] - a.pnodes[(long long)i * a.Cp + c]);
+                    d2 = fmaf(d, d, d2);
+                }
+                const float e = expf(-a.lam * (d2 - dmin));
+                s0 += e;
+                s1 = fmaf((float)(i + 1), e, s1);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            }
+            if (lane == 0) {
+                const float sp = s1 / s0, z = dmin - logf(s0) / a.lam;
+                int bs = (int)floorf((sp - 1.0f) / (float)(a.npath - 1) * (float)a.bins);
+                int bz = (int)floorf((z - a.z_lo) / (a.z_hi - a.z_lo) * (float)a.bins);
+                bs = bs < 0 ? 0 : (bs >= a.bins ? a.bins - 1 : bs);
+                bz = bz < 0 ? 0 : (bz >= a.bins ? a.bins - 1 : bz);
+                atomicAdd(&a.histp[(long long)bs * a.bins + bz], 1ull);
+            }
+        }
     }
 }
 
@@ -158,8 +205,8 @@ struct McBufs {
 }  // namespace
 
 extern "C" RID_API int rid_mcmc(const rid_mcmc_desc* d, const float* s0, float* s_out, uint64_t* hist1_out,
-                                uint64_t* hist2_out, double* pmf1_out, double* pmf2_out, int64_t* n_accepted,
-                                int32_t mem, void* stream) {
+                                uint64_t* hist2_out, double* pmf1_out, double* pmf2_out, uint64_t* histp_out,
+                                double* pmfp_out, int64_t* n_accepted, int32_t mem, void* stream) {
     if (!d || !s0 || !d->weights) return rid_fail(RID_ERR_ARG, "mcmc: NULL argument");
     if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return rid_fail(RID_ERR_ARG, "mcmc: bad mem");
     const int M = d->n_models, C = d->n_cv, L = d->n_layers, H = d->width, W = d->n_walkers, bins = d->bins;
@@ -169,6 +216,14 @@ extern "C" RID_API int rid_mcmc(const rid_mcmc_desc* d, const float* s0, float* 
     if (d->n_steps < 0 || d->n_steps > 0xFFFFFFFFll || d->n_burn < 0 || !(d->kT > 0) || !(d->step_size >= 0) ||
         bins < 1 || bins > 4096 || d->proj_i < 0 || d->proj_i >= C || d->proj_j < 0 || d->proj_j >= C)
         return rid_fail(RID_ERR_ARG, "mcmc: run parameters out of range");
+    const int NP = d->path_n_nodes, Cp = d->path_n_cv;
+    if (NP != 0) {
+        if (NP < 2 || NP > 1024 || Cp < 1 || Cp > C || !d->path_cv || !d->path_nodes || !(d->path_lambda > 0) ||
+            !(d->path_z_hi > d->path_z_lo))
+            return rid_fail(RID_ERR_ARG, "mcmc: path projection parameters out of range");
+        for (int c = 0; c < Cp; ++c)
+            if (d->path_cv[c] < 0 || d->path_cv[c] >= C) return rid_fail(RID_ERR_ARG, "mcmc: path CV index out of range");
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const int D = 2 * C;
     long long woff[RID_MAX_LAYERS], boff[RID_MAX_LAYERS], o = 0;
@@ -183,31 +238,43 @@ extern "C" RID_API int rid_mcmc(const rid_mcmc_desc* d, const float* s0, float* 
     const long long nW = (long long)M * P, nS = (long long)W * C, nU = (long long)W * D, nH = (long long)M * W * H;
     const long long n1 = (long long)C * bins, n2 = (long long)bins * bins;
     const size_t bytes_f = sizeof(float) * (size_t)(nW + 2 * nS + W + nU + (d->resnet ? 3 : 2) * nH);
-    const size_t bytes_u = sizeof(unsigned long long) * (size_t)(n1 + n2 + 1);
-    const size_t bytes_d = sizeof(double) * (size_t)(n1 + n2);
+    const long long np2 = NP ? n2 : 0, npn = (long long)NP * Cp;
+    const size_t bytes_u = sizeof(unsigned long long) * (size_t)(n1 + n2 + np2 + 1);
+    const size_t bytes_d = sizeof(double) * (size_t)(n1 + n2 + np2);
+    const size_t bytes_p = sizeof(float) * (size_t)npn + sizeof(int) * (size_t)Cp;
     McBufs buf;
-    if (cudaMalloc(&buf.p, bytes_u + bytes_d + bytes_f) != cudaSuccess) {
+    if (cudaMalloc(&buf.p, bytes_u + bytes_d + bytes_f + bytes_p) != cudaSuccess) {
         cudaGetLastError();
-        return rid_fail(RID_ERR_OOM, "mcmc: device allocation of %zu bytes failed", bytes_u + bytes_d + bytes_f);
+        return rid_fail(RID_ERR_OOM, "mcmc: device allocation of %zu bytes failed", bytes_u + bytes_d + bytes_f + bytes_p);
     }
     unsigned long long* hist1 = reinterpret_cast<unsigned long long*>(buf.p);
     unsigned long long* hist2 = hist1 + n1;
-    unsigned long long* nacc = hist2 + n2;
+    unsigned long long* histp = hist2 + n2;
+    unsigned long long* nacc = histp + np2;
     double* pmf1 = reinterpret_cast<double*>(nacc + 1);
     double* pmf2 = pmf1 + n1;
-    float* wts = reinterpret_cast<float*>(pmf2 + n2);
+    double* pmfp = pmf2 + n2;
+    float* wts = reinterpret_cast<float*>(pmfp + np2);
     float* s = wts + nW;
     float* sp = s + nS;
     float* A = sp + nS;
     float* U = A + W;
     float* hb[2] = {U + nU, U + nU + nH};
     float* tb = d->resnet ? hb[1] + nH : nullptr;
+    float* pnodes = (d->resnet ? tb + nH : hb[1] + nH);
+    int* pcv = reinterpret_cast<int*>(pnodes + npn);
     const cudaMemcpyKind kin = mem == RID_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     const cudaMemcpyKind kout = mem == RID_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     cudaError_t e;
     if ((e = cudaMemcpyAsync(wts, d->weights, sizeof(float) * nW, kin, st)) != cudaSuccess) return mc_cuda(e, "weights");
     if ((e = cudaMemcpyAsync(s, s0, sizeof(float) * nS, kin, st)) != cudaSuccess) return mc_cuda(e, "s0");
     if ((e = cudaMemsetAsync(hist1, 0, bytes_u, st)) != cudaSuccess) return mc_cuda(e, "memset");
+    if (NP) {
+        if ((e = cudaMemcpyAsync(pnodes, d->path_nodes, sizeof(float) * npn, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return mc_cuda(e, "path nodes");
+        if ((e = cudaMemcpyAsync(pcv, d->path_cv, sizeof(int) * Cp, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return mc_cuda(e, "path CVs");
+    }
 
     const uint32_t k0 = (uint32_t)d->seed, k1 = (uint32_t)(d->seed >> 32);
     const int eb = (int)((nS + 255) / 256 < 4096 ? (nS + 255) / 256 : 4096);
@@ -254,6 +321,14 @@ extern "C" RID_API int rid_mcmc(const rid_mcmc_desc* d, const float* s0, float* 
     aa.hist1 = hist1;
     aa.hist2 = hist2;
     aa.nacc = nacc;
+    aa.npath = NP;
+    aa.Cp = Cp;
+    aa.pcv = pcv;
+    aa.pnodes = pnodes;
+    aa.lam = (float)d->path_lambda;
+    aa.z_lo = (float)d->path_z_lo;
+    aa.z_hi = (float)d->path_z_hi;
+    aa.histp = histp;
     const int wpb = 4;                                  // walkers (warps) per CTA
     const int ab = (W + wpb - 1) / wpb;
     k_mc_features<<<eb, 256, 0, st>>>(s, U, nS);
@@ -270,6 +345,7 @@ extern "C" RID_API int rid_mcmc(const rid_mcmc_desc* d, const float* s0, float* 
     }
     k_mc_pmf<<<C, PT, 0, st>>>(hist1, bins, d->kT, pmf1);
     k_mc_pmf<<<1, PT, 0, st>>>(hist2, (int)n2, d->kT, pmf2);
+    if (NP) k_mc_pmf<<<1, PT, 0, st>>>(histp, (int)n2, d->kT, pmfp);
     if ((e = cudaGetLastError()) != cudaSuccess) return mc_cuda(e, "launch");
     if (s_out && (e = cudaMemcpyAsync(s_out, s, sizeof(float) * nS, kout, st)) != cudaSuccess) return mc_cuda(e, "s_out");
     if (hist1_out && (e = cudaMemcpyAsync(hist1_out, hist1, sizeof(uint64_t) * n1, kout, st)) != cudaSuccess)
@@ -280,6 +356,10 @@ extern "C" RID_API int rid_mcmc(const rid_mcmc_desc* d, const float* s0, float* 
         return mc_cuda(e, "pmf1");
     if (pmf2_out && (e = cudaMemcpyAsync(pmf2_out, pmf2, sizeof(double) * n2, kout, st)) != cudaSuccess)
         return mc_cuda(e, "pmf2");
+    if (NP && histp_out && (e = cudaMemcpyAsync(histp_out, histp, sizeof(uint64_t) * n2, kout, st)) != cudaSuccess)
+        return mc_cuda(e, "hist_path");
+    if (NP && pmfp_out && (e = cudaMemcpyAsync(pmfp_out, pmfp, sizeof(double) * n2, kout, st)) != cudaSuccess)
+        return mc_cuda(e, "pmf_path");
     unsigned long long na = 0;
     if ((e = cudaMemcpyAsync(&na, nacc, sizeof(na), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return mc_cuda(e, "nacc");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return mc_cuda(e, "synchronize");

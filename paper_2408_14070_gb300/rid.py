@@ -66,7 +66,9 @@ class McmcDesc(C.Structure):
     _fields_ = [("n_models", C.c_int32), ("n_cv", C.c_int32), ("n_layers", C.c_int32), ("width", C.c_int32),
                 ("resnet", C.c_int32), ("weights", C.c_void_p), ("n_walkers", C.c_int32), ("n_steps", C.c_int64),
                 ("n_burn", C.c_int64), ("kT", C.c_double), ("step_size", C.c_double), ("seed", C.c_uint64),
-                ("bins", C.c_int32), ("proj_i", C.c_int32), ("proj_j", C.c_int32)]
+                ("bins", C.c_int32), ("proj_i", C.c_int32), ("proj_j", C.c_int32), ("path_n_nodes", C.c_int32),
+                ("path_n_cv", C.c_int32), ("path_cv", C.c_void_p), ("path_nodes", C.c_void_p),
+                ("path_lambda", C.c_double), ("path_z_lo", C.c_double), ("path_z_hi", C.c_double)]
 
 
 class SelectDesc(C.Structure):
@@ -144,7 +146,7 @@ def lib() -> C.CDLL:
                                         i32, vp]
     L.rid_select.argtypes = [C.POINTER(SelectDesc), i32, vp, vp, vp, C.POINTER(i32), C.POINTER(i32),
                              C.POINTER(C.c_double), i32, vp]
-    L.rid_mcmc.argtypes = [C.POINTER(McmcDesc), vp, vp, vp, vp, vp, vp, C.POINTER(i64), i32, vp]
+    L.rid_mcmc.argtypes = [C.POINTER(McmcDesc), vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(i64), i32, vp]
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype or C.c_int
     _lib = L
@@ -581,12 +583,14 @@ class Trainer:
 
 
 def mcmc(weights, n_models, n_cv, n_layers, width, s0, n_steps, n_burn, kT, step_size, seed, bins=101,
-         pair=(0, 1), resnet=False, s_out=None, hist1=None, hist2=None, pmf1=None, pmf2=None, stream=None):
+         pair=(0, 1), resnet=False, s_out=None, hist1=None, hist2=None, pmf1=None, pmf2=None, path=None,
+         hist_path=None, pmf_path=None, stream=None):
     """MCMC dimension reduction (rid_mcmc): W = len(s0) walkers, Metropolis on
     the ensemble-mean free energy; returns the number of accepted moves.
     Outputs (optional, all on the side of s0): s_out [W][C] float32, hist1
     [C][bins] and hist2 [bins][bins] uint64, pmf1 / pmf2 of the same shapes
-    float64."""
+    float64.  path = (nodes [P][Cp], cvs [Cp], lambda, z_lo, z_hi) adds the
+    (s_path, z_path) projection into hist_path / pmf_path [bins][bins]."""
     a = _Args()
     W, Cn = int(s0.shape[0]), int(n_cv)
     pw = a.ptr(weights, np.float32)
@@ -596,10 +600,21 @@ def mcmc(weights, n_models, n_cv, n_layers, width, s0, n_steps, n_burn, kT, step
     h2 = a.ptr(hist2, np.uint64, (bins, bins), True)
     f1 = a.ptr(pmf1, np.float64, (Cn, bins), True)
     f2 = a.ptr(pmf2, np.float64, (bins, bins), True)
+    hp = a.ptr(hist_path, np.uint64, (bins, bins), True)
+    fp = a.ptr(pmf_path, np.float64, (bins, bins), True)
+    nodes = cvs = None
+    npn, ncv, lam, zlo, zhi = 0, 0, 1.0, 0.0, 1.0
+    if path is not None:
+        nodes = np.ascontiguousarray(path[0], dtype=np.float32)
+        cvs = np.ascontiguousarray(path[1], dtype=np.int32)
+        npn, ncv = nodes.shape[0], cvs.size
+        lam, zlo, zhi = float(path[2]), float(path[3]), float(path[4])
     d = McmcDesc(int(n_models), Cn, int(n_layers), int(width), int(bool(resnet)), pw.value, W, int(n_steps),
-                 int(n_burn), float(kT), float(step_size), int(seed), int(bins), int(pair[0]), int(pair[1]))
+                 int(n_burn), float(kT), float(step_size), int(seed), int(bins), int(pair[0]), int(pair[1]),
+                 npn, ncv, None if cvs is None else cvs.ctypes.data, None if nodes is None else nodes.ctypes.data,
+                 lam, zlo, zhi)
     nacc = C.c_int64(0)
-    _check(lib().rid_mcmc(C.byref(d), ps, po, h1, h2, f1, f2, C.byref(nacc), a.mem, _stream_ptr(stream)))
+    _check(lib().rid_mcmc(C.byref(d), ps, po, h1, h2, f1, f2, hp, fp, C.byref(nacc), a.mem, _stream_ptr(stream)))
     return nacc.value
 
 

@@ -133,3 +133,26 @@ def test_errors(R):
     with pytest.raises(R.RidError) as e:
         R.mcmc(ens.weights, 1, 2, 2, 16, s0, 5, 0, 0.0, 0.3, 1, bins=10)
     assert e.value.code == R.RID_ERR_ARG
+
+
+def test_path_projection_follows_the_oracle(R):
+    # path nodes along a line in the (CV 0, CV 2) plane; the walkers' path
+    # histogram against the oracle's on the same trajectories: the walkers
+    # whose accept decisions came near the threshold may differ, and FP32
+    # against FP64 can move a count across a bin edge
+    M, C, L, H, W, K = 2, 4, 2, 32, 256, 30
+    ens = I.make_ensemble(M, 2 * C, L, H, 35)
+    s0 = np.random.default_rng(4).uniform(-math.pi, math.pi, size=(W, C)).astype(np.float32)
+    nodes = np.stack([np.linspace(-2.5, 2.5, 9), np.linspace(1.0, -1.0, 9)], axis=1).astype(np.float32)
+    path = (nodes, [0, 2], 2.0, -1.0, 3.0)
+    bins = 25
+    hp = np.zeros((bins, bins), np.uint64)
+    fp = np.zeros((bins, bins))
+    R.mcmc(ens.weights, M, C, L, H, s0, K, 10, 1.0, 0.4, 12, bins=bins, path=path, hist_path=hp, pmf_path=fp)
+    ref = MC.run(ens.weights, C, L, H, False, s0, K, 10, 1.0, 0.4, 12, bins, (0, 1), path=path)
+    unsafe = int((ref["min_margin"] <= 1e-3).sum())
+    diff = int(np.abs(hp.astype(np.int64) - ref["hist_path"]).sum())
+    print(f"\npath histogram: |GPU - oracle|_1 = {diff} of {W * (K - 10)} counts, near-threshold walkers {unsafe}")
+    assert int(hp.sum()) == W * (K - 10)
+    assert diff <= 2 * unsafe * (K - 10) + 0.01 * W * (K - 10)
+    np.testing.assert_allclose(fp, MC.projected_pmf(hp, 1.0), rtol=1e-12, atol=1e-12)

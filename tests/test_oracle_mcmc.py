@@ -96,3 +96,32 @@ def test_binning_edges_and_projection():
     f = MC.projected_pmf(np.array([10, 0, 40, 50]), 2.0)
     assert f[3] == 0.0 and math.isinf(f[1])
     assert f[0] == pytest.approx(-2.0 * math.log(10 / 50))
+
+
+def test_path_cv_limits():
+    # nodes far apart on the torus: at node k, s -> k and z -> 0; between two
+    # neighbouring nodes s is the weighted index; large and small lambda agree
+    # with the plain formula
+    nodes = np.array([[-2.0, 0.0], [-1.0, 0.5], [0.0, 1.0], [1.0, 0.5], [2.0, 0.0]])
+    pts = np.zeros((5, 3))
+    pts[:, [0, 2]] = nodes
+    sp, z = MC.path_cv(pts, nodes, [0, 2], 40.0)
+    np.testing.assert_allclose(sp, np.arange(1, 6), atol=1e-6)
+    np.testing.assert_allclose(z, 0.0, atol=1e-6)
+    rng = np.random.default_rng(8)
+    q = np.zeros((50, 3))
+    q[:, [0, 2]] = rng.uniform(-0.8, 0.8, size=(50, 2))   # no difference wraps
+    for lam in (0.25, 3.0):
+        sp, z = MC.path_cv(q, nodes, [0, 2], lam)
+        d2 = ((q[:, None, [0, 2]] - nodes[None]) ** 2).sum(-1)
+        e = np.exp(-lam * d2)
+        np.testing.assert_allclose(sp, (e * np.arange(1, 6)).sum(1) / e.sum(1), rtol=1e-12)
+        np.testing.assert_allclose(z, -np.log(e.sum(1)) / lam, rtol=1e-12)
+    # periodic: a point just across pi from the last node
+    far = np.zeros((1, 3))
+    far[0, 0] = 2.0 - 2 * math.pi
+    sp, z = MC.path_cv(far, nodes, [0, 2], 40.0)
+    assert sp[0] == pytest.approx(5.0, abs=1e-6) and z[0] == pytest.approx(0.0, abs=1e-6)
+    bs, bz = MC.path_bins(np.array([1.0, 3.0, 5.0]), np.array([-1.0, 0.5, 9.0]), 5, 0.0, 1.0, 10)
+    np.testing.assert_array_equal(bs, [0, 5, 9])
+    np.testing.assert_array_equal(bz, [0, 5, 9])
