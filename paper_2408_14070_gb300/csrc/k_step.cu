@@ -474,7 +474,7 @@ static void head_e(const HeadArgs& a, cudaStream_t s) {
 
 template <int MODE>
 static void head_m(const HeadArgs& a, cudaStream_t s) {
-    // (FIN, KICK, INT) combinations used by the driver
+    // (FIN, KICK, INT) combinations used by the host code
     if (!a.fin && a.integ == 1) head_e<MODE, false, false, 1>(a, s);
     else if (!a.fin && a.integ == 2) head_e<MODE, false, false, 2>(a, s);
     else if (a.fin && a.kick && a.integ == 2) head_e<MODE, true, true, 2>(a, s);

@@ -478,7 +478,7 @@ static int build_tc_variant(rid_system* sys, const std::vector<float>& W, long l
     TRY(V.wscale.ensure(scale.size() * sizeof(float)));
     CK(cudaMemcpy(V.wscale.p, scale.data(), scale.size() * sizeof(float), cudaMemcpyHostToDevice));
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-    if (!enc) return fail(RID_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    if (!enc) return fail(RID_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the CUDA driver");
     const cuuint64_t dims[2] = {128, (cuuint64_t)M * rows};
     const cuuint64_t strides[1] = {128};
     const cuuint32_t estr[2] = {1, 1};
