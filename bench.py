@@ -45,6 +45,42 @@ from paper_2408_14070_gb300 import inputs as I  # noqa: E402
 WORKLOAD = "chain_n200_w1024"
 FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+_FP32_MEASURED = None
+
+
+def fp32_peak(torch):
+    """(peak TFLOP/s, source) for FP32 ALU-bound kernels: dense FP32 throughput
+    measured on this GPU with a library GEMM (cuBLAS SGEMM 8192^3, TF32 off),
+    as the BF16 peak is measured with cuBLAS; the derived figure if that fails."""
+    global _FP32_MEASURED
+    if _FP32_MEASURED is None:
+        try:
+            prev_tf32, prev_prec = torch.backends.cuda.matmul.allow_tf32, torch.get_float32_matmul_precision()
+            torch.backends.cuda.matmul.allow_tf32 = False
+            torch.set_float32_matmul_precision("highest")
+            n = 8192
+            g = torch.Generator(device="cuda").manual_seed(0)
+            a = torch.randn(n, n, device="cuda", generator=g)
+            b = torch.randn(n, n, device="cuda", generator=g)
+            for _ in range(3):
+                a @ b
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 10
+            torch.backends.cuda.matmul.allow_tf32 = prev_tf32
+            torch.set_float32_matmul_precision(prev_prec)
+            del a, b
+            _FP32_MEASURED = (2.0 * n ** 3 / (ms * 1e-3) / 1e12,
+                              "measured: cuBLAS FP32 SGEMM 8192^3, TF32 off, in this run "
+                              f"(derived {FP32_PEAK_TFLOPS:.1f} TFLOP/s = {FP32_PEAK_NOTE})")
+        except Exception as e:   # measurement unavailable: the derived peak
+            _FP32_MEASURED = (FP32_PEAK_TFLOPS, f"derived: {FP32_PEAK_NOTE} ({type(e).__name__})")
+    return _FP32_MEASURED
 
 
 def workload_desc(wl):
@@ -291,8 +327,8 @@ def run_training(rid, torch, steps, seed=11):
             "ms_per_step": ms / steps, "kernel_launches_per_step": 5 * L + 3,
             "loss_first": float(lo[:warm].mean()), "loss_last": float(lo[-20:].mean()),
             "algorithmic_gflop_per_step": fl / 1e9,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "peak_source": FP32_PEAK_NOTE},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak(torch)[0], "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak(torch)[0], "peak_source": fp32_peak(torch)[1]},
             "timed": "one rid_trainer_run call of all steps (device-resident labels and batch indices), "
                      "CUDA events on the launching stream"}
 
@@ -325,8 +361,8 @@ def run_mcmc(rid, torch, steps, seed=13):
                         f"{bins} bins per CV, 2-D projection on CVs (0, 1)",
             "value": W * steps / (ms * 1e-3), "unit": "walker-steps/s", "ms_per_step": ms / steps,
             "acceptance": acc / (W * steps), "kernel_launches_per_step": L + 2,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "peak_source": FP32_PEAK_NOTE},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak(torch)[0], "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak(torch)[0], "peak_source": fp32_peak(torch)[1]},
             "timed": "one rid_mcmc call (device-resident weights and starting CVs; includes the call's "
                      "allocation, the initial evaluation and the PMF projection), CUDA events"}
 
@@ -720,7 +756,7 @@ def main():
         achieved = work / (avg_ms / 1e3) / 1e12
     elif top == "k_mlp_fp32":
         work, src = mlp_flops_per_walker_step(wl) * W, "k_mlp_fp32.cu"
-        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS, "peak_source": f"derived: {FP32_PEAK_NOTE}"}
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak(torch)[0], "peak_source": fp32_peak(torch)[1]}
         achieved = work / (avg_ms / 1e3) / 1e12
     elif top == "k_head":
         # integrator: read x, v, f and write x, v (12 B each) per bead
@@ -731,7 +767,7 @@ def main():
         achieved = work / (avg_ms / 1e3) / 1e9
     else:
         work, src = pair_flops_per_walker_step(wl) * W, "k_step.cu"
-        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS, "peak_source": f"derived: {FP32_PEAK_NOTE}"}
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak(torch)[0], "peak_source": fp32_peak(torch)[1]}
         achieved = work / (avg_ms / 1e3) / 1e12
     roofline = {"kernel": top, "bound": roof["bound"], "achieved": achieved, "peak": roof["peak"],
                 "unit": roof["unit"], "frac": achieved / roof["peak"] if roof["peak"] else None,
@@ -779,7 +815,8 @@ def main():
                       "mlp_precision": args.precision, "forces_integrator": "f32",
                       "l2": "flushed (256 MiB write) before every timed step; each step timed alone",
                       "parallelism": f"walkers sharded, {world} independent rank(s)"},
-           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary()}
+           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+           "fp32_peak": {"value": fp32_peak(torch)[0], "unit": "TFLOP/s", "source": fp32_peak(torch)[1]}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sp, x0, ens, args.cpu_walkers, args.cpu_steps)
     if rank == 0 and world == 1 and not args.no_batching:
