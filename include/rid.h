@@ -309,6 +309,21 @@ RID_API int rid_mcmc(const rid_mcmc_desc* desc, const float* s0, float* s_out, u
                      int32_t mem, void* stream);
 
 /*
+ * The same MCMC dimension reduction (proposal, rule, counting and PMF as
+ * rid_mcmc) with the ensemble a system holds (rid_set_ensemble): the free
+ * energy of each proposal is evaluated by the system's own ensemble kernels at
+ * the precision the ensemble was set with (RID_PREC_FP32 / BF16 / FP8; the
+ * tensor-core kernels for BF16 and FP8).  C is the system's CV count; s0
+ * [W][C].  The system's resident walker buffers are reused (walkers loaded
+ * with rid_walkers_load must be loaded again).  No path projection.
+ * Errors: RID_ERR_ARG, RID_ERR_STATE (no ensemble), RID_ERR_OOM, RID_ERR_CUDA.
+ */
+RID_API int rid_mcmc_system(rid_system* sys, int32_t n_walkers, const float* s0, int64_t n_steps, int64_t n_burn,
+                            double kT, double step_size, uint64_t seed, int32_t bins, int32_t proj_i, int32_t proj_j,
+                            float* s_out, uint64_t* hist1, uint64_t* hist2, double* pmf1, double* pmf2,
+                            int64_t* n_accepted, int32_t mem, void* stream);
+
+/*
  * Selection (Sec. "Selection phase": cluster_threshold, numb_cluster_lower,
  * numb_cluster_upper, max_selection; Sec. "Selection": explored CVs are
  * clustered and values with high model deviation are collected by the trust

@@ -85,6 +85,9 @@ struct AcceptArgs {
     const float* pnodes;         // [P][Cp]
     float lam, z_lo, z_hi;
     unsigned long long* histp;   // [bins][bins]
+    // member values from a system's ensemble kernels ([na][W], na = M x slices) instead of h . w_out
+    const float* aval;
+    int na;
 };
 
 __global__ void k_mc_accept(AcceptArgs a) {
@@ -92,14 +95,22 @@ __global__ void k_mc_accept(AcceptArgs a) {
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= a.W) return;                       // whole warps only
     float abar = 0.0f;
-    for (int m = 0; m < a.M; ++m) {
-        const float* wo = a.w + (long long)m * a.P + a.ooff;
-        const float* h = a.h + ((long long)m * a.W + w) * a.H;
+    if (a.aval) {
         float part = 0.0f;
-        for (int j = lane; j < a.H; j += 32) part = fmaf(wo[j], h[j], part);
+        for (int k = lane; k < a.na; k += 32) part += a.aval[(long long)k * a.W + w];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        abar += part + wo[a.H];
+        abar = part;
+    } else {
+        for (int m = 0; m < a.M; ++m) {
+            const float* wo = a.w + (long long)m * a.P + a.ooff;
+            const float* h = a.h + ((long long)m * a.W + w) * a.H;
+            float part = 0.0f;
+            for (int j = lane; j < a.H; j += 32) part = fmaf(wo[j], h[j], part);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            abar += part + wo[a.H];
+        }
     }
     abar /= (float)a.M;
     float* s = a.s + (long long)w * a.C;
@@ -365,4 +376,52 @@ extern "C" RID_API int rid_mcmc(const rid_mcmc_desc* d, const float* s0, float* 
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return mc_cuda(e, "synchronize");
     if (n_accepted) *n_accepted = (int64_t)na;
     return RID_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers for rid_mcmc_system (rid_api.cu), which evaluates the ensemble
+// with a system's own kernels and precision.
+void rid_launch_mc_features(const float* s, float* U, long long n, cudaStream_t st) {
+    const int eb = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    k_mc_features<<<eb, 256, 0, st>>>(s, U, n);
+}
+
+void rid_launch_mc_propose(const float* s, float* sp, float* U, int W, int C, uint32_t step, float step_size,
+                           uint32_t k0, uint32_t k1, cudaStream_t st) {
+    const long long n = (long long)W * C;
+    const int eb = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    k_mc_propose<<<eb, 256, 0, st>>>(s, sp, U, W, C, step, step_size, k0, k1);
+}
+
+void rid_launch_mc_accept_values(const float* aval, int na, int M, int W, int C, float* s, const float* sp, float* A,
+                                 uint32_t step, float kT, uint32_t k0, uint32_t k1, int init, int count, int bins,
+                                 int pi, int pj, unsigned long long* hist1, unsigned long long* hist2,
+                                 unsigned long long* nacc, cudaStream_t st) {
+    AcceptArgs a{};
+    a.aval = aval;
+    a.na = na;
+    a.M = M;
+    a.W = W;
+    a.C = C;
+    a.s = s;
+    a.sp = sp;
+    a.A = A;
+    a.step = step;
+    a.k0 = k0;
+    a.k1 = k1;
+    a.kT = kT;
+    a.init = init;
+    a.count = count;
+    a.bins = bins;
+    a.pi = pi;
+    a.pj = pj;
+    a.hist1 = hist1;
+    a.hist2 = hist2;
+    a.nacc = nacc;
+    const int wpb = 4;
+    k_mc_accept<<<(W + wpb - 1) / wpb, 32 * wpb, 0, st>>>(a);
+}
+
+void rid_launch_mc_pmf(const unsigned long long* hist, int rows, int n, double kT, double* pmf, cudaStream_t st) {
+    k_mc_pmf<<<rows, PT, 0, st>>>(hist, n, kT, pmf);
 }

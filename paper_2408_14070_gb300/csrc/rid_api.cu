@@ -1086,6 +1086,80 @@ extern "C" int rid_label(rid_system* sys, int32_t R, const float* x0, const floa
     return RID_OK;
 }
 
+// MCMC dimension reduction with the system's own ensemble evaluation
+// (k_mcmc.cu kernels around launch_mlp): proposals are written as the MLP
+// input of W resident walkers and the member values come from the ensemble
+// kernels at the precision the ensemble was set with.  The walker buffers are
+// reused (like rid_label); scratch for the chain state and histograms is
+// allocated for the call.
+extern "C" int rid_mcmc_system(rid_system* sys, int32_t W, const float* s0, int64_t n_steps, int64_t n_burn,
+                               double kT, double step_size, uint64_t seed, int32_t bins, int32_t proj_i,
+                               int32_t proj_j, float* s_out, uint64_t* hist1_out, uint64_t* hist2_out,
+                               double* pmf1_out, double* pmf2_out, int64_t* n_accepted, int32_t mem, void* stream) {
+    if (!sys || !s0) return fail(RID_ERR_ARG, "NULL argument");
+    if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "mem must be RID_MEM_HOST or RID_MEM_DEVICE");
+    if (!sys->has_ens) return fail(RID_ERR_STATE, "no ensemble set");
+    const int C = sys->S.C;
+    if (W < 1 || n_steps < 0 || n_steps > 0xFFFFFFFFll || n_burn < 0 || !(kT > 0) || !(step_size >= 0) || bins < 1 ||
+        bins > 4096 || proj_i < 0 || proj_i >= C || proj_j < 0 || proj_j >= C)
+        return fail(RID_ERR_ARG, "mcmc: parameters out of range");
+    if ((long long)W * sys->S.N > (1ll << 31)) return fail(RID_ERR_ARG, "n_walkers * n_beads too large");
+    TRY(check_device(sys));
+    sys->loaded = false;   // the resident walker buffers are reused
+    sys->pending = false;
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(ensure_state(sys, W));
+    StateDev sd = state_view(sys);
+    sd.W = W;
+    const long long nS = (long long)W * C, n1 = (long long)C * bins, n2 = (long long)bins * bins;
+    struct Scoped {
+        DevBuf b;
+        ~Scoped() { b.release(); }
+    } scoped;
+    const size_t o_h1 = 0, o_h2 = o_h1 + 8 * n1, o_na = o_h2 + 8 * n2, o_p1 = o_na + 16, o_p2 = o_p1 + 8 * n1;
+    const size_t o_s = o_p2 + 8 * n2, o_sp = o_s + 4 * nS, o_A = o_sp + 4 * nS;
+    TRY(scoped.b.ensure(o_A + 4 * (size_t)W));
+    unsigned char* b = static_cast<unsigned char*>(scoped.b.p);
+    auto* h1 = reinterpret_cast<unsigned long long*>(b + o_h1);
+    auto* h2 = reinterpret_cast<unsigned long long*>(b + o_h2);
+    auto* na = reinterpret_cast<unsigned long long*>(b + o_na);
+    double* p1 = reinterpret_cast<double*>(b + o_p1);
+    double* p2 = reinterpret_cast<double*>(b + o_p2);
+    float* ds = reinterpret_cast<float*>(b + o_s);
+    float* dsp = reinterpret_cast<float*>(b + o_sp);
+    float* dA = reinterpret_cast<float*>(b + o_A);
+    const cudaMemcpyKind kin = mem == RID_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind kout = mem == RID_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(ds, s0, sizeof(float) * nS, kin, st));
+    CK(cudaMemsetAsync(b, 0, o_p1, st));
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const int M = sys->E.M, nav = M * sys->E.aslices;
+    rid_launch_mc_features(ds, sd.u, nS, st);
+    TRY(launch_mlp(sys, W, 1, sd, st));
+    rid_launch_mc_accept_values(sd.Aval, nav, M, W, C, ds, dsp, dA, 0u, (float)kT, k0, k1, 1, 0, bins, proj_i, proj_j,
+                                h1, h2, na, st);
+    for (int64_t t = 0; t < n_steps; ++t) {
+        rid_launch_mc_propose(ds, dsp, sd.u, W, C, (uint32_t)t, (float)step_size, k0, k1, st);
+        TRY(launch_mlp(sys, W, 1, sd, st));
+        rid_launch_mc_accept_values(sd.Aval, nav, M, W, C, ds, dsp, dA, (uint32_t)t, (float)kT, k0, k1, 0,
+                                    t >= n_burn, bins, proj_i, proj_j, h1, h2, na, st);
+    }
+    rid_launch_mc_pmf(h1, C, bins, kT, p1, st);
+    rid_launch_mc_pmf(h2, 1, (int)n2, kT, p2, st);
+    CK(cudaGetLastError());
+    if (s_out) CK(cudaMemcpyAsync(s_out, ds, sizeof(float) * nS, kout, st));
+    if (hist1_out) CK(cudaMemcpyAsync(hist1_out, h1, 8 * n1, kout, st));
+    if (hist2_out) CK(cudaMemcpyAsync(hist2_out, h2, 8 * n2, kout, st));
+    if (pmf1_out) CK(cudaMemcpyAsync(pmf1_out, p1, 8 * n1, kout, st));
+    if (pmf2_out) CK(cudaMemcpyAsync(pmf2_out, p2, 8 * n2, kout, st));
+    unsigned long long hna = 0;
+    CK(cudaMemcpyAsync(&hna, na, sizeof(hna), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (n_accepted) *n_accepted = (int64_t)hna;
+    sys->launches += 3 + 3 * n_steps + 2;
+    return RID_OK;
+}
+
 // Constrained-MD labels on distance CVs (k_label_cons.cu).  Scratch for the
 // call is allocated here and released before returning.
 extern "C" int rid_label_constrained(rid_system* sys, int32_t R, const float* x0, const float* v0, int32_t C,

@@ -161,6 +161,14 @@ void rid_launch_mb(const SysDev& S, StateDev st, int W, uint32_t step0, cudaStre
 void rid_launch_pair_mask(const SysDev& S, StateDev st, int W, uint32_t* mask, cudaStream_t s);
 int rid_ff_smem_bytes(int N);
 size_t rid_label_cons_smem(int N, int C);
+void rid_launch_mc_features(const float* s, float* U, long long n, cudaStream_t st);
+void rid_launch_mc_propose(const float* s, float* sp, float* U, int W, int C, uint32_t step, float step_size,
+                           uint32_t k0, uint32_t k1, cudaStream_t st);
+void rid_launch_mc_accept_values(const float* aval, int na, int M, int W, int C, float* s, const float* sp, float* A,
+                                 uint32_t step, float kT, uint32_t k0, uint32_t k1, int init, int count, int bins,
+                                 int pi, int pj, unsigned long long* hist1, unsigned long long* hist2,
+                                 unsigned long long* nacc, cudaStream_t st);
+void rid_launch_mc_pmf(const unsigned long long* hist, int rows, int n, double kT, double* pmf, cudaStream_t st);
 cudaError_t rid_launch_label_cons(const SysDev& S, int R, int C, int B, long long n_steps, long long n_equil,
                                   uint32_t step0, float kT, const float4* x0, const float4* v0, const int2* pairs,
                                   const float* d0, double* bsum, double* mf, double* se, double* sd, float4* x_out,

@@ -29,7 +29,7 @@ EXPORTS = ("rid_version", "rid_status_string", "rid_last_error", "rid_create_sys
            "rid_server_destroy", "rid_label_batch", "rid_submit", "rid_poll", "rid_server_load",
            "rid_trainer_create", "rid_trainer_destroy", "rid_trainer_set_data", "rid_trainer_run",
            "rid_trainer_grad", "rid_trainer_weights", "rid_mcmc", "rid_select",
-           "rid_label_constrained")
+           "rid_label_constrained", "rid_mcmc_system")
 RID_NOT_READY = 6
 RID_JOB_LABEL, RID_JOB_EXPLORE = 1, 2
 
@@ -144,6 +144,8 @@ def lib() -> C.CDLL:
     L.rid_trainer_weights.argtypes = [vp, vp, C.POINTER(i64), i32, vp]
     L.rid_label_constrained.argtypes = [vp, i32, vp, vp, i32, vp, vp, u64, i64, i64, i32, vp, vp, vp, vp, vp,
                                         i32, vp]
+    L.rid_mcmc_system.argtypes = [vp, i32, vp, i64, i64, C.c_double, C.c_double, u64, i32, i32, i32, vp, vp, vp,
+                                  vp, vp, C.POINTER(i64), i32, vp]
     L.rid_select.argtypes = [C.POINTER(SelectDesc), i32, vp, vp, vp, C.POINTER(i32), C.POINTER(i32),
                              C.POINTER(C.c_double), i32, vp]
     L.rid_mcmc.argtypes = [C.POINTER(McmcDesc), vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(i64), i32, vp]
@@ -292,6 +294,22 @@ class System:
         _check(lib().rid_label_constrained(self.h, R, *args, Cn, pr.ctypes.data, pd0, C.c_uint64(step0),
                                            C.c_int64(n_steps), C.c_int64(n_equil), int(n_blocks), *outs, a.mem,
                                            _stream_ptr(stream)))
+
+    def mcmc(self, s0, n_steps, n_burn, kT, step_size, seed, bins=101, pair=(0, 1), s_out=None, hist1=None,
+             hist2=None, pmf1=None, pmf2=None, stream=None):
+        """MCMC dimension reduction with this system's ensemble at its precision
+        (rid_mcmc_system); returns the number of accepted moves."""
+        W = int(s0.shape[0])
+        a = _Args()
+        ps = a.ptr(s0, np.float32, (W, self.C))
+        outs = [a.ptr(s_out, np.float32, (W, self.C), True), a.ptr(hist1, np.uint64, (self.C, bins), True),
+                a.ptr(hist2, np.uint64, (bins, bins), True), a.ptr(pmf1, np.float64, (self.C, bins), True),
+                a.ptr(pmf2, np.float64, (bins, bins), True)]
+        nacc = C.c_int64(0)
+        _check(lib().rid_mcmc_system(self.h, W, ps, C.c_int64(n_steps), C.c_int64(n_burn), float(kT),
+                                     float(step_size), C.c_uint64(seed), int(bins), int(pair[0]), int(pair[1]), *outs,
+                                     C.byref(nacc), a.mem, _stream_ptr(stream)))
+        return nacc.value
 
     def eval_forces(self, x, bias=RID_BIAS_NONE, s0=None, kappa=None, f_out=None, s_out=None, eps_out=None,
                     abar_out=None, grad_out=None, stream=None):

@@ -156,3 +156,51 @@ def test_path_projection_follows_the_oracle(R):
     assert int(hp.sum()) == W * (K - 10)
     assert diff <= 2 * unsafe * (K - 10) + 0.01 * W * (K - 10)
     np.testing.assert_allclose(fp, MC.projected_pmf(hp, 1.0), rtol=1e-12, atol=1e-12)
+
+
+def test_system_path_fp32_follows_the_oracle(R):
+    # the system's own FP32 ensemble kernels evaluate the proposals
+    M, C, L, H, W, K = 4, 6, 3, 64, 192, 25
+    sp = I.make_system(40, C, 36)
+    ens = I.make_ensemble(M, 2 * C, L, H, 36)
+    s0 = np.random.default_rng(6).uniform(-math.pi, math.pi, size=(W, C)).astype(np.float32)
+    s = np.zeros_like(s0)
+    with R.System(sp) as sysobj:
+        sysobj.set_ensemble(ens, precision=R.RID_PREC_FP32)
+        nacc = sysobj.mcmc(s0, K, 0, 1.0, 0.3, 21, bins=51, s_out=s)
+    ref = MC.run(ens.weights, C, L, H, False, s0, K, 0, 1.0, 0.3, 21, 51, (0, 1))
+    safe = ref["min_margin"] > 1e-3
+    assert safe.mean() > 0.9
+    assert np.max(_wrapdiff(s[safe], ref["s"][safe])) < 1e-4
+    assert abs(nacc - ref["n_accepted"]) <= K * int((~safe).sum())
+
+
+@pytest.mark.parametrize("prec,bound", [("bf16", 0.02), ("fp8", 0.06)])
+def test_system_path_tensor_cores_sample_the_stationary_marginal(R, prec, bound):
+    # BF16 / FP8 ensembles on the tensor cores: the sampled joint of two CVs
+    # against exp(-Abar/kT) of the FP64 network.  The low-precision forward
+    # pass moves Abar by its relative error (BF16 about 5e-3, FP8 e4m3 about
+    # 2e-2, the precision sweep's figures) times a landscape spanning a few kT,
+    # so bin weights move by up to ~1% (BF16) and ~5% (FP8); the sampling
+    # noise adds about 3e-3.  Measured: 3e-3 (BF16), 2.8e-2 (FP8).
+    C, L, H, bins, kT = 2, 2, 32, 12, 1.0
+    rng = np.random.default_rng(2)
+    w = (rng.normal(0.0, 1.0, size=(1, T.param_count(2 * C, L, H))) * 0.5).astype(np.float32)
+    n = bins * 12
+    g = -math.pi + (np.arange(n) + 0.5) * (2 * math.pi / n)
+    gx, gy = np.meshgrid(g, g, indexing="ij")
+    A = MC.ensemble_mean_value(w, 2 * C, L, H, False, np.stack([gx.ravel(), gy.ravel()], 1))
+    p = np.exp(-(A - A.min()) / kT).reshape(n, n)
+    p = np.add.reduceat(np.add.reduceat(p, np.arange(0, n, 12), axis=0), np.arange(0, n, 12), axis=1)
+    p /= p.sum()
+    W, K, burn = 4096, 1200, 200
+    s0 = rng.uniform(-math.pi, math.pi, size=(W, C)).astype(np.float32)
+    h2 = np.zeros((bins, bins), np.uint64)
+    ens = I.EnsembleParams(1, 2 * C, L, H, False, w, 1e9, 2e9)
+    with R.System(I.make_system(22, C, 37)) as sysobj:
+        sysobj.set_ensemble(ens, precision={"bf16": R.RID_PREC_BF16, "fp8": R.RID_PREC_FP8}[prec])
+        sysobj.mcmc(s0, K, burn, kT, 0.9, 3, bins=bins, pair=(0, 1), hist2=h2)
+    assert int(h2.sum()) == W * (K - burn)
+    tv = 0.5 * np.abs(h2 / h2.sum() - p).sum()
+    print(f"\n[{prec}] total variation against the exact joint: {tv:.4f}")
+    assert tv < bound, tv
