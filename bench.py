@@ -48,6 +48,13 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 _FP32_MEASURED = None
 
 
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
 def fp32_peak(torch):
     """(peak TFLOP/s, source) for FP32 ALU-bound kernels: dense FP32 throughput
     measured on this GPU with a library GEMM (cuBLAS SGEMM 8192^3, TF32 off),
@@ -357,6 +364,19 @@ def run_mcmc(rid, torch, steps, seed=13):
     ms = e0.elapsed_time(e1)
     fl = M * 2 * (D * H + (L - 1) * H * H + H) * W        # forward GEMMs and the output layer, per step
     achieved = fl * steps / (ms * 1e-3) / 1e12
+    # the same chain with the system's BF16 ensemble on the tensor cores (rid_mcmc_system)
+    sp = I.make_system(wl["n_beads"], C, seed)
+    with rid.System(sp) as system:
+        system.set_ensemble(ens, precision=rid.RID_PREC_BF16)
+        system.mcmc(s0, 20, 0, 1.0, 0.3, seed, bins=bins, hist1=h1, pmf2=f2, stream=stream)   # warm, tunes
+        torch.cuda.synchronize()
+        e0.record(stream)
+        acc16 = system.mcmc(s0, steps, burn, 1.0, 0.3, seed, bins=bins, hist1=h1, pmf2=f2, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms16 = e0.elapsed_time(e1)
+    bf16 = _peaks().get("bf16_tflops") or 1900.0
+    ach16 = fl * steps / (ms16 * 1e-3) / 1e12
     return {"workload": f"{W} walkers, {M} members {D}-{H}x{L}-1, {steps} Metropolis steps ({burn} burn-in), "
                         f"{bins} bins per CV, 2-D projection on CVs (0, 1)",
             "value": W * steps / (ms * 1e-3), "unit": "walker-steps/s", "ms_per_step": ms / steps,
@@ -364,7 +384,16 @@ def run_mcmc(rid, torch, steps, seed=13):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak(torch)[0], "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak(torch)[0], "peak_source": fp32_peak(torch)[1]},
             "timed": "one rid_mcmc call (device-resident weights and starting CVs; includes the call's "
-                     "allocation, the initial evaluation and the PMF projection), CUDA events"}
+                     "allocation, the initial evaluation and the PMF projection), CUDA events",
+            "bf16_tensor_cores": {
+                "value": W * steps / (ms16 * 1e-3), "unit": "walker-steps/s", "ms_per_step": ms16 / steps,
+                "acceptance": acc16 / (W * steps),
+                "path": "rid_mcmc_system: the system's BF16 ensemble kernel (tcgen05), which also forms the "
+                        "input gradient that MCMC does not use",
+                "roofline": {"bound": "tensor", "achieved": ach16, "peak": bf16, "unit": "TFLOP/s",
+                             "frac": ach16 / bf16, "work": "forward flops only (what the Metropolis test needs)",
+                             "peak_source": "measured bf16_tflops (burst)" if _peaks().get("bf16_tflops")
+                             else "fallback 1.9 PFLOP/s bf16"}}}
 
 
 def run_selection(rid, torch, seed=17):
