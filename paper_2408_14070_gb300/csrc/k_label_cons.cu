@@ -88,10 +88,10 @@ __device__ void cons_forces(const SysDev& S, float4* xs, float4* cbox, float3* f
         const int b1 = whi + 2 < N - 1 ? whi + 2 : N - 1;
         float fx = 0.f, fy = 0.f, fz = 0.f, el = 0.f;
         if (sig1)
-            lj_row_culled<true, false>(S, xs, keep_s[warp], nwords, xi, i, b0 / LJ_CLUSTER, b1 / LJ_CLUSTER, fx, fy,
+            lj_row_culled<true, false, true>(S, xs, cbox, keep_s[warp], nwords, xi, i, b0 / LJ_CLUSTER, b1 / LJ_CLUSTER, fx, fy,
                                        fz, el);
         else
-            lj_row_culled<false, false>(S, xs, keep_s[warp], nwords, xi, i, b0 / LJ_CLUSTER, b1 / LJ_CLUSTER, fx, fy,
+            lj_row_culled<false, false, true>(S, xs, cbox, keep_s[warp], nwords, xi, i, b0 / LJ_CLUSTER, b1 / LJ_CLUSTER, fx, fy,
                                         fz, el);
         __syncwarp();
         if (act) {

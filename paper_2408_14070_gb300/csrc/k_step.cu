@@ -91,10 +91,10 @@ __global__ void __maxnreg__(56) k_ff(SysDev S, StateDev st) {
         const int b1 = whi + 2 < N - 1 ? whi + 2 : N - 1;
         float fx = 0.f, fy = 0.f, fz = 0.f, el = 0.f;
         if (sig1)
-            lj_row_culled<true, ENERGY>(S, xs, keep_s[warp], nwords, xi, i, b0 / LJ_CLUSTER, b1 / LJ_CLUSTER, fx, fy,
+            lj_row_culled<true, ENERGY>(S, xs, cbox, keep_s[warp], nwords, xi, i, b0 / LJ_CLUSTER, b1 / LJ_CLUSTER, fx, fy,
                                         fz, el);
         else
-            lj_row_culled<false, ENERGY>(S, xs, keep_s[warp], nwords, xi, i, b0 / LJ_CLUSTER, b1 / LJ_CLUSTER, fx,
+            lj_row_culled<false, ENERGY>(S, xs, cbox, keep_s[warp], nwords, xi, i, b0 / LJ_CLUSTER, b1 / LJ_CLUSTER, fx,
                                          fy, fz, el);
         __syncwarp();                                         // keep_s is rewritten by the next iteration
         if (act) {

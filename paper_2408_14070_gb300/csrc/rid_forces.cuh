@@ -222,15 +222,27 @@ __device__ __forceinline__ void lj_cluster(const SysDev& S, const float4* xj, fl
 
 // Walk the kept clusters of one warp in increasing order; clusters that meet
 // the band [b0, b1] around the warp's beads test the |i - j| > 2 exclusion.
-template <bool SIG1, bool ENERGY>
-__device__ __forceinline__ void lj_row_culled(const SysDev& S, const float4* xs, const unsigned* keep, int nwords,
-                                              float3 xi, int i, int cb0, int cb1, float& fx, float& fy, float& fz,
-                                              float& el) {
+// LANE: before a cluster's pairs, each lane tests its own bead against the
+// cluster box (the same gap and fused r^2 as the warp mask); a cluster that no
+// lane's bead can reach is skipped whole -- exact for the same reason as the
+// mask, so kernels with and without the test give the same bits.  It pays in
+// the chain-resident label kernels (batching +6%), not in k_ff.
+template <bool SIG1, bool ENERGY, bool LANE = false>
+__device__ __forceinline__ void lj_row_culled(const SysDev& S, const float4* xs, const float4* cbox,
+                                              const unsigned* keep, int nwords, float3 xi, int i, int cb0, int cb1,
+                                              float& fx, float& fy, float& fz, float& el) {
     for (int q = 0; q < nwords; ++q) {
         unsigned m = keep[q];
         while (m) {
             const int c = 32 * q + __ffs(m) - 1;
             m &= m - 1;
+            if (LANE) {
+                const float4 lo = cbox[2 * c], hi = cbox[2 * c + 1];
+                const float gx = fmaxf(0.0f, fmaxf(lo.x - xi.x, xi.x - hi.x));
+                const float gy = fmaxf(0.0f, fmaxf(lo.y - xi.y, xi.y - hi.y));
+                const float gz = fmaxf(0.0f, fmaxf(lo.z - xi.z, xi.z - hi.z));
+                if (!__any_sync(0xffffffffu, !(pair_r2(make_float3(gx, gy, gz)) >= S.rc2))) continue;
+            }
             const int j0 = LJ_CLUSTER * c;
             if (c >= cb0 && c <= cb1) lj_cluster<true, SIG1, ENERGY>(S, xs + j0, xi, i, j0, fx, fy, fz, el);
             else lj_cluster<false, SIG1, ENERGY>(S, xs + j0, xi, i, j0, fx, fy, fz, el);
