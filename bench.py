@@ -297,8 +297,9 @@ def train_flops_per_sample(D, L, H):
 def run_training(rid, torch, steps, seed=11):
     """Ensemble training on mean-force labels (rid_trainer_run) for the
     exploration model of the 200-bead workload: 4 members 40-256x4-1, batch
-    128 per member, labels = the CV gradient of a teacher network at points on
-    the CV torus."""
+    128 per member, the training section's learning-rate schedule and dropout
+    rate 0.1, labels = the CV gradient of a teacher network at points on the CV
+    torus."""
     wl = I.workload(WORKLOAD)
     M, C, L, H, B = wl["n_models"], wl["n_cv"], wl["n_layers"], wl["width"], 128
     D = 2 * C
@@ -316,7 +317,7 @@ def run_training(rid, torch, steps, seed=11):
     idx = torch.from_numpy(rng.integers(0, n, size=(warm + steps, M, B)).astype(np.int32)).cuda()
     loss = torch.zeros((warm + steps, M), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    with rid.Trainer(M, C, L, H, student.weights, batch_size=B) as tr:
+    with rid.Trainer(M, C, L, H, student.weights, batch_size=B, dropout_rate=0.1, dropout_seed=seed) as tr:
         tr.set_data(s, mf, stream=stream)
         tr.run(idx[:warm], loss[:warm], stream=stream)
         torch.cuda.synchronize()
@@ -329,9 +330,10 @@ def run_training(rid, torch, steps, seed=11):
     lo = loss.cpu().numpy()
     fl = train_flops_per_sample(D, L, H) * M * B
     achieved = fl * steps / (ms * 1e-3) / 1e12
-    return {"workload": f"{M} members {D}-{H}x{L}-1, batch {B} per member, {n} labels (teacher CV gradients)",
+    return {"workload": f"{M} members {D}-{H}x{L}-1, batch {B} per member, dropout 0.1, {n} labels "
+                        "(teacher CV gradients)",
             "value": M * B * steps / (ms * 1e-3), "unit": "member-samples/s", "steps": steps,
-            "ms_per_step": ms / steps, "kernel_launches_per_step": 5 * L + 3,
+            "ms_per_step": ms / steps, "kernel_launches_per_step": 5 * L + 4,
             "loss_first": float(lo[:warm].mean()), "loss_last": float(lo[-20:].mean()),
             "algorithmic_gflop_per_step": fl / 1e9,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak(torch)[0], "unit": "TFLOP/s",

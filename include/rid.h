@@ -211,6 +211,15 @@ RID_API int rid_label_constrained(rid_system* sys, int32_t n_runs, const float* 
  * orders (a run is reproducible bit for bit); b_out does not enter the loss
  * and is never changed.
  *
+ * Dropout (drop_out_rate of the training section; rate 0: off): inverted
+ * dropout on the output of every hidden layer, h_l = q_l tanh(z_l) + r_l
+ * h_{l-1}, in the forward pass and in the input gradient dA/ds of the loss
+ * alike.  Unit j of layer l for batch row b of member m at step t is kept
+ * (q = 1 / (1 - rate)) iff word j % 4 of Philox4x32-10 at counter
+ * (j / 4 + ceil(H / 4) (l + L m), b, t, 4), key = dropout_seed, is at least
+ * floor(rate 2^32), else dropped (q = 0).  rid_trainer_grad draws the masks
+ * of the step the trainer would take next.
+ *
  * All calls are synchronous on `stream`.  `mem` says where the array
  * arguments live (RID_MEM_HOST / RID_MEM_DEVICE).  Errors: RID_ERR_ARG (bad
  * sizes, a batch index outside [0, n_data): detected on the device, the step's
@@ -228,6 +237,8 @@ typedef struct {
     double decay_rate;            /* 0.96                                       */
     int32_t decay_steps;          /* 120                                        */
     double beta1, beta2, adam_eps;  /* Adam: 0.9, 0.999, 1e-8                   */
+    double dropout_rate;          /* [0, 1): 0.1 in the paper, 0 = off          */
+    uint64_t dropout_seed;        /* Philox key of the dropout masks            */
 } rid_train_desc;
 
 typedef struct rid_trainer rid_trainer;
@@ -315,13 +326,26 @@ RID_API int rid_mcmc(const rid_mcmc_desc* desc, const float* s0, float* s_out, u
  * the precision the ensemble was set with (RID_PREC_FP32 / BF16 / FP8; the
  * tensor-core kernels for BF16 and FP8).  C is the system's CV count; s0
  * [W][C].  The system's resident walker buffers are reused (walkers loaded
- * with rid_walkers_load must be loaded again).  No path projection.
+ * with rid_walkers_load must be loaded again).  `path` (NULL, or n_nodes = 0:
+ * off) adds the path projection of rid_mcmc_desc, with the same fields and
+ * limits, counted into hist_path / pmf_path [bins][bins] (either may be NULL);
+ * its arrays are host memory whatever `mem` says.
  * Errors: RID_ERR_ARG, RID_ERR_STATE (no ensemble), RID_ERR_OOM, RID_ERR_CUDA.
  */
+typedef struct {
+    int32_t n_nodes;              /* P, 0 or 2..1024                            */
+    int32_t n_cv;                 /* CVs of the path, 1..C                      */
+    const int32_t* cv;            /* [n_cv] host                                */
+    const float* nodes;           /* [P][n_cv] host, radians                    */
+    double lambda;                /* > 0                                        */
+    double z_lo, z_hi;            /* z range of hist_path                       */
+} rid_mcmc_path;
+
 RID_API int rid_mcmc_system(rid_system* sys, int32_t n_walkers, const float* s0, int64_t n_steps, int64_t n_burn,
                             double kT, double step_size, uint64_t seed, int32_t bins, int32_t proj_i, int32_t proj_j,
-                            float* s_out, uint64_t* hist1, uint64_t* hist2, double* pmf1, double* pmf2,
-                            int64_t* n_accepted, int32_t mem, void* stream);
+                            const rid_mcmc_path* path, float* s_out, uint64_t* hist1, uint64_t* hist2, double* pmf1,
+                            double* pmf2, uint64_t* hist_path, double* pmf_path, int64_t* n_accepted, int32_t mem,
+                            void* stream);
 
 /*
  * Selection (Sec. "Selection phase": cluster_threshold, numb_cluster_lower,

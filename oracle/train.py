@@ -37,12 +37,31 @@ reader would derive it:
                 hbar_{l-1} = W_l^T zbar_l + r_l hbar_l.
 b_out does not enter the loss (its gradient is exactly zero).
 
+Dropout (the training section's drop_out_rate; the paper gives the rate, not
+the form).  Reading: inverted dropout on the output of every hidden layer,
+during training only.  Unit j of hidden layer l for batch row b of member m at
+training step t is kept iff word j % 4 of the Philox4x32-10 block at counter
+(j // 4 + ceil(H / 4) (l + L m), b, t, 4), key = dropout seed, is at least
+floor(rate 2^32); a kept unit is scaled by q = 1 / (1 - rate), a dropped one
+by q = 0.  With q_l the scales of layer l the passes above become
+  h_l = q_l t_l + r_l h_{l-1},  d_l = g_l q_l (1 - t_l^2),
+  gbar_l = dbar_l q_l (1 - t_l^2) + r_l gbar_{l-1},  tbar_l = -2 q_l t_l g_l dbar_l,
+  zbar_l = (tbar_l + q_l hbar_l) (1 - t_l^2):
+every derivative of the activation q tanh(z) carries q, and the input
+gradient dA/ds of the loss is that of the thinned network of the step.
+
 Everything is float64 numpy; batches are plain loops over samples where that
 keeps the formulas readable.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
+
+import oracle
+
+DROPOUT_STREAM = 4
 
 
 def param_count(D: int, L: int, H: int) -> int:
@@ -75,46 +94,67 @@ def features(s):
     return u
 
 
-def member_value_and_grad(w, D, L, H, resnet, s):
-    """A(s) and dA/ds for one member at one point (passes 1 and 2)."""
+def dropout_threshold(rate: float) -> int:
+    """A unit is kept iff its 32-bit Philox word is >= this integer."""
+    return int(math.floor(rate * 2.0 ** 32))
+
+
+def dropout_scales(M, B, L, H, step, seed, rate):
+    """q [M][B][L][H] of training step `step`: 1 / (1 - rate) for a kept unit,
+    0 for a dropped one (counters as in the module docstring)."""
+    nw = (H + 3) // 4
+    m, b, l, k = np.meshgrid(np.arange(M), np.arange(B), np.arange(L), np.arange(nw), indexing="ij")
+    ctr = np.stack([k + nw * (l + L * m), b, np.full_like(b, step), np.full_like(b, DROPOUT_STREAM)], axis=-1)
+    words = oracle.philox(ctr.reshape(-1, 4), seed).reshape(M, B, L, 4 * nw)[..., :H]
+    keep = words.astype(np.int64) >= dropout_threshold(rate)
+    return np.where(keep, 1.0 / (1.0 - rate), 0.0)
+
+
+def member_value_and_grad(w, D, L, H, resnet, s, q=None):
+    """A(s) and dA/ds for one member at one point (passes 1 and 2); q [L][H]
+    are the dropout scales of the point (None: no dropout)."""
     layers, w_out, b_out = unpack(np.asarray(w, dtype=np.float64), D, L, H)
+    q = np.ones((L, H)) if q is None else np.asarray(q, dtype=np.float64)
     u = features(s)
     h, ts = u, []
     for l, (W, b) in enumerate(layers):
         t = np.tanh(W @ h + b)
         ts.append(t)
-        h = t + (h if (resnet and l >= 1) else 0.0)
+        h = q[l] * t + (h if (resnet and l >= 1) else 0.0)
     A = float(w_out @ h + b_out[0])
     g = w_out.copy()
     for l in range(L - 1, -1, -1):
         W = layers[l][0]
-        g = W.T @ (g * (1.0 - ts[l] ** 2)) + (g if (resnet and l >= 1) else 0.0)
+        g = W.T @ (g * q[l] * (1.0 - ts[l] ** 2)) + (g if (resnet and l >= 1) else 0.0)
     s = np.asarray(s, dtype=np.float64)
     dAds = -np.sin(s) * g[0::2] + np.cos(s) * g[1::2]
     return A, dAds
 
 
-def loss(w, D, L, H, resnet, s_batch, mf_batch):
-    """L = mean over the batch and the C components of (dA/ds - MF)^2."""
+def loss(w, D, L, H, resnet, s_batch, mf_batch, q=None):
+    """L = mean over the batch and the C components of (dA/ds - MF)^2; q
+    [B][L][H] dropout scales (None: no dropout)."""
     s_batch = np.asarray(s_batch, dtype=np.float64)
     tot = 0.0
-    for s, mf in zip(s_batch, np.asarray(mf_batch, dtype=np.float64)):
-        _, g = member_value_and_grad(w, D, L, H, resnet, s)
+    for k, (s, mf) in enumerate(zip(s_batch, np.asarray(mf_batch, dtype=np.float64))):
+        _, g = member_value_and_grad(w, D, L, H, resnet, s, None if q is None else q[k])
         tot += float(np.sum((g - mf) ** 2))
     return tot / s_batch.size
 
 
-def loss_and_grad(w, D, L, H, resnet, s_batch, mf_batch):
-    """Loss of one member on a batch and dL/dtheta in the packed layout."""
+def loss_and_grad(w, D, L, H, resnet, s_batch, mf_batch, q=None):
+    """Loss of one member on a batch and dL/dtheta in the packed layout; q
+    [B][L][H] dropout scales of the batch rows (None: no dropout)."""
     w = np.asarray(w, dtype=np.float64)
     s_batch = np.asarray(s_batch, dtype=np.float64)
     mf_batch = np.asarray(mf_batch, dtype=np.float64)
     B, C = s_batch.shape
+    q = np.ones((B, L, H)) if q is None else np.asarray(q, dtype=np.float64)
     layers, w_out, _ = unpack(w, D, L, H)
     grad = np.zeros_like(w)
     glayers, gw_out, _ = unpack(grad, D, L, H)   # views into grad
     tot = 0.0
-    for s, mf in zip(s_batch, mf_batch):
+    for s, mf, qs in zip(s_batch, mf_batch, q):
         r_ = [bool(resnet and l >= 1) for l in range(L)]
         # 1. forward
         hs = [features(s)]                       # hs[l + 1] = h_l, hs[0] = u
@@ -122,13 +162,13 @@ def loss_and_grad(w, D, L, H, resnet, s_batch, mf_batch):
         for l, (W, b) in enumerate(layers):
             t = np.tanh(W @ hs[l] + b)
             ts.append(t)
-            hs.append(t + (hs[l] if r_[l] else 0.0))
+            hs.append(qs[l] * t + (hs[l] if r_[l] else 0.0))
         # 2. input gradient
         gs = [None] * (L + 1)                    # gs[l + 1] = g_l, gs[0] = dA/du
-        ds = [None] * L                          # d_l = g_l * (1 - t_l^2)
+        ds = [None] * L                          # d_l = g_l * q_l * (1 - t_l^2)
         gs[L] = w_out.copy()
         for l in range(L - 1, -1, -1):
-            ds[l] = gs[l + 1] * (1.0 - ts[l] ** 2)
+            ds[l] = gs[l + 1] * qs[l] * (1.0 - ts[l] ** 2)
             gs[l] = layers[l][0].T @ ds[l] + (gs[l + 1] if r_[l] else 0.0)
         # 3. loss and its adjoint with respect to dA/du
         dAds = -np.sin(s) * gs[0][0::2] + np.cos(s) * gs[0][1::2]
@@ -144,14 +184,14 @@ def loss_and_grad(w, D, L, H, resnet, s_batch, mf_batch):
             W = layers[l][0]
             dbar = W @ gbar
             glayers[l][0][...] += np.outer(ds[l], gbar)
-            tbar[l] = -2.0 * ts[l] * gs[l + 1] * dbar
-            gbar = dbar * (1.0 - ts[l] ** 2) + (gbar if r_[l] else 0.0)
+            tbar[l] = -2.0 * qs[l] * ts[l] * gs[l + 1] * dbar
+            gbar = dbar * qs[l] * (1.0 - ts[l] ** 2) + (gbar if r_[l] else 0.0)
         gw_out[...] += gbar
         # 5. back through the forward pass, decreasing l
         hbar = np.zeros(H)
         for l in range(L - 1, -1, -1):
             W = layers[l][0]
-            zbar = (tbar[l] + hbar) * (1.0 - ts[l] ** 2)
+            zbar = (tbar[l] + qs[l] * hbar) * (1.0 - ts[l] ** 2)
             glayers[l][0][...] += np.outer(zbar, hs[l])
             glayers[l][1][...] += zbar
             hbar = W.T @ zbar + (hbar if r_[l] else 0.0)
@@ -174,7 +214,7 @@ def adam_update(w, g, m, v, step: int, lr: float, beta1: float, beta2: float, ep
 
 
 def train(weights, D, L, H, resnet, s_data, mf_data, idx, init_lr=8e-4, decay_rate=0.96, decay_steps=120,
-          beta1=0.9, beta2=0.999, eps=1e-8, step0=0, m=None, v=None):
+          beta1=0.9, beta2=0.999, eps=1e-8, step0=0, m=None, v=None, dropout_rate=0.0, dropout_seed=0):
     """Run len(idx) steps; idx [n_steps][M][B] holds each member's batch of
     sample indices.  Returns (weights [M][P], losses [n_steps][M], m, v)."""
     w = np.array(weights, dtype=np.float64)
@@ -188,8 +228,12 @@ def train(weights, D, L, H, resnet, s_data, mf_data, idx, init_lr=8e-4, decay_ra
     for k in range(idx.shape[0]):
         t = step0 + k
         lr = learning_rate(t, init_lr, decay_rate, decay_steps)
+        q = None
+        if dropout_rate > 0:
+            q = dropout_scales(Mn, idx.shape[2], L, H, t, dropout_seed, dropout_rate)
         for i in range(Mn):
             b = idx[k, i]
-            losses[k, i], g = loss_and_grad(w[i], D, L, H, resnet, s_data[b], mf_data[b])
+            losses[k, i], g = loss_and_grad(w[i], D, L, H, resnet, s_data[b], mf_data[b],
+                                            None if q is None else q[i])
             w[i], m[i], v[i] = adam_update(w[i], g, m[i], v[i], t, lr, beta1, beta2, eps)
     return w, losses, m, v

@@ -215,6 +215,16 @@ struct McBufs {
 
 }  // namespace
 
+int rid_mc_path_check(int NP, int Cp, int C, const int32_t* cv, const float* nodes, double lambda, double z_lo,
+                      double z_hi) {
+    if (NP == 0) return RID_OK;
+    if (NP < 2 || NP > 1024 || Cp < 1 || Cp > C || !cv || !nodes || !(lambda > 0) || !(z_hi > z_lo))
+        return rid_fail(RID_ERR_ARG, "mcmc: path projection parameters out of range");
+    for (int c = 0; c < Cp; ++c)
+        if (cv[c] < 0 || cv[c] >= C) return rid_fail(RID_ERR_ARG, "mcmc: path CV index out of range");
+    return RID_OK;
+}
+
 extern "C" RID_API int rid_mcmc(const rid_mcmc_desc* d, const float* s0, float* s_out, uint64_t* hist1_out,
                                 uint64_t* hist2_out, double* pmf1_out, double* pmf2_out, uint64_t* histp_out,
                                 double* pmfp_out, int64_t* n_accepted, int32_t mem, void* stream) {
@@ -228,13 +238,8 @@ extern "C" RID_API int rid_mcmc(const rid_mcmc_desc* d, const float* s0, float* 
         bins < 1 || bins > 4096 || d->proj_i < 0 || d->proj_i >= C || d->proj_j < 0 || d->proj_j >= C)
         return rid_fail(RID_ERR_ARG, "mcmc: run parameters out of range");
     const int NP = d->path_n_nodes, Cp = d->path_n_cv;
-    if (NP != 0) {
-        if (NP < 2 || NP > 1024 || Cp < 1 || Cp > C || !d->path_cv || !d->path_nodes || !(d->path_lambda > 0) ||
-            !(d->path_z_hi > d->path_z_lo))
-            return rid_fail(RID_ERR_ARG, "mcmc: path projection parameters out of range");
-        for (int c = 0; c < Cp; ++c)
-            if (d->path_cv[c] < 0 || d->path_cv[c] >= C) return rid_fail(RID_ERR_ARG, "mcmc: path CV index out of range");
-    }
+    if (int r = rid_mc_path_check(NP, Cp, C, d->path_cv, d->path_nodes, d->path_lambda, d->path_z_lo, d->path_z_hi))
+        return r;
     cudaStream_t st = (cudaStream_t)stream;
     const int D = 2 * C;
     long long woff[RID_MAX_LAYERS], boff[RID_MAX_LAYERS], o = 0;
@@ -396,8 +401,16 @@ void rid_launch_mc_propose(const float* s, float* sp, float* U, int W, int C, ui
 void rid_launch_mc_accept_values(const float* aval, int na, int M, int W, int C, float* s, const float* sp, float* A,
                                  uint32_t step, float kT, uint32_t k0, uint32_t k1, int init, int count, int bins,
                                  int pi, int pj, unsigned long long* hist1, unsigned long long* hist2,
-                                 unsigned long long* nacc, cudaStream_t st) {
+                                 unsigned long long* nacc, const McPathDev& path, cudaStream_t st) {
     AcceptArgs a{};
+    a.npath = path.n_nodes;
+    a.Cp = path.n_cv;
+    a.pcv = path.cv;
+    a.pnodes = path.nodes;
+    a.lam = path.lambda;
+    a.z_lo = path.z_lo;
+    a.z_hi = path.z_hi;
+    a.histp = path.hist;
     a.aval = aval;
     a.na = na;
     a.M = M;

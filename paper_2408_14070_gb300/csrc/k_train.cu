@@ -22,6 +22,11 @@
 //   weights:   dW_l = d_l^T gbar_{l-1} + zbar_l^T h_{l-1} (one GEMM over 2B rows),
 //              db_l = sum_b zbar_l, dw_out = sum_b gbar_{L-1}, db_out = 0
 //   Adam (Kingma & Ba) on every parameter.
+// Dropout (drop_out_rate) scales each hidden unit's tanh by q in {0, 1/(1-p)}:
+// h_l = q t_l + r_l h_{l-1}, and every (1 - t^2) above that belongs to a
+// layer's activation derivative becomes q (1 - t^2), tbar_l gains the factor
+// q, and zbar_{l-1} = (tbar + q hbar)(1 - t^2).  The masks come from Philox
+// (k_tr_mask), one counter per four units.
 // Every sum is taken in a fixed order, so a run is reproducible bit for bit.
 #include <cmath>
 #include <vector>
@@ -104,6 +109,27 @@ __global__ void k_tr_colsum(ColSums cs, int B, int H, long long act_sm, float* _
     grad[(long long)m * P + cs.dst_off[v] + j] = a;
 }
 
+// Dropout scales of one step: Q[l][m][b][j] = 1/(1-p) iff word j % 4 of
+// Philox(j / 4 + nw (l + L m), b, step, 4) >= thr, else 0 (nw = ceil(H / 4)).
+__global__ void k_tr_mask(float* __restrict__ Q, int M, int B, int L, int H, uint32_t step, uint32_t thr,
+                          float scale, uint32_t k0, uint32_t k1) {
+    const int nw = (H + 3) / 4;
+    const long long tot = (long long)L * M * B * nw;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e % nw);
+        const long long r = e / nw;                       // (l, m, b)
+        const int b = (int)(r % B);
+        const long long lm = r / B;                       // l M + m
+        const int m = (int)(lm % M), l = (int)(lm / M);
+        const uint4 x = rid_philox(make_uint4((uint32_t)(k + nw * (l + L * m)), (uint32_t)b, step, 4u), k0, k1);
+        const uint32_t wd[4] = {x.x, x.y, x.z, x.w};
+        float* q = Q + r * H + 4 * k;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (4 * k + c < H) q[c] = wd[c] >= thr ? scale : 0.0f;
+    }
+}
+
 __global__ void k_tr_adam(float* __restrict__ w, float* __restrict__ am, float* __restrict__ av,
                           const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps, float c1,
                           float c2) {
@@ -140,6 +166,9 @@ struct rid_trainer {
     int* dbad = nullptr;
     // carve of act, all [M][B][X]
     float *U, *SB, *MFB, *G0, *GB0;
+    float* Q[RID_MAX_LAYERS] = {};   // dropout scales [M][B][H] per layer (NULL: no dropout)
+    uint32_t dthr = 0;               // keep iff the Philox word >= dthr
+    float dscale = 1.0f;             // 1 / (1 - rate)
     float *T[RID_MAX_LAYERS], *Hh[RID_MAX_LAYERS], *G[RID_MAX_LAYERS], *Dl[RID_MAX_LAYERS], *GB[RID_MAX_LAYERS],
         *TB[RID_MAX_LAYERS], *ZB[RID_MAX_LAYERS], *HB[RID_MAX_LAYERS];
 };
@@ -169,12 +198,19 @@ int grow(void** p, long long* cap, long long need, size_t elem) {
 }
 
 // One step's gradient into tr->grad and the per-member loss into loss[M],
-// for the batch indices idx [M][B] (device).
-int tr_gradient(rid_trainer* tr, const int* idx, float* loss, cudaStream_t st) {
+// for the batch indices idx [M][B] (device) at training step `step` (the
+// step index of the dropout masks).
+int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, cudaStream_t st) {
     const rid_train_desc& d = tr->d;
     const int M = d.n_models, B = d.batch_size, C = d.n_cv, D = tr->D, L = d.n_layers, H = d.width;
     const long long P = tr->P;
     const long long smH = (long long)B * H, smD = (long long)B * D;
+    if (tr->Q[0]) {
+        const long long tot = (long long)L * M * B * ((H + 3) / 4);
+        const int blocks = (int)((tot + 255) / 256 < 2048 ? (tot + 255) / 256 : 2048);
+        k_tr_mask<<<blocks, 256, 0, st>>>(tr->Q[0], M, B, L, H, (uint32_t)step, tr->dthr, tr->dscale,
+                                          (uint32_t)d.dropout_seed, (uint32_t)(d.dropout_seed >> 32));
+    }
     {
         const long long tot = (long long)M * B * C;
         const int blocks = (int)((tot + 255) / 256 < 1024 ? (tot + 255) / 256 : 1024);
@@ -205,6 +241,7 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, cudaStream_t st) {
         e.w_sm = P;
         e.Gout = tr->G[L - 1];
         e.Dout = tr->Dl[L - 1];
+        e.Q = tr->Q[l];
         launch_gemm<EPI_FWD>(g, M, st);
     }
     // input gradient, decreasing l: g_{l-1} = d_l W_l (+ r g_l)
@@ -225,6 +262,7 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, cudaStream_t st) {
         e.res = tr->G[l];
         e.Tl = l == 0 ? nullptr : tr->T[l - 1];
         e.Dout = l == 0 ? nullptr : tr->Dl[l - 1];
+        e.Q = l == 0 ? nullptr : tr->Q[l - 1];
         launch_gemm<EPI_BWD>(g, M, st);
     }
     k_tr_loss<<<M, LT, 0, st>>>(tr->G0, tr->SB, tr->MFB, B, C, tr->GB0, loss);
@@ -249,6 +287,7 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, cudaStream_t st) {
         e.out2 = tr->TB[l];
         e.last = l == L - 1;
         e.out3 = tr->ZB[L - 1];
+        e.Q = tr->Q[l];
         launch_gemm<EPI_ADJ>(g, M, st);
     }
     // back through the forward pass, decreasing l (hbar_{L-1} = 0)
@@ -269,6 +308,7 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, cudaStream_t st) {
         e.Tl = tr->T[l - 1];
         e.tb = tr->TB[l - 1];
         e.out3 = tr->ZB[l - 1];
+        e.Q = tr->Q[l - 1];
         launch_gemm<EPI_BACK>(g, M, st);
     }
     // weight gradients: dW_l[a][b] = sum_k d_l[k][a] gbar_{l-1}[k][b] + zbar_l[k][a] h_{l-1}[k][b]
@@ -313,6 +353,7 @@ int tr_check_desc(const rid_train_desc* d) {
         return rid_fail(RID_ERR_ARG, "trainer: learning-rate schedule out of range");
     if (!(d->beta1 >= 0 && d->beta1 < 1) || !(d->beta2 >= 0 && d->beta2 < 1) || !(d->adam_eps > 0))
         return rid_fail(RID_ERR_ARG, "trainer: Adam parameters out of range");
+    if (!(d->dropout_rate >= 0 && d->dropout_rate < 1)) return rid_fail(RID_ERR_ARG, "trainer: dropout_rate outside [0, 1)");
     return RID_OK;
 }
 
@@ -365,8 +406,10 @@ RID_API int rid_trainer_create(const rid_train_desc* desc, const float* weights,
     tr->P = (int)o;
     const long long nP = (long long)M * tr->P;
     const long long smH = (long long)B * H, smD = (long long)B * D, smC = (long long)B * C;
-    // activations: U, G0, GB0 [M][B][D]; SB, MFB [M][B][C]; per layer T, Hh (resnet), G, Dl, GB, TB, ZB, HB
-    const long long per_layer = (desc->resnet ? 8 : 7) * smH;
+    // activations: U, G0, GB0 [M][B][D]; SB, MFB [M][B][C]; per layer T, Hh (resnet or dropout), G, Dl, GB,
+    // TB, ZB, HB, and Q (dropout)
+    const bool drop = desc->dropout_rate > 0;
+    const long long per_layer = ((desc->resnet || drop ? 8 : 7) + (drop ? 1 : 0)) * smH;
     const long long nact = (long long)M * (3 * smD + 2 * smC + L * per_layer);
     bool ok = cudaMalloc(&tr->w, sizeof(float) * 4 * nP) == cudaSuccess;
     ok = ok && cudaMalloc(&tr->act, sizeof(float) * nact) == cudaSuccess;
@@ -388,13 +431,18 @@ RID_API int rid_trainer_create(const rid_train_desc* desc, const float* weights,
     tr->MFB = take(smC);
     for (int l = 0; l < L; ++l) {
         tr->T[l] = take(smH);
-        tr->Hh[l] = desc->resnet ? take(smH) : tr->T[l];
+        tr->Hh[l] = desc->resnet || drop ? take(smH) : tr->T[l];
         tr->G[l] = take(smH);
         tr->Dl[l] = take(smH);
         tr->GB[l] = take(smH);
         tr->TB[l] = take(smH);
         tr->ZB[l] = take(smH);
         tr->HB[l] = take(smH);
+    }
+    if (drop) {   // the scales of all layers are contiguous: k_tr_mask writes them in one launch
+        for (int l = 0; l < L; ++l) tr->Q[l] = take(smH);
+        tr->dthr = (uint32_t)std::floor(desc->dropout_rate * 4294967296.0);
+        tr->dscale = (float)(1.0 / (1.0 - desc->dropout_rate));
     }
     if (cudaMemcpy(tr->w, weights, sizeof(float) * nP, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(tr->am, 0, sizeof(float) * 3 * nP) != cudaSuccess || cudaMemset(tr->act, 0, sizeof(float) * nact) != cudaSuccess ||
@@ -452,7 +500,7 @@ RID_API int rid_trainer_grad(rid_trainer* tr, const int32_t* idx, float* loss_ou
     if (int rc = grow((void**)&tr->didx, &tr->cap_idx, (long long)M * B, sizeof(int))) return rc;
     if (int rc = grow((void**)&tr->dloss, &tr->cap_loss, M, sizeof(float))) return rc;
     if (int rc = tr_copy_in(tr->didx, idx, sizeof(int) * (size_t)M * B, mem, st)) return rc;
-    if (int rc = tr_gradient(tr, tr->didx, tr->dloss, st)) return rc;
+    if (int rc = tr_gradient(tr, tr->didx, tr->dloss, tr->steps, st)) return rc;
     TCK(cudaGetLastError());
     if (loss_out)
         if (int rc = tr_copy_out(loss_out, tr->dloss, sizeof(float) * M, mem, st)) return rc;
@@ -477,8 +525,8 @@ RID_API int rid_trainer_run(rid_trainer* tr, int32_t n_steps, const int32_t* idx
     const long long nP = (long long)M * tr->P;
     const int ablocks = (int)((nP + 255) / 256 < 2048 ? (nP + 255) / 256 : 2048);
     for (int k = 0; k < n_steps; ++k) {
-        if (int rc = tr_gradient(tr, tr->didx + per * k, tr->dloss + (long long)M * k, st)) return rc;
         const int64_t t = tr->steps + k;
+        if (int rc = tr_gradient(tr, tr->didx + per * k, tr->dloss + (long long)M * k, t, st)) return rc;
         const double lr = d.init_lr * std::pow(d.decay_rate, (double)t / (double)d.decay_steps);
         const double c1 = 1.0 - std::pow(d.beta1, (double)(t + 1)), c2 = 1.0 - std::pow(d.beta2, (double)(t + 1));
         k_tr_adam<<<ablocks, 256, 0, st>>>(tr->w, tr->am, tr->av, tr->grad, nP, (float)lr, (float)d.beta1,

@@ -1094,8 +1094,9 @@ extern "C" int rid_label(rid_system* sys, int32_t R, const float* x0, const floa
 // allocated for the call.
 extern "C" int rid_mcmc_system(rid_system* sys, int32_t W, const float* s0, int64_t n_steps, int64_t n_burn,
                                double kT, double step_size, uint64_t seed, int32_t bins, int32_t proj_i,
-                               int32_t proj_j, float* s_out, uint64_t* hist1_out, uint64_t* hist2_out,
-                               double* pmf1_out, double* pmf2_out, int64_t* n_accepted, int32_t mem, void* stream) {
+                               int32_t proj_j, const rid_mcmc_path* path, float* s_out, uint64_t* hist1_out,
+                               uint64_t* hist2_out, double* pmf1_out, double* pmf2_out, uint64_t* histp_out,
+                               double* pmfp_out, int64_t* n_accepted, int32_t mem, void* stream) {
     if (!sys || !s0) return fail(RID_ERR_ARG, "NULL argument");
     if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "mem must be RID_MEM_HOST or RID_MEM_DEVICE");
     if (!sys->has_ens) return fail(RID_ERR_STATE, "no ensemble set");
@@ -1104,6 +1105,8 @@ extern "C" int rid_mcmc_system(rid_system* sys, int32_t W, const float* s0, int6
         bins > 4096 || proj_i < 0 || proj_i >= C || proj_j < 0 || proj_j >= C)
         return fail(RID_ERR_ARG, "mcmc: parameters out of range");
     if ((long long)W * sys->S.N > (1ll << 31)) return fail(RID_ERR_ARG, "n_walkers * n_beads too large");
+    const int NP = path ? path->n_nodes : 0, Cp = path ? path->n_cv : 0;
+    if (path) TRY(rid_mc_path_check(NP, Cp, C, path->cv, path->nodes, path->lambda, path->z_lo, path->z_hi));
     TRY(check_device(sys));
     sys->loaded = false;   // the resident walker buffers are reused
     sys->pending = false;
@@ -1116,9 +1119,12 @@ extern "C" int rid_mcmc_system(rid_system* sys, int32_t W, const float* s0, int6
         DevBuf b;
         ~Scoped() { b.release(); }
     } scoped;
-    const size_t o_h1 = 0, o_h2 = o_h1 + 8 * n1, o_na = o_h2 + 8 * n2, o_p1 = o_na + 16, o_p2 = o_p1 + 8 * n1;
-    const size_t o_s = o_p2 + 8 * n2, o_sp = o_s + 4 * nS, o_A = o_sp + 4 * nS;
-    TRY(scoped.b.ensure(o_A + 4 * (size_t)W));
+    // counters first (zeroed together), then the PMFs, states and path nodes
+    const long long np2 = NP ? n2 : 0, npn = (long long)NP * Cp;
+    const size_t o_h1 = 0, o_h2 = o_h1 + 8 * n1, o_hp = o_h2 + 8 * n2, o_na = o_hp + 8 * np2, o_p1 = o_na + 16;
+    const size_t o_p2 = o_p1 + 8 * n1, o_pp = o_p2 + 8 * n2, o_s = o_pp + 8 * np2, o_sp = o_s + 4 * nS;
+    const size_t o_A = o_sp + 4 * nS, o_pn = o_A + ((4 * (size_t)W + 15) & ~(size_t)15), o_pc = o_pn + 4 * npn;
+    TRY(scoped.b.ensure(o_pc + 4 * (size_t)Cp));
     unsigned char* b = static_cast<unsigned char*>(scoped.b.p);
     auto* h1 = reinterpret_cast<unsigned long long*>(b + o_h1);
     auto* h2 = reinterpret_cast<unsigned long long*>(b + o_h2);
@@ -1128,6 +1134,20 @@ extern "C" int rid_mcmc_system(rid_system* sys, int32_t W, const float* s0, int6
     float* ds = reinterpret_cast<float*>(b + o_s);
     float* dsp = reinterpret_cast<float*>(b + o_sp);
     float* dA = reinterpret_cast<float*>(b + o_A);
+    double* pp = reinterpret_cast<double*>(b + o_pp);
+    McPathDev pd;
+    if (NP) {
+        pd.n_nodes = NP;
+        pd.n_cv = Cp;
+        pd.nodes = reinterpret_cast<float*>(b + o_pn);
+        pd.cv = reinterpret_cast<int*>(b + o_pc);
+        pd.lambda = (float)path->lambda;
+        pd.z_lo = (float)path->z_lo;
+        pd.z_hi = (float)path->z_hi;
+        pd.hist = reinterpret_cast<unsigned long long*>(b + o_hp);
+        CK(cudaMemcpyAsync(b + o_pn, path->nodes, 4 * npn, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(b + o_pc, path->cv, 4 * (size_t)Cp, cudaMemcpyHostToDevice, st));
+    }
     const cudaMemcpyKind kin = mem == RID_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     const cudaMemcpyKind kout = mem == RID_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     CK(cudaMemcpyAsync(ds, s0, sizeof(float) * nS, kin, st));
@@ -1137,26 +1157,29 @@ extern "C" int rid_mcmc_system(rid_system* sys, int32_t W, const float* s0, int6
     rid_launch_mc_features(ds, sd.u, nS, st);
     TRY(launch_mlp(sys, W, 1, sd, st));
     rid_launch_mc_accept_values(sd.Aval, nav, M, W, C, ds, dsp, dA, 0u, (float)kT, k0, k1, 1, 0, bins, proj_i, proj_j,
-                                h1, h2, na, st);
+                                h1, h2, na, pd, st);
     for (int64_t t = 0; t < n_steps; ++t) {
         rid_launch_mc_propose(ds, dsp, sd.u, W, C, (uint32_t)t, (float)step_size, k0, k1, st);
         TRY(launch_mlp(sys, W, 1, sd, st));
         rid_launch_mc_accept_values(sd.Aval, nav, M, W, C, ds, dsp, dA, (uint32_t)t, (float)kT, k0, k1, 0,
-                                    t >= n_burn, bins, proj_i, proj_j, h1, h2, na, st);
+                                    t >= n_burn, bins, proj_i, proj_j, h1, h2, na, pd, st);
     }
     rid_launch_mc_pmf(h1, C, bins, kT, p1, st);
     rid_launch_mc_pmf(h2, 1, (int)n2, kT, p2, st);
+    if (NP) rid_launch_mc_pmf(pd.hist, 1, (int)n2, kT, pp, st);
     CK(cudaGetLastError());
     if (s_out) CK(cudaMemcpyAsync(s_out, ds, sizeof(float) * nS, kout, st));
     if (hist1_out) CK(cudaMemcpyAsync(hist1_out, h1, 8 * n1, kout, st));
     if (hist2_out) CK(cudaMemcpyAsync(hist2_out, h2, 8 * n2, kout, st));
     if (pmf1_out) CK(cudaMemcpyAsync(pmf1_out, p1, 8 * n1, kout, st));
     if (pmf2_out) CK(cudaMemcpyAsync(pmf2_out, p2, 8 * n2, kout, st));
+    if (NP && histp_out) CK(cudaMemcpyAsync(histp_out, pd.hist, 8 * n2, kout, st));
+    if (NP && pmfp_out) CK(cudaMemcpyAsync(pmfp_out, pp, 8 * n2, kout, st));
     unsigned long long hna = 0;
     CK(cudaMemcpyAsync(&hna, na, sizeof(hna), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (n_accepted) *n_accepted = (int64_t)hna;
-    sys->launches += 3 + 3 * n_steps + 2;
+    sys->launches += 3 + 3 * n_steps + 2 + (NP ? 1 : 0);
     return RID_OK;
 }
 

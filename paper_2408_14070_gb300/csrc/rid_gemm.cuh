@@ -13,12 +13,19 @@ namespace {
 // Square output tiles of TS = 32 (128 threads, 2 x 4 outputs each: the
 // training GEMMs have 128-row batches, and small tiles are what fills the SMs)
 // or TS = 64 (256 threads, 4 x 4 outputs: MCMC's thousands of walkers); K tiles
-// of 32, the next one staged in registers.  Every output sums its K terms in
-// increasing order whatever the tile, so both sizes give the same bits.
+// of 32.  The operand tiles stream through a ring of NS shared-memory stages
+// filled by element-wise cp.async (any strides, zero fill past the edges), so
+// NS - 1 tiles are in flight while one is multiplied: at these sizes each
+// GEMM is bound by the load latency of its K loop, not by its FMAs.  Every
+// output sums its K terms in increasing order whatever the tile or ring, so
+// all configurations give the same bits.
 constexpr int GK = 32;
 template <int TS> struct TileCfg {
     static constexpr int threads = TS == 32 ? 128 : 256;
     static constexpr int rp = TS * TS / threads / 4;   // rows per thread (4 columns each)
+    static constexpr int stages = TS == 32 ? 6 : 3;
+    static constexpr int ld = TS + 4;                  // row pitch of a stage's [GK][ld] tile
+    static constexpr size_t smem = sizeof(float) * 2 * stages * GK * ld;
 };
 
 // A operand: element (i, k) at p + z sm + i si + k sk.  B operand: element
@@ -48,6 +55,9 @@ struct EpiArgs {
     // backward / adjoint / back: residual input, T of the layer, second outputs
     const float* res; const float* Tl; const float* Gl; float* out2; const float* tb; float* out3;
     long long act_sm;  // member stride of the [rows][ld] activations
+    // dropout scales q of the layer whose tanh the epilogue forms or reads
+    // (forward, adjoint: layer l; backward, back: layer l - 1); NULL: q = 1
+    const float* Q;
     int resid;         // r_l
     int last;          // forward / adjoint on the last layer
 };
@@ -59,70 +69,78 @@ struct GemmArgs {
     EpiArgs e;
 };
 
-__device__ __forceinline__ float ldop(const Operand& o, int z, int r, int k) {
-    return o.p[(long long)z * o.sm + (long long)r * o.si + (long long)k * o.sk];
+// 4-byte asynchronous copy global -> shared; src_bytes = 0 writes a zero.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, int src_bytes) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <int EPI, int TS>
 __global__ void __launch_bounds__(TileCfg<TS>::threads) k_tr_gemm(GemmArgs g) {
-    constexpr int NT = TileCfg<TS>::threads, RP = TileCfg<TS>::rp;
-    __shared__ __align__(16) float As[GK][TS + 4];
-    __shared__ __align__(16) float Bs[GK][TS + 4];
+    constexpr int NT = TileCfg<TS>::threads, RP = TileCfg<TS>::rp, NS = TileCfg<TS>::stages;
+    constexpr int LD = TileCfg<TS>::ld;
+    extern __shared__ __align__(16) float gsm[];
+    float* As = gsm;                     // [NS][GK][LD]
+    float* Bs = gsm + NS * GK * LD;      // [NS][GK][LD]
     const int z = blockIdx.z, i0 = blockIdx.y * TS, j0 = blockIdx.x * TS;
     const int tid = threadIdx.x, tx = tid % (TS / 4), ty = tid / (TS / 4);   // rows RP ty .., columns 4 tx ..
     float acc[RP][4] = {};
-    // K tiles of both segments in one sequence; the next tile's elements are
-    // loaded into registers while the current one is multiplied
+    // K tiles of both segments in one sequence
     const int nt0 = (g.seg[0].K + GK - 1) / GK;
     const int nt = nt0 + (g.nseg > 1 ? (g.seg[1].K + GK - 1) / GK : 0);
     constexpr int PER = TS * GK / NT;
-    float ra[PER], rb[PER];
-    auto fetch = [&](int t) {
-        const int sidx = t < nt0 ? 0 : 1;
-        const Seg& S = g.seg[sidx];
-        const int k0 = (t - (sidx ? nt0 : 0)) * GK;
-        const bool a_kfast = S.a.sk == 1;   // A row-major along K: threads walk K
-        const bool b_jfast = S.b.si == 1;   // B (k, j) with j contiguous: threads walk j
+    // issue the copies of K tile t into ring stage t % NS (then one commit group)
+    auto issue = [&](int t) {
+        if (t < nt) {
+            const int sidx = t < nt0 ? 0 : 1;
+            const Seg& S = g.seg[sidx];
+            const int k0 = (t - (sidx ? nt0 : 0)) * GK;
+            const bool a_kfast = S.a.sk == 1;   // A row-major along K: threads walk K
+            const bool b_jfast = S.b.si == 1;   // B (k, j) with j contiguous: threads walk j
+            float* as = As + (t % NS) * GK * LD;
+            float* bs = Bs + (t % NS) * GK * LD;
+            const float* pa = S.a.p + (long long)z * S.a.sm;
+            const float* pb = S.b.p + (long long)z * S.b.sm;
 #pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int idx = tid + NT * r;
-            const int ii = a_kfast ? idx / GK : idx % TS, kk = a_kfast ? idx % GK : idx / TS;
-            const int gi = i0 + ii, gk = k0 + kk;
-            ra[r] = (gi < g.rows && gk < S.K) ? ldop(S.a, z, gi, gk) : 0.0f;
-            const int jj = b_jfast ? idx % TS : idx / GK, kb = b_jfast ? idx / TS : idx % GK;
-            const int gj = j0 + jj, gkb = k0 + kb;
-            rb[r] = (gj < g.cols && gkb < S.K) ? ldop(S.b, z, gj, gkb) : 0.0f;
+            for (int r = 0; r < PER; ++r) {
+                const int idx = tid + NT * r;
+                const int ii = a_kfast ? idx / GK : idx % TS, kk = a_kfast ? idx % GK : idx / TS;
+                const int gi = i0 + ii, gk = k0 + kk;
+                const bool ia = gi < g.rows && gk < S.K;
+                cp_async4(as + kk * LD + ii, ia ? pa + (long long)gi * S.a.si + (long long)gk * S.a.sk : pa, ia ? 4 : 0);
+                const int jj = b_jfast ? idx % TS : idx / GK, kb = b_jfast ? idx / TS : idx % GK;
+                const int gj = j0 + jj, gkb = k0 + kb;
+                const bool ib = gj < g.cols && gkb < S.K;
+                cp_async4(bs + kb * LD + jj, ib ? pb + (long long)gj * S.b.si + (long long)gkb * S.b.sk : pb, ib ? 4 : 0);
+            }
         }
+        cp_async_commit();                 // an empty group past the end keeps the count uniform
     };
-    auto stash = [&](int t) {
-        const Seg& S = g.seg[t < nt0 ? 0 : 1];
-        const bool a_kfast = S.a.sk == 1, b_jfast = S.b.si == 1;
 #pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int idx = tid + NT * r;
-            As[a_kfast ? idx % GK : idx / TS][a_kfast ? idx / GK : idx % TS] = ra[r];
-            Bs[b_jfast ? idx / TS : idx % GK][b_jfast ? idx % TS : idx / GK] = rb[r];
-        }
-    };
-    if (nt > 0) fetch(0);
+    for (int t = 0; t < NS - 1; ++t) issue(t);
     for (int t = 0; t < nt; ++t) {
-        stash(t);
-        __syncthreads();
-        if (t + 1 < nt) fetch(t + 1);
+        cp_async_wait<NS - 2>();           // this thread's copies of tile t have landed
+        __syncthreads();                   // everyone's have, and everyone is done with tile t - 1
+        issue(t + NS - 1);                 // refills the stage of tile t - 1
+        const float* as = As + (t % NS) * GK * LD;
+        const float* bs = Bs + (t % NS) * GK * LD;
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
             float av[RP];
 #pragma unroll
-            for (int p = 0; p < RP; ++p) av[p] = As[kk][ty * RP + p];
-            const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+            for (int p = 0; p < RP; ++p) av[p] = as[kk * LD + ty * RP + p];
+            const float4 b = *reinterpret_cast<const float4*>(&bs[kk * LD + tx * 4]);
             const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
             for (int p = 0; p < RP; ++p)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
         }
-        __syncthreads();
     }
+    cp_async_wait<0>();
     const EpiArgs& e = g.e;
 #pragma unroll
     for (int p = 0; p < RP; ++p) {
@@ -137,50 +155,63 @@ __global__ void __launch_bounds__(TileCfg<TS>::threads) k_tr_gemm(GemmArgs g) {
             if (EPI == EPI_STORE) {
                 e.out[(long long)z * e.out_sm + (long long)i * e.ld + j] = a;
             } else if (EPI == EPI_FWD) {
+                // t_l = tanh(z_l); h_l = q t_l + r h_{l-1}; last: g = w_out, d = g q (1 - t^2)
                 const float t = tanhf(a + e.bias[(long long)z * e.bias_sm + j]);
+                const float q = e.Q ? e.Q[o] : 1.0f;
                 e.T[o] = t;
-                if (e.Hout != e.T) e.Hout[o] = e.resid ? t + e.Hin[o] : t;
+                if (e.Hout != e.T) e.Hout[o] = e.resid ? fmaf(q, t, e.Hin[o]) : q * t;
                 if (e.last) {
                     const float w = e.wout[(long long)z * e.w_sm + j];
                     e.Gout[o] = w;
-                    e.Dout[o] = w * (1.0f - t * t);
+                    e.Dout[o] = w * (q * (1.0f - t * t));
                 }
             } else if (EPI == EPI_BWD) {
-                // g_{l-1} = d_l W_l + r_l g_l; d_{l-1} = g_{l-1} (1 - t_{l-1}^2)
+                // g_{l-1} = d_l W_l + r_l g_l; d_{l-1} = g_{l-1} q (1 - t_{l-1}^2)
                 const float gv = e.resid ? a + e.res[o] : a;
                 e.out[o] = gv;
                 if (e.Dout) {
                     const float t = e.Tl[o];
-                    e.Dout[o] = gv * (1.0f - t * t);
+                    const float q = e.Q ? e.Q[o] : 1.0f;
+                    e.Dout[o] = gv * (q * (1.0f - t * t));
                 }
             } else if (EPI == EPI_ADJ) {
-                // dbar = acc; gbar_l = dbar (1 - t^2) + r gbar_{l-1}; tbar = -2 t g dbar
+                // dbar = acc; gbar_l = dbar q (1 - t^2) + r gbar_{l-1}; tbar = -2 q t g dbar
                 const float t = e.Tl[o];
-                const float sp = 1.0f - t * t;
-                e.out[o] = e.resid ? a * sp + e.res[o] : a * sp;
-                const float tb = -2.0f * t * e.Gl[o] * a;
+                const float q = e.Q ? e.Q[o] : 1.0f;
+                const float sp = 1.0f - t * t, spq = q * sp;
+                e.out[o] = e.resid ? a * spq + e.res[o] : a * spq;
+                const float tb = -2.0f * (q * t) * e.Gl[o] * a;
                 e.out2[o] = tb;
                 if (e.last) e.out3[o] = tb * sp;      // zbar_{L-1} (hbar_{L-1} = 0)
             } else if (EPI == EPI_BACK) {
-                // hbar_{l-1} = zbar_l W_l + r hbar_l; zbar_{l-1} = (tbar + hbar)(1 - t^2)
+                // hbar_{l-1} = zbar_l W_l + r hbar_l; zbar_{l-1} = (tbar + q hbar)(1 - t^2)
                 const float hb = e.resid ? a + e.res[o] : a;
                 e.out[o] = hb;
                 const float t = e.Tl[o];
-                e.out3[o] = (e.tb[o] + hb) * (1.0f - t * t);
+                const float q = e.Q ? e.Q[o] : 1.0f;
+                e.out3[o] = fmaf(q, hb, e.tb[o]) * (1.0f - t * t);
             }
         }
     }
 }
 
+template <int EPI, int TS>
+void launch_gemm_ts(const GemmArgs& g, int M, cudaStream_t st) {
+    static bool attr = false;   // the ring exceeds the default 48 KB of shared memory
+    if (!attr) {
+        cudaFuncSetAttribute(k_tr_gemm<EPI, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TileCfg<TS>::smem);
+        attr = true;
+    }
+    dim3 grid((g.cols + TS - 1) / TS, (g.rows + TS - 1) / TS, M);
+    k_tr_gemm<EPI, TS><<<grid, TileCfg<TS>::threads, TileCfg<TS>::smem, st>>>(g);
+}
+
 template <int EPI>
 void launch_gemm(const GemmArgs& g, int M, cudaStream_t st) {
-    if (g.rows >= 1024 && g.cols >= 64) {
-        dim3 grid((g.cols + 63) / 64, (g.rows + 63) / 64, M);
-        k_tr_gemm<EPI, 64><<<grid, TileCfg<64>::threads, 0, st>>>(g);
-    } else {
-        dim3 grid((g.cols + 31) / 32, (g.rows + 31) / 32, M);
-        k_tr_gemm<EPI, 32><<<grid, TileCfg<32>::threads, 0, st>>>(g);
-    }
+    if (g.rows >= 1024 && g.cols >= 64)
+        launch_gemm_ts<EPI, 64>(g, M, st);
+    else
+        launch_gemm_ts<EPI, 32>(g, M, st);
 }
 
 // Operand helpers over [M][rows][ld] activations.

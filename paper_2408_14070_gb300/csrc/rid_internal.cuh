@@ -164,10 +164,21 @@ size_t rid_label_cons_smem(int N, int C);
 void rid_launch_mc_features(const float* s, float* U, long long n, cudaStream_t st);
 void rid_launch_mc_propose(const float* s, float* sp, float* U, int W, int C, uint32_t step, float step_size,
                            uint32_t k0, uint32_t k1, cudaStream_t st);
+// Device side of a path projection (n_nodes = 0: off).
+struct McPathDev {
+    int n_nodes = 0, n_cv = 0;
+    const int* cv = nullptr;               // [n_cv]
+    const float* nodes = nullptr;          // [n_nodes][n_cv]
+    float lambda = 0.0f, z_lo = 0.0f, z_hi = 0.0f;
+    unsigned long long* hist = nullptr;    // [bins][bins]
+};
+// Checks a path projection's host arguments against C CVs (RID_OK or RID_ERR_ARG).
+int rid_mc_path_check(int n_nodes, int n_cv, int C, const int32_t* cv, const float* nodes, double lambda,
+                      double z_lo, double z_hi);
 void rid_launch_mc_accept_values(const float* aval, int na, int M, int W, int C, float* s, const float* sp, float* A,
                                  uint32_t step, float kT, uint32_t k0, uint32_t k1, int init, int count, int bins,
                                  int pi, int pj, unsigned long long* hist1, unsigned long long* hist2,
-                                 unsigned long long* nacc, cudaStream_t st);
+                                 unsigned long long* nacc, const McPathDev& path, cudaStream_t st);
 void rid_launch_mc_pmf(const unsigned long long* hist, int rows, int n, double kT, double* pmf, cudaStream_t st);
 cudaError_t rid_launch_label_cons(const SysDev& S, int R, int C, int B, long long n_steps, long long n_equil,
                                   uint32_t step0, float kT, const float4* x0, const float4* v0, const int2* pairs,

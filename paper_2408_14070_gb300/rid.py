@@ -59,7 +59,8 @@ class TrainDesc(C.Structure):
     _fields_ = [("n_models", C.c_int32), ("n_cv", C.c_int32), ("n_layers", C.c_int32), ("width", C.c_int32),
                 ("resnet", C.c_int32), ("batch_size", C.c_int32), ("init_lr", C.c_double),
                 ("decay_rate", C.c_double), ("decay_steps", C.c_int32), ("beta1", C.c_double),
-                ("beta2", C.c_double), ("adam_eps", C.c_double)]
+                ("beta2", C.c_double), ("adam_eps", C.c_double), ("dropout_rate", C.c_double),
+                ("dropout_seed", C.c_uint64)]
 
 
 class McmcDesc(C.Structure):
@@ -69,6 +70,18 @@ class McmcDesc(C.Structure):
                 ("bins", C.c_int32), ("proj_i", C.c_int32), ("proj_j", C.c_int32), ("path_n_nodes", C.c_int32),
                 ("path_n_cv", C.c_int32), ("path_cv", C.c_void_p), ("path_nodes", C.c_void_p),
                 ("path_lambda", C.c_double), ("path_z_lo", C.c_double), ("path_z_hi", C.c_double)]
+
+
+class McmcPath(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("n_cv", C.c_int32), ("cv", C.c_void_p), ("nodes", C.c_void_p),
+                ("lam", C.c_double), ("z_lo", C.c_double), ("z_hi", C.c_double)]
+
+
+def _path_arrays(path):
+    """(nodes float32 [P][Cp], cvs int32 [Cp], lambda, z_lo, z_hi) from a path tuple."""
+    nodes = np.ascontiguousarray(path[0], dtype=np.float32)
+    cvs = np.ascontiguousarray(path[1], dtype=np.int32)
+    return nodes, cvs, float(path[2]), float(path[3]), float(path[4])
 
 
 class SelectDesc(C.Structure):
@@ -144,8 +157,8 @@ def lib() -> C.CDLL:
     L.rid_trainer_weights.argtypes = [vp, vp, C.POINTER(i64), i32, vp]
     L.rid_label_constrained.argtypes = [vp, i32, vp, vp, i32, vp, vp, u64, i64, i64, i32, vp, vp, vp, vp, vp,
                                         i32, vp]
-    L.rid_mcmc_system.argtypes = [vp, i32, vp, i64, i64, C.c_double, C.c_double, u64, i32, i32, i32, vp, vp, vp,
-                                  vp, vp, C.POINTER(i64), i32, vp]
+    L.rid_mcmc_system.argtypes = [vp, i32, vp, i64, i64, C.c_double, C.c_double, u64, i32, i32, i32,
+                                  C.POINTER(McmcPath), vp, vp, vp, vp, vp, vp, vp, C.POINTER(i64), i32, vp]
     L.rid_select.argtypes = [C.POINTER(SelectDesc), i32, vp, vp, vp, C.POINTER(i32), C.POINTER(i32),
                              C.POINTER(C.c_double), i32, vp]
     L.rid_mcmc.argtypes = [C.POINTER(McmcDesc), vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(i64), i32, vp]
@@ -296,19 +309,27 @@ class System:
                                            _stream_ptr(stream)))
 
     def mcmc(self, s0, n_steps, n_burn, kT, step_size, seed, bins=101, pair=(0, 1), s_out=None, hist1=None,
-             hist2=None, pmf1=None, pmf2=None, stream=None):
+             hist2=None, pmf1=None, pmf2=None, path=None, hist_path=None, pmf_path=None, stream=None):
         """MCMC dimension reduction with this system's ensemble at its precision
-        (rid_mcmc_system); returns the number of accepted moves."""
+        (rid_mcmc_system); returns the number of accepted moves.  path = (nodes
+        [P][Cp], cvs [Cp], lambda, z_lo, z_hi) adds the (s_path, z_path)
+        projection into hist_path / pmf_path [bins][bins]."""
         W = int(s0.shape[0])
         a = _Args()
         ps = a.ptr(s0, np.float32, (W, self.C))
         outs = [a.ptr(s_out, np.float32, (W, self.C), True), a.ptr(hist1, np.uint64, (self.C, bins), True),
                 a.ptr(hist2, np.uint64, (bins, bins), True), a.ptr(pmf1, np.float64, (self.C, bins), True),
-                a.ptr(pmf2, np.float64, (bins, bins), True)]
+                a.ptr(pmf2, np.float64, (bins, bins), True), a.ptr(hist_path, np.uint64, (bins, bins), True),
+                a.ptr(pmf_path, np.float64, (bins, bins), True)]
+        pp = None
+        if path is not None:
+            nodes, cvs, lam, zlo, zhi = _path_arrays(path)
+            pp = McmcPath(nodes.shape[0], cvs.size, cvs.ctypes.data, nodes.ctypes.data, lam, zlo, zhi)
         nacc = C.c_int64(0)
         _check(lib().rid_mcmc_system(self.h, W, ps, C.c_int64(n_steps), C.c_int64(n_burn), float(kT),
-                                     float(step_size), C.c_uint64(seed), int(bins), int(pair[0]), int(pair[1]), *outs,
-                                     C.byref(nacc), a.mem, _stream_ptr(stream)))
+                                     float(step_size), C.c_uint64(seed), int(bins), int(pair[0]), int(pair[1]),
+                                     None if pp is None else C.byref(pp), *outs, C.byref(nacc), a.mem,
+                                     _stream_ptr(stream)))
         return nacc.value
 
     def eval_forces(self, x, bias=RID_BIAS_NONE, s0=None, kappa=None, f_out=None, s_out=None, eps_out=None,
@@ -535,16 +556,20 @@ class Trainer:
     """Fits an ensemble to mean-force labels on the current CUDA device (wraps
     rid_trainer*): per member, Adam steps on the mean squared difference
     between dA_i/ds and the labels, learning rate init_lr * decay_rate^(t /
-    decay_steps).  Weights use the packed layout of EnsembleParams.weights."""
+    decay_steps).  Weights use the packed layout of EnsembleParams.weights.
+    dropout_rate > 0 thins every hidden layer during training (inverted
+    dropout, masks from Philox keyed by dropout_seed)."""
 
     def __init__(self, n_models, n_cv, n_layers, width, weights, batch_size=128, resnet=False, init_lr=8e-4,
-                 decay_rate=0.96, decay_steps=120, beta1=0.9, beta2=0.999, adam_eps=1e-8):
+                 decay_rate=0.96, decay_steps=120, beta1=0.9, beta2=0.999, adam_eps=1e-8, dropout_rate=0.0,
+                 dropout_seed=0):
         L = lib()
         self.M, self.C, self.B = int(n_models), int(n_cv), int(batch_size)
         w = np.ascontiguousarray(weights, dtype=np.float32)
         self.P = w.size // self.M
         d = TrainDesc(self.M, self.C, int(n_layers), int(width), int(bool(resnet)), self.B, float(init_lr),
-                      float(decay_rate), int(decay_steps), float(beta1), float(beta2), float(adam_eps))
+                      float(decay_rate), int(decay_steps), float(beta1), float(beta2), float(adam_eps),
+                      float(dropout_rate), int(dropout_seed))
         h = C.c_void_p()
         _check(L.rid_trainer_create(C.byref(d), w.ctypes.data, C.byref(h)))
         self.h = h
@@ -623,10 +648,8 @@ def mcmc(weights, n_models, n_cv, n_layers, width, s0, n_steps, n_burn, kT, step
     nodes = cvs = None
     npn, ncv, lam, zlo, zhi = 0, 0, 1.0, 0.0, 1.0
     if path is not None:
-        nodes = np.ascontiguousarray(path[0], dtype=np.float32)
-        cvs = np.ascontiguousarray(path[1], dtype=np.int32)
+        nodes, cvs, lam, zlo, zhi = _path_arrays(path)
         npn, ncv = nodes.shape[0], cvs.size
-        lam, zlo, zhi = float(path[2]), float(path[3]), float(path[4])
     d = McmcDesc(int(n_models), Cn, int(n_layers), int(width), int(bool(resnet)), pw.value, W, int(n_steps),
                  int(n_burn), float(kT), float(step_size), int(seed), int(bins), int(pair[0]), int(pair[1]),
                  npn, ncv, None if cvs is None else cvs.ctypes.data, None if nodes is None else nodes.ctypes.data,

@@ -175,6 +175,48 @@ def test_system_path_fp32_follows_the_oracle(R):
     assert abs(nacc - ref["n_accepted"]) <= K * int((~safe).sum())
 
 
+def test_system_path_projection_follows_the_oracle(R):
+    # the path projection through rid_mcmc_system (FP32 ensemble kernels of a
+    # system) against the oracle's path histogram on the same trajectories,
+    # with the bound of the standalone path test
+    M, C, L, H, W, K, burn, bins = 2, 4, 2, 32, 256, 30, 10, 25
+    ens = I.make_ensemble(M, 2 * C, L, H, 38)
+    s0 = np.random.default_rng(8).uniform(-math.pi, math.pi, size=(W, C)).astype(np.float32)
+    nodes = np.stack([np.linspace(-2.5, 2.5, 9), np.linspace(1.0, -1.0, 9)], axis=1).astype(np.float32)
+    path = (nodes, [1, 3], 2.0, -1.0, 3.0)
+    hp = np.zeros((bins, bins), np.uint64)
+    fp = np.zeros((bins, bins))
+    h2 = np.zeros((bins, bins), np.uint64)
+    with R.System(I.make_system(30, C, 38)) as sysobj:
+        sysobj.set_ensemble(ens, precision=R.RID_PREC_FP32)
+        sysobj.mcmc(s0, K, burn, 1.0, 0.4, 14, bins=bins, hist2=h2, path=path, hist_path=hp, pmf_path=fp)
+        h2b = np.zeros_like(h2)
+        sysobj.mcmc(s0, K, burn, 1.0, 0.4, 14, bins=bins, hist2=h2b)
+    ref = MC.run(ens.weights, C, L, H, False, s0, K, burn, 1.0, 0.4, 14, bins, (0, 1), path=path)
+    unsafe = int((ref["min_margin"] <= 1e-3).sum())
+    diff = int(np.abs(hp.astype(np.int64) - ref["hist_path"]).sum())
+    print(f"\nsystem path histogram: |GPU - oracle|_1 = {diff} of {W * (K - burn)} counts, near-threshold {unsafe}")
+    assert int(hp.sum()) == W * (K - burn)
+    assert diff <= 2 * unsafe * (K - burn) + 0.01 * W * (K - burn)
+    np.testing.assert_allclose(fp, MC.projected_pmf(hp, 1.0), rtol=1e-12, atol=1e-12)
+    # the projection only counts: the chain and its other histograms are those of a run without it
+    assert np.array_equal(h2, h2b)
+
+
+def test_system_path_errors(R):
+    C = 3
+    ens = I.make_ensemble(1, 2 * C, 2, 32, 39)
+    s0 = np.zeros((4, C), np.float32)
+    nodes = np.zeros((3, 2), np.float32)
+    with R.System(I.make_system(22, C, 39)) as sysobj:
+        sysobj.set_ensemble(ens, precision=R.RID_PREC_FP32)
+        for bad in ((nodes[:1], [0, 1], 1.0, 0.0, 1.0), (nodes, [0, 3], 1.0, 0.0, 1.0),
+                    (nodes, [0, 1], 0.0, 0.0, 1.0), (nodes, [0, 1], 1.0, 1.0, 1.0)):
+            with pytest.raises(R.RidError) as e:
+                sysobj.mcmc(s0, 5, 0, 1.0, 0.3, 1, bins=10, path=bad)
+            assert e.value.code == R.RID_ERR_ARG
+
+
 @pytest.mark.parametrize("prec,bound", [("bf16", 0.02), ("fp8", 0.06)])
 def test_system_path_tensor_cores_sample_the_stationary_marginal(R, prec, bound):
     # BF16 / FP8 ensembles on the tensor cores: the sampled joint of two CVs

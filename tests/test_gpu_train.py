@@ -1,5 +1,6 @@
 """Ensemble training on mean-force labels (rid_trainer_*) against the FP64
 training oracle: batch loss and its gradient through the input-gradient pass,
+with and without dropout,
 Adam steps with the exponential learning-rate decay, bit-for-bit
 reproducibility, host / device arguments, errors, a fit of a teacher's
 gradient field, and the hand-off of the trained weights to the ensemble path.
@@ -121,6 +122,53 @@ def test_trajectory_follows_the_oracle(R, M, C, L, H, B, n, resnet):
     assert not np.array_equal(w, ens.weights)
 
 
+@pytest.mark.parametrize("rate", [0.1, 0.5])
+@pytest.mark.parametrize("M,C,L,H,B,n,resnet", SHAPES[:2])
+def test_dropout_loss_and_gradient_match_the_oracle(R, M, C, L, H, B, n, resnet, rate):
+    # the thinned network of the trainer's next step (t = 0): the masks are
+    # the oracle's own Philox draws, so the comparison is the no-dropout one
+    ens, s, mf, idx = _problem(M, C, L, H, B, n, 13, resnet)
+    seed = 0x5EED0000DEADBEEF
+    loss = np.zeros(M, np.float32)
+    grad = np.zeros((M, ens.weights.shape[1]), np.float32)
+    with R.Trainer(M, C, L, H, ens.weights, batch_size=B, resnet=resnet, dropout_rate=rate,
+                   dropout_seed=seed) as tr:
+        tr.set_data(s, mf)
+        tr.grad(idx, loss, grad)
+    q = T.dropout_scales(M, B, L, H, 0, seed, rate)
+    for m in range(M):
+        lo, go = T.loss_and_grad(ens.weights[m].astype(np.float64), 2 * C, L, H, resnet, s[idx[m]], mf[idx[m]],
+                                 q[m])
+        _, gp = T.loss_and_grad(ens.weights[m].astype(np.float64), 2 * C, L, H, resnet, s[idx[m]], mf[idx[m]])
+        assert np.linalg.norm(go - gp) > 0.3 * np.linalg.norm(gp)   # the masks change the gradient
+        assert abs(loss[m] - lo) <= 1e-5 * lo
+        err = np.linalg.norm(grad[m] - go) / np.linalg.norm(go)
+        assert err < 1e-4, err
+
+
+@pytest.mark.parametrize("M,C,L,H,B,n,resnet", SHAPES[:2])
+def test_dropout_trajectory_follows_the_oracle(R, M, C, L, H, B, n, resnet):
+    # K steps with the paper's rate: every step draws its own masks
+    ens, s, mf, _ = _problem(M, C, L, H, B, n, 14, resnet)
+    rng = np.random.default_rng(10)
+    K, rate, seed = 4, 0.1, 99
+    idx = np.stack([np.stack([rng.choice(n, size=B, replace=B > n) for _ in range(M)]) for _ in range(K)])
+    idx = idx.astype(np.int32)
+    kw = dict(init_lr=2e-3, decay_rate=0.5, decay_steps=2)
+    losses = np.zeros((K, M), np.float32)
+    with R.Trainer(M, C, L, H, ens.weights, batch_size=B, resnet=resnet, dropout_rate=rate, dropout_seed=seed,
+                   **kw) as tr:
+        tr.set_data(s, mf)
+        tr.run(idx, losses)
+        w, _ = tr.weights()
+    wo, lo, _, _ = T.train(ens.weights, 2 * C, L, H, resnet, s, mf, idx, dropout_rate=rate, dropout_seed=seed, **kw)
+    np.testing.assert_allclose(losses, lo, rtol=1e-5)
+    d = np.abs(w.astype(np.float64) - wo)
+    print(f"\n[{M}x{H}x{L} dropout] weights beyond 1e-6 of the oracle: {np.mean(d > 1e-6):.2e}, max {d.max():.2e}")
+    assert np.mean(d > 1e-6) <= 1e-3
+    assert d.max() <= K * kw["init_lr"]
+
+
 def test_runs_are_reproducible_and_split_runs_equal_one_run(R):
     M, C, L, H, B, n = 2, 6, 3, 64, 64, 500
     ens, s, mf, _ = _problem(M, C, L, H, B, n, 5)
@@ -129,6 +177,18 @@ def test_runs_are_reproducible_and_split_runs_equal_one_run(R):
     out = []
     for split in (False, True):
         with R.Trainer(M, C, L, H, ens.weights, batch_size=B) as tr:
+            tr.set_data(s, mf)
+            if split:
+                tr.run(idx[:3])
+                tr.run(idx[3:])
+            else:
+                tr.run(idx)
+            out.append(tr.weights()[0])
+    assert np.array_equal(out[0], out[1])
+    # with dropout the masks follow the trainer's step count across calls
+    out = []
+    for split in (False, True):
+        with R.Trainer(M, C, L, H, ens.weights, batch_size=B, dropout_rate=0.2, dropout_seed=4) as tr:
             tr.set_data(s, mf)
             if split:
                 tr.run(idx[:3])
@@ -179,6 +239,10 @@ def test_errors(R):
     with pytest.raises(R.RidError) as e:
         R.Trainer(M, C, L, H, ens.weights, batch_size=0)
     assert e.value.code == R.RID_ERR_ARG
+    for rate in (1.0, -0.1):
+        with pytest.raises(R.RidError) as e:
+            R.Trainer(M, C, L, H, ens.weights, batch_size=B, dropout_rate=rate)
+        assert e.value.code == R.RID_ERR_ARG
 
 
 def test_fit_of_a_teacher_gradient_field_and_hand_off_to_the_ensemble(R):

@@ -235,7 +235,7 @@ def _torch_member(ens, m, u):
         h = t + h if (ens.resnet and l > 0) else t
     A = w[p:p + H] @ h + w[p + H]
     (g,) = torch.autograd.grad(A, uu)
-    return float(A), g.numpy()
+    return float(A.detach()), g.numpy()
 
 
 @pytest.mark.parametrize("resnet", [False, True])
