@@ -25,8 +25,8 @@
 // Dropout (drop_out_rate) scales each hidden unit's tanh by q in {0, 1/(1-p)}:
 // h_l = q t_l + r_l h_{l-1}, and every (1 - t^2) above that belongs to a
 // layer's activation derivative becomes q (1 - t^2), tbar_l gains the factor
-// q, and zbar_{l-1} = (tbar + q hbar)(1 - t^2).  The masks come from Philox
-// (k_tr_mask), one counter per four units.
+// q, and zbar_{l-1} = (tbar + q hbar)(1 - t^2).  The masks come from Philox,
+// one counter per four units, drawn by the batch gather of each step.
 // Every sum is taken in a fixed order, so a run is reproducible bit for bit.
 #include <cmath>
 #include <vector>
@@ -35,11 +35,41 @@
 
 namespace {
 
-// u = (cos s, sin s) of each member's batch, plus the batch's s and labels.
-// idx is checked; an index outside [0, n) reads sample 0 and sets *bad.
+// Dropout scales of one step (one Philox block per four units):
+// Q[l][m][b][j] = 1/(1-p) iff word j % 4 of Philox(j / 4 + nw (l + L m), b,
+// step, 4) >= thr, else 0 (nw = ceil(H / 4)).
+struct MaskArgs {
+    float* Q;                  // NULL: no dropout
+    int L, H;
+    uint32_t step, thr, k0, k1;
+    float scale;
+};
+__device__ __forceinline__ void tr_mask_block(const MaskArgs& a, int M, int B, long long e) {
+    const int nw = (a.H + 3) / 4;
+    const int k = (int)(e % nw);
+    const long long r = e / nw;                       // (l, m, b)
+    const int b = (int)(r % B);
+    const long long lm = r / B;                       // l M + m
+    const int m = (int)(lm % M), l = (int)(lm / M);
+    const uint4 x = rid_philox(make_uint4((uint32_t)(k + nw * (l + a.L * m)), (uint32_t)b, a.step, 4u), a.k0, a.k1);
+    const uint32_t wd[4] = {x.x, x.y, x.z, x.w};
+    float* q = a.Q + r * a.H + 4 * k;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (4 * k + c < a.H) q[c] = wd[c] >= a.thr ? a.scale : 0.0f;
+}
+
+// u = (cos s, sin s) of each member's batch, plus the batch's s and labels,
+// and the step's dropout scales.  idx is checked; an index outside [0, n)
+// reads sample 0 and sets *bad.
 __global__ void k_tr_gather(const int* __restrict__ idx, const float* __restrict__ s, const float* __restrict__ mf,
                             int n, int M, int B, int C, float* __restrict__ U, float* __restrict__ SB,
-                            float* __restrict__ MFB, int* bad) {
+                            float* __restrict__ MFB, int* bad, MaskArgs mk) {
+    if (mk.Q) {
+        const long long nm = (long long)mk.L * M * B * ((mk.H + 3) / 4);
+        for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nm; e += (long long)gridDim.x * blockDim.x)
+            tr_mask_block(mk, M, B, e);
+    }
     const long long tot = (long long)M * B * C;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
         const long long mb = e / C;
@@ -59,18 +89,21 @@ __global__ void k_tr_gather(const int* __restrict__ idx, const float* __restrict
     }
 }
 
-// Per member (grid x): residual dA/ds - MF, the loss (mean of its square over
-// B x C, summed in a fixed order), and gbar_{-1} = d loss / d(dA/du).
+// Per member (grid y) and chunk of LT (sample, CV) pairs (grid x): residual
+// dA/ds - MF, gbar_{-1} = d loss / d(dA/du), and the chunk's sum of squared
+// residuals (a fixed-order tree) into lpart[m][chunk]; k_tr_colsum adds the
+// chunks in order into the loss.
 constexpr int LT = 256;
 __global__ void __launch_bounds__(LT) k_tr_loss(const float* __restrict__ G0, const float* __restrict__ SB,
                                                 const float* __restrict__ MFB, int B, int C,
-                                                float* __restrict__ GB0, float* __restrict__ loss) {
+                                                float* __restrict__ GB0, double* __restrict__ lpart) {
     __shared__ double red[LT];
-    const int m = blockIdx.x;
+    const int m = blockIdx.y;
     const long long n = (long long)B * C;
     const float scale = 2.0f / (float)n;
     double part = 0.0;
-    for (long long e = threadIdx.x; e < n; e += LT) {
+    const long long e = (long long)blockIdx.x * LT + threadIdx.x;
+    if (e < n) {
         const long long o = (long long)m * n + e;
         const float sv = SB[o];
         float sn, cs;
@@ -89,45 +122,46 @@ __global__ void __launch_bounds__(LT) k_tr_loss(const float* __restrict__ G0, co
         if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) loss[m] = (float)(red[0] / (double)n);
+    if (threadIdx.x == 0) lpart[(long long)m * gridDim.x + blockIdx.x] = red[0];
 }
 
 // Column sums over the batch rows of [M][B][H] activations into the packed
-// gradient: grid (ceil(H / 128), M, nvec).
+// gradient: grid (ceil(H / 128), M, nvec + 1).  The last z slice adds the
+// loss chunks of each member in order: loss[m] = sum lpart[m][.] / (B C).
 struct ColSums {
     const float* src[RID_MAX_LAYERS + 1];
     long long dst_off[RID_MAX_LAYERS + 1];
     int n;
+    const double* lpart;
+    int nchunk;
+    double nBC;
+    float* loss;
 };
 __global__ void k_tr_colsum(ColSums cs, int B, int H, long long act_sm, float* __restrict__ grad, long long P) {
     const int m = blockIdx.y, v = blockIdx.z;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= cs.n || j >= H) return;
-    const float* src = cs.src[v] + (long long)m * act_sm;
-    float a = 0.0f;
-    for (int b = 0; b < B; ++b) a += src[(long long)b * H + j];
-    grad[(long long)m * P + cs.dst_off[v] + j] = a;
-}
-
-// Dropout scales of one step: Q[l][m][b][j] = 1/(1-p) iff word j % 4 of
-// Philox(j / 4 + nw (l + L m), b, step, 4) >= thr, else 0 (nw = ceil(H / 4)).
-__global__ void k_tr_mask(float* __restrict__ Q, int M, int B, int L, int H, uint32_t step, uint32_t thr,
-                          float scale, uint32_t k0, uint32_t k1) {
-    const int nw = (H + 3) / 4;
-    const long long tot = (long long)L * M * B * nw;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(e % nw);
-        const long long r = e / nw;                       // (l, m, b)
-        const int b = (int)(r % B);
-        const long long lm = r / B;                       // l M + m
-        const int m = (int)(lm % M), l = (int)(lm / M);
-        const uint4 x = rid_philox(make_uint4((uint32_t)(k + nw * (l + L * m)), (uint32_t)b, step, 4u), k0, k1);
-        const uint32_t wd[4] = {x.x, x.y, x.z, x.w};
-        float* q = Q + r * H + 4 * k;
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (4 * k + c < H) q[c] = wd[c] >= thr ? scale : 0.0f;
+    if (v == cs.n) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            double t = 0.0;
+            for (int c = 0; c < cs.nchunk; ++c) t += cs.lpart[(long long)m * cs.nchunk + c];
+            cs.loss[m] = (float)(t / cs.nBC);
+        }
+        return;
     }
+    if (v > cs.n || j >= H) return;
+    const float* src = cs.src[v] + (long long)m * act_sm + j;
+    // rows in increasing order; eight loads are issued ahead of their adds
+    float a = 0.0f;
+    int b = 0;
+    for (; b + 8 <= B; b += 8) {
+        float x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = src[(long long)(b + k) * H];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a += x[k];
+    }
+    for (; b < B; ++b) a += src[(long long)b * H];
+    grad[(long long)m * P + cs.dst_off[v] + j] = a;
 }
 
 __global__ void k_tr_adam(float* __restrict__ w, float* __restrict__ am, float* __restrict__ av,
@@ -164,6 +198,7 @@ struct rid_trainer {
     float* dloss = nullptr;  // [cap_loss]
     long long cap_loss = 0;
     int* dbad = nullptr;
+    double* lpart = nullptr;  // [M][ceil(B C / 256)] loss chunk sums
     // carve of act, all [M][B][X]
     float *U, *SB, *MFB, *G0, *GB0;
     float* Q[RID_MAX_LAYERS] = {};   // dropout scales [M][B][H] per layer (NULL: no dropout)
@@ -205,17 +240,14 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, cuda
     const int M = d.n_models, B = d.batch_size, C = d.n_cv, D = tr->D, L = d.n_layers, H = d.width;
     const long long P = tr->P;
     const long long smH = (long long)B * H, smD = (long long)B * D;
-    if (tr->Q[0]) {
-        const long long tot = (long long)L * M * B * ((H + 3) / 4);
-        const int blocks = (int)((tot + 255) / 256 < 2048 ? (tot + 255) / 256 : 2048);
-        k_tr_mask<<<blocks, 256, 0, st>>>(tr->Q[0], M, B, L, H, (uint32_t)step, tr->dthr, tr->dscale,
-                                          (uint32_t)d.dropout_seed, (uint32_t)(d.dropout_seed >> 32));
-    }
     {
-        const long long tot = (long long)M * B * C;
+        MaskArgs mk{tr->Q[0], L, H, (uint32_t)step, tr->dthr, (uint32_t)d.dropout_seed,
+                    (uint32_t)(d.dropout_seed >> 32), tr->dscale};
+        long long tot = (long long)M * B * C;
+        if (mk.Q && (long long)L * M * B * ((H + 3) / 4) > tot) tot = (long long)L * M * B * ((H + 3) / 4);
         const int blocks = (int)((tot + 255) / 256 < 1024 ? (tot + 255) / 256 : 1024);
         k_tr_gather<<<blocks, 256, 0, st>>>(idx, tr->ds, tr->dmf, tr->n_data, M, B, C, tr->U, tr->SB, tr->MFB,
-                                            tr->dbad);
+                                            tr->dbad, mk);
     }
     // forward
     for (int l = 0; l < L; ++l) {
@@ -265,7 +297,8 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, cuda
         e.Q = l == 0 ? nullptr : tr->Q[l - 1];
         launch_gemm<EPI_BWD>(g, M, st);
     }
-    k_tr_loss<<<M, LT, 0, st>>>(tr->G0, tr->SB, tr->MFB, B, C, tr->GB0, loss);
+    const int nchunk = (int)(((long long)B * C + LT - 1) / LT);
+    k_tr_loss<<<dim3(nchunk, M), LT, 0, st>>>(tr->G0, tr->SB, tr->MFB, B, C, tr->GB0, tr->lpart);
     // adjoint of the input-gradient pass, increasing l
     for (int l = 0; l < L; ++l) {
         const int fin = l == 0 ? D : H;
@@ -311,11 +344,15 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, cuda
         e.Q = tr->Q[l - 1];
         launch_gemm<EPI_BACK>(g, M, st);
     }
-    // weight gradients: dW_l[a][b] = sum_k d_l[k][a] gbar_{l-1}[k][b] + zbar_l[k][a] h_{l-1}[k][b]
+    // weight gradients, all layers in one launch:
+    // dW_l[a][b] = sum_k d_l[k][a] gbar_{l-1}[k][b] + zbar_l[k][a] h_{l-1}[k][b]
+    GemmBatch wb{};
+    wb.n = L;
+    wb.M = M;
     for (int l = 0; l < L; ++l) {
         const int fin = l == 0 ? D : H;
         const long long smF = l == 0 ? smD : smH;
-        GemmArgs g{};
+        GemmArgs& g = wb.g[l];
         g.nseg = 2;
         g.seg[0].a = act_transposed(tr->Dl[l], H, smH);
         g.seg[0].b = Operand{l == 0 ? tr->GB0 : tr->GB[l - 1], 1, (long long)fin, smF};
@@ -328,8 +365,8 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, cuda
         g.e.out = tr->grad + tr->woff[l];
         g.e.out_sm = P;
         g.e.ld = fin;
-        launch_gemm<EPI_STORE>(g, M, st);
     }
+    launch_gemm_batch<EPI_STORE>(wb, st);
     ColSums cs{};
     for (int l = 0; l < L; ++l) {
         cs.src[l] = tr->ZB[l];
@@ -338,7 +375,11 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, cuda
     cs.src[L] = tr->GB[L - 1];
     cs.dst_off[L] = tr->ooff;
     cs.n = L + 1;
-    k_tr_colsum<<<dim3((H + 127) / 128, M, L + 1), 128, 0, st>>>(cs, B, H, smH, tr->grad, P);
+    cs.lpart = tr->lpart;
+    cs.nchunk = nchunk;
+    cs.nBC = (double)B * C;
+    cs.loss = loss;
+    k_tr_colsum<<<dim3((H + 127) / 128, M, L + 2), 128, 0, st>>>(cs, B, H, smH, tr->grad, P);
     return RID_OK;
 }
 
@@ -414,6 +455,7 @@ RID_API int rid_trainer_create(const rid_train_desc* desc, const float* weights,
     bool ok = cudaMalloc(&tr->w, sizeof(float) * 4 * nP) == cudaSuccess;
     ok = ok && cudaMalloc(&tr->act, sizeof(float) * nact) == cudaSuccess;
     ok = ok && cudaMalloc(&tr->dbad, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMalloc(&tr->lpart, sizeof(double) * M * (((long long)B * C + 255) / 256)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         rid_trainer_destroy(tr);
@@ -460,6 +502,7 @@ RID_API int rid_trainer_destroy(rid_trainer* tr) {
     cudaFree(tr->w);
     cudaFree(tr->act);
     cudaFree(tr->dbad);
+    cudaFree(tr->lpart);
     cudaFree(tr->ds);
     cudaFree(tr->didx);
     cudaFree(tr->dloss);
