@@ -333,7 +333,7 @@ def run_training(rid, torch, steps, seed=11):
     return {"workload": f"{M} members {D}-{H}x{L}-1, batch {B} per member, dropout 0.1, {n} labels "
                         "(teacher CV gradients)",
             "value": M * B * steps / (ms * 1e-3), "unit": "member-samples/s", "steps": steps,
-            "ms_per_step": ms / steps, "kernel_launches_per_step": 5 * L + 4,
+            "ms_per_step": ms / steps, "kernel_launches_per_step": 4 * L + 4,
             "loss_first": float(lo[:warm].mean()), "loss_last": float(lo[-20:].mean()),
             "algorithmic_gflop_per_step": fl / 1e9,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak(torch)[0], "unit": "TFLOP/s",

@@ -65,6 +65,8 @@ __device__ __forceinline__ void tr_mask_block(const MaskArgs& a, int M, int B, l
 __global__ void k_tr_gather(const int* __restrict__ idx, const float* __restrict__ s, const float* __restrict__ mf,
                             int n, int M, int B, int C, float* __restrict__ U, float* __restrict__ SB,
                             float* __restrict__ MFB, int* bad, MaskArgs mk) {
+    pdl_trigger();
+    pdl_wait();
     if (mk.Q) {
         const long long nm = (long long)mk.L * M * B * ((mk.H + 3) / 4);
         for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nm; e += (long long)gridDim.x * blockDim.x)
@@ -97,6 +99,8 @@ constexpr int LT = 256;
 __global__ void __launch_bounds__(LT) k_tr_loss(const float* __restrict__ G0, const float* __restrict__ SB,
                                                 const float* __restrict__ MFB, int B, int C,
                                                 float* __restrict__ GB0, double* __restrict__ lpart) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ double red[LT];
     const int m = blockIdx.y;
     const long long n = (long long)B * C;
@@ -138,6 +142,8 @@ struct ColSums {
     float* loss;
 };
 __global__ void k_tr_colsum(ColSums cs, int B, int H, long long act_sm, float* __restrict__ grad, long long P) {
+    pdl_trigger();
+    pdl_wait();
     const int m = blockIdx.y, v = blockIdx.z;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (v == cs.n) {
@@ -167,6 +173,8 @@ __global__ void k_tr_colsum(ColSums cs, int B, int H, long long act_sm, float* _
 __global__ void k_tr_adam(float* __restrict__ w, float* __restrict__ am, float* __restrict__ av,
                           const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps, float c1,
                           float c2) {
+    pdl_trigger();
+    pdl_wait();
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const float gv = g[e];
         const float m = fmaf(b1, am[e], (1.0f - b1) * gv);
@@ -234,8 +242,10 @@ int grow(void** p, long long* cap, long long need, size_t elem) {
 
 // One step's gradient into tr->grad and the per-member loss into loss[M],
 // for the batch indices idx [M][B] (device) at training step `step` (the
-// step index of the dropout masks).
-int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, cudaStream_t st) {
+// step index of the dropout masks).  Every kernel after the first is a
+// programmatic dependent of its predecessor (pdl_wait before any access);
+// the first is one too unless `after_copy` (it then follows a memory copy).
+int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, bool after_copy, cudaStream_t st) {
     const rid_train_desc& d = tr->d;
     const int M = d.n_models, B = d.batch_size, C = d.n_cv, D = tr->D, L = d.n_layers, H = d.width;
     const long long P = tr->P;
@@ -246,8 +256,8 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, cuda
         long long tot = (long long)M * B * C;
         if (mk.Q && (long long)L * M * B * ((H + 3) / 4) > tot) tot = (long long)L * M * B * ((H + 3) / 4);
         const int blocks = (int)((tot + 255) / 256 < 1024 ? (tot + 255) / 256 : 1024);
-        k_tr_gather<<<blocks, 256, 0, st>>>(idx, tr->ds, tr->dmf, tr->n_data, M, B, C, tr->U, tr->SB, tr->MFB,
-                                            tr->dbad, mk);
+        TCK(launch_k(k_tr_gather, dim3(blocks), dim3(256), 0, st, !after_copy, idx, (const float*)tr->ds,
+                     (const float*)tr->dmf, tr->n_data, M, B, C, tr->U, tr->SB, tr->MFB, tr->dbad, mk));
     }
     // forward
     for (int l = 0; l < L; ++l) {
@@ -274,7 +284,7 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, cuda
         e.Gout = tr->G[L - 1];
         e.Dout = tr->Dl[L - 1];
         e.Q = tr->Q[l];
-        launch_gemm<EPI_FWD>(g, M, st);
+        launch_gemm<EPI_FWD>(g, M, st, true);
     }
     // input gradient, decreasing l: g_{l-1} = d_l W_l (+ r g_l)
     for (int l = L - 1; l >= 0; --l) {
@@ -295,10 +305,11 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, cuda
         e.Tl = l == 0 ? nullptr : tr->T[l - 1];
         e.Dout = l == 0 ? nullptr : tr->Dl[l - 1];
         e.Q = l == 0 ? nullptr : tr->Q[l - 1];
-        launch_gemm<EPI_BWD>(g, M, st);
+        launch_gemm<EPI_BWD>(g, M, st, true);
     }
     const int nchunk = (int)(((long long)B * C + LT - 1) / LT);
-    k_tr_loss<<<dim3(nchunk, M), LT, 0, st>>>(tr->G0, tr->SB, tr->MFB, B, C, tr->GB0, tr->lpart);
+    TCK(launch_k(k_tr_loss, dim3(nchunk, M), dim3(LT), 0, st, true, (const float*)tr->G0, (const float*)tr->SB,
+                 (const float*)tr->MFB, B, C, tr->GB0, tr->lpart));
     // adjoint of the input-gradient pass, increasing l
     for (int l = 0; l < L; ++l) {
         const int fin = l == 0 ? D : H;
@@ -321,7 +332,7 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, cuda
         e.last = l == L - 1;
         e.out3 = tr->ZB[L - 1];
         e.Q = tr->Q[l];
-        launch_gemm<EPI_ADJ>(g, M, st);
+        launch_gemm<EPI_ADJ>(g, M, st, true);
     }
     // back through the forward pass, decreasing l (hbar_{L-1} = 0)
     for (int l = L - 1; l >= 1; --l) {
@@ -342,7 +353,7 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, cuda
         e.tb = tr->TB[l - 1];
         e.out3 = tr->ZB[l - 1];
         e.Q = tr->Q[l - 1];
-        launch_gemm<EPI_BACK>(g, M, st);
+        launch_gemm<EPI_BACK>(g, M, st, true);
     }
     // weight gradients, all layers in one launch:
     // dW_l[a][b] = sum_k d_l[k][a] gbar_{l-1}[k][b] + zbar_l[k][a] h_{l-1}[k][b]
@@ -366,7 +377,7 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, cuda
         g.e.out_sm = P;
         g.e.ld = fin;
     }
-    launch_gemm_batch<EPI_STORE>(wb, st);
+    launch_gemm_batch<EPI_STORE>(wb, st, true);
     ColSums cs{};
     for (int l = 0; l < L; ++l) {
         cs.src[l] = tr->ZB[l];
@@ -379,7 +390,8 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, cuda
     cs.nchunk = nchunk;
     cs.nBC = (double)B * C;
     cs.loss = loss;
-    k_tr_colsum<<<dim3((H + 127) / 128, M, L + 2), 128, 0, st>>>(cs, B, H, smH, tr->grad, P);
+    TCK(launch_k(k_tr_colsum, dim3((H + 127) / 128, M, L + 2), dim3(128), 0, st, true, cs, B, H, smH, tr->grad,
+                 (long long)P));
     return RID_OK;
 }
 
@@ -543,7 +555,7 @@ RID_API int rid_trainer_grad(rid_trainer* tr, const int32_t* idx, float* loss_ou
     if (int rc = grow((void**)&tr->didx, &tr->cap_idx, (long long)M * B, sizeof(int))) return rc;
     if (int rc = grow((void**)&tr->dloss, &tr->cap_loss, M, sizeof(float))) return rc;
     if (int rc = tr_copy_in(tr->didx, idx, sizeof(int) * (size_t)M * B, mem, st)) return rc;
-    if (int rc = tr_gradient(tr, tr->didx, tr->dloss, tr->steps, st)) return rc;
+    if (int rc = tr_gradient(tr, tr->didx, tr->dloss, tr->steps, true, st)) return rc;
     TCK(cudaGetLastError());
     if (loss_out)
         if (int rc = tr_copy_out(loss_out, tr->dloss, sizeof(float) * M, mem, st)) return rc;
@@ -569,11 +581,11 @@ RID_API int rid_trainer_run(rid_trainer* tr, int32_t n_steps, const int32_t* idx
     const int ablocks = (int)((nP + 255) / 256 < 2048 ? (nP + 255) / 256 : 2048);
     for (int k = 0; k < n_steps; ++k) {
         const int64_t t = tr->steps + k;
-        if (int rc = tr_gradient(tr, tr->didx + per * k, tr->dloss + (long long)M * k, t, st)) return rc;
+        if (int rc = tr_gradient(tr, tr->didx + per * k, tr->dloss + (long long)M * k, t, k == 0, st)) return rc;
         const double lr = d.init_lr * std::pow(d.decay_rate, (double)t / (double)d.decay_steps);
         const double c1 = 1.0 - std::pow(d.beta1, (double)(t + 1)), c2 = 1.0 - std::pow(d.beta2, (double)(t + 1));
-        k_tr_adam<<<ablocks, 256, 0, st>>>(tr->w, tr->am, tr->av, tr->grad, nP, (float)lr, (float)d.beta1,
-                                           (float)d.beta2, (float)d.adam_eps, (float)c1, (float)c2);
+        TCK(launch_k(k_tr_adam, dim3(ablocks), dim3(256), 0, st, true, tr->w, tr->am, tr->av, (const float*)tr->grad,
+                     nP, (float)lr, (float)d.beta1, (float)d.beta2, (float)d.adam_eps, (float)c1, (float)c2));
     }
     TCK(cudaGetLastError());
     if (loss_out)

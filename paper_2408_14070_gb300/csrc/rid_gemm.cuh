@@ -85,6 +85,35 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may be scheduled before its predecessor on the stream has
+// finished; pdl_wait() returns once the predecessor has completed and its
+// memory is visible (at once for a normal launch).  pdl_trigger() lets the
+// next such kernel be scheduled.  Every kernel of the chain calls pdl_wait()
+// before its first memory access.  The GEMMs trigger after their K loop, so
+// at most the next grid waits resident during their epilogue (a trigger at
+// kernel entry let the whole chain of grids sit resident and slowed the
+// training step from 244 to 327 us); the small kernels trigger at entry.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+// Launch with programmatic stream serialization when pdl is set.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                     Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // One output tile (bx, by) of member z.
 template <int EPI, int TS>
 __device__ __forceinline__ void gemm_tile(const GemmArgs& g, int z, int by, int bx) {
@@ -157,6 +186,7 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs& g, int z, int by, int 
             cp_async_commit();
             mma_tile(t);
         }
+        pdl_trigger();                     // the next kernel may be scheduled during the epilogue
         cp_async_wait<0>();
     } else {
         // rounds of G tiles (one per group); RR - 1 rounds in flight
@@ -174,6 +204,7 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs& g, int z, int by, int 
             issue_round(R + RR - 1);       // refills the stages of round R - 1
             if (R * G + grp < nt) mma_tile(R * G + grp);
         }
+        pdl_trigger();                     // the next kernel may be scheduled during the epilogue
         cp_async_wait<0>();
         __syncthreads();                   // the ring is free: it takes the partial sums
         float* red = gsm;                  // [G - 1][TS][TS]
@@ -249,6 +280,7 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs& g, int z, int by, int 
 
 template <int EPI, int TS>
 __global__ void __launch_bounds__(TileCfg<TS>::threads) k_tr_gemm(GemmArgs g) {
+    pdl_wait();
     gemm_tile<EPI, TS>(g, blockIdx.z, blockIdx.y, blockIdx.x);
 }
 
@@ -260,33 +292,35 @@ struct GemmBatch {
 };
 template <int EPI, int TS>
 __global__ void __launch_bounds__(TileCfg<TS>::threads) k_tr_gemm_batch(GemmBatch b) {
+    pdl_wait();
     const GemmArgs& g = b.g[blockIdx.z / b.M];
     if ((int)blockIdx.x * TS >= g.cols || (int)blockIdx.y * TS >= g.rows) return;
     gemm_tile<EPI, TS>(g, blockIdx.z % b.M, blockIdx.y, blockIdx.x);
 }
 
 template <int EPI, int TS>
-void launch_gemm_ts(const GemmArgs& g, int M, cudaStream_t st) {
+void launch_gemm_ts(const GemmArgs& g, int M, cudaStream_t st, bool pdl) {
     static bool attr = false;   // the ring exceeds the default 48 KB of shared memory
     if (!attr) {
         cudaFuncSetAttribute(k_tr_gemm<EPI, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TileCfg<TS>::smem);
         attr = true;
     }
     dim3 grid((g.cols + TS - 1) / TS, (g.rows + TS - 1) / TS, M);
-    k_tr_gemm<EPI, TS><<<grid, TileCfg<TS>::threads, TileCfg<TS>::smem, st>>>(g);
+    launch_k(k_tr_gemm<EPI, TS>, grid, dim3(TileCfg<TS>::threads), TileCfg<TS>::smem, st, pdl, g);
 }
 
+// pdl: launch as a programmatic dependent of the previous kernel on st.
 template <int EPI>
-void launch_gemm(const GemmArgs& g, int M, cudaStream_t st) {
+void launch_gemm(const GemmArgs& g, int M, cudaStream_t st, bool pdl = false) {
     if (g.rows >= 1024 && g.cols >= 64)
-        launch_gemm_ts<EPI, 64>(g, M, st);
+        launch_gemm_ts<EPI, 64>(g, M, st, pdl);
     else
-        launch_gemm_ts<EPI, 32>(g, M, st);
+        launch_gemm_ts<EPI, 32>(g, M, st, pdl);
 }
 
 // The GEMMs of b (each as launch_gemm would run it with 32-wide tiles) in one launch.
 template <int EPI>
-void launch_gemm_batch(const GemmBatch& b, cudaStream_t st) {
+void launch_gemm_batch(const GemmBatch& b, cudaStream_t st, bool pdl = false) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_tr_gemm_batch<EPI, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -298,7 +332,8 @@ void launch_gemm_batch(const GemmBatch& b, cudaStream_t st) {
         cx = (b.g[k].cols + 31) / 32 > cx ? (b.g[k].cols + 31) / 32 : cx;
         cy = (b.g[k].rows + 31) / 32 > cy ? (b.g[k].rows + 31) / 32 : cy;
     }
-    k_tr_gemm_batch<EPI, 32><<<dim3(cx, cy, b.n * b.M), TileCfg<32>::threads, TileCfg<32>::smem, st>>>(b);
+    launch_k(k_tr_gemm_batch<EPI, 32>, dim3(cx, cy, b.n * b.M), dim3(TileCfg<32>::threads), TileCfg<32>::smem, st,
+             pdl, b);
 }
 
 // Operand helpers over [M][rows][ld] activations.
