@@ -564,6 +564,48 @@ def run_serving(rid, n_req, rate, plain_req, seed=5):
                                                                           "p99": pct(served_first["explore"], 99)}}}
 
 
+def run_fp32_plain(rid, torch, steps, seed=1):
+    """The headline workload (1024 walkers, 200-bead chain, 4 x 40-256x4-1)
+    with the FP32 ensemble (SIMT kernels) against the BF16 tensor-core
+    ensemble: walker-steps/s of both, timed like the headline (each step alone
+    between CUDA events, L2 flushed before it), and the BF16 path's deviation
+    from FP32 in the mean CV force and in epsilon on the same positions."""
+    wl = I.workload(WORKLOAD)
+    sp, x0, ens = make_inputs(wl, seed)
+    W, C = wl["n_walkers"], wl["n_cv"]
+    stream = torch.cuda.current_stream()
+    xd = torch.from_numpy(x0).cuda()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    res, grads, eps = {}, {}, {}
+    for name, prec in (("fp32", rid.RID_PREC_FP32), ("bf16", rid.RID_PREC_BF16)):
+        with rid.System(sp) as system:
+            system.set_ensemble(ens, precision=prec)
+            g = torch.zeros((wl["n_models"], W, C), dtype=torch.float32, device="cuda")
+            e = torch.zeros(W, dtype=torch.float32, device="cuda")
+            system.eval_forces(xd, rid.RID_BIAS_ENSEMBLE, grad_out=g, eps_out=e, stream=stream)
+            grads[name], eps[name] = g.mean(dim=0).double(), e.double()
+            system.walkers_load(xd, stream=stream)
+            system.walkers_advance(3, stream=stream)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for k in range(steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                system.walkers_advance(1, stream=stream)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in ev)
+            system.walkers_read()
+        res[name] = {"value": W * steps / (ms / 1e3), "unit": "walker-steps/s", "ms_per_step": ms / steps}
+    d = (grads["bf16"] - grads["fp32"]).norm(dim=1) / grads["fp32"].norm(dim=1).clamp_min(1e-30)
+    de = (eps["bf16"] - eps["fp32"]).abs() / eps["fp32"].abs().clamp_min(1e-30)
+    res["bf16"]["mean_force_rel_dev_from_fp32"] = {"median": float(d.median()), "max": float(d.max())}
+    res["bf16"]["eps_rel_dev_from_fp32"] = {"median": float(de.median()), "max": float(de.max())}
+    res["bf16_speedup_vs_fp32"] = res["bf16"]["value"] / res["fp32"]["value"]
+    res["workload"] = f"{WORKLOAD}: the headline step with each ensemble precision, {steps} steps"
+    return res
+
+
 def run_precision(rid, torch, steps=10, nve_walkers=64, nve_steps=10000, seed=4):
     """Precision sweep: 8192 walkers of a 100-bead chain, 32 torsion CVs,
     8 x MLP 64 -> 512 x 4 -> 1.  Per ensemble precision: throughput of full
@@ -697,6 +739,7 @@ def main():
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-fp32-plain", action="store_true")
     ap.add_argument("--no-training", action="store_true")
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--no-mcmc", action="store_true")
@@ -850,6 +893,8 @@ def main():
            "fp32_peak": {"value": fp32_peak(torch)[0], "unit": "TFLOP/s", "source": fp32_peak(torch)[1]}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sp, x0, ens, args.cpu_walkers, args.cpu_steps)
+    if rank == 0 and world == 1 and not args.no_fp32_plain:
+        out["fp32_plain"] = run_fp32_plain(rid, torch, args.steps)
     if rank == 0 and world == 1 and not args.no_batching:
         out["batching"] = run_batching(rid, args.batch_jobs, args.batch_steps, args.batch_plain_jobs)
     if rank == 0 and world == 1 and not args.no_precision:
