@@ -6,8 +6,12 @@
 // 8 x 8 register tile.  Activations live in shared memory transposed as
 // [neuron][walker] rows of 36 floats (32 walkers + 4 pad: 16-byte aligned
 // rows whose float4 stores by 8 consecutive lanes hit distinct banks).
-// Weights stream from L2 through the read-only path, coalesced along the
-// output neuron (forward reads W^T [in][out], backward reads W [out][in]).
+// Weight rows (forward: W^T [in][out], backward: W [out][in], 256 output
+// neurons at a time) stream from L2 into a 4-stage ring of 8 rows in shared
+// memory by cp.async, so the four warps share one copy and three stages are
+// in flight while one is multiplied.  Reading every weight from L2 per warp
+// (four copies, two rows in flight) took 622 us per step of 1024 walkers x
+// 4 x 40-256x4-1; the ring takes 263 us.
 // tanh(z_l) of every layer is kept in a global scratch [M][tile][L][32][H]
 // (L2-resident at the sizes used) for the backward pass:
 //   g_L = w_out,  delta_l = g_l * (1 - tanh^2 z_l),
@@ -21,26 +25,77 @@ constexpr int TW = 32;    // walkers per CTA
 constexpr int ROW = 36;   // shared row stride in floats
 constexpr int NT = 128;   // threads per CTA
 
+constexpr int KC = 8;     // weight rows per ring stage
+constexpr int NSW = 4;    // ring stages
+constexpr int WCOLS = 256;
+
+__device__ __forceinline__ void cpa4(float* dst, const float* src, int bytes) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cpa16(float* dst, const float* src, int bytes) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // acc[i][kk] += sum_k in[k][8 warp + i] * Wg[k * ldw + nb + lane + 32 kk]
+// The CTA's weight rows stream through a ring of NSW stages of KC rows x 256
+// columns in shared memory (ws), so the four warps share one copy; every
+// accumulator still sums its K terms in increasing order.
 __device__ __forceinline__ void tile_gemm(const float* __restrict__ in, int K, const float* __restrict__ Wg, int ldw,
-                                          int N, int nb, int warp, int lane, float (&acc)[8][8]) {
-    bool ok[8];
+                                          int N, int nb, int warp, int lane, float (&acc)[8][8], float* ws) {
+    const int nst = (K + KC - 1) / KC;
+    const int ncol = N - nb < WCOLS ? N - nb : WCOLS;
+    const bool vec = (ldw & 3) == 0 && (nb & 3) == 0 && (reinterpret_cast<uintptr_t>(Wg) & 15) == 0;
+    auto issue = [&](int t) {
+        if (t < nst) {
+            float* dst = ws + (t % NSW) * KC * WCOLS;
+            const int k0 = t * KC;
+            if (vec) {
+                for (int q = threadIdx.x; q < KC * WCOLS / 4; q += NT) {
+                    const int r = q / (WCOLS / 4), c4 = 4 * (q % (WCOLS / 4)), k = k0 + r;
+                    int valid = k < K ? ncol - c4 : 0;
+                    valid = valid < 0 ? 0 : (valid > 4 ? 4 : valid);
+                    cpa16(dst + r * WCOLS + c4, valid ? Wg + (size_t)k * ldw + nb + c4 : Wg, 4 * valid);
+                }
+            } else {
+                for (int q = threadIdx.x; q < KC * WCOLS; q += NT) {
+                    const int r = q / WCOLS, c = q % WCOLS, k = k0 + r;
+                    const bool ok = k < K && c < ncol;
+                    cpa4(dst + r * WCOLS + c, ok ? Wg + (size_t)k * ldw + nb + c : Wg, ok ? 4 : 0);
+                }
+            }
+        }
+        cpa_commit();
+    };
 #pragma unroll
-    for (int kk = 0; kk < 8; ++kk) ok[kk] = nb + lane + 32 * kk < N;
-    const float* wp = Wg + nb + lane;
-#pragma unroll 2
-    for (int k = 0; k < K; ++k) {
-        const float4 a0 = *reinterpret_cast<const float4*>(in + k * ROW + 8 * warp);
-        const float4 a1 = *reinterpret_cast<const float4*>(in + k * ROW + 8 * warp + 4);
-        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        float wv[8];
+    for (int t = 0; t < NSW - 1; ++t) issue(t);
+    for (int t = 0; t < nst; ++t) {
+        cpa_wait<NSW - 2>();
+        __syncthreads();
+        issue(t + NSW - 1);
+        const float* wsr = ws + (t % NSW) * KC * WCOLS + lane;
+        const int kn = K - t * KC < KC ? K - t * KC : KC;
+#pragma unroll 4
+        for (int r = 0; r < kn; ++r) {
+            const int k = t * KC + r;
+            const float4 a0 = *reinterpret_cast<const float4*>(in + k * ROW + 8 * warp);
+            const float4 a1 = *reinterpret_cast<const float4*>(in + k * ROW + 8 * warp + 4);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            float wv[8];
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) wv[kk] = ok[kk] ? __ldg(wp + (size_t)k * ldw + 32 * kk) : 0.0f;
+            for (int kk = 0; kk < 8; ++kk) wv[kk] = wsr[r * WCOLS + 32 * kk];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) acc[i][kk] = fmaf(a[i], wv[kk], acc[i][kk]);
+                for (int kk = 0; kk < 8; ++kk) acc[i][kk] = fmaf(a[i], wv[kk], acc[i][kk]);
+        }
     }
+    cpa_wait<0>();
+    __syncthreads();   // the ring is refilled by the next call
 }
 
 __global__ void __launch_bounds__(NT) k_mlp_fp32(EnsDev E, StateDev st, int W, int C) {
@@ -50,6 +105,7 @@ __global__ void __launch_bounds__(NT) k_mlp_fp32(EnsDev E, StateDev st, int W, i
     float* bufA = sm;
     float* bufB = bufA + Kmax * ROW;
     float* ubuf = bufB + Kmax * ROW;
+    float* ws = ubuf + D * ROW;   // weight ring [NSW][KC][256]
     const int m = blockIdx.y, tile = blockIdx.x, ntiles = gridDim.x;
     const int w0 = tile * TW;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -76,7 +132,7 @@ __global__ void __launch_bounds__(NT) k_mlp_fp32(EnsDev E, StateDev st, int W, i
             for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int kk = 0; kk < 8; ++kk) acc[i][kk] = 0.0f;
-            tile_gemm(in, K, Wt, H, H, nb, warp, lane, acc);
+            tile_gemm(in, K, Wt, H, H, nb, warp, lane, acc, ws);
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk) {
                 const int n = nb + lane + 32 * kk;
@@ -150,7 +206,7 @@ __global__ void __launch_bounds__(NT) k_mlp_fp32(EnsDev E, StateDev st, int W, i
 #pragma unroll
                 for (int i = 0; i < 8; ++i) accs[i][kk] = (res && n < Nout) ? G[n * ROW + 8 * warp + i] : 0.0f;
             }
-            tile_gemm(Dl, K, Wl, Nout, Nout, nb, warp, lane, accs);
+            tile_gemm(Dl, K, Wl, Nout, Nout, nb, warp, lane, accs, ws);
             __syncthreads();   // every thread has read G for its initial values
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk) {
@@ -187,10 +243,11 @@ size_t rid_mlp_fp32_scratch_floats(int W, int M, int L, int H) {
 
 void rid_launch_mlp_fp32(const EnsDev& E, StateDev st, int W, int C, cudaStream_t s) {
     const int Kmax = E.H > E.D ? E.H : E.D;
-    const size_t sm = sizeof(float) * ((size_t)2 * Kmax * ROW + (size_t)E.D * ROW);
+    const size_t sm = sizeof(float) * ((size_t)2 * Kmax * ROW + (size_t)E.D * ROW + (size_t)NSW * KC * WCOLS);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        // activations 2 x 512 x 36 + inputs 256 x 36 + ring 4 x 8 x 256 floats = 212 KB at the limits
+        cudaFuncSetAttribute(k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr_set = true;
     }
     dim3 grid((W + TW - 1) / TW, E.M);
