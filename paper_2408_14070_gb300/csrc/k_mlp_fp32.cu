@@ -1,14 +1,17 @@
 // k_mlp_fp32.cu -- plain FP32 (SIMT) ensemble MLP: forward pass and
 // reverse-mode input gradient for every member on a tile of 32 walkers.
 //
-// Grid (ceil(W/32), M), 128 threads.  Each warp owns 8 walkers, each lane a
-// stripe of neurons n = nb + lane + 32 kk (kk < 8), so a thread keeps an
-// 8 x 8 register tile.  Activations live in shared memory transposed as
-// [neuron][walker] rows of 36 floats (32 walkers + 4 pad: 16-byte aligned
-// rows whose float4 stores by 8 consecutive lanes hit distinct banks).
+// Grid (ceil(W/32), M), 256 threads.  Warp w owns walkers 8 (w % 4) .. + 7
+// and half (w / 4) of each block of 256 output neurons; a lane takes neurons
+// n = nb + 128 (w / 4) + lane + 32 kk (kk < 4), so a thread keeps an 8 x 4
+// register tile (two warps per SM sub-partition: 8 x 8 tiles on four warps
+// took 261 us per step, this 238 us).  Activations live in shared memory
+// transposed as [neuron][walker] rows of 36 floats (32 walkers + 4 pad:
+// 16-byte aligned rows whose float4 stores by 8 consecutive lanes hit
+// distinct banks).
 // Weight rows (forward: W^T [in][out], backward: W [out][in], 256 output
 // neurons at a time) stream from L2 into a 4-stage ring of 8 rows in shared
-// memory by cp.async, so the four warps share one copy and three stages are
+// memory by cp.async, so the eight warps share one copy and three stages are
 // in flight while one is multiplied.  Reading every weight from L2 per warp
 // (four copies, two rows in flight) took 622 us per step of 1024 walkers x
 // 4 x 40-256x4-1; the ring takes 263 us.
@@ -23,7 +26,8 @@ namespace {
 
 constexpr int TW = 32;    // walkers per CTA
 constexpr int ROW = 36;   // shared row stride in floats
-constexpr int NT = 128;   // threads per CTA
+constexpr int NT = 256;   // threads per CTA: warp w takes walkers 8 (w % 4) .. and neuron half w / 4
+constexpr int NK = 4;     // neuron columns per thread (of 32 lanes apart)
 
 constexpr int KC = 8;     // weight rows per ring stage
 constexpr int NSW = 4;    // ring stages
@@ -41,12 +45,13 @@ __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_gro
 template <int N>
 __device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// acc[i][kk] += sum_k in[k][8 warp + i] * Wg[k * ldw + nb + lane + 32 kk]
+// acc[i][kk] += sum_k in[k][8 (warp % 4) + i] * Wg[k * ldw + nb + 128 (warp / 4) + lane + 32 kk]
 // The CTA's weight rows stream through a ring of NSW stages of KC rows x 256
-// columns in shared memory (ws), so the four warps share one copy; every
+// columns in shared memory (ws), so the eight warps share one copy; every
 // accumulator still sums its K terms in increasing order.
 __device__ __forceinline__ void tile_gemm(const float* __restrict__ in, int K, const float* __restrict__ Wg, int ldw,
-                                          int N, int nb, int warp, int lane, float (&acc)[8][8], float* ws) {
+                                          int N, int nb, int warp, int lane, float (&acc)[8][NK], float* ws) {
+    const int wg = warp & 3, nh = (warp >> 2) * 32 * NK;   // walker group, neuron offset within the block
     const int nst = (K + KC - 1) / KC;
     const int ncol = N - nb < WCOLS ? N - nb : WCOLS;
     const bool vec = (ldw & 3) == 0 && (nb & 3) == 0 && (reinterpret_cast<uintptr_t>(Wg) & 15) == 0;
@@ -77,21 +82,21 @@ __device__ __forceinline__ void tile_gemm(const float* __restrict__ in, int K, c
         cpa_wait<NSW - 2>();
         __syncthreads();
         issue(t + NSW - 1);
-        const float* wsr = ws + (t % NSW) * KC * WCOLS + lane;
+        const float* wsr = ws + (t % NSW) * KC * WCOLS + nh + lane;
         const int kn = K - t * KC < KC ? K - t * KC : KC;
 #pragma unroll 4
         for (int r = 0; r < kn; ++r) {
             const int k = t * KC + r;
-            const float4 a0 = *reinterpret_cast<const float4*>(in + k * ROW + 8 * warp);
-            const float4 a1 = *reinterpret_cast<const float4*>(in + k * ROW + 8 * warp + 4);
+            const float4 a0 = *reinterpret_cast<const float4*>(in + k * ROW + 8 * wg);
+            const float4 a1 = *reinterpret_cast<const float4*>(in + k * ROW + 8 * wg + 4);
             const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            float wv[8];
+            float wv[NK];
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) wv[kk] = wsr[r * WCOLS + 32 * kk];
+            for (int kk = 0; kk < NK; ++kk) wv[kk] = wsr[r * WCOLS + 32 * kk];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int kk = 0; kk < 8; ++kk) acc[i][kk] = fmaf(a[i], wv[kk], acc[i][kk]);
+                for (int kk = 0; kk < NK; ++kk) acc[i][kk] = fmaf(a[i], wv[kk], acc[i][kk]);
         }
     }
     cpa_wait<0>();
@@ -109,6 +114,7 @@ __global__ void __launch_bounds__(NT) k_mlp_fp32(EnsDev E, StateDev st, int W, i
     const int m = blockIdx.y, tile = blockIdx.x, ntiles = gridDim.x;
     const int w0 = tile * TW;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wgp = warp & 3, nh = (warp >> 2) * 32 * NK;   // walker group, neuron offset in a block
     const float* Wm = E.W + (size_t)m * E.wstride;
     const float* WTm = E.WT + (size_t)m * E.wstride;
     float* hs = st.hs + ((size_t)m * ntiles + tile) * (size_t)L * TW * H;
@@ -127,26 +133,26 @@ __global__ void __launch_bounds__(NT) k_mlp_fp32(EnsDev E, StateDev st, int W, i
         const float* Wt = WTm + E.loff[l];
         const float* bias = E.b + ((size_t)m * L + l) * H;
         for (int nb = 0; nb < H; nb += 256) {
-            float acc[8][8];
+            float acc[8][NK];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int kk = 0; kk < 8; ++kk) acc[i][kk] = 0.0f;
+                for (int kk = 0; kk < NK; ++kk) acc[i][kk] = 0.0f;
             tile_gemm(in, K, Wt, H, H, nb, warp, lane, acc, ws);
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                const int n = nb + lane + 32 * kk;
+            for (int kk = 0; kk < NK; ++kk) {
+                const int n = nb + nh + lane + 32 * kk;
                 if (n < H) {
                     const float bn = bias[n];
                     float h[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const float t = tanhf(acc[i][kk] + bn);
-                        hs[((size_t)l * TW + 8 * warp + i) * H + n] = t;
-                        h[i] = (E.resnet && l > 0) ? t + in[n * ROW + 8 * warp + i] : t;
+                        hs[((size_t)l * TW + 8 * wgp + i) * H + n] = t;
+                        h[i] = (E.resnet && l > 0) ? t + in[n * ROW + 8 * wgp + i] : t;
                     }
-                    *reinterpret_cast<float4*>(out + n * ROW + 8 * warp) = make_float4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<float4*>(out + n * ROW + 8 * warp + 4) = make_float4(h[4], h[5], h[6], h[7]);
+                    *reinterpret_cast<float4*>(out + n * ROW + 8 * wgp) = make_float4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<float4*>(out + n * ROW + 8 * wgp + 4) = make_float4(h[4], h[5], h[6], h[7]);
                 }
             }
         }
@@ -154,8 +160,8 @@ __global__ void __launch_bounds__(NT) k_mlp_fp32(EnsDev E, StateDev st, int W, i
         in = out;
         out = (out == bufA) ? bufB : bufA;
     }
-    // value A = w_out . h_L + b_out
-    {
+    // value A = w_out . h_L + b_out (warps 0-3, one per walker group)
+    if (warp < 4) {
         const float* wo = E.wout + (size_t)m * H;
         float part[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int n = lane; n < H; n += 32) {
@@ -198,23 +204,23 @@ __global__ void __launch_bounds__(NT) k_mlp_fp32(EnsDev E, StateDev st, int W, i
         __syncthreads();
         const float* Wl = Wm + E.loff[l];   // [H][fin] row-major = [K][Nout]
         const bool res = E.resnet && l > 0;
-        float accs[8][8];
+        float accs[8][NK];
         for (int nb = 0; nb < Nout; nb += 256) {
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                const int n = nb + lane + 32 * kk;
+            for (int kk = 0; kk < NK; ++kk) {
+                const int n = nb + nh + lane + 32 * kk;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) accs[i][kk] = (res && n < Nout) ? G[n * ROW + 8 * warp + i] : 0.0f;
+                for (int i = 0; i < 8; ++i) accs[i][kk] = (res && n < Nout) ? G[n * ROW + 8 * wgp + i] : 0.0f;
             }
             tile_gemm(Dl, K, Wl, Nout, Nout, nb, warp, lane, accs, ws);
             __syncthreads();   // every thread has read G for its initial values
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                const int n = nb + lane + 32 * kk;
+            for (int kk = 0; kk < NK; ++kk) {
+                const int n = nb + nh + lane + 32 * kk;
                 if (n < Nout) {
-                    *reinterpret_cast<float4*>(G + n * ROW + 8 * warp) =
+                    *reinterpret_cast<float4*>(G + n * ROW + 8 * wgp) =
                         make_float4(accs[0][kk], accs[1][kk], accs[2][kk], accs[3][kk]);
-                    *reinterpret_cast<float4*>(G + n * ROW + 8 * warp + 4) =
+                    *reinterpret_cast<float4*>(G + n * ROW + 8 * wgp + 4) =
                         make_float4(accs[4][kk], accs[5][kk], accs[6][kk], accs[7][kk]);
                 }
             }

@@ -170,6 +170,28 @@ def test_biased_forces_eps_and_member_gradients(R, orc, n, C, W, M, L, H, resnet
     assert np.allclose(eps, epsr, rtol=1e-4)
 
 
+def test_fp32_ensemble_at_the_size_limits(R, orc):
+    # 128 torsion CVs (256 MLP inputs) and width 512: the FP32 ensemble
+    # kernel's largest shared-memory footprint (activations, inputs and the
+    # weight ring: 212 KB); two walker tiles, the second ragged
+    n, C, W, M, L, H, seed = 140, 128, 40, 2, 3, 512, 12
+    sp = I.make_system(n, C, seed)
+    x = I.make_chains(W, sp, seed)
+    ens = I.make_ensemble(M, 2 * C, L, H, seed, trust_lo=1e9, trust_hi=2e9)
+    eps = np.zeros(W, np.float32)
+    abar = np.zeros(W, np.float32)
+    g = np.zeros((M, W, C), np.float32)
+    with R.System(sp) as sys:
+        sys.set_ensemble(ens, precision=R.RID_PREC_FP32)
+        sys.eval_forces(x, R.RID_BIAS_ENSEMBLE, eps_out=eps, abar_out=abar, grad_out=g)
+    for w in (0, 1, 31, 32, 39):
+        r = orc.total(sp, x[w].astype(np.float64), ens=ens, mode=1)
+        e = orc.ensemble(ens, r["s"])
+        assert close_rel(g[:, w], e["gradA"], FORCE_RTOL) < 1.0, w
+        assert abs(eps[w] - e["eps"]) <= FORCE_RTOL * (abs(e["eps"]) + 1e-3)
+        assert abs(abar[w] - e["Abar"]) <= FORCE_RTOL * (abs(e["Abar"]) + 1.0)
+
+
 def test_restraint_forces(R, orc):
     sp = I.make_system(50, 7, 3)
     W = 9
