@@ -228,6 +228,7 @@ int rid_mc_path_check(int NP, int Cp, int C, const int32_t* cv, const float* nod
 extern "C" RID_API int rid_mcmc(const rid_mcmc_desc* d, const float* s0, float* s_out, uint64_t* hist1_out,
                                 uint64_t* hist2_out, double* pmf1_out, double* pmf2_out, uint64_t* histp_out,
                                 double* pmfp_out, int64_t* n_accepted, int32_t mem, void* stream) {
+    NvtxScope nvtx_("rid_mcmc");
     if (!d || !s0 || !d->weights) return rid_fail(RID_ERR_ARG, "mcmc: NULL argument");
     if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return rid_fail(RID_ERR_ARG, "mcmc: bad mem");
     const int M = d->n_models, C = d->n_cv, L = d->n_layers, H = d->width, W = d->n_walkers, bins = d->bins;

@@ -212,6 +212,7 @@ float* g_scratch_ptr[RID_NOALLOC_MAX_DEVICES] = {nullptr};
 extern "C" int rid_ensemble_grad_noalloc(int32_t n_points, int32_t n_cv, const float* s, int32_t n_models,
                                          int32_t n_layers, int32_t width, int32_t resnet, const float* weights,
                                          float* grad_out, float* value_out, void* stream) {
+    NvtxScope nvtx_("rid_ensemble_grad_noalloc");
     const int W = n_points, C = n_cv, M = n_models, L = n_layers, H = width, D = 2 * n_cv;
     if (!s || !weights || !grad_out) return rid_fail(RID_ERR_ARG, "rid_ensemble_grad_noalloc: NULL array argument");
     if (W < 1 || C < 1 || C > RID_MAX_CV || M < 1 || M > RID_MAX_MODELS || L < 1 || L > RID_MAX_LAYERS || H < 32 ||

@@ -168,6 +168,7 @@ struct SelBuf {
 extern "C" RID_API int rid_select(const rid_select_desc* d, int32_t n, const float* cv, const float* eps,
                                   int32_t* selected, int32_t* n_selected, int32_t* n_clusters, double* threshold_out,
                                   int32_t mem, void* stream) {
+    NvtxScope nvtx_("rid_select");
     if (!d || !cv || !eps) return rid_fail(RID_ERR_ARG, "select: NULL argument");
     if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return rid_fail(RID_ERR_ARG, "select: bad mem");
     const int C = d->n_cv;

@@ -547,6 +547,7 @@ RID_API int rid_trainer_set_data(rid_trainer* tr, int32_t n, const float* s, con
 
 RID_API int rid_trainer_grad(rid_trainer* tr, const int32_t* idx, float* loss_out, float* grad_out, int32_t mem,
                              void* stream) {
+    NvtxScope nvtx_("rid_trainer_grad");
     if (!tr || !idx) return rid_fail(RID_ERR_ARG, "trainer: NULL argument");
     if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return rid_fail(RID_ERR_ARG, "trainer: bad mem");
     if (tr->n_data < 1) return rid_fail(RID_ERR_STATE, "trainer: no data set");
@@ -566,6 +567,7 @@ RID_API int rid_trainer_grad(rid_trainer* tr, const int32_t* idx, float* loss_ou
 
 RID_API int rid_trainer_run(rid_trainer* tr, int32_t n_steps, const int32_t* idx, float* loss_out, int32_t mem,
                             void* stream) {
+    NvtxScope nvtx_("rid_trainer_run");
     if (!tr || !idx || n_steps < 0) return rid_fail(RID_ERR_ARG, "trainer: bad run arguments");
     if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return rid_fail(RID_ERR_ARG, "trainer: bad mem");
     if (tr->n_data < 1) return rid_fail(RID_ERR_STATE, "trainer: no data set");

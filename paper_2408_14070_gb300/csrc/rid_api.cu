@@ -961,6 +961,7 @@ extern "C" int rid_walkers_load(rid_system* sys, int32_t W, const float* x0, con
 
 extern "C" int rid_walkers_advance(rid_system* sys, int64_t n_steps, float* cv_out, float* eps_out,
                                    double* energy_out, int32_t mem, void* stream) {
+    NvtxScope nvtx_("rid_walkers_advance");
     if (!sys) return fail(RID_ERR_ARG, "NULL system");
     return do_advance(sys, n_steps, cv_out, eps_out, energy_out, mem, (cudaStream_t)stream);
 }
@@ -1008,6 +1009,7 @@ extern "C" int64_t rid_launch_count(rid_system* sys) { return sys ? sys->launche
 extern "C" int rid_explore(rid_system* sys, int32_t W, const float* x0, const float* v0, uint64_t step0,
                            int64_t n_steps, float* cv_out, float* eps_out, double* energy_out, float* x_out,
                            float* v_out, int32_t mem, void* stream) {
+    NvtxScope nvtx_("rid_explore");
     if (!sys || !x0) return fail(RID_ERR_ARG, "NULL argument");
     if (n_steps < 0) return fail(RID_ERR_ARG, "n_steps < 0");
     if (step0 + (uint64_t)n_steps > (1ull << 32)) return fail(RID_ERR_ARG, "step0 + n_steps exceeds 2^32");
@@ -1021,6 +1023,7 @@ extern "C" int rid_label(rid_system* sys, int32_t R, const float* x0, const floa
                          const double* kappa, uint64_t step0, int64_t n_steps, int64_t n_equil, int32_t n_blocks,
                          double* mf_out, double* se_out, double* std_out, float* x_out, float* v_out, int32_t mem,
                          void* stream) {
+    NvtxScope nvtx_("rid_label");
     if (!sys || !x0 || !s0 || !kappa || !mf_out || !se_out || !std_out) return fail(RID_ERR_ARG, "NULL argument");
     if (R < 1) return fail(RID_ERR_ARG, "n_runs=%d must be >= 1", R);
     if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "mem must be RID_MEM_HOST or RID_MEM_DEVICE");
@@ -1097,6 +1100,7 @@ extern "C" int rid_mcmc_system(rid_system* sys, int32_t W, const float* s0, int6
                                int32_t proj_j, const rid_mcmc_path* path, float* s_out, uint64_t* hist1_out,
                                uint64_t* hist2_out, double* pmf1_out, double* pmf2_out, uint64_t* histp_out,
                                double* pmfp_out, int64_t* n_accepted, int32_t mem, void* stream) {
+    NvtxScope nvtx_("rid_mcmc_system");
     if (!sys || !s0) return fail(RID_ERR_ARG, "NULL argument");
     if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "mem must be RID_MEM_HOST or RID_MEM_DEVICE");
     if (!sys->has_ens) return fail(RID_ERR_STATE, "no ensemble set");
@@ -1189,6 +1193,7 @@ extern "C" int rid_label_constrained(rid_system* sys, int32_t R, const float* x0
                                      const int32_t* pairs, const double* d0, uint64_t step0, int64_t n_steps,
                                      int64_t n_equil, int32_t n_blocks, double* mf_out, double* se_out,
                                      double* std_out, float* x_out, float* v_out, int32_t mem, void* stream) {
+    NvtxScope nvtx_("rid_label_constrained");
     if (!sys || !x0 || !pairs || !d0 || !mf_out || !se_out || !std_out) return fail(RID_ERR_ARG, "NULL argument");
     if (R < 1 || C < 1 || C > RID_MAX_CV) return fail(RID_ERR_ARG, "n_runs >= 1 and 1 <= n_cv <= %d required", RID_MAX_CV);
     if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "mem must be RID_MEM_HOST or RID_MEM_DEVICE");
@@ -1282,6 +1287,7 @@ extern "C" int rid_label_constrained(rid_system* sys, int32_t R, const float* x0
 extern "C" int rid_eval_forces(rid_system* sys, int32_t W, const float* x, int32_t bias, const double* s0,
                                const double* kappa, float* f_out, float* s_out, float* eps_out, float* abar_out,
                                float* grad_out, int32_t mem, void* stream) {
+    NvtxScope nvtx_("rid_eval_forces");
     if (!sys || !x) return fail(RID_ERR_ARG, "NULL argument");
     if (W < 1) return fail(RID_ERR_ARG, "n_walkers must be >= 1");
     if (mem != RID_MEM_HOST && mem != RID_MEM_DEVICE) return fail(RID_ERR_ARG, "bad mem");

@@ -3,9 +3,20 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "rid.h"
+
+// A named NVTX range over the lifetime of the object: each public call and
+// each server tick shows as one range in a profiler that records NVTX (a
+// no-op when none is attached).
+struct NvtxScope {
+    explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope&) = delete;
+    NvtxScope& operator=(const NvtxScope&) = delete;
+};
 
 #define RID_MAX_LAYERS 8
 #define RID_MAX_MODELS 16

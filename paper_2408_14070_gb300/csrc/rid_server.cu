@@ -491,6 +491,7 @@ void release_job_memory(rid_server* srv, SJob* j) {
 
 // ---- exploration jobs
 int explore_launch_chunk(rid_server* srv, SJob* j) {
+    NvtxScope nvtx_("explore chunk");
     ESlot& e = srv->es[j->slot];
     rid_system* sys = j->rq.sys;
     j->cur = std::min(j->chunk, j->rq.n_steps - j->done);
@@ -579,6 +580,7 @@ bool explore_progress(rid_server* srv, SJob* j) {
 
 // ---- label jobs: one tick of the persistent kernel over every admitted job
 int label_tick_launch(rid_server* srv) {
+    NvtxScope nvtx_("label tick");
     std::vector<SJob*> act;
     for (SJob* j : srv->labels) act.push_back(j);
     if (act.empty()) return RID_OK;
@@ -950,6 +952,7 @@ extern "C" int rid_server_load(rid_server* srv, int32_t* queued, int32_t* runnin
 
 extern "C" int rid_label_batch(rid_server* srv, const rid_label_job* jobs, int32_t n_jobs, int32_t threads,
                                int32_t* status_out, int32_t mem, void* stream) {
+    NvtxScope nvtx_("rid_label_batch");
     if (!srv || (!jobs && n_jobs > 0)) return rid_fail(RID_ERR_ARG, "NULL argument");
     if (n_jobs < 0) return rid_fail(RID_ERR_ARG, "n_jobs=%d must be >= 0", n_jobs);
     if (threads != 0 && threads != 128 && threads != 256 && threads != 512)
