@@ -7,6 +7,7 @@ import re
 import shutil
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -97,3 +98,47 @@ def test_ctypes_structures_match_the_header(tmp_path):
     subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got == want
+
+
+def test_descriptor_checks_answer_before_device_work(L):
+    # the argument checks of the training, MCMC, selection and constrained
+    # entry points run before any device call, so they answer on a machine
+    # without a GPU
+    from paper_2408_14070_gb300 import rid
+    w = np.zeros(1024, np.float32)
+    P = C.POINTER(C.c_float)
+    h = C.c_void_p()
+    good = dict(n_models=1, n_cv=1, n_layers=1, width=8, resnet=0, batch_size=4, init_lr=1e-3, decay_rate=0.9,
+                decay_steps=10, beta1=0.9, beta2=0.999, adam_eps=1e-8, dropout_rate=0.0, dropout_seed=0)
+    for bad in ({"n_models": 0}, {"width": 0}, {"batch_size": 0}, {"init_lr": 0.0}, {"beta1": 1.0},
+                {"dropout_rate": 1.0}, {"dropout_rate": -0.5}):
+        d = rid.TrainDesc(**{**good, **bad})
+        assert L.rid_trainer_create(C.byref(d), w.ctypes.data_as(P), C.byref(h)) == rid.RID_ERR_ARG, bad
+    s0 = np.zeros((4, 2), np.float32)
+    cv = np.array([0, 1], np.int32)
+    nodes = np.zeros((3, 2), np.float32)
+    mgood = dict(n_models=1, n_cv=2, n_layers=1, width=8, resnet=0, weights=w.ctypes.data, n_walkers=4, n_steps=5,
+                 n_burn=0, kT=1.0, step_size=0.3, seed=1, bins=10, proj_i=0, proj_j=1, path_n_nodes=0, path_n_cv=0,
+                 path_cv=None, path_nodes=None, path_lambda=1.0, path_z_lo=0.0, path_z_hi=1.0)
+    path = dict(path_n_nodes=3, path_n_cv=2, path_cv=cv.ctypes.data, path_nodes=nodes.ctypes.data)
+    for bad in ({"bins": 0}, {"kT": 0.0}, {"proj_j": 2}, {"n_walkers": 0}, {**path, "path_n_nodes": 1},
+                {**path, "path_lambda": 0.0}, {**path, "path_z_hi": 0.0}, {**path, "path_n_cv": 3}):
+        d = rid.McmcDesc(**{**mgood, **bad})
+        assert L.rid_mcmc(C.byref(d), s0.ctypes.data, *([None] * 8), 0, None) == rid.RID_ERR_ARG, bad
+    bad_cv = np.array([0, 5], np.int32)
+    d = rid.McmcDesc(**{**mgood, **path, "path_cv": bad_cv.ctypes.data})
+    assert L.rid_mcmc(C.byref(d), s0.ctypes.data, *([None] * 8), 0, None) == rid.RID_ERR_ARG
+    assert b"path CV index" in L.rid_last_error()
+    eps = np.zeros(4, np.float32)
+    sel = np.zeros(4, np.int32)
+    sgood = dict(n_cv=2, weights=None, periodic=None, trust_lo=0.0, trust_hi=1.0, cluster_threshold=1.0,
+                 numb_cluster_lower=1, numb_cluster_upper=5, adapt=0, max_selection=4)
+    for bad in ({"n_cv": 0}, {"cluster_threshold": 0.0}, {"adapt": 1, "numb_cluster_upper": 0}):
+        d = rid.SelectDesc(**{**sgood, **bad})
+        n1, n2, t = C.c_int32(), C.c_int32(), C.c_double()
+        assert L.rid_select(C.byref(d), 4, s0.ctypes.data, eps.ctypes.data, sel.ctypes.data, C.byref(n1),
+                            C.byref(n2), C.byref(t), 0, None) == rid.RID_ERR_ARG, bad
+    assert L.rid_mcmc_system(None, 4, s0.ctypes.data, 5, 0, 1.0, 0.3, 1, 10, 0, 1, None, *([None] * 7), None, 0,
+                             None) == rid.RID_ERR_ARG
+    assert L.rid_label_constrained(None, 1, None, None, 1, None, None, 0, 10, 0, 2, None, None, None, None, None, 0,
+                                   None) == rid.RID_ERR_ARG
