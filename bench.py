@@ -390,8 +390,8 @@ def run_mcmc(rid, torch, steps, seed=13):
             "bf16_tensor_cores": {
                 "value": W * steps / (ms16 * 1e-3), "unit": "walker-steps/s", "ms_per_step": ms16 / steps,
                 "acceptance": acc16 / (W * steps),
-                "path": "rid_mcmc_system: the system's BF16 ensemble kernel (tcgen05), which also forms the "
-                        "input gradient that MCMC does not use",
+                "path": "rid_mcmc_system: the system's BF16 ensemble kernel (tcgen05) in its forward-only "
+                        "mode (the L forward GEMMs and the member values; no input gradient)",
                 "roofline": {"bound": "tensor", "achieved": ach16, "peak": bf16, "unit": "TFLOP/s",
                              "frac": ach16 / bf16, "work": "forward flops only (what the Metropolis test needs)",
                              "peak_source": "measured bf16_tflops (burst)" if _peaks().get("bf16_tflops")

@@ -238,7 +238,7 @@ __global__ void __maxnreg__(96)
     __shared__ Smem S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x, m = blockIdx.y;
-    const int L = P.L, G = 2 * L;
+    const int L = P.L, G = P.ngemm;   // 2L, or L for the member values alone
     unsigned char* Abuf = dsm;                                     // [Kpmax/64][128 rows][128 B]
     unsigned char* stages = dsm + (size_t)P.Kpmax * 256u;          // 128 rows x 2 B per column
     const uint32_t stage_bytes = P.stage_bytes;
@@ -412,8 +412,8 @@ __global__ void __maxnreg__(96)
             // span two of these 64-column chunks, and its K padding is zeroed too
             const int ebn = (F8 && g + 1 < G) ? P.geb[g + 1] : 2;
             const int nch = ebn == 1 ? 2 * ((N + 127) / 128) : (N + 63) / 64;
-            const float ws = F8 ? P.wscale[(size_t)m * G + g] : 1.0f;
-            const int l = fwd ? g : (G - 1 - g);       // layer of this GEMM
+            const float ws = F8 ? P.wscale[(size_t)m * 2 * L + g] : 1.0f;   // [M][2L]
+            const int l = fwd ? g : (2 * L - 1 - g);   // layer of this GEMM
             const int b = g % NACC;
             // saved tanh of layer l-1 for this warp's columns, loaded before the wait
             constexpr int PREF = 2;                    // chunks prefetched; later ones load in place
@@ -549,6 +549,7 @@ size_t rid_mlp_tc_smem_bytes(const TcArgs& P) {
 }
 
 cudaError_t rid_launch_mlp_tc(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, cudaStream_t s) {
+    if (P.ngemm != P.L && P.ngemm != 2 * P.L) return cudaErrorInvalidValue;
     const size_t smem = rid_mlp_tc_smem_bytes(P);
     const bool f8 = P.geb[0] == 1;
     static size_t attr[2] = {0, 0};

@@ -617,7 +617,7 @@ static int fetch_flags(rid_system* sys, int W, cudaStream_t st, bool* any) {
     return RID_OK;
 }
 
-static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_t st);
+static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_t st, bool values_only = false);
 
 // Side stream (lowest priority) and fork / join events, created on first use.
 static int ensure_side(rid_system* sys) {
@@ -696,7 +696,9 @@ static int tune_tc_stages(rid_system* sys, TcArgs P, cudaStream_t st) {
     return RID_OK;
 }
 
-static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_t st) {
+// values_only: the member values alone (the tensor-core kernel then runs the
+// L forward GEMMs and skips the input gradient; the FP32 kernel forms both).
+static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_t st, bool values_only) {
     EnsDev& E = sys->E;
     if (mode == 1 && sys->precision != RID_PREC_FP32) {
         const TcVariant& V = sys->tcv;
@@ -714,6 +716,7 @@ static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_
             P.geb[g] = V.geb[g];
         }
         P.wscale = V.wscale.as<float>();
+        P.ngemm = values_only ? E.L : 2 * E.L;
         cudaError_t le = cudaSuccess;
         if (V.tuned_W != W) TRY(tune_tc_stages(sys, P, st));
         P.stages = V.stages;
@@ -1159,12 +1162,12 @@ extern "C" int rid_mcmc_system(rid_system* sys, int32_t W, const float* s0, int6
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     const int M = sys->E.M, nav = M * sys->E.aslices;
     rid_launch_mc_features(ds, sd.u, nS, st);
-    TRY(launch_mlp(sys, W, 1, sd, st));
+    TRY(launch_mlp(sys, W, 1, sd, st, true));
     rid_launch_mc_accept_values(sd.Aval, nav, M, W, C, ds, dsp, dA, 0u, (float)kT, k0, k1, 1, 0, bins, proj_i, proj_j,
                                 h1, h2, na, pd, st);
     for (int64_t t = 0; t < n_steps; ++t) {
         rid_launch_mc_propose(ds, dsp, sd.u, W, C, (uint32_t)t, (float)step_size, k0, k1, st);
-        TRY(launch_mlp(sys, W, 1, sd, st));
+        TRY(launch_mlp(sys, W, 1, sd, st, true));
         rid_launch_mc_accept_values(sd.Aval, nav, M, W, C, ds, dsp, dA, (uint32_t)t, (float)kT, k0, k1, 0,
                                     t >= n_burn, bins, proj_i, proj_j, h1, h2, na, pd, st);
     }

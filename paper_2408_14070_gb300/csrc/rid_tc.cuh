@@ -34,6 +34,8 @@ struct TcArgs {
     int gN[2 * RID_MAX_LAYERS], gKp[2 * RID_MAX_LAYERS];   // N, and K padded to a 128-byte chunk
     int geb[2 * RID_MAX_LAYERS];                           // operand bytes per element: 2 BF16, 1 FP8 e4m3
     const float* wscale;     // [M][2L] weight scale of every GEMM (1 for BF16)
+    int ngemm;               // GEMMs to run: 2L (forward and input gradient) or L (forward only:
+                             // member values, gradA untouched)
 };
 
 size_t rid_mlp_tc_smem_bytes(const TcArgs& P);
