@@ -282,12 +282,11 @@ size_t rid_label_fused_smem(int N, int C, int threads) {
 
 template <int NT>
 static cudaError_t launch_nt(const FusedArgs& A, int grid, size_t smem, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
+    static unsigned long long attr = 0;
+    if (rid_first_on_device(attr)) {
         const cudaError_t e = cudaFuncSetAttribute(k_label_fused<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    220 * 1024);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     k_label_fused<NT><<<grid, NT, smem, s>>>(A);
     return cudaGetLastError();

@@ -250,11 +250,10 @@ size_t rid_mlp_fp32_scratch_floats(int W, int M, int L, int H) {
 void rid_launch_mlp_fp32(const EnsDev& E, StateDev st, int W, int C, cudaStream_t s) {
     const int Kmax = E.H > E.D ? E.H : E.D;
     const size_t sm = sizeof(float) * ((size_t)2 * Kmax * ROW + (size_t)E.D * ROW + (size_t)NSW * KC * WCOLS);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static unsigned long long attr_set = 0;
+    if (rid_first_on_device(attr_set)) {
         // activations 2 x 512 x 36 + inputs 256 x 36 + ring 4 x 8 x 256 floats = 212 KB at the limits
         cudaFuncSetAttribute(k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr_set = true;
     }
     dim3 grid((W + TW - 1) / TW, E.M);
     k_mlp_fp32<<<grid, NT, sm, s>>>(E, st, W, C);

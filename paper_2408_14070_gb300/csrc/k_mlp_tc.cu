@@ -552,12 +552,15 @@ cudaError_t rid_launch_mlp_tc(const TcArgs& P, const CUtensorMap& big, const CUt
     if (P.ngemm != P.L && P.ngemm != 2 * P.L) return cudaErrorInvalidValue;
     const size_t smem = rid_mlp_tc_smem_bytes(P);
     const bool f8 = P.geb[0] == 1;
-    static size_t attr[2] = {0, 0};
-    if (smem > attr[f8]) {
+    static size_t attr[2][64] = {};   // shared memory opted into, per format and device
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    size_t& have = attr[f8][dev & 63];
+    if (smem > have) {
         cudaError_t e = f8 ? cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                            : cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr[f8] = smem;
+        have = smem;
     }
     if (f8) k_mlp_tc<true><<<dim3(P.ntiles, P.M, 1), NTHREADS, smem, s>>>(P, big, small);
     else k_mlp_tc<false><<<dim3(P.ntiles, P.M, 1), NTHREADS, smem, s>>>(P, big, small);

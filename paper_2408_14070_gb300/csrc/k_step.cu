@@ -415,10 +415,9 @@ void rid_launch_mb(const SysDev& S, StateDev st, int W, uint32_t step0, cudaStre
     if (n > 0) k_mb<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S, st, W, step0);
 }
 void rid_launch_pair_mask(const SysDev& S, StateDev st, int W, uint32_t* mask, cudaStream_t s) {
-    static bool attr = false;   // positions of up to RID_MAX_BEADS beads exceed the default 48 KB
-    if (!attr) {
+    static unsigned long long attr = 0;   // positions of up to RID_MAX_BEADS beads exceed the default 48 KB
+    if (rid_first_on_device(attr)) {
         cudaFuncSetAttribute(k_pair_mask, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
     }
     k_pair_mask<<<W, chain_threads(S.N), sizeof(float4) * (size_t)S.N, s>>>(S, st, mask);
 }
@@ -436,13 +435,12 @@ void rid_launch_ff(const SysDev& S, StateDev st, int W, bool energy, cudaStream_
     const int th = chain_threads(S.N) < FF_THREADS ? chain_threads(S.N) : FF_THREADS;
     const size_t sm = (size_t)rid_ff_smem_bytes(S.N);
     const bool bsm = S.N <= RID_BONDED_SMEM_MAX;
-    static bool attr = false;
-    if (!attr) {
+    static unsigned long long attr = 0;
+    if (rid_first_on_device(attr)) {
         cudaFuncSetAttribute(k_ff<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(k_ff<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(k_ff<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(k_ff<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
     }
     if (bsm) {
         if (energy) k_ff<true, true><<<W, th, sm, s>>>(S, st);
@@ -457,12 +455,11 @@ template <int MODE, bool FIN, bool KICK, int INT>
 static void head_e(const HeadArgs& a, cudaStream_t s) {
     const int th = HEAD_THREADS;
     const size_t sm = sizeof(float4) * (size_t)a.S.N + (FIN ? (sizeof(float4) + sizeof(int2)) * 4 * (size_t)a.S.C : 0);
-    static bool attr = false;   // positions of up to RID_MAX_BEADS beads exceed the default 48 KB
-    if (!attr) {
+    static unsigned long long attr = 0;   // positions of up to RID_MAX_BEADS beads exceed the default 48 KB
+    if (rid_first_on_device(attr)) {
         const int mx = (int)(sizeof(float4) * RID_MAX_BEADS + (sizeof(float4) + sizeof(int2)) * 4 * RID_MAX_CV);
         cudaFuncSetAttribute(k_head<MODE, FIN, KICK, INT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         cudaFuncSetAttribute(k_head<MODE, FIN, KICK, INT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        attr = true;
     }
     if (a.energy)
         k_head<MODE, FIN, KICK, INT, true><<<a.W, th, sm, s>>>(a.S, a.st, a.E, a.lab, a.t_fin, a.slot, a.cv_out,

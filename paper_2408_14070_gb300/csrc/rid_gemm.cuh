@@ -300,10 +300,9 @@ __global__ void __launch_bounds__(TileCfg<TS>::threads) k_tr_gemm_batch(GemmBatc
 
 template <int EPI, int TS>
 void launch_gemm_ts(const GemmArgs& g, int M, cudaStream_t st, bool pdl) {
-    static bool attr = false;   // the ring exceeds the default 48 KB of shared memory
-    if (!attr) {
+    static unsigned long long attr = 0;   // the ring exceeds the default 48 KB of shared memory
+    if (rid_first_on_device(attr)) {
         cudaFuncSetAttribute(k_tr_gemm<EPI, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TileCfg<TS>::smem);
-        attr = true;
     }
     dim3 grid((g.cols + TS - 1) / TS, (g.rows + TS - 1) / TS, M);
     launch_k(k_tr_gemm<EPI, TS>, grid, dim3(TileCfg<TS>::threads), TileCfg<TS>::smem, st, pdl, g);
@@ -321,11 +320,10 @@ void launch_gemm(const GemmArgs& g, int M, cudaStream_t st, bool pdl = false) {
 // The GEMMs of b (each as launch_gemm would run it with 32-wide tiles) in one launch.
 template <int EPI>
 void launch_gemm_batch(const GemmBatch& b, cudaStream_t st, bool pdl = false) {
-    static bool attr = false;
-    if (!attr) {
+    static unsigned long long attr = 0;
+    if (rid_first_on_device(attr)) {
         cudaFuncSetAttribute(k_tr_gemm_batch<EPI, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TileCfg<32>::smem);
-        attr = true;
     }
     int cx = 1, cy = 1;
     for (int k = 0; k < b.n; ++k) {

@@ -165,6 +165,19 @@ __device__ __forceinline__ double rid_wrapd(double d) {
 }
 
 // --------------------------------------------------------------------------
+// cudaFuncSetAttribute acts on the current device only: a launcher that opts
+// a kernel into more shared memory asks this first, and it answers true once
+// per device (one bit of `done` per device ordinal).
+inline bool rid_first_on_device(unsigned long long& done) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return true;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done & bit) return false;
+    done |= bit;
+    return true;
+}
+
+// --------------------------------------------------------------------------
 // Host-side kernel launchers (defined in the .cu files).
 void rid_launch_pack(const float* src, float4* dst, long long n, cudaStream_t st);
 void rid_launch_unpack(const float4* src, float* dst, long long n, cudaStream_t st);
