@@ -435,3 +435,101 @@ def test_maxwell_boltzmann_start_and_resume_bitwise(orc):
     # resuming from an FP32 snapshot changes the state by rounding only
     assert np.abs(b["x"] - full["x"]).max() < 1e-4
     assert np.array_equal(full["cv"][:, :4], a["cv"])
+
+
+# --------------------------------------------------------------------------- non-unit physics
+# (m, kT) pairs: kT = 2.49 is R T at 300 K in kJ/mol (the configuration loader's
+# default); the second pair puts kT/m far from 1, so that kT/m used for
+# sqrt(kT/m), or m and kT swapped, also changes every moment below.
+PHYS = [(2.5, 2.49), (3.0, 0.6), (0.4, 2.49)]
+
+
+@pytest.mark.parametrize("m,kT", PHYS)
+def test_maxwell_boltzmann_start_has_variance_kT_over_m(orc, m, kT):
+    """Maxwell-Boltzmann start (reading: Philox stream 1 at step0) over 10^5
+    beads: each velocity component has mean 0 and variance kT/m within 5 sigma,
+    Gaussian tails (fourth moment 3 (kT/m)^2), and no correlation between
+    neighbouring beads, components or walkers."""
+    sp = I.make_system(200, 2, 31, mass=m, kT=kT)
+    x0 = I.make_chains(500, sp, 31, min_dist=1.0)
+    v = orc.explore(sp, x0, 0)["v"]                  # zero steps: the drawn start
+    var0 = kT / m
+    n = v.shape[0] * v.shape[1]
+    for k in range(3):
+        c = v[..., k].ravel()
+        assert abs(c.mean()) < 5 * math.sqrt(var0 / n)
+        assert abs(c.var() - var0) < 5 * var0 * math.sqrt(2.0 / n)
+        # Var(c^4) = (105 - 9) var0^4 for a Gaussian
+        assert abs(np.mean(c ** 4) - 3 * var0 ** 2) < 5 * math.sqrt(96.0 / n) * var0 ** 2
+    for a, b in [(v[:, :-1, :], v[:, 1:, :]), (v[..., 0], v[..., 1]), (v[:-1], v[1:])]:
+        a, b = a.ravel(), b.ravel()
+        assert abs(np.mean(a * b)) / var0 < 5 / math.sqrt(a.size)
+    # the start is not the O-step noise of step 0 (stream 0)
+    xi0 = orc.normals(np.array([[i, 0, 0, 0] for i in range(200)]), sp.seed)
+    assert not np.allclose(v[0], math.sqrt(var0) * xi0)
+
+
+@pytest.mark.parametrize("m,kT", PHYS)
+def test_baoab_harmonic_variance_at_non_unit_mass(orc, m, kT):
+    """BAOAB's configurational variance of a harmonic well is kT/a at any
+    stable dt, whatever the mass: a dropped 1/m in a kick, or kT/m in the
+    noise amplitude instead of its square root, moves it by a factor m or
+    kT/m."""
+    a = 3.0
+    dt = 0.5 * math.sqrt(m / a)            # omega dt = 0.5
+    r = orc.harmonic1d(a=a, c=0.2, kappa=0.0, s0=0.0, n_steps=1_000_000, n_equil=1000, dt=dt, m=m, kT=kT,
+                       gamma=0.5, seed=41)
+    assert r["mean"] == pytest.approx(0.2, abs=0.03 * math.sqrt(kT / a))
+    assert r["mean2"] - r["mean"] ** 2 == pytest.approx(kT / a, rel=0.03)
+
+
+@pytest.mark.parametrize("m,kT", PHYS)
+def test_restrained_mean_force_closed_form_at_non_unit_mass(orc, m, kT):
+    """The restrained 1-D mean force kappa a (s0 - c)/(a + kappa) holds for any
+    mass and temperature (the configurational distribution does not depend on
+    m); its spread, std = kappa sqrt(kT/(a + kappa)), does depend on kT."""
+    a, c, kap, s0 = 2.0, 0.3, 50.0, 1.0
+    r = orc.harmonic1d(a=a, c=c, kappa=kap, s0=s0, n_steps=1_000_000, n_equil=2000, m=m, kT=kT,
+                       dt=0.4 * math.sqrt(m / (a + kap)), gamma=0.5, seed=43)
+    want = kap * a * (s0 - c) / (a + kap)
+    assert abs(r["mf"] - want) < 3.5 * r["se"]
+    assert r["std"] == pytest.approx(kap * math.sqrt(kT / (a + kap)), rel=0.02)
+
+
+@pytest.mark.parametrize("m,kT", PHYS)
+def test_langevin_chain_equipartition_at_non_unit_physics(orc, m, kT):
+    """Kinetic temperature of a Langevin chain with m, kT, dt, gamma and the
+    LJ sigma, epsilon all off 1: <KE> = 3 N kT / 2 (BAOAB's kinetic error is
+    O(dt^2), far below the 4% bound here)."""
+    sp = I.make_system(22, 2, 3, output_freq=10, mass=m, kT=kT, dt=0.004, gamma=0.5, lj_sigma=1.1, lj_eps=0.7)
+    x0 = I.make_chains(8, sp, 3, min_dist=1.0)
+    r = orc.explore(sp, x0, 6000, energy=True)
+    ke = r["energy"][:, 150:, 2]                 # discard the first 1500 steps
+    T = ke.mean() * 2 / (3 * sp.n_beads)
+    assert T == pytest.approx(kT, rel=0.04)
+
+
+def test_lj_sigma_and_epsilon_scale_the_pair_energy(orc):
+    """Beads 0 and 3 of a 4-bead chain (bonded terms switched off) interact
+    through 4 eps ((sig/r)^12 - (sig/r)^6) - U(rc), with rc an absolute
+    cutoff: the minimum sits at r = 2^(1/6) sig with U = -eps - U(rc), the
+    force vanishes there, and past rc both are exactly zero."""
+    sp = I.make_system(4, 1, 5, lj_sigma=1.1, lj_eps=0.7, bond_k=0.0, angle_k=0.0)
+    sp.dihedral_k[:] = 0.0
+    rmin = 2 ** (1 / 6) * 1.1
+    x = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, rmin, 0]], np.float64)
+    U, f, terms = orc.ff(sp, x)
+    uc = 4 * 0.7 * ((1.1 / 2.5) ** 12 - (1.1 / 2.5) ** 6)
+    assert U == pytest.approx(-0.7 - uc, rel=1e-12)
+    assert np.abs(f).max() < 1e-9
+    # at r = 1.2 sig: U and the radial force from the closed form
+    r = 1.2 * 1.1
+    x[3] = [0, r, 0]
+    U, f, terms = orc.ff(sp, x)
+    sr6 = (1.1 / r) ** 6
+    assert U == pytest.approx(4 * 0.7 * (sr6 * sr6 - sr6) - uc, rel=1e-12)
+    assert f[3, 1] == pytest.approx(24 * 0.7 * (2 * sr6 * sr6 - sr6) / r, rel=1e-12)
+    assert f[0, 1] == pytest.approx(-f[3, 1], rel=1e-12)
+    x[3] = [0, 2.5001, 0]
+    U, f, terms = orc.ff(sp, x)
+    assert U == 0.0 and not f.any()
