@@ -109,9 +109,10 @@ typedef struct {
     int32_t n_models;             /* M, 1..16                                   */
     int32_t n_in;                 /* D, must equal 2 * n_cv                     */
     int32_t n_layers;             /* L, 1..8                                    */
-    int32_t width;                /* H, multiple of 32, 32..512                 */
-    int32_t resnet;               /* 0 / 1                                      */
-    int32_t precision;            /* RID_PREC_* (FP8 / BF16: resnet = 0 only)   */
+    int32_t width;                /* H, 1..512 (padded inside to a multiple of  */
+                                  /* 32 with zero units: the same function)     */
+    int32_t resnet;               /* 0 / 1, at every precision                  */
+    int32_t precision;            /* RID_PREC_*                                 */
     double trust_lo, trust_hi;    /* trust_lo < trust_hi                        */
     const float* weights;         /* host [M][P], copied by the call            */
 } rid_ensemble_desc;

@@ -227,7 +227,9 @@ struct Smem {
 // F8: the forward GEMMs take FP8 e4m3 operands (the input-gradient GEMMs
 // stay BF16); the BF16 instantiation has every operand format fixed at
 // compile time.
-template <bool F8>
+// RES: residual ensemble (h_l = h_{l-1} + tanh(z_l) for l >= 1), its own
+// instantiation so that the plain networks keep their register allocation.
+template <bool F8, bool RES>
 __global__ void __maxnreg__(96)
     k_mlp_tc(const __grid_constant__ TcArgs P, const __grid_constant__ CUtensorMap map_big,
              const __grid_constant__ CUtensorMap map_small) {
@@ -404,6 +406,9 @@ __global__ void __maxnreg__(96)
         }
         asm volatile("bar.sync 1, %0;" ::"r"(ET) : "memory");   // all epilogue warps, before any bounded wait
         __nv_bfloat16* tsave_tile = P.tsave + ((size_t)m * P.ntiles + tile) * (size_t)L * 128 * H;
+        // residual stream of a resnet ensemble: h_l (forward) and dA/dh_l (backward)
+        // in FP32, one [H/8][128][8] block per tile and member, overwritten in place
+        float* rsave_tile = RES ? P.rsave + ((size_t)m * P.ntiles + tile) * (size_t)128 * H : nullptr;
         float apart = 0.0f;
         for (int g = 0; g < G; ++g) {
             const int N = P.gN[g];
@@ -415,8 +420,15 @@ __global__ void __maxnreg__(96)
             const float ws = F8 ? P.wscale[(size_t)m * 2 * L + g] : 1.0f;   // [M][2L]
             const int l = fwd ? g : (2 * L - 1 - g);   // layer of this GEMM
             const int b = g % NACC;
+            // resnet: h_{l-1} is added to this layer's tanh (forward, l >= 1);
+            // dA/dh_l is added to the product W_l^T Delta_l (backward, l >= 1),
+            // read from the stream below l = L-1 and from w_out at l = L-1
+            const bool res_fwd = RES && fwd && l >= 1;
+            const bool res_bwd = RES && !fwd && l >= 1;
+            const bool res_ld = res_fwd || (res_bwd && l < L - 1);
+            const bool res_st = RES && (fwd ? l < L - 1 : l >= 2);
             // saved tanh of layer l-1 for this warp's columns, loaded before the wait
-            constexpr int PREF = 2;                    // chunks prefetched; later ones load in place
+            constexpr int PREF = RES ? 1 : 2;          // chunks prefetched; later ones load in place
             uint4 tall[PREF][2];
             if (!fwd && l > 0) {
 #pragma unroll
@@ -448,6 +460,16 @@ __global__ void __maxnreg__(96)
                             if (k < ng) tcur[k] = *reinterpret_cast<const uint4*>(tsave_tile + ts_off(l - 1, row, col0 + k * 8, H));
                     }
                 }
+                float4 rprev[2][2];
+                if (res_ld) {
+#pragma unroll
+                    for (int k = 0; k < 2; ++k)
+                        if (k < ng) {
+                            const float4* rp = reinterpret_cast<const float4*>(rsave_tile + ts_off(0, row, col0 + k * 8, H));
+                            rprev[k][0] = rp[0];
+                            rprev[k][1] = rp[1];
+                        }
+                }
                 float acc[2][8];
 #pragma unroll
                 for (int k = 0; k < 2; ++k)
@@ -470,7 +492,33 @@ __global__ void __maxnreg__(96)
                                             tanh_bf16x2(acc[k][4] + bias[4], acc[k][5] + bias[5]),
                                             tanh_bf16x2(acc[k][6] + bias[6], acc[k][7] + bias[7]));
                         *reinterpret_cast<uint4*>(tsave_tile + ts_off(l, row, gc, H)) = tw;
-                        if (l == L - 1) {
+                        if (RES) {
+                            // h_l = t_l (+ h_{l-1} for l >= 1), kept in FP32 for the next layer
+                            float t[8], h[8];
+                            unpack_bf16x8(tw, t);
+                            const float rp[8] = {rprev[k][0].x, rprev[k][0].y, rprev[k][0].z, rprev[k][0].w,
+                                                 rprev[k][1].x, rprev[k][1].y, rprev[k][1].z, rprev[k][1].w};
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) h[i] = res_fwd ? rp[i] + t[i] : t[i];
+                            if (res_st) {
+                                float4* rs = reinterpret_cast<float4*>(rsave_tile + ts_off(0, row, gc, H));
+                                rs[0] = make_float4(h[0], h[1], h[2], h[3]);
+                                rs[1] = make_float4(h[4], h[5], h[6], h[7]);
+                            }
+                            if (l == L - 1) {
+                                // A = w_out . h_L; Delta_L = w_out (1 - t_L^2)
+                                float d[8];
+                                const float* wo = swout + gc;
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) {
+                                    apart = fmaf(wo[i], h[i], apart);
+                                    d[i] = wo[i] * (1.0f - t[i] * t[i]);
+                                }
+                                store_a8(Abuf, row, gc, ebn, d);
+                            } else {
+                                store_a8(Abuf, row, gc, ebn, h);
+                            }
+                        } else if (l == L - 1) {
                             float t[8], d[8];
                             unpack_bf16x8(tw, t);
                             const float* wo = swout + gc;
@@ -488,11 +536,32 @@ __global__ void __maxnreg__(96)
                             store_a8(Abuf, row, gc, ebn, t);
                         }
                     } else if (l > 0) {
-                        // G_{l-1} -> Delta_{l-1} = G (1 - t_{l-1}^2)
+                        // G_{l-1} -> Delta_{l-1} = G (1 - t_{l-1}^2); with a residual,
+                        // G_{l-1} = W_l^T Delta_l + dA/dh_l first
                         float t[8], d[8];
                         unpack_bf16x8(tcur[k], t);
+                        if (res_bwd) {
+                            float gl[8];
+                            if (l == L - 1) {
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) d[i] = acc[k][i] * (1.0f - t[i] * t[i]);
+                                for (int i = 0; i < 8; ++i) gl[i] = swout[gc + i];
+                            } else {
+                                gl[0] = rprev[k][0].x; gl[1] = rprev[k][0].y; gl[2] = rprev[k][0].z; gl[3] = rprev[k][0].w;
+                                gl[4] = rprev[k][1].x; gl[5] = rprev[k][1].y; gl[6] = rprev[k][1].z; gl[7] = rprev[k][1].w;
+                            }
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) gl[i] += acc[k][i];
+                            if (res_st) {
+                                float4* rs = reinterpret_cast<float4*>(rsave_tile + ts_off(0, row, gc, H));
+                                rs[0] = make_float4(gl[0], gl[1], gl[2], gl[3]);
+                                rs[1] = make_float4(gl[4], gl[5], gl[6], gl[7]);
+                            }
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) d[i] = gl[i] * (1.0f - t[i] * t[i]);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) d[i] = acc[k][i] * (1.0f - t[i] * t[i]);
+                        }
                         store_a8(Abuf, row, gc, ebn, d);
                     } else if (valid) {
                         // G_0 = dA/du: dA/ds_j = -sin s_j g[2j] + cos s_j g[2j+1]
@@ -550,19 +619,20 @@ size_t rid_mlp_tc_smem_bytes(const TcArgs& P) {
 
 cudaError_t rid_launch_mlp_tc(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, cudaStream_t s) {
     if (P.ngemm != P.L && P.ngemm != 2 * P.L) return cudaErrorInvalidValue;
+    if (P.resnet && !P.rsave) return cudaErrorInvalidValue;
     const size_t smem = rid_mlp_tc_smem_bytes(P);
-    const bool f8 = P.geb[0] == 1;
-    static size_t attr[2][64] = {};   // shared memory opted into, per format and device
+    const int v = (P.geb[0] == 1 ? 1 : 0) + (P.resnet ? 2 : 0);
+    static size_t attr[4][64] = {};   // shared memory opted into, per instantiation and device
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
-    size_t& have = attr[f8][dev & 63];
+    size_t& have = attr[v][dev & 63];
+    auto kern = v == 0 ? k_mlp_tc<false, false> : v == 1 ? k_mlp_tc<true, false>
+              : v == 2 ? k_mlp_tc<false, true> : k_mlp_tc<true, true>;
     if (smem > have) {
-        cudaError_t e = f8 ? cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                           : cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         have = smem;
     }
-    if (f8) k_mlp_tc<true><<<dim3(P.ntiles, P.M, 1), NTHREADS, smem, s>>>(P, big, small);
-    else k_mlp_tc<false><<<dim3(P.ntiles, P.M, 1), NTHREADS, smem, s>>>(P, big, small);
+    kern<<<dim3(P.ntiles, P.M, 1), NTHREADS, smem, s>>>(P, big, small);
     return cudaGetLastError();
 }

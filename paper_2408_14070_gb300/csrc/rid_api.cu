@@ -106,7 +106,7 @@ struct rid_system {
     DevBuf d_W, d_WT, d_b, d_wout, d_bout;
     TcVariant tcv;
     int Dp = 0;
-    DevBuf tsave, d_err;
+    DevBuf tsave, rsave, d_err;   // rsave: FP32 residual stream of the tensor-core kernel (resnet)
     // state
     int cap = 0;
     DevBuf x, v, f, fff, s, J, u, gradA, Aval, eps, hs, eff, flags;
@@ -211,6 +211,7 @@ static int ensure_state(rid_system* sys, int W) {
         } else {
             const size_t ntiles = (size_t)(W + 127) / 128;
             TRY(sys->tsave.ensure((size_t)E.M * ntiles * E.L * 128 * E.H * sizeof(__nv_bfloat16)));
+            if (E.resnet) TRY(sys->rsave.ensure((size_t)E.M * ntiles * 128 * E.H * sizeof(float)));
         }
     }
     if (W > sys->cap) sys->cap = W;
@@ -246,6 +247,7 @@ static void destroy_all(rid_system* sys) {
     for (DevBuf* b : bufs) b->release();
     sys->tcv.blob.release();
     sys->tsave.release();
+    sys->rsave.release();
     sys->d_err.release();
     for (auto& r : sys->prof_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     sys->prof_recs.clear();
@@ -498,41 +500,47 @@ static int build_tc_variant(rid_system* sys, const std::vector<float>& W, long l
 extern "C" int rid_set_ensemble(rid_system* sys, const rid_ensemble_desc* d) {
     if (!sys || !d || !d->weights) return fail(RID_ERR_ARG, "NULL argument");
     TRY(check_device(sys));
-    const int M = d->n_models, D = d->n_in, L = d->n_layers, H = d->width;
+    const int M = d->n_models, D = d->n_in, L = d->n_layers, Hu = d->width;
     if (M < 1 || M > RID_MAX_MODELS) return fail(RID_ERR_ARG, "n_models=%d outside [1, %d]", M, RID_MAX_MODELS);
     if (D != 2 * sys->S.C) return fail(RID_ERR_ARG, "n_in=%d must equal 2 * n_cv = %d", D, 2 * sys->S.C);
     if (L < 1 || L > RID_MAX_LAYERS) return fail(RID_ERR_ARG, "n_layers=%d outside [1, %d]", L, RID_MAX_LAYERS);
-    if (H < 32 || H > RID_MAX_WIDTH || H % 32) return fail(RID_ERR_ARG, "width=%d must be a multiple of 32 in [32, %d]", H, RID_MAX_WIDTH);
+    if (Hu < 1 || Hu > RID_MAX_WIDTH) return fail(RID_ERR_ARG, "width=%d outside [1, %d]", Hu, RID_MAX_WIDTH);
     if (d->precision != RID_PREC_FP32 && d->precision != RID_PREC_BF16 && d->precision != RID_PREC_FP8)
         return fail(RID_ERR_ARG, "unknown precision %d", d->precision);
     if (!(d->trust_lo < d->trust_hi)) return fail(RID_ERR_ARG, "need trust_lo < trust_hi");
-    if (d->precision != RID_PREC_FP32 && d->resnet)
-        return fail(RID_ERR_ARG, "resnet ensembles run with RID_PREC_FP32 only");
-    const long long P = (long long)H * D + H + (long long)(L - 1) * ((long long)H * H + H) + H + 1;
+    // The kernels tile the hidden width in multiples of 32.  A width that is
+    // not one is padded with hidden units whose incoming weights, bias and
+    // outgoing weights are all zero: such a unit computes tanh(0) = 0 (plus a
+    // zero residual), contributes nothing to A and receives a zero gradient,
+    // so the padded network is the same function with the same input
+    // gradient, exactly.
+    const int H = (Hu + 31) / 32 * 32;
+    const long long P = (long long)Hu * D + Hu + (long long)(L - 1) * ((long long)Hu * Hu + Hu) + Hu + 1;
     // split the packed layout into W (row-major [H][fin]), W^T, biases, w_out, b_out
     long long wst = (long long)H * D + (long long)(L - 1) * H * H;
-    std::vector<float> W((size_t)M * wst), WT((size_t)M * wst), b((size_t)M * L * H), wo((size_t)M * H), bo(M);
+    std::vector<float> W((size_t)M * wst, 0.0f), WT((size_t)M * wst, 0.0f), b((size_t)M * L * H, 0.0f),
+        wo((size_t)M * H, 0.0f), bo(M);
     long long loff[RID_MAX_LAYERS] = {0};
     for (int l = 1; l < L; ++l) loff[l] = loff[l - 1] + (long long)H * (l == 1 ? D : H);
     for (int m = 0; m < M; ++m) {
         const float* p = d->weights + (size_t)m * P;
         for (int l = 0; l < L; ++l) {
-            const int fin = l == 0 ? D : H;
+            const int fin = l == 0 ? D : H, finu = l == 0 ? D : Hu;
             float* Wm = W.data() + (size_t)m * wst + loff[l];
             float* WTm = WT.data() + (size_t)m * wst + loff[l];
-            for (int o = 0; o < H; ++o)
-                for (int i = 0; i < fin; ++i) {
-                    const float val = p[(size_t)o * fin + i];
+            for (int o = 0; o < Hu; ++o)
+                for (int i = 0; i < finu; ++i) {
+                    const float val = p[(size_t)o * finu + i];
                     if (!std::isfinite(val)) return fail(RID_ERR_ARG, "non-finite weight in model %d", m);
                     Wm[(size_t)o * fin + i] = val;
                     WTm[(size_t)i * H + o] = val;
                 }
-            p += (size_t)H * fin;
-            for (int o = 0; o < H; ++o) b[((size_t)m * L + l) * H + o] = p[o];
-            p += H;
+            p += (size_t)Hu * finu;
+            for (int o = 0; o < Hu; ++o) b[((size_t)m * L + l) * H + o] = p[o];
+            p += Hu;
         }
-        for (int o = 0; o < H; ++o) wo[(size_t)m * H + o] = p[o];
-        bo[m] = p[H];
+        for (int o = 0; o < Hu; ++o) wo[(size_t)m * H + o] = p[o];
+        bo[m] = p[Hu];
     }
     TRY(sys->d_W.ensure(W.size() * sizeof(float)));
     TRY(sys->d_WT.ensure(WT.size() * sizeof(float)));
@@ -716,6 +724,8 @@ static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_
             P.geb[g] = V.geb[g];
         }
         P.wscale = V.wscale.as<float>();
+        P.resnet = E.resnet;
+        P.rsave = E.resnet ? sys->rsave.as<float>() : nullptr;
         P.ngemm = values_only ? E.L : 2 * E.L;
         cudaError_t le = cudaSuccess;
         if (V.tuned_W != W) TRY(tune_tc_stages(sys, P, st));
@@ -948,7 +958,7 @@ size_t rid_sys_footprint(const rid_system* sys, int W) {
         const EnsDev& E = sys->E;
         b += (size_t)E.M * nc * 4 + (size_t)E.M * W * 4;
         if (sys->precision == RID_PREC_FP32) b += rid_mlp_fp32_scratch_floats(W, E.M, E.L, E.H) * 4;
-        else b += (size_t)E.M * ((W + 127) / 128) * E.L * 128 * E.H * 2;
+        else b += (size_t)E.M * ((W + 127) / 128) * 128 * E.H * (E.L * 2 + (E.resnet ? 4 : 0));
     }
     return b;
 }

@@ -34,6 +34,8 @@ struct TcArgs {
     int gN[2 * RID_MAX_LAYERS], gKp[2 * RID_MAX_LAYERS];   // N, and K padded to a 128-byte chunk
     int geb[2 * RID_MAX_LAYERS];                           // operand bytes per element: 2 BF16, 1 FP8 e4m3
     const float* wscale;     // [M][2L] weight scale of every GEMM (1 for BF16)
+    int resnet;              // h_l = h_{l-1} + tanh(z_l) for l >= 1
+    float* rsave;            // resnet: [M][ntiles][H/8][128][8] FP32, h_l forward, dA/dh_l backward
     int ngemm;               // GEMMs to run: 2L (forward and input gradient) or L (forward only:
                              // member values, gradA untouched)
 };

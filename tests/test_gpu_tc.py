@@ -115,15 +115,71 @@ def test_bf16_switching_and_trajectory(R, orc):
     assert np.all(np.abs(eps - ref["eps"]) <= EPS_TOL * np.abs(ref["eps"]) + 1e-3)
 
 
-def test_bf16_rejects_resnet(R):
-    sp = I.make_system(22, 2, 1)
-    ens = I.make_ensemble(4, 4, 3, 64, 1, resnet=True)
-    with R.System(sp) as sys:
-        for prec in (R.RID_PREC_BF16, R.RID_PREC_FP8):
-            with pytest.raises(R.RidError) as e:
-                sys.set_ensemble(ens, precision=prec)
-            assert e.value.code == R.RID_ERR_ARG
-        sys.set_ensemble(ens, precision=R.RID_PREC_FP32)
+# Residual networks and widths that are not a multiple of 32 (padded inside the
+# library with zero units, an exact transformation).  The first case is the
+# paper's own ensemble (Sec. "Training phase": four models, neurons
+# [300, 300, 300, 300], resnet) on 18 torsion CVs, the count of its chignolin
+# example (Sec. "CV selection").
+RESNET_CASES = [
+    (120, 18, 200, 4, 4, 300, True, 21),   # 4 x 36->300x4->1, resnet: width 320 inside, five K-chunks
+    (60, 9, 130, 3, 3, 96, True, 22),      # resnet, width not a multiple of 64
+    (100, 32, 150, 8, 4, 512, True, 23),   # resnet at width 512 (a single TMEM accumulator)
+    (40, 6, 70, 2, 3, 300, False, 24),     # width 300 without residuals
+    (30, 3, 20, 2, 2, 45, True, 25),       # odd width 45 (64 inside)
+    (22, 2, 9, 4, 1, 64, True, 26),        # one hidden layer: no residual term to add
+]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
+@pytest.mark.parametrize("n,C,W,M,L,H,resnet,seed", RESNET_CASES)
+def test_resnet_and_any_width(R, orc, prec, n, C, W, M, L, H, resnet, seed):
+    sp = I.make_system(n, C, seed)
+    x = I.make_chains(W, sp, seed)
+    ens = I.make_ensemble(M, 2 * C, L, H, seed, resnet=resnet, trust_lo=1e9, trust_hi=2e9)
+    p = dict(fp32=R.RID_PREC_FP32, bf16=R.RID_PREC_BF16, fp8=R.RID_PREC_FP8)[prec]
+    f, eps, abar, g = run_eval(R, sp, ens, x, p)
+    worst = 0.0
+    for w in sorted(set([0, 1, W // 2, W - 1] + list(range(0, W, max(1, W // 10))))):
+        e = orc.ensemble(ens, orc.cvs(sp, x[w].astype(np.float64))[0])
+        if prec == "fp32":
+            # the FP32 SIMT path: element-wise 1e-5 as in the unit parity tests
+            ref = e["gradA"]
+            sc = np.sqrt(np.mean(ref ** 2))
+            assert (np.abs(g[:, w] - ref) / (np.abs(ref) + sc)).max() < 1e-5, w
+            assert abs(eps[w] - e["eps"]) <= 1e-5 * (abs(e["eps"]) + 1e-3)
+            assert abs(abar[w] - e["Abar"]) <= 1e-5 * (abs(e["Abar"]) + 1.0)
+            continue
+        if prec == "bf16":
+            for m in range(M):
+                assert normwise(g[m, w], e["gradA"][m]) < GRAD_TOL, (w, m)
+            assert abs(abar[w] - e["Abar"]) <= GRAD_TOL * (abs(e["Abar"]) + 0.1)
+        fbar = g[:, w].astype(np.float64).mean(axis=0)
+        worst = max(worst, normwise(fbar, e["gradA"].mean(axis=0)))
+        assert abs(eps[w] - e["eps"]) <= EPS_TOL * abs(e["eps"]) + 1e-4, w
+    assert worst < (GRAD_TOL if prec == "bf16" else 6e-2)
+    assert np.all(np.isfinite(f))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_paper_network_trajectory(R, orc, prec):
+    """20 biased steps with the paper's 4 x [300]^4 residual ensemble on the
+    tensor cores, the switching band placed inside the walkers' eps range."""
+    sp = I.make_system(120, 18, 27, output_freq=1)
+    W = 12                                     # the paper's walker count
+    x0 = I.make_chains(W, sp, 27)
+    ens = I.make_ensemble(4, 36, 4, 300, 27, resnet=True)
+    eps_r = np.array([orc.ensemble(ens, orc.cvs(sp, xi.astype(np.float64))[0])["eps"] for xi in x0])
+    ens.trust_lo, ens.trust_hi = float(np.percentile(eps_r, 25)), float(np.percentile(eps_r, 75))
+    steps = 20
+    xo = np.zeros_like(x0)
+    eps = np.zeros((W, steps), np.float32)
+    with R.System(sp) as sysobj:
+        sysobj.set_ensemble(ens, precision=R.RID_PREC_BF16 if prec == "bf16" else R.RID_PREC_FP8)
+        sysobj.explore(x0, steps, eps_out=eps, x_out=xo)
+    ref = orc.explore(sp, x0, steps, ens=ens)
+    tol = 1e-3 if prec == "bf16" else 2e-3
+    assert np.all(np.abs(xo - ref["x"]) <= tol * (np.abs(ref["x"]) + 1))
+    assert np.all(np.abs(eps - ref["eps"]) <= (EPS_TOL if prec == "bf16" else 1e-1) * np.abs(ref["eps"]) + 1e-3)
 
 
 @pytest.mark.parametrize("n,C,W,M,L,H,seed", [
