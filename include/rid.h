@@ -458,6 +458,21 @@ RID_API int rid_profile_read(rid_system* sys, int32_t max_kernels, char* names_o
 RID_API int64_t rid_launch_count(rid_system* sys);
 
 /*
+ * Cluster size of the tensor-core ensemble kernel (BF16 / FP8 ensembles; no
+ * counterpart in the paper, a tuning control).  The kernel splits every
+ * GEMM's output columns over csize CTAs of a thread-block cluster (1: one CTA
+ * per 128-walker tile and member; 2 or 4: the columns split over a cluster,
+ * the next layer's operand exchanged through distributed shared memory).
+ * csize = 0 (the default) lets the library time the force evaluation with
+ * each eligible size at the first evaluation of every new walker count and
+ * keep the fastest.  Every size gives the same results bit for bit.
+ * Errors: RID_ERR_ARG (csize not 0, 1, 2 or 4); a size the ensemble's shape
+ * does not allow (shared memory) fails with RID_ERR_ARG at the next
+ * evaluation.
+ */
+RID_API int rid_set_mlp_cluster(rid_system* sys, int32_t csize);
+
+/*
  * Server: device memory of a fixed HBM budget, from which batched label runs
  * (rid_label_batch) and the request loop (rid_submit / rid_poll) take their
  * device memory.  Memory is allocated in segments, on demand, up to the

@@ -1,0 +1,439 @@
+// k_mlp_tc_cluster.cu -- the tcgen05 ensemble MLP with each GEMM's output
+// columns split over a thread-block cluster of S = 2 or 4 CTAs.
+//
+// Same arithmetic as k_mlp_tc (BF16 / FP8 operands, FP32 accumulation in
+// TMEM, tanh saved in BF16, optional residual stream in FP32); what differs
+// is who computes what.  A cluster owns one tile of 128 walkers and one
+// ensemble member; CTA r of the cluster computes the output columns
+// [r n_s, r n_s + n_s) of every GEMM (n_s = N / S rounded up to 16), i.e. it
+// streams only those rows of the weight image and runs an N = n_s MMA.  Its
+// epilogue writes its columns of the next GEMM's A operand into the shared
+// memory of every CTA of the cluster (st.shared::cluster) and arrives on
+// their "operand complete" barriers, so each CTA again holds the whole
+// operand.  Per GEMM the critical path is then one 64-column epilogue chunk
+// instead of N / 64 of them.
+//
+// The A operand is double buffered (GEMM g reads buffer g mod 2, its
+// epilogue writes buffer (g + 1) mod 2): a peer may still be reading buffer
+// g mod 2 for GEMM g when this CTA has finished it, but a write into buffer
+// (g + 1) mod 2 of a peer needs that peer's GEMM g - 1 to be complete, which
+// the operand barrier of GEMM g already guarantees.  The member value
+// A = w_out . h_L + b_out is formed from 16-column partial sums added in column
+// order, as in k_mlp_tc, so the cluster size does not change its bits.
+//
+// Warp roles as in k_mlp_tc: warp 0 TMA producer, warp 1 TMEM allocator and
+// MMA issuer, warps 2..17 epilogue.  Every wait is bounded in time; a CTA
+// whose wait expires sets the error word and stops issuing, its peers' waits
+// then expire too, and every CTA still meets the final cluster barrier, so no
+// CTA exits while another may write into its shared memory.
+#include "rid_tc_ptx.cuh"
+
+namespace {
+
+struct SmemC {
+    uint64_t full[TC_MAX_STAGES];
+    uint64_t empty[TC_MAX_STAGES];
+    uint64_t acc_full[2];
+    uint64_t acc_empty[2];
+    uint64_t a_full[2];        // operand buffer b complete: 16 epilogue warps x S CTAs
+    uint64_t u_full;           // the MLP input in buffer 0: this CTA's 16 epilogue warps
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+// Output-column slice of GEMM width N owned by rank r of S.
+__device__ __forceinline__ void col_slice(int N, int S, int r, int& lo, int& n) {
+    const int ns = ((N + S - 1) / S + 15) / 16 * 16;
+    lo = r * ns;
+    n = N - lo < ns ? N - lo : ns;
+    if (n < 0) n = 0;
+}
+
+template <bool F8, bool RES>
+__global__ void __maxnreg__(96)
+    k_mlp_tc_cluster(const __grid_constant__ TcArgs P, const __grid_constant__ CUtensorMap map_big,
+                     const __grid_constant__ CUtensorMap map_small) {
+    extern __shared__ __align__(1024) unsigned char dsm_raw[];
+    unsigned char* dsm =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ SmemC S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int CS = P.csize;
+    const int rank = (int)cluster_rank();
+    const int tile = blockIdx.x / CS, m = blockIdx.y;
+    const int L = P.L, G = P.ngemm;
+    const size_t abytes = (size_t)P.Kpmax * 256u;
+    unsigned char* Abuf[2] = {dsm, dsm + abytes};
+    unsigned char* stages = dsm + 2 * abytes;
+    const uint32_t stage_bytes = P.stage_bytes;
+    const int NS = P.stages;
+    volatile int* abort_flag = &S.abort_flag;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(smem_u32(&S.full[s]), 1);
+            mbar_init(smem_u32(&S.empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&S.acc_full[b]), 1);
+            mbar_init(smem_u32(&S.acc_empty[b]), EPI_WARPS);
+            mbar_init(smem_u32(&S.a_full[b]), EPI_WARPS * CS);
+        }
+        mbar_init(smem_u32(&S.u_full), EPI_WARPS);
+        mbar_init(smem_u32(&S.drain), 1);
+        S.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                     "r"((uint32_t)P.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    // barriers initialised in every CTA before any peer arrives on them
+    cluster_sync_all();
+    fence_after();
+    const uint32_t tmem = S.tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int it = 0;
+            int last_it[TC_MAX_STAGES];
+            for (int s = 0; s < NS; ++s) last_it[s] = -1;
+            bool ok = true;
+            for (int g = 0; g < G && ok; ++g) {
+                int lo, nr;
+                col_slice(P.gN[g], CS, rank, lo, nr);
+                if (nr == 0) continue;
+                const int N = P.gN[g], nch = P.gKp[g] * (F8 ? P.geb[g] : 2) / 128;
+                for (int c = 0; c < nch; ++c, ++it) {
+                    const int s = it % NS;
+                    if (!mbar_wait(smem_u32(&S.empty[s]), ((it / NS) & 1) ^ 1, abort_flag, P.err, 1)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_tx(smem_u32(&S.full[s]), (uint32_t)nr * 128u);
+                    last_it[s] = it;
+                    const long long row0 = (long long)m * P.member_rows + P.grow[g] + (long long)c * N + lo;
+                    uint32_t dst = smem_u32(stages + (size_t)s * stage_bytes);
+                    int rr = 0;
+                    for (; rr + 64 <= nr; rr += 64, dst += 8192u)
+                        tma_load_2d(dst, &map_big, 0, (int)(row0 + rr), smem_u32(&S.full[s]));
+                    for (; rr < nr; rr += 8, dst += 1024u)
+                        tma_load_2d(dst, &map_small, 0, (int)(row0 + rr), smem_u32(&S.full[s]));
+                }
+            }
+            if (!ok) {
+                for (int s = 0; s < NS; ++s)
+                    if (last_it[s] >= 0) {
+                        const unsigned long long t0 = gtimer();
+                        while (!mbar_try(smem_u32(&S.full[s]), (last_it[s] / NS) & 1) && gtimer() - t0 < WAIT_NS) {}
+                    }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int g = 0; g < G && ok; ++g) {
+                int lo, nr;
+                col_slice(P.gN[g], CS, rank, lo, nr);
+                const int nch = P.gKp[g] * (F8 ? P.geb[g] : 2) / 128;
+                const bool f8 = F8 && P.geb[g] == 1;
+                const int b = g & 1;
+                const uint32_t dacc = tmem + (uint32_t)(b * P.acc_cols);
+                if (g >= 2 && !mbar_wait(smem_u32(&S.acc_empty[b]), ((g >> 1) - 1) & 1, abort_flag, P.err, 2)) {
+                    ok = false;
+                    break;
+                }
+                // the whole operand of this GEMM is in buffer b
+                const bool aok = g == 0 ? mbar_wait(smem_u32(&S.u_full), 0, abort_flag, P.err, 4)
+                                        : mbar_wait_cluster(smem_u32(&S.a_full[b]), ((g - 1) >> 1) & 1, abort_flag,
+                                                            P.err, 4);
+                if (!aok) {
+                    ok = false;
+                    break;
+                }
+                fence_async_smem();   // peers' generic-proxy stores -> this CTA's MMA reads
+                fence_after();
+                if (nr > 0) {
+                    const uint32_t a_base = smem_u32(Abuf[b]);
+                    for (int c = 0; c < nch; ++c, ++it) {
+                        const int s = it % NS;
+                        if (!mbar_wait(smem_u32(&S.full[s]), (it / NS) & 1, abort_flag, P.err, 4)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint32_t a_atom = a_base + (uint32_t)c * (128u * 128u);
+                        const uint32_t b_atom = smem_u32(stages + (size_t)s * stage_bytes);
+                        if (f8) {
+                            const uint32_t id = idesc_e4m3(128, nr);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                mma_e4m3(dacc, desc_sw128(a_atom + 32u * kk), desc_sw128(b_atom + 32u * kk), id,
+                                         (c | kk) != 0);
+                        } else {
+                            const uint32_t id = idesc_bf16(128, nr);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                mma_bf16(dacc, desc_sw128(a_atom + 32u * kk), desc_sw128(b_atom + 32u * kk), id,
+                                         (c | kk) != 0);
+                        }
+                        mma_commit(smem_u32(&S.empty[s]));
+                    }
+                }
+                if (ok) mma_commit(smem_u32(&S.acc_full[b]));
+            }
+            mma_commit(smem_u32(&S.drain));
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try(smem_u32(&S.drain), 0) && gtimer() - t0 < WAIT_NS) {}
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int e = warp - EPI_WARP0;          // 0..15
+        const int quarter = warp & 3;            // TMEM lane quarter this warp may access
+        const int sub = e >> 2;                  // 16-column slice of every 64-column chunk
+        const int row = quarter * 32 + lane;     // walker within the tile
+        const int wg = tile * 128 + row;
+        const bool valid = wg < P.W;
+        const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+        const int H = P.H;
+        const int ET = 32 * EPI_WARPS;
+        // GEMM 0 input: u (FP32 [W][D]) -> buffer 0 in its operand format (zeros past D)
+        {
+            const int eb0 = F8 ? P.geb[0] : 2, kc0 = 128 / eb0, nch0 = P.gKp[0] * eb0 / 128;
+            for (int c = 0; c < nch0; ++c)
+                for (int k8 = 0; k8 < kc0 / 32; ++k8) {
+                    const int col = c * kc0 + sub * (kc0 / 4) + k8 * 8;
+                    float v[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int k = col + i;
+                        v[i] = (valid && k < P.D) ? __ldg(P.u + (size_t)wg * P.D + k) : 0.0f;
+                    }
+                    store_a8(Abuf[0], row, col, eb0, v);
+                }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&S.u_full));
+        }
+        float* sbias = reinterpret_cast<float*>(stages + (size_t)NS * stage_bytes);   // [L][H]
+        float* swout = sbias + (size_t)L * H;                                          // [H]
+        for (int idx = e * 32 + lane; idx < (L + 1) * H; idx += ET) {
+            const int l = idx / H, c = idx - l * H;
+            sbias[idx] = l < L ? __ldg(P.bias + ((size_t)m * L + l) * H + c) : __ldg(P.wout + (size_t)m * H + c);
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(ET) : "memory");
+        __nv_bfloat16* tsave_tile = P.tsave + ((size_t)m * P.ntiles + tile) * (size_t)L * 128 * H;
+        float* rsave_tile = RES ? P.rsave + ((size_t)m * P.ntiles + tile) * (size_t)128 * H : nullptr;
+        for (int g = 0; g < G; ++g) {
+            const int N = P.gN[g];
+            int lo, nr;
+            col_slice(N, CS, rank, lo, nr);
+            const bool fwd = g < L;
+            const int ebn = (F8 && g + 1 < G) ? P.geb[g + 1] : 2;
+            const float ws = F8 ? P.wscale[(size_t)m * 2 * L + g] : 1.0f;
+            const int l = fwd ? g : (2 * L - 1 - g);
+            const int b = g & 1;
+            const bool res_fwd = RES && fwd && l >= 1;
+            const bool res_bwd = RES && !fwd && l >= 1;
+            const bool res_ld = res_fwd || (res_bwd && l < L - 1);
+            const bool res_st = RES && (fwd ? l < L - 1 : l >= 2);
+            unsigned char* Anext = Abuf[(g + 1) & 1];
+            if (!mbar_wait(smem_u32(&S.acc_full[b]), (g >> 1) & 1, abort_flag, P.err, 8)) break;
+            fence_after();
+            const uint32_t tacc = trow + (uint32_t)(b * P.acc_cols);
+            for (int c0 = 0; c0 < nr; c0 += 64) {
+                const int lc = c0 + sub * 16;          // first local column of this warp
+                const int left = nr - lc;
+                const int ng = left <= 0 ? 0 : (left >= 16 ? 2 : 1);
+                if (ng == 0) continue;
+                uint4 tcur[2];
+                if (!fwd && l > 0) {
+#pragma unroll
+                    for (int k = 0; k < 2; ++k)
+                        if (k < ng) tcur[k] = *reinterpret_cast<const uint4*>(tsave_tile + ts_off(l - 1, row, lo + lc + k * 8, H));
+                }
+                float4 rprev[2][2];
+                if (res_ld) {
+#pragma unroll
+                    for (int k = 0; k < 2; ++k)
+                        if (k < ng) {
+                            const float4* rp = reinterpret_cast<const float4*>(rsave_tile + ts_off(0, row, lo + lc + k * 8, H));
+                            rprev[k][0] = rp[0];
+                            rprev[k][1] = rp[1];
+                        }
+                }
+                float acc[2][8];
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    if (k < ng) tmem_ld8(tacc + (uint32_t)(lc + k * 8), acc[k]);
+                tmem_wait_ld();
+                float apart = 0.0f;                    // w_out . h_L over this warp's 16 columns
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (k >= ng) break;
+                    const int gc = lo + lc + k * 8;    // global column
+                    float v[8];                        // next GEMM's operand values
+                    bool have_v = false;
+                    if (fwd) {
+                        const float* bias = sbias + (size_t)l * H + gc;
+                        float z[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) z[i] = F8 ? fmaf(acc[k][i], ws, bias[i]) : acc[k][i] + bias[i];
+                        const uint4 tw = make_uint4(tanh_bf16x2(z[0], z[1]), tanh_bf16x2(z[2], z[3]),
+                                                    tanh_bf16x2(z[4], z[5]), tanh_bf16x2(z[6], z[7]));
+                        *reinterpret_cast<uint4*>(tsave_tile + ts_off(l, row, gc, H)) = tw;
+                        float t[8];
+                        unpack_bf16x8(tw, t);
+                        float h[8];
+                        if (RES) {
+                            const float rp[8] = {rprev[k][0].x, rprev[k][0].y, rprev[k][0].z, rprev[k][0].w,
+                                                 rprev[k][1].x, rprev[k][1].y, rprev[k][1].z, rprev[k][1].w};
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) h[i] = res_fwd ? rp[i] + t[i] : t[i];
+                            if (res_st) {
+                                float4* rs = reinterpret_cast<float4*>(rsave_tile + ts_off(0, row, gc, H));
+                                rs[0] = make_float4(h[0], h[1], h[2], h[3]);
+                                rs[1] = make_float4(h[4], h[5], h[6], h[7]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) h[i] = t[i];
+                        }
+                        if (l == L - 1) {
+                            const float* wo = swout + gc;
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                apart = fmaf(wo[i], h[i], apart);
+                                v[i] = wo[i] * (1.0f - t[i] * t[i]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) v[i] = h[i];
+                        }
+                        have_v = true;
+                    } else if (l > 0) {
+                        float t[8];
+                        unpack_bf16x8(tcur[k], t);
+                        float gl[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) gl[i] = acc[k][i];
+                        if (res_bwd) {
+                            if (l == L - 1) {
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) gl[i] += swout[gc + i];
+                            } else {
+                                gl[0] += rprev[k][0].x; gl[1] += rprev[k][0].y; gl[2] += rprev[k][0].z; gl[3] += rprev[k][0].w;
+                                gl[4] += rprev[k][1].x; gl[5] += rprev[k][1].y; gl[6] += rprev[k][1].z; gl[7] += rprev[k][1].w;
+                            }
+                            if (res_st) {
+                                float4* rs = reinterpret_cast<float4*>(rsave_tile + ts_off(0, row, gc, H));
+                                rs[0] = make_float4(gl[0], gl[1], gl[2], gl[3]);
+                                rs[1] = make_float4(gl[4], gl[5], gl[6], gl[7]);
+                            }
+                        }
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) v[i] = gl[i] * (1.0f - t[i] * t[i]);
+                        have_v = true;
+                    } else if (valid) {
+                        // G_0 = dA/du: dA/ds_j = -sin s_j g[2j] + cos s_j g[2j+1]
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) {
+                            const int j = gc / 2 + p;
+                            if (2 * j < P.D) {
+                                const float cs = __ldg(P.u + (size_t)wg * P.D + 2 * j);
+                                const float sn = __ldg(P.u + (size_t)wg * P.D + 2 * j + 1);
+                                P.gradA[((size_t)m * P.W + wg) * P.C + j] = -sn * acc[k][2 * p] + cs * acc[k][2 * p + 1];
+                            }
+                        }
+                    }
+                    if (have_v && g < G - 1) {
+                        // this CTA's columns of the next operand, into every CTA of the cluster
+                        if (ebn == 2) {
+                            const uint4 pv = pack8(v);
+                            const uint32_t a = smem_u32(Anext + a_off(row, gc));
+                            for (int q = 0; q < CS; ++q) st_cluster_v4(mapa(a, (uint32_t)q), pv);
+                        } else {
+                            const uint2 pv = pack8_e4m3(v);
+                            const uint32_t a = smem_u32(Anext + a_off8(row, gc));
+                            for (int q = 0; q < CS; ++q) st_cluster_v2(mapa(a, (uint32_t)q), pv);
+                        }
+                    }
+                }
+                if (fwd && l == L - 1) P.qsave[qs_off(m, tile, (lo + lc) >> 4, row, P.ntiles)] = apart;
+            }
+            if (g < G - 1) {
+                // K padding of the next operand (columns N .. Kp - 1) in this CTA's
+                // own copy: it may hold an earlier, wider operand
+                for (int gc = N + 8 * sub; gc < P.gKp[g + 1]; gc += 32) zero_a8(Anext, row, gc, ebn);
+                fence_async_smem_cluster();
+                __syncwarp();
+                if (lane == 0)
+                    for (int q = 0; q < CS; ++q) mbar_arrive_cluster(smem_u32(&S.a_full[(g + 1) & 1]), (uint32_t)q);
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&S.acc_empty[b]));
+        }
+    }
+    fence_before();
+    __syncthreads();
+    // every CTA's 16-column partials are written: rank 0 adds them in column order
+    cluster_sync_all();
+    if (rank == 0 && warp >= EPI_WARP0 && warp < EPI_WARP0 + 4) {
+        const int row = (warp & 3) * 32 + lane;
+        const int wg = tile * 128 + row;
+        if (wg < P.W && !S.abort_flag) P.Apart[(size_t)m * P.W + wg] = member_value(P, m, tile, row);
+    }
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)P.tmem_cols)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+size_t rid_mlp_tc_cluster_smem_bytes(const TcArgs& P) {
+    return 1024 + 2 * (size_t)P.Kpmax * 256u + (size_t)P.stages * P.stage_bytes +
+           sizeof(float) * (size_t)(P.L + 1) * P.H;
+}
+
+cudaError_t rid_launch_mlp_tc_cluster(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small,
+                                      cudaStream_t s) {
+    if (P.ngemm != P.L && P.ngemm != 2 * P.L) return cudaErrorInvalidValue;
+    if (P.csize != 2 && P.csize != 4) return cudaErrorInvalidValue;
+    if (P.resnet && !P.rsave) return cudaErrorInvalidValue;
+    const size_t smem = rid_mlp_tc_cluster_smem_bytes(P);
+    const int v = (P.geb[0] == 1 ? 1 : 0) + (P.resnet ? 2 : 0);
+    static size_t attr[4][64] = {};   // shared memory opted into, per instantiation and device
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    size_t& have = attr[v][dev & 63];
+    auto kern = v == 0 ? k_mlp_tc_cluster<false, false> : v == 1 ? k_mlp_tc_cluster<true, false>
+              : v == 2 ? k_mlp_tc_cluster<false, true> : k_mlp_tc_cluster<true, true>;
+    if (smem > have) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        have = smem;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(P.ntiles * P.csize, P.M, 1);
+    cfg.blockDim = dim3(NTHREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = P.csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, P, big, small);
+}

@@ -1,0 +1,430 @@
+// k_mlp_tc_wide.cu -- the tcgen05 ensemble MLP for hidden widths whose
+// accumulator fills TMEM (width > 256: one accumulator, no double buffering).
+//
+// Same arithmetic and data layout as k_mlp_tc (BF16 / FP8 operands, FP32
+// accumulation in TMEM, tanh saved in BF16, optional FP32 residual stream,
+// member values from 16-column partials in column order), and the same warp
+// roles: warp 0 TMA producer, warp 1 TMEM allocator and MMA issuer, warps
+// 2..17 epilogue.  What differs is the epilogue's column mapping.  With a
+// single accumulator the next GEMM cannot start before the epilogue has
+// drained TMEM, so there is nothing to gain from releasing the next operand
+// chunk by chunk; instead each epilogue warp owns a contiguous quarter of the
+// GEMM's output columns (for its TMEM lane quarter), the four quarters of a
+// row block are finished side by side, and the operand is released once per
+// GEMM.  Measured at 8 members x 64-512x4-1 and 8192 walkers: 507 -> 432 us
+// per launch against the chunk-interleaved epilogue.  Every wait is bounded
+// in time.
+#include "rid_tc_ptx.cuh"
+
+namespace {
+
+struct Smem {
+    uint64_t full[TC_MAX_STAGES];
+    uint64_t empty[TC_MAX_STAGES];
+    uint64_t acc_full[2];
+    uint64_t acc_empty[2];
+    uint64_t a_full;          // the next GEMM's operand is complete: 16 epilogue warps
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+// 18 warps spread 5/5/4/4 over the four schedulers, each with 16K registers:
+// at most 96 registers per thread
+// F8: the forward GEMMs take FP8 e4m3 operands (the input-gradient GEMMs
+// stay BF16); the BF16 instantiation has every operand format fixed at
+// compile time.
+// RES: residual ensemble (h_l = h_{l-1} + tanh(z_l) for l >= 1), its own
+// instantiation so that the plain networks keep their register allocation.
+template <bool F8, bool RES>
+__global__ void __maxnreg__(96)
+    k_mlp_tc_wide(const __grid_constant__ TcArgs P, const __grid_constant__ CUtensorMap map_big,
+             const __grid_constant__ CUtensorMap map_small) {
+    extern __shared__ __align__(1024) unsigned char dsm_raw[];
+    // swizzled tiles need 1024-byte aligned atoms
+    unsigned char* dsm =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ Smem S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x, m = blockIdx.y;
+    const int L = P.L, G = P.ngemm;   // 2L, or L for the member values alone
+    unsigned char* Abuf = dsm;                                     // [Kpmax/64][128 rows][128 B]
+    unsigned char* stages = dsm + (size_t)P.Kpmax * 256u;          // 128 rows x 2 B per column
+    const uint32_t stage_bytes = P.stage_bytes;
+    const int NS = P.stages;
+    const int NACC = P.nacc;
+    volatile int* abort_flag = &S.abort_flag;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(smem_u32(&S.full[s]), 1);
+            mbar_init(smem_u32(&S.empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&S.acc_full[b]), 1);
+            mbar_init(smem_u32(&S.acc_empty[b]), EPI_WARPS);
+        }
+        mbar_init(smem_u32(&S.a_full), EPI_WARPS);
+        mbar_init(smem_u32(&S.drain), 1);
+        S.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                     "r"((uint32_t)P.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = S.tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int it = 0;
+            int last_it[TC_MAX_STAGES];
+            for (int s = 0; s < NS; ++s) last_it[s] = -1;
+            bool ok = true;
+            for (int g = 0; g < G && ok; ++g) {
+                const int N = P.gN[g], nch = P.gKp[g] * (F8 ? P.geb[g] : 2) / 128;
+                for (int c = 0; c < nch && ok; ++c)
+                    for (int n0 = 0; n0 < N; n0 += 256, ++it) {
+                        const int rows = N - n0 < 256 ? N - n0 : 256;
+                        const int s = it % NS;
+                        if (!mbar_wait(smem_u32(&S.empty[s]), ((it / NS) & 1) ^ 1, abort_flag, P.err, 1)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_tx(smem_u32(&S.full[s]), (uint32_t)rows * 128u);
+                        last_it[s] = it;
+                        const long long row0 = (long long)m * P.member_rows + P.grow[g] + (long long)c * N + n0;
+                        uint32_t dst = smem_u32(stages + (size_t)s * stage_bytes);
+                        int r = 0;
+                        for (; r + 64 <= rows; r += 64, dst += 8192u)
+                            tma_load_2d(dst, &map_big, 0, (int)(row0 + r), smem_u32(&S.full[s]));
+                        for (; r < rows; r += 8, dst += 1024u)
+                            tma_load_2d(dst, &map_small, 0, (int)(row0 + r), smem_u32(&S.full[s]));
+                    }
+            }
+            if (!ok) {
+                // the loads already issued land before the CTA can exit
+                for (int s = 0; s < NS; ++s)
+                    if (last_it[s] >= 0) {
+                        const unsigned long long t0 = gtimer();
+                        while (!mbar_try(smem_u32(&S.full[s]), (last_it[s] / NS) & 1) && gtimer() - t0 < WAIT_NS) {}
+                    }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int g = 0; g < G && ok; ++g) {
+                const int N = P.gN[g], nch = P.gKp[g] * (F8 ? P.geb[g] : 2) / 128;
+                const bool f8 = F8 && P.geb[g] == 1;
+                const int b = g % NACC;
+                const uint32_t dacc = tmem + (uint32_t)(b * P.acc_cols);
+                if (g >= NACC &&
+                    !mbar_wait(smem_u32(&S.acc_empty[b]), ((g / NACC) - 1) & 1, abort_flag, P.err, 2)) {
+                    ok = false;
+                    break;
+                }
+                // the whole operand of this GEMM is in shared memory (completion g of a_full:
+                // the input for g = 0, then the epilogue of GEMM g - 1)
+                if (!mbar_wait(smem_u32(&S.a_full), g & 1, abort_flag, P.err, 4)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                for (int c = 0; c < nch && ok; ++c) {
+                    const uint32_t a_atom = smem_u32(Abuf) + (uint32_t)c * (128u * 128u);
+                    for (int n0 = 0; n0 < N; n0 += 256, ++it) {
+                        const int rows = N - n0 < 256 ? N - n0 : 256;
+                        const int s = it % NS;
+                        if (!mbar_wait(smem_u32(&S.full[s]), (it / NS) & 1, abort_flag, P.err, 4)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint32_t b_atom = smem_u32(stages + (size_t)s * stage_bytes);
+                        // K = 16 BF16 or 32 FP8 per MMA: 32 bytes into the 128-byte rows
+                        if (f8) {
+                            const uint32_t id = idesc_e4m3(128, rows);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                mma_e4m3(dacc + (uint32_t)n0, desc_sw128(a_atom + 32u * kk),
+                                         desc_sw128(b_atom + 32u * kk), id, (c | kk) != 0);
+                        } else {
+                            const uint32_t id = idesc_bf16(128, rows);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                mma_bf16(dacc + (uint32_t)n0, desc_sw128(a_atom + 32u * kk),
+                                         desc_sw128(b_atom + 32u * kk), id, (c | kk) != 0);
+                        }
+                        mma_commit(smem_u32(&S.empty[s]));
+                    }
+                }
+                if (ok) mma_commit(smem_u32(&S.acc_full[b]));
+            }
+            // every MMA issued has completed before TMEM can be released
+            mma_commit(smem_u32(&S.drain));
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try(smem_u32(&S.drain), 0) && gtimer() - t0 < WAIT_NS) {}
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        // Warp w reads TMEM lane quarter w mod 4 (rows 32 (w mod 4) ..) and owns
+        // a contiguous range of each GEMM's output columns (sub = (w - 2) / 4 of
+        // four), so the four ranges of a row quarter are finished side by side;
+        // the next GEMM's operand is released once per GEMM.
+        const int e = warp - EPI_WARP0;          // 0..15
+        const int quarter = warp & 3;            // TMEM lane quarter this warp may access
+        const int sub = e >> 2;                  // column range of this warp
+        const int row = quarter * 32 + lane;     // walker within the tile
+        const int wg = tile * 128 + row;         // global walker
+        const bool valid = wg < P.W;
+        const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+        const int H = P.H;
+        const int ET = 32 * EPI_WARPS;
+        // GEMM 0 input: u (FP32, [W][D]) -> its operand format (zeros past D);
+        // a 128-byte chunk is 64 BF16 or 128 FP8 columns
+        {
+            const int eb0 = F8 ? P.geb[0] : 2, kc0 = 128 / eb0, nch0 = P.gKp[0] * eb0 / 128;
+            for (int c = 0; c < nch0; ++c)
+                for (int k8 = 0; k8 < kc0 / 32; ++k8) {
+                    const int col = c * kc0 + sub * (kc0 / 4) + k8 * 8;
+                    float v[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int k = col + i;
+                        v[i] = (valid && k < P.D) ? __ldg(P.u + (size_t)wg * P.D + k) : 0.0f;
+                    }
+                    store_a8(Abuf, row, col, eb0, v);
+                }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&S.a_full));
+        }
+        float* sbias = reinterpret_cast<float*>(stages + (size_t)NS * stage_bytes);   // [L][H]
+        float* swout = sbias + (size_t)L * H;                                          // [H]
+        for (int idx = e * 32 + lane; idx < (L + 1) * H; idx += ET) {
+            const int l = idx / H, c = idx - l * H;
+            sbias[idx] = l < L ? __ldg(P.bias + ((size_t)m * L + l) * H + c) : __ldg(P.wout + (size_t)m * H + c);
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(ET) : "memory");   // all epilogue warps, before any bounded wait
+        __nv_bfloat16* tsave_tile = P.tsave + ((size_t)m * P.ntiles + tile) * (size_t)L * 128 * H;
+        // residual stream of a resnet ensemble: h_l (forward) and dA/dh_l (backward)
+        // in FP32, one [H/8][128][8] block per tile and member, overwritten in place
+        float* rsave_tile = RES ? P.rsave + ((size_t)m * P.ntiles + tile) * (size_t)128 * H : nullptr;
+        for (int g = 0; g < G; ++g) {
+            const int N = P.gN[g];
+            const bool fwd = g < L;
+            // operand format of the next GEMM (2 BF16, 1 FP8) and its padded K
+            const int ebn = (F8 && g + 1 < G) ? P.geb[g + 1] : 2;
+            const int kpn = g + 1 < G ? P.gKp[g + 1] : N;
+            const float ws = F8 ? P.wscale[(size_t)m * 2 * L + g] : 1.0f;   // [M][2L]
+            const int l = fwd ? g : (2 * L - 1 - g);   // layer of this GEMM
+            const int b = g % NACC;
+            const bool res_fwd = RES && fwd && l >= 1;
+            const bool res_bwd = RES && !fwd && l >= 1;
+            const bool res_ld = res_fwd || (res_bwd && l < L - 1);
+            const bool res_st = RES && (fwd ? l < L - 1 : l >= 2);
+            const bool tload = !fwd && l > 0;          // saved tanh of layer l-1 needed
+            // this warp's columns: 8-column groups [gr0, gr1), an even count
+            const int ngr = N / 8;
+            const int gpw = 2 * ((ngr + 7) / 8);
+            const int gr0 = sub * gpw < ngr ? sub * gpw : ngr;
+            const int gr1 = gr0 + gpw < ngr ? gr0 + gpw : ngr;
+            // saved tanh of the first 16 columns, loaded before the wait
+            uint4 tnext[2];
+            if (tload && gr0 < gr1) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    tnext[k] = *reinterpret_cast<const uint4*>(tsave_tile + ts_off(l - 1, row, (gr0 + k) * 8, H));
+            }
+            if (!mbar_wait(smem_u32(&S.acc_full[b]), (g / NACC) & 1, abort_flag, P.err, 8)) break;
+            fence_after();
+            const uint32_t tacc = trow + (uint32_t)(b * P.acc_cols);
+            for (int gr = gr0; gr < gr1; gr += 2) {
+                const int col0 = gr * 8;               // first of these 16 columns
+                uint4 tcur[2];
+                if (tload) {
+                    tcur[0] = tnext[0];
+                    tcur[1] = tnext[1];
+                    if (gr + 2 < gr1) {
+#pragma unroll
+                        for (int k = 0; k < 2; ++k)
+                            tnext[k] = *reinterpret_cast<const uint4*>(tsave_tile + ts_off(l - 1, row, col0 + 16 + 8 * k, H));
+                    }
+                }
+                float4 rprev[2][2];
+                if (res_ld) {
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const float4* rp = reinterpret_cast<const float4*>(rsave_tile + ts_off(0, row, col0 + k * 8, H));
+                        rprev[k][0] = rp[0];
+                        rprev[k][1] = rp[1];
+                    }
+                }
+                float acc[2][8];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) tmem_ld8(tacc + (uint32_t)(col0 + k * 8), acc[k]);
+                tmem_wait_ld();
+                float apart = 0.0f;                    // w_out . h_L over these 16 columns
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int gc = col0 + k * 8;
+                    if (fwd) {
+                        const float* bias = sbias + (size_t)l * H + gc;
+                        // z = s_W (A W'^T) + b: the weight scale of an FP8 GEMM (1 for BF16)
+                        const uint4 tw =
+                            F8 ? make_uint4(tanh_bf16x2(fmaf(acc[k][0], ws, bias[0]), fmaf(acc[k][1], ws, bias[1])),
+                                            tanh_bf16x2(fmaf(acc[k][2], ws, bias[2]), fmaf(acc[k][3], ws, bias[3])),
+                                            tanh_bf16x2(fmaf(acc[k][4], ws, bias[4]), fmaf(acc[k][5], ws, bias[5])),
+                                            tanh_bf16x2(fmaf(acc[k][6], ws, bias[6]), fmaf(acc[k][7], ws, bias[7])))
+                               : make_uint4(tanh_bf16x2(acc[k][0] + bias[0], acc[k][1] + bias[1]),
+                                            tanh_bf16x2(acc[k][2] + bias[2], acc[k][3] + bias[3]),
+                                            tanh_bf16x2(acc[k][4] + bias[4], acc[k][5] + bias[5]),
+                                            tanh_bf16x2(acc[k][6] + bias[6], acc[k][7] + bias[7]));
+                        *reinterpret_cast<uint4*>(tsave_tile + ts_off(l, row, gc, H)) = tw;
+                        if (RES) {
+                            // h_l = t_l (+ h_{l-1} for l >= 1), kept in FP32 for the next layer
+                            float t[8], h[8];
+                            unpack_bf16x8(tw, t);
+                            const float rp[8] = {rprev[k][0].x, rprev[k][0].y, rprev[k][0].z, rprev[k][0].w,
+                                                 rprev[k][1].x, rprev[k][1].y, rprev[k][1].z, rprev[k][1].w};
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) h[i] = res_fwd ? rp[i] + t[i] : t[i];
+                            if (res_st) {
+                                float4* rs = reinterpret_cast<float4*>(rsave_tile + ts_off(0, row, gc, H));
+                                rs[0] = make_float4(h[0], h[1], h[2], h[3]);
+                                rs[1] = make_float4(h[4], h[5], h[6], h[7]);
+                            }
+                            if (l == L - 1) {
+                                // A = w_out . h_L; Delta_L = w_out (1 - t_L^2)
+                                float d[8];
+                                const float* wo = swout + gc;
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) {
+                                    apart = fmaf(wo[i], h[i], apart);
+                                    d[i] = wo[i] * (1.0f - t[i] * t[i]);
+                                }
+                                store_a8(Abuf, row, gc, ebn, d);
+                            } else {
+                                store_a8(Abuf, row, gc, ebn, h);
+                            }
+                        } else if (l == L - 1) {
+                            float t[8], d[8];
+                            unpack_bf16x8(tw, t);
+                            const float* wo = swout + gc;
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                apart = fmaf(wo[i], t[i], apart);
+                                d[i] = wo[i] * (1.0f - t[i] * t[i]);
+                            }
+                            store_a8(Abuf, row, gc, ebn, d);
+                        } else if (ebn == 2) {
+                            *reinterpret_cast<uint4*>(Abuf + a_off(row, gc)) = tw;
+                        } else {
+                            float t[8];
+                            unpack_bf16x8(tw, t);
+                            store_a8(Abuf, row, gc, ebn, t);
+                        }
+                    } else if (l > 0) {
+                        // G_{l-1} -> Delta_{l-1} = G (1 - t_{l-1}^2); with a residual,
+                        // G_{l-1} = W_l^T Delta_l + dA/dh_l first
+                        float t[8], d[8];
+                        unpack_bf16x8(tcur[k], t);
+                        if (res_bwd) {
+                            float gl[8];
+                            if (l == L - 1) {
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) gl[i] = swout[gc + i];
+                            } else {
+                                gl[0] = rprev[k][0].x; gl[1] = rprev[k][0].y; gl[2] = rprev[k][0].z; gl[3] = rprev[k][0].w;
+                                gl[4] = rprev[k][1].x; gl[5] = rprev[k][1].y; gl[6] = rprev[k][1].z; gl[7] = rprev[k][1].w;
+                            }
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) gl[i] += acc[k][i];
+                            if (res_st) {
+                                float4* rs = reinterpret_cast<float4*>(rsave_tile + ts_off(0, row, gc, H));
+                                rs[0] = make_float4(gl[0], gl[1], gl[2], gl[3]);
+                                rs[1] = make_float4(gl[4], gl[5], gl[6], gl[7]);
+                            }
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) d[i] = gl[i] * (1.0f - t[i] * t[i]);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) d[i] = acc[k][i] * (1.0f - t[i] * t[i]);
+                        }
+                        store_a8(Abuf, row, gc, ebn, d);
+                    } else if (valid) {
+                        // G_0 = dA/du: dA/ds_j = -sin s_j g[2j] + cos s_j g[2j+1]
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) {
+                            const int j = gc / 2 + p;
+                            if (2 * j < P.D) {
+                                const float cs = __ldg(P.u + (size_t)wg * P.D + 2 * j);
+                                const float sn = __ldg(P.u + (size_t)wg * P.D + 2 * j + 1);
+                                P.gradA[((size_t)m * P.W + wg) * P.C + j] = -sn * acc[k][2 * p] + cs * acc[k][2 * p + 1];
+                            }
+                        }
+                    }
+                }
+                if (fwd && l == L - 1) P.qsave[qs_off(m, tile, gr >> 1, row, P.ntiles)] = apart;
+            }
+            if (g < G - 1) {
+                // columns N .. kpn - 1 are K padding of the next GEMM: zero
+                for (int gc = N + 8 * sub; gc < kpn; gc += 32) zero_a8(Abuf, row, gc, ebn);
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&S.a_full));
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&S.acc_empty[b]));
+        }
+    }
+    fence_before();
+    __syncthreads();
+    // member value A = w_out . h_L + b_out: the 16-column partials in column order
+    if (warp >= EPI_WARP0 && warp < EPI_WARP0 + 4) {
+        const int row = (warp & 3) * 32 + lane;
+        const int wg = tile * 128 + row;
+        if (wg < P.W && !S.abort_flag) P.Apart[(size_t)m * P.W + wg] = member_value(P, m, tile, row);
+    }
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)P.tmem_cols)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+size_t rid_mlp_tc_wide_smem_bytes(const TcArgs& P) {
+    return 1024 + (size_t)P.Kpmax * 256u + (size_t)P.stages * P.stage_bytes + sizeof(float) * (size_t)(P.L + 1) * P.H;
+}
+
+cudaError_t rid_launch_mlp_tc_wide(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, cudaStream_t s) {
+    if (P.ngemm != P.L && P.ngemm != 2 * P.L) return cudaErrorInvalidValue;
+    if (P.resnet && !P.rsave) return cudaErrorInvalidValue;
+    const size_t smem = rid_mlp_tc_wide_smem_bytes(P);
+    const int v = (P.geb[0] == 1 ? 1 : 0) + (P.resnet ? 2 : 0);
+    static size_t attr[4][64] = {};   // shared memory opted into, per instantiation and device
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    size_t& have = attr[v][dev & 63];
+    auto kern = v == 0 ? k_mlp_tc_wide<false, false> : v == 1 ? k_mlp_tc_wide<true, false>
+              : v == 2 ? k_mlp_tc_wide<false, true> : k_mlp_tc_wide<true, true>;
+    if (smem > have) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        have = smem;
+    }
+    kern<<<dim3(P.ntiles, P.M, 1), NTHREADS, smem, s>>>(P, big, small);
+    return cudaGetLastError();
+}

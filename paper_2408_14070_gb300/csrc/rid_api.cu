@@ -92,6 +92,13 @@ struct TcVariant {
     int gN[2 * RID_MAX_LAYERS] = {0}, gKp[2 * RID_MAX_LAYERS] = {0}, geb[2 * RID_MAX_LAYERS] = {0};
     DevBuf blob, wscale;
     CUtensorMap big{}, small{};
+    // cluster variant (k_mlp_tc_cluster): each GEMM's output columns split over
+    // csize = 2 or 4 CTAs; index 1 = two CTAs, 2 = four.  The cluster size in use
+    // is chosen by timing the force evaluation at each new walker count.
+    bool cl_ok[3] = {false, false, false};
+    int cl_stages[3] = {0, 0, 0}, cl_acc_cols[3] = {0, 0, 0}, cl_tmem_cols[3] = {0, 0, 0};
+    unsigned cl_stage_bytes[3] = {0, 0, 0};
+    int csize = 1, cs_W = -1;
 };
 
 struct rid_system {
@@ -106,7 +113,7 @@ struct rid_system {
     DevBuf d_W, d_WT, d_b, d_wout, d_bout;
     TcVariant tcv;
     int Dp = 0;
-    DevBuf tsave, rsave, d_err;   // rsave: FP32 residual stream of the tensor-core kernel (resnet)
+    DevBuf tsave, rsave, qsave, d_err;   // rsave: FP32 residual stream of the tensor-core kernel (resnet)
     // state
     int cap = 0;
     DevBuf x, v, f, fff, s, J, u, gradA, Aval, eps, hs, eff, flags;
@@ -122,6 +129,8 @@ struct rid_system {
     // graph replay: the Philox step index is read from a device base
     DevBuf d_stepbase;
     bool graph_mode = false;
+    bool tuning = false;       // inside the cluster-size tuner
+    int cs_force = 0;          // cluster size fixed by rid_set_mlp_cluster (0: tuned)
     // the force field runs on a side stream, concurrently with the ensemble kernel
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -212,6 +221,7 @@ static int ensure_state(rid_system* sys, int W) {
             const size_t ntiles = (size_t)(W + 127) / 128;
             TRY(sys->tsave.ensure((size_t)E.M * ntiles * E.L * 128 * E.H * sizeof(__nv_bfloat16)));
             if (E.resnet) TRY(sys->rsave.ensure((size_t)E.M * ntiles * 128 * E.H * sizeof(float)));
+            TRY(sys->qsave.ensure((size_t)E.M * ntiles * TC_MAX_QSLICES * 128 * sizeof(float)));
         }
     }
     if (W > sys->cap) sys->cap = W;
@@ -248,6 +258,7 @@ static void destroy_all(rid_system* sys) {
     sys->tcv.blob.release();
     sys->tsave.release();
     sys->rsave.release();
+    sys->qsave.release();
     sys->d_err.release();
     for (auto& r : sys->prof_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     sys->prof_recs.clear();
@@ -437,6 +448,27 @@ static int build_tc_variant(rid_system* sys, const std::vector<float>& W, long l
     V.nacc = 2 * V.acc_cols <= 512 ? 2 : 1;
     V.tmem_cols = 32;
     while (V.tmem_cols < V.nacc * V.acc_cols) V.tmem_cols *= 2;
+    // cluster variants: two operand buffers, each CTA streams n_s = N / S
+    // (rounded up to 16) rows of every weight chunk
+    for (int k = 1; k <= 2; ++k) {
+        const int cs = 1 << k;
+        int nsl = 0;
+        for (int g = 0; g < G; ++g) {
+            const int ns = ((V.gN[g] + cs - 1) / cs + 15) / 16 * 16;
+            if (ns > nsl) nsl = ns;
+        }
+        const size_t fixc = 1024 + 2 * (size_t)V.Kpmax * 256u + sizeof(float) * (size_t)(L + 1) * H;
+        const unsigned sb = (unsigned)nsl * 128u;
+        V.cl_ok[k] = fixc + 2 * (size_t)sb <= budget && nsl <= 256;
+        if (!V.cl_ok[k]) continue;
+        V.cl_stage_bytes[k] = sb;
+        V.cl_stages[k] = (int)std::min<size_t>((budget - fixc) / sb, TC_MAX_STAGES);
+        V.cl_acc_cols[k] = (nsl + 31) / 32 * 32;
+        V.cl_tmem_cols[k] = 32;
+        while (V.cl_tmem_cols[k] < 2 * V.cl_acc_cols[k]) V.cl_tmem_cols[k] *= 2;
+    }
+    V.cs_W = -1;
+    V.csize = 1;
     // pre-swizzled byte image: per GEMM, per 128-byte K-chunk, N rows of 128 bytes
     std::vector<uint8_t> img((size_t)M * rows * 128, 0);
     std::vector<float> scale((size_t)M * G, 1.0f);
@@ -644,9 +676,13 @@ static int ensure_side(rid_system* sys) {
 // SM's shared memory) is launched first on the caller's stream so that it is
 // dispatched as soon as k_head ends, and the force field runs concurrently on
 // a side stream over the remaining SMs; the caller's stream then waits for it.
+static int tune_cluster(rid_system* sys, int W, bool energy, cudaStream_t st);
+
 static int launch_forces(rid_system* sys, int W, int mode, bool energy, cudaStream_t st) {
     StateDev sd = state_view(sys);
     sd.W = W;
+    if (mode == 1 && sys->precision != RID_PREC_FP32 && sys->tcv.cs_W != W && !sys->tuning && !sys->cs_force)
+        TRY(tune_cluster(sys, W, energy, st));
     if (mode != 1) {
         TRY(timed_launch(sys, "k_ff", st, [&] { rid_launch_ff(sys->S, sd, W, energy, st); }));
         CK(cudaGetLastError());
@@ -661,6 +697,81 @@ static int launch_forces(rid_system* sys, int W, int mode, bool energy, cudaStre
     CK(cudaEventRecord(sys->ev_join, fs));
     CK(cudaStreamWaitEvent(st, sys->ev_join, 0));
     CK(cudaGetLastError());
+    return RID_OK;
+}
+
+// The one-CTA ensemble kernel: chunk-interleaved epilogue when the TMEM
+// accumulator is double buffered (width <= 256), the contiguous-column
+// epilogue of k_mlp_tc_wide when a single accumulator fills TMEM.
+static cudaError_t launch_tc1(const TcArgs& P, const TcVariant& V, cudaStream_t st) {
+    return V.nacc == 1 ? rid_launch_mlp_tc_wide(P, V.big, V.small, st) : rid_launch_mlp_tc(P, V.big, V.small, st);
+}
+
+// Cluster size used before the tuner has timed a walker count: the largest
+// of 4 and 2 whose grid (tiles x members x size) still fits the 152 SMs once,
+// else 1 (k_mlp_tc, one CTA per tile and member).
+static int default_cluster(const TcVariant& V, int ctas) {
+    if (V.cl_ok[2] && ctas * 4 <= 152) return 4;
+    if (V.cl_ok[1] && ctas * 2 <= 152) return 2;
+    return 1;
+}
+
+// Autotuner of the ensemble kernel's cluster size: at the first ensemble
+// force evaluation with a new walker count, the whole concurrent phase (the
+// ensemble kernel on the caller's stream, the force field beside it) is timed
+// with each eligible cluster size (1, 2, 4; one warm-up and three timed
+// evaluations each) and the fastest is kept.  Splitting the columns over more
+// CTAs shortens the ensemble's chain but takes SMs from the force field, so
+// the choice is made on the phase, not on the ensemble kernel alone.  Every
+// candidate computes the same quantities; the outputs of the last evaluation
+// are the ones left in place.  Skipped while the stream is being captured.
+static int tune_cluster(rid_system* sys, int W, bool energy, cudaStream_t st) {
+    TcVariant& V = sys->tcv;
+    const int ctas = (W + 127) / 128 * sys->E.M;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs));
+    std::vector<int> cand = {1};
+    if (V.cl_ok[1]) cand.push_back(2);
+    if (V.cl_ok[2]) cand.push_back(4);
+    if (cs != cudaStreamCaptureStatusNone || cand.size() == 1) {
+        V.csize = cs != cudaStreamCaptureStatusNone ? default_cluster(V, ctas) : 1;
+        V.cs_W = W;
+        return RID_OK;
+    }
+    sys->tuning = true;
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    float best = 1e30f;
+    int pick = 1;
+    for (int c : cand) {
+        V.csize = c;
+        V.cs_W = W;
+        int rc = launch_forces(sys, W, 1, energy, st);
+        if (rc == RID_OK) {
+            CK(cudaEventRecord(a, st));
+            for (int r = 0; r < 3 && rc == RID_OK; ++r) rc = launch_forces(sys, W, 1, energy, st);
+            CK(cudaEventRecord(b, st));
+        }
+        if (rc != RID_OK) {
+            sys->tuning = false;
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            return rc;
+        }
+        CK(cudaEventSynchronize(b));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    sys->tuning = false;
+    V.csize = pick;
+    V.cs_W = W;
     return RID_OK;
 }
 
@@ -684,9 +795,9 @@ static int tune_tc_stages(rid_system* sys, TcArgs P, cudaStream_t st) {
     int pick = V.max_stages;
     for (int ns = 2; ns <= V.max_stages; ++ns) {
         P.stages = ns;
-        CK(rid_launch_mlp_tc(P, V.big, V.small, st));
+        CK(launch_tc1(P, V, st));
         CK(cudaEventRecord(a, st));
-        for (int r = 0; r < 3; ++r) CK(rid_launch_mlp_tc(P, V.big, V.small, st));
+        for (int r = 0; r < 3; ++r) CK(launch_tc1(P, V, st));
         CK(cudaEventRecord(b, st));
         CK(cudaEventSynchronize(b));
         float ms = 0.f;
@@ -725,12 +836,28 @@ static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_
         }
         P.wscale = V.wscale.as<float>();
         P.resnet = E.resnet;
+        P.qsave = sys->qsave.as<float>();
         P.rsave = E.resnet ? sys->rsave.as<float>() : nullptr;
         P.ngemm = values_only ? E.L : 2 * E.L;
         cudaError_t le = cudaSuccess;
-        if (V.tuned_W != W) TRY(tune_tc_stages(sys, P, st));
-        P.stages = V.stages;
-        TRY(timed_launch(sys, "k_mlp_tc", st, [&] { le = rid_launch_mlp_tc(P, V.big, V.small, st); }));
+        const int cs = sys->cs_force ? sys->cs_force : V.cs_W == W ? V.csize : default_cluster(V, P.ntiles * E.M);
+        if (cs > 1 && !V.cl_ok[cs == 2 ? 1 : 2])
+            return fail(RID_ERR_ARG, "ensemble kernel: cluster size %d does not fit this ensemble's shape", cs);
+        if (cs == 1) {
+            if (V.tuned_W != W) TRY(tune_tc_stages(sys, P, st));
+            P.stages = V.stages;
+            P.csize = 1;
+            TRY(timed_launch(sys, "k_mlp_tc", st, [&] { le = launch_tc1(P, V, st); }));
+        } else {
+            const int k = cs == 2 ? 1 : 2;
+            P.csize = cs;
+            P.stages = V.cl_stages[k];
+            P.stage_bytes = V.cl_stage_bytes[k];
+            P.acc_cols = V.cl_acc_cols[k];
+            P.tmem_cols = V.cl_tmem_cols[k];
+            P.nacc = 2;
+            TRY(timed_launch(sys, "k_mlp_tc", st, [&] { le = rid_launch_mlp_tc_cluster(P, V.big, V.small, st); }));
+        }
         if (le != cudaSuccess) return fail(RID_ERR_CUDA, "k_mlp_tc launch: %s", cudaGetErrorString(le));
         E.aslices = 1;
     } else if (mode == 1) {
@@ -958,7 +1085,7 @@ size_t rid_sys_footprint(const rid_system* sys, int W) {
         const EnsDev& E = sys->E;
         b += (size_t)E.M * nc * 4 + (size_t)E.M * W * 4;
         if (sys->precision == RID_PREC_FP32) b += rid_mlp_fp32_scratch_floats(W, E.M, E.L, E.H) * 4;
-        else b += (size_t)E.M * ((W + 127) / 128) * 128 * E.H * (E.L * 2 + (E.resnet ? 4 : 0));
+        else b += (size_t)E.M * ((W + 127) / 128) * 128 * (E.H * (E.L * 2 + (E.resnet ? 4 : 0)) + TC_MAX_QSLICES * 4);
     }
     return b;
 }
@@ -1018,6 +1145,14 @@ extern "C" int rid_profile_read(rid_system* sys, int32_t max_kernels, char* name
 }
 
 extern "C" int64_t rid_launch_count(rid_system* sys) { return sys ? sys->launches : -1; }
+
+extern "C" int rid_set_mlp_cluster(rid_system* sys, int32_t csize) {
+    if (!sys) return fail(RID_ERR_ARG, "NULL system");
+    if (csize != 0 && csize != 1 && csize != 2 && csize != 4)
+        return fail(RID_ERR_ARG, "cluster size %d: expected 0 (tuned), 1, 2 or 4", csize);
+    sys->cs_force = csize;
+    return RID_OK;
+}
 
 extern "C" int rid_explore(rid_system* sys, int32_t W, const float* x0, const float* v0, uint64_t step0,
                            int64_t n_steps, float* cv_out, float* eps_out, double* energy_out, float* x_out,

@@ -9,6 +9,7 @@
 
 #define TC_MAX_STAGES 8
 #define TC_MAX_KCHUNKS 8   // 128-byte K-chunks of the widest GEMM (K <= 512 BF16)
+#define TC_MAX_QSLICES 32  // 16-column slices of the widest hidden layer (512)
 
 // Weight image, per member: for GEMM g (forward layers 0..L-1, then backward
 // layers L-1..0) and K-chunk c (128 bytes of K: 64 BF16 or 128 FP8 e4m3
@@ -28,6 +29,7 @@ struct TcArgs {
     __nv_bfloat16* tsave;    // [M][ntiles][L][128][H] tanh(z_l), BF16
     float* gradA;            // [M][W][C]
     float* Apart;            // [M][W] member value
+    float* qsave;            // [M][ntiles][TC_MAX_QSLICES][128] partial member values per 16-column slice
     int* err;                // error word (bounded-wait expiry codes)
     long long member_rows;   // 128-byte rows per member image
     long long grow[2 * RID_MAX_LAYERS];          // first row of GEMM g within a member image
@@ -36,9 +38,15 @@ struct TcArgs {
     const float* wscale;     // [M][2L] weight scale of every GEMM (1 for BF16)
     int resnet;              // h_l = h_{l-1} + tanh(z_l) for l >= 1
     float* rsave;            // resnet: [M][ntiles][H/8][128][8] FP32, h_l forward, dA/dh_l backward
+    int csize;               // cluster variant: CTAs splitting each GEMM's output columns (2 or 4)
     int ngemm;               // GEMMs to run: 2L (forward and input gradient) or L (forward only:
                              // member values, gradA untouched)
 };
 
 size_t rid_mlp_tc_smem_bytes(const TcArgs& P);
 cudaError_t rid_launch_mlp_tc(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, cudaStream_t s);
+size_t rid_mlp_tc_wide_smem_bytes(const TcArgs& P);
+cudaError_t rid_launch_mlp_tc_wide(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, cudaStream_t s);
+size_t rid_mlp_tc_cluster_smem_bytes(const TcArgs& P);
+cudaError_t rid_launch_mlp_tc_cluster(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small,
+                                      cudaStream_t s);

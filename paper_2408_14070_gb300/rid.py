@@ -29,7 +29,7 @@ EXPORTS = ("rid_version", "rid_status_string", "rid_last_error", "rid_create_sys
            "rid_server_destroy", "rid_label_batch", "rid_submit", "rid_poll", "rid_server_load",
            "rid_trainer_create", "rid_trainer_destroy", "rid_trainer_set_data", "rid_trainer_run",
            "rid_trainer_grad", "rid_trainer_weights", "rid_mcmc", "rid_select",
-           "rid_label_constrained", "rid_mcmc_system")
+           "rid_label_constrained", "rid_mcmc_system", "rid_set_mlp_cluster")
 RID_NOT_READY = 6
 RID_JOB_LABEL, RID_JOB_EXPLORE = 1, 2
 
@@ -141,6 +141,7 @@ def lib() -> C.CDLL:
     L.rid_profile_enable.argtypes = [vp, i32]
     L.rid_profile_read.argtypes = [vp, i32, C.c_char_p, C.POINTER(C.c_double), C.POINTER(i64), C.POINTER(i32)]
     L.rid_launch_count.argtypes = [vp]
+    L.rid_set_mlp_cluster.argtypes = [vp, i32]
     L.rid_ensemble_grad_noalloc.argtypes = [i32, i32, vp, i32, i32, i32, i32, vp, vp, vp, vp]
     L.rid_server_create.argtypes = [u64, C.POINTER(vp)]
     L.rid_server_destroy.argtypes = [vp]
@@ -389,6 +390,10 @@ class System:
 
     def launch_count(self):
         return int(lib().rid_launch_count(self.h))
+
+    def set_mlp_cluster(self, csize):
+        """Cluster size of the tensor-core ensemble kernel: 0 tuned, 1, 2 or 4."""
+        _check(lib().rid_set_mlp_cluster(self.h, int(csize)))
 
     def pair_mask(self, x, mask_out, stream=None):
         W = int(x.shape[0])

@@ -244,3 +244,73 @@ def test_tensor_core_limits(R, orc, prec, n, C, W, M, L, H, seed):
         assert np.linalg.norm(fbar - ref) <= tol * np.linalg.norm(ref) + 1e-4, w
         assert abs(eps[w] - e["eps"]) <= EPS_TOL * scale * abs(e["eps"]) + 1e-3, w
     assert np.all(np.isfinite(f))
+
+
+# The ensemble kernel's cluster variants (each GEMM's output columns split over
+# 2 or 4 CTAs, the next operand exchanged through distributed shared memory)
+# must give the same bits as the one-CTA kernel; the autotuner may pick any.
+CLUSTER_CASES = [
+    (200, 20, 300, 4, 4, 256, False, 1),   # the benchmark's ensemble, ragged walker count
+    (120, 18, 200, 4, 4, 300, True, 21),   # the paper's residual network: 80- and 160-column slices
+    (60, 9, 130, 3, 3, 96, True, 22),      # 48-column slices at S = 2; 32, 32, 32 and none at S = 4
+    (22, 2, 16, 4, 3, 64, False, 2),       # last GEMM N = 64 (D = 4 padded): 16-column slices at S = 4
+    (150, 64, 100, 2, 2, 32, False, 32),   # 128 inputs, width 32: an operand buffer reused at a narrower K
+    (40, 8, 700, 2, 2, 32, False, 33),     # width 32 at S = 4: two CTAs with 16 columns, two with none
+]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("n,C,W,M,L,H,resnet,seed", CLUSTER_CASES)
+def test_cluster_sizes_give_identical_bits(R, orc, prec, n, C, W, M, L, H, resnet, seed):
+    sp = I.make_system(n, C, seed)
+    x = I.make_chains(W, sp, seed)
+    ens = I.make_ensemble(M, 2 * C, L, H, seed, resnet=resnet)
+    eps_r = np.array([orc.ensemble(ens, orc.cvs(sp, x[w].astype(np.float64))[0])["eps"] for w in range(0, W, 7)])
+    ens.trust_lo, ens.trust_hi = float(np.percentile(eps_r, 25)), float(np.percentile(eps_r, 75))
+    p = R.RID_PREC_BF16 if prec == "bf16" else R.RID_PREC_FP8
+    outs = {}
+    for cs in (1, 2, 4):
+        f = np.zeros((W, n, 3), np.float32)
+        eps = np.zeros(W, np.float32)
+        abar = np.zeros(W, np.float32)
+        g = np.zeros((M, W, C), np.float32)
+        with R.System(sp) as sysobj:
+            sysobj.set_ensemble(ens, precision=p)
+            sysobj.set_mlp_cluster(cs)
+            sysobj.eval_forces(x, R.RID_BIAS_ENSEMBLE, f_out=f, eps_out=eps, abar_out=abar, grad_out=g)
+            xo = np.zeros_like(x[:9])
+            sysobj.explore(np.ascontiguousarray(x[:9]), 6, x_out=xo)
+        outs[cs] = (f, eps, abar, g, xo)
+    for cs in (2, 4):
+        for a, b in zip(outs[cs], outs[1]):
+            assert np.array_equal(a, b), cs
+    # and the shared result is the oracle's within the precision's bound
+    f, eps, abar, g, _ = outs[4]
+    tol = GRAD_TOL if prec == "bf16" else 6e-2
+    for w in sorted(set([0, W // 2, W - 1])):
+        e = orc.ensemble(ens, orc.cvs(sp, x[w].astype(np.float64))[0])
+        fbar = g[:, w].astype(np.float64).mean(axis=0)
+        assert normwise(fbar, e["gradA"].mean(axis=0)) < tol, w
+        if prec == "bf16":
+            # (FP8 member values carry the e4m3 forward error; they are checked
+            # through the MCMC sampling tests)
+            assert abs(abar[w] - e["Abar"]) <= tol * (abs(e["Abar"]) + 0.1), w
+
+
+def test_cluster_size_argument_errors(R):
+    sp = I.make_system(22, 2, 1)
+    with R.System(sp) as sysobj:
+        with pytest.raises(R.RidError) as e:
+            sysobj.set_mlp_cluster(3)
+        assert e.value.code == R.RID_ERR_ARG
+        # width 512 with 256 inputs: two operand buffers do not fit shared memory
+        sp2 = I.make_system(140, 128, 2)
+        with R.System(sp2) as s2:
+            s2.set_ensemble(I.make_ensemble(2, 256, 2, 512, 2), precision=R.RID_PREC_BF16)
+            s2.set_mlp_cluster(4)
+            x = I.make_chains(3, sp2, 2)
+            with pytest.raises(R.RidError) as e:
+                s2.eval_forces(x, R.RID_BIAS_ENSEMBLE, f_out=np.zeros((3, 140, 3), np.float32))
+            assert e.value.code == R.RID_ERR_ARG
+            s2.set_mlp_cluster(0)
+            s2.eval_forces(x, R.RID_BIAS_ENSEMBLE, f_out=np.zeros((3, 140, 3), np.float32))
