@@ -602,9 +602,12 @@ RID_API int rid_server_load(rid_server* srv, int32_t* queued, int32_t* running, 
 /*
  * Ensemble member gradients with no device allocation.  The paper has no
  * counterpart: this is a library facility for callers that cannot allocate
- * device memory (a framework that owns all device memory through its own pool,
- * code between the start and end of a stream capture that must not allocate,
- * an embedding that forbids allocation after start-up).
+ * device memory.  Two kinds of caller need it: a host framework that hands
+ * out all device memory from its own pool (a cudaMalloc behind its back is
+ * memory its accounting does not see, and fails once the pool has reserved
+ * the device), and an embedding that forbids allocation after start-up
+ * (cudaMalloc can synchronise the device and take unbounded time, which a
+ * latency-bound or certified code path cannot allow).
  *
  * For P points s [P][C] (device, float32, radians) and the packed ensemble
  * `weights` [M][Pw] (device, float32, the layout of rid_ensemble_desc.weights,

@@ -1,10 +1,11 @@
 // k_noalloc.cu -- ensemble member gradients without any device allocation.
 //
 // For callers that cannot allocate device memory themselves or through the
-// library (for example code running inside a stream capture that must not
-// allocate, a host framework that owns all device memory through its own
-// pool, or an embedding where the first allocation after start-up is not
-// allowed), rid_ensemble_grad_noalloc evaluates the ensemble on caller-given
+// library -- a host framework that hands out all device memory from its own
+// pool (an allocation behind its back escapes its accounting and fails once
+// the pool has reserved the device), or an embedding that forbids allocation
+// after start-up (cudaMalloc can synchronise the device and take unbounded
+// time) -- rid_ensemble_grad_noalloc evaluates the ensemble on caller-given
 // CV points with caller-given device arrays only.  The one piece of scratch the
 // computation needs -- the tanh activations of every hidden layer, kept for
 // the reverse pass -- lives in a file-scope static device array of fixed size
@@ -12,7 +13,10 @@
 //
 // The arithmetic is the FP32 SIMT ensemble kernel's (same tiles, same
 // summation order), reading the weights straight from the packed model layout
-// instead of the library's transposed device copies.
+// instead of the library's transposed device copies.  That costs speed in the
+// forward pass: the lanes of a warp read weights of different output units,
+// K floats apart, so every weight load touches 32 sectors; the entry point is
+// therefore several times slower than the ensemble stage of rid_eval_forces.
 #include <mutex>
 
 #include "rid_internal.cuh"

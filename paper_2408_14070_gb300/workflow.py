@@ -9,10 +9,13 @@ Readings, where the paper leaves the cycle to its workflow engine:
   * exploration runs in chunks of `chunk` steps (a multiple of the system's
     output_freq); the configuration at the end of every chunk is a frame,
     with the CVs and model deviation of that step;
-  * the first iteration has no model, so its exploration is unbiased and
-    every frame is a selection candidate (the trust window is unbounded);
-  * a label is kept when the standard deviation of each of its CV components
-    is at most std_threshold (LabelMDConfig);
+  * a first iteration without a model (no `weights` given) explores
+    unbiased and takes every frame as a selection candidate (the trust window
+    is unbounded); with `weights` given, the first iteration already explores
+    with that ensemble's bias and its trust window;
+  * a label is kept when the standard deviation of each of its mean-force
+    components (kappa times the CV offset from the restraint centre) is at
+    most std_threshold (LabelMDConfig; a mean-force threshold);
   * labeling runs n_steps with the first tenth as equilibration and 20
     blocks for the standard error (the restrained-label readings);
   * each iteration trains from the current weights with fresh Adam moments,
@@ -57,6 +60,7 @@ def run(cfg, sp: I.SystemParams, x0: np.ndarray, weights: np.ndarray | None = No
         raise ValueError(f"x0 holds {W} walkers, numb_walkers is {c.n_walkers}")
     t = c.train
     D, L, H, M = 2 * C, t["n_layers"], t["width"], t["n_models"]
+    biased_first = weights is not None        # a given ensemble biases the first iteration too
     if weights is None:
         weights = I.make_ensemble(M, D, L, H, seed, resnet=t["resnet"]).weights
     weights = np.ascontiguousarray(weights, dtype=np.float32)
@@ -74,7 +78,7 @@ def run(cfg, sp: I.SystemParams, x0: np.ndarray, weights: np.ndarray | None = No
     with rid.System(sp) as s:
         for it in range(n_iters if n_iters is not None else c.n_iters):
             rec = {"iteration": it}
-            have_model = it > 0
+            have_model = it > 0 or biased_first
             if have_model:
                 s.set_ensemble(I.EnsembleParams(M, D, L, H, t["resnet"], weights, c.trust_lo, c.trust_hi),
                                precision=precision)

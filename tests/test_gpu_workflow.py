@@ -1,6 +1,6 @@
 """Two iterations of the RiD cycle through workflow.run from a RiD-style
-configuration: the first iteration explores without a model and takes every
-frame as a candidate, the labels it keeps train the ensemble, and the second
+configuration: the first iteration explores without a model (none given) and
+takes every frame as a candidate, the labels it keeps train the ensemble, and the second
 explores with the trained ensemble.  Checked against each phase's
 definition: frame counts, selections within max_selection, labels kept by
 the std threshold, the training loss falling, and the trained weights
@@ -37,8 +37,8 @@ def test_two_iterations_of_the_cycle(R):
     c = K.load(CFG, reduced=True)
     sp = I.make_system(22, c.n_cv, 3, output_freq=50)
     x0 = I.make_chains(16, sp, 3)
-    w0 = I.make_ensemble(3, 4, 2, 32, 1).weights
-    res = workflow.run(c, sp, x0, weights=w0, seed=1)
+    w0 = I.make_ensemble(3, 4, 2, 32, 1).weights        # the seeded start run() draws with seed = 1
+    res = workflow.run(c, sp, x0, seed=1)
     it0, it1 = res.iterations
     assert it0["frames"] == it1["frames"] == 16 * 8            # one frame per 50-step chunk and walker
     assert it0["eps_mean"] == 0.0 and it1["eps_mean"] > 0.0    # no model first, the trained ensemble next
@@ -48,3 +48,15 @@ def test_two_iterations_of_the_cycle(R):
     assert it0["loss_last"] < 0.5 * it0["loss_first"]
     assert not np.array_equal(res.weights, w0) and np.all(np.isfinite(res.weights))
     assert np.all(np.isfinite(res.x))
+
+
+def test_a_given_ensemble_biases_the_first_iteration(R):
+    """Restarting from a trained ensemble: the first iteration explores with
+    its bias and trust window instead of unbiased."""
+    from paper_2408_14070_gb300 import workflow
+    c = K.load(CFG, reduced=True)
+    sp = I.make_system(22, c.n_cv, 3, output_freq=50)
+    x0 = I.make_chains(16, sp, 3)
+    w0 = I.make_ensemble(3, 4, 2, 32, 5).weights
+    res = workflow.run(c, sp, x0, weights=w0, n_iters=1, seed=2)
+    assert res.iterations[0]["eps_mean"] > 0.0

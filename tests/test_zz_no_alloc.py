@@ -1,8 +1,8 @@
 """rid_ensemble_grad_noalloc (member gradients with static scratch, no device
-allocation) against the FP32 ensemble path of rid_eval_forces.
-
-Both compute dA_i/ds with the same FP32 SIMT arithmetic; the bound is the
-FP32 parity tolerance of the force tests (1e-5 normwise per point).
+allocation): checked against the FP64 oracle directly (member gradients and
+member values at every point, 1e-5 relative, the FP32 parity tolerance of the
+force tests) and against the FP32 ensemble path of rid_eval_forces, on two
+calls in a row.
 """
 import numpy as np
 import pytest
@@ -62,7 +62,20 @@ def check(ref_s, ref_g, ref_abar, g, v):
     np.testing.assert_allclose(v.mean(axis=0), ref_abar, rtol=TOL, atol=TOL)
 
 
-def test_two_calls_in_a_row_match_eval_forces(env):
+def check_oracle(orc, ens, s, g, v):
+    """Every point against the FP64 oracle at the same (FP32) CV values:
+    dA_i/ds normwise within 1e-5, A_i within 1e-5 (|A_i| + 1)."""
+    sd = s.astype(np.float64)
+    for p in range(s.shape[0]):
+        e = orc.ensemble(ens, sd[p])
+        u = np.stack([np.cos(sd[p]), np.sin(sd[p])], axis=1).ravel()
+        for m in range(ens.n_models):
+            assert normwise(g[m, p], e["gradA"][m]) < TOL, (p, m)
+            A, _ = orc.mlp(ens, m, u)
+            assert abs(v[m, p] - A) <= TOL * (abs(A) + 1.0), (p, m)
+
+
+def test_two_calls_in_a_row_match_the_oracle_and_eval_forces(env, orc):
     rid, torch = env
     sp = I.make_system(200, 20, 11)
     ens = I.make_ensemble(4, 40, 4, 256, 11)
@@ -72,6 +85,8 @@ def test_two_calls_in_a_row_match_eval_forces(env):
     rb = reference(rid, sp, ens, xb)
     ga, va = run_noalloc(rid, torch, ens, ra[0])
     gb, vb = run_noalloc(rid, torch, ens, rb[0])
+    check_oracle(orc, ens, ra[0], ga, va)
+    check_oracle(orc, ens, rb[0], gb, vb)
     check(*ra, ga, va)
     check(*rb, gb, vb)
     # the scratch keeps the second call's contents: repeating the first call
@@ -80,13 +95,14 @@ def test_two_calls_in_a_row_match_eval_forces(env):
     assert np.array_equal(ga, ga2) and np.array_equal(va, va2)
 
 
-def test_residual_net_and_narrow_shape(env):
+def test_residual_net_and_narrow_shape(env, orc):
     rid, torch = env
     sp = I.make_system(60, 9, 13)
     ens = I.make_ensemble(3, 18, 3, 96, 13, resnet=True)
     x = I.make_chains(70, sp, 13)
     r = reference(rid, sp, ens, x)
     g, v = run_noalloc(rid, torch, ens, r[0])
+    check_oracle(orc, ens, r[0], g, v)
     check(*r, g, v)
 
 
