@@ -11,13 +11,21 @@ with CUDA events on the stream the kernels run on.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
                   [--impl ours|reference]
 
-Three more legs on rank 0 (N = 1) go into the same JSON line: "precision"
-(the 8192-walker precision sweep: FP32 / BF16 / FP8 throughput, deviation
-from FP32, NVE drift), "batching"
-(512 uneven restrained labeling jobs in one persistent launch against the
-plain per-job path) and "serving" (a Poisson stream of mixed labeling /
-exploration requests through rid_submit / rid_poll: throughput and p50 / p99
-latency, against the plain FP32 per-job path on the first requests).
+More legs on rank 0 (N = 1) go into the same JSON line: "fp32_plain" (the
+same step with the FP32 SIMT ensemble), "paper_network" (the paper's own
+4 x [300]^4 residual ensemble on 18 torsions: FP32 / BF16 / FP8 and the
+ensemble kernel's roofline at that shape), "tiny" (the 22-bead
+configuration through rid_explore and rid_label), "precision" (the
+8192-walker sweep: FP32 / BF16 / FP8 throughput, ensemble roofline,
+deviation from FP32, NVE drift), "batching" (512 uneven restrained labeling
+jobs in one persistent launch against the per-job path), "training",
+"constrained", "selection", "mcmc", "serving" (a Poisson stream of mixed
+requests through rid_submit / rid_poll at 200/s against the plain FP32
+per-job path) and "serving_sustained" (the same mix at a rate the GPU
+clears).  "cpu_baseline" times the FP64 oracle on the host cores (the
+headline workload, the small configuration, a sample of the precision
+sweep) and gives the precision sweep's errors against the oracle.  The line
+ends with "legs", a short summary of every leg's headline figures.
 
 --impl reference times the FP64 CPU oracle on the host cores (a bounded
 sample of the same workload per step).  Under torchrun every rank runs its
@@ -535,7 +543,7 @@ def run_serving(rid, n_req, rate, plain_req, seed=5):
     for d in plain:
         d["system"].close()
     served_first = {"label": [], "explore": []}
-    for idx in range(min(plain_req, len(served))):
+    for idx in range(min(plain_req, len(served))) if plain else []:
         st, info = out[idx]
         served_first[served[idx]["kind"]].append(info["t_end_ms"] - info["t_submit_ms"])
 
@@ -621,12 +629,17 @@ def run_precision(rid, torch, steps=10, nve_walkers=64, nve_steps=10000, seed=4)
     xd = torch.from_numpy(x0).cuda()
     stream = torch.cuda.current_stream()
     grads = {}
+    sample = {"seed": seed, "walkers": 16, "gpu": {}}
+    flops = mlp_flops_per_walker_step(wl) * W
+    mlp_ms = {}
     for name, prec in (("fp32", rid.RID_PREC_FP32), ("bf16", rid.RID_PREC_BF16), ("fp8", rid.RID_PREC_FP8)):
         with rid.System(sp) as system:
             system.set_ensemble(ens, precision=prec)
             g = torch.zeros((wl["n_models"], W, wl["n_cv"]), dtype=torch.float32, device="cuda")
-            system.eval_forces(xd, rid.RID_BIAS_ENSEMBLE, grad_out=g, stream=stream)
+            ee = torch.zeros(W, dtype=torch.float32, device="cuda")
+            system.eval_forces(xd, rid.RID_BIAS_ENSEMBLE, grad_out=g, eps_out=ee, stream=stream)
             grads[name] = g.mean(dim=0).double()
+            sample["gpu"][name] = (grads[name][:16].cpu().numpy(), ee[:16].double().cpu().numpy())
             system.walkers_load(xd, stream=stream)
             system.walkers_advance(3, stream=stream)
             torch.cuda.synchronize()
@@ -636,6 +649,13 @@ def run_precision(rid, torch, steps=10, nve_walkers=64, nve_steps=10000, seed=4)
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
+            system.profile_enable(True)
+            system.walkers_advance(steps, stream=stream)
+            torch.cuda.synchronize()
+            prof = system.profile_read()
+            system.profile_enable(False)
+            mlp = "k_mlp_tc" if prec != rid.RID_PREC_FP32 else "k_mlp_fp32"
+            mlp_ms[name] = prof[mlp][0] / prof[mlp][1]
             system.walkers_read()
         # NVE drift: gamma = 0, bias on with sigma = 1 (a conservative force)
         spn = I.make_system(wl["n_beads"], wl["n_cv"], seed, output_freq=nve_steps // 100, gamma=0.0)
@@ -654,8 +674,175 @@ def run_precision(rid, torch, steps=10, nve_walkers=64, nve_steps=10000, seed=4)
     for name in ("bf16", "fp8"):
         d = (grads[name] - grads["fp32"]).norm(dim=1) / grads["fp32"].norm(dim=1).clamp_min(1e-30)
         res[name]["mean_force_rel_dev_from_fp32"] = {"median": float(d.median()), "max": float(d.max())}
+        res[name]["roofline"] = tensor_roofline(flops, mlp_ms[name])
+    fp = fp32_peak(torch)[0]
+    res["fp32"]["roofline"] = {"bound": "alu", "kernel": "k_mlp_fp32", "achieved": flops / (mlp_ms["fp32"] / 1e3) / 1e12,
+                               "peak": fp, "unit": "TFLOP/s", "frac": flops / (mlp_ms["fp32"] / 1e3) / 1e12 / fp,
+                               "avg_launch_ms": mlp_ms["fp32"]}
     res["fp8"]["arithmetic"] = "forward GEMMs e4m3 (weights / (amax/448) per matrix), input-gradient GEMMs BF16"
+    res["_sample"] = sample
     return res
+
+
+def _timed_steps(torch, system, xd, stream, steps, flush):
+    """Walker-steps timing of `steps` full steps (each alone between CUDA
+    events, L2 flushed before it) and the per-kernel live times."""
+    system.walkers_load(xd, stream=stream)
+    system.walkers_advance(3, stream=stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        system.walkers_advance(1, stream=stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    system.profile_enable(True)
+    for k in range(steps):
+        flush.zero_()
+        system.walkers_advance(1, stream=stream)
+    torch.cuda.synchronize()
+    prof = system.profile_read()
+    system.profile_enable(False)
+    system.walkers_read()
+    return ms, {k: v[0] / v[1] for k, v in prof.items()}
+
+
+def tensor_roofline(flops, ms):
+    peak = _peaks().get("bf16_tflops") or 1900.0
+    ach = flops / (ms / 1e3) / 1e12
+    return {"bound": "tensor", "kernel": "k_mlp_tc", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "avg_launch_ms": ms,
+            "peak_source": "measured bf16_tflops (burst)" if _peaks().get("bf16_tflops") else "fallback 1.9 PFLOP/s"}
+
+
+def run_paper_network(rid, torch, steps, seed=21):
+    """The paper's own ensemble (Sec. "Training phase": four models, neurons
+    [300, 300, 300, 300], resnet) on 18 torsion CVs (its chignolin example's
+    count) of the 200-bead chain: 1024 walkers, FP32 / BF16 / FP8 steps timed
+    like the headline, the ensemble kernel's roofline at this shape, the
+    deviation of BF16 / FP8 from FP32, and the step time at the paper's 12
+    walkers."""
+    C, M, L, H = 18, 4, 4, 300
+    sp = I.make_system(200, C, seed, output_freq=10)
+    W = 1024
+    x0 = I.make_chains(W, sp, seed)
+    ens = I.make_ensemble(M, 2 * C, L, H, seed, resnet=True)
+    stream = torch.cuda.current_stream()
+    xd = torch.from_numpy(x0).cuda()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    flops = M * 4 * (2 * C * H + (L - 1) * H * H) * W
+    res = {"workload": f"{W} walkers, 200-bead chain, {C} torsion CVs, {M} x MLP {2 * C}-{H}x{L}-1 with residual "
+                       f"connections (the paper's network)"}
+    grads = {}
+    for name, prec in (("fp32", rid.RID_PREC_FP32), ("bf16", rid.RID_PREC_BF16), ("fp8", rid.RID_PREC_FP8)):
+        with rid.System(sp) as system:
+            system.set_ensemble(ens, precision=prec)
+            g = torch.zeros((M, W, C), dtype=torch.float32, device="cuda")
+            system.eval_forces(xd, rid.RID_BIAS_ENSEMBLE, grad_out=g, stream=stream)
+            grads[name] = g.mean(dim=0).double()
+            ms, kern = _timed_steps(torch, system, xd, stream, steps, flush)
+            r = {"value": W * steps / (ms / 1e3), "unit": "walker-steps/s", "ms_per_step": ms / steps,
+                 "kernels_ms": kern}
+            if name != "fp32":
+                r["roofline"] = tensor_roofline(flops, kern["k_mlp_tc"])
+            res[name] = r
+        if name == "bf16":
+            # the paper's walker count: step latency
+            with rid.System(sp) as system:
+                system.set_ensemble(ens, precision=prec)
+                x12 = xd[:12].contiguous()
+                ms12, _ = _timed_steps(torch, system, x12, stream, steps, flush)
+            res["bf16_12_walkers_ms_per_step"] = ms12 / steps
+    for name in ("bf16", "fp8"):
+        d = (grads[name] - grads["fp32"]).norm(dim=1) / grads["fp32"].norm(dim=1).clamp_min(1e-30)
+        res[name]["mean_force_rel_dev_from_fp32"] = {"median": float(d.median()), "max": float(d.max())}
+    res["bf16_speedup_vs_fp32"] = res["bf16"]["value"] / res["fp32"]["value"]
+    return res
+
+
+def run_tiny(rid, torch, seed=1):
+    """The small configuration (22-bead chain, 2 torsion CVs, 4 x MLP
+    4-64x3-1, FP32): 16 biased walkers x 2000 steps through one rid_explore
+    call and 16 restrained runs (kappa 50) x 1000 steps through one rid_label
+    call, device buffers, timed with CUDA events around each call."""
+    wl = I.workload("tiny_n22")
+    sp = I.make_system(wl["n_beads"], wl["n_cv"], seed, output_freq=10)
+    W = 16
+    x0 = torch.from_numpy(I.make_chains(W, sp, seed)).cuda()
+    ens = I.make_ensemble(wl["n_models"], 2 * wl["n_cv"], wl["n_layers"], wl["width"], seed)
+    stream = torch.cuda.current_stream()
+    out = {"workload": "tiny_n22: 22-bead chain, 2 torsion CVs, 4 x MLP 4-64x3-1 (FP32); 16 walkers x 2000 "
+                       "biased steps and 16 restrained runs x 1000 steps"}
+    with rid.System(sp) as system:
+        system.set_ensemble(ens, precision=rid.RID_PREC_FP32)
+        T = 2000 // sp.output_freq
+        cv = torch.zeros((W, T, wl["n_cv"]), device="cuda")
+        eps = torch.zeros((W, T), device="cuda")
+        s0 = torch.from_numpy(I.make_label_targets(W, wl["n_cv"], seed)).cuda()
+        kap = torch.full((W, wl["n_cv"]), 50.0, dtype=torch.float64, device="cuda")
+        mf, se, sd = (torch.zeros((W, wl["n_cv"]), dtype=torch.float64, device="cuda") for _ in range(3))
+        for rep in range(2):          # the first call of each kind warms up
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            system.explore(x0, 2000, cv_out=cv, eps_out=eps, stream=stream)
+            e1.record(stream)
+            system.label(x0, s0, kap, 1000, 100, 20, mf, se, sd, stream=stream)
+            e2.record(stream)
+            torch.cuda.synchronize()
+        out["explore"] = {"value": W * 2000 / (e0.elapsed_time(e1) / 1e3), "unit": "walker-steps/s",
+                          "ms_per_call": e0.elapsed_time(e1)}
+        out["label"] = {"value": W * 1000 / (e1.elapsed_time(e2) / 1e3), "unit": "walker-steps/s",
+                        "ms_per_call": e1.elapsed_time(e2)}
+    return out
+
+
+def cpu_configs(precision_sample):
+    """The oracle on the host cores for the small configuration (all of it) and
+    on a sample of the precision sweep's workload, plus the precision sweep's
+    errors against the oracle on that sample (the GPU mean forces and model
+    deviations of its first walkers, passed in)."""
+    import oracle
+    oracle.build()
+    out = {}
+    wl = I.workload("tiny_n22")
+    sp = I.make_system(wl["n_beads"], wl["n_cv"], 1, output_freq=10)
+    x0 = I.make_chains(16, sp, 1)
+    ens = I.make_ensemble(wl["n_models"], 2 * wl["n_cv"], wl["n_layers"], wl["width"], 1)
+    t0 = time.perf_counter()
+    r = oracle.explore(sp, x0, 2000, ens=ens)
+    t1 = time.perf_counter()
+    oracle.label(sp, x0, I.make_label_targets(16, wl["n_cv"], 1), 50.0, 1000, 100, 20)
+    t2 = time.perf_counter()
+    out["tiny_n22"] = {"explore": {"value": 16 * 2000 / (t1 - t0), "unit": "walker-steps/s"},
+                       "label": {"value": 16 * 1000 / (t2 - t1), "unit": "walker-steps/s"},
+                       "cores": int(r["threads"]), "sample": "all of it: 16 walkers x 2000 steps, 16 runs x 1000"}
+    if precision_sample is not None:
+        wl4 = I.workload("chain_n100_w8192")
+        sp4, x4, ens4 = make_inputs(wl4, precision_sample["seed"])
+        ens4.trust_lo, ens4.trust_hi = 1e9, 2e9
+        n = precision_sample["walkers"]
+        t0 = time.perf_counter()
+        r = oracle.explore(sp4, x4[:64], 4, ens=ens4)
+        dt = time.perf_counter() - t0
+        out["chain_n100_w8192"] = {"value": 64 * 4 / dt, "unit": "walker-steps/s", "cores": int(r["threads"]),
+                                   "sample": "64 walkers x 4 steps"}
+        errs = {}
+        ref_f, ref_e = [], []
+        for w in range(n):
+            e = oracle.ensemble(ens4, oracle.cvs(sp4, x4[w].astype(np.float64))[0])
+            ref_f.append(e["gradA"].mean(axis=0))
+            ref_e.append(e["eps"])
+        ref_f, ref_e = np.array(ref_f), np.array(ref_e)
+        for name, (fbar, eps) in precision_sample["gpu"].items():
+            d = np.linalg.norm(fbar - ref_f, axis=1) / np.linalg.norm(ref_f, axis=1)
+            de = np.abs(eps - ref_e) / np.abs(ref_e)
+            errs[name] = {"mean_force_rel_err": {"median": float(np.median(d)), "max": float(d.max())},
+                          "eps_rel_err": {"median": float(np.median(de)), "max": float(de.max())}}
+        out["precision_errors_vs_oracle"] = dict(errs, sample=f"the first {n} walkers of the precision sweep, "
+                                                                "FP64 oracle at the same positions")
+    return out
 
 
 def rank_seed(rank):
@@ -718,6 +905,43 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def legs_summary(out):
+    """One short object at the end of the line with each leg's headline
+    figures (the full legs precede it)."""
+    def g(*path):
+        v = out
+        for k in path:
+            if not isinstance(v, dict) or k not in v:
+                return None
+            v = v[k]
+        return round(v, 4) if isinstance(v, float) and abs(v) < 10 else (round(v) if isinstance(v, float) else v)
+    return {
+        "headline": {"value": g("value"), "e2e": g("e2e", "value"), "ms_per_step": g("ms_per_step"),
+                     "roofline": [g("roofline", "kernel"), g("roofline", "frac")]},
+        "fp32_plain": {"fp32": g("fp32_plain", "fp32", "value"), "bf16": g("fp32_plain", "bf16", "value"),
+                       "speedup": g("fp32_plain", "bf16_speedup_vs_fp32")},
+        "paper_network": {p: [g("paper_network", p, "value"), g("paper_network", p, "roofline", "frac")]
+                          for p in ("fp32", "bf16", "fp8")} | {"bf16_12_walkers_ms": g("paper_network",
+                                                                                            "bf16_12_walkers_ms_per_step")},
+        "precision": {p: [g("precision", p, "value"), g("precision", p, "roofline", "frac"),
+                          g("cpu_baseline", "configs", "precision_errors_vs_oracle", p, "mean_force_rel_err", "max")]
+                      for p in ("fp32", "bf16", "fp8")},
+        "tiny": [g("tiny", "explore", "value"), g("tiny", "label", "value")],
+        "batching": g("batching", "value"),
+        "training": g("training", "value"),
+        "mcmc": [g("mcmc", "value"), g("mcmc", "bf16_tensor_cores", "value")],
+        "constrained": g("constrained", "value"),
+        "selection_ms": g("selection", "wall_ms"),
+        "serving": {"tput": g("serving", "throughput"), "label_p99_ms": g("serving", "label_latency_ms", "p99"),
+                    "plain_label_p99_ms": g("serving", "plain_per_job", "label_latency_ms", "p99")},
+        "serving_sustained": {"tput": g("serving_sustained", "throughput"),
+                              "req_s": g("serving_sustained", "requests_per_s"),
+                              "label_p50_ms": g("serving_sustained", "label_latency_ms", "p50"),
+                              "label_p99_ms": g("serving_sustained", "label_latency_ms", "p99")},
+        "cpu": [g("cpu_baseline", "value"), g("cpu_baseline", "cores")],
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -748,6 +972,12 @@ def main():
     ap.add_argument("--cons-runs", type=int, default=1024)
     ap.add_argument("--cons-steps", type=int, default=1000)
     ap.add_argument("--mcmc-steps", type=int, default=500)
+    ap.add_argument("--mlp-cluster", type=int, default=0,
+                    help="cluster size of the tensor-core ensemble kernel (0: tuned by the library)")
+    ap.add_argument("--no-paper-net", action="store_true")
+    ap.add_argument("--no-tiny", action="store_true")
+    ap.add_argument("--serve-sustained-rate", type=float, default=50.0)
+    ap.add_argument("--serve-sustained-requests", type=int, default=200)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -777,6 +1007,7 @@ def main():
     stream = torch.cuda.current_stream()
     system = rid.System(sp)
     system.set_ensemble(ens, precision=prec)
+    system.set_mlp_cluster(args.mlp_cluster)
     xd = torch.from_numpy(x0).cuda()
     system.walkers_load(xd, stream=stream)
     system.walkers_advance(args.warmup, stream=stream)
@@ -891,10 +1122,12 @@ def main():
                       "parallelism": f"walkers sharded, {world} independent rank(s)"},
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
            "fp32_peak": {"value": fp32_peak(torch)[0], "unit": "TFLOP/s", "source": fp32_peak(torch)[1]}}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(sp, x0, ens, args.cpu_walkers, args.cpu_steps)
     if rank == 0 and world == 1 and not args.no_fp32_plain:
         out["fp32_plain"] = run_fp32_plain(rid, torch, args.steps)
+    if rank == 0 and world == 1 and not args.no_paper_net:
+        out["paper_network"] = run_paper_network(rid, torch, args.steps)
+    if rank == 0 and world == 1 and not args.no_tiny:
+        out["tiny"] = run_tiny(rid, torch)
     if rank == 0 and world == 1 and not args.no_batching:
         out["batching"] = run_batching(rid, args.batch_jobs, args.batch_steps, args.batch_plain_jobs)
     if rank == 0 and world == 1 and not args.no_precision:
@@ -909,7 +1142,15 @@ def main():
         out["mcmc"] = run_mcmc(rid, torch, args.mcmc_steps)
     if rank == 0 and world == 1 and not args.no_serving:
         out["serving"] = run_serving(rid, args.serve_requests, args.serve_rate, args.serve_plain_requests)
+        if args.serve_sustained_rate > 0:
+            out["serving_sustained"] = run_serving(rid, args.serve_sustained_requests, args.serve_sustained_rate, 0,
+                                                   seed=7)
+    sample = out["precision"].pop("_sample", None) if "precision" in out else None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(sp, x0, ens, args.cpu_walkers, args.cpu_steps)
+        out["cpu_baseline"]["configs"] = cpu_configs(sample)
     if rank == 0:
+        out["legs"] = legs_summary(out)
         print(json.dumps(out))
     system.close()
     if pg:
