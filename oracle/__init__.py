@@ -69,7 +69,7 @@ def lib():
             L.orc_eval_ff.restype = C.c_double
             L.orc_eval_cvs.argtypes = sys_args + [_d, _d, _d]
             L.orc_mlp.argtypes = [C.c_int] * 5 + [_d, C.c_int, _d, _d, _d]
-            L.orc_eval_ensemble.argtypes = [_i32, _d, _d, C.c_int, _d, _d, _d, _d]
+            L.orc_eval_ensemble.argtypes = [_i32, _d, _d, C.c_int, _i32, _d, _d, _d, _d]
             L.orc_eval_total.argtypes = sys_args + [_i32, _d, _d, C.c_int, _d, _d, _d, _d, _d, _d]
             L.orc_explore.argtypes = sys_args + [_i32, _d, _d, C.c_int, _f, _f, C.c_uint64, C.c_int64,
                                                  _f, _f, _d, _d, _d, C.c_int]
@@ -175,14 +175,17 @@ def mlp(ens, m, u):
     return A[0], du
 
 
-def ensemble(ens, s):
+def ensemble(ens, s, cv_atoms=None):
+    """Ensemble at CV point s; cv_atoms [C][4] gives the CV kinds (a row
+    ending in -1, -1 is a distance), None for torsions only."""
     keep, ea = _ens(ens)
     s = np.ascontiguousarray(s, dtype=np.float64)
     Cn = s.shape[0]
+    cva = None if cv_atoms is None else np.ascontiguousarray(cv_atoms, dtype=np.int32)
     Fs = np.zeros(Cn)
     o3 = np.zeros(3)
     gA = np.zeros((ens.n_models, Cn))
-    lib().orc_eval_ensemble(ea[0], ea[1], ea[2], Cn, _P(s, C.c_double), _P(Fs, C.c_double),
+    lib().orc_eval_ensemble(ea[0], ea[1], ea[2], Cn, _P(cva, C.c_int32), _P(s, C.c_double), _P(Fs, C.c_double),
                             _P(o3, C.c_double), _P(gA, C.c_double))
     return dict(Fs=Fs, eps=o3[0], Abar=o3[1], sigma=o3[2], gradA=gA)
 

@@ -24,7 +24,8 @@
  *                                                        (Sec. "Training phase")
  *   - ensemble MLP with `neurons` hidden widths and optional residual
  *     connections between equal-width layers             (Sec. "Training phase")
- *   - torsion CVs, periodic over 2 pi                    (Sec. "CV selection")
+ *   - torsion CVs, periodic over 2 pi, and distance CVs between two beads
+ *     (not periodic; the MLP takes (s, 0) for them)     (Sec. "CV selection")
  *   - restrained MD labelling: harmonic restraints with force constants
  *     `kappas`, mean force estimated by the spring force   (Sec. "Labeling
  *     phase", restrained method; Sec. "Development of the protocol")
@@ -112,9 +113,13 @@ typedef struct {
     const double* dd;           /* [n-3][3] dihedral phases delta_1..delta_3 */
     double lj_eps, lj_sig, lj_rc;
     int n_cv;
-    const int32_t* cv;          /* [C][4] bead indices of each torsion CV */
+    const int32_t* cv;          /* [C][4] bead indices of each CV: a torsion of four beads, or the
+                                   distance between the first two when the last two are -1 */
     int output_freq;
 } orc_sys;
+
+/* CV kind: the distance between beads cv[j][0] and cv[j][1] when cv[j][2] < 0. */
+static int cv_is_distance(const int32_t* cv, int j) { return cv[4 * j + 2] < 0; }
 
 typedef struct {
     int M, D, L, H, resnet;
@@ -151,6 +156,13 @@ static double wrap_pi(double d)
     return d - 2.0 * ORC_PI * floor(d / (2.0 * ORC_PI) + 0.5);
 }
 double orc_wrap_pi(double d) { return wrap_pi(d); }
+
+/* Restraint offset of CV j from its centre: wrapped for a torsion, plain
+ * for a distance. */
+static double cv_offset(const int32_t* cv, int j, double s, double s0)
+{
+    return (cv && cv[4 * j + 2] < 0) ? s - s0 : wrap_pi(s - s0);
+}
 
 /* ------------------------------------------------------------------------ */
 /* Torsion angle of four points and its gradient.                            */
@@ -303,11 +315,26 @@ int64_t orc_lj_pairs(int n, const float* xf /* [n][3] */, double rc, int64_t cap
 }
 
 /* ------------------------------------------------------------------------ */
-/* CVs: s_j = torsion of beads cv[j][0..3]; J[j] = d s_j / d x (4 beads).     */
+/* CVs (Sec. "CV selection": torsions and distances): s_j = torsion of beads  */
+/* cv[j][0..3], or s_j = |x_b - x_a| for a distance CV (a, b, -1, -1);       */
+/* J[j] = d s_j / d x on its 4 slots (a distance uses slots 0 and 1:          */
+/* -(x_b - x_a)/s and +(x_b - x_a)/s; slots 2, 3 are zero).                   */
 /* ------------------------------------------------------------------------ */
 static void cvs_eval(const orc_sys* S, const double* x, double* s, double* J /* [C][12] */)
 {
     for (int j = 0; j < S->n_cv; ++j) {
+        if (cv_is_distance(S->cv, j)) {
+            const int a = S->cv[4 * j], b = S->cv[4 * j + 1];
+            double r[3];
+            vsub(x + 3 * b, x + 3 * a, r);
+            const double d = vnorm(r);
+            s[j] = d;
+            if (J) {
+                double* g = J + 12 * j;
+                for (int k = 0; k < 3; ++k) { g[k] = -r[k] / d; g[3 + k] = r[k] / d; g[6 + k] = 0; g[9 + k] = 0; }
+            }
+            continue;
+        }
         double p[12];
         for (int a = 0; a < 4; ++a)
             for (int k = 0; k < 3; ++k) p[3 * a + k] = x[3 * S->cv[4 * j + a] + k];
@@ -401,21 +428,28 @@ double orc_switch(double eps, double e0, double e1) { return switch_sigma(eps, e
  * (population, Euclidean over the C CV components), switched CV force
  * F_s = sigma(eps) Fbar (the bias potential is -Abar, so its force on s is
  * +grad Abar).  Abar = mean member value. */
-static void ensemble_eval(const orc_ens* E, int C, const double* s, double* Fs,
+/* MLP input of CV j (reading: the paper feeds periodic CVs through their   */
+/* cosine and sine; a distance CV, not periodic, enters as (s_j, 0)), and    */
+/* dA/ds_j from dA/du by the chain rule through that map.                   */
+static void ensemble_eval(const orc_ens* E, int C, const double* s, const int32_t* cv, double* Fs,
                           double* eps_out, double* Abar_out, double* sig_out, double* gradA /* [M][C] or NULL */)
 {
     const int M = E->M, D = E->D;
     double* u = (double*)malloc(sizeof(double) * (size_t)D);
     double* du = (double*)malloc(sizeof(double) * (size_t)D);
     double* gA = (double*)malloc(sizeof(double) * (size_t)M * C);
-    for (int j = 0; j < C; ++j) { u[2 * j] = cos(s[j]); u[2 * j + 1] = sin(s[j]); }
+    for (int j = 0; j < C; ++j) {
+        if (cv && cv_is_distance(cv, j)) { u[2 * j] = s[j]; u[2 * j + 1] = 0.0; }
+        else { u[2 * j] = cos(s[j]); u[2 * j + 1] = sin(s[j]); }
+    }
     double Abar = 0;
     for (int m = 0; m < M; ++m) {
         double A;
         mlp_eval(E, m, u, &A, du);
         Abar += A / M;
         for (int j = 0; j < C; ++j)
-            gA[m * C + j] = -sin(s[j]) * du[2 * j] + cos(s[j]) * du[2 * j + 1];
+            gA[m * C + j] = (cv && cv_is_distance(cv, j)) ? du[2 * j]
+                                                          : -sin(s[j]) * du[2 * j] + cos(s[j]) * du[2 * j + 1];
     }
     double e2 = 0;
     for (int j = 0; j < C; ++j) {
@@ -459,10 +493,10 @@ static double total_force(const orc_sys* S, const orc_bias* B, const double* x, 
     cvs_eval(S, x, s, J);
     double e = 0, ab = 0, ur = 0;
     if (B->mode == 1 && B->E) {
-        ensemble_eval(B->E, C, s, Fs, &e, &ab, NULL, NULL);
+        ensemble_eval(B->E, C, s, S->cv, Fs, &e, &ab, NULL, NULL);
     } else if (B->mode == 2) {
         for (int j = 0; j < C; ++j) {
-            double d = wrap_pi(s[j] - B->s0[j]);
+            double d = cv_offset(S->cv, j, s[j], B->s0[j]);
             Fs[j] = -B->kappa[j] * d;
             ur += 0.5 * B->kappa[j] * d * d;
         }
@@ -472,6 +506,7 @@ static double total_force(const orc_sys* S, const orc_bias* B, const double* x, 
     for (int j = 0; j < C; ++j)
         for (int a = 0; a < 4; ++a) {
             int at = S->cv[4 * j + a];
+            if (at < 0) continue;
             for (int k = 0; k < 3; ++k) f[3 * at + k] += Fs[j] * J[12 * j + 3 * a + k];
         }
     if (eps) *eps = e;
@@ -638,7 +673,7 @@ static void run_walker(run_ctx* R, int w)
         double Uff = total_force(S, &B, x, f, s, &eps, &Abar, NULL);
         baoab_post(N, 3, v, f, S->mass, S->dt);
         if (R->label && t >= R->n_equil) {
-            for (int j = 0; j < C; ++j) d[j] = wrap_pi(s[j] - B.s0[j]);
+            for (int j = 0; j < C; ++j) d[j] = cv_offset(S->cv, j, s[j], B.s0[j]);
             stats_add(&st, t - R->n_equil, d);
         }
         if (!R->label && S->output_freq > 0 && (t + 1) % S->output_freq == 0) {
@@ -728,12 +763,13 @@ void orc_eval_cvs(SYS_ARGS, const double* x, double* s, double* J)
     cvs_eval(&S, x, s, J);
 }
 
-/* Ensemble quantities at CV point s: F_s (switched), eps, Abar, sigma, dA_i/ds. */
-void orc_eval_ensemble(const int32_t* ens_i, const double* ens_d, const double* w, int C,
+/* Ensemble quantities at CV point s: F_s (switched), eps, Abar, sigma, dA_i/ds.
+ * cv: the system's [C][4] CV atoms (for the CV kinds), or NULL for torsions only. */
+void orc_eval_ensemble(const int32_t* ens_i, const double* ens_d, const double* w, int C, const int32_t* cv,
                        const double* s, double* Fs, double* out3 /* eps, Abar, sigma */, double* gradA)
 {
     orc_ens E = {ens_i[0], ens_i[1], ens_i[2], ens_i[3], ens_i[4], ens_d[0], ens_d[1], w};
-    ensemble_eval(&E, C, s, Fs, &out3[0], &out3[1], &out3[2], gradA);
+    ensemble_eval(&E, C, s, cv, Fs, &out3[0], &out3[1], &out3[2], gradA);
 }
 
 /* Total force at one configuration: mode 0 none, 1 ensemble bias, 2 restraint.

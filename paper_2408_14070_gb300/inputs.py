@@ -31,7 +31,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "SystemParams", "EnsembleParams", "make_system", "make_chains",
+    "SystemParams", "EnsembleParams", "make_system", "cv_is_distance", "make_chains",
     "make_ensemble", "make_label_targets", "ensemble_param_count",
     "WORKLOADS", "workload", "chain_length_buckets", "label_batch_jobs", "serving_requests",
 ]
@@ -86,14 +86,30 @@ def evenly_spaced_cvs(n_beads: int, n_cv: int) -> np.ndarray:
     return (first[:, None] + np.arange(4)[None, :]).astype(np.int32)
 
 
-def make_system(n_beads: int, n_cv: int, seed: int, **overrides) -> SystemParams:
+def make_system(n_beads: int, n_cv: int, seed: int, n_dist: int = 0, dist_span: int = 5,
+                **overrides) -> SystemParams:
+    """A chain with n_cv CVs: n_cv - n_dist evenly spaced torsions, then
+    n_dist distance CVs between beads (a, a + dist_span), their first beads
+    spread evenly along the chain (rows (a, a + span, -1, -1))."""
     sp = SystemParams(n_beads=n_beads, n_cv=n_cv, seed=seed, **overrides)
     g = _rng(seed, _TAG_SYSTEM)
     nd = n_beads - 3
     sp.dihedral_k = g.uniform(0.0, 2.0, size=(nd, 3))
     sp.dihedral_delta = g.uniform(0.0, 2.0 * math.pi, size=(nd, 3))
-    sp.cv_atoms = evenly_spaced_cvs(n_beads, n_cv)
+    nt = n_cv - n_dist
+    if n_dist < 0 or nt < 0 or (n_dist and n_beads <= dist_span):
+        raise ValueError("need 0 <= n_dist <= n_cv and n_beads > dist_span")
+    rows = [evenly_spaced_cvs(n_beads, nt)] if nt else []
+    if n_dist:
+        first = np.floor((np.arange(n_dist) + 0.5) * (n_beads - dist_span) / n_dist).astype(np.int32)
+        rows.append(np.stack([first, first + dist_span, -np.ones_like(first), -np.ones_like(first)], axis=1))
+    sp.cv_atoms = np.ascontiguousarray(np.concatenate(rows).astype(np.int32))
     return sp
+
+
+def cv_is_distance(sp: SystemParams) -> np.ndarray:
+    """Boolean [C]: which CVs are distances (rows ending in -1, -1)."""
+    return np.asarray(sp.cv_atoms)[:, 2] < 0
 
 
 def _place_next(a, b, c, bond, theta, phi):
