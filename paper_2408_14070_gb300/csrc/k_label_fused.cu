@@ -7,8 +7,9 @@
 // steps, so a step costs no HBM traffic besides the noise-free label sums.
 // Each step applies, in the order of the per-step kernels (k_head / k_ff):
 //   B A O A (Philox noise at counter (bead, run, step, 0)),
-//   torsion CVs and Jacobians, restraint force F_j = -kappa_j wrap(s_j - s0_j),
-//   FP64 label sample of d = wrap(s - s0) past n_equil,
+//   torsion / distance CVs and Jacobians, restraint force F_j = -kappa_j d_j
+//   with d = wrap(s - s0) for a torsion and s - s0 for a distance,
+//   FP64 label sample of d past n_equil,
 //   force field (bonded + cluster-culled all-pairs LJ) + chain rule,
 //   closing B half-kick.
 // Every per-bead sum is taken in the same order as the per-step kernels, so a
@@ -130,11 +131,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_label_fused(FusedArgs A) {
             for (int j = tid; j < C; j += NT) {
                 const int4 q = S.cv[j];
                 float3 g[4];
-                const float sj = rid_torsion(f3(xs[q.x]), f3(xs[q.y]), f3(xs[q.z]), f3(xs[q.w]), g);
+                const float sj = rid_cv(q, xs, g);
 #pragma unroll
                 for (int a = 0; a < 4; ++a) Jm[4 * j + a] = make_float4(g[a].x, g[a].y, g[a].z, 0.0f);
                 const long long o = (long long)r * C + j;
-                const double d = rid_wrapd((double)sj - J.s0[o]);
+                const double d = rid_cv_offset(q, (double)sj, J.s0[o]);
                 Fs[j] = (float)(-J.kappa[o] * d);
                 if (sample) {
                     if (newblock) {

@@ -227,13 +227,14 @@ __global__ void __launch_bounds__(NT) k_mlp_fp32(EnsDev E, StateDev st, int W, i
         }
         __syncthreads();
     }
-    // dA/ds_j = -sin s_j g0[2j] + cos s_j g0[2j+1]
+    // dA/ds_j = -sin s_j g0[2j] + cos s_j g0[2j+1] (torsion), g0[2j] (distance: input (s, 0))
     for (int idx = threadIdx.x; idx < C * TW; idx += NT) {
         const int wl = idx / C, j = idx - wl * C;
         const int wg = w0 + wl;
         if (wg < W) {
             const float cs = ubuf[(2 * j) * ROW + wl], sn = ubuf[(2 * j + 1) * ROW + wl];
-            const float g = -sn * G[(2 * j) * ROW + wl] + cs * G[(2 * j + 1) * ROW + wl];
+            const bool dist = E.cvdist && __ldg(E.cvdist + j);
+            const float g = dist ? G[(2 * j) * ROW + wl] : -sn * G[(2 * j) * ROW + wl] + cs * G[(2 * j + 1) * ROW + wl];
             st.gradA[((size_t)m * W + wg) * C + j] = g;
         }
     }

@@ -362,14 +362,16 @@ __global__ void __maxnreg__(96)
                         }
                         store_a8(Abuf, row, gc, ebn, d);
                     } else if (valid) {
-                        // G_0 = dA/du: dA/ds_j = -sin s_j g[2j] + cos s_j g[2j+1]
+                        // G_0 = dA/du: dA/ds_j = -sin s_j g[2j] + cos s_j g[2j+1] (torsion), g[2j] (distance)
 #pragma unroll
                         for (int p = 0; p < 4; ++p) {
                             const int j = gc / 2 + p;
                             if (2 * j < P.D) {
                                 const float cs = __ldg(P.u + (size_t)wg * P.D + 2 * j);
                                 const float sn = __ldg(P.u + (size_t)wg * P.D + 2 * j + 1);
-                                P.gradA[((size_t)m * P.W + wg) * P.C + j] = -sn * acc[k][2 * p] + cs * acc[k][2 * p + 1];
+                                const bool dist = P.cvdist && __ldg(P.cvdist + j);   // input (s, 0)
+                                P.gradA[((size_t)m * P.W + wg) * P.C + j] =
+                                    dist ? acc[k][2 * p] : -sn * acc[k][2 * p] + cs * acc[k][2 * p + 1];
                             }
                         }
                     }

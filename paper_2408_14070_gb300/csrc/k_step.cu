@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
             if (sample) b = ((t_fin - lab.n_equil) * lab.B) / lab.K;
             for (int j = threadIdx.x; j < C; j += blockDim.x) {
                 const long long o = (long long)w * C + j;
-                const double d = rid_wrapd((double)st.s[o] - lab.s0[o]);
+                const double d = rid_cv_offset(S.cv[j], (double)st.s[o], lab.s0[o]);
                 Fs[j] = (float)(-lab.kappa[o] * d);
                 if (sample) {
                     lab.sum[o] += d;
@@ -330,15 +330,15 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
         for (int j = threadIdx.x; j < C; j += blockDim.x) {
             const int4 q = S.cv[j];
             float3 g[4];
-            const float sj = rid_torsion(f3(xs[q.x]), f3(xs[q.y]), f3(xs[q.z]), f3(xs[q.w]), g);
+            const float sj = rid_cv(q, xs, g);
             const long long o = (long long)w * C + j;
             st.s[o] = sj;
 #pragma unroll
             for (int a = 0; a < 4; ++a) st.J[o * 4 + a] = make_float4(g[a].x, g[a].y, g[a].z, 0.0f);
-            float sn, cs;
-            sincosf(sj, &sn, &cs);
-            st.u[(long long)w * 2 * C + 2 * j] = cs;
-            st.u[(long long)w * 2 * C + 2 * j + 1] = sn;
+            float u0, u1;
+            rid_cv_input(q, sj, u0, u1);
+            st.u[(long long)w * 2 * C + 2 * j] = u0;
+            st.u[(long long)w * 2 * C + 2 * j + 1] = u1;
         }
     }
 }

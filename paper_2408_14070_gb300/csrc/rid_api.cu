@@ -105,7 +105,8 @@ struct rid_system {
     rid_system_desc desc{};
     SysDev S{};
     int device = 0;
-    DevBuf d_dih, d_cv, d_acv_off, d_acv;
+    DevBuf d_dih, d_cv, d_acv_off, d_acv, d_cvdist;
+    bool has_dist = false;     // some CV is a distance (cv_atoms row (a, b, -1, -1))
     // ensemble
     bool has_ens = false;
     EnsDev E{};
@@ -249,7 +250,7 @@ extern "C" const char* rid_status_string(int s) {
 extern "C" const char* rid_last_error(void) { return g_err.c_str(); }
 
 static void destroy_all(rid_system* sys) {
-    DevBuf* bufs[] = {&sys->d_dih, &sys->d_cv, &sys->d_acv_off, &sys->d_acv, &sys->d_W, &sys->d_WT, &sys->d_b,
+    DevBuf* bufs[] = {&sys->d_dih, &sys->d_cv, &sys->d_acv_off, &sys->d_acv, &sys->d_cvdist, &sys->d_W, &sys->d_WT, &sys->d_b,
                       &sys->d_wout, &sys->d_bout, &sys->x, &sys->v, &sys->f, &sys->fff, &sys->s, &sys->J,
                       &sys->u, &sys->gradA, &sys->Aval, &sys->eps, &sys->hs, &sys->eff, &sys->flags,
                       &sys->lsum, &sys->lsum2, &sys->lbsum, &sys->ls0, &sys->lkap, &sys->io0, &sys->io1,
@@ -281,13 +282,15 @@ extern "C" int rid_create_system(const rid_system_desc* d, rid_system** out) {
         return fail(RID_ERR_ARG, "need mass > 0, kT >= 0, dt > 0, gamma >= 0");
     if (!(d->lj_rc > 0) || !(d->lj_sigma > 0)) return fail(RID_ERR_ARG, "need lj_rc > 0, lj_sigma > 0");
     if (!d->dihedral_k || !d->dihedral_delta || !d->cv_atoms) return fail(RID_ERR_ARG, "NULL parameter array");
+    bool any_dist = false;
     for (int j = 0; j < C; ++j) {
-        for (int a = 0; a < 4; ++a) {
-            const int q = d->cv_atoms[4 * j + a];
-            if (q < 0 || q >= N) return fail(RID_ERR_ARG, "cv_atoms[%d][%d]=%d outside [0, %d)", j, a, q, N);
-        }
         const int* q = d->cv_atoms + 4 * j;
-        if (q[0] == q[1] || q[1] == q[2] || q[2] == q[3] || q[0] == q[2] || q[1] == q[3] || q[0] == q[3])
+        const bool dist = q[2] == -1 && q[3] == -1;   // the distance between beads q[0] and q[1]
+        any_dist |= dist;
+        for (int a = 0; a < (dist ? 2 : 4); ++a)
+            if (q[a] < 0 || q[a] >= N) return fail(RID_ERR_ARG, "cv_atoms[%d][%d]=%d outside [0, %d)", j, a, q[a], N);
+        if (dist ? q[0] == q[1]
+                 : (q[0] == q[1] || q[1] == q[2] || q[2] == q[3] || q[0] == q[2] || q[1] == q[3] || q[0] == q[3]))
             return fail(RID_ERR_ARG, "cv %d has repeated beads", j);
     }
     int dev = 0;
@@ -329,19 +332,26 @@ extern "C" int rid_create_system(const rid_system_desc* d, rid_system** out) {
             dih[6 * k + n] = (float)d->dihedral_k[3 * k + n];
             dih[6 * k + 3 + n] = (float)d->dihedral_delta[3 * k + n];
         }
+    // chain-rule list: the (CV, slot) pairs touching each bead, in CV order
+    // (a distance CV has two slots; the list is padded to 4 C entries)
     std::vector<int> off(N + 1, 0);
     for (int j = 0; j < C; ++j)
-        for (int a = 0; a < 4; ++a) off[d->cv_atoms[4 * j + a] + 1]++;
+        for (int a = 0; a < 4; ++a)
+            if (d->cv_atoms[4 * j + a] >= 0) off[d->cv_atoms[4 * j + a] + 1]++;
     for (int i = 0; i < N; ++i) off[i + 1] += off[i];
-    std::vector<int2> acv(4 * C);
+    std::vector<int2> acv(4 * C, make_int2(0, 0));
     {
         std::vector<int> fill(off.begin(), off.end() - 1);
         for (int j = 0; j < C; ++j)
-            for (int a = 0; a < 4; ++a) acv[fill[d->cv_atoms[4 * j + a]]++] = make_int2(j, a);
+            for (int a = 0; a < 4; ++a)
+                if (d->cv_atoms[4 * j + a] >= 0) acv[fill[d->cv_atoms[4 * j + a]]++] = make_int2(j, a);
     }
+    std::vector<int> cvdist(C);
+    for (int j = 0; j < C; ++j) cvdist[j] = d->cv_atoms[4 * j + 2] < 0 ? 1 : 0;
     int r = RID_OK;
     if ((r = sys->d_dih.ensure(dih.size() * sizeof(float))) || (r = sys->d_cv.ensure(C * sizeof(int4))) ||
-        (r = sys->d_acv_off.ensure((N + 1) * sizeof(int))) || (r = sys->d_acv.ensure(4 * C * sizeof(int2)))) {
+        (r = sys->d_acv_off.ensure((N + 1) * sizeof(int))) || (r = sys->d_acv.ensure(4 * C * sizeof(int2))) ||
+        (r = sys->d_cvdist.ensure(C * sizeof(int)))) {
         destroy_all(sys);
         delete sys;
         return r;
@@ -350,6 +360,7 @@ extern "C" int rid_create_system(const rid_system_desc* d, rid_system** out) {
     if (e == cudaSuccess) e = cudaMemcpy(sys->d_cv.p, d->cv_atoms, C * sizeof(int4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(sys->d_acv_off.p, off.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(sys->d_acv.p, acv.data(), 4 * C * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(sys->d_cvdist.p, cvdist.data(), C * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         destroy_all(sys);
         delete sys;
@@ -359,6 +370,7 @@ extern "C" int rid_create_system(const rid_system_desc* d, rid_system** out) {
     S.cv = sys->d_cv.as<int4>();
     S.acv_off = sys->d_acv_off.as<int>();
     S.acv = sys->d_acv.as<int2>();
+    sys->has_dist = any_dist;
     *out = sys;
     return RID_OK;
 }
@@ -595,6 +607,7 @@ extern "C" int rid_set_ensemble(rid_system* sys, const rid_ensemble_desc* d) {
     E.bout = sys->d_bout.as<float>();
     E.wstride = wst;
     for (int l = 0; l < RID_MAX_LAYERS; ++l) E.loff[l] = loff[l];
+    E.cvdist = sys->has_dist ? sys->d_cvdist.as<int>() : nullptr;
     sys->precision = d->precision;
     sys->has_ens = true;
     E.aslices = 1;
@@ -825,7 +838,7 @@ static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_
         P.W = W; P.C = sys->S.C; P.D = E.D; P.Dp = sys->Dp; P.L = E.L; P.H = E.H; P.M = E.M;
         P.stages = V.stages; P.Kpmax = V.Kpmax; P.ntiles = (W + 127) / 128;
         P.tmem_cols = V.tmem_cols; P.nacc = V.nacc; P.acc_cols = V.acc_cols; P.stage_bytes = V.stage_bytes;
-        P.u = sd.u; P.bias = E.b; P.wout = E.wout; P.bout = E.bout;
+        P.u = sd.u; P.bias = E.b; P.wout = E.wout; P.bout = E.bout; P.cvdist = E.cvdist;
         P.tsave = sys->tsave.as<__nv_bfloat16>(); P.gradA = sd.gradA; P.Apart = sd.Aval; P.err = sys->d_err.as<int>();
         P.member_rows = V.member_rows;
         for (int g = 0; g < 2 * E.L; ++g) {

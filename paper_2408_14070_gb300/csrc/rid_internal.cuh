@@ -35,7 +35,7 @@ struct SysDev {
     float lj_eps24, lj_eps4, sig2, rc2, urc; // urc: U_LJ(rc) shift
     uint32_t key0, key1;
     const float* dih;        // [N-3][6]: k_1, k_2, k_3, delta_1, delta_2, delta_3
-    const int4* cv;          // [C] bead quadruples
+    const int4* cv;          // [C] bead quadruples (z < 0: the distance between x and y)
     const int* acv_off;      // [N+1] CSR offsets: CV slots touching each bead
     const int2* acv;         // (cv index, slot 0..3), ordered by cv index
 };
@@ -52,6 +52,7 @@ struct EnsDev {
     const float* bout;       // [M]
     long long wstride;       // floats per model in W / WT
     long long loff[RID_MAX_LAYERS];  // offset of layer l within a model
+    const int* cvdist;       // [C] 1 for a distance CV (input (s, 0)), or NULL when all are torsions
 };
 
 // Resident walker state (capacity W walkers).
@@ -156,12 +157,45 @@ __device__ __forceinline__ float rid_torsion(float3 p0, float3 p1, float3 p2, fl
     return phi;
 }
 
+// One CV of a system (Sec. "CV selection"): q = (a, b, c, d) is the torsion
+// of four beads, or, when q.z < 0, the distance |x_b - x_a| (not periodic).
+// Returns s and its gradient on the CV's four slots (a distance fills slots
+// 0 and 1 with -(x_b - x_a)/s and +(x_b - x_a)/s, slots 2 and 3 with zero).
+__device__ __forceinline__ bool rid_cv_is_distance(int4 q) { return q.z < 0; }
+template <typename X>
+__device__ __forceinline__ float rid_cv(int4 q, const X* xs, float3* g) {
+    if (rid_cv_is_distance(q)) {
+        const float3 r = f3(xs[q.y]) - f3(xs[q.x]);
+        const float d = sqrtf(dot3(r, r));
+        const float id = 1.0f / d;
+        g[1] = id * r;
+        g[0] = make_float3(-g[1].x, -g[1].y, -g[1].z);
+        g[2] = g[3] = make_float3(0.f, 0.f, 0.f);
+        return d;
+    }
+    return rid_torsion(f3(xs[q.x]), f3(xs[q.y]), f3(xs[q.z]), f3(xs[q.w]), g);
+}
+// MLP input pair of a CV: (cos s, sin s) for a torsion, (s, 0) for a distance.
+__device__ __forceinline__ void rid_cv_input(int4 q, float s, float& u0, float& u1) {
+    if (rid_cv_is_distance(q)) {
+        u0 = s;
+        u1 = 0.0f;
+    } else {
+        sincosf(s, &u1, &u0);
+    }
+}
+
 // wrap onto [-pi, pi): d - 2 pi floor(d / 2 pi + 1/2)
 __device__ __forceinline__ float rid_wrapf(float d) {
     return d - 6.28318530717959f * floorf(d * 0.159154943091895f + 0.5f);
 }
 __device__ __forceinline__ double rid_wrapd(double d) {
     return d - 6.283185307179586 * floor(d * 0.15915494309189535 + 0.5);
+}
+// Restraint offset of a CV from its centre: wrapped for a torsion, plain for
+// a distance.
+__device__ __forceinline__ double rid_cv_offset(int4 q, double s, double s0) {
+    return rid_cv_is_distance(q) ? s - s0 : rid_wrapd(s - s0);
 }
 
 // --------------------------------------------------------------------------

@@ -22,7 +22,8 @@ struct TcArgs {
     int W, C, D, Dp, L, H, M;
     int stages, Kpmax, ntiles, tmem_cols, nacc, acc_cols;   // Kpmax: A-tile row bytes / 2
     unsigned stage_bytes;
-    const float* u;          // [W][D] MLP input (cos, sin), FP32
+    const float* u;          // [W][D] MLP input (cos, sin) or (s, 0), FP32
+    const int* cvdist;       // [C] 1 for a distance CV, or NULL when all are torsions
     const float* bias;       // [M][L][H]
     const float* wout;       // [M][H]
     const float* bout;       // [M]
