@@ -314,6 +314,16 @@ typedef struct {
     const float* path_nodes;      /* [P][path_n_cv] host, radians               */
     double path_lambda;           /* > 0 (path_lm in the paper)                 */
     double path_z_lo, path_z_hi;  /* z range of hist_path                       */
+    /* Distance CVs (the paper's cv_type "dis" with cv_lower_bound /
+     * cv_upper_bound; NULL cv_dist: every CV a torsion).  A distance CV is
+     * not periodic: its proposal s + step_size xi is not wrapped, a proposal
+     * that takes any distance CV out of [cv_lo, cv_hi] is refused (the walk
+     * samples exp(-Abar/kT) restricted to the box), its MLP input is (s, 0),
+     * it is binned as floor((s - cv_lo) / (cv_hi - cv_lo) * bins) (clamped),
+     * and path differences over it are plain. */
+    const int32_t* cv_dist;       /* [C] host or NULL: 1 marks a distance CV    */
+    const double* cv_lo;          /* [C] host: range of each distance CV        */
+    const double* cv_hi;          /*   (entries of torsions are ignored)        */
 } rid_mcmc_desc;
 
 RID_API int rid_mcmc(const rid_mcmc_desc* desc, const float* s0, float* s_out, uint64_t* hist1, uint64_t* hist2,
@@ -330,7 +340,10 @@ RID_API int rid_mcmc(const rid_mcmc_desc* desc, const float* s0, float* s_out, u
  * with rid_walkers_load must be loaded again).  `path` (NULL, or n_nodes = 0:
  * off) adds the path projection of rid_mcmc_desc, with the same fields and
  * limits, counted into hist_path / pmf_path [bins][bins] (either may be NULL);
- * its arrays are host memory whatever `mem` says.
+ * its arrays are host memory whatever `mem` says.  A system with distance CVs
+ * (cv_atoms rows (a, b, -1, -1)) needs cv_lo / cv_hi [C] (host; the range of
+ * each distance CV, torsion entries ignored), read as in rid_mcmc_desc; for a
+ * torsion-only system they may be NULL.
  * Errors: RID_ERR_ARG, RID_ERR_STATE (no ensemble), RID_ERR_OOM, RID_ERR_CUDA.
  */
 typedef struct {
@@ -344,7 +357,7 @@ typedef struct {
 
 RID_API int rid_mcmc_system(rid_system* sys, int32_t n_walkers, const float* s0, int64_t n_steps, int64_t n_burn,
                             double kT, double step_size, uint64_t seed, int32_t bins, int32_t proj_i, int32_t proj_j,
-                            const rid_mcmc_path* path, float* s_out, uint64_t* hist1, uint64_t* hist2, double* pmf1,
+                            const double* cv_lo, const double* cv_hi, const rid_mcmc_path* path, float* s_out, uint64_t* hist1, uint64_t* hist2, double* pmf1,
                             double* pmf2, uint64_t* hist_path, double* pmf_path, int64_t* n_accepted, int32_t mem,
                             void* stream);
 

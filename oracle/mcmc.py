@@ -20,6 +20,12 @@ Readings (the paper names the parameters, not the move):
   counting  after every step t >= n_burn, every walker's current state;
   bins      floor((s + pi) / (2 pi) * bins), clamped to [0, bins - 1];
   wrap      d - 2 pi floor(d / (2 pi) + 1/2).
+Distance CVs (Sec. "CV selection"; the dimension reduction's cv_type "dis"
+with cv_lower_bound / cv_upper_bound): a distance CV is not wrapped, its
+proposal s' = s + step_size xi is refused when any distance CV leaves its
+range [lo, hi] (the walk then samples exp(-Abar/kT) restricted to the box),
+its bins are floor((s - lo) / (hi - lo) * bins) clamped, its MLP input is
+(s, 0), and path differences over it are plain.
 The "path" projection maps a state onto the path collective variables of
 Branduardi, Gervasio and Parrinello (2007) for nodes p_1..p_P over a subset of
 the CVs (wrapped differences): with d_i = |s - p_i|^2,
@@ -42,9 +48,22 @@ def wrap(d):
     return d - 2.0 * math.pi * np.floor(d / (2.0 * math.pi) + 0.5)
 
 
-def ensemble_mean_value(weights, D, L, H, resnet, s):
-    """Abar at points s [W][C] (float64), members' forward passes as matmuls."""
+def features(s, dist=None):
+    """MLP input [W][2C]: (cos s, sin s) per torsion, (s, 0) per distance CV."""
+    s = np.asarray(s, dtype=np.float64)
     u = T.features(s)
+    if dist is not None and np.any(dist):
+        d = np.asarray(dist, dtype=bool)
+        u = u.reshape(s.shape[0], -1, 2)
+        u[:, d, 0] = s[:, d]
+        u[:, d, 1] = 0.0
+        u = u.reshape(s.shape[0], -1)
+    return u
+
+
+def ensemble_mean_value(weights, D, L, H, resnet, s, dist=None):
+    """Abar at points s [W][C] (float64), members' forward passes as matmuls."""
+    u = features(s, dist)
     tot = np.zeros(s.shape[0])
     for w in np.asarray(weights, dtype=np.float64):
         layers, w_out, b_out = T.unpack(w, D, L, H)
@@ -68,15 +87,21 @@ def accept_log_u(W, step, seed):
     return np.log((x + 0.5) * 2.0 ** -32)
 
 
-def bin_index(s, bins):
-    b = np.floor((np.asarray(s, dtype=np.float64) + math.pi) / (2.0 * math.pi) * bins).astype(np.int64)
-    return np.clip(b, 0, bins - 1)
+def bin_index(s, bins, dist=None, lo=None, hi=None):
+    s = np.asarray(s, dtype=np.float64)
+    b = np.floor((s + math.pi) / (2.0 * math.pi) * bins)
+    if dist is not None and np.any(dist):
+        d = np.asarray(dist, dtype=bool)
+        b[..., d] = np.floor((s[..., d] - np.asarray(lo)[d]) / (np.asarray(hi)[d] - np.asarray(lo)[d]) * bins)
+    return np.clip(b.astype(np.int64), 0, bins - 1)
 
 
-def path_cv(s, nodes, cvs, lam):
+def path_cv(s, nodes, cvs, lam, dist=None):
     """(s_path, z_path) of points s [W][C] for path nodes [P][Cp] over the CVs `cvs`."""
     nodes = np.asarray(nodes, dtype=np.float64)
-    d = wrap(np.asarray(s, dtype=np.float64)[:, None, list(cvs)] - nodes[None])
+    d = np.asarray(s, dtype=np.float64)[:, None, list(cvs)] - nodes[None]
+    per = np.ones(len(cvs), dtype=bool) if dist is None else ~np.asarray(dist, dtype=bool)[list(cvs)]
+    d[..., per] = wrap(d[..., per])
     d2 = (d * d).sum(axis=-1)                          # [W][P]
     m = d2.min(axis=1)
     e = np.exp(-lam * (d2 - m[:, None]))
@@ -91,37 +116,48 @@ def path_bins(sp, z, n_nodes, z_lo, z_hi, bins):
     return np.clip(bs, 0, bins - 1), np.clip(bz, 0, bins - 1)
 
 
-def run(weights, C, L, H, resnet, s0, n_steps, n_burn, kT, step_size, seed, bins, pair, path=None):
+def run(weights, C, L, H, resnet, s0, n_steps, n_burn, kT, step_size, seed, bins, pair, path=None,
+        dist=None, lo=None, hi=None):
     """Returns dict(s, A, n_accepted, hist1 [C][bins], hist2 [bins][bins],
     hist_path [bins][bins] (when path = (nodes, cvs, lam, z_lo, z_hi)),
     min_margin [W]): min_margin is each walker's smallest |kT ln u + dA| over
-    the run (how close its closest accept decision came to the threshold)."""
+    the run (how close its closest accept decision came to the threshold),
+    and with distance CVs (dist [C] bool, ranges lo / hi [C]) also the closest
+    approach of a proposal to a range edge."""
     D = 2 * C
     s = np.array(s0, dtype=np.float64)
     W = s.shape[0]
-    A = ensemble_mean_value(weights, D, L, H, resnet, s)
+    dmask = np.zeros(C, dtype=bool) if dist is None else np.asarray(dist, dtype=bool)
+    lo = np.zeros(C) if lo is None else np.asarray(lo, dtype=np.float64)
+    hi = np.zeros(C) if hi is None else np.asarray(hi, dtype=np.float64)
+    A = ensemble_mean_value(weights, D, L, H, resnet, s, dmask)
     hist1 = np.zeros((C, bins), dtype=np.int64)
     hist2 = np.zeros((bins, bins), dtype=np.int64)
     histp = np.zeros((bins, bins), dtype=np.int64)
     n_acc = 0
     min_margin = np.full(W, np.inf)
     for t in range(n_steps):
-        sp = wrap(s + step_size * proposal_normals(W, C, t, seed))
-        Ap = ensemble_mean_value(weights, D, L, H, resnet, sp)
+        sp = s + step_size * proposal_normals(W, C, t, seed)
+        sp[:, ~dmask] = wrap(sp[:, ~dmask])
+        inside = np.all((sp[:, dmask] >= lo[dmask]) & (sp[:, dmask] <= hi[dmask]), axis=1)
+        if dmask.any():
+            edge = np.minimum(np.abs(sp[:, dmask] - lo[dmask]), np.abs(sp[:, dmask] - hi[dmask])).min(axis=1)
+            min_margin = np.minimum(min_margin, edge)
+        Ap = ensemble_mean_value(weights, D, L, H, resnet, sp, dmask)
         margin = kT * accept_log_u(W, t, seed) + (Ap - A)
-        acc = margin < 0.0
-        min_margin = np.minimum(min_margin, np.abs(margin))
+        acc = (margin < 0.0) & inside
+        min_margin = np.minimum(min_margin, np.where(inside, np.abs(margin), np.inf))
         s[acc] = sp[acc]
         A[acc] = Ap[acc]
         n_acc += int(acc.sum())
         if t >= n_burn:
-            b = bin_index(s, bins)
+            b = bin_index(s, bins, dmask, lo, hi)
             for c in range(C):
                 hist1[c] += np.bincount(b[:, c], minlength=bins)
             np.add.at(hist2, (b[:, pair[0]], b[:, pair[1]]), 1)
             if path is not None:
                 nodes, cvs, lam, z_lo, z_hi = path
-                sp_, z_ = path_cv(s, nodes, cvs, lam)
+                sp_, z_ = path_cv(s, nodes, cvs, lam, dmask)
                 bs, bz = path_bins(sp_, z_, len(nodes), z_lo, z_hi, bins)
                 np.add.at(histp, (bs, bz), 1)
     return dict(s=s, A=A, n_accepted=n_acc, hist1=hist1, hist2=hist2, hist_path=histp, min_margin=min_margin)

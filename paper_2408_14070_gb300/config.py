@@ -17,7 +17,8 @@ calls, so a configuration written for the paper's workflow carries over:
                      numb_cluster_upper, max_selection
   "Train"            numb_models, neurons, resnet, batch_size, epochs,
                      init_lr, decay_steps, decay_rate, drop_out_rate
-  "MCMC_Config"      numb_steps, numb_walkers, temperature, bins, cv_type,
+  "MCMC_Config"      numb_steps, numb_walkers, temperature, bins, cv_type
+                     ("dih" | "dis"), cv_lower_bound, cv_upper_bound,
                      proj_info {proj_mode, proj_cv_index, path_list, path_lm}
 
 Units: energies (trust levels, kappas, std_threshold) are passed through in
@@ -74,6 +75,18 @@ def _per_cv(values, n_cv: int, name: str, dtype) -> np.ndarray:
 
 def _kT(temperature, reduced: bool, kb: float) -> float:
     return 1.0 if reduced else kb * float(temperature)
+
+
+def cv_atoms(c: "RidConfig", torsion_atoms: np.ndarray | None = None) -> np.ndarray:
+    """cv_atoms rows of rid_create_system for the configuration's CVs: the
+    given torsion quadruples in torsion mode, rows (a, b, -1, -1) (0-based)
+    for the distance pairs in distance mode."""
+    if c.cv_mode == "distance":
+        p = np.asarray(c.distance_pairs, dtype=np.int32)
+        return np.ascontiguousarray(np.concatenate([p, -np.ones_like(p)], axis=1))
+    if torsion_atoms is None:
+        raise ValueError("torsion mode: the torsion quadruples come from the system")
+    return np.ascontiguousarray(torsion_atoms, dtype=np.int32)
 
 
 def load(cfg, reduced: bool = False, kb: float = KB_KJ_PER_MOL_K) -> RidConfig:
@@ -140,15 +153,31 @@ def load(cfg, reduced: bool = False, kb: float = KB_KJ_PER_MOL_K) -> RidConfig:
     mc = cfg.get("MCMC_Config", {})
     mcmc = {}
     if mc:
-        if mc.get("cv_type", "dih") != "dih":
-            raise ValueError("MCMC dimension reduction runs on torsion CVs ('dih') only")
+        cv_type = mc.get("cv_type", "dih")
+        if cv_type not in ("dih", "dis"):
+            raise ValueError(f"MCMC cv_type {cv_type!r}: 'dih' (torsions) or 'dis' (distances)")
+        if (cv_type == "dis") != (mode == "distance"):
+            raise ValueError(f"MCMC cv_type {cv_type!r} does not match the CV mode {mode!r}")
         proj = mc.get("proj_info", {"proj_mode": "cv", "proj_cv_index": [0, 1]})
         idx = [int(i) for i in proj.get("proj_cv_index", [0, 1])]
         if any(i < 0 or i >= n_cv for i in idx):
             raise ValueError("proj_cv_index outside the CVs")
         mcmc = {"n_walkers": int(mc.get("numb_walkers", 2000)), "n_steps": int(mc.get("numb_steps", 0)),
                 "kT": _kT(mc.get("temperature", 300.0), reduced, kb), "bins": int(mc.get("bins", 101)),
-                "pair": (0, min(1, n_cv - 1)), "path": None}
+                "pair": (0, min(1, n_cv - 1)), "path": None, "cv_dist": np.zeros(n_cv, dtype=bool),
+                "cv_range": None}
+        if cv_type == "dis":
+            # reading: cv_lower_bound / cv_upper_bound (the paper's range of the
+            # initial values, "usually set for distance CVs") bound the walk of
+            # each distance CV; the library needs a range, so they are required
+            if "cv_lower_bound" not in mc or "cv_upper_bound" not in mc:
+                raise ValueError("distance CVs in MCMC need cv_lower_bound and cv_upper_bound")
+            lo = _per_cv(mc["cv_lower_bound"], n_cv, "cv_lower_bound", np.float64)
+            hi = _per_cv(mc["cv_upper_bound"], n_cv, "cv_upper_bound", np.float64)
+            if not np.all(hi > lo):
+                raise ValueError("cv_upper_bound must exceed cv_lower_bound")
+            mcmc["cv_dist"] = np.ones(n_cv, dtype=bool)
+            mcmc["cv_range"] = (lo, hi)
         if proj.get("proj_mode", "cv") == "cv":
             if len(idx) != 2:
                 raise ValueError("the 'cv' projection takes two CV indices")
@@ -160,9 +189,14 @@ def load(cfg, reduced: bool = False, kb: float = KB_KJ_PER_MOL_K) -> RidConfig:
             lam = float(proj.get("path_lm", 1.0))
             if not lam > 0:
                 raise ValueError("path_lm must be positive")
-            # z_path spans [-ln(P) / lambda, max d] with d <= Cp pi^2 for wrapped differences
+            # z_path spans [-ln(P) / lambda, max d]: d <= Cp pi^2 for wrapped
+            # differences, d <= sum (hi - lo)^2 over the path's distance CVs
             z_lo = -math.log(nodes.shape[0]) / lam
-            z_hi = len(idx) * math.pi ** 2
+            if cv_type == "dis":
+                lo, hi = mcmc["cv_range"]
+                z_hi = float(sum((hi[i] - lo[i]) ** 2 for i in idx))
+            else:
+                z_hi = len(idx) * math.pi ** 2
             mcmc["path"] = (nodes, idx, lam, z_lo, z_hi)
         else:
             raise ValueError(f"proj_mode {proj['proj_mode']!r}")

@@ -4,13 +4,15 @@
 //
 // W walkers run Metropolis Monte Carlo in CV space on the ensemble-mean free
 // energy Abar(s) = (1/M) sum_i A_i(s) at temperature kT.  Every step:
-//   k_mc_propose  s' = wrap(s + step_size xi), xi: normal c % 3 of the
-//                 Box-Muller triple of Philox counter (c / 3, walker, step, 2);
-//                 writes the MLP input u' = (cos s', sin s')
+//   k_mc_propose  s' = wrap(s + step_size xi) (a distance CV: not wrapped),
+//                 xi: normal c % 3 of the Box-Muller triple of Philox counter
+//                 (c / 3, walker, step, 2); writes the MLP input
+//                 u' = (cos s', sin s') (a distance CV: (s', 0))
 //   forward GEMMs one batched FP32 GEMM per layer (rid_gemm.cuh), members on
 //                 grid z, the input u' shared by all members
 //   k_mc_accept   one warp per walker: A_i = w_out . h + b_out, Abar' as the
 //                 mean in member order; accept iff kT ln u + (Abar' - Abar) < 0
+//                 and every distance CV of s' lies in its range [lo, hi]
 //                 with u = (x + 1/2) 2^-32, x = word 0 of counter
 //                 (0, walker, step, 3); from step n_burn on, the current state
 //                 of every walker is counted into one histogram per CV and one
@@ -21,6 +23,7 @@
 // the nodes, the smallest distance factored out, sums in a fixed order) and
 // counts (s_path, z_path).
 #include <cmath>
+#include <vector>
 
 #include "rid_gemm.cuh"
 
@@ -36,30 +39,44 @@ __device__ __forceinline__ int mc_bin(float v, int bins) {
     int b = (int)floorf(t);
     return b < 0 ? 0 : (b >= bins ? bins - 1 : b);
 }
-
-__global__ void k_mc_features(const float* __restrict__ s, float* __restrict__ U, long long n) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+// bin of CV c: the angle bin for a torsion, floor((v - lo) / (hi - lo) * bins)
+// (each operation rounded once) for a distance CV, clamped
+__device__ __forceinline__ int mc_bin_cv(float v, int c, int bins, const McCvDev& k) {
+    if (!(k.dist && k.dist[c])) return mc_bin(v, bins);
+    const float t = __fmul_rn(__fdiv_rn(__fsub_rn(v, k.lo[c]), __fsub_rn(k.hi[c], k.lo[c])), (float)bins);
+    int b = (int)floorf(t);
+    return b < 0 ? 0 : (b >= bins ? bins - 1 : b);
+}
+// MLP input pair of CV c: (cos v, sin v) for a torsion, (v, 0) for a distance
+__device__ __forceinline__ void mc_input(float v, bool dist, float* U) {
+    if (dist) {
+        U[0] = v;
+        U[1] = 0.0f;
+    } else {
         float sn, cs;
-        sincosf(s[e], &sn, &cs);
-        U[2 * e] = cs;
-        U[2 * e + 1] = sn;
+        sincosf(v, &sn, &cs);
+        U[0] = cs;
+        U[1] = sn;
     }
 }
 
+__global__ void k_mc_features(const float* __restrict__ s, float* __restrict__ U, long long n, int C, McCvDev k) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        mc_input(s[e], k.dist && k.dist[(int)(e % C)], U + 2 * e);
+}
+
 __global__ void k_mc_propose(const float* __restrict__ s, float* __restrict__ sp, float* __restrict__ U, int W, int C,
-                             uint32_t step, float step_size, uint32_t k0, uint32_t k1) {
+                             uint32_t step, float step_size, uint32_t k0, uint32_t k1, McCvDev k) {
     const long long n = (long long)W * C;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const int w = (int)(e / C), c = (int)(e - (long long)w * C);
         const float3 z = rid_normals3(rid_philox(make_uint4((uint32_t)(c / 3), (uint32_t)w, step, 2u), k0, k1));
         const int r = c % 3;
         const float xi = r == 0 ? z.x : (r == 1 ? z.y : z.z);
-        const float v = rid_wrapf(fmaf(step_size, xi, s[e]));
+        const bool dist = k.dist && k.dist[c];
+        const float v = dist ? fmaf(step_size, xi, s[e]) : rid_wrapf(fmaf(step_size, xi, s[e]));
         sp[e] = v;
-        float sn, cs;
-        sincosf(v, &sn, &cs);
-        U[2 * e] = cs;
-        U[2 * e + 1] = sn;
+        mc_input(v, dist, U + 2 * e);
     }
 }
 
@@ -88,6 +105,7 @@ struct AcceptArgs {
     // member values from a system's ensemble kernels ([na][W], na = M x slices) instead of h . w_out
     const float* aval;
     int na;
+    McCvDev cvk;                 // distance CVs: range, bins, plain path differences
 };
 
 __global__ void k_mc_accept(AcceptArgs a) {
@@ -120,7 +138,15 @@ __global__ void k_mc_accept(AcceptArgs a) {
     }
     const uint4 r = rid_philox(make_uint4(0u, (uint32_t)w, a.step, 3u), a.k0, a.k1);
     const float margin = (abar - a.A[w]) - 0.5f * a.kT * rid_m2logu(r.x);   // kT ln u + dAbar
-    if (margin < 0.0f) {
+    // a proposal that takes a distance CV out of its range is refused
+    bool inside = true;
+    if (a.cvk.dist) {
+        const float* sp = a.sp + (long long)w * a.C;
+        for (int c = lane; c < a.C; c += 32)
+            if (a.cvk.dist[c] && !(sp[c] >= a.cvk.lo[c] && sp[c] <= a.cvk.hi[c])) inside = false;
+        inside = __all_sync(0xffffffffu, inside);
+    }
+    if (margin < 0.0f && inside) {
         const float* sp = a.sp + (long long)w * a.C;
         for (int c = lane; c < a.C; c += 32) s[c] = sp[c];
         if (lane == 0) {
@@ -130,16 +156,21 @@ __global__ void k_mc_accept(AcceptArgs a) {
     }
     __syncwarp();
     if (a.count) {
-        for (int c = lane; c < a.C; c += 32) atomicAdd(&a.hist1[(long long)c * a.bins + mc_bin(s[c], a.bins)], 1ull);
+        for (int c = lane; c < a.C; c += 32)
+            atomicAdd(&a.hist1[(long long)c * a.bins + mc_bin_cv(s[c], c, a.bins, a.cvk)], 1ull);
         if (lane == 0 && a.hist2)
-            atomicAdd(&a.hist2[(long long)mc_bin(s[a.pi], a.bins) * a.bins + mc_bin(s[a.pj], a.bins)], 1ull);
+            atomicAdd(&a.hist2[(long long)mc_bin_cv(s[a.pi], a.pi, a.bins, a.cvk) * a.bins +
+                               mc_bin_cv(s[a.pj], a.pj, a.bins, a.cvk)],
+                      1ull);
         if (a.npath > 0) {
             // d_i for the nodes of this lane, then the smallest over the warp
             float dmin = INFINITY;
             for (int i = lane; i < a.npath; i += 32) {
                 float d2 = 0.0f;
                 for (int c = 0; c < a.Cp; ++c) {
-                    const float d = rid_wrapf(s[a.pcv[c]] - a.pnodes[(long long)i * a.Cp + c]);
+                    const int cv = a.pcv[c];
+                    const float dd = s[cv] - a.pnodes[(long long)i * a.Cp + c];
+                    const float d = (a.cvk.dist && a.cvk.dist[cv]) ? dd : rid_wrapf(dd);
                     d2 = fmaf(d, d, d2);
                 }
                 dmin = fminf(dmin, d2);
@@ -150,7 +181,9 @@ __global__ void k_mc_accept(AcceptArgs a) {
             for (int i = lane; i < a.npath; i += 32) {
                 float d2 = 0.0f;
                 for (int c = 0; c < a.Cp; ++c) {
-                    const float d = rid_wrapf(s[a.pcv[c]] - a.pnodes[(long long)i * a.Cp + c]);
+                    const int cv = a.pcv[c];
+                    const float dd = s[cv] - a.pnodes[(long long)i * a.Cp + c];
+                    const float d = (a.cvk.dist && a.cvk.dist[cv]) ? dd : rid_wrapf(dd);
                     d2 = fmaf(d, d, d2);
                 }
                 const float e = expf(-a.lam * (d2 - dmin));
@@ -215,6 +248,15 @@ struct McBufs {
 
 }  // namespace
 
+int rid_mc_range_check(int C, const int32_t* dist, const double* lo, const double* hi) {
+    if (!dist) return RID_OK;
+    if (!lo || !hi) return rid_fail(RID_ERR_ARG, "mcmc: distance CVs need cv_lo and cv_hi");
+    for (int c = 0; c < C; ++c)
+        if (dist[c] && !(std::isfinite(lo[c]) && std::isfinite(hi[c]) && lo[c] < hi[c]))
+            return rid_fail(RID_ERR_ARG, "mcmc: distance CV %d needs finite cv_lo < cv_hi", c);
+    return RID_OK;
+}
+
 int rid_mc_path_check(int NP, int Cp, int C, const int32_t* cv, const float* nodes, double lambda, double z_lo,
                       double z_hi) {
     if (NP == 0) return RID_OK;
@@ -241,6 +283,8 @@ extern "C" RID_API int rid_mcmc(const rid_mcmc_desc* d, const float* s0, float* 
     const int NP = d->path_n_nodes, Cp = d->path_n_cv;
     if (int r = rid_mc_path_check(NP, Cp, C, d->path_cv, d->path_nodes, d->path_lambda, d->path_z_lo, d->path_z_hi))
         return r;
+    if (int r = rid_mc_range_check(C, d->cv_dist, d->cv_lo, d->cv_hi)) return r;
+    const bool has_dist = d->cv_dist != nullptr;
     cudaStream_t st = (cudaStream_t)stream;
     const int D = 2 * C;
     long long woff[RID_MAX_LAYERS], boff[RID_MAX_LAYERS], o = 0;
@@ -259,10 +303,12 @@ extern "C" RID_API int rid_mcmc(const rid_mcmc_desc* d, const float* s0, float* 
     const size_t bytes_u = sizeof(unsigned long long) * (size_t)(n1 + n2 + np2 + 1);
     const size_t bytes_d = sizeof(double) * (size_t)(n1 + n2 + np2);
     const size_t bytes_p = sizeof(float) * (size_t)npn + sizeof(int) * (size_t)Cp;
+    const size_t bytes_k = has_dist ? (sizeof(int) + 2 * sizeof(float)) * (size_t)C : 0;
     McBufs buf;
-    if (cudaMalloc(&buf.p, bytes_u + bytes_d + bytes_f + bytes_p) != cudaSuccess) {
+    if (cudaMalloc(&buf.p, bytes_u + bytes_d + bytes_f + bytes_p + bytes_k) != cudaSuccess) {
         cudaGetLastError();
-        return rid_fail(RID_ERR_OOM, "mcmc: device allocation of %zu bytes failed", bytes_u + bytes_d + bytes_f + bytes_p);
+        return rid_fail(RID_ERR_OOM, "mcmc: device allocation of %zu bytes failed",
+                        bytes_u + bytes_d + bytes_f + bytes_p + bytes_k);
     }
     unsigned long long* hist1 = reinterpret_cast<unsigned long long*>(buf.p);
     unsigned long long* hist2 = hist1 + n1;
@@ -280,6 +326,28 @@ extern "C" RID_API int rid_mcmc(const rid_mcmc_desc* d, const float* s0, float* 
     float* tb = d->resnet ? hb[1] + nH : nullptr;
     float* pnodes = (d->resnet ? tb + nH : hb[1] + nH);
     int* pcv = reinterpret_cast<int*>(pnodes + npn);
+    McCvDev cvk;
+    if (has_dist) {
+        int* kd = pcv + Cp;
+        float* klo = reinterpret_cast<float*>(kd + C);
+        std::vector<int> hd(C);
+        std::vector<float> hr(2 * (size_t)C, 0.0f);
+        for (int c = 0; c < C; ++c) {
+            hd[c] = d->cv_dist[c] ? 1 : 0;
+            if (hd[c]) {
+                hr[c] = (float)d->cv_lo[c];
+                hr[C + c] = (float)d->cv_hi[c];
+            }
+        }
+        cudaError_t e1 = cudaMemcpyAsync(kd, hd.data(), sizeof(int) * C, cudaMemcpyHostToDevice, (cudaStream_t)stream);
+        if (e1 == cudaSuccess)
+            e1 = cudaMemcpyAsync(klo, hr.data(), sizeof(float) * 2 * C, cudaMemcpyHostToDevice, (cudaStream_t)stream);
+        if (e1 == cudaSuccess) e1 = cudaStreamSynchronize((cudaStream_t)stream);   // host staging goes out of scope
+        if (e1 != cudaSuccess) return mc_cuda(e1, "CV ranges");
+        cvk.dist = kd;
+        cvk.lo = klo;
+        cvk.hi = klo + C;
+    }
     const cudaMemcpyKind kin = mem == RID_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     const cudaMemcpyKind kout = mem == RID_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     cudaError_t e;
@@ -346,15 +414,16 @@ extern "C" RID_API int rid_mcmc(const rid_mcmc_desc* d, const float* s0, float* 
     aa.z_lo = (float)d->path_z_lo;
     aa.z_hi = (float)d->path_z_hi;
     aa.histp = histp;
+    aa.cvk = cvk;
     const int wpb = 4;                                  // walkers (warps) per CTA
     const int ab = (W + wpb - 1) / wpb;
-    k_mc_features<<<eb, 256, 0, st>>>(s, U, nS);
+    k_mc_features<<<eb, 256, 0, st>>>(s, U, nS, C, cvk);
     forward();
     aa.init = 1;
     k_mc_accept<<<ab, 32 * wpb, 0, st>>>(aa);
     aa.init = 0;
     for (int64_t t = 0; t < d->n_steps; ++t) {
-        k_mc_propose<<<eb, 256, 0, st>>>(s, sp, U, W, C, (uint32_t)t, (float)d->step_size, k0, k1);
+        k_mc_propose<<<eb, 256, 0, st>>>(s, sp, U, W, C, (uint32_t)t, (float)d->step_size, k0, k1, cvk);
         forward();
         aa.step = (uint32_t)t;
         aa.count = t >= d->n_burn;
@@ -387,23 +456,25 @@ extern "C" RID_API int rid_mcmc(const rid_mcmc_desc* d, const float* s0, float* 
 // ---------------------------------------------------------------------------
 // Launchers for rid_mcmc_system (rid_api.cu), which evaluates the ensemble
 // with a system's own kernels and precision.
-void rid_launch_mc_features(const float* s, float* U, long long n, cudaStream_t st) {
+void rid_launch_mc_features(const float* s, float* U, long long n, int C, const McCvDev& cvk, cudaStream_t st) {
     const int eb = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    k_mc_features<<<eb, 256, 0, st>>>(s, U, n);
+    k_mc_features<<<eb, 256, 0, st>>>(s, U, n, C, cvk);
 }
 
 void rid_launch_mc_propose(const float* s, float* sp, float* U, int W, int C, uint32_t step, float step_size,
-                           uint32_t k0, uint32_t k1, cudaStream_t st) {
+                           uint32_t k0, uint32_t k1, const McCvDev& cvk, cudaStream_t st) {
     const long long n = (long long)W * C;
     const int eb = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    k_mc_propose<<<eb, 256, 0, st>>>(s, sp, U, W, C, step, step_size, k0, k1);
+    k_mc_propose<<<eb, 256, 0, st>>>(s, sp, U, W, C, step, step_size, k0, k1, cvk);
 }
 
 void rid_launch_mc_accept_values(const float* aval, int na, int M, int W, int C, float* s, const float* sp, float* A,
                                  uint32_t step, float kT, uint32_t k0, uint32_t k1, int init, int count, int bins,
                                  int pi, int pj, unsigned long long* hist1, unsigned long long* hist2,
-                                 unsigned long long* nacc, const McPathDev& path, cudaStream_t st) {
+                                 unsigned long long* nacc, const McPathDev& path, const McCvDev& cvk,
+                                 cudaStream_t st) {
     AcceptArgs a{};
+    a.cvk = cvk;
     a.npath = path.n_nodes;
     a.Cp = path.n_cv;
     a.pcv = path.cv;

@@ -1258,7 +1258,8 @@ extern "C" int rid_label(rid_system* sys, int32_t R, const float* x0, const floa
 // allocated for the call.
 extern "C" int rid_mcmc_system(rid_system* sys, int32_t W, const float* s0, int64_t n_steps, int64_t n_burn,
                                double kT, double step_size, uint64_t seed, int32_t bins, int32_t proj_i,
-                               int32_t proj_j, const rid_mcmc_path* path, float* s_out, uint64_t* hist1_out,
+                               int32_t proj_j, const double* cv_lo, const double* cv_hi, const rid_mcmc_path* path,
+                               float* s_out, uint64_t* hist1_out,
                                uint64_t* hist2_out, double* pmf1_out, double* pmf2_out, uint64_t* histp_out,
                                double* pmfp_out, int64_t* n_accepted, int32_t mem, void* stream) {
     NvtxScope nvtx_("rid_mcmc_system");
@@ -1272,6 +1273,11 @@ extern "C" int rid_mcmc_system(rid_system* sys, int32_t W, const float* s0, int6
     if ((long long)W * sys->S.N > (1ll << 31)) return fail(RID_ERR_ARG, "n_walkers * n_beads too large");
     const int NP = path ? path->n_nodes : 0, Cp = path ? path->n_cv : 0;
     if (path) TRY(rid_mc_path_check(NP, Cp, C, path->cv, path->nodes, path->lambda, path->z_lo, path->z_hi));
+    std::vector<int32_t> kinds(C, 0);
+    if (sys->has_dist) {
+        CK(cudaMemcpy(kinds.data(), sys->d_cvdist.p, sizeof(int) * C, cudaMemcpyDeviceToHost));
+        TRY(rid_mc_range_check(C, kinds.data(), cv_lo, cv_hi));
+    }
     TRY(check_device(sys));
     sys->loaded = false;   // the resident walker buffers are reused
     sys->pending = false;
@@ -1289,7 +1295,8 @@ extern "C" int rid_mcmc_system(rid_system* sys, int32_t W, const float* s0, int6
     const size_t o_h1 = 0, o_h2 = o_h1 + 8 * n1, o_hp = o_h2 + 8 * n2, o_na = o_hp + 8 * np2, o_p1 = o_na + 16;
     const size_t o_p2 = o_p1 + 8 * n1, o_pp = o_p2 + 8 * n2, o_s = o_pp + 8 * np2, o_sp = o_s + 4 * nS;
     const size_t o_A = o_sp + 4 * nS, o_pn = o_A + ((4 * (size_t)W + 15) & ~(size_t)15), o_pc = o_pn + 4 * npn;
-    TRY(scoped.b.ensure(o_pc + 4 * (size_t)Cp));
+    const size_t o_rg = o_pc + 4 * (size_t)Cp;   // distance-CV ranges lo [C], hi [C]
+    TRY(scoped.b.ensure(o_rg + 8 * (size_t)C));
     unsigned char* b = static_cast<unsigned char*>(scoped.b.p);
     auto* h1 = reinterpret_cast<unsigned long long*>(b + o_h1);
     auto* h2 = reinterpret_cast<unsigned long long*>(b + o_h2);
@@ -1315,19 +1322,32 @@ extern "C" int rid_mcmc_system(rid_system* sys, int32_t W, const float* s0, int6
     }
     const cudaMemcpyKind kin = mem == RID_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     const cudaMemcpyKind kout = mem == RID_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    McCvDev cvk;
+    std::vector<float> rg(2 * (size_t)C, 0.0f);
+    if (sys->has_dist) {
+        for (int c = 0; c < C; ++c)
+            if (kinds[c]) {
+                rg[c] = (float)cv_lo[c];
+                rg[C + c] = (float)cv_hi[c];
+            }
+        CK(cudaMemcpy(b + o_rg, rg.data(), 8 * (size_t)C, cudaMemcpyHostToDevice));
+        cvk.dist = sys->d_cvdist.as<int>();
+        cvk.lo = reinterpret_cast<float*>(b + o_rg);
+        cvk.hi = cvk.lo + C;
+    }
     CK(cudaMemcpyAsync(ds, s0, sizeof(float) * nS, kin, st));
     CK(cudaMemsetAsync(b, 0, o_p1, st));
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     const int M = sys->E.M, nav = M * sys->E.aslices;
-    rid_launch_mc_features(ds, sd.u, nS, st);
+    rid_launch_mc_features(ds, sd.u, nS, C, cvk, st);
     TRY(launch_mlp(sys, W, 1, sd, st, true));
     rid_launch_mc_accept_values(sd.Aval, nav, M, W, C, ds, dsp, dA, 0u, (float)kT, k0, k1, 1, 0, bins, proj_i, proj_j,
-                                h1, h2, na, pd, st);
+                                h1, h2, na, pd, cvk, st);
     for (int64_t t = 0; t < n_steps; ++t) {
-        rid_launch_mc_propose(ds, dsp, sd.u, W, C, (uint32_t)t, (float)step_size, k0, k1, st);
+        rid_launch_mc_propose(ds, dsp, sd.u, W, C, (uint32_t)t, (float)step_size, k0, k1, cvk, st);
         TRY(launch_mlp(sys, W, 1, sd, st, true));
         rid_launch_mc_accept_values(sd.Aval, nav, M, W, C, ds, dsp, dA, (uint32_t)t, (float)kT, k0, k1, 0,
-                                    t >= n_burn, bins, proj_i, proj_j, h1, h2, na, pd, st);
+                                    t >= n_burn, bins, proj_i, proj_j, h1, h2, na, pd, cvk, st);
     }
     rid_launch_mc_pmf(h1, C, bins, kT, p1, st);
     rid_launch_mc_pmf(h2, 1, (int)n2, kT, p2, st);

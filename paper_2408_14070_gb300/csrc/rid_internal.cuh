@@ -219,9 +219,16 @@ void rid_launch_mb(const SysDev& S, StateDev st, int W, uint32_t step0, cudaStre
 void rid_launch_pair_mask(const SysDev& S, StateDev st, int W, uint32_t* mask, cudaStream_t s);
 int rid_ff_smem_bytes(int N);
 size_t rid_label_cons_smem(int N, int C);
-void rid_launch_mc_features(const float* s, float* U, long long n, cudaStream_t st);
+// CV kinds of an MCMC run: dist [C] (1: a distance CV, not periodic, moved and
+// binned inside [lo, hi]; NULL: every CV a torsion), lo / hi [C].
+struct McCvDev {
+    const int* dist = nullptr;
+    const float* lo = nullptr;
+    const float* hi = nullptr;
+};
+void rid_launch_mc_features(const float* s, float* U, long long n, int C, const McCvDev& cvk, cudaStream_t st);
 void rid_launch_mc_propose(const float* s, float* sp, float* U, int W, int C, uint32_t step, float step_size,
-                           uint32_t k0, uint32_t k1, cudaStream_t st);
+                           uint32_t k0, uint32_t k1, const McCvDev& cvk, cudaStream_t st);
 // Device side of a path projection (n_nodes = 0: off).
 struct McPathDev {
     int n_nodes = 0, n_cv = 0;
@@ -230,13 +237,16 @@ struct McPathDev {
     float lambda = 0.0f, z_lo = 0.0f, z_hi = 0.0f;
     unsigned long long* hist = nullptr;    // [bins][bins]
 };
+// Checks the ranges of the distance CVs of an MCMC run (RID_OK or RID_ERR_ARG).
+int rid_mc_range_check(int C, const int32_t* dist, const double* lo, const double* hi);
 // Checks a path projection's host arguments against C CVs (RID_OK or RID_ERR_ARG).
 int rid_mc_path_check(int n_nodes, int n_cv, int C, const int32_t* cv, const float* nodes, double lambda,
                       double z_lo, double z_hi);
 void rid_launch_mc_accept_values(const float* aval, int na, int M, int W, int C, float* s, const float* sp, float* A,
                                  uint32_t step, float kT, uint32_t k0, uint32_t k1, int init, int count, int bins,
                                  int pi, int pj, unsigned long long* hist1, unsigned long long* hist2,
-                                 unsigned long long* nacc, const McPathDev& path, cudaStream_t st);
+                                 unsigned long long* nacc, const McPathDev& path, const McCvDev& cvk,
+                                 cudaStream_t st);
 void rid_launch_mc_pmf(const unsigned long long* hist, int rows, int n, double kT, double* pmf, cudaStream_t st);
 cudaError_t rid_launch_label_cons(const SysDev& S, int R, int C, int B, long long n_steps, long long n_equil,
                                   uint32_t step0, float kT, const float4* x0, const float4* v0, const int2* pairs,

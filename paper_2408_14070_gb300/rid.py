@@ -69,7 +69,8 @@ class McmcDesc(C.Structure):
                 ("n_burn", C.c_int64), ("kT", C.c_double), ("step_size", C.c_double), ("seed", C.c_uint64),
                 ("bins", C.c_int32), ("proj_i", C.c_int32), ("proj_j", C.c_int32), ("path_n_nodes", C.c_int32),
                 ("path_n_cv", C.c_int32), ("path_cv", C.c_void_p), ("path_nodes", C.c_void_p),
-                ("path_lambda", C.c_double), ("path_z_lo", C.c_double), ("path_z_hi", C.c_double)]
+                ("path_lambda", C.c_double), ("path_z_lo", C.c_double), ("path_z_hi", C.c_double),
+                ("cv_dist", C.c_void_p), ("cv_lo", C.c_void_p), ("cv_hi", C.c_void_p)]
 
 
 class McmcPath(C.Structure):
@@ -158,7 +159,7 @@ def lib() -> C.CDLL:
     L.rid_trainer_weights.argtypes = [vp, vp, C.POINTER(i64), i32, vp]
     L.rid_label_constrained.argtypes = [vp, i32, vp, vp, i32, vp, vp, u64, i64, i64, i32, vp, vp, vp, vp, vp,
                                         i32, vp]
-    L.rid_mcmc_system.argtypes = [vp, i32, vp, i64, i64, C.c_double, C.c_double, u64, i32, i32, i32,
+    L.rid_mcmc_system.argtypes = [vp, i32, vp, i64, i64, C.c_double, C.c_double, u64, i32, i32, i32, vp, vp,
                                   C.POINTER(McmcPath), vp, vp, vp, vp, vp, vp, vp, C.POINTER(i64), i32, vp]
     L.rid_select.argtypes = [C.POINTER(SelectDesc), i32, vp, vp, vp, C.POINTER(i32), C.POINTER(i32),
                              C.POINTER(C.c_double), i32, vp]
@@ -310,13 +311,19 @@ class System:
                                            _stream_ptr(stream)))
 
     def mcmc(self, s0, n_steps, n_burn, kT, step_size, seed, bins=101, pair=(0, 1), s_out=None, hist1=None,
-             hist2=None, pmf1=None, pmf2=None, path=None, hist_path=None, pmf_path=None, stream=None):
+             hist2=None, pmf1=None, pmf2=None, path=None, hist_path=None, pmf_path=None, cv_range=None,
+             stream=None):
         """MCMC dimension reduction with this system's ensemble at its precision
         (rid_mcmc_system); returns the number of accepted moves.  path = (nodes
         [P][Cp], cvs [Cp], lambda, z_lo, z_hi) adds the (s_path, z_path)
-        projection into hist_path / pmf_path [bins][bins]."""
+        projection into hist_path / pmf_path [bins][bins].  cv_range = (lo [C],
+        hi [C]): the range of each distance CV (systems with distance CVs)."""
         W = int(s0.shape[0])
         a = _Args()
+        lo = hi = None
+        if cv_range is not None:
+            lo = np.ascontiguousarray(cv_range[0], dtype=np.float64)
+            hi = np.ascontiguousarray(cv_range[1], dtype=np.float64)
         ps = a.ptr(s0, np.float32, (W, self.C))
         outs = [a.ptr(s_out, np.float32, (W, self.C), True), a.ptr(hist1, np.uint64, (self.C, bins), True),
                 a.ptr(hist2, np.uint64, (bins, bins), True), a.ptr(pmf1, np.float64, (self.C, bins), True),
@@ -329,6 +336,7 @@ class System:
         nacc = C.c_int64(0)
         _check(lib().rid_mcmc_system(self.h, W, ps, C.c_int64(n_steps), C.c_int64(n_burn), float(kT),
                                      float(step_size), C.c_uint64(seed), int(bins), int(pair[0]), int(pair[1]),
+                                     None if lo is None else lo.ctypes.data, None if hi is None else hi.ctypes.data,
                                      None if pp is None else C.byref(pp), *outs, C.byref(nacc), a.mem,
                                      _stream_ptr(stream)))
         return nacc.value
@@ -632,13 +640,15 @@ class Trainer:
 
 def mcmc(weights, n_models, n_cv, n_layers, width, s0, n_steps, n_burn, kT, step_size, seed, bins=101,
          pair=(0, 1), resnet=False, s_out=None, hist1=None, hist2=None, pmf1=None, pmf2=None, path=None,
-         hist_path=None, pmf_path=None, stream=None):
+         hist_path=None, pmf_path=None, cv_dist=None, cv_range=None, stream=None):
     """MCMC dimension reduction (rid_mcmc): W = len(s0) walkers, Metropolis on
     the ensemble-mean free energy; returns the number of accepted moves.
     Outputs (optional, all on the side of s0): s_out [W][C] float32, hist1
     [C][bins] and hist2 [bins][bins] uint64, pmf1 / pmf2 of the same shapes
     float64.  path = (nodes [P][Cp], cvs [Cp], lambda, z_lo, z_hi) adds the
-    (s_path, z_path) projection into hist_path / pmf_path [bins][bins]."""
+    (s_path, z_path) projection into hist_path / pmf_path [bins][bins].
+    cv_dist [C] (bool) marks distance CVs, moved and binned inside cv_range =
+    (lo [C], hi [C])."""
     a = _Args()
     W, Cn = int(s0.shape[0]), int(n_cv)
     pw = a.ptr(weights, np.float32)
@@ -655,10 +665,17 @@ def mcmc(weights, n_models, n_cv, n_layers, width, s0, n_steps, n_burn, kT, step
     if path is not None:
         nodes, cvs, lam, zlo, zhi = _path_arrays(path)
         npn, ncv = nodes.shape[0], cvs.size
+    kd = lo = hi = None
+    if cv_dist is not None:
+        kd = np.ascontiguousarray(cv_dist, dtype=np.int32)
+        if cv_range is not None:
+            lo = np.ascontiguousarray(cv_range[0], dtype=np.float64)
+            hi = np.ascontiguousarray(cv_range[1], dtype=np.float64)
     d = McmcDesc(int(n_models), Cn, int(n_layers), int(width), int(bool(resnet)), pw.value, W, int(n_steps),
                  int(n_burn), float(kT), float(step_size), int(seed), int(bins), int(pair[0]), int(pair[1]),
                  npn, ncv, None if cvs is None else cvs.ctypes.data, None if nodes is None else nodes.ctypes.data,
-                 lam, zlo, zhi)
+                 lam, zlo, zhi, None if kd is None else kd.ctypes.data, None if lo is None else lo.ctypes.data,
+                 None if hi is None else hi.ctypes.data)
     nacc = C.c_int64(0)
     _check(lib().rid_mcmc(C.byref(d), ps, po, h1, h2, f1, f2, hp, fp, C.byref(nacc), a.mem, _stream_ptr(stream)))
     return nacc.value

@@ -138,7 +138,7 @@ def test_descriptor_checks_answer_before_device_work(L):
         n1, n2, t = C.c_int32(), C.c_int32(), C.c_double()
         assert L.rid_select(C.byref(d), 4, s0.ctypes.data, eps.ctypes.data, sel.ctypes.data, C.byref(n1),
                             C.byref(n2), C.byref(t), 0, None) == rid.RID_ERR_ARG, bad
-    assert L.rid_mcmc_system(None, 4, s0.ctypes.data, 5, 0, 1.0, 0.3, 1, 10, 0, 1, None, *([None] * 7), None, 0,
-                             None) == rid.RID_ERR_ARG
+    assert L.rid_mcmc_system(None, 4, s0.ctypes.data, 5, 0, 1.0, 0.3, 1, 10, 0, 1, None, None, None, *([None] * 7),
+                             None, 0, None) == rid.RID_ERR_ARG
     assert L.rid_label_constrained(None, 1, None, None, 1, None, None, 0, 10, 0, 2, None, None, None, None, None, 0,
                                    None) == rid.RID_ERR_ARG

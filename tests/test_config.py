@@ -100,7 +100,8 @@ def test_path_projection_and_its_z_range():
     ({"LabelMDConfig": {"method": "constrained"}}, "distance CVs"),
     ({"Train": {"neurons": [64, 32]}}, "one width"),
     ({"trust_lvl_1": 3, "trust_lvl_2": 3}, "trust_lvl_2"),
-    ({"MCMC_Config": {"cv_type": "dis"}}, "torsion CVs"),
+    ({"MCMC_Config": {"cv_type": "dis"}}, "does not match"),
+    ({"MCMC_Config": {"cv_type": "xyz"}}, "'dih'"),
     ({"MCMC_Config": {"proj_info": {"proj_mode": "cv", "proj_cv_index": [0, 9]}}}, "outside"),
 ])
 def test_errors(patch, msg):
@@ -123,3 +124,28 @@ def test_mapped_arguments_bind_to_the_binding():
     m = c.mcmc
     inspect.signature(rid.System.mcmc).bind(None, None, m["n_steps"], 0, m["kT"], 0.3, 1, bins=m["bins"],
                                             pair=m["pair"], path=m["path"])
+
+
+def test_distance_mcmc_ranges_and_cv_rows():
+    """cv_type "dis" with the paper's cv_lower_bound / cv_upper_bound: the
+    walk's ranges, the path's z range from them, and the system's CV rows."""
+    cfg = {"CV": {"mode": "distance", "selected_atomid": [[2, 5], [5, 7], [9, 12]], "angular_mask": [0, 0, 0]},
+           "LabelMDConfig": {"method": "restrained", "kappas": [500, 500, 500]},
+           "MCMC_Config": {"numb_walkers": 64, "numb_steps": 100, "temperature": 300, "bins": 41,
+                           "cv_type": "dis", "cv_lower_bound": [1.0, 2.0, 0.5], "cv_upper_bound": [4.5, 5.0, 3.5],
+                           "proj_info": {"proj_mode": "path", "proj_cv_index": [0, 2],
+                                         "path_list": [[1.5, 1.0], [3.0, 2.0], [4.0, 3.0]], "path_lm": 2.0}}}
+    c = K.load(cfg, reduced=True)
+    assert np.array_equal(c.mcmc["cv_dist"], [True, True, True])
+    lo, hi = c.mcmc["cv_range"]
+    assert np.array_equal(lo, [1.0, 2.0, 0.5]) and np.array_equal(hi, [4.5, 5.0, 3.5])
+    nodes, idx, lam, z_lo, z_hi = c.mcmc["path"]
+    assert z_lo == pytest.approx(-np.log(3) / 2.0) and z_hi == pytest.approx(3.5 ** 2 + 3.0 ** 2)
+    assert np.array_equal(K.cv_atoms(c), [[1, 4, -1, -1], [4, 6, -1, -1], [8, 11, -1, -1]])
+    bad = dict(cfg["MCMC_Config"])
+    del bad["cv_lower_bound"]
+    with pytest.raises(ValueError, match="cv_lower_bound"):
+        K.load(dict(cfg, MCMC_Config=bad), reduced=True)
+    bad = dict(cfg["MCMC_Config"], cv_upper_bound=[1.0, 2.0, 0.5])
+    with pytest.raises(ValueError, match="exceed"):
+        K.load(dict(cfg, MCMC_Config=bad), reduced=True)

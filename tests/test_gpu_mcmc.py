@@ -246,3 +246,108 @@ def test_system_path_tensor_cores_sample_the_stationary_marginal(R, prec, bound)
     tv = 0.5 * np.abs(h2 / h2.sum() - p).sum()
     print(f"\n[{prec}] total variation against the exact joint: {tv:.4f}")
     assert tv < bound, tv
+
+
+# ------------------------------------------------------------------ distance CVs
+def _mixed_diff(a, b, dist):
+    d = np.asarray(a, np.float64) - np.asarray(b, np.float64)
+    d[:, ~dist] = d[:, ~dist] - 2 * math.pi * np.round(d[:, ~dist] / (2 * math.pi))
+    return np.abs(d)
+
+
+def _bins_f32_range(s, lo, hi, bins):
+    # floor((s - lo) / (hi - lo) * bins), each operation rounded to FP32
+    t = (np.float32(s) - np.float32(lo)).astype(np.float32)
+    t = (t / (np.float32(hi) - np.float32(lo))).astype(np.float32)
+    t = (t * np.float32(bins)).astype(np.float32)
+    return np.clip(np.floor(t).astype(np.int64), 0, bins - 1)
+
+
+def _mixed_start(W, C, dist, lo, hi, seed):
+    rng = np.random.default_rng(seed)
+    s0 = rng.uniform(-math.pi, math.pi, size=(W, C))
+    for c in np.flatnonzero(dist):
+        s0[:, c] = rng.uniform(lo[c], hi[c], size=W)
+    return s0.astype(np.float32)
+
+
+def test_distance_cvs_follow_the_oracle_and_bin_exactly(R):
+    """rid_mcmc with two distance CVs (ranges [1, 3] and [2, 5]) beside three
+    torsions: walker paths against the oracle (near-threshold and near-edge
+    walkers left out), every state inside its range, exact counting in the
+    range bins."""
+    M, C, L, H, W, K = 3, 5, 3, 48, 256, 30
+    dist = np.array([False, True, False, True, False])
+    lo = np.array([0.0, 1.0, 0.0, 2.0, 0.0])
+    hi = np.array([0.0, 3.0, 0.0, 5.0, 0.0])
+    ens = I.make_ensemble(M, 2 * C, L, H, 41, resnet=True)
+    s0 = _mixed_start(W, C, dist, lo, hi, 41)
+    bins = 23
+    s = np.zeros_like(s0)
+    h1 = np.zeros((C, bins), np.uint64)
+    h2 = np.zeros((bins, bins), np.uint64)
+    nacc = R.mcmc(ens.weights, M, C, L, H, s0, K, K - 1, 1.0, 0.4, 19, bins=bins, pair=(1, 2), resnet=True,
+                  s_out=s, hist1=h1, hist2=h2, cv_dist=dist, cv_range=(lo, hi))
+    ref = MC.run(ens.weights, C, L, H, True, s0, K, K - 1, 1.0, 0.4, 19, bins, (1, 2), dist=dist, lo=lo, hi=hi)
+    safe = ref["min_margin"] > 1e-3
+    print(f"\n[mixed] near-threshold / near-edge walkers: {int((~safe).sum())} of {W}; accepted {nacc} "
+          f"(oracle {ref['n_accepted']})")
+    assert safe.mean() > 0.9
+    assert np.max(_mixed_diff(s[safe], ref["s"][safe], dist)) < 1e-4
+    assert abs(nacc - ref["n_accepted"]) <= K * int((~safe).sum())
+    assert 0 < nacc < W * K
+    for c in np.flatnonzero(dist):
+        assert np.all((s[:, c] >= lo[c]) & (s[:, c] <= hi[c]))
+    # only the last step is counted: the final states, binned with the FP32 operations
+    for c in range(C):
+        b = _bins_f32_range(s[:, c], lo[c], hi[c], bins) if dist[c] else _bins_f32(s[:, c], bins)
+        np.testing.assert_array_equal(h1[c], np.bincount(b, minlength=bins))
+    want2 = np.zeros((bins, bins), np.int64)
+    np.add.at(want2, (_bins_f32_range(s[:, 1], lo[1], hi[1], bins), _bins_f32(s[:, 2], bins)), 1)
+    np.testing.assert_array_equal(h2, want2)
+
+
+def test_system_with_distance_cvs_follows_the_oracle(R):
+    """rid_mcmc_system on a system mixing torsions and distances (FP32
+    ensemble kernels; the kinds come from the system's cv_atoms)."""
+    M, C, L, H, W, K = 4, 6, 3, 64, 192, 25
+    sp = I.make_system(40, C, 42, n_dist=2)
+    dist = I.cv_is_distance(sp)
+    lo = np.where(dist, 1.5, 0.0)
+    hi = np.where(dist, 4.5, 0.0)
+    ens = I.make_ensemble(M, 2 * C, L, H, 42)
+    s0 = _mixed_start(W, C, dist, lo, hi, 42)
+    s = np.zeros_like(s0)
+    with R.System(sp) as sysobj:
+        sysobj.set_ensemble(ens, precision=R.RID_PREC_FP32)
+        nacc = sysobj.mcmc(s0, K, 0, 1.0, 0.3, 23, bins=51, s_out=s, cv_range=(lo, hi))
+        with pytest.raises(R.RidError) as e:
+            sysobj.mcmc(s0, 5, 0, 1.0, 0.3, 23, bins=51)            # distance CVs need their ranges
+        assert e.value.code == R.RID_ERR_ARG
+        with pytest.raises(R.RidError) as e:
+            sysobj.mcmc(s0, 5, 0, 1.0, 0.3, 23, bins=51, cv_range=(hi, lo))
+        assert e.value.code == R.RID_ERR_ARG
+    ref = MC.run(ens.weights, C, L, H, False, s0, K, 0, 1.0, 0.3, 23, 51, (0, 1), dist=dist, lo=lo, hi=hi)
+    safe = ref["min_margin"] > 1e-3
+    assert safe.mean() > 0.9
+    assert np.max(_mixed_diff(s[safe], ref["s"][safe], dist)) < 1e-4
+    assert abs(nacc - ref["n_accepted"]) <= K * int((~safe).sum())
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_system_with_distance_cvs_on_the_tensor_cores(R, prec):
+    """The same mixed system with a BF16 / FP8 ensemble: runs, keeps every
+    distance CV inside its range, and accepts moves."""
+    M, C, L, H, W, K = 4, 6, 3, 64, 512, 40
+    sp = I.make_system(40, C, 43, n_dist=2)
+    dist = I.cv_is_distance(sp)
+    lo, hi = np.where(dist, 1.5, 0.0), np.where(dist, 4.5, 0.0)
+    ens = I.make_ensemble(M, 2 * C, L, H, 43)
+    s0 = _mixed_start(W, C, dist, lo, hi, 43)
+    s = np.zeros_like(s0)
+    with R.System(sp) as sysobj:
+        sysobj.set_ensemble(ens, precision=R.RID_PREC_BF16 if prec == "bf16" else R.RID_PREC_FP8)
+        nacc = sysobj.mcmc(s0, K, 0, 1.0, 0.3, 29, bins=51, s_out=s, cv_range=(lo, hi))
+    assert 0 < nacc < W * K
+    for c in np.flatnonzero(dist):
+        assert np.all((s[:, c] >= lo[c]) & (s[:, c] <= hi[c]))

@@ -125,3 +125,81 @@ def test_path_cv_limits():
     bs, bz = MC.path_bins(np.array([1.0, 3.0, 5.0]), np.array([-1.0, 0.5, 9.0]), 5, 0.0, 1.0, 10)
     np.testing.assert_array_equal(bs, [0, 5, 9])
     np.testing.assert_array_equal(bz, [0, 5, 9])
+
+
+# --------------------------------------------------------------------------- distance CVs
+def _exact_mixed_bin_probs(weights, L, H, bins, kT, dist, lo, hi, sub=12):
+    """p(s) ~ exp(-Abar(s)/kT) on a midpoint grid of the box: [-pi, pi) for a
+    torsion, [lo, hi] for a distance CV, summed per bin."""
+    C = len(dist)
+    n = bins * sub
+    axes = []
+    for c in range(C):
+        a, b = (lo[c], hi[c]) if dist[c] else (-math.pi, math.pi)
+        axes.append(a + (np.arange(n) + 0.5) * ((b - a) / n))
+    grids = np.meshgrid(*axes, indexing="ij")
+    s = np.stack([x.ravel() for x in grids], axis=1)
+    A = MC.ensemble_mean_value(weights, 2 * C, L, H, False, s, np.asarray(dist))
+    p = np.exp(-(A - A.min()) / kT).reshape([n] * C)
+    p /= p.sum()
+    for ax in range(C):
+        p = np.add.reduceat(p, np.arange(0, n, sub), axis=ax)
+    return p, A.max() - A.min()
+
+
+def test_distance_cv_marginal_and_mixed_joint_match_the_stationary_density():
+    """A distance CV in [1, 4] next to a torsion: the walk must sample
+    exp(-Abar/kT) restricted to the box (moves leaving the range refused)."""
+    L, H, bins, kT = 2, 8, 12, 1.0
+    dist, lo, hi = np.array([False, True]), np.array([0.0, 1.0]), np.array([0.0, 4.0])
+    w = _net(4, L, H, 7, 1.3)
+    p, span = _exact_mixed_bin_probs(w, L, H, bins, kT, dist, lo, hi)
+    assert span > 2.0 * kT
+    rng = np.random.default_rng(5)
+    W = 400
+    s0 = np.stack([rng.uniform(-math.pi, math.pi, W), rng.uniform(1.0, 4.0, W)], axis=1)
+    r = MC.run(w, 2, L, H, False, s0, 500, 100, kT, 0.6, 13, bins, (0, 1), dist=dist, lo=lo, hi=hi)
+    assert np.all((r["s"][:, 1] >= 1.0) & (r["s"][:, 1] <= 4.0))
+    h2 = r["hist2"]
+    tv = 0.5 * np.abs(h2 / h2.sum() - p).sum()
+    assert tv < 0.06, tv
+    h1 = r["hist1"][1]
+    tv1 = 0.5 * np.abs(h1 / h1.sum() - p.sum(axis=0)).sum()
+    assert tv1 < 0.04, tv1
+    # read as a torsion (wrapped, (cos, sin) input) the same walk is a different density
+    q, _ = _exact_mixed_bin_probs(w, L, H, bins, kT, np.array([False, False]), lo, hi)
+    assert 0.5 * np.abs(h2 / h2.sum() - q).sum() > 0.1
+
+
+def test_distance_cv_range_refuses_moves_and_bins_span_it():
+    # a flat landscape: every proposal inside the range is taken, none outside
+    C, L, H = 1, 1, 4
+    w = np.zeros((1, T.param_count(2 * C, L, H)))
+    s0 = np.full((64, 1), 1.05)
+    r = MC.run(w, C, L, H, False, s0, 40, 0, 1.0, 0.5, 21, 10, (0, 0), dist=[True], lo=[1.0], hi=[2.0])
+    assert np.all((r["s"] >= 1.0) & (r["s"] <= 2.0))
+    moves = 0
+    s = s0[:, 0].astype(np.float64).copy()
+    for t in range(40):
+        sp = s + 0.5 * MC.proposal_normals(64, 1, t, 21)[:, 0]
+        ok = (sp >= 1.0) & (sp <= 2.0)
+        s[ok] = sp[ok]
+        moves += int(ok.sum())
+    assert r["n_accepted"] == moves
+    np.testing.assert_allclose(r["s"][:, 0], s, rtol=0, atol=0)
+    # bins over [lo, hi]
+    b = MC.bin_index(np.array([[1.0], [1.0999], [1.1], [1.95], [2.0]]), 10, [True], [1.0], [2.0])
+    assert list(b[:, 0]) == [0, 0, 1, 9, 9]
+
+
+def test_path_over_a_distance_cv_uses_plain_differences():
+    nodes = np.array([[0.5], [3.5]])
+    s = np.array([[6.3]])
+    sp, z = MC.path_cv(s, nodes, [0], 2.0, dist=np.array([True]))
+    d2 = np.array([5.8 ** 2, 2.8 ** 2])
+    e = np.exp(-2.0 * (d2 - d2.min()))
+    assert sp[0] == pytest.approx((e * [1, 2]).sum() / e.sum(), rel=1e-12)
+    assert z[0] == pytest.approx(d2.min() - math.log(e.sum()) / 2.0, rel=1e-12)
+    # a torsion reading would wrap 6.3 - 0.5 onto -0.48: node 1 nearest instead
+    sp_t, _ = MC.path_cv(s, nodes, [0], 2.0)
+    assert sp_t[0] < 1.5 < sp[0]
