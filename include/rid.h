@@ -240,6 +240,9 @@ typedef struct {
     double beta1, beta2, adam_eps;  /* Adam: 0.9, 0.999, 1e-8                   */
     double dropout_rate;          /* [0, 1): 0.1 in the paper, 0 = off          */
     uint64_t dropout_seed;        /* Philox key of the dropout masks            */
+    const int32_t* cv_dist;       /* [C] host or NULL: 1 marks a distance CV,   */
+                                  /* whose input pair is (s, 0) and dA/ds =     */
+                                  /* dA/du_2j (read at creation, not kept)      */
 } rid_train_desc;
 
 typedef struct rid_trainer rid_trainer;

@@ -48,22 +48,9 @@ def wrap(d):
     return d - 2.0 * math.pi * np.floor(d / (2.0 * math.pi) + 0.5)
 
 
-def features(s, dist=None):
-    """MLP input [W][2C]: (cos s, sin s) per torsion, (s, 0) per distance CV."""
-    s = np.asarray(s, dtype=np.float64)
-    u = T.features(s)
-    if dist is not None and np.any(dist):
-        d = np.asarray(dist, dtype=bool)
-        u = u.reshape(s.shape[0], -1, 2)
-        u[:, d, 0] = s[:, d]
-        u[:, d, 1] = 0.0
-        u = u.reshape(s.shape[0], -1)
-    return u
-
-
 def ensemble_mean_value(weights, D, L, H, resnet, s, dist=None):
     """Abar at points s [W][C] (float64), members' forward passes as matmuls."""
-    u = features(s, dist)
+    u = T.features(s, dist)
     tot = np.zeros(s.shape[0])
     for w in np.asarray(weights, dtype=np.float64):
         layers, w_out, b_out = T.unpack(w, D, L, H)

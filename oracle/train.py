@@ -6,7 +6,8 @@ CUDA library; both read the arrays made by ``paper_2408_14070_gb300.inputs``.
 
 What it computes (Sec. "Training phase" and Sec. "Training"; Introduction:
 the free energy is learnt by fitting its derivatives, the mean forces).  Every
-member i of the ensemble is a tanh MLP A_i(s) of u = (cos s_0, sin s_0, ...),
+member i of the ensemble is a tanh MLP A_i(s) of u = (cos s_0, sin s_0, ...)
+(a distance CV enters as (s_j, 0)),
 with the packed weight layout of the exploration kernels.  On a batch of
 labels (s_k, MF_k) the member's loss is the mean squared difference between
 its CV gradient and the label,
@@ -85,13 +86,42 @@ def unpack(w, D: int, L: int, H: int):
     return layers, w_out, b_out
 
 
-def features(s):
-    """u = (cos s_0, sin s_0, cos s_1, sin s_1, ...) for s [..., C]."""
+def features(s, dist=None):
+    """u = (cos s_0, sin s_0, cos s_1, sin s_1, ...) for s [..., C]; a distance
+    CV (dist [C] true) enters as (s_j, 0)."""
     s = np.asarray(s, dtype=np.float64)
     u = np.empty(s.shape[:-1] + (2 * s.shape[-1],))
     u[..., 0::2] = np.cos(s)
     u[..., 1::2] = np.sin(s)
+    if dist is not None and np.any(dist):
+        d = np.asarray(dist, dtype=bool)
+        u[..., 0::2][..., d] = s[..., d]
+        u[..., 1::2][..., d] = 0.0
     return u
+
+
+def cv_gradient(s, g, dist=None):
+    """dA/ds from dA/du through the input map: -sin s g[2j] + cos s g[2j+1] for
+    a torsion, g[2j] for a distance CV."""
+    s = np.asarray(s, dtype=np.float64)
+    out = -np.sin(s) * g[0::2] + np.cos(s) * g[1::2]
+    if dist is not None and np.any(dist):
+        d = np.asarray(dist, dtype=bool)
+        out[d] = g[0::2][d]
+    return out
+
+
+def cv_gradient_adjoint(s, v, dist=None):
+    """The adjoint of cv_gradient: d(v . dA/ds) / d(dA/du)."""
+    s = np.asarray(s, dtype=np.float64)
+    gbar = np.empty(2 * s.shape[-1])
+    gbar[0::2] = -np.sin(s) * v
+    gbar[1::2] = np.cos(s) * v
+    if dist is not None and np.any(dist):
+        d = np.asarray(dist, dtype=bool)
+        gbar[0::2][d] = v[d]
+        gbar[1::2][d] = 0.0
+    return gbar
 
 
 def dropout_threshold(rate: float) -> int:
@@ -110,12 +140,13 @@ def dropout_scales(M, B, L, H, step, seed, rate):
     return np.where(keep, 1.0 / (1.0 - rate), 0.0)
 
 
-def member_value_and_grad(w, D, L, H, resnet, s, q=None):
+def member_value_and_grad(w, D, L, H, resnet, s, q=None, dist=None):
     """A(s) and dA/ds for one member at one point (passes 1 and 2); q [L][H]
-    are the dropout scales of the point (None: no dropout)."""
+    are the dropout scales of the point (None: no dropout); dist [C] marks
+    distance CVs (None: all torsions)."""
     layers, w_out, b_out = unpack(np.asarray(w, dtype=np.float64), D, L, H)
     q = np.ones((L, H)) if q is None else np.asarray(q, dtype=np.float64)
-    u = features(s)
+    u = features(s, dist)
     h, ts = u, []
     for l, (W, b) in enumerate(layers):
         t = np.tanh(W @ h + b)
@@ -126,25 +157,24 @@ def member_value_and_grad(w, D, L, H, resnet, s, q=None):
     for l in range(L - 1, -1, -1):
         W = layers[l][0]
         g = W.T @ (g * q[l] * (1.0 - ts[l] ** 2)) + (g if (resnet and l >= 1) else 0.0)
-    s = np.asarray(s, dtype=np.float64)
-    dAds = -np.sin(s) * g[0::2] + np.cos(s) * g[1::2]
-    return A, dAds
+    return A, cv_gradient(s, g, dist)
 
 
-def loss(w, D, L, H, resnet, s_batch, mf_batch, q=None):
+def loss(w, D, L, H, resnet, s_batch, mf_batch, q=None, dist=None):
     """L = mean over the batch and the C components of (dA/ds - MF)^2; q
     [B][L][H] dropout scales (None: no dropout)."""
     s_batch = np.asarray(s_batch, dtype=np.float64)
     tot = 0.0
     for k, (s, mf) in enumerate(zip(s_batch, np.asarray(mf_batch, dtype=np.float64))):
-        _, g = member_value_and_grad(w, D, L, H, resnet, s, None if q is None else q[k])
+        _, g = member_value_and_grad(w, D, L, H, resnet, s, None if q is None else q[k], dist)
         tot += float(np.sum((g - mf) ** 2))
     return tot / s_batch.size
 
 
-def loss_and_grad(w, D, L, H, resnet, s_batch, mf_batch, q=None):
+def loss_and_grad(w, D, L, H, resnet, s_batch, mf_batch, q=None, dist=None):
     """Loss of one member on a batch and dL/dtheta in the packed layout; q
-    [B][L][H] dropout scales of the batch rows (None: no dropout)."""
+    [B][L][H] dropout scales of the batch rows (None: no dropout); dist [C]
+    marks distance CVs."""
     w = np.asarray(w, dtype=np.float64)
     s_batch = np.asarray(s_batch, dtype=np.float64)
     mf_batch = np.asarray(mf_batch, dtype=np.float64)
@@ -157,7 +187,7 @@ def loss_and_grad(w, D, L, H, resnet, s_batch, mf_batch, q=None):
     for s, mf, qs in zip(s_batch, mf_batch, q):
         r_ = [bool(resnet and l >= 1) for l in range(L)]
         # 1. forward
-        hs = [features(s)]                       # hs[l + 1] = h_l, hs[0] = u
+        hs = [features(s, dist)]                 # hs[l + 1] = h_l, hs[0] = u
         ts = []
         for l, (W, b) in enumerate(layers):
             t = np.tanh(W @ hs[l] + b)
@@ -171,13 +201,11 @@ def loss_and_grad(w, D, L, H, resnet, s_batch, mf_batch, q=None):
             ds[l] = gs[l + 1] * qs[l] * (1.0 - ts[l] ** 2)
             gs[l] = layers[l][0].T @ ds[l] + (gs[l + 1] if r_[l] else 0.0)
         # 3. loss and its adjoint with respect to dA/du
-        dAds = -np.sin(s) * gs[0][0::2] + np.cos(s) * gs[0][1::2]
+        dAds = cv_gradient(s, gs[0], dist)
         res = dAds - mf
         tot += float(np.sum(res ** 2))
         v = 2.0 * res / (B * C)
-        gbar = np.empty(D)
-        gbar[0::2] = -np.sin(s) * v
-        gbar[1::2] = np.cos(s) * v
+        gbar = cv_gradient_adjoint(s, v, dist)
         # 4. adjoint of the input-gradient pass, increasing l
         tbar = [None] * L
         for l in range(L):
@@ -214,7 +242,7 @@ def adam_update(w, g, m, v, step: int, lr: float, beta1: float, beta2: float, ep
 
 
 def train(weights, D, L, H, resnet, s_data, mf_data, idx, init_lr=8e-4, decay_rate=0.96, decay_steps=120,
-          beta1=0.9, beta2=0.999, eps=1e-8, step0=0, m=None, v=None, dropout_rate=0.0, dropout_seed=0):
+          beta1=0.9, beta2=0.999, eps=1e-8, step0=0, m=None, v=None, dropout_rate=0.0, dropout_seed=0, dist=None):
     """Run len(idx) steps; idx [n_steps][M][B] holds each member's batch of
     sample indices.  Returns (weights [M][P], losses [n_steps][M], m, v)."""
     w = np.array(weights, dtype=np.float64)
@@ -234,6 +262,6 @@ def train(weights, D, L, H, resnet, s_data, mf_data, idx, init_lr=8e-4, decay_ra
         for i in range(Mn):
             b = idx[k, i]
             losses[k, i], g = loss_and_grad(w[i], D, L, H, resnet, s_data[b], mf_data[b],
-                                            None if q is None else q[i])
+                                            None if q is None else q[i], dist)
             w[i], m[i], v[i] = adam_update(w[i], g, m[i], v[i], t, lr, beta1, beta2, eps)
     return w, losses, m, v

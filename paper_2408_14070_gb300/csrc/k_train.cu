@@ -59,12 +59,12 @@ __device__ __forceinline__ void tr_mask_block(const MaskArgs& a, int M, int B, l
         if (4 * k + c < a.H) q[c] = wd[c] >= a.thr ? a.scale : 0.0f;
 }
 
-// u = (cos s, sin s) of each member's batch, plus the batch's s and labels,
-// and the step's dropout scales.  idx is checked; an index outside [0, n)
-// reads sample 0 and sets *bad.
+// u = (cos s, sin s) of each member's batch ((s, 0) for a distance CV:
+// dist[j] != 0), plus the batch's s and labels, and the step's dropout
+// scales.  idx is checked; an index outside [0, n) reads sample 0 and sets *bad.
 __global__ void k_tr_gather(const int* __restrict__ idx, const float* __restrict__ s, const float* __restrict__ mf,
                             int n, int M, int B, int C, float* __restrict__ U, float* __restrict__ SB,
-                            float* __restrict__ MFB, int* bad, MaskArgs mk) {
+                            float* __restrict__ MFB, int* bad, MaskArgs mk, const int* __restrict__ dist) {
     pdl_trigger();
     pdl_wait();
     if (mk.Q) {
@@ -82,10 +82,15 @@ __global__ void k_tr_gather(const int* __restrict__ idx, const float* __restrict
             k = 0;
         }
         const float sv = s[(long long)k * C + j];
-        float sn, cs;
-        sincosf(sv, &sn, &cs);
-        U[mb * 2 * C + 2 * j] = cs;
-        U[mb * 2 * C + 2 * j + 1] = sn;
+        if (dist && dist[j]) {
+            U[mb * 2 * C + 2 * j] = sv;
+            U[mb * 2 * C + 2 * j + 1] = 0.0f;
+        } else {
+            float sn, cs;
+            sincosf(sv, &sn, &cs);
+            U[mb * 2 * C + 2 * j] = cs;
+            U[mb * 2 * C + 2 * j + 1] = sn;
+        }
         SB[e] = sv;
         MFB[e] = mf[(long long)k * C + j];
     }
@@ -98,7 +103,8 @@ __global__ void k_tr_gather(const int* __restrict__ idx, const float* __restrict
 constexpr int LT = 256;
 __global__ void __launch_bounds__(LT) k_tr_loss(const float* __restrict__ G0, const float* __restrict__ SB,
                                                 const float* __restrict__ MFB, int B, int C,
-                                                float* __restrict__ GB0, double* __restrict__ lpart) {
+                                                float* __restrict__ GB0, double* __restrict__ lpart,
+                                                const int* __restrict__ dist) {
     pdl_trigger();
     pdl_wait();
     __shared__ double red[LT];
@@ -110,15 +116,17 @@ __global__ void __launch_bounds__(LT) k_tr_loss(const float* __restrict__ G0, co
     if (e < n) {
         const long long o = (long long)m * n + e;
         const float sv = SB[o];
-        float sn, cs;
-        sincosf(sv, &sn, &cs);
         const long long u = (long long)m * 2 * n + 2 * e;     // (b, j) -> u index 2 (b C + j)
-        const float dads = fmaf(cs, G0[u + 1], -sn * G0[u]);
+        // a distance CV (input (s, 0)): dA/ds = dA/du_2j; a torsion: through (cos, sin)
+        const bool dj = dist && dist[e % C];
+        float sn = 0.0f, cs = 1.0f;
+        if (!dj) sincosf(sv, &sn, &cs);
+        const float dads = dj ? G0[u] : fmaf(cs, G0[u + 1], -sn * G0[u]);
         const float r = dads - MFB[o];
         part += (double)r * r;
         const float v = scale * r;
-        GB0[u] = -sn * v;
-        GB0[u + 1] = cs * v;
+        GB0[u] = dj ? v : -sn * v;
+        GB0[u + 1] = dj ? 0.0f : cs * v;
     }
     red[threadIdx.x] = part;
     __syncthreads();
@@ -206,6 +214,7 @@ struct rid_trainer {
     float* dloss = nullptr;  // [cap_loss]
     long long cap_loss = 0;
     int* dbad = nullptr;
+    int* ddist = nullptr;     // [C] 1 for a distance CV, or NULL (all torsions)
     double* lpart = nullptr;  // [M][ceil(B C / 256)] loss chunk sums
     // carve of act, all [M][B][X]
     float *U, *SB, *MFB, *G0, *GB0;
@@ -257,7 +266,8 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, bool
         if (mk.Q && (long long)L * M * B * ((H + 3) / 4) > tot) tot = (long long)L * M * B * ((H + 3) / 4);
         const int blocks = (int)((tot + 255) / 256 < 1024 ? (tot + 255) / 256 : 1024);
         TCK(launch_k(k_tr_gather, dim3(blocks), dim3(256), 0, st, !after_copy, idx, (const float*)tr->ds,
-                     (const float*)tr->dmf, tr->n_data, M, B, C, tr->U, tr->SB, tr->MFB, tr->dbad, mk));
+                     (const float*)tr->dmf, tr->n_data, M, B, C, tr->U, tr->SB, tr->MFB, tr->dbad, mk,
+                     (const int*)tr->ddist));
     }
     // forward
     for (int l = 0; l < L; ++l) {
@@ -309,7 +319,7 @@ int tr_gradient(rid_trainer* tr, const int* idx, float* loss, int64_t step, bool
     }
     const int nchunk = (int)(((long long)B * C + LT - 1) / LT);
     TCK(launch_k(k_tr_loss, dim3(nchunk, M), dim3(LT), 0, st, true, (const float*)tr->G0, (const float*)tr->SB,
-                 (const float*)tr->MFB, B, C, tr->GB0, tr->lpart));
+                 (const float*)tr->MFB, B, C, tr->GB0, tr->lpart, (const int*)tr->ddist));
     // adjoint of the input-gradient pass, increasing l
     for (int l = 0; l < L; ++l) {
         const int fin = l == 0 ? D : H;
@@ -498,6 +508,19 @@ RID_API int rid_trainer_create(const rid_train_desc* desc, const float* weights,
         tr->dthr = (uint32_t)std::floor(desc->dropout_rate * 4294967296.0);
         tr->dscale = (float)(1.0 / (1.0 - desc->dropout_rate));
     }
+    bool any_dist = false;
+    for (int j = 0; desc->cv_dist && j < C; ++j) any_dist |= desc->cv_dist[j] != 0;
+    if (any_dist) {
+        std::vector<int> h(C);
+        for (int j = 0; j < C; ++j) h[j] = desc->cv_dist[j] ? 1 : 0;
+        if (cudaMalloc(&tr->ddist, sizeof(int) * C) != cudaSuccess ||
+            cudaMemcpy(tr->ddist, h.data(), sizeof(int) * C, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            rid_trainer_destroy(tr);
+            return rid_fail(RID_ERR_OOM, "trainer: device allocation failed");
+        }
+    }
+    tr->d.cv_dist = nullptr;   // the caller's array is not kept
     if (cudaMemcpy(tr->w, weights, sizeof(float) * nP, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(tr->am, 0, sizeof(float) * 3 * nP) != cudaSuccess || cudaMemset(tr->act, 0, sizeof(float) * nact) != cudaSuccess ||
         cudaMemset(tr->dbad, 0, sizeof(int)) != cudaSuccess) {
@@ -514,6 +537,7 @@ RID_API int rid_trainer_destroy(rid_trainer* tr) {
     cudaFree(tr->w);
     cudaFree(tr->act);
     cudaFree(tr->dbad);
+    cudaFree(tr->ddist);
     cudaFree(tr->lpart);
     cudaFree(tr->ds);
     cudaFree(tr->didx);

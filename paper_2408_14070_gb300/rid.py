@@ -60,7 +60,7 @@ class TrainDesc(C.Structure):
                 ("resnet", C.c_int32), ("batch_size", C.c_int32), ("init_lr", C.c_double),
                 ("decay_rate", C.c_double), ("decay_steps", C.c_int32), ("beta1", C.c_double),
                 ("beta2", C.c_double), ("adam_eps", C.c_double), ("dropout_rate", C.c_double),
-                ("dropout_seed", C.c_uint64)]
+                ("dropout_seed", C.c_uint64), ("cv_dist", C.c_void_p)]
 
 
 class McmcDesc(C.Structure):
@@ -571,18 +571,20 @@ class Trainer:
     between dA_i/ds and the labels, learning rate init_lr * decay_rate^(t /
     decay_steps).  Weights use the packed layout of EnsembleParams.weights.
     dropout_rate > 0 thins every hidden layer during training (inverted
-    dropout, masks from Philox keyed by dropout_seed)."""
+    dropout, masks from Philox keyed by dropout_seed).  cv_dist [C] marks
+    distance CVs (input (s, 0))."""
 
     def __init__(self, n_models, n_cv, n_layers, width, weights, batch_size=128, resnet=False, init_lr=8e-4,
                  decay_rate=0.96, decay_steps=120, beta1=0.9, beta2=0.999, adam_eps=1e-8, dropout_rate=0.0,
-                 dropout_seed=0):
+                 dropout_seed=0, cv_dist=None):
         L = lib()
         self.M, self.C, self.B = int(n_models), int(n_cv), int(batch_size)
         w = np.ascontiguousarray(weights, dtype=np.float32)
         self.P = w.size // self.M
+        kd = None if cv_dist is None else np.ascontiguousarray(cv_dist, dtype=np.int32)
         d = TrainDesc(self.M, self.C, int(n_layers), int(width), int(bool(resnet)), self.B, float(init_lr),
                       float(decay_rate), int(decay_steps), float(beta1), float(beta2), float(adam_eps),
-                      float(dropout_rate), int(dropout_seed))
+                      float(dropout_rate), int(dropout_seed), None if kd is None else kd.ctypes.data)
         h = C.c_void_p()
         _check(L.rid_trainer_create(C.byref(d), w.ctypes.data, C.byref(h)))
         self.h = h

@@ -273,3 +273,39 @@ def test_fit_of_a_teacher_gradient_field_and_hand_off_to_the_ensemble(R):
     start = ((np.array([[T.member_value_and_grad(student.weights[m], 2 * C, L, H, False, x)[1] for x in s[:64]]
                         for m in range(M)]) - mf[None, :64]) ** 2).mean(axis=(1, 2))
     assert np.all(mse < 0.05 * start), (mse, start)
+
+
+# ------------------------------------------------------------------ distance CVs
+@pytest.mark.parametrize("resnet", [False, True])
+def test_distance_cvs_loss_gradient_and_trajectory_match_the_oracle(R, resnet):
+    """Labels over torsions and distance CVs (a distance enters the network as
+    (s, 0)): the batch loss and gradient, then four Adam steps, against the
+    oracle with the same kinds, at the tolerances above."""
+    M, C, L, H, B, n = 3, 6, 3, 64, 40, 200
+    dist = np.array([False, True, False, True, True, False])
+    ens, s, mf, idx = _problem(M, C, L, H, B, n, 7, resnet)
+    rng = np.random.default_rng(8)
+    s[:, dist] = rng.uniform(1.0, 4.0, size=(n, dist.sum())).astype(np.float32)
+    loss = np.zeros(M, np.float32)
+    grad = np.zeros((M, ens.weights.shape[1]), np.float32)
+    kw = dict(init_lr=2e-3, decay_rate=0.5, decay_steps=2)
+    K = 4
+    idxs = np.stack([np.stack([rng.choice(n, size=B) for _ in range(M)]) for _ in range(K)]).astype(np.int32)
+    losses = np.zeros((K, M), np.float32)
+    with R.Trainer(M, C, L, H, ens.weights, batch_size=B, resnet=resnet, cv_dist=dist, **kw) as tr:
+        tr.set_data(s, mf)
+        tr.grad(idx, loss, grad)
+        tr.run(idxs, losses)
+        w, _ = tr.weights()
+    for m in range(M):
+        lo, go = T.loss_and_grad(ens.weights[m].astype(np.float64), 2 * C, L, H, resnet, s[idx[m]], mf[idx[m]],
+                                 None, dist)
+        assert abs(loss[m] - lo) <= 1e-5 * lo
+        assert np.linalg.norm(grad[m] - go) / np.linalg.norm(go) < 1e-4
+        # the torsion reading of the same labels has another gradient
+        _, gt = T.loss_and_grad(ens.weights[m].astype(np.float64), 2 * C, L, H, resnet, s[idx[m]], mf[idx[m]])
+        assert np.linalg.norm(gt - go) > 1e-2 * np.linalg.norm(go)
+    wo, lo, _, _ = T.train(ens.weights, 2 * C, L, H, resnet, s, mf, idxs, dist=dist, **kw)
+    np.testing.assert_allclose(losses, lo, rtol=1e-5)
+    d = np.abs(w.astype(np.float64) - wo)
+    assert np.mean(d > 1e-6) <= 1e-3 and d.max() <= K * kw["init_lr"]

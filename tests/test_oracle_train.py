@@ -177,3 +177,50 @@ def test_dropout_mask_statistics(rate):
     assert T.dropout_threshold(0.5) == 2 ** 31 and T.dropout_threshold(0.25) == 2 ** 30
     q1 = T.dropout_scales(M, B, L, H, 1, 77, rate)
     assert 0.5 < np.mean((q > 0) == (q1 > 0)) < 1.0
+
+
+# --------------------------------------------------------------------------- distance CVs
+def test_mixed_cv_gradient_matches_finite_differences_and_torch():
+    """Training on labels over torsions and distance CVs (a distance enters as
+    (s, 0), dA/ds = dA/du_2j): the weight gradient against central differences
+    of the oracle's loss and against torch double backward."""
+    torch = pytest.importorskip("torch")
+    C, L, H, B = 3, 3, 6, 4
+    D = 2 * C
+    dist = np.array([False, True, True])
+    rng = np.random.default_rng(13)
+    w = _net(D, L, H, 5)
+    s = np.stack([rng.uniform(-np.pi, np.pi, B), rng.uniform(1.0, 4.0, B), rng.uniform(1.0, 4.0, B)], axis=1)
+    mf = rng.normal(0.0, 1.0, size=(B, C))
+    loss, g = T.loss_and_grad(w, D, L, H, True, s, mf, None, dist)
+    assert loss == pytest.approx(T.loss(w, D, L, H, True, s, mf, None, dist), rel=1e-13)
+    h = 1e-6
+    fd = np.empty_like(w)
+    for p in range(w.size):
+        wp, wm = w.copy(), w.copy()
+        wp[p] += h
+        wm[p] -= h
+        fd[p] = (T.loss(wp, D, L, H, True, s, mf, None, dist) - T.loss(wm, D, L, H, True, s, mf, None, dist)) / (2 * h)
+    assert np.max(np.abs(g - fd)) < 1e-7 * max(1.0, np.max(np.abs(fd)))
+    wt = torch.tensor(w, dtype=torch.float64, requires_grad=True)
+    st = torch.tensor(s, dtype=torch.float64, requires_grad=True)
+    dt = torch.tensor(dist)
+    u = torch.stack([torch.where(dt, st, torch.cos(st)), torch.where(dt, torch.zeros_like(st), torch.sin(st))],
+                    dim=-1).reshape(B, D)
+    o, fin, hh = 0, D, u
+    for l in range(L):
+        W = wt[o:o + H * fin].reshape(H, fin)
+        o += H * fin
+        b = wt[o:o + H]
+        o += H
+        t = torch.tanh(hh @ W.T + b)
+        hh = t + hh if l >= 1 else t
+        fin = H
+    A = hh @ wt[o:o + H] + wt[o + H]
+    (dAds,) = torch.autograd.grad(A.sum(), st, create_graph=True)
+    lt = ((dAds - torch.tensor(mf)) ** 2).mean()
+    (gt,) = torch.autograd.grad(lt, wt)
+    assert lt.item() == pytest.approx(loss, rel=1e-12)
+    np.testing.assert_allclose(g, gt.numpy(), rtol=1e-10, atol=1e-13)
+    # the torsion reading of the same CVs is a different loss
+    assert abs(T.loss(w, D, L, H, True, s, mf) - loss) > 1e-3 * loss
