@@ -21,8 +21,13 @@
 // A = w_out . h_L + b_out is formed from 16-column partial sums added in column
 // order, as in k_mlp_tc, so the cluster size does not change its bits.
 //
-// Warp roles as in k_mlp_tc: warp 0 TMA producer, warp 1 TMEM allocator and
-// MMA issuer, warps 2..17 epilogue.  Every wait is bounded in time; a CTA
+// When every CTA's slice is whole 128-byte-wide atoms of the next operand, the
+// slice is one contiguous block: the epilogue writes it locally and a copy warp
+// sends it to each peer with one bulk shared-to-shared copy that completes on
+// the peer's barrier (no per-value remote stores, no cluster-scope fence).
+//
+// Warp roles: warp 0 TMA producer, warp 1 TMEM allocator and MMA issuer,
+// warps 2..17 epilogue, warp 18 bulk copies of the exchange.  Every wait is bounded in time; a CTA
 // whose wait expires sets the error word and stops issuing, its peers' waits
 // then expire too, and every CTA still meets the final cluster barrier, so no
 // CTA exits while another may write into its shared memory.
@@ -30,12 +35,19 @@
 
 namespace {
 
+// A copy warp after the epilogue warps issues the bulk copies of the exchange.
+constexpr int COPY_WARP = EPI_WARP0 + EPI_WARPS;
+constexpr int CL_THREADS = 32 * (COPY_WARP + 1);
+
 struct SmemC {
     uint64_t full[TC_MAX_STAGES];
     uint64_t empty[TC_MAX_STAGES];
     uint64_t acc_full[2];
     uint64_t acc_empty[2];
-    uint64_t a_full[2];        // operand buffer b complete: 16 epilogue warps x S CTAs
+    uint64_t a_full[2];        // operand buffer b complete (store exchange): 16 epilogue warps x S CTAs
+    uint64_t a_bulk[2];        // operand buffer b complete (bulk exchange): 16 local warps + the expect_tx
+                               // arrival, and the peers' bytes
+    uint64_t slice_done;       // this CTA's slice written (bulk exchange): 16 epilogue warps
     uint64_t u_full;           // the MLP input in buffer 0: this CTA's 16 epilogue warps
     uint64_t drain;
     uint32_t tmem_base;
@@ -48,6 +60,22 @@ __device__ __forceinline__ void col_slice(int N, int S, int r, int& lo, int& n) 
     lo = r * ns;
     n = N - lo < ns ? N - lo : ns;
     if (n < 0) n = 0;
+}
+
+// Exchange of the operand GEMM g writes for GEMM g + 1.  When every CTA's
+// slice is whole 128-byte-wide atoms of that operand (64 BF16 or 128 FP8
+// columns, 16 KB for 128 rows), the slice is one contiguous block of shared
+// memory: the epilogue writes it locally and the copy warp sends it to every
+// peer with one bulk copy each (completing on the peer's a_bulk barrier).
+// Otherwise the epilogue stores each value into every CTA (st.shared::cluster).
+// Returns the slice's atom count (0: store exchange).
+template <bool F8>
+__device__ __forceinline__ int bulk_atoms(const TcArgs& P, int g, int G, int CS) {
+    if (g + 1 >= G) return 0;
+    const int N = P.gN[g];
+    const int cols = (F8 && P.geb[g + 1] == 1) ? 128 : 64;
+    if (N % (CS * cols)) return 0;
+    return N / (CS * cols);
 }
 
 template <bool F8, bool RES>
@@ -79,7 +107,9 @@ __global__ void __maxnreg__(96)
             mbar_init(smem_u32(&S.acc_full[b]), 1);
             mbar_init(smem_u32(&S.acc_empty[b]), EPI_WARPS);
             mbar_init(smem_u32(&S.a_full[b]), EPI_WARPS * CS);
+            mbar_init(smem_u32(&S.a_bulk[b]), EPI_WARPS + 1);
         }
+        mbar_init(smem_u32(&S.slice_done), EPI_WARPS);
         mbar_init(smem_u32(&S.u_full), EPI_WARPS);
         mbar_init(smem_u32(&S.drain), 1);
         S.abort_flag = 0;
@@ -139,6 +169,7 @@ __global__ void __maxnreg__(96)
         if (lane == 0) {
             int it = 0;
             bool ok = true;
+            uint32_t ph_full = 0, ph_bulk = 0;   // phase bits of a_full[b] / a_bulk[b] (bit b)
             for (int g = 0; g < G && ok; ++g) {
                 int lo, nr;
                 col_slice(P.gN[g], CS, rank, lo, nr);
@@ -151,9 +182,18 @@ __global__ void __maxnreg__(96)
                     break;
                 }
                 // the whole operand of this GEMM is in buffer b
-                const bool aok = g == 0 ? mbar_wait(smem_u32(&S.u_full), 0, abort_flag, P.err, 4)
-                                        : mbar_wait_cluster(smem_u32(&S.a_full[b]), ((g - 1) >> 1) & 1, abort_flag,
-                                                            P.err, 4);
+                bool aok;
+                if (g == 0) {
+                    aok = mbar_wait(smem_u32(&S.u_full), 0, abort_flag, P.err, 4);
+                } else if (const int na = bulk_atoms<F8>(P, g - 1, G, CS)) {
+                    // the peers' slices arrive as bytes on a_bulk[b]
+                    mbar_arrive_expect_tx(smem_u32(&S.a_bulk[b]), (uint32_t)(CS - 1) * (uint32_t)na * 16384u);
+                    aok = mbar_wait_cluster(smem_u32(&S.a_bulk[b]), (ph_bulk >> b) & 1u, abort_flag, P.err, 4);
+                    ph_bulk ^= 1u << b;
+                } else {
+                    aok = mbar_wait_cluster(smem_u32(&S.a_full[b]), (ph_full >> b) & 1u, abort_flag, P.err, 4);
+                    ph_full ^= 1u << b;
+                }
                 if (!aok) {
                     ok = false;
                     break;
@@ -192,6 +232,22 @@ __global__ void __maxnreg__(96)
             mma_commit(smem_u32(&S.drain));
             const unsigned long long t0 = gtimer();
             while (!mbar_try(smem_u32(&S.drain), 0) && gtimer() - t0 < WAIT_NS) {}
+        }
+    } else if (warp == COPY_WARP) {
+        // ------------------------------------------------------------ bulk exchange
+        if (lane == 0) {
+            uint32_t ph = 0;
+            for (int g = 0; g + 1 < G; ++g) {
+                const int na = bulk_atoms<F8>(P, g, G, CS);
+                if (!na) continue;
+                if (!mbar_wait(smem_u32(&S.slice_done), ph, abort_flag, P.err, 16)) break;
+                ph ^= 1u;
+                const uint32_t bytes = (uint32_t)na * 16384u;
+                const uint32_t src = smem_u32(Abuf[(g + 1) & 1]) + (uint32_t)rank * bytes;
+                for (int q = 0; q < CS; ++q)
+                    if (q != rank) bulk_copy_to_peer(src, bytes, smem_u32(&S.a_bulk[(g + 1) & 1]), (uint32_t)q);
+                bulk_commit_and_wait_read();
+            }
         }
     } else {
         // ------------------------------------------------------------ epilogue
@@ -240,6 +296,7 @@ __global__ void __maxnreg__(96)
             const float ws = F8 ? P.wscale[(size_t)m * 2 * L + g] : 1.0f;
             const int l = fwd ? g : (2 * L - 1 - g);
             const int b = g & 1;
+            const bool bulk = bulk_atoms<F8>(P, g, G, CS) != 0;   // local writes + the copy warp
             const bool res_fwd = RES && fwd && l >= 1;
             const bool res_bwd = RES && !fwd && l >= 1;
             const bool res_ld = res_fwd || (res_bwd && l < L - 1);
@@ -355,7 +412,9 @@ __global__ void __maxnreg__(96)
                             }
                         }
                     }
-                    if (have_v && g < G - 1) {
+                    if (have_v && g < G - 1 && bulk) {
+                        store_a8(Anext, row, gc, ebn, v);   // this CTA's copy; the copy warp sends the slice
+                    } else if (have_v && g < G - 1) {
                         // this CTA's columns of the next operand, into every CTA of the cluster
                         if (ebn == 2) {
                             const uint4 pv = pack8(v);
@@ -370,7 +429,15 @@ __global__ void __maxnreg__(96)
                 }
                 if (fwd && l == L - 1) P.qsave[qs_off(m, tile, (lo + lc) >> 4, row, P.ntiles)] = apart;
             }
-            if (g < G - 1) {
+            if (g < G - 1 && bulk) {
+                // a whole-atom slice: no K padding (N is a multiple of the atom width)
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(smem_u32(&S.a_bulk[(g + 1) & 1]));
+                    mbar_arrive(smem_u32(&S.slice_done));
+                }
+            } else if (g < G - 1) {
                 // K padding of the next operand (columns N .. Kp - 1) in this CTA's
                 // own copy: it may hold an earlier, wider operand
                 for (int gc = N + 8 * sub; gc < P.gKp[g + 1]; gc += 32) zero_a8(Anext, row, gc, ebn);
@@ -427,7 +494,7 @@ cudaError_t rid_launch_mlp_tc_cluster(const TcArgs& P, const CUtensorMap& big, c
     }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(P.ntiles * P.csize, P.M, 1);
-    cfg.blockDim = dim3(NTHREADS, 1, 1);
+    cfg.blockDim = dim3(CL_THREADS, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];

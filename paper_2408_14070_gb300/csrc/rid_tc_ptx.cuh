@@ -250,6 +250,24 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint32_t a, uint32_t parity, v
 __device__ __forceinline__ void fence_async_smem_cluster() {
     asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
 }
+// Arrive on a local mbarrier and raise its expected transaction bytes.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t a, uint32_t bytes) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(a), "r"(bytes)
+                 : "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16) from this CTA's shared memory to the
+// same offset in CTA `rank`, completing on that CTA's mbarrier (complete_tx).
+__device__ __forceinline__ void bulk_copy_to_peer(uint32_t local_src, uint32_t bytes, uint32_t local_bar,
+                                                  uint32_t rank) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            mapa(local_src, rank)),
+        "r"(local_src), "r"(bytes), "r"(mapa(local_bar, rank))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit_and_wait_read() {
+    asm volatile("cp.async.bulk.commit_group;\n\tcp.async.bulk.wait_group.read 0;" ::: "memory");
+}
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
