@@ -121,7 +121,7 @@ struct rid_system {
     // label
     DevBuf lsum, lsum2, lbsum, ls0, lkap;
     // staging for host I/O and traces
-    DevBuf io0, io1, tr_cv, tr_eps, tr_en, out_mf, out_se, out_sd;
+    DevBuf io0, io1, tr_cv, tr_eps, tr_en, tr_chunk, out_mf, out_se, out_sd;
     // resident walker session
     int W_act = 0;
     uint64_t step_next = 0;
@@ -135,6 +135,7 @@ struct rid_system {
     // the force field runs on a side stream, concurrently with the ensemble kernel
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t cap_stream = nullptr;   // captures the graph of a long run's chunk
     // kernel timing
     bool prof_on = false;
     std::vector<std::string> prof_names;
@@ -254,7 +255,8 @@ static void destroy_all(rid_system* sys) {
                       &sys->d_wout, &sys->d_bout, &sys->x, &sys->v, &sys->f, &sys->fff, &sys->s, &sys->J,
                       &sys->u, &sys->gradA, &sys->Aval, &sys->eps, &sys->hs, &sys->eff, &sys->flags,
                       &sys->lsum, &sys->lsum2, &sys->lbsum, &sys->ls0, &sys->lkap, &sys->io0, &sys->io1,
-                      &sys->tr_cv, &sys->tr_eps, &sys->tr_en, &sys->out_mf, &sys->out_se, &sys->out_sd};
+                      &sys->tr_cv, &sys->tr_eps, &sys->tr_en, &sys->tr_chunk, &sys->out_mf, &sys->out_se,
+                      &sys->out_sd};
     for (DevBuf* b : bufs) b->release();
     sys->tcv.blob.release();
     sys->tsave.release();
@@ -266,8 +268,9 @@ static void destroy_all(rid_system* sys) {
     if (sys->ev_fork) cudaEventDestroy(sys->ev_fork);
     if (sys->ev_join) cudaEventDestroy(sys->ev_join);
     if (sys->side) cudaStreamDestroy(sys->side);
+    if (sys->cap_stream) cudaStreamDestroy(sys->cap_stream);
     sys->ev_fork = sys->ev_join = nullptr;
-    sys->side = nullptr;
+    sys->side = sys->cap_stream = nullptr;
 }
 
 extern "C" int rid_create_system(const rid_system_desc* d, rid_system** out) {
@@ -975,6 +978,91 @@ static int do_load(rid_system* sys, int W, const float* x0, const float* v0, uin
     return RID_OK;
 }
 
+// Steps of resident walkers from step_next on, traces into cv / eps / en
+// ([W][T][...] device).  A run of at least two chunks (a chunk: the multiple
+// of output_freq nearest 256 steps) without an energy trace is replayed as a
+// CUDA graph of one chunk: the integrator then reads its Philox step from a
+// device base that the graph advances, each chunk ends with the closing half
+// of its last step (its last step has a trace slot), and the chunk's traces go
+// from a staging block to their slots.  The arithmetic is that of the direct
+// run, so the results are the same bits; only the launches are fewer.
+static int advance_steps(rid_system* sys, int W, int mode, int64_t n_steps, float* cv, float* eps, double* en,
+                         long long T, cudaStream_t st) {
+    const int of = sys->S.output_freq, C = sys->S.C;
+    const long long chunk = std::max<long long>(of, ((256 + of - 1) / of) * of);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs));
+    if (n_steps < 2 * chunk || en || sys->prof_on || cs != cudaStreamCaptureStatusNone)
+        return run_steps(sys, W, mode, nullptr, n_steps, sys->step_next, cv, eps, en, T, sys->pending, false, st);
+    TRY(ensure_side(sys));
+    TRY(settle(sys, st));
+    const long long tc = chunk / of, nchunk = n_steps / chunk;
+    TRY(sys->d_stepbase.ensure(sizeof(uint32_t)));
+    TRY(sys->tr_chunk.ensure((size_t)W * tc * (C + 1) * sizeof(float)));
+    float* ccv = sys->tr_chunk.as<float>();
+    float* ceps = ccv + (size_t)W * tc * C;
+    CK(cudaMemsetAsync(sys->d_stepbase.p, 0, sizeof(uint32_t), st));
+    rid_launch_add_u32(sys->d_stepbase.as<uint32_t>(), (uint32_t)sys->step_next, st);
+    // capture one chunk on a private stream (the caller's may be the legacy
+    // default stream, which cannot be captured; nothing runs during a capture)
+    if (!sys->cap_stream) CK(cudaStreamCreateWithFlags(&sys->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cst = sys->cap_stream;
+    const long long l0 = sys->launches;
+    CK(cudaStreamBeginCapture(cst, cudaStreamCaptureModeRelaxed));
+    sys->graph_mode = true;
+    bool pend = false;
+    int rc = run_steps(sys, W, mode, nullptr, chunk, 0, cv ? ccv : nullptr, eps ? ceps : nullptr, nullptr, tc, pend,
+                       false, cst);
+    if (rc == RID_OK) rid_launch_add_u32(sys->d_stepbase.as<uint32_t>(), (uint32_t)chunk, cst);
+    sys->graph_mode = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cst, &g);
+    if (rc != RID_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (ec != cudaSuccess) return fail(RID_ERR_CUDA, "stream capture: %s", cudaGetErrorString(ec));
+    cudaGraphExec_t ge = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return fail(RID_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+    // the capture counted one chunk's kernels; every replay launches them again
+    sys->launches += (nchunk - 1) * (sys->launches - l0);
+    cudaError_t e = cudaSuccess;
+    for (long long k = 0; k < nchunk && e == cudaSuccess; ++k) {
+        e = cudaGraphLaunch(ge, st);
+        if (e == cudaSuccess && cv)
+            e = cudaMemcpy2DAsync(cv + (size_t)k * tc * C, (size_t)T * C * sizeof(float), ccv,
+                                  (size_t)tc * C * sizeof(float), (size_t)tc * C * sizeof(float), W,
+                                  cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && eps)
+            e = cudaMemcpy2DAsync(eps + (size_t)k * tc, (size_t)T * sizeof(float), ceps, (size_t)tc * sizeof(float),
+                                  (size_t)tc * sizeof(float), W, cudaMemcpyDeviceToDevice, st);
+    }
+    cudaGraphExecDestroy(ge);
+    if (e != cudaSuccess) return fail(RID_ERR_CUDA, "graph replay: %s", cudaGetErrorString(e));
+    sys->pending = false;
+    // the remainder, directly, with the Philox step read from the same device base
+    const long long rem = n_steps - nchunk * chunk;
+    if (rem > 0) {
+        const long long tr = rem / of;
+        sys->graph_mode = true;
+        rc = run_steps(sys, W, mode, nullptr, rem, 0, cv ? ccv : nullptr, eps ? ceps : nullptr, nullptr, tr,
+                       sys->pending, false, st);
+        sys->graph_mode = false;
+        TRY(rc);
+        rid_launch_add_u32(sys->d_stepbase.as<uint32_t>(), (uint32_t)rem, st);
+        if (tr > 0 && cv)
+            CK(cudaMemcpy2DAsync(cv + (size_t)nchunk * tc * C, (size_t)T * C * sizeof(float), ccv,
+                                 (size_t)tr * C * sizeof(float), (size_t)tr * C * sizeof(float), W,
+                                 cudaMemcpyDeviceToDevice, st));
+        if (tr > 0 && eps)
+            CK(cudaMemcpy2DAsync(eps + (size_t)nchunk * tc, (size_t)T * sizeof(float), ceps, (size_t)tr * sizeof(float),
+                                 (size_t)tr * sizeof(float), W, cudaMemcpyDeviceToDevice, st));
+    }
+    return RID_OK;
+}
+
 static int do_advance(rid_system* sys, int64_t n_steps, float* cv_out, float* eps_out, double* energy_out, int mem,
                       cudaStream_t st) {
     if (!sys->loaded) return fail(RID_ERR_STATE, "no walkers loaded");
@@ -994,7 +1082,7 @@ static int do_advance(rid_system* sys, int64_t n_steps, float* cv_out, float* ep
         if (eps_out) { TRY(sys->tr_eps.ensure((size_t)W * T * sizeof(float))); deps = sys->tr_eps.as<float>(); }
         if (energy_out) { TRY(sys->tr_en.ensure((size_t)W * T * 3 * sizeof(double))); den = sys->tr_en.as<double>(); }
     }
-    TRY(run_steps(sys, W, mode, nullptr, n_steps, sys->step_next, dcv, deps, den, T, sys->pending, false, st));
+    TRY(advance_steps(sys, W, mode, n_steps, dcv, deps, den, T, st));
     sys->step_next += (uint64_t)n_steps;
     if (mem == RID_MEM_HOST && T > 0 && (cv_out || eps_out || energy_out)) {
         if (cv_out) CK(cudaMemcpyAsync(cv_out, dcv, (size_t)W * T * C * sizeof(float), cudaMemcpyDeviceToHost, st));
