@@ -747,6 +747,7 @@ def run_paper_network(rid, torch, steps, seed=21):
                  "kernels_ms": kern}
             if name != "fp32":
                 r["roofline"] = tensor_roofline(flops, kern["k_mlp_tc"])
+                r["mlp_kernel"] = mlp_kernel_desc(system)
             res[name] = r
         if name == "bf16":
             # the paper's walker count: step latency
@@ -760,6 +761,16 @@ def run_paper_network(rid, torch, steps, seed=21):
         res[name]["mean_force_rel_dev_from_fp32"] = {"median": float(d.median()), "max": float(d.max())}
     res["bf16_speedup_vs_fp32"] = res["bf16"]["value"] / res["fp32"]["value"]
     return res
+
+
+def mlp_kernel_desc(system):
+    """The tensor-core ensemble kernel variant of the system's last launch."""
+    cs = system.mlp_cluster()
+    if cs == 0:
+        return "FP32 SIMT (k_mlp_fp32)"
+    if cs == 1:
+        return "k_mlp_tc: one CTA per 128-walker tile and member"
+    return f"k_mlp_tc_cluster: clusters of {cs} CTAs per 128-walker tile and member"
 
 
 def run_tiny(rid, torch, seed=1):
@@ -1053,8 +1064,11 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
+    tkey = top
     if top == "k_mlp_tc":
-        work, src = mlp_flops_per_walker_step(wl) * W, "k_mlp_tc.cu"
+        # the variant the tuner kept names the source and the traffic record
+        tkey = "k_mlp_tc" if system.mlp_cluster() == 1 else "k_mlp_tc_cluster"
+        work, src = mlp_flops_per_walker_step(wl) * W, tkey + ".cu"
         peak = peaks.get("bf16_tflops")
         roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak if peak else 1900.0,
                 "peak_source": "measured bf16_tflops (burst)" if peak else "fallback 1.9 PFLOP/s bf16"}
@@ -1076,7 +1090,7 @@ def main():
         achieved = work / (avg_ms / 1e3) / 1e12
     roofline = {"kernel": top, "bound": roof["bound"], "achieved": achieved, "peak": roof["peak"],
                 "unit": roof["unit"], "frac": achieved / roof["peak"] if roof["peak"] else None,
-                "traffic": traffic_for(top, src, WORKLOAD), "work_per_launch": work,
+                "traffic": traffic_for(tkey, src, WORKLOAD), "work_per_launch": work, "source": src,
                 "avg_launch_ms": avg_ms, "peak_source": roof["peak_source"],
                 "kernels": {k: {"total_ms": v[0], "launches": v[1], "share": v[0] / sum(x[0] for x in prof.values())}
                             for k, v in prof.items()}}
@@ -1118,6 +1132,7 @@ def main():
                       "n_beads": wl["n_beads"], "n_cv": wl["n_cv"], "ensemble": f"{wl['n_models']}x"
                       f"[{2 * wl['n_cv']}-{wl['width']}x{wl['n_layers']}-1]",
                       "mlp_precision": args.precision, "forces_integrator": "f32",
+                      "mlp_kernel": mlp_kernel_desc(system),
                       "l2": "flushed (256 MiB write) before every timed step; each step timed alone",
                       "parallelism": f"walkers sharded, {world} independent rank(s)"},
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),

@@ -489,6 +489,14 @@ RID_API int64_t rid_launch_count(rid_system* sys);
 RID_API int rid_set_mlp_cluster(rid_system* sys, int32_t csize);
 
 /*
+ * Cluster size of the tensor-core ensemble kernel's last launch (as tuned or
+ * as fixed by rid_set_mlp_cluster), written to the host int csize; 0 before
+ * any BF16 / FP8 ensemble evaluation and for FP32 ensembles.
+ * Errors: RID_ERR_ARG (NULL argument).
+ */
+RID_API int rid_get_mlp_cluster(rid_system* sys, int32_t* csize);
+
+/*
  * Server: device memory of a fixed HBM budget, from which batched label runs
  * (rid_label_batch) and the request loop (rid_submit / rid_poll) take their
  * device memory.  Memory is allocated in segments, on demand, up to the

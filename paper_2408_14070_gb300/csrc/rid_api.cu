@@ -99,6 +99,7 @@ struct TcVariant {
     int cl_stages[3] = {0, 0, 0}, cl_acc_cols[3] = {0, 0, 0}, cl_tmem_cols[3] = {0, 0, 0};
     unsigned cl_stage_bytes[3] = {0, 0, 0};
     int csize = 1, cs_W = -1;
+    int used_cs = 0;   // cluster size of the last launch (0: none yet)
 };
 
 struct rid_system {
@@ -859,6 +860,7 @@ static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_
         const int cs = sys->cs_force ? sys->cs_force : V.cs_W == W ? V.csize : default_cluster(V, P.ntiles * E.M);
         if (cs > 1 && !V.cl_ok[cs == 2 ? 1 : 2])
             return fail(RID_ERR_ARG, "ensemble kernel: cluster size %d does not fit this ensemble's shape", cs);
+        sys->tcv.used_cs = cs;
         if (cs == 1) {
             if (V.tuned_W != W) TRY(tune_tc_stages(sys, P, st));
             P.stages = V.stages;
@@ -1252,6 +1254,12 @@ extern "C" int rid_set_mlp_cluster(rid_system* sys, int32_t csize) {
     if (csize != 0 && csize != 1 && csize != 2 && csize != 4)
         return fail(RID_ERR_ARG, "cluster size %d: expected 0 (tuned), 1, 2 or 4", csize);
     sys->cs_force = csize;
+    return RID_OK;
+}
+
+extern "C" int rid_get_mlp_cluster(rid_system* sys, int32_t* csize) {
+    if (!sys || !csize) return fail(RID_ERR_ARG, "NULL argument");
+    *csize = sys->has_ens && sys->precision != RID_PREC_FP32 ? sys->tcv.used_cs : 0;
     return RID_OK;
 }
 

@@ -29,7 +29,8 @@ EXPORTS = ("rid_version", "rid_status_string", "rid_last_error", "rid_create_sys
            "rid_server_destroy", "rid_label_batch", "rid_submit", "rid_poll", "rid_server_load",
            "rid_trainer_create", "rid_trainer_destroy", "rid_trainer_set_data", "rid_trainer_run",
            "rid_trainer_grad", "rid_trainer_weights", "rid_mcmc", "rid_select",
-           "rid_label_constrained", "rid_mcmc_system", "rid_set_mlp_cluster")
+           "rid_label_constrained", "rid_mcmc_system", "rid_set_mlp_cluster",
+           "rid_get_mlp_cluster")
 RID_NOT_READY = 6
 RID_JOB_LABEL, RID_JOB_EXPLORE = 1, 2
 
@@ -143,6 +144,7 @@ def lib() -> C.CDLL:
     L.rid_profile_read.argtypes = [vp, i32, C.c_char_p, C.POINTER(C.c_double), C.POINTER(i64), C.POINTER(i32)]
     L.rid_launch_count.argtypes = [vp]
     L.rid_set_mlp_cluster.argtypes = [vp, i32]
+    L.rid_get_mlp_cluster.argtypes = [vp, C.POINTER(i32)]
     L.rid_ensemble_grad_noalloc.argtypes = [i32, i32, vp, i32, i32, i32, i32, vp, vp, vp, vp]
     L.rid_server_create.argtypes = [u64, C.POINTER(vp)]
     L.rid_server_destroy.argtypes = [vp]
@@ -402,6 +404,12 @@ class System:
     def set_mlp_cluster(self, csize):
         """Cluster size of the tensor-core ensemble kernel: 0 tuned, 1, 2 or 4."""
         _check(lib().rid_set_mlp_cluster(self.h, int(csize)))
+
+    def mlp_cluster(self):
+        """Cluster size of the tensor-core ensemble kernel's last launch (0 before any)."""
+        cs = C.c_int32(0)
+        _check(lib().rid_get_mlp_cluster(self.h, C.byref(cs)))
+        return int(cs.value)
 
     def pair_mask(self, x, mask_out, stream=None):
         W = int(x.shape[0])

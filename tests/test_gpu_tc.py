@@ -278,6 +278,7 @@ def test_cluster_sizes_give_identical_bits(R, orc, prec, n, C, W, M, L, H, resne
             sysobj.set_ensemble(ens, precision=p)
             sysobj.set_mlp_cluster(cs)
             sysobj.eval_forces(x, R.RID_BIAS_ENSEMBLE, f_out=f, eps_out=eps, abar_out=abar, grad_out=g)
+            assert sysobj.mlp_cluster() == cs
             xo = np.zeros_like(x[:9])
             sysobj.explore(np.ascontiguousarray(x[:9]), 6, x_out=xo)
         outs[cs] = (f, eps, abar, g, xo)
