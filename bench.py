@@ -1132,7 +1132,7 @@ def main():
                       "n_beads": wl["n_beads"], "n_cv": wl["n_cv"], "ensemble": f"{wl['n_models']}x"
                       f"[{2 * wl['n_cv']}-{wl['width']}x{wl['n_layers']}-1]",
                       "mlp_precision": args.precision, "forces_integrator": "f32",
-                      "mlp_kernel": mlp_kernel_desc(system),
+                      "mlp_kernel": mlp_kernel_desc(system), "ff_cta_threads": system.ff_threads(),
                       "l2": "flushed (256 MiB write) before every timed step; each step timed alone",
                       "parallelism": f"walkers sharded, {world} independent rank(s)"},
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),

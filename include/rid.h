@@ -497,6 +497,25 @@ RID_API int rid_set_mlp_cluster(rid_system* sys, int32_t csize);
 RID_API int rid_get_mlp_cluster(rid_system* sys, int32_t* csize);
 
 /*
+ * CTA size of the force-field kernel (threads per walker CTA: beads per pass
+ * and CTAs per SM; a tuning control, no counterpart in the paper).  threads =
+ * 0 (the default) lets the library time the kernel with every multiple of 32
+ * from 64 up to its default size (the chain's bead count rounded up to 32, at
+ * most 224) at the first force evaluation of every new walker count and keep
+ * the fastest.  Forces are the same bits with every size; force-field energy
+ * evaluations always use the default size.
+ * Errors: RID_ERR_ARG (threads not 0 or a multiple of 32 in [32, default]).
+ */
+RID_API int rid_set_ff_threads(rid_system* sys, int32_t threads);
+
+/*
+ * The force-field CTA size in use (host int written): the fixed one, the
+ * tuned one for the last walker count, or the default before any evaluation.
+ * Errors: RID_ERR_ARG (NULL argument).
+ */
+RID_API int rid_get_ff_threads(rid_system* sys, int32_t* threads);
+
+/*
  * Server: device memory of a fixed HBM budget, from which batched label runs
  * (rid_label_batch) and the request loop (rid_submit / rid_poll) take their
  * device memory.  Memory is allocated in segments, on demand, up to the

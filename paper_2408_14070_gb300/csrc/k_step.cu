@@ -431,8 +431,16 @@ int rid_ff_smem_bytes(int N) {
                  (N <= RID_BONDED_SMEM_MAX ? sizeof(float3) * 8 * (size_t)N : 0));
 }
 
-void rid_launch_ff(const SysDev& S, StateDev st, int W, bool energy, cudaStream_t s) {
-    const int th = chain_threads(S.N) < FF_THREADS ? chain_threads(S.N) : FF_THREADS;
+int rid_ff_default_threads(int N) { return chain_threads(N) < FF_THREADS ? chain_threads(N) : FF_THREADS; }
+
+// threads: CTA size (a multiple of 32 up to the default), 0 for the default.
+// Each thread sums its own beads' forces in a fixed order and warps always
+// cover the same 32-bead groups, so the forces do not depend on it; the
+// energy sum does (its per-thread partials), so energy launches keep the
+// default.
+void rid_launch_ff(const SysDev& S, StateDev st, int W, bool energy, cudaStream_t s, int threads) {
+    const int dth = rid_ff_default_threads(S.N);
+    const int th = (energy || threads <= 0 || threads > dth) ? dth : threads;
     const size_t sm = (size_t)rid_ff_smem_bytes(S.N);
     const bool bsm = S.N <= RID_BONDED_SMEM_MAX;
     static unsigned long long attr = 0;

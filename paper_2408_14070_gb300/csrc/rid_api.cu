@@ -133,6 +133,8 @@ struct rid_system {
     bool graph_mode = false;
     bool tuning = false;       // inside the cluster-size tuner
     int cs_force = 0;          // cluster size fixed by rid_set_mlp_cluster (0: tuned)
+    // force-field CTA size: tuned at each new walker count (ff_W), or fixed
+    int ff_th = 0, ff_W = -1, ff_force = 0;
     // the force field runs on a side stream, concurrently with the ensemble kernel
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -695,13 +697,57 @@ static int ensure_side(rid_system* sys) {
 // a side stream over the remaining SMs; the caller's stream then waits for it.
 static int tune_cluster(rid_system* sys, int W, bool energy, cudaStream_t st);
 
+// Autotuner of the force field's CTA size (threads per walker CTA, hence
+// beads per pass and CTAs per SM): at the first force evaluation with a new
+// walker count, k_ff alone is timed with every multiple of 32 from 64 up to
+// its default (one warm-up and three timed launches each) and the fastest is
+// kept, the default unless another is 2% faster.  The forces are the same bits
+// with every size.  Skipped while the stream is being captured.
+static int tune_ff(rid_system* sys, int W, cudaStream_t st) {
+    const int dth = rid_ff_default_threads(sys->S.N);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs));
+    sys->ff_W = W;
+    sys->ff_th = dth;
+    if (cs != cudaStreamCaptureStatusNone || dth <= 64) return RID_OK;
+    StateDev sd = state_view(sys);
+    sd.W = W;
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    float best = 1e30f, tdef = 1e30f;
+    int pick = dth;
+    for (int th = dth; th >= 64; th -= 32) {
+        rid_launch_ff(sys->S, sd, W, false, st, th);
+        CK(cudaEventRecord(a, st));
+        for (int r = 0; r < 3; ++r) rid_launch_ff(sys->S, sd, W, false, st, th);
+        CK(cudaEventRecord(b, st));
+        CK(cudaEventSynchronize(b));
+        CK(cudaGetLastError());
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        if (th == dth) tdef = ms;
+        if (ms < best) {
+            best = ms;
+            pick = th;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    sys->launches += 4 * ((dth - 64) / 32 + 1);
+    sys->ff_th = best < 0.98f * tdef ? pick : dth;
+    return RID_OK;
+}
+
 static int launch_forces(rid_system* sys, int W, int mode, bool energy, cudaStream_t st) {
     StateDev sd = state_view(sys);
     sd.W = W;
+    if (sys->ff_W != W && !sys->tuning && !sys->ff_force) TRY(tune_ff(sys, W, st));
+    const int ffth = sys->ff_force ? sys->ff_force : sys->ff_th;
     if (mode == 1 && sys->precision != RID_PREC_FP32 && sys->tcv.cs_W != W && !sys->tuning && !sys->cs_force)
         TRY(tune_cluster(sys, W, energy, st));
     if (mode != 1) {
-        TRY(timed_launch(sys, "k_ff", st, [&] { rid_launch_ff(sys->S, sd, W, energy, st); }));
+        TRY(timed_launch(sys, "k_ff", st, [&] { rid_launch_ff(sys->S, sd, W, energy, st, ffth); }));
         CK(cudaGetLastError());
         return RID_OK;
     }
@@ -710,7 +756,7 @@ static int launch_forces(rid_system* sys, int W, int mode, bool energy, cudaStre
     CK(cudaStreamWaitEvent(sys->side, sys->ev_fork, 0));
     TRY(launch_mlp(sys, W, mode, sd, st));
     cudaStream_t fs = sys->side;
-    TRY(timed_launch(sys, "k_ff", fs, [&] { rid_launch_ff(sys->S, sd, W, energy, fs); }));
+    TRY(timed_launch(sys, "k_ff", fs, [&] { rid_launch_ff(sys->S, sd, W, energy, fs, ffth); }));
     CK(cudaEventRecord(sys->ev_join, fs));
     CK(cudaStreamWaitEvent(st, sys->ev_join, 0));
     CK(cudaGetLastError());
@@ -1254,6 +1300,23 @@ extern "C" int rid_set_mlp_cluster(rid_system* sys, int32_t csize) {
     if (csize != 0 && csize != 1 && csize != 2 && csize != 4)
         return fail(RID_ERR_ARG, "cluster size %d: expected 0 (tuned), 1, 2 or 4", csize);
     sys->cs_force = csize;
+    return RID_OK;
+}
+
+extern "C" int rid_set_ff_threads(rid_system* sys, int32_t threads) {
+    if (!sys) return fail(RID_ERR_ARG, "NULL system");
+    const int dth = rid_ff_default_threads(sys->S.N);
+    if (threads != 0 && (threads < 32 || threads > dth || threads % 32))
+        return fail(RID_ERR_ARG, "force-field CTA size %d: expected 0 (tuned) or a multiple of 32 in [32, %d]", threads,
+                    dth);
+    sys->ff_force = threads;
+    sys->ff_W = -1;
+    return RID_OK;
+}
+
+extern "C" int rid_get_ff_threads(rid_system* sys, int32_t* threads) {
+    if (!sys || !threads) return fail(RID_ERR_ARG, "NULL argument");
+    *threads = sys->ff_force ? sys->ff_force : (sys->ff_W >= 0 ? sys->ff_th : rid_ff_default_threads(sys->S.N));
     return RID_OK;
 }
 

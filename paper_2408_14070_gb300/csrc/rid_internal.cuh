@@ -252,7 +252,8 @@ cudaError_t rid_launch_label_cons(const SysDev& S, int R, int C, int B, long lon
                                   uint32_t step0, float kT, const float4* x0, const float4* v0, const int2* pairs,
                                   const float* d0, double* bsum, double* mf, double* se, double* sd, float4* x_out,
                                   float4* v_out, int* bad, cudaStream_t st);
-void rid_launch_ff(const SysDev& S, StateDev st, int W, bool energy, cudaStream_t s);
+void rid_launch_ff(const SysDev& S, StateDev st, int W, bool energy, cudaStream_t s, int threads = 0);
+int rid_ff_default_threads(int N);
 
 // Arguments of the fused finish / B-A-O-A / CV kernel.
 struct HeadArgs {

@@ -30,7 +30,7 @@ EXPORTS = ("rid_version", "rid_status_string", "rid_last_error", "rid_create_sys
            "rid_trainer_create", "rid_trainer_destroy", "rid_trainer_set_data", "rid_trainer_run",
            "rid_trainer_grad", "rid_trainer_weights", "rid_mcmc", "rid_select",
            "rid_label_constrained", "rid_mcmc_system", "rid_set_mlp_cluster",
-           "rid_get_mlp_cluster")
+           "rid_get_mlp_cluster", "rid_set_ff_threads", "rid_get_ff_threads")
 RID_NOT_READY = 6
 RID_JOB_LABEL, RID_JOB_EXPLORE = 1, 2
 
@@ -145,6 +145,8 @@ def lib() -> C.CDLL:
     L.rid_launch_count.argtypes = [vp]
     L.rid_set_mlp_cluster.argtypes = [vp, i32]
     L.rid_get_mlp_cluster.argtypes = [vp, C.POINTER(i32)]
+    L.rid_set_ff_threads.argtypes = [vp, i32]
+    L.rid_get_ff_threads.argtypes = [vp, C.POINTER(i32)]
     L.rid_ensemble_grad_noalloc.argtypes = [i32, i32, vp, i32, i32, i32, i32, vp, vp, vp, vp]
     L.rid_server_create.argtypes = [u64, C.POINTER(vp)]
     L.rid_server_destroy.argtypes = [vp]
@@ -404,6 +406,16 @@ class System:
     def set_mlp_cluster(self, csize):
         """Cluster size of the tensor-core ensemble kernel: 0 tuned, 1, 2 or 4."""
         _check(lib().rid_set_mlp_cluster(self.h, int(csize)))
+
+    def set_ff_threads(self, threads):
+        """CTA size of the force-field kernel: 0 tuned, else a multiple of 32."""
+        _check(lib().rid_set_ff_threads(self.h, int(threads)))
+
+    def ff_threads(self):
+        """CTA size of the force-field kernel in use."""
+        t = C.c_int32(0)
+        _check(lib().rid_get_ff_threads(self.h, C.byref(t)))
+        return int(t.value)
 
     def mlp_cluster(self):
         """Cluster size of the tensor-core ensemble kernel's last launch (0 before any)."""
