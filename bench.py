@@ -985,6 +985,8 @@ def main():
     ap.add_argument("--mcmc-steps", type=int, default=500)
     ap.add_argument("--mlp-cluster", type=int, default=0,
                     help="cluster size of the tensor-core ensemble kernel (0: tuned by the library)")
+    ap.add_argument("--ff-threads", type=int, default=0,
+                    help="CTA size of the force-field kernel (0: tuned by the library)")
     ap.add_argument("--no-paper-net", action="store_true")
     ap.add_argument("--no-tiny", action="store_true")
     ap.add_argument("--serve-sustained-rate", type=float, default=50.0)
@@ -1019,6 +1021,7 @@ def main():
     system = rid.System(sp)
     system.set_ensemble(ens, precision=prec)
     system.set_mlp_cluster(args.mlp_cluster)
+    system.set_ff_threads(args.ff_threads)
     xd = torch.from_numpy(x0).cuda()
     system.walkers_load(xd, stream=stream)
     system.walkers_advance(args.warmup, stream=stream)
