@@ -30,11 +30,13 @@ def R():
 
 
 def close_rel(got, ref, rtol, axis=None):
+    """Largest elementwise error relative to |ref| + rms(ref), in units of
+    rtol: below 1 when every element is within rtol."""
     ref = np.asarray(ref, np.float64)
     got = np.asarray(got, np.float64)
     scale = np.sqrt(np.mean(ref ** 2, axis=axis, keepdims=True)) if axis is not None else np.sqrt(np.mean(ref ** 2))
     err = np.abs(got - ref) / (np.abs(ref) + scale)
-    return err.max()
+    return err.max() / rtol
 
 
 def wrapd(d):
