@@ -241,6 +241,178 @@ __global__ void __launch_bounds__(NT) k_mlp_fp32(EnsDev E, StateDev st, int W, i
     (void)M;
 }
 
+// Small ensembles (every layer of a member fits in shared memory at once, as
+// for widths up to about 96): one CTA per (tile of 32 walkers, member) loads
+// the member's weights once -- rows of W_l [H][fin] padded to fin + 1 floats,
+// so the lanes of a warp (consecutive output neurons) read distinct banks --
+// and runs every layer from shared memory, with no weight ring to wait on.
+// The operations are those of k_mlp_fp32 in the same order: each forward
+// output is the FMA chain over its K inputs in increasing order from zero,
+// then + b and tanh; each input-gradient output starts from the residual term
+// (or zero) and chains over the H outputs of the layer in increasing order;
+// the member value is the same lane-strided partial sums and butterfly.
+constexpr int SM_MAX_FLOATS = 50 * 1024;   // 200 KB of shared memory
+constexpr int SM_MAX_WIDTH = 128;          // at least two walker groups per neuron
+constexpr int SR_MAX = TW / (NT / SM_MAX_WIDTH);   // walkers per thread at the widest layer: 16
+
+struct SmallLayout {
+    int woff[RID_MAX_LAYERS + 1];
+    int bias, wout, u, t, h0, h1, G0, G1, total;
+};
+__host__ __device__ inline SmallLayout small_layout(int D, int L, int H, int resnet, int TW) {
+    SmallLayout S{};
+    int o = 0;
+    for (int l = 0; l < L; ++l) {
+        S.woff[l] = o;
+        o += H * ((l == 0 ? D : H) + 1);
+    }
+    S.woff[L] = o;
+    S.bias = o; o += L * H;
+    S.wout = o; o += H;
+    S.u = o;    o += TW * D;
+    S.t = o;    o += L * TW * H;
+    S.h0 = o;   o += resnet ? TW * H : 0;
+    S.h1 = o;   o += resnet ? TW * H : 0;
+    const int gw = H > D ? H : D;
+    S.G0 = o;   o += TW * gw;
+    S.G1 = o;   o += TW * gw;
+    S.total = o;
+    return S;
+}
+
+// Offset of layer l's padded weight rows (the same as SmallLayout::woff, in registers).
+__device__ __forceinline__ int small_woff(int D, int H, int l) { return l == 0 ? 0 : H * (D + 1) + (l - 1) * H * (H + 1); }
+
+// TW: walkers per CTA (1 .. 32), chosen by the launcher so that small walker
+// counts still spread over many SMs; SR: a power of two bounding the walkers
+// one thread carries (ceil(TW / (NT / H)) at most).
+template <int SR>
+__global__ void __launch_bounds__(NT) k_mlp_fp32_small(EnsDev E, StateDev st, int W, int C, int TW) {
+    extern __shared__ __align__(16) float sm[];
+    const int D = E.D, L = E.L, H = E.H;
+    const SmallLayout Y = small_layout(D, L, H, E.resnet, TW);
+    const int m = blockIdx.y, w0 = blockIdx.x * TW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float* Wm = E.W + (size_t)m * E.wstride;
+    // the member's weights: every copy in flight at once, one wait
+    for (int l = 0; l < L; ++l) {
+        const int fin = l == 0 ? D : H;
+        const float* Wl = Wm + E.loff[l];
+        for (int idx = threadIdx.x; idx < H * fin; idx += NT) {
+            const int n = idx / fin, k = idx - n * fin;
+            cpa4(sm + small_woff(D, H, l) + n * (fin + 1) + k, Wl + idx, 4);
+        }
+    }
+    cpa_commit();
+    for (int idx = threadIdx.x; idx < L * H; idx += NT) sm[Y.bias + idx] = __ldg(E.b + (size_t)m * L * H + idx);
+    for (int idx = threadIdx.x; idx < H; idx += NT) sm[Y.wout + idx] = __ldg(E.wout + (size_t)m * H + idx);
+    for (int idx = threadIdx.x; idx < TW * D; idx += NT) {
+        const int wl = idx / D, k = idx - wl * D;
+        sm[Y.u + idx] = (w0 + wl < W) ? st.u[(size_t)(w0 + wl) * D + k] : 0.0f;
+    }
+    cpa_wait<0>();
+    __syncthreads();
+    // forward: t_l = tanh(in W_l^T + b_l), h_l = t_l (+ h_{l-1} for a residual layer)
+    const float* in = sm + Y.u;
+    for (int l = 0; l < L; ++l) {
+        const int K = l == 0 ? D : H;
+        const float* Wl = sm + small_woff(D, H, l);
+        float* tl = sm + Y.t + l * TW * H;
+        const bool res = E.resnet && l > 0;
+        float* hout = E.resnet ? sm + ((l & 1) ? Y.h1 : Y.h0) : tl;
+        // thread -> neuron n and walkers g, g + P, ...: one weight read per k
+        // serves SR independent chains
+        const int P = NT / H, n = threadIdx.x % H, g = threadIdx.x / H;
+        if (g < P) {
+            float acc[SR];
+#pragma unroll
+            for (int r = 0; r < SR; ++r) acc[r] = 0.0f;
+            const float* wr = Wl + n * (K + 1);
+            for (int k = 0; k < K; ++k) {
+                const float wv = wr[k];
+#pragma unroll
+                for (int r = 0; r < SR; ++r)
+                    if (g + P * r < TW) acc[r] = fmaf(in[(g + P * r) * K + k], wv, acc[r]);
+            }
+            const float bn = sm[Y.bias + l * H + n];
+#pragma unroll
+            for (int r = 0; r < SR; ++r) {
+                const int wl = g + P * r;
+                if (wl < TW) {
+                    const float t = tanhf(acc[r] + bn);
+                    tl[wl * H + n] = t;
+                    if (E.resnet) hout[wl * H + n] = res ? t + in[wl * K + n] : t;
+                }
+            }
+        }
+        __syncthreads();
+        in = hout;
+    }
+    // member value A = w_out . h_L + b_out: lane-strided partials, then the butterfly
+    for (int wl = warp; wl < TW; wl += NT / 32) {
+        float part = 0.0f;
+        for (int n = lane; n < H; n += 32) part = fmaf(sm[Y.wout + n], in[wl * H + n], part);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0 && w0 + wl < W) st.Aval[(size_t)m * W + w0 + wl] = part + E.bout[m];
+    }
+    // input gradient: g_L = w_out, Delta_l = g_l (1 - t_l^2), g_{l-1} = Delta_l W_l (+ g_l)
+    float* G = sm + Y.G0;
+    float* Gn = sm + Y.G1;
+    for (int o = threadIdx.x; o < TW * H; o += NT) G[o] = sm[Y.wout + (o % H)];
+    __syncthreads();
+    for (int l = L - 1; l >= 0; --l) {
+        const int Nout = l == 0 ? D : H, fin = Nout;
+        const float* tl = sm + Y.t + l * TW * H;
+        const float* Wl = sm + small_woff(D, H, l);
+        const bool res = E.resnet && l > 0;
+        float* Dl = Gn;   // Delta_l in the free buffer, then g_{l-1} over G
+        for (int o = threadIdx.x; o < TW * H; o += NT) {
+            const float t = tl[o];
+            Dl[o] = G[o] * (1.0f - t * t);
+        }
+        __syncthreads();
+        // g_{l-1}[j] = (g_l[j] if residual) + sum_k Delta_l[k] W_l[k][j], written over G after all reads
+        // thread -> input j and walkers g, g + P, ... (P = NT / Nout groups, at most TW)
+        {
+            const int P = NT / Nout < TW ? NT / Nout : TW, j = threadIdx.x % Nout, g = threadIdx.x / Nout;
+            float acc[SR];
+            const bool act = g < P;
+#pragma unroll
+            for (int r = 0; r < SR; ++r) {
+                const int wl = g + P * r;
+                acc[r] = (act && wl < TW && res) ? G[wl * H + j] : 0.0f;
+            }
+            if (act)
+                for (int k = 0; k < H; ++k) {
+                    const float wv = Wl[k * (fin + 1) + j];
+#pragma unroll
+                    for (int r = 0; r < SR; ++r)
+                        if (g + P * r < TW) acc[r] = fmaf(Dl[(g + P * r) * H + k], wv, acc[r]);
+                }
+            __syncthreads();   // every thread has read G for its initial values
+            if (act)
+#pragma unroll
+                for (int r = 0; r < SR; ++r) {
+                    const int wl = g + P * r;
+                    if (wl < TW) G[wl * (l == 0 ? D : H) + j] = acc[r];
+                }
+            __syncthreads();
+        }
+    }
+    // dA/ds_j = -sin s_j g0[2j] + cos s_j g0[2j+1] (torsion), g0[2j] (distance: input (s, 0))
+    for (int idx = threadIdx.x; idx < C * TW; idx += NT) {
+        const int wl = idx / C, j = idx - wl * C;
+        const int wg = w0 + wl;
+        if (wg < W) {
+            const float cs = sm[Y.u + wl * D + 2 * j], sn = sm[Y.u + wl * D + 2 * j + 1];
+            const float* g0 = G + wl * D;
+            const bool dist = E.cvdist && __ldg(E.cvdist + j);
+            st.gradA[((size_t)m * W + wg) * C + j] = dist ? g0[2 * j] : -sn * g0[2 * j] + cs * g0[2 * j + 1];
+        }
+    }
+}
+
 }  // namespace
 
 size_t rid_mlp_fp32_scratch_floats(int W, int M, int L, int H) {
@@ -249,6 +421,26 @@ size_t rid_mlp_fp32_scratch_floats(int W, int M, int L, int H) {
 }
 
 void rid_launch_mlp_fp32(const EnsDev& E, StateDev st, int W, int C, cudaStream_t s) {
+    // walkers per CTA: the largest power of two up to 32 that still gives one
+    // wave of CTAs (152 SMs), at least one walker
+    int tw = 32;
+    while (tw > 1 && (long long)((W + tw - 1) / tw) * E.M < 152) tw >>= 1;
+    const SmallLayout Y = small_layout(E.D, E.L, E.H, E.resnet, tw);
+    if (Y.total <= SM_MAX_FLOATS && small_layout(E.D, E.L, E.H, E.resnet, 32).total <= SM_MAX_FLOATS &&
+        E.H <= SM_MAX_WIDTH && E.D <= NT) {
+        const int wpt = (tw + NT / E.H - 1) / (NT / E.H);
+        int sr = 1;
+        while (sr < wpt) sr <<= 1;
+        auto kern = sr == 1 ? k_mlp_fp32_small<1> : sr == 2 ? k_mlp_fp32_small<2> : sr == 4 ? k_mlp_fp32_small<4>
+                  : sr == 8 ? k_mlp_fp32_small<8> : k_mlp_fp32_small<SR_MAX>;
+        static unsigned long long attr_small = 0;
+        if (rid_first_on_device(attr_small))
+            for (auto k : {k_mlp_fp32_small<1>, k_mlp_fp32_small<2>, k_mlp_fp32_small<4>, k_mlp_fp32_small<8>,
+                           k_mlp_fp32_small<SR_MAX>})
+                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_MAX_FLOATS * 4);
+        kern<<<dim3((W + tw - 1) / tw, E.M), NT, (size_t)Y.total * sizeof(float), s>>>(E, st, W, C, tw);
+        return;
+    }
     const int Kmax = E.H > E.D ? E.H : E.D;
     const size_t sm = sizeof(float) * ((size_t)2 * Kmax * ROW + (size_t)E.D * ROW + (size_t)NSW * KC * WCOLS);
     static unsigned long long attr_set = 0;

@@ -139,6 +139,8 @@ def test_force_field_and_cvs(R, orc, n, C, W, seed, squeeze):
     (22, 2, 16, 4, 3, 64, False, 1),
     (200, 20, 37, 4, 4, 256, False, 2),
     (60, 12, 70, 3, 2, 96, True, 6),
+    (30, 1, 5, 2, 2, 32, True, 8),          # five walkers, one CV, width 32 (member in shared memory)
+    (140, 64, 33, 2, 2, 96, False, 9),      # 128 inputs at width 96: the largest member held in shared memory
 ])
 def test_biased_forces_eps_and_member_gradients(R, orc, n, C, W, M, L, H, resnet, seed):
     sp = I.make_system(n, C, seed)
@@ -170,6 +172,29 @@ def test_biased_forces_eps_and_member_gradients(R, orc, n, C, W, M, L, H, resnet
     sig = np.array(sigmas)
     assert (sig == 1).any() and (sig == 0).any() and ((sig > 0) & (sig < 1)).any()
     assert np.allclose(eps, epsr, rtol=1e-4)
+
+
+@pytest.mark.parametrize("n,C,W,M,L,H,resnet,seed", [
+    (40, 6, 1003, 2, 3, 64, False, 31),     # 8-walker tiles, a ragged last tile of 3
+    (30, 4, 4096, 4, 2, 32, True, 32),      # 32-walker tiles, residual
+    (50, 8, 300, 3, 3, 96, True, 33),       # 2-walker tiles at width 96
+])
+def test_small_ensembles_on_walker_tiles(R, orc, n, C, W, M, L, H, resnet, seed):
+    """Ensembles whose members fit in shared memory run one CTA per (tile,
+    member) with the tile's walker count set by the walker count; sampled
+    walkers (first, tile edges, last) against the oracle at 1e-5."""
+    sp = I.make_system(n, C, seed)
+    x = I.make_chains(W, sp, seed)
+    ens = I.make_ensemble(M, 2 * C, L, H, seed, resnet=resnet, trust_lo=1e9, trust_hi=2e9)
+    g = np.zeros((M, W, C), np.float32)
+    abar = np.zeros(W, np.float32)
+    with R.System(sp) as sys:
+        sys.set_ensemble(ens)
+        sys.eval_forces(x, R.RID_BIAS_ENSEMBLE, abar_out=abar, grad_out=g)
+    for w in sorted({0, 1, 7, 8, 31, 32, W // 2, W - 2, W - 1}):
+        e = orc.ensemble(ens, orc.cvs(sp, x[w].astype(np.float64))[0])
+        assert close_rel(g[:, w], e["gradA"], FORCE_RTOL) < 1.0, w
+        assert abs(abar[w] - e["Abar"]) <= FORCE_RTOL * (abs(e["Abar"]) + 1.0), w
 
 
 def test_fp32_ensemble_at_the_size_limits(R, orc):
