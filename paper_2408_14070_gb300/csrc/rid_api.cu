@@ -135,6 +135,10 @@ struct rid_system {
     int cs_force = 0;          // cluster size fixed by rid_set_mlp_cluster (0: tuned)
     // force-field CTA size: tuned at each new walker count (ff_W), or fixed
     int ff_th = 0, ff_W = -1, ff_force = 0;
+    // run by the request loop: no tuners (their timing syncs would stall the
+    // loop, and a choice timed alone is not the one for a shared GPU): one CTA
+    // per tile, the default force-field size, the deepest weight ring
+    bool serving = false;
     // the force field runs on a side stream, concurrently with the ensemble kernel
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -709,7 +713,7 @@ static int tune_ff(rid_system* sys, int W, cudaStream_t st) {
     CK(cudaStreamIsCapturing(st, &cs));
     sys->ff_W = W;
     sys->ff_th = dth;
-    if (cs != cudaStreamCaptureStatusNone || dth <= 64) return RID_OK;
+    if (cs != cudaStreamCaptureStatusNone || dth <= 64 || sys->serving) return RID_OK;
     StateDev sd = state_view(sys);
     sd.W = W;
     cudaEvent_t a = nullptr, b = nullptr;
@@ -796,6 +800,11 @@ static int tune_cluster(rid_system* sys, int W, bool energy, cudaStream_t st) {
     std::vector<int> cand = {1};
     if (V.cl_ok[1]) cand.push_back(2);
     if (V.cl_ok[2]) cand.push_back(4);
+    if (sys->serving) {
+        V.csize = 1;
+        V.cs_W = W;
+        return RID_OK;
+    }
     if (cs != cudaStreamCaptureStatusNone || cand.size() == 1) {
         V.csize = cs != cudaStreamCaptureStatusNone ? default_cluster(V, ctas) : 1;
         V.cs_W = W;
@@ -847,7 +856,7 @@ static int tune_tc_stages(rid_system* sys, TcArgs P, cudaStream_t st) {
     TcVariant& V = sys->tcv;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(st, &cs));
-    if (cs != cudaStreamCaptureStatusNone || V.max_stages <= 2) {
+    if (cs != cudaStreamCaptureStatusNone || V.max_stages <= 2 || sys->serving) {
         V.tuned_W = P.W;
         return RID_OK;
     }
@@ -1166,6 +1175,15 @@ int rid_sys_load(rid_system* sys, int W, const float* x0, const float* v0, uint6
     rid_launch_add_u32(sys->d_stepbase.as<uint32_t>(), (uint32_t)step0, st);
     CK(cudaGetLastError());
     return RID_OK;
+}
+
+void rid_sys_serving(rid_system* sys, bool on) {
+    sys->serving = on;
+    if (!on) {   // the next direct use tunes again
+        sys->ff_W = -1;
+        sys->tcv.cs_W = -1;
+        sys->tcv.tuned_W = -1;
+    }
 }
 
 int rid_sys_graph_advance(rid_system* sys, int64_t n_steps, float* dcv, float* deps, cudaStream_t st,

@@ -296,6 +296,8 @@ int rid_sys_device(const rid_system* sys);
 //   read_async: unpack x, v (either may be NULL) into device xyz arrays.
 //   flags: whether any walker went non-finite since the load (synchronises st).
 int rid_sys_load(rid_system* sys, int W, const float* x0, const float* v0, uint64_t step0, cudaStream_t st);
+// while on, the system's kernels run without their tuners (see rid_system::serving)
+void rid_sys_serving(rid_system* sys, bool on);
 int rid_sys_graph_advance(rid_system* sys, int64_t n_steps, float* dcv, float* deps, cudaStream_t st,
                           cudaGraphExec_t* out);
 int rid_sys_advance(rid_system* sys, int64_t n_steps, float* dcv, float* deps, cudaStream_t st);

@@ -486,6 +486,7 @@ void release_job_memory(rid_server* srv, SJob* j) {
         srv->pool.unreserve(j->foot - j->dbuf_bytes);
         j->dbuf = nullptr;
         srv->es[j->slot].job = nullptr;
+        rid_sys_serving(j->rq.sys, false);
     }
 }
 
@@ -516,6 +517,7 @@ int explore_launch_chunk(rid_server* srv, SJob* j) {
 int explore_start(rid_server* srv, SJob* j) {
     ESlot& e = srv->es[j->slot];
     rid_system* sys = j->rq.sys;
+    rid_sys_serving(sys, true);
     STRY(rid_sys_load(sys, j->W, j->x0.data(), j->v0.empty() ? nullptr : j->v0.data(), j->rq.step0, e.st));
     j->chunk = explore_chunk(j->of, j->rq.n_steps);
     if (j->rq.n_steps >= j->chunk) {
