@@ -481,7 +481,10 @@ RID_API int64_t rid_launch_count(rid_system* sys);
  * the next layer's operand exchanged through distributed shared memory).
  * csize = 0 (the default) lets the library time the force evaluation with
  * each eligible size at the first evaluation of every new walker count and
- * keep the fastest.  Every size gives the same results bit for bit.
+ * keep the fastest.  Every size gives the same results bit for bit.  While a
+ * server runs an exploration job on the system (rid_submit), csize = 0 means 1
+ * and nothing is timed: the request loop does not wait on timing runs, and a
+ * size timed on an idle GPU is not the one for a shared GPU.
  * Errors: RID_ERR_ARG (csize not 0, 1, 2 or 4); a size the ensemble's shape
  * does not allow (shared memory) fails with RID_ERR_ARG at the next
  * evaluation.
@@ -502,7 +505,8 @@ RID_API int rid_get_mlp_cluster(rid_system* sys, int32_t* csize);
  * 0 (the default) lets the library time the kernel with every multiple of 32
  * from 64 up to its default size (the chain's bead count rounded up to 32, at
  * most 224) at the first force evaluation of every new walker count and keep
- * the fastest.  Forces are the same bits with every size; force-field energy
+ * the fastest (the default, untimed, while a server runs a job on the
+ * system).  Forces are the same bits with every size; force-field energy
  * evaluations always use the default size.
  * Errors: RID_ERR_ARG (threads not 0 or a multiple of 32 in [32, default]).
  */
