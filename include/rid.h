@@ -481,7 +481,11 @@ RID_API int64_t rid_launch_count(rid_system* sys);
  * the next layer's operand exchanged through distributed shared memory).
  * csize = 0 (the default) lets the library time the force evaluation with
  * each eligible size at the first evaluation of every new walker count and
- * keep the fastest.  Every size gives the same results bit for bit.  While a
+ * keep the fastest.  Every size gives the same results bit for bit.  BF16
+ * ensembles evaluated for at most 16 walkers run a small-batch kernel instead
+ * (the GEMMs transposed, one CTA per member) whatever the size: its results
+ * agree with the other kernels within the BF16 bounds, not bit for bit, and
+ * depend only on the walker count.  While a
  * server runs an exploration job on the system (rid_submit), csize = 0 means 1
  * and nothing is timed: the request loop does not wait on timing runs, and a
  * size timed on an idle GPU is not the one for a shared GPU.

@@ -100,6 +100,9 @@ struct TcVariant {
     unsigned cl_stage_bytes[3] = {0, 0, 0};
     int csize = 1, cs_W = -1;
     int used_cs = 0;   // cluster size of the last launch (0: none yet)
+    // small-batch kernel (k_mlp_tc_small), index 0, 1, 2 = 16, 32, 64 MMA columns
+    bool s_ok[3] = {false, false, false};
+    int s_stages[3] = {0, 0, 0}, s_acc_cols[3] = {0, 0, 0}, s_tmem_cols[3] = {0, 0, 0}, s_nacc[3] = {0, 0, 0};
 };
 
 struct rid_system {
@@ -489,6 +492,21 @@ static int build_tc_variant(rid_system* sys, const std::vector<float>& W, long l
         V.cl_tmem_cols[k] = 32;
         while (V.cl_tmem_cols[k] < 2 * V.cl_acc_cols[k]) V.cl_tmem_cols[k] *= 2;
     }
+    // small-batch variants (BF16 only: the transposed GEMMs take the forward
+    // weights as the A operand in their BF16 image)
+    for (int k = 0; k < 3; ++k) {
+        const int nw = 16 << k;
+        int nmx = 0;
+        for (int g = 0; g < G; ++g) nmx = std::max(nmx, (V.gN[g] + 127) / 128);
+        const int acc = (nmx * nw + 31) / 32 * 32;
+        V.s_nacc[k] = 2 * acc <= 512 ? 2 : 1;
+        V.s_acc_cols[k] = acc;
+        V.s_tmem_cols[k] = 32;
+        while (V.s_tmem_cols[k] < V.s_nacc[k] * acc) V.s_tmem_cols[k] *= 2;
+        const size_t fixs = 1024 + (size_t)V.Kpmax * 2u * nw + sizeof(float) * ((size_t)(L + 1) * H + 16 * (size_t)nw);
+        V.s_stages[k] = fixs + 2 * 16384 <= budget ? (int)std::min<size_t>((budget - fixs) / 16384, TC_MAX_STAGES) : 0;
+        V.s_ok[k] = !fp8 && nmx <= 4 && acc <= 512 && V.s_stages[k] >= 2;
+    }
     V.cs_W = -1;
     V.csize = 1;
     // pre-swizzled byte image: per GEMM, per 128-byte K-chunk, N rows of 128 bytes
@@ -701,6 +719,20 @@ static int ensure_side(rid_system* sys) {
 // a side stream over the remaining SMs; the caller's stream then waits for it.
 static int tune_cluster(rid_system* sys, int W, bool energy, cudaStream_t st);
 
+// The small-batch ensemble kernel's variant for W walkers (0, 1, 2: 16, 32, 64
+// MMA columns), or -1 when the batch is larger or the variant does not fit.
+// Chosen by walker count alone, never by timing.
+static int small_variant(const rid_system* sys, int W) {
+    // 16 MMA columns only: a tcgen05.mma costs about the same whatever its N,
+    // so the transposed form pays more MMAs per GEMM (one per 128 outputs
+    // instead of per 256) and wins only while its epilogue is much smaller
+    // (measured: the paper's 4 x [300]^4 network at 12 walkers 64 us against
+    // 84 us for the row kernel; at 64 walkers 134 us against 84)
+    if (sys->precision != RID_PREC_BF16 || W > 16) return -1;
+    return sys->tcv.s_ok[0] ? 0 : -1;
+}
+
+
 // Autotuner of the force field's CTA size (threads per walker CTA, hence
 // beads per pass and CTAs per SM): at the first force evaluation with a new
 // walker count, k_ff alone is timed with every multiple of 32 from 64 up to
@@ -748,7 +780,8 @@ static int launch_forces(rid_system* sys, int W, int mode, bool energy, cudaStre
     sd.W = W;
     if (sys->ff_W != W && !sys->tuning && !sys->ff_force) TRY(tune_ff(sys, W, st));
     const int ffth = sys->ff_force ? sys->ff_force : sys->ff_th;
-    if (mode == 1 && sys->precision != RID_PREC_FP32 && sys->tcv.cs_W != W && !sys->tuning && !sys->cs_force)
+    if (mode == 1 && sys->precision != RID_PREC_FP32 && sys->tcv.cs_W != W && !sys->tuning && !sys->cs_force &&
+        small_variant(sys, W) < 0)
         TRY(tune_cluster(sys, W, energy, st));
     if (mode != 1) {
         TRY(timed_launch(sys, "k_ff", st, [&] { rid_launch_ff(sys->S, sd, W, energy, st, ffth); }));
@@ -912,6 +945,21 @@ static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_
         P.rsave = E.resnet ? sys->rsave.as<float>() : nullptr;
         P.ngemm = values_only ? E.L : 2 * E.L;
         cudaError_t le = cudaSuccess;
+        const int sk = small_variant(sys, W);
+        if (sk >= 0 && !values_only) {
+            // up to 16 walkers: the transposed small-batch kernel, whatever the cluster setting
+            const int nw = 16 << sk;
+            P.stages = V.s_stages[sk];
+            P.acc_cols = V.s_acc_cols[sk];
+            P.tmem_cols = V.s_tmem_cols[sk];
+            P.nacc = V.s_nacc[sk];
+            P.csize = 1;
+            sys->tcv.used_cs = 1;
+            TRY(timed_launch(sys, "k_mlp_tc", st, [&] { le = rid_launch_mlp_tc_small(P, V.big, V.small, nw, st); }));
+            if (le != cudaSuccess) return fail(RID_ERR_CUDA, "k_mlp_tc_small launch: %s", cudaGetErrorString(le));
+            E.aslices = 1;
+            return RID_OK;
+        }
         const int cs = sys->cs_force ? sys->cs_force : V.cs_W == W ? V.csize : default_cluster(V, P.ntiles * E.M);
         if (cs > 1 && !V.cl_ok[cs == 2 ? 1 : 2])
             return fail(RID_ERR_ARG, "ensemble kernel: cluster size %d does not fit this ensemble's shape", cs);
