@@ -47,6 +47,10 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# 32 hardware work queues for the request loop's 16 exploration streams (the
+# runtime's default of 8 makes streams wait on one another); read when the
+# CUDA context is created, so set before torch starts CUDA.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 from paper_2408_14070_gb300 import inputs as I  # noqa: E402
 
@@ -561,6 +565,7 @@ def run_serving(rid, n_req, rate, plain_req, seed=5):
             "nonfinite": int(sum(1 for st, _ in out.values() if st == rid.RID_ERR_NONFINITE)),
             "failed": int(sum(1 for st, _ in out.values() if st not in (rid.RID_OK, rid.RID_ERR_NONFINITE))),
             "mlp_precision": "bf16",
+            "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
             "plain_per_job": {"requests": len(plain), "path": "rid_label / rid_explore per request in arrival "
                                                               "order, FP32 ensembles, one at a time",
                               "label_latency_ms": {"p50": pct(lat_p["label"], 50), "p99": pct(lat_p["label"], 99)},

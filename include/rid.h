@@ -531,6 +531,12 @@ RID_API int rid_get_ff_threads(rid_system* sys, int32_t* threads);
  * be made with that device current.  rid_submit and rid_poll may be called
  * from any thread; rid_label_batch and rid_server_destroy from one thread at
  * a time.  rid_server_destroy waits for every submitted job to finish.
+ * Exploration jobs run on up to 16 streams of their own.  The CUDA runtime
+ * maps a process's streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware work
+ * queues (8 unless the variable is set, at most 32) and streams sharing a
+ * queue wait on one another's launches, so a process that serves should set
+ * it to 32 before its first CUDA call (the Python binding does so at import
+ * unless it is already set).
  * Errors: RID_ERR_ARG (budget below 1 MiB), RID_ERR_OOM (the budget cannot be
  * allocated), RID_ERR_CUDA.
  */

@@ -12,6 +12,15 @@ import os
 
 import numpy as np
 
+# The request loop runs exploration jobs on up to 16 streams.  The CUDA runtime
+# maps streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware work queues (8 unless
+# set), and streams that share a queue wait on one another's launches: with 32
+# queues the served mix overlaps fully (measured: 1.06 -> 1.58 M walker-steps/s
+# on the serving stream at 200 requests/s).  The runtime reads the variable
+# when the process creates its CUDA context, so it is set here, before any
+# CUDA call the binding makes, unless the caller chose a value.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "librid.so")
 
