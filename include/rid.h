@@ -483,12 +483,15 @@ RID_API int64_t rid_launch_count(rid_system* sys);
  * each eligible size at the first evaluation of every new walker count and
  * keep the fastest.  Every size gives the same results bit for bit.  BF16
  * ensembles evaluated for at most 16 walkers run a small-batch kernel instead
- * (the GEMMs transposed, one CTA per member) whatever the size: its results
- * agree with the other kernels within the BF16 bounds, not bit for bit, and
- * depend only on the walker count.  While a
+ * (the GEMMs transposed, each GEMM's 128-output tiles split over a cluster of
+ * one CTA per tile, at most 4, or at most csize CTAs when csize is fixed; no
+ * timing): its results agree with the other kernels within the BF16 bounds,
+ * not bit for bit, depend only on the walker count and are the same bits for
+ * every split.  While a
  * server runs an exploration job on the system (rid_submit), csize = 0 means 1
- * and nothing is timed: the request loop does not wait on timing runs, and a
- * size timed on an idle GPU is not the one for a shared GPU.
+ * for the row kernels and nothing is timed: the request loop does not wait on
+ * timing runs, and a size timed on an idle GPU is not the one for a shared
+ * GPU.
  * Errors: RID_ERR_ARG (csize not 0, 1, 2 or 4); a size the ensemble's shape
  * does not allow (shared memory) fails with RID_ERR_ARG at the next
  * evaluation.

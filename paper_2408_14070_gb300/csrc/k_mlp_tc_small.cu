@@ -1,5 +1,6 @@
 // k_mlp_tc_small.cu -- the tensor-core ensemble MLP (forward pass and input
-// gradient) for small walker counts, with the GEMMs transposed.
+// gradient) for small walker counts, with the GEMMs transposed and each
+// GEMM's 128-output tiles split over a thread-block cluster.
 //
 // With few walkers a 128-row tile of k_mlp_tc is mostly empty, yet its
 // epilogue turns a 128 x N accumulator into the next operand for every GEMM.
@@ -12,43 +13,65 @@
 // operand is the activation tile [walker][K] in the 128-byte swizzled K-major
 // layout, NW rows per 64-column atom.
 //
-// TMEM: accumulator b of GEMM g holds M-tile mt in columns b * acc_cols +
-// mt * NW .. + NW - 1; lane r of M-tile mt is output mt * 128 + r.  Epilogue
-// warp w (w = 2..17) owns lane quarter w mod 4 and the M-tiles (w - 2) / 4,
-// + 4, ...: a thread holds one output for NW walkers, reads them 16 columns at
-// a time, and writes the next operand one BF16 value per walker.  The next
-// GEMM's operand is released once per GEMM (every epilogue warp arrives on
-// b_ready), after all of this GEMM's MMAs have completed, so a single operand
-// buffer suffices.
+// Cluster split: a cluster of CS CTAs (1..4) serves one member; CTA rank r
+// owns the M-tiles mt = r, r + CS, ... of every GEMM (local tile j = mt / CS),
+// streams only their weight rows and issues only their MMAs.  The outputs of
+// tile mt are columns [128 mt, 128 mt + 128) of the next GEMM's operand: two
+// whole 64-column atoms, one contiguous block of NW x 256 bytes.  The
+// epilogue writes them into this CTA's operand buffer and a copy warp sends
+// the block to every peer that owns tiles of the next GEMM with one bulk
+// shared-to-shared copy, completing on the peer's operand barrier (its MMA
+// warp raises the barrier's expected bytes by what the peers send).  The
+// operand is double buffered (GEMM g reads buffer g mod 2), so a copy for
+// GEMM g + 1 never lands in a buffer a peer's GEMM g still reads.  A tcgen05
+// .mma costs about 90 ns whatever its N (measured), so the split divides the
+// chain's MMA time by CS.  Every M-tile is accumulated by the same sequence of
+// MMAs whichever CTA owns it, and the member value is added in a fixed order
+// on rank 0, so every cluster size gives the same bits.
 //
-// Per element the arithmetic is that of k_mlp_tc (bias, BF16 tanh, saved
-// tanh in BF16, the FP32 residual stream, Delta = g (1 - t^2)); the member
-// value A = w_out . h_L + b_out is reduced per (M-tile, lane quarter) by a
-// warp butterfly and the partials added in a fixed order.  The MMA's operand
-// roles are swapped, so its accumulation may round differently from the
-// other variants: results agree with them within the BF16 bounds, not bit for
-// bit, and the host selects this kernel by walker count alone (never by
-// timing), so a given shape always gives the same bits.  A tcgen05.mma costs
-// about the same whatever its N (measured: 60 MMAs of 128 x 16 x 16 take as
-// long as 60 of 128 x 64 x 16, about 90 ns each, and interleaving M-tiles
-// between K-steps made it slower), so the transposed form issues more MMAs
-// per GEMM than the row form and wins only while its epilogue is much
-// smaller: the host uses it for up to 16 walkers (NW = 16); the kernel also
-// takes NW = 32 and 64.
-// Scratch (per member, in the buffers the other variants use): saved tanh
-// [L][Hp][NW] BF16 in tsave, the residual stream [Hp][NW] FP32 in rsave.
+// TMEM: accumulator b of GEMM g holds local tile j in columns b * acc_cols +
+// j * NW .. + NW - 1; lane r of tile mt is output 128 mt + r.  Epilogue warp w
+// (w = 2..17) owns lane quarter w mod 4; its work items are (local tile,
+// group of 4 walkers), taken in turn by the quarter's four warps.  Per element
+// the arithmetic is that of k_mlp_tc (bias, BF16 tanh, saved tanh in BF16, the
+// FP32 residual stream, Delta = g (1 - t^2)); the member value A = w_out . h_L
+// + b_out is reduced per (M-tile, lane quarter) by a warp butterfly and the
+// partials added in a fixed order.  The MMA's operand roles are swapped, so
+// its accumulation may round differently from the row variants: results
+// agree with them within the BF16 bounds, not bit for bit, and the host
+// selects this kernel by walker count alone (never by timing).
+//
+// The saved tanh [L][rows][NW] BF16 and the residual stream [rows][NW] FP32 of
+// a CTA's own outputs stay in its shared memory: the backward pass reads
+// exactly the outputs the same CTA produced in the forward pass (the backward
+// GEMM of layer l has layer l - 1's neurons as outputs, tiled the same way).
+// Both are stored in 4-walker chunks with the chunk index XOR-swizzled by
+// row, so that a warp's 32 consecutive rows hit distinct banks.
+//
+// Warp roles: warp 0 TMA producer, warp 1 TMEM allocator and MMA issuer,
+// warps 2..17 epilogue, warp 18 bulk copies of the exchange.  Every wait is
+// bounded in time; a CTA whose wait expires sets the error word and stops
+// issuing, its peers' waits then expire too, and every CTA still meets the
+// final cluster barrier, so no CTA exits while another may write into it.
+#include <algorithm>
+
 #include "rid_tc_ptx.cuh"
 
 namespace {
 
-constexpr int SM_MT = 4;     // M-tiles per GEMM (outputs up to 512)
+constexpr int SM_MT = 4;                       // M-tiles per GEMM (outputs up to 512)
+constexpr int SM_GRP = 4;                      // walkers per epilogue work item
+constexpr int SM_COPY_WARP = EPI_WARP0 + EPI_WARPS;
+constexpr int SM_THREADS = 32 * (SM_COPY_WARP + 1);
 
 struct SmemS {
     uint64_t full[TC_MAX_STAGES];
     uint64_t empty[TC_MAX_STAGES];
     uint64_t acc_full[2];
     uint64_t acc_empty[2];
-    uint64_t b_ready;
+    uint64_t b_ready[2];      // operand buffer b complete: 16 epilogue warps + the MMA warp's expect-tx
+                              // arrival, and the peers' bytes
+    uint64_t slice_done[2];   // this CTA's tiles of the operand in buffer b written: 16 epilogue warps
     uint64_t drain;
     uint32_t tmem_base;
     int abort_flag;
@@ -65,21 +88,49 @@ __device__ __forceinline__ uint32_t bs_off(int NW, int r, int col) {
 __device__ __forceinline__ void st_bf16(unsigned char* B, uint32_t off, float v) {
     *reinterpret_cast<__nv_bfloat16*>(B + off) = __float2bfloat16_rn(v);
 }
-// tanh in BF16 of one value (the paired instruction on (x, x)), as a float
-__device__ __forceinline__ float tanh_bf16(float x) {
-    const uint32_t y = tanh_bf16x2(x, x);
-    return __uint_as_float(y << 16);
+// Residual stream: row `row` (a local output), 4-walker chunk cg, as a float4
+// index.  A 128-byte line holds 8 chunks; the chunk is XOR-ed with the row's
+// position among the rows that share a bank pattern.
+__device__ __forceinline__ int rs_idx(int NW, int row, int cg) {
+    const int cpr = NW / SM_GRP;                          // chunks per row: 4, 8, 16
+    const int sw = NW == 16 ? (row >> 1) & 3 : row & 7;
+    return row * cpr + (cg ^ sw);
 }
-// 32 lanes x 16 columns of TMEM into v[0..15]
-__device__ __forceinline__ void tmem_ld16s(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+// Saved tanh: layer l, row, 4-walker chunk cg (8 bytes), as a uint2 index.
+// A 128-byte line holds 16 chunks.
+__device__ __forceinline__ int ts_idx(int NW, int rows, int l, int row, int cg) {
+    const int cpr = NW / SM_GRP;
+    const int sw = NW == 16 ? (row >> 2) & 3 : NW == 32 ? (row >> 1) & 7 : row & 15;
+    return (l * rows + row) * cpr + (cg ^ sw);
+}
+// 32 lanes x 4 columns of TMEM
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                  : "r"(taddr));
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
+// M-tiles of GEMM g owned by rank r of CS (mt = r + j CS < nm)
+__device__ __forceinline__ int owned_tiles(int nm, int r, int CS) { return r < nm ? (nm - r + CS - 1) / CS : 0; }
+// Atoms [a0, a1) of the next operand written by tile mt (kpn: the next GEMM's K)
+__device__ __forceinline__ void tile_atoms(int mt, int kpn, int& a0, int& a1) {
+    a0 = 2 * mt;
+    a1 = 2 * mt + 2 < kpn / 64 ? 2 * mt + 2 : kpn / 64;
+}
+// Bytes of GEMM g's operand (g >= 1) that CTA `rank` receives from its peers
+__device__ __forceinline__ uint32_t peer_bytes(const TcArgs& P, int g, int rank, int CS, int NW) {
+    const int kp = P.gKp[g], nmp = (P.gN[g - 1] + 127) / 128;
+    int own = 0;
+    for (int mt = rank; mt < nmp; mt += CS) {
+        int a0, a1;
+        tile_atoms(mt, kp, a0, a1);
+        own += a1 - a0;
+    }
+    return (uint32_t)(kp / 64 - own) * (uint32_t)NW * 128u;
+}
+
 
 template <bool RES>
 __global__ void __maxnreg__(96)
@@ -90,16 +141,26 @@ __global__ void __maxnreg__(96)
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
     __shared__ SmemS S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int CS = P.csize;
+    const int rank = (int)cluster_rank();
     const int m = blockIdx.y;
     const int L = P.L, G = P.ngemm, H = P.H;
-    unsigned char* Bbuf = dsm;                                             // [Kpmax/64][NW rows][128 B]
-    unsigned char* stages = dsm + (size_t)P.Kpmax * 2u * (size_t)NW;       // [NS][128 rows][128 B]
+    int nmx = 1;
+    for (int g = 0; g < G; ++g) nmx = max(nmx, (P.gN[g] + 127) / 128);
+    const int rows = owned_tiles(nmx, 0, CS) * 128;                        // local output rows (rank 0 owns most)
+    const int ngrp = NW / SM_GRP;
+    const size_t bbytes = (size_t)P.Kpmax * 2u * (size_t)NW;
+    // operand buffers 0 and 1, [Kp/64][NW rows][128 B] each
+    auto Bbuf = [&](int i) -> unsigned char* { return dsm + (size_t)i * bbytes; };
+    unsigned char* stages = dsm + 2 * bbytes;                               // [NS][128 rows][128 B]
     const uint32_t stage_bytes = 128u * 128u;
     const int NS = P.stages;
     const int NACC = P.nacc;
-    float* sbias = reinterpret_cast<float*>(stages + (size_t)NS * stage_bytes);   // [L][H]
-    float* swout = sbias + (size_t)L * H;                                          // [H]
-    float* spart = swout + H;                                                      // [SM_MT * 4][NW]
+    uint2* tsv = reinterpret_cast<uint2*>(stages + (size_t)NS * stage_bytes);             // [L][rows][NW/4]
+    float4* rsv = reinterpret_cast<float4*>(tsv + (size_t)L * rows * ngrp);               // [rows][NW/4] (RES)
+    float* sbias = reinterpret_cast<float*>(rsv + (RES ? (size_t)rows * ngrp : 0));       // [L][H]
+    float* swout = sbias + (size_t)L * H;                                                  // [H]
+    float* spart = swout + H;                                                              // [SM_MT * 4][NW]
     volatile int* abort_flag = &S.abort_flag;
 
     if (threadIdx.x == 0) {
@@ -110,8 +171,9 @@ __global__ void __maxnreg__(96)
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&S.acc_full[b]), 1);
             mbar_init(smem_u32(&S.acc_empty[b]), EPI_WARPS);
+            mbar_init(smem_u32(&S.b_ready[b]), EPI_WARPS + 1);
+            mbar_init(smem_u32(&S.slice_done[b]), EPI_WARPS);
         }
-        mbar_init(smem_u32(&S.b_ready), EPI_WARPS);
         mbar_init(smem_u32(&S.drain), 1);
         S.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -123,34 +185,37 @@ __global__ void __maxnreg__(96)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     fence_before();
-    __syncthreads();
+    // barriers initialised in every CTA before any peer copies into them
+    cluster_sync_all();
     fence_after();
     const uint32_t tmem = S.tmem_base;
     if (warp == 0) {
-        // ------------------------------------------------------------ TMA producer: weight M-tiles
+        // ------------------------------------------------------------ TMA producer: this CTA's weight M-tiles
         if (lane == 0) {
             int it = 0;
             int last_it[TC_MAX_STAGES];
             for (int s = 0; s < NS; ++s) last_it[s] = -1;
             bool ok = true;
             for (int g = 0; g < G && ok; ++g) {
-                const int N = P.gN[g], nch = P.gKp[g] * 2 / 128, nm = (N + 127) / 128;
+                const int N = P.gN[g], nch = P.gKp[g] * 2 / 128;
+                const int nj = owned_tiles((N + 127) / 128, rank, CS);
                 for (int c = 0; c < nch && ok; ++c)
-                    for (int mt = 0; mt < nm; ++mt, ++it) {
-                        const int rows = N - mt * 128 < 128 ? N - mt * 128 : 128;
+                    for (int j = 0; j < nj; ++j, ++it) {
+                        const int mt = rank + j * CS;
+                        const int rws = N - mt * 128 < 128 ? N - mt * 128 : 128;
                         const int s = it % NS;
                         if (!mbar_wait(smem_u32(&S.empty[s]), ((it / NS) & 1) ^ 1, abort_flag, P.err, 1)) {
                             ok = false;
                             break;
                         }
-                        mbar_arrive_tx(smem_u32(&S.full[s]), (uint32_t)rows * 128u);
+                        mbar_arrive_tx(smem_u32(&S.full[s]), (uint32_t)rws * 128u);
                         last_it[s] = it;
                         const long long row0 = (long long)m * P.member_rows + P.grow[g] + (long long)c * N + mt * 128;
                         uint32_t dst = smem_u32(stages + (size_t)s * stage_bytes);
                         int r = 0;
-                        for (; r + 64 <= rows; r += 64, dst += 8192u)
+                        for (; r + 64 <= rws; r += 64, dst += 8192u)
                             tma_load_2d(dst, &map_big, 0, (int)(row0 + r), smem_u32(&S.full[s]));
-                        for (; r < rows; r += 8, dst += 1024u)
+                        for (; r < rws; r += 8, dst += 1024u)
                             tma_load_2d(dst, &map_small, 0, (int)(row0 + r), smem_u32(&S.full[s]));
                     }
             }
@@ -170,6 +235,7 @@ __global__ void __maxnreg__(96)
             const uint32_t id = idesc_bf16(128, NW);
             for (int g = 0; g < G && ok; ++g) {
                 const int N = P.gN[g], nch = P.gKp[g] * 2 / 128, nm = (N + 127) / 128;
+                const int nj = owned_tiles(nm, rank, CS);
                 const int b = g % NACC;
                 const uint32_t dacc = tmem + (uint32_t)(b * P.acc_cols);
                 if (g >= NACC &&
@@ -177,15 +243,18 @@ __global__ void __maxnreg__(96)
                     ok = false;
                     break;
                 }
-                // the operand of GEMM g: written by the prologue (g = 0) or by GEMM g-1's epilogue
-                if (!mbar_wait(smem_u32(&S.b_ready), g & 1, abort_flag, P.err, 4)) {
+                // the operand of GEMM g: the prologue (g = 0) or GEMM g-1's epilogues, this CTA's
+                // tiles written locally, the peers' tiles arriving as bytes
+                const uint32_t pb = (g > 0 && rank < nm) ? peer_bytes(P, g, rank, CS, NW) : 0u;
+                mbar_arrive_expect_tx(smem_u32(&S.b_ready[g & 1]), pb);
+                if (!mbar_wait_cluster(smem_u32(&S.b_ready[g & 1]), (g >> 1) & 1, abort_flag, P.err, 4)) {
                     ok = false;
                     break;
                 }
                 fence_after();
                 for (int c = 0; c < nch && ok; ++c) {
-                    const uint32_t b_atom = smem_u32(Bbuf) + (uint32_t)(c * NW * 128);
-                    for (int mt = 0; mt < nm; ++mt, ++it) {
+                    const uint32_t b_atom = smem_u32(Bbuf(g & 1)) + (uint32_t)(c * NW * 128);
+                    for (int j = 0; j < nj; ++j, ++it) {
                         const int s = it % NS;
                         if (!mbar_wait(smem_u32(&S.full[s]), (it / NS) & 1, abort_flag, P.err, 4)) {
                             ok = false;
@@ -195,7 +264,7 @@ __global__ void __maxnreg__(96)
                         const uint32_t a_atom = smem_u32(stages + (size_t)s * stage_bytes);
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)
-                            mma_bf16(dacc + (uint32_t)(mt * NW), desc_sw128(a_atom + 32u * kk),
+                            mma_bf16(dacc + (uint32_t)(j * NW), desc_sw128(a_atom + 32u * kk),
                                      desc_sw128(b_atom + 32u * kk), id, (c | kk) != 0);
                         mma_commit(smem_u32(&S.empty[s]));
                     }
@@ -206,11 +275,31 @@ __global__ void __maxnreg__(96)
             const unsigned long long t0 = gtimer();
             while (!mbar_try(smem_u32(&S.drain), 0) && gtimer() - t0 < WAIT_NS) {}
         }
+    } else if (warp == SM_COPY_WARP) {
+        // ------------------------------------------------------------ bulk exchange
+        if (lane == 0 && CS > 1) {
+            for (int g = 0; g + 1 < G; ++g) {
+                if (!mbar_wait(smem_u32(&S.slice_done[g & 1]), (g >> 1) & 1, abort_flag, P.err, 16)) break;
+                const int nm = (P.gN[g] + 127) / 128, kpn = P.gKp[g + 1];
+                const int nmn = (P.gN[g + 1] + 127) / 128;   // peers owning tiles of GEMM g+1 need the operand
+                const int nq = CS < nmn ? CS : nmn;
+                for (int mt = rank; mt < nm; mt += CS) {
+                    int a0, a1;
+                    tile_atoms(mt, kpn, a0, a1);
+                    if (a1 <= a0) continue;
+                    const uint32_t bytes = (uint32_t)(a1 - a0) * (uint32_t)NW * 128u;
+                    const uint32_t src = smem_u32(Bbuf((g + 1) & 1)) + (uint32_t)a0 * (uint32_t)NW * 128u;
+                    for (int q = 0; q < nq; ++q)
+                        if (q != rank) bulk_copy_to_peer(src, bytes, smem_u32(&S.b_ready[(g + 1) & 1]), (uint32_t)q);
+                }
+                bulk_commit_and_wait_read();
+            }
+        }
     } else {
         // ------------------------------------------------------------ epilogue
         const int e = warp - EPI_WARP0;          // 0..15
         const int quarter = warp & 3;            // TMEM lane quarter this warp may access
-        const int sub = e >> 2;                  // first M-tile of this warp
+        const int sub = e >> 2;                  // this warp's turn among the quarter's four
         const int ET = 32 * EPI_WARPS;
         const int W = P.W;
         // GEMM 0 operand: u (FP32, [W][D]) -> [walker][K] BF16, zeros past D and for walkers >= W
@@ -224,22 +313,20 @@ __global__ void __maxnreg__(96)
                     const int k = col + i;
                     v[i] = (w < W && k < P.D) ? __ldg(P.u + (size_t)w * P.D + k) : 0.0f;
                 }
-                *reinterpret_cast<uint4*>(Bbuf + bs_off(NW, w, col)) = pack8(v);
+                *reinterpret_cast<uint4*>(Bbuf(0) + bs_off(NW, w, col)) = pack8(v);
             }
             fence_async_smem();
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&S.b_ready));
+            if (lane == 0) mbar_arrive(smem_u32(&S.b_ready[0]));
         }
         for (int idx = e * 32 + lane; idx < (L + 1) * H; idx += ET) {
             const int l = idx / H, c = idx - l * H;
             sbias[idx] = l < L ? __ldg(P.bias + ((size_t)m * L + l) * H + c) : __ldg(P.wout + (size_t)m * H + c);
         }
         asm volatile("bar.sync 1, %0;" ::"r"(ET) : "memory");   // all epilogue warps, before any bounded wait
-        // per-member scratch: saved tanh [L][H][NW] BF16, residual stream [H][NW] FP32
-        __nv_bfloat16* tsv = P.tsave + (size_t)m * P.ntiles * (size_t)L * 128 * H;
-        float* rsv = RES ? P.rsave + (size_t)m * P.ntiles * (size_t)128 * H : nullptr;
         for (int g = 0; g < G; ++g) {
             const int N = P.gN[g], nm = (N + 127) / 128;
+            const int nj = owned_tiles(nm, rank, CS);
             const bool fwd = g < L;
             const int l = fwd ? g : (2 * L - 1 - g);
             const int b = g % NACC;
@@ -247,104 +334,106 @@ __global__ void __maxnreg__(96)
             const bool res_fwd = RES && fwd && l >= 1;
             const bool res_bwd = RES && !fwd && l >= 1;
             const bool res_st = RES && (fwd ? l < L - 1 : l >= 2);
+            const bool res_ld = res_fwd || (res_bwd && l < L - 1);
+            unsigned char* Bn = Bbuf((g + 1) & 1);
             if (!mbar_wait(smem_u32(&S.acc_full[b]), (g / NACC) & 1, abort_flag, P.err, 8)) break;
             fence_after();
-            for (int mt = sub; mt < nm; mt += 4) {
-                const int n = mt * 128 + quarter * 32 + lane;   // the output this thread holds
-                const bool vn = n < N;
-                const uint32_t tacc = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * P.acc_cols + mt * NW);
-                const float bn = (fwd && vn) ? sbias[l * H + n] : 0.0f;
-                const float wo = vn && n < H ? swout[n] : 0.0f;
-                for (int w0 = 0; w0 < NW; w0 += 16) {
-                    float a[16];
-                    tmem_ld16s(tacc + (uint32_t)w0, a);
-                    // the residual stream of this output for the 16 walkers, read whole
-                    // before any of it is overwritten
-                    float rp[16];
-                    float4* rq = RES ? reinterpret_cast<float4*>(rsv + (size_t)n * NW + w0) : nullptr;
-                    if (RES && vn && (res_fwd || (res_bwd && l < L - 1))) {
+            const int items = nj * ngrp;
+            const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * P.acc_cols);
+            for (int base = sub; base < items; base += 16) {
+                // up to four items (base, base + 4, ...) loaded before one wait
+                float a[4][4];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const float4 v = rq[q];
-                            rp[4 * q] = v.x;
-                            rp[4 * q + 1] = v.y;
-                            rp[4 * q + 2] = v.z;
-                            rp[4 * q + 3] = v.w;
-                        }
+                for (int k = 0; k < 4; ++k) {
+                    const int itm = base + 4 * k;
+                    if (itm < items) {
+                        const int j = itm / ngrp, cg = itm - (itm / ngrp) * ngrp;
+                        tmem_ld4(tq + (uint32_t)(j * NW + cg * SM_GRP), a[k]);
                     }
-                    tmem_wait_ld();
-                    float out[16];   // this GEMM's contribution to the next operand
-                    float part[16];  // member value terms w_out[n] h_L[n][w] (last forward layer)
-                    float rs[16];    // residual stream values to store
-                    if (fwd) {
-                        __nv_bfloat16 tb[16];
+                }
+                tmem_wait_ld();
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const float t = tanh_bf16(a[i] + bn);
-                            tb[i] = __float2bfloat16_rn(t);
-                            float h = t;
-                            if (RES && res_fwd && vn) h = rp[i] + t;
+                for (int k = 0; k < 4; ++k) {
+                    const int itm = base + 4 * k;
+                    if (itm >= items) break;
+                    const int j = itm / ngrp, cg = itm - (itm / ngrp) * ngrp;
+                    const int mt = rank + j * CS;
+                    const int row = j * 128 + quarter * 32 + lane;   // local output row
+                    const int n = mt * 128 + quarter * 32 + lane;    // the output this thread holds
+                    const bool vn = n < N;
+                    const float bn = (fwd && vn) ? sbias[l * H + n] : 0.0f;
+                    const float wo = vn && n < H ? swout[n] : 0.0f;
+                    float rp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                    if (RES && vn && res_ld) {
+                        const float4 v = rsv[rs_idx(NW, row, cg)];
+                        rp[0] = v.x;
+                        rp[1] = v.y;
+                        rp[2] = v.z;
+                        rp[3] = v.w;
+                    }
+                    float out[4];    // this GEMM's contribution to the next operand
+                    float part[4];   // member value terms w_out[n] h_L[n][w] (last forward layer)
+                    float rs[4];     // residual stream values to store
+                    if (fwd) {
+                        // t = tanh(z) in BF16, elementwise on pairs of walkers
+                        const uint32_t y01 = tanh_bf16x2(a[k][0] + bn, a[k][1] + bn);
+                        const uint32_t y23 = tanh_bf16x2(a[k][2] + bn, a[k][3] + bn);
+                        const float t[4] = {__uint_as_float(y01 << 16), __uint_as_float(y01 & 0xffff0000u),
+                                            __uint_as_float(y23 << 16), __uint_as_float(y23 & 0xffff0000u)};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            float h = t[i];
+                            if (RES && res_fwd && vn) h = rp[i] + t[i];
                             rs[i] = h;
                             part[i] = vn ? wo * h : 0.0f;
-                            out[i] = l == L - 1 ? wo * (1.0f - t * t) : h;
+                            out[i] = l == L - 1 ? wo * (1.0f - t[i] * t[i]) : h;
                         }
-                        if (vn) {
-                            uint4* dst = reinterpret_cast<uint4*>(tsv + ((size_t)l * H + n) * NW + w0);
-                            dst[0] = *reinterpret_cast<const uint4*>(&tb[0]);
-                            dst[1] = *reinterpret_cast<const uint4*>(&tb[8]);
-                        }
+                        if (vn) tsv[ts_idx(NW, rows, l, row, cg)] = make_uint2(y01, y23);
                     } else if (l > 0) {
                         // G_{l-1} (+ dA/dh_l) -> Delta_{l-1} = G (1 - t_{l-1}^2)
-                        __nv_bfloat16 tb[16];
-                        if (vn) {
-                            const uint4* src = reinterpret_cast<const uint4*>(tsv + ((size_t)(l - 1) * H + n) * NW + w0);
-                            *reinterpret_cast<uint4*>(&tb[0]) = src[0];
-                            *reinterpret_cast<uint4*>(&tb[8]) = src[1];
-                        }
+                        const uint2 tw = vn ? tsv[ts_idx(NW, rows, l - 1, row, cg)] : make_uint2(0u, 0u);
+                        const float t[4] = {__uint_as_float(tw.x << 16), __uint_as_float(tw.x & 0xffff0000u),
+                                            __uint_as_float(tw.y << 16), __uint_as_float(tw.y & 0xffff0000u)};
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            float gv = a[i];
+                        for (int i = 0; i < 4; ++i) {
+                            float gv = a[k][i];
                             if (RES && res_bwd && vn) gv = (l == L - 1 ? wo : rp[i]) + gv;
                             rs[i] = gv;
-                            const float t = vn ? __bfloat162float(tb[i]) : 0.0f;
-                            out[i] = gv * (1.0f - t * t);
+                            out[i] = gv * (1.0f - t[i] * t[i]);
                             part[i] = 0.0f;
                         }
                     } else {
                         // G_0 = dA/du (n is an input index): dA/ds_j = -sin s_j g[2j] + cos s_j g[2j+1]
                         // (torsion), g[2j] (distance); the pair's odd element comes from the next lane
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const float g1 = __shfl_down_sync(0xffffffffu, a[i], 1);
-                            const int w = w0 + i, j = n >> 1;
-                            if (!(n & 1) && 2 * j < P.D && w < W && !*abort_flag) {
-                                const float cs = __ldg(P.u + (size_t)w * P.D + 2 * j);
-                                const float sn = __ldg(P.u + (size_t)w * P.D + 2 * j + 1);
-                                const bool dist = P.cvdist && __ldg(P.cvdist + j);
-                                P.gradA[((size_t)m * W + w) * P.C + j] = dist ? a[i] : -sn * a[i] + cs * g1;
+                        for (int i = 0; i < 4; ++i) {
+                            const float g1 = __shfl_down_sync(0xffffffffu, a[k][i], 1);
+                            const int w = cg * SM_GRP + i, jc = n >> 1;
+                            if (!(n & 1) && 2 * jc < P.D && w < W && !*abort_flag) {
+                                const float cs = __ldg(P.u + (size_t)w * P.D + 2 * jc);
+                                const float sn = __ldg(P.u + (size_t)w * P.D + 2 * jc + 1);
+                                const bool dist = P.cvdist && __ldg(P.cvdist + jc);
+                                P.gradA[((size_t)m * W + w) * P.C + jc] = dist ? a[k][i] : -sn * a[k][i] + cs * g1;
                             }
                             out[i] = 0.0f;
                             part[i] = 0.0f;
                             rs[i] = 0.0f;
                         }
                     }
-                    if (RES && res_st && vn) {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            rq[q] = make_float4(rs[4 * q], rs[4 * q + 1], rs[4 * q + 2], rs[4 * q + 3]);
-                    }
+                    if (RES && res_st && vn) rsv[rs_idx(NW, row, cg)] = make_float4(rs[0], rs[1], rs[2], rs[3]);
                     if (g < G - 1 && n < kpn) {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) st_bf16(Bbuf, bs_off(NW, w0 + i, n), vn ? out[i] : 0.0f);
+                        for (int i = 0; i < 4; ++i) st_bf16(Bn, bs_off(NW, cg * SM_GRP + i, n), vn ? out[i] : 0.0f);
                     }
                     if (fwd && l == L - 1) {
-                        // member value: this warp's 32 outputs, butterfly over the lanes
+                        // member value: this warp's 32 outputs, butterfly over the lanes, into rank 0
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
+                        for (int i = 0; i < 4; ++i) {
                             float p = part[i];
 #pragma unroll
                             for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-                            if (lane == 0) spart[(mt * 4 + quarter) * NW + w0 + i] = p;
+                            if (lane == 0)
+                                st_cluster_f32(mapa(smem_u32(&spart[(mt * 4 + quarter) * NW + cg * SM_GRP + i]), 0u), p);
                         }
                     }
                 }
@@ -352,7 +441,10 @@ __global__ void __maxnreg__(96)
             if (g < G - 1) {
                 fence_async_smem();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&S.b_ready));
+                if (lane == 0) {
+                    mbar_arrive(smem_u32(&S.b_ready[(g + 1) & 1]));
+                    if (CS > 1) mbar_arrive(smem_u32(&S.slice_done[g & 1]));
+                }
             }
             fence_before();
             __syncwarp();
@@ -361,8 +453,10 @@ __global__ void __maxnreg__(96)
     }
     fence_before();
     __syncthreads();
-    // member value A = sum over (M-tile, lane quarter) partials in that order, + b_out
-    if (warp >= EPI_WARP0 && warp < EPI_WARP0 + 2) {
+    // every CTA's partials are in rank 0: member value A = sum over (M-tile, lane quarter)
+    // in that order, + b_out
+    cluster_sync_all();
+    if (rank == 0 && warp >= EPI_WARP0 && warp < EPI_WARP0 + 2) {
         const int w = (warp - EPI_WARP0) * 32 + lane;
         const int nmL = (P.gN[L - 1] + 127) / 128;
         if (w < P.W && w < NW && !S.abort_flag) {
@@ -380,19 +474,27 @@ __global__ void __maxnreg__(96)
 
 }  // namespace
 
+// Shared memory of the small-batch kernel at P.csize CTAs per member and
+// P.stages weight stages (0: the fixed part alone).
 size_t rid_mlp_tc_small_smem_bytes(const TcArgs& P, int NW) {
-    return 1024 + (size_t)P.Kpmax * 2u * NW + (size_t)P.stages * 128u * 128u +
-           sizeof(float) * ((size_t)(P.L + 1) * P.H + (size_t)SM_MT * 4 * NW);
+    int nmx = 1;
+    for (int g = 0; g < 2 * P.L; ++g) nmx = std::max(nmx, (P.gN[g] + 127) / 128);
+    const int CS = P.csize < 1 ? 1 : P.csize;
+    const size_t rows = (size_t)((nmx + CS - 1) / CS) * 128;
+    return 1024 + 2 * (size_t)P.Kpmax * 2u * NW + (size_t)P.stages * 128u * 128u + (size_t)P.L * rows * NW * 2u +
+           (P.resnet ? rows * NW * 4u : 0) + sizeof(float) * ((size_t)(P.L + 1) * P.H + (size_t)SM_MT * 4 * NW);
 }
 
 cudaError_t rid_launch_mlp_tc_small(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, int NW,
                                     cudaStream_t s) {
     if (P.ngemm != 2 * P.L || P.W > NW || (NW != 16 && NW != 32 && NW != 64)) return cudaErrorInvalidValue;
-    if (P.resnet && !P.rsave) return cudaErrorInvalidValue;
+    if (P.csize < 1 || P.csize > SM_MT || P.stages < 2 || P.stages > TC_MAX_STAGES) return cudaErrorInvalidValue;
     if (P.geb[0] != 2) return cudaErrorInvalidValue;   // BF16 only
+    for (int g = 0; g < 2 * P.L; ++g)
+        if (P.gN[g] > 128 * SM_MT) return cudaErrorInvalidValue;
     const size_t smem = rid_mlp_tc_small_smem_bytes(P, NW);
     const int v = P.resnet ? 1 : 0;
-    static size_t attr[2][64] = {};
+    static size_t attr[2][64] = {};   // shared memory opted into, per instantiation and device
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
     size_t& have = attr[v][dev & 63];
@@ -402,6 +504,17 @@ cudaError_t rid_launch_mlp_tc_small(const TcArgs& P, const CUtensorMap& big, con
         if (e != cudaSuccess) return e;
         have = smem;
     }
-    kern<<<dim3(1, P.M, 1), NTHREADS, smem, s>>>(P, big, small, NW);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(P.csize, P.M, 1);
+    cfg.blockDim = dim3(SM_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = P.csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, P, big, small, NW);
 }

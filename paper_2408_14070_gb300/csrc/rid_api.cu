@@ -100,9 +100,11 @@ struct TcVariant {
     unsigned cl_stage_bytes[3] = {0, 0, 0};
     int csize = 1, cs_W = -1;
     int used_cs = 0;   // cluster size of the last launch (0: none yet)
-    // small-batch kernel (k_mlp_tc_small), index 0, 1, 2 = 16, 32, 64 MMA columns
-    bool s_ok[3] = {false, false, false};
-    int s_stages[3] = {0, 0, 0}, s_acc_cols[3] = {0, 0, 0}, s_tmem_cols[3] = {0, 0, 0}, s_nacc[3] = {0, 0, 0};
+    // small-batch kernel (k_mlp_tc_small): [k][cs], k = 0, 1, 2 for 16, 32, 64
+    // MMA columns, cs = 1..4 CTAs per member splitting the 128-output tiles
+    int s_tiles = 0;   // 128-output tiles of the widest GEMM
+    bool s_ok[3][5] = {};
+    int s_stages[3][5] = {}, s_acc_cols[3][5] = {}, s_tmem_cols[3][5] = {}, s_nacc[3][5] = {};
 };
 
 struct rid_system {
@@ -493,20 +495,32 @@ static int build_tc_variant(rid_system* sys, const std::vector<float>& W, long l
         while (V.cl_tmem_cols[k] < 2 * V.cl_acc_cols[k]) V.cl_tmem_cols[k] *= 2;
     }
     // small-batch variants (BF16 only: the transposed GEMMs take the forward
-    // weights as the A operand in their BF16 image)
-    for (int k = 0; k < 3; ++k) {
-        const int nw = 16 << k;
-        int nmx = 0;
-        for (int g = 0; g < G; ++g) nmx = std::max(nmx, (V.gN[g] + 127) / 128);
-        const int acc = (nmx * nw + 31) / 32 * 32;
-        V.s_nacc[k] = 2 * acc <= 512 ? 2 : 1;
-        V.s_acc_cols[k] = acc;
-        V.s_tmem_cols[k] = 32;
-        while (V.s_tmem_cols[k] < V.s_nacc[k] * acc) V.s_tmem_cols[k] *= 2;
-        const size_t fixs = 1024 + (size_t)V.Kpmax * 2u * nw + sizeof(float) * ((size_t)(L + 1) * H + 16 * (size_t)nw);
-        V.s_stages[k] = fixs + 2 * 16384 <= budget ? (int)std::min<size_t>((budget - fixs) / 16384, TC_MAX_STAGES) : 0;
-        V.s_ok[k] = !fp8 && nmx <= 4 && acc <= 512 && V.s_stages[k] >= 2;
-    }
+    // weights as the A operand in their BF16 image), per MMA width and number
+    // of CTAs splitting the 128-output tiles
+    int nmx = 0;
+    for (int g = 0; g < G; ++g) nmx = std::max(nmx, (V.gN[g] + 127) / 128);
+    V.s_tiles = nmx;
+    for (int k = 0; k < 3; ++k)
+        for (int cs = 1; cs <= 4; ++cs) {
+            const int nw = 16 << k, own = (nmx + cs - 1) / cs;
+            TcArgs Q{};
+            Q.L = L;
+            Q.H = H;
+            Q.Kpmax = V.Kpmax;
+            Q.resnet = sys->E.resnet;
+            Q.csize = cs;
+            Q.stages = 0;
+            for (int g = 0; g < G; ++g) Q.gN[g] = V.gN[g];
+            const size_t fixs = rid_mlp_tc_small_smem_bytes(Q, nw);
+            const int acc = (own * nw + 31) / 32 * 32;
+            V.s_nacc[k][cs] = 2 * acc <= 512 ? 2 : 1;
+            V.s_acc_cols[k][cs] = acc;
+            V.s_tmem_cols[k][cs] = 32;
+            while (V.s_tmem_cols[k][cs] < V.s_nacc[k][cs] * acc) V.s_tmem_cols[k][cs] *= 2;
+            V.s_stages[k][cs] =
+                fixs + 2 * 16384 <= budget ? (int)std::min<size_t>((budget - fixs) / 16384, TC_MAX_STAGES) : 0;
+            V.s_ok[k][cs] = !fp8 && nmx <= 4 && cs <= nmx && acc <= 512 && V.s_stages[k][cs] >= 2;
+        }
     V.cs_W = -1;
     V.csize = 1;
     // pre-swizzled byte image: per GEMM, per 128-byte K-chunk, N rows of 128 bytes
@@ -722,14 +736,22 @@ static int tune_cluster(rid_system* sys, int W, bool energy, cudaStream_t st);
 // The small-batch ensemble kernel's variant for W walkers (0, 1, 2: 16, 32, 64
 // MMA columns), or -1 when the batch is larger or the variant does not fit.
 // Chosen by walker count alone, never by timing.
+// Its CTAs per member: one per 128-output tile of the widest GEMM (up to 4),
+// or at most the size fixed by rid_set_mlp_cluster.  Every size gives the
+// same bits.
+static int small_cs(const rid_system* sys) {
+    const int t = std::max(1, sys->tcv.s_tiles);
+    return sys->cs_force ? std::min(sys->cs_force, t) : std::min(t, 4);
+}
 static int small_variant(const rid_system* sys, int W) {
     // 16 MMA columns only: a tcgen05.mma costs about the same whatever its N,
     // so the transposed form pays more MMAs per GEMM (one per 128 outputs
     // instead of per 256) and wins only while its epilogue is much smaller
-    // (measured: the paper's 4 x [300]^4 network at 12 walkers 64 us against
-    // 84 us for the row kernel; at 64 walkers 134 us against 84)
+    // (measured with one CTA per member: the paper's 4 x [300]^4 network at
+    // 12 walkers 64 us against 84 us for the row kernel; at 64 walkers 134 us
+    // against 84)
     if (sys->precision != RID_PREC_BF16 || W > 16) return -1;
-    return sys->tcv.s_ok[0] ? 0 : -1;
+    return sys->tcv.s_ok[0][small_cs(sys)] ? 0 : -1;
 }
 
 
@@ -947,14 +969,14 @@ static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_
         cudaError_t le = cudaSuccess;
         const int sk = small_variant(sys, W);
         if (sk >= 0 && !values_only) {
-            // up to 16 walkers: the transposed small-batch kernel, whatever the cluster setting
-            const int nw = 16 << sk;
-            P.stages = V.s_stages[sk];
-            P.acc_cols = V.s_acc_cols[sk];
-            P.tmem_cols = V.s_tmem_cols[sk];
-            P.nacc = V.s_nacc[sk];
-            P.csize = 1;
-            sys->tcv.used_cs = 1;
+            // up to 16 walkers: the transposed small-batch kernel, its output tiles split over a cluster
+            const int nw = 16 << sk, scs = small_cs(sys);
+            P.stages = V.s_stages[sk][scs];
+            P.acc_cols = V.s_acc_cols[sk][scs];
+            P.tmem_cols = V.s_tmem_cols[sk][scs];
+            P.nacc = V.s_nacc[sk][scs];
+            P.csize = scs;
+            sys->tcv.used_cs = scs;
             TRY(timed_launch(sys, "k_mlp_tc", st, [&] { le = rid_launch_mlp_tc_small(P, V.big, V.small, nw, st); }));
             if (le != cudaSuccess) return fail(RID_ERR_CUDA, "k_mlp_tc_small launch: %s", cudaGetErrorString(le));
             E.aslices = 1;

@@ -259,6 +259,12 @@ CLUSTER_CASES = [
 ]
 
 
+def small_batch_tiles(H, D):
+    """128-output tiles of the widest GEMM (hidden width H, or the input
+    gradient's D inputs padded to 64)."""
+    return -(-max(H, -(-D // 64) * 64) // 128)
+
+
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
 @pytest.mark.parametrize("n,C,W,M,L,H,resnet,seed", CLUSTER_CASES)
 def test_cluster_sizes_give_identical_bits(R, orc, prec, n, C, W, M, L, H, resnet, seed):
@@ -278,8 +284,10 @@ def test_cluster_sizes_give_identical_bits(R, orc, prec, n, C, W, M, L, H, resne
             sysobj.set_ensemble(ens, precision=p)
             sysobj.set_mlp_cluster(cs)
             sysobj.eval_forces(x, R.RID_BIAS_ENSEMBLE, f_out=f, eps_out=eps, abar_out=abar, grad_out=g)
-            # up to 16 walkers a BF16 ensemble runs the small-batch kernel (one CTA per member)
-            assert sysobj.mlp_cluster() == (1 if W <= 16 and prec == "bf16" else cs)
+            # up to 16 walkers a BF16 ensemble runs the small-batch kernel, its 128-output
+            # tiles split over at most cs CTAs
+            t = small_batch_tiles(H, 2 * C)
+            assert sysobj.mlp_cluster() == (min(cs, t) if W <= 16 and prec == "bf16" and t <= 4 else cs)
             xo = np.zeros_like(x[:9])
             sysobj.explore(np.ascontiguousarray(x[:9]), 6, x_out=xo)
         outs[cs] = (f, eps, abar, g, xo)
@@ -318,8 +326,10 @@ def test_cluster_size_argument_errors(R):
             assert e.value.code == R.RID_ERR_ARG
             s2.set_mlp_cluster(0)
             s2.eval_forces(x, R.RID_BIAS_ENSEMBLE, f_out=np.zeros((65, 140, 3), np.float32))
-            # up to 16 walkers the small-batch kernel runs, whatever the cluster setting
-            s2.set_mlp_cluster(4)
+            # up to 16 walkers the small-batch kernel runs, its four 128-output tiles
+            # split over at most the fixed number of CTAs
             x3 = np.ascontiguousarray(x[:3])
-            s2.eval_forces(x3, R.RID_BIAS_ENSEMBLE, f_out=np.zeros((3, 140, 3), np.float32))
-            assert s2.mlp_cluster() == 1
+            for cs, used in ((4, 4), (2, 2), (1, 1), (0, 4)):
+                s2.set_mlp_cluster(cs)
+                s2.eval_forces(x3, R.RID_BIAS_ENSEMBLE, f_out=np.zeros((3, 140, 3), np.float32))
+                assert s2.mlp_cluster() == used, cs

@@ -1,13 +1,14 @@
 """The small-batch tensor-core ensemble kernel (k_mlp_tc_small: up to 16
-walkers, BF16, the GEMMs transposed so that the outputs fill the MMA's rows).
+walkers, BF16, the GEMMs transposed so that the outputs fill the MMA's rows,
+the 128-output tiles split over the CTAs of a cluster).
 
 Against the FP64 oracle at the BF16 bounds of the other tensor-core tests
 (mean CV gradient normwise 3e-2, member values and model deviation likewise),
 on walker counts 1 to 16 (ragged and full), residual networks, the paper's
 width 300 at its 12 walkers and width 512 (four M-tiles), 128 inputs;
-determinism (repeated evaluations and trajectories are the same bits); and
-agreement with the 128-row kernel, which evaluates the same walkers inside a
-larger batch.
+determinism (repeated evaluations and trajectories are the same bits); the
+same bits with the tiles split over 1, 2, 3 or 4 CTAs; and agreement with the
+128-row kernel, which evaluates the same walkers inside a larger batch.
 """
 import numpy as np
 import pytest
@@ -86,6 +87,49 @@ def test_small_batch_is_deterministic(R):
             sysobj.explore(x, 30, cv_out=cv, x_out=xo)
         runs.append((xo, cv))
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+
+
+SPLIT_CASES = [
+    (200, 18, 12, 4, 4, 300, True, 11),    # the paper's network: 3 tiles
+    (60, 9, 16, 3, 3, 160, False, 12),     # 2 tiles, 16 walkers
+    (120, 20, 5, 2, 2, 512, True, 13),     # 4 tiles, ragged walkers
+    (80, 64, 1, 2, 3, 416, False, 14),     # 4 tiles (the last ragged), 128 inputs, one walker
+]
+
+
+@pytest.mark.parametrize("n,C,W,M,L,H,resnet,seed", SPLIT_CASES)
+def test_tile_split_gives_identical_bits(R, orc, n, C, W, M, L, H, resnet, seed):
+    """The 128-output tiles split over 1, 2, up to 4 CTAs of a cluster: every
+    split accumulates each tile by the same MMAs and adds the member value in
+    the same order, so forces, member gradients, values and a short
+    trajectory are the same bits; the default splits one CTA per tile."""
+    sp = I.make_system(n, C, seed)
+    x = I.make_chains(W, sp, seed)
+    ens = I.make_ensemble(M, 2 * C, L, H, seed, resnet=resnet, trust_lo=1e9, trust_hi=2e9)
+    tiles = -(-max(H, -(-2 * C // 64) * 64) // 128)
+    outs = {}
+    for cs in (1, 2, 4, 0):
+        f = np.zeros((W, n, 3), np.float32)
+        eps = np.zeros(W, np.float32)
+        abar = np.zeros(W, np.float32)
+        g = np.zeros((M, W, C), np.float32)
+        with R.System(sp) as sysobj:
+            sysobj.set_ensemble(ens, precision=R.RID_PREC_BF16)
+            sysobj.set_mlp_cluster(cs)
+            sysobj.eval_forces(x, R.RID_BIAS_ENSEMBLE, f_out=f, eps_out=eps, abar_out=abar, grad_out=g)
+            assert sysobj.mlp_cluster() == (min(cs, tiles) if cs else tiles), cs
+            xo = np.zeros_like(x)
+            sysobj.explore(x, 8, x_out=xo)
+        outs[cs] = (f, eps, abar, g, xo)
+    for cs in (2, 4, 0):
+        for a, b in zip(outs[cs], outs[1]):
+            assert np.array_equal(a, b), cs
+    f, eps, abar, g, _ = outs[0]
+    assert np.all(np.isfinite(g)) and np.all(np.isfinite(outs[0][4]))
+    for w in sorted({0, W - 1}):
+        e = orc.ensemble(ens, orc.cvs(sp, x[w].astype(np.float64))[0])
+        assert normwise(g[:, w].mean(axis=0), e["gradA"].mean(axis=0)) < GRAD_TOL, w
+        assert abs(abar[w] - e["Abar"]) <= GRAD_TOL * (abs(e["Abar"]) + 0.1), w
 
 
 @pytest.mark.parametrize("W", [1, 12, 16])
