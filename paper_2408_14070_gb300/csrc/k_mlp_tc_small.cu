@@ -6,7 +6,7 @@
 // epilogue turns a 128 x N accumulator into the next operand for every GEMM.
 // Here each GEMM is computed as D^T = Wt . Act^T: the GEMM's outputs (neurons,
 // or inputs in the backward pass) fill the MMA's M = 128 rows and the walkers,
-// padded to NW = 16, 32 or 64, are its N columns.  The A operand is the same
+// padded to NW = 16, are its N columns.  The A operand is the same
 // pre-swizzled weight image the other variants stream as their B operand --
 // for GEMM g and 128-byte K-chunk c its rows are the GEMM's outputs, K-major
 // -- so the same tensor maps load it, one 128-row M-tile per stage.  The B
@@ -20,19 +20,26 @@
 // whole 64-column atoms, one contiguous block of NW x 256 bytes.  The
 // epilogue writes them into this CTA's operand buffer and a copy warp sends
 // the block to every peer that owns tiles of the next GEMM with one bulk
-// shared-to-shared copy, completing on the peer's operand barrier (its MMA
-// warp raises the barrier's expected bytes by what the peers send).  The
-// operand is double buffered (GEMM g reads buffer g mod 2), so a copy for
+// shared-to-shared copy, completing on the peer's barrier of received bytes
+// (its MMA warp raises the barrier's expected bytes by what the peers send).
+// The operand is double buffered (GEMM g reads buffer g mod 2), so a copy for
 // GEMM g + 1 never lands in a buffer a peer's GEMM g still reads.  A tcgen05
-// .mma costs about 90 ns whatever its N (measured), so the split divides the
-// chain's MMA time by CS.  Every M-tile is accumulated by the same sequence of
-// MMAs whichever CTA owns it, and the member value is added in a fixed order
-// on rank 0, so every cluster size gives the same bits.
+// .mma costs about 90-115 ns whatever its N (measured), so the split divides
+// the chain's MMA time by CS.
+//
+// Every tile accumulates its K-chunks in order; a CTA waits for the received
+// bytes only before its first chunk from a peer (rank 0 starts on its own).
+// Every M-tile is accumulated by the same sequence of MMAs whichever CTA owns
+// it, and the member value is added in a fixed order on rank 0, so every
+// cluster size gives the same bits.  Measured and not kept: starting each
+// tile on the chunks its own CTA wrote (a rotated K order: every MMA became
+// slower, 42 -> 49 us for the paper's network at 12 walkers), and even and odd
+// K-steps in two accumulators added in the epilogue (slower too).
 //
 // TMEM: accumulator b of GEMM g holds local tile j in columns b * acc_cols +
 // j * NW .. + NW - 1; lane r of tile mt is output 128 mt + r.  Epilogue warp w
-// (w = 2..17) owns lane quarter w mod 4; its work items are (local tile,
-// group of 4 walkers), taken in turn by the quarter's four warps.  Per element
+// (w = 2..17) owns lane quarter w mod 4 and the 4-walker group (w - 2) / 4 of
+// every local tile.  Per element
 // the arithmetic is that of k_mlp_tc (bias, BF16 tanh, saved tanh in BF16, the
 // FP32 residual stream, Delta = g (1 - t^2)); the member value A = w_out . h_L
 // + b_out is reduced per (M-tile, lane quarter) by a warp butterfly and the
@@ -64,23 +71,26 @@ constexpr int SM_GRP = 4;                      // walkers per epilogue work item
 constexpr int SM_COPY_WARP = EPI_WARP0 + EPI_WARPS;
 constexpr int SM_THREADS = 32 * (SM_COPY_WARP + 1);
 
+constexpr int NW = 16;                         // MMA columns: walkers padded to 16
+
 struct SmemS {
     uint64_t full[TC_MAX_STAGES];
     uint64_t empty[TC_MAX_STAGES];
     uint64_t acc_full[2];
     uint64_t acc_empty[2];
-    uint64_t b_ready[2];      // operand buffer b complete: 16 epilogue warps + the MMA warp's expect-tx
-                              // arrival, and the peers' bytes
-    uint64_t slice_done[2];   // this CTA's tiles of the operand in buffer b written: 16 epilogue warps
+    uint64_t b_local[2];      // this CTA's chunks of operand buffer b written: 16 epilogue warps
+    uint64_t b_peer[2];       // the peers' chunks of buffer b received: the MMA warp's expect-tx arrival
+                              // and the peers' bytes
+    uint64_t slice_done[2];   // this CTA's chunks of the operand in buffer b written: 16 epilogue warps
     uint64_t drain;
     uint32_t tmem_base;
     int abort_flag;
 };
 
 // Byte offset of (walker row r, column col) in the activation operand: atoms
-// of 64 BF16 columns x NW rows x 128 bytes, 16-byte chunk j of row r at
+// of 64 BF16 columns x 16 rows x 128 bytes, 16-byte chunk j of row r at
 // position j ^ (r mod 8).
-__device__ __forceinline__ uint32_t bs_off(int NW, int r, int col) {
+__device__ __forceinline__ uint32_t bs_off(int r, int col) {
     const int atom = col >> 6, ch = (col >> 3) & 7;
     return (uint32_t)atom * (uint32_t)(NW * 128) + (uint32_t)r * 128u + (uint32_t)((ch ^ (r & 7)) << 4) +
            (uint32_t)((col & 7) * 2);
@@ -88,20 +98,14 @@ __device__ __forceinline__ uint32_t bs_off(int NW, int r, int col) {
 __device__ __forceinline__ void st_bf16(unsigned char* B, uint32_t off, float v) {
     *reinterpret_cast<__nv_bfloat16*>(B + off) = __float2bfloat16_rn(v);
 }
-// Residual stream: row `row` (a local output), 4-walker chunk cg, as a float4
-// index.  A 128-byte line holds 8 chunks; the chunk is XOR-ed with the row's
-// position among the rows that share a bank pattern.
-__device__ __forceinline__ int rs_idx(int NW, int row, int cg) {
-    const int cpr = NW / SM_GRP;                          // chunks per row: 4, 8, 16
-    const int sw = NW == 16 ? (row >> 1) & 3 : row & 7;
-    return row * cpr + (cg ^ sw);
-}
-// Saved tanh: layer l, row, 4-walker chunk cg (8 bytes), as a uint2 index.
-// A 128-byte line holds 16 chunks.
-__device__ __forceinline__ int ts_idx(int NW, int rows, int l, int row, int cg) {
-    const int cpr = NW / SM_GRP;
-    const int sw = NW == 16 ? (row >> 2) & 3 : NW == 32 ? (row >> 1) & 7 : row & 15;
-    return (l * rows + row) * cpr + (cg ^ sw);
+// Residual stream: local output row, 4-walker chunk cg, as a float4 index.
+// Two rows share a 128-byte line (8 chunks); the chunk is XOR-ed with the
+// row's pair index so that 8 consecutive rows hit 8 distinct chunk slots.
+__device__ __forceinline__ int rs_idx(int row, int cg) { return row * 4 + (cg ^ ((row >> 1) & 3)); }
+// Saved tanh: layer l, local row, 4-walker chunk cg (8 bytes), as a uint2
+// index.  Four rows share a 128-byte line (16 slots of 8 bytes).
+__device__ __forceinline__ int ts_idx(int rows, int l, int row, int cg) {
+    return (l * rows + row) * 4 + (cg ^ ((row >> 2) & 3));
 }
 // 32 lanes x 4 columns of TMEM
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
@@ -120,7 +124,7 @@ __device__ __forceinline__ void tile_atoms(int mt, int kpn, int& a0, int& a1) {
     a1 = 2 * mt + 2 < kpn / 64 ? 2 * mt + 2 : kpn / 64;
 }
 // Bytes of GEMM g's operand (g >= 1) that CTA `rank` receives from its peers
-__device__ __forceinline__ uint32_t peer_bytes(const TcArgs& P, int g, int rank, int CS, int NW) {
+__device__ __forceinline__ uint32_t peer_bytes(const TcArgs& P, int g, int rank, int CS) {
     const int kp = P.gKp[g], nmp = (P.gN[g - 1] + 127) / 128;
     int own = 0;
     for (int mt = rank; mt < nmp; mt += CS) {
@@ -130,12 +134,15 @@ __device__ __forceinline__ uint32_t peer_bytes(const TcArgs& P, int g, int rank,
     }
     return (uint32_t)(kp / 64 - own) * (uint32_t)NW * 128u;
 }
+// Is K-chunk c of GEMM g's operand (g >= 1) written by this CTA?  Chunk c
+// comes from tile c / 2 of GEMM g - 1.
+__device__ __forceinline__ bool own_chunk(int c, int rank, int CS) { return (c >> 1) % CS == rank; }
 
-
+// 608 threads x 96 registers (a launch with 104 asks for too many)
 template <bool RES>
 __global__ void __maxnreg__(96)
     k_mlp_tc_small(const __grid_constant__ TcArgs P, const __grid_constant__ CUtensorMap map_big,
-                   const __grid_constant__ CUtensorMap map_small, int NW) {
+                   const __grid_constant__ CUtensorMap map_small) {
     extern __shared__ __align__(1024) unsigned char dsm_raw[];
     unsigned char* dsm =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
@@ -148,17 +155,16 @@ __global__ void __maxnreg__(96)
     int nmx = 1;
     for (int g = 0; g < G; ++g) nmx = max(nmx, (P.gN[g] + 127) / 128);
     const int rows = owned_tiles(nmx, 0, CS) * 128;                        // local output rows (rank 0 owns most)
-    const int ngrp = NW / SM_GRP;
     const size_t bbytes = (size_t)P.Kpmax * 2u * (size_t)NW;
-    // operand buffers 0 and 1, [Kp/64][NW rows][128 B] each
+    // operand buffers 0 and 1, [Kp/64][16 rows][128 B] each
     auto Bbuf = [&](int i) -> unsigned char* { return dsm + (size_t)i * bbytes; };
     unsigned char* stages = dsm + 2 * bbytes;                               // [NS][128 rows][128 B]
     const uint32_t stage_bytes = 128u * 128u;
     const int NS = P.stages;
     const int NACC = P.nacc;
-    uint2* tsv = reinterpret_cast<uint2*>(stages + (size_t)NS * stage_bytes);             // [L][rows][NW/4]
-    float4* rsv = reinterpret_cast<float4*>(tsv + (size_t)L * rows * ngrp);               // [rows][NW/4] (RES)
-    float* sbias = reinterpret_cast<float*>(rsv + (RES ? (size_t)rows * ngrp : 0));       // [L][H]
+    uint2* tsv = reinterpret_cast<uint2*>(stages + (size_t)NS * stage_bytes);             // [L][rows][4]
+    float4* rsv = reinterpret_cast<float4*>(tsv + (size_t)L * rows * 4);                  // [rows][4] (RES)
+    float* sbias = reinterpret_cast<float*>(rsv + (RES ? (size_t)rows * 4 : 0));          // [L][H]
     float* swout = sbias + (size_t)L * H;                                                  // [H]
     float* spart = swout + H;                                                              // [SM_MT * 4][NW]
     volatile int* abort_flag = &S.abort_flag;
@@ -171,7 +177,8 @@ __global__ void __maxnreg__(96)
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&S.acc_full[b]), 1);
             mbar_init(smem_u32(&S.acc_empty[b]), EPI_WARPS);
-            mbar_init(smem_u32(&S.b_ready[b]), EPI_WARPS + 1);
+            mbar_init(smem_u32(&S.b_local[b]), EPI_WARPS);
+            mbar_init(smem_u32(&S.b_peer[b]), 1);
             mbar_init(smem_u32(&S.slice_done[b]), EPI_WARPS);
         }
         mbar_init(smem_u32(&S.drain), 1);
@@ -228,7 +235,7 @@ __global__ void __maxnreg__(96)
             }
         }
     } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer: M = 128 outputs, N = NW walkers
+        // ------------------------------------------------------------ MMA issuer: M = 128 outputs, N = 16 walkers
         if (lane == 0) {
             int it = 0;
             bool ok = true;
@@ -243,17 +250,27 @@ __global__ void __maxnreg__(96)
                     ok = false;
                     break;
                 }
-                // the operand of GEMM g: the prologue (g = 0) or GEMM g-1's epilogues, this CTA's
-                // tiles written locally, the peers' tiles arriving as bytes
-                const uint32_t pb = (g > 0 && rank < nm) ? peer_bytes(P, g, rank, CS, NW) : 0u;
-                mbar_arrive_expect_tx(smem_u32(&S.b_ready[g & 1]), pb);
-                if (!mbar_wait_cluster(smem_u32(&S.b_ready[g & 1]), (g >> 1) & 1, abort_flag, P.err, 4)) {
+                // the operand of GEMM g: the prologue (g = 0) or GEMM g-1's epilogues; this CTA's
+                // chunks written locally, the peers' chunks arriving as bytes on b_peer
+                const uint32_t pb = (g > 0 && rank < nm) ? peer_bytes(P, g, rank, CS) : 0u;
+                mbar_arrive_expect_tx(smem_u32(&S.b_peer[g & 1]), pb);
+                if (!mbar_wait(smem_u32(&S.b_local[g & 1]), (g >> 1) & 1, abort_flag, P.err, 4)) {
                     ok = false;
                     break;
                 }
                 fence_after();
+                bool have_peer = false;
+                const uint32_t bbase = smem_u32(Bbuf(g & 1));
                 for (int c = 0; c < nch && ok; ++c) {
-                    const uint32_t b_atom = smem_u32(Bbuf(g & 1)) + (uint32_t)(c * NW * 128);
+                    if (!have_peer && g > 0 && !own_chunk(c, rank, CS)) {
+                        if (!mbar_wait_cluster(smem_u32(&S.b_peer[g & 1]), (g >> 1) & 1, abort_flag, P.err, 4)) {
+                            ok = false;
+                            break;
+                        }
+                        have_peer = true;
+                        fence_after();
+                    }
+                    const uint32_t b_atom = bbase + (uint32_t)(c * NW * 128);
                     for (int j = 0; j < nj; ++j, ++it) {
                         const int s = it % NS;
                         if (!mbar_wait(smem_u32(&S.full[s]), (it / NS) & 1, abort_flag, P.err, 4)) {
@@ -269,6 +286,10 @@ __global__ void __maxnreg__(96)
                         mma_commit(smem_u32(&S.empty[s]));
                     }
                 }
+                // every phase of b_peer is waited on, so that no peer's copy is still landing at exit
+                if (ok && !have_peer &&
+                    !mbar_wait_cluster(smem_u32(&S.b_peer[g & 1]), (g >> 1) & 1, abort_flag, P.err, 4))
+                    ok = false;
                 if (ok) mma_commit(smem_u32(&S.acc_full[b]));
             }
             mma_commit(smem_u32(&S.drain));
@@ -290,7 +311,7 @@ __global__ void __maxnreg__(96)
                     const uint32_t bytes = (uint32_t)(a1 - a0) * (uint32_t)NW * 128u;
                     const uint32_t src = smem_u32(Bbuf((g + 1) & 1)) + (uint32_t)a0 * (uint32_t)NW * 128u;
                     for (int q = 0; q < nq; ++q)
-                        if (q != rank) bulk_copy_to_peer(src, bytes, smem_u32(&S.b_ready[(g + 1) & 1]), (uint32_t)q);
+                        if (q != rank) bulk_copy_to_peer(src, bytes, smem_u32(&S.b_peer[(g + 1) & 1]), (uint32_t)q);
                 }
                 bulk_commit_and_wait_read();
             }
@@ -299,9 +320,10 @@ __global__ void __maxnreg__(96)
         // ------------------------------------------------------------ epilogue
         const int e = warp - EPI_WARP0;          // 0..15
         const int quarter = warp & 3;            // TMEM lane quarter this warp may access
-        const int sub = e >> 2;                  // this warp's turn among the quarter's four
+        const int cg = e >> 2;                   // this warp's 4-walker group
         const int ET = 32 * EPI_WARPS;
         const int W = P.W;
+        const int q32 = quarter * 32 + lane;     // the row within a tile this thread holds
         // GEMM 0 operand: u (FP32, [W][D]) -> [walker][K] BF16, zeros past D and for walkers >= W
         {
             const int kp0 = P.gKp[0];
@@ -313,11 +335,11 @@ __global__ void __maxnreg__(96)
                     const int k = col + i;
                     v[i] = (w < W && k < P.D) ? __ldg(P.u + (size_t)w * P.D + k) : 0.0f;
                 }
-                *reinterpret_cast<uint4*>(Bbuf(0) + bs_off(NW, w, col)) = pack8(v);
+                *reinterpret_cast<uint4*>(Bbuf(0) + bs_off(w, col)) = pack8(v);
             }
             fence_async_smem();
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&S.b_ready[0]));
+            if (lane == 0) mbar_arrive(smem_u32(&S.b_local[0]));
         }
         for (int idx = e * 32 + lane; idx < (L + 1) * H; idx += ET) {
             const int l = idx / H, c = idx - l * H;
@@ -338,34 +360,27 @@ __global__ void __maxnreg__(96)
             unsigned char* Bn = Bbuf((g + 1) & 1);
             if (!mbar_wait(smem_u32(&S.acc_full[b]), (g / NACC) & 1, abort_flag, P.err, 8)) break;
             fence_after();
-            const int items = nj * ngrp;
-            const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * P.acc_cols);
-            for (int base = sub; base < items; base += 16) {
-                // up to four items (base, base + 4, ...) loaded before one wait
-                float a[4][4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int itm = base + 4 * k;
-                    if (itm < items) {
-                        const int j = itm / ngrp, cg = itm - (itm / ngrp) * ngrp;
-                        tmem_ld4(tq + (uint32_t)(j * NW + cg * SM_GRP), a[k]);
-                    }
-                }
+            // this warp's 4 walkers of the local tiles, two tiles loaded before each wait
+            const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * P.acc_cols + cg * SM_GRP);
+#pragma unroll 1
+            for (int j0 = 0; j0 < nj; j0 += 2) {
+                float a[2][SM_GRP];
+                tmem_ld4(tq + (uint32_t)(j0 * NW), a[0]);
+                if (j0 + 1 < nj) tmem_ld4(tq + (uint32_t)((j0 + 1) * NW), a[1]);
                 tmem_wait_ld();
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int itm = base + 4 * k;
-                    if (itm >= items) break;
-                    const int j = itm / ngrp, cg = itm - (itm / ngrp) * ngrp;
+                for (int jj = 0; jj < 2; ++jj) {
+                    const int j = j0 + jj;
+                    if (j >= nj) break;
                     const int mt = rank + j * CS;
-                    const int row = j * 128 + quarter * 32 + lane;   // local output row
-                    const int n = mt * 128 + quarter * 32 + lane;    // the output this thread holds
+                    const int row = j * 128 + q32;          // local output row
+                    const int n = mt * 128 + q32;           // the output this thread holds
                     const bool vn = n < N;
                     const float bn = (fwd && vn) ? sbias[l * H + n] : 0.0f;
                     const float wo = vn && n < H ? swout[n] : 0.0f;
                     float rp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                     if (RES && vn && res_ld) {
-                        const float4 v = rsv[rs_idx(NW, row, cg)];
+                        const float4 v = rsv[rs_idx(row, cg)];
                         rp[0] = v.x;
                         rp[1] = v.y;
                         rp[2] = v.z;
@@ -376,8 +391,8 @@ __global__ void __maxnreg__(96)
                     float rs[4];     // residual stream values to store
                     if (fwd) {
                         // t = tanh(z) in BF16, elementwise on pairs of walkers
-                        const uint32_t y01 = tanh_bf16x2(a[k][0] + bn, a[k][1] + bn);
-                        const uint32_t y23 = tanh_bf16x2(a[k][2] + bn, a[k][3] + bn);
+                        const uint32_t y01 = tanh_bf16x2(a[jj][0] + bn, a[jj][1] + bn);
+                        const uint32_t y23 = tanh_bf16x2(a[jj][2] + bn, a[jj][3] + bn);
                         const float t[4] = {__uint_as_float(y01 << 16), __uint_as_float(y01 & 0xffff0000u),
                                             __uint_as_float(y23 << 16), __uint_as_float(y23 & 0xffff0000u)};
 #pragma unroll
@@ -388,15 +403,15 @@ __global__ void __maxnreg__(96)
                             part[i] = vn ? wo * h : 0.0f;
                             out[i] = l == L - 1 ? wo * (1.0f - t[i] * t[i]) : h;
                         }
-                        if (vn) tsv[ts_idx(NW, rows, l, row, cg)] = make_uint2(y01, y23);
+                        if (vn) tsv[ts_idx(rows, l, row, cg)] = make_uint2(y01, y23);
                     } else if (l > 0) {
                         // G_{l-1} (+ dA/dh_l) -> Delta_{l-1} = G (1 - t_{l-1}^2)
-                        const uint2 tw = vn ? tsv[ts_idx(NW, rows, l - 1, row, cg)] : make_uint2(0u, 0u);
+                        const uint2 tw = vn ? tsv[ts_idx(rows, l - 1, row, cg)] : make_uint2(0u, 0u);
                         const float t[4] = {__uint_as_float(tw.x << 16), __uint_as_float(tw.x & 0xffff0000u),
                                             __uint_as_float(tw.y << 16), __uint_as_float(tw.y & 0xffff0000u)};
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            float gv = a[k][i];
+                            float gv = a[jj][i];
                             if (RES && res_bwd && vn) gv = (l == L - 1 ? wo : rp[i]) + gv;
                             rs[i] = gv;
                             out[i] = gv * (1.0f - t[i] * t[i]);
@@ -407,23 +422,27 @@ __global__ void __maxnreg__(96)
                         // (torsion), g[2j] (distance); the pair's odd element comes from the next lane
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            const float g1 = __shfl_down_sync(0xffffffffu, a[k][i], 1);
+                            const float g1 = __shfl_down_sync(0xffffffffu, a[jj][i], 1);
                             const int w = cg * SM_GRP + i, jc = n >> 1;
                             if (!(n & 1) && 2 * jc < P.D && w < W && !*abort_flag) {
                                 const float cs = __ldg(P.u + (size_t)w * P.D + 2 * jc);
                                 const float sn = __ldg(P.u + (size_t)w * P.D + 2 * jc + 1);
                                 const bool dist = P.cvdist && __ldg(P.cvdist + jc);
-                                P.gradA[((size_t)m * W + w) * P.C + jc] = dist ? a[k][i] : -sn * a[k][i] + cs * g1;
+                                P.gradA[((size_t)m * W + w) * P.C + jc] = dist ? a[jj][i] : -sn * a[jj][i] + cs * g1;
                             }
                             out[i] = 0.0f;
                             part[i] = 0.0f;
                             rs[i] = 0.0f;
                         }
                     }
-                    if (RES && res_st && vn) rsv[rs_idx(NW, row, cg)] = make_float4(rs[0], rs[1], rs[2], rs[3]);
+                    if (RES && res_st && vn) rsv[rs_idx(row, cg)] = make_float4(rs[0], rs[1], rs[2], rs[3]);
                     if (g < G - 1 && n < kpn) {
+                        const int ch = (n >> 3) & 7;
+                        const uint32_t cb = (uint32_t)(n >> 6) * (uint32_t)(NW * 128) + (uint32_t)((n & 7) * 2);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) st_bf16(Bn, bs_off(NW, cg * SM_GRP + i, n), vn ? out[i] : 0.0f);
+                        for (int i = 0; i < 4; ++i)
+                            st_bf16(Bn, cb + (uint32_t)(cg * SM_GRP + i) * 128u + (uint32_t)((ch ^ ((cg * SM_GRP + i) & 7)) << 4),
+                                    vn ? out[i] : 0.0f);
                     }
                     if (fwd && l == L - 1) {
                         // member value: this warp's 32 outputs, butterfly over the lanes, into rank 0
@@ -442,7 +461,7 @@ __global__ void __maxnreg__(96)
                 fence_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive(smem_u32(&S.b_ready[(g + 1) & 1]));
+                    mbar_arrive(smem_u32(&S.b_local[(g + 1) & 1]));
                     if (CS > 1) mbar_arrive(smem_u32(&S.slice_done[g & 1]));
                 }
             }
@@ -476,18 +495,18 @@ __global__ void __maxnreg__(96)
 
 // Shared memory of the small-batch kernel at P.csize CTAs per member and
 // P.stages weight stages (0: the fixed part alone).
-size_t rid_mlp_tc_small_smem_bytes(const TcArgs& P, int NW) {
+size_t rid_mlp_tc_small_smem_bytes(const TcArgs& P, int nw) {
     int nmx = 1;
     for (int g = 0; g < 2 * P.L; ++g) nmx = std::max(nmx, (P.gN[g] + 127) / 128);
     const int CS = P.csize < 1 ? 1 : P.csize;
     const size_t rows = (size_t)((nmx + CS - 1) / CS) * 128;
-    return 1024 + 2 * (size_t)P.Kpmax * 2u * NW + (size_t)P.stages * 128u * 128u + (size_t)P.L * rows * NW * 2u +
-           (P.resnet ? rows * NW * 4u : 0) + sizeof(float) * ((size_t)(P.L + 1) * P.H + (size_t)SM_MT * 4 * NW);
+    return 1024 + 2 * (size_t)P.Kpmax * 2u * nw + (size_t)P.stages * 128u * 128u + (size_t)P.L * rows * nw * 2u +
+           (P.resnet ? rows * nw * 4u : 0) + sizeof(float) * ((size_t)(P.L + 1) * P.H + (size_t)SM_MT * 4 * nw);
 }
 
-cudaError_t rid_launch_mlp_tc_small(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, int NW,
+cudaError_t rid_launch_mlp_tc_small(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, int nw,
                                     cudaStream_t s) {
-    if (P.ngemm != 2 * P.L || P.W > NW || (NW != 16 && NW != 32 && NW != 64)) return cudaErrorInvalidValue;
+    if (P.ngemm != 2 * P.L || P.W > NW || nw != NW) return cudaErrorInvalidValue;
     if (P.csize < 1 || P.csize > SM_MT || P.stages < 2 || P.stages > TC_MAX_STAGES) return cudaErrorInvalidValue;
     if (P.geb[0] != 2) return cudaErrorInvalidValue;   // BF16 only
     for (int g = 0; g < 2 * P.L; ++g)
@@ -516,5 +535,5 @@ cudaError_t rid_launch_mlp_tc_small(const TcArgs& P, const CUtensorMap& big, con
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, P, big, small, NW);
+    return cudaLaunchKernelEx(&cfg, kern, P, big, small);
 }

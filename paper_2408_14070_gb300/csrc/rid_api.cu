@@ -519,7 +519,8 @@ static int build_tc_variant(rid_system* sys, const std::vector<float>& W, long l
             while (V.s_tmem_cols[k][cs] < V.s_nacc[k][cs] * acc) V.s_tmem_cols[k][cs] *= 2;
             V.s_stages[k][cs] =
                 fixs + 2 * 16384 <= budget ? (int)std::min<size_t>((budget - fixs) / 16384, TC_MAX_STAGES) : 0;
-            V.s_ok[k][cs] = !fp8 && nmx <= 4 && cs <= nmx && acc <= 512 && V.s_stages[k][cs] >= 2;
+            // (the kernel is built for 16 MMA columns only)
+            V.s_ok[k][cs] = k == 0 && !fp8 && nmx <= 4 && cs <= nmx && acc <= 512 && V.s_stages[k][cs] >= 2;
         }
     V.cs_W = -1;
     V.csize = 1;

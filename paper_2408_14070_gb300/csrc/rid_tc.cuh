@@ -48,9 +48,10 @@ size_t rid_mlp_tc_smem_bytes(const TcArgs& P);
 cudaError_t rid_launch_mlp_tc(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, cudaStream_t s);
 size_t rid_mlp_tc_wide_smem_bytes(const TcArgs& P);
 cudaError_t rid_launch_mlp_tc_wide(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, cudaStream_t s);
-// Small walker counts (NW = 16, 32 or 64 MMA columns; the host uses 16), BF16,
-// forward and input gradient: one CTA per member, the GEMMs transposed
-// (outputs on the MMA's M = 128 rows, walkers on its N columns).
+// Small walker counts (up to 16: NW = 16 MMA columns), BF16, forward and
+// input gradient: the GEMMs transposed (outputs on the MMA's M = 128 rows,
+// walkers on its N columns), each GEMM's 128-output tiles split over a cluster
+// of P.csize (1..4) CTAs per member.
 size_t rid_mlp_tc_small_smem_bytes(const TcArgs& P, int NW);
 cudaError_t rid_launch_mlp_tc_small(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, int NW,
                                     cudaStream_t s);
