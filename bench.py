@@ -766,7 +766,9 @@ def run_paper_network(rid, torch, steps, seed=21):
             with rid.System(sp) as system:
                 system.set_ensemble(ens, precision=prec)
                 x12 = xd[:12].contiguous()
-                ms12, _ = _timed_steps(torch, system, x12, stream, steps, flush)
+                ms12, kern12 = _timed_steps(torch, system, x12, stream, steps, flush)
+                res["bf16_12_walkers"] = {"ms_per_step": ms12 / steps, "kernels_ms": kern12,
+                                          "mlp_kernel": mlp_kernel_desc(system, 12)}
             res["bf16_12_walkers_ms_per_step"] = ms12 / steps
     for name in ("bf16", "fp8"):
         d = (grads[name] - grads["fp32"]).norm(dim=1) / grads["fp32"].norm(dim=1).clamp_min(1e-30)
@@ -775,11 +777,14 @@ def run_paper_network(rid, torch, steps, seed=21):
     return res
 
 
-def mlp_kernel_desc(system):
-    """The tensor-core ensemble kernel variant of the system's last launch."""
+def mlp_kernel_desc(system, walkers=None, bf16=True):
+    """The tensor-core ensemble kernel variant of the system's last launch
+    (BF16 ensembles at up to 16 walkers run the small-batch kernel)."""
     cs = system.mlp_cluster()
     if cs == 0:
         return "FP32 SIMT (k_mlp_fp32)"
+    if walkers is not None and walkers <= 16 and bf16:
+        return f"k_mlp_tc_small: GEMMs transposed, 128-output tiles over clusters of {cs} CTAs per member"
     if cs == 1:
         return "k_mlp_tc: one CTA per 128-walker tile and member"
     return f"k_mlp_tc_cluster: clusters of {cs} CTAs per 128-walker tile and member"
