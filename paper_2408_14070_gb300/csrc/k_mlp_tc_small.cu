@@ -38,7 +38,7 @@
 //
 // TMEM: accumulator b of GEMM g holds local tile j in columns b * acc_cols +
 // j * NW .. + NW - 1; lane r of tile mt is output 128 mt + r.  Epilogue warp w
-// (w = 2..17) owns lane quarter w mod 4 and the 4-walker group (w - 2) / 4 of
+// owns lane quarter w mod 4 and the 4-walker groups (w - 2) / 4 (+ E / 4) of
 // every local tile.  Per element
 // the arithmetic is that of k_mlp_tc (bias, BF16 tanh, saved tanh in BF16, the
 // FP32 residual stream, Delta = g (1 - t^2)); the member value A = w_out . h_L
@@ -56,7 +56,10 @@
 // row, so that a warp's 32 consecutive rows hit distinct banks.
 //
 // Warp roles: warp 0 TMA producer, warp 1 TMEM allocator and MMA issuer,
-// warps 2..17 epilogue, warp 18 bulk copies of the exchange.  Every wait is
+// warps 2..2+E-1 epilogue (E = 16, or 8 in the lean variant, whose warps each
+// take two 4-walker groups: 352 threads instead of 608, so that with few
+// weight stages a CTA can share an SM with other kernels' CTAs), warp 2+E bulk
+// copies of the exchange.  Every wait is
 // bounded in time; a CTA whose wait expires sets the error word and stops
 // issuing, its peers' waits then expire too, and every CTA still meets the
 // final cluster barrier, so no CTA exits while another may write into it.
@@ -68,8 +71,8 @@ namespace {
 
 constexpr int SM_MT = 4;                       // M-tiles per GEMM (outputs up to 512)
 constexpr int SM_GRP = 4;                      // walkers per epilogue work item
-constexpr int SM_COPY_WARP = EPI_WARP0 + EPI_WARPS;
-constexpr int SM_THREADS = 32 * (SM_COPY_WARP + 1);
+// threads of a CTA with `epi` epilogue warps (16, or 8 for the lean variant)
+constexpr int sm_threads(int epi) { return 32 * (EPI_WARP0 + epi + 1); }
 
 constexpr int NW = 16;                         // MMA columns: walkers padded to 16
 
@@ -138,8 +141,8 @@ __device__ __forceinline__ uint32_t peer_bytes(const TcArgs& P, int g, int rank,
 // comes from tile c / 2 of GEMM g - 1.
 __device__ __forceinline__ bool own_chunk(int c, int rank, int CS) { return (c >> 1) % CS == rank; }
 
-// 608 threads x 96 registers (a launch with 104 asks for too many)
-template <bool RES>
+// 608 threads x 96 registers at 16 epilogue warps (a launch with 104 asks for too many)
+template <bool RES, int EPI>
 __global__ void __maxnreg__(96)
     k_mlp_tc_small(const __grid_constant__ TcArgs P, const __grid_constant__ CUtensorMap map_big,
                    const __grid_constant__ CUtensorMap map_small) {
@@ -176,10 +179,10 @@ __global__ void __maxnreg__(96)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&S.acc_full[b]), 1);
-            mbar_init(smem_u32(&S.acc_empty[b]), EPI_WARPS);
-            mbar_init(smem_u32(&S.b_local[b]), EPI_WARPS);
+            mbar_init(smem_u32(&S.acc_empty[b]), EPI);
+            mbar_init(smem_u32(&S.b_local[b]), EPI);
             mbar_init(smem_u32(&S.b_peer[b]), 1);
-            mbar_init(smem_u32(&S.slice_done[b]), EPI_WARPS);
+            mbar_init(smem_u32(&S.slice_done[b]), EPI);
         }
         mbar_init(smem_u32(&S.drain), 1);
         S.abort_flag = 0;
@@ -296,7 +299,7 @@ __global__ void __maxnreg__(96)
             const unsigned long long t0 = gtimer();
             while (!mbar_try(smem_u32(&S.drain), 0) && gtimer() - t0 < WAIT_NS) {}
         }
-    } else if (warp == SM_COPY_WARP) {
+    } else if (warp == EPI_WARP0 + EPI) {
         // ------------------------------------------------------------ bulk exchange
         if (lane == 0 && CS > 1) {
             for (int g = 0; g + 1 < G; ++g) {
@@ -318,10 +321,10 @@ __global__ void __maxnreg__(96)
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int e = warp - EPI_WARP0;          // 0..15
+        const int e = warp - EPI_WARP0;          // 0..EPI-1
         const int quarter = warp & 3;            // TMEM lane quarter this warp may access
-        const int cg = e >> 2;                   // this warp's 4-walker group
-        const int ET = 32 * EPI_WARPS;
+        const int sub = e >> 2;                  // this warp's first 4-walker group
+        const int ET = 32 * EPI;
         const int W = P.W;
         const int q32 = quarter * 32 + lane;     // the row within a tile this thread holds
         // GEMM 0 operand: u (FP32, [W][D]) -> [walker][K] BF16, zeros past D and for walkers >= W
@@ -361,98 +364,102 @@ __global__ void __maxnreg__(96)
             if (!mbar_wait(smem_u32(&S.acc_full[b]), (g / NACC) & 1, abort_flag, P.err, 8)) break;
             fence_after();
             // this warp's 4 walkers of the local tiles, two tiles loaded before each wait
-            const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * P.acc_cols + cg * SM_GRP);
+            // the warp's 4-walker groups cg = sub, sub + EPI / 4, ...
 #pragma unroll 1
-            for (int j0 = 0; j0 < nj; j0 += 2) {
-                float a[2][SM_GRP];
-                tmem_ld4(tq + (uint32_t)(j0 * NW), a[0]);
-                if (j0 + 1 < nj) tmem_ld4(tq + (uint32_t)((j0 + 1) * NW), a[1]);
-                tmem_wait_ld();
+            for (int cg = sub; cg < NW / SM_GRP; cg += EPI / 4) {
+                const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * P.acc_cols + cg * SM_GRP);
+#pragma unroll 1
+                for (int j0 = 0; j0 < nj; j0 += 2) {
+                    float a[2][SM_GRP];
+                    tmem_ld4(tq + (uint32_t)(j0 * NW), a[0]);
+                    if (j0 + 1 < nj) tmem_ld4(tq + (uint32_t)((j0 + 1) * NW), a[1]);
+                    tmem_wait_ld();
 #pragma unroll
-                for (int jj = 0; jj < 2; ++jj) {
-                    const int j = j0 + jj;
-                    if (j >= nj) break;
-                    const int mt = rank + j * CS;
-                    const int row = j * 128 + q32;          // local output row
-                    const int n = mt * 128 + q32;           // the output this thread holds
-                    const bool vn = n < N;
-                    const float bn = (fwd && vn) ? sbias[l * H + n] : 0.0f;
-                    const float wo = vn && n < H ? swout[n] : 0.0f;
-                    float rp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-                    if (RES && vn && res_ld) {
-                        const float4 v = rsv[rs_idx(row, cg)];
-                        rp[0] = v.x;
-                        rp[1] = v.y;
-                        rp[2] = v.z;
-                        rp[3] = v.w;
-                    }
-                    float out[4];    // this GEMM's contribution to the next operand
-                    float part[4];   // member value terms w_out[n] h_L[n][w] (last forward layer)
-                    float rs[4];     // residual stream values to store
-                    if (fwd) {
-                        // t = tanh(z) in BF16, elementwise on pairs of walkers
-                        const uint32_t y01 = tanh_bf16x2(a[jj][0] + bn, a[jj][1] + bn);
-                        const uint32_t y23 = tanh_bf16x2(a[jj][2] + bn, a[jj][3] + bn);
-                        const float t[4] = {__uint_as_float(y01 << 16), __uint_as_float(y01 & 0xffff0000u),
-                                            __uint_as_float(y23 << 16), __uint_as_float(y23 & 0xffff0000u)};
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            float h = t[i];
-                            if (RES && res_fwd && vn) h = rp[i] + t[i];
-                            rs[i] = h;
-                            part[i] = vn ? wo * h : 0.0f;
-                            out[i] = l == L - 1 ? wo * (1.0f - t[i] * t[i]) : h;
+                    for (int jj = 0; jj < 2; ++jj) {
+                        const int j = j0 + jj;
+                        if (j >= nj) break;
+                        const int mt = rank + j * CS;
+                        const int row = j * 128 + q32;          // local output row
+                        const int n = mt * 128 + q32;           // the output this thread holds
+                        const bool vn = n < N;
+                        const float bn = (fwd && vn) ? sbias[l * H + n] : 0.0f;
+                        const float wo = vn && n < H ? swout[n] : 0.0f;
+                        float rp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                        if (RES && vn && res_ld) {
+                            const float4 v = rsv[rs_idx(row, cg)];
+                            rp[0] = v.x;
+                            rp[1] = v.y;
+                            rp[2] = v.z;
+                            rp[3] = v.w;
                         }
-                        if (vn) tsv[ts_idx(rows, l, row, cg)] = make_uint2(y01, y23);
-                    } else if (l > 0) {
-                        // G_{l-1} (+ dA/dh_l) -> Delta_{l-1} = G (1 - t_{l-1}^2)
-                        const uint2 tw = vn ? tsv[ts_idx(rows, l - 1, row, cg)] : make_uint2(0u, 0u);
-                        const float t[4] = {__uint_as_float(tw.x << 16), __uint_as_float(tw.x & 0xffff0000u),
-                                            __uint_as_float(tw.y << 16), __uint_as_float(tw.y & 0xffff0000u)};
+                        float out[4];    // this GEMM's contribution to the next operand
+                        float part[4];   // member value terms w_out[n] h_L[n][w] (last forward layer)
+                        float rs[4];     // residual stream values to store
+                        if (fwd) {
+                            // t = tanh(z) in BF16, elementwise on pairs of walkers
+                            const uint32_t y01 = tanh_bf16x2(a[jj][0] + bn, a[jj][1] + bn);
+                            const uint32_t y23 = tanh_bf16x2(a[jj][2] + bn, a[jj][3] + bn);
+                            const float t[4] = {__uint_as_float(y01 << 16), __uint_as_float(y01 & 0xffff0000u),
+                                                __uint_as_float(y23 << 16), __uint_as_float(y23 & 0xffff0000u)};
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            float gv = a[jj][i];
-                            if (RES && res_bwd && vn) gv = (l == L - 1 ? wo : rp[i]) + gv;
-                            rs[i] = gv;
-                            out[i] = gv * (1.0f - t[i] * t[i]);
-                            part[i] = 0.0f;
-                        }
-                    } else {
-                        // G_0 = dA/du (n is an input index): dA/ds_j = -sin s_j g[2j] + cos s_j g[2j+1]
-                        // (torsion), g[2j] (distance); the pair's odd element comes from the next lane
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const float g1 = __shfl_down_sync(0xffffffffu, a[jj][i], 1);
-                            const int w = cg * SM_GRP + i, jc = n >> 1;
-                            if (!(n & 1) && 2 * jc < P.D && w < W && !*abort_flag) {
-                                const float cs = __ldg(P.u + (size_t)w * P.D + 2 * jc);
-                                const float sn = __ldg(P.u + (size_t)w * P.D + 2 * jc + 1);
-                                const bool dist = P.cvdist && __ldg(P.cvdist + jc);
-                                P.gradA[((size_t)m * W + w) * P.C + jc] = dist ? a[jj][i] : -sn * a[jj][i] + cs * g1;
+                            for (int i = 0; i < 4; ++i) {
+                                float h = t[i];
+                                if (RES && res_fwd && vn) h = rp[i] + t[i];
+                                rs[i] = h;
+                                part[i] = vn ? wo * h : 0.0f;
+                                out[i] = l == L - 1 ? wo * (1.0f - t[i] * t[i]) : h;
                             }
-                            out[i] = 0.0f;
-                            part[i] = 0.0f;
-                            rs[i] = 0.0f;
+                            if (vn) tsv[ts_idx(rows, l, row, cg)] = make_uint2(y01, y23);
+                        } else if (l > 0) {
+                            // G_{l-1} (+ dA/dh_l) -> Delta_{l-1} = G (1 - t_{l-1}^2)
+                            const uint2 tw = vn ? tsv[ts_idx(rows, l - 1, row, cg)] : make_uint2(0u, 0u);
+                            const float t[4] = {__uint_as_float(tw.x << 16), __uint_as_float(tw.x & 0xffff0000u),
+                                                __uint_as_float(tw.y << 16), __uint_as_float(tw.y & 0xffff0000u)};
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                float gv = a[jj][i];
+                                if (RES && res_bwd && vn) gv = (l == L - 1 ? wo : rp[i]) + gv;
+                                rs[i] = gv;
+                                out[i] = gv * (1.0f - t[i] * t[i]);
+                                part[i] = 0.0f;
+                            }
+                        } else {
+                            // G_0 = dA/du (n is an input index): dA/ds_j = -sin s_j g[2j] + cos s_j g[2j+1]
+                            // (torsion), g[2j] (distance); the pair's odd element comes from the next lane
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const float g1 = __shfl_down_sync(0xffffffffu, a[jj][i], 1);
+                                const int w = cg * SM_GRP + i, jc = n >> 1;
+                                if (!(n & 1) && 2 * jc < P.D && w < W && !*abort_flag) {
+                                    const float cs = __ldg(P.u + (size_t)w * P.D + 2 * jc);
+                                    const float sn = __ldg(P.u + (size_t)w * P.D + 2 * jc + 1);
+                                    const bool dist = P.cvdist && __ldg(P.cvdist + jc);
+                                    P.gradA[((size_t)m * W + w) * P.C + jc] = dist ? a[jj][i] : -sn * a[jj][i] + cs * g1;
+                                }
+                                out[i] = 0.0f;
+                                part[i] = 0.0f;
+                                rs[i] = 0.0f;
+                            }
                         }
-                    }
-                    if (RES && res_st && vn) rsv[rs_idx(row, cg)] = make_float4(rs[0], rs[1], rs[2], rs[3]);
-                    if (g < G - 1 && n < kpn) {
-                        const int ch = (n >> 3) & 7;
-                        const uint32_t cb = (uint32_t)(n >> 6) * (uint32_t)(NW * 128) + (uint32_t)((n & 7) * 2);
+                        if (RES && res_st && vn) rsv[rs_idx(row, cg)] = make_float4(rs[0], rs[1], rs[2], rs[3]);
+                        if (g < G - 1 && n < kpn) {
+                            const int ch = (n >> 3) & 7;
+                            const uint32_t cb = (uint32_t)(n >> 6) * (uint32_t)(NW * 128) + (uint32_t)((n & 7) * 2);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            st_bf16(Bn, cb + (uint32_t)(cg * SM_GRP + i) * 128u + (uint32_t)((ch ^ ((cg * SM_GRP + i) & 7)) << 4),
-                                    vn ? out[i] : 0.0f);
-                    }
-                    if (fwd && l == L - 1) {
-                        // member value: this warp's 32 outputs, butterfly over the lanes, into rank 0
+                            for (int i = 0; i < 4; ++i)
+                                st_bf16(Bn, cb + (uint32_t)(cg * SM_GRP + i) * 128u + (uint32_t)((ch ^ ((cg * SM_GRP + i) & 7)) << 4),
+                                        vn ? out[i] : 0.0f);
+                        }
+                        if (fwd && l == L - 1) {
+                            // member value: this warp's 32 outputs, butterfly over the lanes, into rank 0
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            float p = part[i];
+                            for (int i = 0; i < 4; ++i) {
+                                float p = part[i];
 #pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-                            if (lane == 0)
-                                st_cluster_f32(mapa(smem_u32(&spart[(mt * 4 + quarter) * NW + cg * SM_GRP + i]), 0u), p);
+                                for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+                                if (lane == 0)
+                                    st_cluster_f32(mapa(smem_u32(&spart[(mt * 4 + quarter) * NW + cg * SM_GRP + i]), 0u), p);
+                            }
                         }
                     }
                 }
@@ -505,19 +512,21 @@ size_t rid_mlp_tc_small_smem_bytes(const TcArgs& P, int nw) {
 }
 
 cudaError_t rid_launch_mlp_tc_small(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, int nw,
-                                    cudaStream_t s) {
+                                    int epi_warps, cudaStream_t s) {
     if (P.ngemm != 2 * P.L || P.W > NW || nw != NW) return cudaErrorInvalidValue;
     if (P.csize < 1 || P.csize > SM_MT || P.stages < 2 || P.stages > TC_MAX_STAGES) return cudaErrorInvalidValue;
+    if (epi_warps != 16 && epi_warps != 8) return cudaErrorInvalidValue;
     if (P.geb[0] != 2) return cudaErrorInvalidValue;   // BF16 only
     for (int g = 0; g < 2 * P.L; ++g)
         if (P.gN[g] > 128 * SM_MT) return cudaErrorInvalidValue;
     const size_t smem = rid_mlp_tc_small_smem_bytes(P, NW);
-    const int v = P.resnet ? 1 : 0;
-    static size_t attr[2][64] = {};   // shared memory opted into, per instantiation and device
+    const int v = (P.resnet ? 1 : 0) + (epi_warps == 8 ? 2 : 0);
+    static size_t attr[4][64] = {};   // shared memory opted into, per instantiation and device
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
     size_t& have = attr[v][dev & 63];
-    auto kern = v == 0 ? k_mlp_tc_small<false> : k_mlp_tc_small<true>;
+    auto kern = v == 0 ? k_mlp_tc_small<false, 16> : v == 1 ? k_mlp_tc_small<true, 16>
+              : v == 2 ? k_mlp_tc_small<false, 8> : k_mlp_tc_small<true, 8>;
     if (smem > have) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -525,7 +534,7 @@ cudaError_t rid_launch_mlp_tc_small(const TcArgs& P, const CUtensorMap& big, con
     }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(P.csize, P.M, 1);
-    cfg.blockDim = dim3(SM_THREADS, 1, 1);
+    cfg.blockDim = dim3(sm_threads(epi_warps), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];

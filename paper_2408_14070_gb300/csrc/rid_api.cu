@@ -971,14 +971,17 @@ static int launch_mlp(rid_system* sys, int W, int mode, StateDev sd, cudaStream_
         const int sk = small_variant(sys, W);
         if (sk >= 0 && !values_only) {
             // up to 16 walkers: the transposed small-batch kernel, its output tiles split over a cluster
+            // while a server runs a job on the system, the lean variant: 8 epilogue warps and
+            // 3 weight stages, so that its CTAs can share SMs with the other jobs' kernels
             const int nw = 16 << sk, scs = small_cs(sys);
-            P.stages = V.s_stages[sk][scs];
+            const int epi = sys->serving ? 8 : 16;
+            P.stages = sys->serving ? std::min(3, V.s_stages[sk][scs]) : V.s_stages[sk][scs];
             P.acc_cols = V.s_acc_cols[sk][scs];
             P.tmem_cols = V.s_tmem_cols[sk][scs];
             P.nacc = V.s_nacc[sk][scs];
             P.csize = scs;
             sys->tcv.used_cs = scs;
-            TRY(timed_launch(sys, "k_mlp_tc", st, [&] { le = rid_launch_mlp_tc_small(P, V.big, V.small, nw, st); }));
+            TRY(timed_launch(sys, "k_mlp_tc", st, [&] { le = rid_launch_mlp_tc_small(P, V.big, V.small, nw, epi, st); }));
             if (le != cudaSuccess) return fail(RID_ERR_CUDA, "k_mlp_tc_small launch: %s", cudaGetErrorString(le));
             E.aslices = 1;
             return RID_OK;

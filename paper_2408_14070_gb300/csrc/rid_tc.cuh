@@ -53,8 +53,9 @@ cudaError_t rid_launch_mlp_tc_wide(const TcArgs& P, const CUtensorMap& big, cons
 // walkers on its N columns), each GEMM's 128-output tiles split over a cluster
 // of P.csize (1..4) CTAs per member.
 size_t rid_mlp_tc_small_smem_bytes(const TcArgs& P, int NW);
+// epi_warps: 16, or 8 (the lean variant: half the threads, same results bit for bit)
 cudaError_t rid_launch_mlp_tc_small(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small, int NW,
-                                    cudaStream_t s);
+                                    int epi_warps, cudaStream_t s);
 size_t rid_mlp_tc_cluster_smem_bytes(const TcArgs& P);
 cudaError_t rid_launch_mlp_tc_cluster(const TcArgs& P, const CUtensorMap& big, const CUtensorMap& small,
                                       cudaStream_t s);

@@ -5,7 +5,9 @@ persistent kernel, exploration jobs as replayed CUDA graphs).
 
 Each job's results must be the same bits as the per-job path (rid_label,
 rid_explore) on the same inputs, and the same bits alone in the server as in
-any mix.
+any mix.  (BF16 exploration jobs of up to 16 walkers run the small-batch
+ensemble kernel's lean variant in the server, 8 epilogue warps and 3 weight
+stages, and the full variant per job: the same bits.)
 """
 import time
 
@@ -87,6 +89,7 @@ def mixed_specs(R):
     return [
         Spec(R, "label", 22, 2, 3, 400, 1),
         Spec(R, "explore", 200, 20, 12, 520, 2, prec=R.RID_PREC_BF16, H=128),
+        Spec(R, "explore", 150, 18, 12, 530, 9, prec=R.RID_PREC_BF16, H=300),  # small-batch kernel, 3 tiles
         Spec(R, "label", 200, 20, 1, 300, 3),
         Spec(R, "label", 130, 40, 2, 250, 4),
         shared,
