@@ -51,15 +51,19 @@ __global__ void k_mb(SysDev S, StateDev st, int W, uint32_t step0) {
 constexpr int FF_THREADS = 224;
 
 // Force-field forces (bonded + all-pairs LJ, culled by cluster boxes) of
-// every bead at the current positions -> fff.  One CTA per walker.  BSMEM:
-// bonded terms through shared per-term slots (chains up to
-// RID_BONDED_SMEM_MAX beads), else per bead.
+// every bead at the current positions -> fff.  P CTAs per walker (CTA
+// w * P + p): each loads the walker's chain and cluster boxes and computes the
+// forces of its ipc passes of blockDim beads (passes p * ipc ..), so a bead's
+// force is the same code and order whatever P (P = 1 for energy launches,
+// whose per-walker sum is over every pass).  BSMEM: bonded terms through shared
+// per-term slots (chains up to RID_BONDED_SMEM_MAX beads), else per bead.
 template <bool ENERGY, bool BSMEM>
-__global__ void __maxnreg__(56) k_ff(SysDev S, StateDev st) {
+__global__ void __maxnreg__(56) k_ff(SysDev S, StateDev st, int P, int ipc) {
     extern __shared__ float4 sm4[];
     __shared__ double red[32];
     __shared__ unsigned keep_s[FF_THREADS / 32][LJ_MAX_MASK_WORDS];
-    const int w = blockIdx.x, N = S.N;
+    const int w = blockIdx.x / P, N = S.N;
+    const int p0 = (blockIdx.x - w * P) * ipc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nclus = (N + LJ_CLUSTER - 1) / LJ_CLUSTER, N8 = nclus * LJ_CLUSTER;
     const int nwords = (nclus + 31) / 32;
@@ -80,7 +84,8 @@ __global__ void __maxnreg__(56) k_ff(SysDev S, StateDev st) {
     const bool sig1 = S.sig2 == 1.0f;
     double e = 0.0;
     const int iters = (N + blockDim.x - 1) / blockDim.x;
-    for (int it = 0; it < iters; ++it) {
+    const int it1 = p0 + ipc < iters ? p0 + ipc : iters;
+    for (int it = p0; it < it1; ++it) {
         const int i = it * blockDim.x + threadIdx.x;
         const int wlo = i - lane, whi = wlo + 31;
         if (wlo >= N) break;                                  // warp-uniform: no bead of this warp
@@ -433,16 +438,36 @@ int rid_ff_smem_bytes(int N) {
 
 int rid_ff_default_threads(int N) { return chain_threads(N) < FF_THREADS ? chain_threads(N) : FF_THREADS; }
 
+// CTAs per walker for W walkers and `iters` passes of the CTA's threads over
+// the chain: with fewer walkers than two per SM, each walker's passes are split
+// over up to 8 CTAs (passes per CTA *ipc).  Chosen from the shape alone.
+static int ff_split(int W, int iters, int& ipc) {
+    static int nsm[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    int& n = nsm[dev & 63];
+    if (n == 0 && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n = 1;
+    int want = (2 * n + W - 1) / (W > 0 ? W : 1);
+    want = want < 1 ? 1 : (want > 8 ? 8 : want);
+    if (want > iters) want = iters;
+    ipc = (iters + want - 1) / want;
+    return (iters + ipc - 1) / ipc;
+}
+
 // threads: CTA size (a multiple of 32 up to the default), 0 for the default.
 // Each thread sums its own beads' forces in a fixed order and warps always
-// cover the same 32-bead groups, so the forces do not depend on it; the
-// energy sum does (its per-thread partials), so energy launches keep the
-// default.
+// cover the same 32-bead groups, so the forces do not depend on it, nor on
+// the split of a walker's passes over CTAs; the energy sum does (its
+// per-thread partials), so energy launches keep the default size and one CTA
+// per walker.
 void rid_launch_ff(const SysDev& S, StateDev st, int W, bool energy, cudaStream_t s, int threads) {
     const int dth = rid_ff_default_threads(S.N);
     const int th = (energy || threads <= 0 || threads > dth) ? dth : threads;
     const size_t sm = (size_t)rid_ff_smem_bytes(S.N);
     const bool bsm = S.N <= RID_BONDED_SMEM_MAX;
+    const int iters = (S.N + th - 1) / th;
+    int ipc = iters;
+    const int P = energy ? 1 : ff_split(W, iters, ipc);
     static unsigned long long attr = 0;
     if (rid_first_on_device(attr)) {
         cudaFuncSetAttribute(k_ff<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -450,12 +475,13 @@ void rid_launch_ff(const SysDev& S, StateDev st, int W, bool energy, cudaStream_
         cudaFuncSetAttribute(k_ff<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(k_ff<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     }
+    const unsigned grid = (unsigned)W * (unsigned)P;
     if (bsm) {
-        if (energy) k_ff<true, true><<<W, th, sm, s>>>(S, st);
-        else k_ff<false, true><<<W, th, sm, s>>>(S, st);
+        if (energy) k_ff<true, true><<<grid, th, sm, s>>>(S, st, P, ipc);
+        else k_ff<false, true><<<grid, th, sm, s>>>(S, st, P, ipc);
     } else {
-        if (energy) k_ff<true, false><<<W, th, sm, s>>>(S, st);
-        else k_ff<false, false><<<W, th, sm, s>>>(S, st);
+        if (energy) k_ff<true, false><<<grid, th, sm, s>>>(S, st, P, ipc);
+        else k_ff<false, false><<<grid, th, sm, s>>>(S, st, P, ipc);
     }
 }
 

@@ -1,5 +1,6 @@
-"""The force-field kernel's CTA-size tuner: every size it may pick gives the
-same forces bit for bit (each thread sums its own beads in a fixed order), the
+"""The force-field kernel's CTA-size tuner and its split of a walker's chain
+over several CTAs at few walkers: every size it may pick and every split give
+the same forces bit for bit (each thread sums its own beads in a fixed order), the
 energy trace does not depend on the size (energy launches keep the default),
 and a whole biased trajectory is the same with a fixed small size, the tuned
 size and the default.  Forces are also checked against the oracle at 1e-5,
@@ -78,3 +79,26 @@ def test_cta_size_argument_errors(R):
         assert sysm.ff_threads() == 96
         sysm.set_ff_threads(0)
         assert sysm.ff_threads() == 96   # the default for 70 beads, before any evaluation
+
+
+@pytest.mark.parametrize("n,seed", [(200, 11), (700, 12), (2000, 13)])
+def test_walker_split_over_ctas_gives_the_same_forces(R, orc, n, seed):
+    """With fewer walkers than two per SM each walker's passes over its chain are
+    split over up to 8 CTAs; a bead's force is the same code and order whatever
+    the split, so 6 walkers alone (split) and the same 6 inside a batch of 312
+    (one CTA per walker) give the same bits, at every CTA size."""
+    sp = I.make_system(n, 6, seed)
+    x = I.make_chains(6, sp, seed)
+    xb = np.ascontiguousarray(np.tile(x, (52, 1, 1)))
+    with R.System(sp) as sysm:
+        for th in (0, 64):
+            sysm.set_ff_threads(th)
+            f = np.zeros((6, n, 3), np.float32)
+            sysm.eval_forces(x, R.RID_BIAS_NONE, f_out=f)
+            fb = np.zeros((312, n, 3), np.float32)
+            sysm.eval_forces(xb, R.RID_BIAS_NONE, f_out=fb)
+            assert np.array_equal(f, fb[:6]), th
+            assert np.array_equal(fb[6:12], fb[:6])
+    ref = orc.total(sp, x[0].astype(np.float64))["f"]
+    scale = np.abs(ref) + np.sqrt(np.mean(ref ** 2))
+    assert (np.abs(f[0] - ref) / scale).max() < 1e-5
