@@ -306,7 +306,10 @@ struct rid_server {
     std::vector<SJob*> labels;           // admitted label jobs
     std::vector<SJob*> tick;             // jobs of the tick in flight
     bool tick_busy = false;
-    double tick_target_ms = 4.0, cost = 3.0e-5;   // ms per step per N^1.5, refined after every tick
+    // per-step cost model of a label run, cost x (N + 200) ms, refined after every tick (measured
+    // alone, one run per CTA: 9.2, 18.9 and 57.6 us per step at 200, 700 and 2000 beads, the
+    // cluster-culled pairs growing about linearly in N)
+    double tick_target_ms = 4.0, cost = 2.6e-5;
     double tick_pred = 0.0;
     Pinned lmeta_h, lio_h;
     void* lmeta_d = nullptr;
@@ -597,7 +600,7 @@ int label_tick_launch(rid_server* srv) {
     size_t smem = 0;
     for (size_t k = 0; k < act.size(); ++k) {
         SJob* j = act[k];
-        const double per = srv->cost * std::pow((double)j->N, 1.5);
+        const double per = srv->cost * ((double)j->N + 200.0);
         long long steps = (long long)(srv->tick_target_ms / per);
         steps = std::max<long long>(8, steps);
         steps = std::min<long long>(steps, j->rq.n_steps - j->t_done);
