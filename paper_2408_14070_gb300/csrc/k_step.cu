@@ -125,6 +125,27 @@ __global__ void __maxnreg__(56) k_ff(SysDev S, StateDev st, int P, int ipc) {
 //   INT: 0 nothing, 1 CVs at the current positions, 2 B-A-O-A then CVs
 // With FIN and INT = 0 the total force is stored (end of a call); with
 // FIN = 0 the opening kick uses the stored force.
+// P CTAs per walker (a thread-block cluster, P > 1 only without ENERGY): CTA p
+// integrates its slice of bead batches and keeps the new positions in its
+// shared memory; after a cluster barrier it forms its share of the CVs,
+// reading atoms of other slices from their CTAs' shared memory.  Every CTA
+// forms the CV force (the same arithmetic); CTA 0 alone writes the traces, eps
+// and the label sums.  A bead's update and a CV are the same arithmetic
+// whatever P.
+// Thread-block cluster helpers of the split k_head: a barrier over the
+// cluster's CTAs, and a float4 of a peer CTA's shared memory.
+__device__ __forceinline__ void head_cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float4 head_ld_peer(const float4* local, uint32_t rank) {
+    uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(local)), r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(r)
+                 : "memory");
+    return v;
+}
+
 constexpr int HEAD_THREADS = 128;  // four warps per walker, seven CTAs per SM: the grid is resident at once
 constexpr int HEAD_BEADS = 2;      // beads per thread per batch, loaded before they are needed
 
@@ -132,12 +153,13 @@ template <int MODE, bool FIN, bool KICK, int INT, bool ENERGY>
 __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st, EnsDev E, LabelDev lab, long long t_fin,
                                                         int slot, float* __restrict__ cv_out,
                                                         float* __restrict__ eps_out, double* __restrict__ energy_out,
-                                                        long long T, uint32_t step) {
+                                                        long long T, uint32_t step, int P) {
     extern __shared__ float4 xs[];                     // [N] positions, then (FIN) [4C] Jacobian rows, [4C] slots
     __shared__ float Fs[RID_MAX_CV];
     __shared__ float s_eps, s_abar;
     __shared__ double red[32];
-    const int w = blockIdx.x, N = S.N, C = S.C, W = st.W;
+    const int w = blockIdx.x / P, N = S.N, C = S.C, W = st.W;
+    const int p = blockIdx.x - w * P;                      // rank in the walker's cluster
     float4* Jsm = xs + N;                                   // this walker's torsion Jacobians [C][4]
     int2* acv_s = reinterpret_cast<int2*>(Jsm + 4 * C);     // (cv, slot) list of the chain rule
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -145,6 +167,8 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
     const float kick = S.half_dt * S.inv_mass;
     const uint32_t stp = step + ((INT == 2 && st.stepbase) ? *st.stepbase : 0u);
     constexpr int BATCH = HEAD_THREADS * HEAD_BEADS;
+    const int bpc = ((N + BATCH - 1) / BATCH + P - 1) / P;  // bead batches per CTA
+    const int bb0 = p * bpc * BATCH, bb1 = min(N, (p + 1) * bpc * BATCH);
     // bead data of the first batch (and its Langevin noise) is loaded / drawn
     // before the ensemble reduction, so the two overlap
     float3 px[HEAD_BEADS], pv[HEAD_BEADS], pf[HEAD_BEADS], pz[HEAD_BEADS];
@@ -179,7 +203,7 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
         for (int m = 0; m < PM; ++m)
             gpre[m] = (m < E.M && lane < C) ? st.gradA[((long long)m * W + w) * C + lane] : 0.0f;
     }
-    load_batch(0);
+    if (bb0 < N) load_batch(bb0);
     if (FIN) {
         // the Jacobians of the finished evaluation and the chain-rule list go to
         // shared memory while the CV force is formed
@@ -234,11 +258,11 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
                 if (lane == 0) {
                     s_abar = av * invM;
                     s_eps = eps;
-                    st.eps[w] = eps;
+                    if (p == 0) st.eps[w] = eps;
                 }
             }
         } else if (MODE == 2) {
-            const bool sample = KICK && t_fin >= lab.n_equil;
+            const bool sample = KICK && t_fin >= lab.n_equil && p == 0;
             long long b = 0;
             if (sample) b = ((t_fin - lab.n_equil) * lab.B) / lab.K;
             for (int j = threadIdx.x; j < C; j += blockDim.x) {
@@ -258,7 +282,7 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
         }
         __syncthreads();
         // traces of the finished step read the CVs before they are recomputed
-        if (slot >= 0) {
+        if (slot >= 0 && p == 0) {
             if (cv_out)
                 for (int j = threadIdx.x; j < C; j += blockDim.x)
                     cv_out[((long long)w * T + slot) * C + j] = st.s[(long long)w * C + j];
@@ -267,8 +291,8 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
     }
     double ke = 0.0;
     int bad = 0;
-    for (int b0 = 0; b0 < N; b0 += BATCH) {
-        if (b0 > 0) load_batch(b0);
+    for (int b0 = bb0; b0 < bb1; b0 += BATCH) {
+        if (b0 > bb0) load_batch(b0);
 #pragma unroll
         for (int k = 0; k < HEAD_BEADS; ++k) {
             const int i = b0 + k * HEAD_THREADS + threadIdx.x;
@@ -332,10 +356,27 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
     }
     if (INT != 0) {
         __syncthreads();   // all Jacobian reads of the finish are done; positions staged
-        for (int j = threadIdx.x; j < C; j += blockDim.x) {
+        if (P > 1) head_cluster_sync();   // and every slice's in its CTA
+        const int cpc = (C + P - 1) / P;
+        const int jend = min(C, (p + 1) * cpc);
+        for (int j = p * cpc + threadIdx.x; j < jend; j += blockDim.x) {
             const int4 q = S.cv[j];
             float3 g[4];
-            const float sj = rid_cv(q, xs, g);
+            float sj;
+            if (P == 1) {
+                sj = rid_cv(q, xs, g);
+            } else {
+                // the CV's atoms, from the shared memory of the CTAs whose slices hold them
+                const bool dist = rid_cv_is_distance(q);
+                const int at[4] = {q.x, q.y, dist ? q.x : q.z, dist ? q.x : q.w};
+                float4 pos[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int owner = (at[a] / BATCH) / bpc;
+                    pos[a] = owner == p ? xs[at[a]] : head_ld_peer(&xs[at[a]], (uint32_t)owner);
+                }
+                sj = rid_cv(dist ? make_int4(0, 1, -1, -1) : make_int4(0, 1, 2, 3), pos, g);
+            }
             const long long o = (long long)w * C + j;
             st.s[o] = sj;
 #pragma unroll
@@ -345,6 +386,7 @@ __global__ void __launch_bounds__(HEAD_THREADS, 7) k_head(SysDev S, StateDev st,
             st.u[(long long)w * 2 * C + 2 * j] = u0;
             st.u[(long long)w * 2 * C + 2 * j + 1] = u1;
         }
+        if (P > 1) head_cluster_sync();   // no CTA leaves while a peer may read its positions
     }
 }
 
@@ -438,9 +480,10 @@ int rid_ff_smem_bytes(int N) {
 
 int rid_ff_default_threads(int N) { return chain_threads(N) < FF_THREADS ? chain_threads(N) : FF_THREADS; }
 
-// CTAs per walker for W walkers and `iters` passes of the CTA's threads over
-// the chain: with fewer walkers than two per SM, each walker's passes are split
-// over up to 8 CTAs (passes per CTA *ipc).  Chosen from the shape alone.
+// CTAs per walker for W walkers and `iters` units of a walker's work (the
+// force field's passes of the CTA's threads over the chain, k_head's bead
+// batches): with fewer walkers than two per SM, each walker's units are split
+// over up to 8 CTAs (units per CTA *ipc).  Chosen from the shape alone.
 static int ff_split(int W, int iters, int& ipc) {
     static int nsm[64] = {};
     int dev = 0;
@@ -495,12 +538,35 @@ static void head_e(const HeadArgs& a, cudaStream_t s) {
         cudaFuncSetAttribute(k_head<MODE, FIN, KICK, INT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         cudaFuncSetAttribute(k_head<MODE, FIN, KICK, INT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     }
-    if (a.energy)
+    // CTAs per walker: a cluster over the bead batches with fewer walkers than two
+    // per SM (not for energy launches, whose per-walker sums stay in one CTA, nor
+    // for a server's jobs: under 16 concurrent jobs the clusters measured slower,
+    // exploration p50 255 -> 281 ms on the 200/s serving stream)
+    const int nb = (a.S.N + th * HEAD_BEADS - 1) / (th * HEAD_BEADS);
+    int bpc = nb;
+    const int P = (a.energy || INT == 0 || a.no_split) ? 1 : ff_split(a.W, nb, bpc);
+    if (a.energy) {
         k_head<MODE, FIN, KICK, INT, true><<<a.W, th, sm, s>>>(a.S, a.st, a.E, a.lab, a.t_fin, a.slot, a.cv_out,
-                                                                 a.eps_out, a.energy_out, a.T, a.step);
-    else
+                                                                 a.eps_out, a.energy_out, a.T, a.step, 1);
+    } else if (P == 1) {
         k_head<MODE, FIN, KICK, INT, false><<<a.W, th, sm, s>>>(a.S, a.st, a.E, a.lab, a.t_fin, a.slot, a.cv_out,
-                                                                  a.eps_out, a.energy_out, a.T, a.step);
+                                                                  a.eps_out, a.energy_out, a.T, a.step, 1);
+    } else {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)(a.W * P), 1, 1);
+        cfg.blockDim = dim3(th, 1, 1);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)P;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_head<MODE, FIN, KICK, INT, false>, a.S, a.st, a.E, a.lab, a.t_fin, a.slot,
+                           a.cv_out, a.eps_out, a.energy_out, a.T, a.step, P);
+    }
 }
 
 template <int MODE>

@@ -1029,6 +1029,7 @@ static int launch_head(rid_system* sys, int W, int mode, const LabelDev* lab, bo
     a.fin = fin;
     a.kick = kick;
     a.integ = integ;
+    a.no_split = sys->serving;
     a.t_fin = t_fin;
     a.slot = fin ? slot : -1;
     a.cv_out = cv;

@@ -271,6 +271,8 @@ struct HeadArgs {
     double* energy_out;
     long long T;
     uint32_t step;             // Philox step of the opened step
+    bool no_split;             // one CTA per walker whatever W (a server's jobs: measured better under
+                               // concurrency than clusters per walker)
 };
 void rid_launch_head(const HeadArgs& a, cudaStream_t s);
 void rid_launch_add_u32(uint32_t* p, uint32_t d, cudaStream_t s);
