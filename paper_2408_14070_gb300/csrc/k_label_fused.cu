@@ -14,6 +14,14 @@
 //   closing B half-kick.
 // Every per-bead sum is taken in the same order as the per-step kernels, so a
 // job gives the same bits here as through rid_label.
+//
+// Long chains run as thread-block clusters of P CTAs (CL = true): each CTA
+// holds the whole chain, integrates and forms the force-field rows of its
+// slice of bead passes, and sends its slice's new positions to the peers'
+// shared memory (st.shared::cluster) between two cluster barriers per step;
+// every CTA forms the CVs and the restraint force itself (the same
+// arithmetic), CTA 0 alone keeps the label sums.  Rank 0 takes the work item
+// and hands it to its peers, so a cluster leaves the loop together.
 #include "rid_batch.cuh"
 #include "rid_forces.cuh"
 
@@ -47,22 +55,45 @@ __host__ __device__ inline LfLayout lf_layout(int N, int C) {
     return L;
 }
 
+__device__ __forceinline__ uint32_t lf_peer(const void* local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(r)
+                 : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(local))), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void lf_cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t lf_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
 // Block of label sample k (of K) among B blocks.
 __device__ __forceinline__ int lf_block(long long k, int B, long long K) { return (int)((k * B) / K); }
 
-template <int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_label_fused(FusedArgs A) {
+template <int NT, bool CL>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_label_fused(FusedArgs A, int P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ FusedJob J;
     __shared__ int s_item;
     __shared__ unsigned keep_s[NT / 32][LJ_MAX_MASK_WORDS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rank = CL ? (int)lf_rank() : 0;
     for (;;) {
-        if (tid == 0) {
+        if (tid == 0 && rank == 0) {
             const int it = atomicAdd(A.next, 1);
             s_item = it;
-            if (it < A.n_items) J = A.jobs[A.items[it].job];
+            if (CL)
+                for (int q = 1; q < P; ++q)
+                    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(lf_peer(&s_item, (uint32_t)q)), "r"(it)
+                                 : "memory");
         }
+        if (CL) lf_cluster_sync();
+        else __syncthreads();
+        if (tid == 0 && s_item < A.n_items) J = A.jobs[A.items[s_item].job];
         __syncthreads();
         const int it = s_item;
         if (it >= A.n_items) break;
@@ -70,6 +101,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_label_fused(FusedArgs A) {
         const SysDev& S = J.S;
         const int N = S.N, C = S.C;
         const LfLayout L = lf_layout(N, C);
+        // this CTA's bead passes (all of them without a cluster)
+        const int npass = (N + NT - 1) / NT, ppc = (npass + P - 1) / P;
+        const int pass0 = rank * ppc, pass1 = min(npass, pass0 + ppc);
+        const int lo = pass0 * NT, hi = min(N, pass1 * NT);
         float4* xs = reinterpret_cast<float4*>(smem + L.xs);
         float4* cbox = reinterpret_cast<float4*>(smem + L.cbox);
         float4* vs = reinterpret_cast<float4*>(smem + L.vs);
@@ -117,7 +152,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_label_fused(FusedArgs A) {
                 lbp[j] = J.bsum[o * J.B + cur_b];
             }
         }
-        __syncthreads();
+        // (cluster: every CTA has staged the chain before any peer writes new positions into it)
+        if (CL) lf_cluster_sync();
+        else __syncthreads();
 
         // Evaluate: CVs, restraint force (and label sample at step ts >= n_equil
         // when ts >= 0), force field, chain rule; closing kick when `kick_v`.
@@ -127,6 +164,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_label_fused(FusedArgs A) {
                 for (int t = tid; t < N; t += NT) bonded_dihedrals_to_smem(S, xs, t, fD);
             const bool sample = ts >= J.n_equil;
             const int b = sample ? lf_block(ts - J.n_equil, J.B, J.K) : cur_b;
+            const bool keep = rank == 0;   // the label sums live in CTA 0
             const bool newblock = b != cur_b;
             for (int j = tid; j < C; j += NT) {
                 const int4 q = S.cv[j];
@@ -137,7 +175,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_label_fused(FusedArgs A) {
                 const long long o = (long long)r * C + j;
                 const double d = rid_cv_offset(q, (double)sj, J.s0[o]);
                 Fs[j] = (float)(-J.kappa[o] * d);
-                if (sample) {
+                if (sample && keep) {
                     if (newblock) {
                         J.bsum[o * J.B + cur_b] = lbp[j];
                         lbp[j] = 0.0;
@@ -149,7 +187,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_label_fused(FusedArgs A) {
             }
             cur_b = b;
             __syncthreads();
-            for (int pass = 0; pass * NT < N; ++pass) {
+            for (int pass = pass0; pass < pass1; ++pass) {
                 const int i = pass * NT + tid;
                 const int wlo = i - lane, whi = wlo + 31;
                 if (wlo >= N) break;                        // warp-uniform
@@ -189,13 +227,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_label_fused(FusedArgs A) {
                     fs[i] = f;
                 }
             }
-            __syncthreads();
+            // (cluster: every CTA is done reading the positions the next step overwrites)
+            if (CL) lf_cluster_sync();
+            else __syncthreads();
         };
 
         if (J.init) evaluate(-1, false);   // force at x0 (no sample: ts = -1 < n_equil)
         for (long long t = t0; t < t1; ++t) {
             const uint32_t step = J.step0 + (uint32_t)t;
-            for (int i = tid; i < N; i += NT) {
+            for (int i = lo + tid; i < hi; i += NT) {
                 float4 x = xs[i], v = vs[i];
                 const float4 f = fs[i];
                 v.x = fmaf(kick, f.x, v.x);                 // B
@@ -215,18 +255,26 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_label_fused(FusedArgs A) {
                 x.z = fmaf(S.half_dt, v.z, x.z);
                 xs[i] = make_float4(x.x, x.y, x.z, 0.0f);
                 vs[i] = v;
+                if (CL)
+                    for (int q = 0; q < P; ++q)
+                        if (q != rank)
+                            asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(
+                                             lf_peer(&xs[i], (uint32_t)q)),
+                                         "f"(x.x), "f"(x.y), "f"(x.z), "f"(0.0f)
+                                         : "memory");
             }
-            __syncthreads();
+            if (CL) lf_cluster_sync();   // every slice's new positions in every CTA
+            else __syncthreads();
             evaluate(t, true);
         }
 
-        // ---- write back the run
-        for (int i = tid; i < N; i += NT) {
+        // ---- write back the run (this CTA's slice; the label sums from CTA 0)
+        for (int i = lo + tid; i < hi; i += NT) {
             J.x[base + i] = xs[i];
             J.v[base + i] = vs[i];
             J.f[base + i] = fs[i];
         }
-        for (int j = tid; j < C; j += NT) {
+        for (int j = tid; j < (rank == 0 ? C : 0); j += NT) {
             const long long o = (long long)r * C + j;
             J.sum[o] = lsum[j];
             J.sum2[o] = lsum2[j];
@@ -236,7 +284,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_label_fused(FusedArgs A) {
         }
         bad = __syncthreads_or(bad);
         if (tid == 0 && bad) J.flags[r] = 1;
-        __syncthreads();   // J and s_item are rewritten by the next item
+        // J and s_item are rewritten by the next item
+        if (CL) lf_cluster_sync();
+        else __syncthreads();
     }
 }
 
@@ -282,21 +332,39 @@ size_t rid_label_fused_smem(int N, int C, int threads) {
 }
 
 template <int NT>
-static cudaError_t launch_nt(const FusedArgs& A, int grid, size_t smem, cudaStream_t s) {
+static cudaError_t launch_nt(const FusedArgs& A, int grid, size_t smem, int P, cudaStream_t s) {
     static unsigned long long attr = 0;
     if (rid_first_on_device(attr)) {
-        const cudaError_t e = cudaFuncSetAttribute(k_label_fused<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   220 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(k_label_fused<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             220 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_label_fused<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         if (e != cudaSuccess) return e;
     }
-    k_label_fused<NT><<<grid, NT, smem, s>>>(A);
-    return cudaGetLastError();
+    if (P <= 1) {
+        k_label_fused<NT, false><<<grid, NT, smem, s>>>(A, 1);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)P;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_label_fused<NT, true>, A, P);
 }
 
-cudaError_t rid_launch_label_fused(const FusedArgs& A, int threads, int grid, size_t smem, cudaStream_t s) {
-    if (threads == 128) return launch_nt<128>(A, grid, smem, s);
-    if (threads == 256) return launch_nt<256>(A, grid, smem, s);
-    if (threads == 512) return launch_nt<512>(A, grid, smem, s);
+cudaError_t rid_launch_label_fused(const FusedArgs& A, int threads, int grid, size_t smem, cudaStream_t s, int cluster) {
+    if (cluster > 1 && (grid % cluster || cluster > 8)) return cudaErrorInvalidValue;
+    if (threads == 128) return launch_nt<128>(A, grid, smem, cluster, s);
+    if (threads == 256) return launch_nt<256>(A, grid, smem, cluster, s);
+    if (threads == 512) return launch_nt<512>(A, grid, smem, cluster, s);
     return cudaErrorInvalidValue;
 }
 
@@ -304,14 +372,14 @@ int rid_label_fused_occupancy(int threads, size_t smem) {
     int n = 0;
     cudaError_t e = cudaSuccess;
     if (threads == 128) {
-        cudaFuncSetAttribute(k_label_fused<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_label_fused<128>, 128, smem);
+        cudaFuncSetAttribute(k_label_fused<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_label_fused<128, false>, 128, smem);
     } else if (threads == 256) {
-        cudaFuncSetAttribute(k_label_fused<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_label_fused<256>, 256, smem);
+        cudaFuncSetAttribute(k_label_fused<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_label_fused<256, false>, 256, smem);
     } else if (threads == 512) {
-        cudaFuncSetAttribute(k_label_fused<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_label_fused<512>, 512, smem);
+        cudaFuncSetAttribute(k_label_fused<512, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_label_fused<512, false>, 512, smem);
     }
     return e == cudaSuccess ? n : 0;
 }

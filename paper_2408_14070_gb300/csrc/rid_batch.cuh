@@ -45,7 +45,10 @@ struct FusedArgs {
 size_t rid_label_fused_smem(int N, int C, int threads);
 // Launch on `s` with `threads` per CTA (128, 256 or 512) and `grid` CTAs;
 // smem from rid_label_fused_smem over the largest job of the batch.
-cudaError_t rid_launch_label_fused(const FusedArgs& A, int threads, int grid, size_t smem, cudaStream_t s);
+// cluster > 1: every run by a thread-block cluster of that many CTAs (at most
+// 8; grid a multiple of it), each forming the forces of its slice of beads.
+cudaError_t rid_launch_label_fused(const FusedArgs& A, int threads, int grid, size_t smem, cudaStream_t s,
+                                   int cluster = 1);
 // CTAs of k_label_fused resident per SM for a block size and shared memory size.
 int rid_label_fused_occupancy(int threads, size_t smem);
 

@@ -303,6 +303,9 @@ struct rid_server {
     // worker-owned
     cudaStream_t lst = nullptr;
     cudaEvent_t lev = nullptr, le0 = nullptr;
+    // long chains' runs go to a second launch of thread-block clusters beside the tick's kernel
+    cudaStream_t lst2 = nullptr;
+    cudaEvent_t lfork = nullptr, ljoin = nullptr;
     std::vector<SJob*> labels;           // admitted label jobs
     std::vector<SJob*> tick;             // jobs of the tick in flight
     bool tick_busy = false;
@@ -583,6 +586,14 @@ bool explore_progress(rid_server* srv, SJob* j) {
     return true;
 }
 
+// Label runs of chains of at least LF_CL_MIN_N beads go to a second launch of
+// the persistent kernel in thread-block clusters of LF_CL CTAs, beside the
+// tick's main launch; the cost model counts their steps as LF_CL_SPEED times
+// cheaper.
+constexpr int LF_CL_MIN_N = 768;
+constexpr int LF_CL = 4;
+constexpr double LF_CL_SPEED = 2.5;
+
 // ---- label jobs: one tick of the persistent kernel over every admitted job
 int label_tick_launch(rid_server* srv) {
     NvtxScope nvtx_("label tick");
@@ -597,10 +608,11 @@ int label_tick_launch(rid_server* srv) {
     size_t in_h = 0, out_h = 0;
     double pred = 0.0;
     int maxN = 0;
-    size_t smem = 0;
+    size_t smem = 0, smem_cl = 0;
     for (size_t k = 0; k < act.size(); ++k) {
         SJob* j = act[k];
-        const double per = srv->cost * ((double)j->N + 200.0);
+        const bool cl = j->N >= LF_CL_MIN_N;
+        const double per = srv->cost * ((double)j->N / (cl ? LF_CL_SPEED : 1.0) + 200.0);
         long long steps = (long long)(srv->tick_target_ms / per);
         steps = std::max<long long>(8, steps);
         steps = std::min<long long>(steps, j->rq.n_steps - j->t_done);
@@ -612,7 +624,7 @@ int label_tick_launch(rid_server* srv) {
         fj[k] = J;
         pred = std::max(pred, per * steps);
         maxN = std::max(maxN, j->N);
-        smem = std::max(smem, rid_label_fused_smem(j->N, j->C, 0));
+        (cl ? smem_cl : smem) = std::max(cl ? smem_cl : smem, rid_label_fused_smem(j->N, j->C, 0));
         for (int r = 0; r < j->W; ++r) items.push_back({(int)k, r});
         if (!j->staged) {
             // staging order s0 | kappa | x0 | v0: the doubles first, so every array stays aligned
@@ -632,6 +644,12 @@ int label_tick_launch(rid_server* srv) {
         return (fj[a.job].t1 - fj[a.job].t0) * (double)fj[a.job].S.N * fj[a.job].S.N >
                (fj[b.job].t1 - fj[b.job].t0) * (double)fj[b.job].S.N * fj[b.job].S.N;
     });
+    // the short chains' items first (the main launch), then the long chains' (the clusters)
+    std::stable_partition(items.begin(), items.end(),
+                          [&](const FusedItem& a) { return fj[a.job].S.N < LF_CL_MIN_N; });
+    int n_small = 0;
+    while (n_small < (int)items.size() && fj[items[n_small].job].S.N < LF_CL_MIN_N) ++n_small;
+    const int n_big = (int)items.size() - n_small;
     // host staging of new inputs, then the tables
     STRY(srv->lio_h.ensure(std::max(in_h, out_h) + 256));
     const size_t o_items = align_up(sizeof(FusedJob) * fj.size());
@@ -669,20 +687,37 @@ int label_tick_launch(rid_server* srv) {
     FusedArgs A{};
     A.jobs = reinterpret_cast<const FusedJob*>(dm);
     A.items = reinterpret_cast<const FusedItem*>(dm + o_items);
-    A.n_items = (int)items.size();
+    A.n_items = n_small;
     A.next = reinterpret_cast<int*>(dm + o_cnt);
+    FusedArgs A2 = A;
+    A2.items = A.items + n_small;
+    A2.n_items = n_big;
+    A2.next = reinterpret_cast<int*>(dm + o_cnt + 128);
     int nt = 256;
     {
         std::lock_guard<std::mutex> lk(srv->pool_mu);
         auto hit = srv->tuned.find(shape_key((int)items.size(), maxN));
         if (hit != srv->tuned.end()) nt = hit->second;
     }
-    if (rid_label_fused_occupancy(nt, smem) < 1) nt = 128;
-    const int occ = std::max(1, rid_label_fused_occupancy(nt, smem));
-    const int grid = (int)std::min<long long>((long long)items.size(), (long long)occ * srv->n_sm);
-    SCK(cudaMemsetAsync(A.next, 0, sizeof(int), st));
+    const size_t smem_all = std::max(smem, smem_cl);
+    if (rid_label_fused_occupancy(nt, smem_all) < 1) nt = 128;
+    SCK(cudaMemsetAsync(A.next, 0, 256, st));
     SCK(cudaEventRecord(srv->le0, st));
-    SCK(rid_launch_label_fused(A, nt, grid, smem, st));
+    if (n_big > 0) {
+        const int occ_cl = std::max(1, rid_label_fused_occupancy(nt, smem_cl));
+        const long long clusters = std::max<long long>(1, (long long)occ_cl * srv->n_sm / LF_CL);
+        const int grid_cl = (int)(std::min<long long>(n_big, clusters) * LF_CL);
+        SCK(cudaEventRecord(srv->lfork, st));
+        SCK(cudaStreamWaitEvent(srv->lst2, srv->lfork, 0));
+        SCK(rid_launch_label_fused(A2, nt, grid_cl, smem_cl, srv->lst2, LF_CL));
+        SCK(cudaEventRecord(srv->ljoin, srv->lst2));
+    }
+    if (n_small > 0) {
+        const int occ = std::max(1, rid_label_fused_occupancy(nt, smem));
+        const int grid = (int)std::min<long long>(n_small, (long long)occ * srv->n_sm);
+        SCK(rid_launch_label_fused(A, nt, grid, smem, st));
+    }
+    if (n_big > 0) SCK(cudaStreamWaitEvent(st, srv->ljoin, 0));
     if (!dout.empty()) rid_launch_copy_descs(reinterpret_cast<const CopyDesc*>(dm + o_dout), (int)dout.size(), st);
     SCK(cudaEventRecord(srv->lev, st));
     ho = 0;
@@ -828,6 +863,9 @@ extern "C" int rid_server_create(uint64_t budget, rid_server** out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&srv->lst, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&srv->lev);
     if (e == cudaSuccess) e = cudaEventCreate(&srv->le0);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&srv->lst2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&srv->lfork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&srv->ljoin, cudaEventDisableTiming);
     for (int k = 0; k < N_ESLOTS && e == cudaSuccess; ++k) {
         e = cudaStreamCreateWithFlags(&srv->es[k].st, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&srv->es[k].ev, cudaEventDisableTiming);
@@ -865,6 +903,9 @@ extern "C" int rid_server_destroy(rid_server* srv) {
     if (srv->lev) cudaEventDestroy(srv->lev);
     if (srv->le0) cudaEventDestroy(srv->le0);
     if (srv->lst) cudaStreamDestroy(srv->lst);
+    if (srv->lfork) cudaEventDestroy(srv->lfork);
+    if (srv->ljoin) cudaEventDestroy(srv->ljoin);
+    if (srv->lst2) cudaStreamDestroy(srv->lst2);
     delete srv;
     return RID_OK;
 }

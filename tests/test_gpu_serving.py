@@ -7,7 +7,9 @@ Each job's results must be the same bits as the per-job path (rid_label,
 rid_explore) on the same inputs, and the same bits alone in the server as in
 any mix.  (BF16 exploration jobs of up to 16 walkers run the small-batch
 ensemble kernel's lean variant in the server, 8 epilogue warps and 3 weight
-stages, and the full variant per job: the same bits.)
+stages, and the full variant per job; label runs of long chains run as
+thread-block clusters of the persistent kernel in the server and through the
+per-step kernels per job: the same bits.)
 """
 import time
 
@@ -98,6 +100,8 @@ def mixed_specs(R):
         Spec(R, "explore", 22, 2, 16, 333, 6, prec=R.RID_PREC_FP32),  # graph chunks + a remainder chunk
         Spec(R, "label", 300, 12, 1, 120, 7),
         Spec(R, "label", 51, 7, 1, 100, 8),                            # odd bead count, no v0
+        Spec(R, "label", 900, 16, 2, 150, 10),                         # long chain: clusters of CTAs
+        Spec(R, "label", 1777, 30, 1, 90, 11),                         # long chain, ragged last slice
     ]
 
 
