@@ -28,9 +28,12 @@ def tiled(a):
     return np.ascontiguousarray(np.tile(a, (COPIES,) + (1,) * (a.ndim - 1)))
 
 
-@pytest.mark.parametrize("n,C,seed", [(200, 20, 1), (700, 33, 2), (2000, 64, 3), (517, 7, 4)])
-def test_cvs_and_forces_alone_equal_inside_a_batch(R, orc, n, C, seed):
-    sp = I.make_system(n, C, seed)
+@pytest.mark.parametrize("n,C,seed,nd,span", [(200, 20, 1, 0, 5), (700, 33, 2, 0, 5), (2000, 64, 3, 0, 5),
+                                              (517, 7, 4, 0, 5), (1500, 12, 7, 4, 600)])
+def test_cvs_and_forces_alone_equal_inside_a_batch(R, orc, n, C, seed, nd, span):
+    """(the last case has distance CVs between beads 600 apart: their atoms lie
+    in different CTAs' slices)"""
+    sp = I.make_system(n, C, seed, n_dist=nd, dist_span=span)
     x = I.make_chains(6, sp, seed)
     with R.System(sp) as sysm:
         s1, f1 = np.zeros((6, C), np.float32), np.zeros((6, n, 3), np.float32)
@@ -39,13 +42,14 @@ def test_cvs_and_forces_alone_equal_inside_a_batch(R, orc, n, C, seed):
         sysm.eval_forces(tiled(x), R.RID_BIAS_NONE, s_out=sb, f_out=fb)
     assert np.array_equal(s1, sb[:6]) and np.array_equal(f1, fb[:6])
     ref = orc.cvs(sp, x[5].astype(np.float64))[0]
-    d = np.angle(np.exp(1j * (s1[5].astype(np.float64) - ref)))
+    dist = I.cv_is_distance(sp)
+    d = np.where(dist, (s1[5] - ref) / np.maximum(np.abs(ref), 1.0), np.angle(np.exp(1j * (s1[5] - ref))))
     assert np.abs(d).max() < 1e-5
 
 
-@pytest.mark.parametrize("n,C,seed", [(300, 12, 5), (2000, 40, 6)])
-def test_labels_alone_equal_inside_a_batch(R, n, C, seed):
-    sp = I.make_system(n, C, seed)
+@pytest.mark.parametrize("n,C,seed,nd,span", [(300, 12, 5, 0, 5), (2000, 40, 6, 0, 5), (1200, 10, 8, 3, 500)])
+def test_labels_alone_equal_inside_a_batch(R, n, C, seed, nd, span):
+    sp = I.make_system(n, C, seed, n_dist=nd, dist_span=span)
     x = I.make_chains(6, sp, seed)
     rng = np.random.default_rng(seed)
     with R.System(sp) as sysm:
