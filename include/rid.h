@@ -514,7 +514,12 @@ RID_API int rid_get_mlp_cluster(rid_system* sys, int32_t* csize);
  * most 224) at the first force evaluation of every new walker count and keep
  * the fastest (the default, untimed, while a server runs a job on the
  * system).  Forces are the same bits with every size; force-field energy
- * evaluations always use the default size.
+ * evaluations always use the default size.  With fewer walkers than two per
+ * SM (no setting: from the shape alone) each walker's passes over its chain
+ * are split over up to 8 CTAs, and the integrator kernel runs each walker as a
+ * thread-block cluster of up to 8 CTAs over its bead batches (not for energy
+ * evaluations, nor while a server runs a job on the system); results are the
+ * same bits either way.
  * Errors: RID_ERR_ARG (threads not 0 or a multiple of 32 in [32, default]).
  */
 RID_API int rid_set_ff_threads(rid_system* sys, int32_t threads);
