@@ -709,7 +709,12 @@ int label_tick_launch(rid_server* srv) {
         const int grid_cl = (int)(std::min<long long>(n_big, clusters) * LF_CL);
         SCK(cudaEventRecord(srv->lfork, st));
         SCK(cudaStreamWaitEvent(srv->lst2, srv->lfork, 0));
-        SCK(rid_launch_label_fused(A2, nt, grid_cl, smem_cl, srv->lst2, LF_CL));
+        if (rid_launch_label_fused(A2, nt, grid_cl, smem_cl, srv->lst2, LF_CL) != cudaSuccess) {
+            // a cluster launch the device refuses: the same items one CTA per run (the same bits)
+            (void)cudaGetLastError();
+            const int grid1 = (int)std::min<long long>(n_big, (long long)occ_cl * srv->n_sm);
+            SCK(rid_launch_label_fused(A2, nt, grid1, smem_cl, srv->lst2, 1));
+        }
         SCK(cudaEventRecord(srv->ljoin, srv->lst2));
     }
     if (n_small > 0) {
