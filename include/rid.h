@@ -532,6 +532,22 @@ RID_API int rid_set_ff_threads(rid_system* sys, int32_t threads);
 RID_API int rid_get_ff_threads(rid_system* sys, int32_t* threads);
 
 /*
+ * Fused exploration steps (no counterpart in the paper, a tuning control): on
+ * = 1 (the default) runs every step of an exploration call (rid_explore,
+ * rid_walkers_advance) in one persistent launch, one CTA per walker holding
+ * its chain, CVs and the whole ensemble in shared memory, when the ensemble is
+ * FP32 and non-residual with at most 8 members, the CVs number at most 32, the
+ * state fits the CTA's shared memory (a few dozen to a few hundred beads with
+ * small ensembles), the walkers fit one wave of CTAs, and no energy trace is
+ * asked for; otherwise, and with on = 0, the steps run as per-step kernels.
+ * Each step is the per-step kernels' arithmetic in the same order, so the
+ * results are the same bits either way; a fused call ends with its last step
+ * closed.
+ * Errors: RID_ERR_ARG (on not 0 or 1).
+ */
+RID_API int rid_set_fused_steps(rid_system* sys, int32_t on);
+
+/*
  * Server: device memory of a fixed HBM budget, from which batched label runs
  * (rid_label_batch) and the request loop (rid_submit / rid_poll) take their
  * device memory.  Memory is allocated in segments, on demand, up to the

@@ -150,6 +150,7 @@ struct rid_system {
     cudaStream_t cap_stream = nullptr;   // captures the graph of a long run's chunk
     // kernel timing
     bool prof_on = false;
+    bool fused_on = true;      // small exploration calls in one persistent launch (rid_set_fused_steps)
     std::vector<std::string> prof_names;
     struct Rec { int id; cudaEvent_t a, b; };
     std::vector<Rec> prof_recs;
@@ -1118,12 +1119,39 @@ static int do_load(rid_system* sys, int W, const float* x0, const float* v0, uin
 // of its last step (its last step has a trace slot), and the chunk's traces go
 // from a staging block to their slots.  The arithmetic is that of the direct
 // run, so the results are the same bits; only the launches are fewer.
+// Whether an exploration call runs in one persistent launch (k_explore_small):
+// FP32 ensembles of a shape whose walker, ensemble and CVs fit one CTA's shared
+// memory, walkers in one wave, no energy trace, profiling off.
+static bool fused_explore(const rid_system* sys, int W, int mode, const double* en) {
+    if (!sys->fused_on || mode != 1 || sys->precision != RID_PREC_FP32 || en || sys->prof_on) return false;
+    static int nsm[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    int& n = nsm[dev & 63];
+    if (n == 0 && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+    return W <= n && rid_explore_small_smem(sys->S, sys->E) > 0;
+}
+
 static int advance_steps(rid_system* sys, int W, int mode, int64_t n_steps, float* cv, float* eps, double* en,
                          long long T, cudaStream_t st) {
     const int of = sys->S.output_freq, C = sys->S.C;
     const long long chunk = std::max<long long>(of, ((256 + of - 1) / of) * of);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(st, &cs));
+    if (n_steps > 0 && fused_explore(sys, W, mode, en)) {
+        // every step in one launch: the same arithmetic as the per-step kernels, and the
+        // call ends with its last step closed (as a settled per-step call)
+        TRY(settle(sys, st));
+        StateDev sd = state_view(sys);
+        sd.W = W;
+        cudaError_t le = cudaSuccess;
+        TRY(timed_launch(sys, "k_explore_small", st, [&] {
+            le = rid_launch_explore_small(sys->S, sd, sys->E, W, n_steps, (uint32_t)sys->step_next, cv, eps, T, st);
+        }));
+        if (le != cudaSuccess) return fail(RID_ERR_CUDA, "k_explore_small launch: %s", cudaGetErrorString(le));
+        sys->pending = false;
+        return RID_OK;
+    }
     if (n_steps < 2 * chunk || en || sys->prof_on || cs != cudaStreamCaptureStatusNone)
         return run_steps(sys, W, mode, nullptr, n_steps, sys->step_next, cv, eps, en, T, sys->pending, false, st);
     TRY(ensure_side(sys));
@@ -1410,6 +1438,13 @@ extern "C" int rid_set_ff_threads(rid_system* sys, int32_t threads) {
 extern "C" int rid_get_ff_threads(rid_system* sys, int32_t* threads) {
     if (!sys || !threads) return fail(RID_ERR_ARG, "NULL argument");
     *threads = sys->ff_force ? sys->ff_force : (sys->ff_W >= 0 ? sys->ff_th : rid_ff_default_threads(sys->S.N));
+    return RID_OK;
+}
+
+extern "C" int rid_set_fused_steps(rid_system* sys, int32_t on) {
+    if (!sys) return fail(RID_ERR_ARG, "NULL system");
+    if (on != 0 && on != 1) return fail(RID_ERR_ARG, "fused steps: expected 0 or 1, got %d", on);
+    sys->fused_on = on != 0;
     return RID_OK;
 }
 

@@ -275,6 +275,11 @@ struct HeadArgs {
                                // concurrency than clusters per walker)
 };
 void rid_launch_head(const HeadArgs& a, cudaStream_t s);
+// Every step of an exploration call in one persistent launch (k_explore_small):
+// shared memory it needs, 0 when the shape is not eligible.
+size_t rid_explore_small_smem(const SysDev& S, const EnsDev& E);
+cudaError_t rid_launch_explore_small(const SysDev& S, StateDev st, const EnsDev& E, int W, long long n_steps,
+                                     uint32_t step0, float* cv_out, float* eps_out, long long T, cudaStream_t s);
 void rid_launch_add_u32(uint32_t* p, uint32_t d, cudaStream_t s);
 void rid_launch_label_final(const LabelDev& lab, int W, int C, double* mf, double* se, double* sd,
                             cudaStream_t s);

@@ -39,7 +39,7 @@ EXPORTS = ("rid_version", "rid_status_string", "rid_last_error", "rid_create_sys
            "rid_trainer_create", "rid_trainer_destroy", "rid_trainer_set_data", "rid_trainer_run",
            "rid_trainer_grad", "rid_trainer_weights", "rid_mcmc", "rid_select",
            "rid_label_constrained", "rid_mcmc_system", "rid_set_mlp_cluster",
-           "rid_get_mlp_cluster", "rid_set_ff_threads", "rid_get_ff_threads")
+           "rid_get_mlp_cluster", "rid_set_ff_threads", "rid_get_ff_threads", "rid_set_fused_steps")
 RID_NOT_READY = 6
 RID_JOB_LABEL, RID_JOB_EXPLORE = 1, 2
 
@@ -419,6 +419,10 @@ class System:
     def set_ff_threads(self, threads):
         """CTA size of the force-field kernel: 0 tuned, else a multiple of 32."""
         _check(lib().rid_set_ff_threads(self.h, int(threads)))
+
+    def set_fused_steps(self, on):
+        """Fused exploration steps (one persistent launch per call) on or off."""
+        _check(lib().rid_set_fused_steps(self.h, 1 if on else 0))
 
     def ff_threads(self):
         """CTA size of the force-field kernel in use."""

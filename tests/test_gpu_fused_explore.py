@@ -1,0 +1,92 @@
+"""Fused exploration steps (k_explore_small): for small systems with FP32
+ensembles every step of a call runs in one persistent launch, one CTA per
+walker.  Each step is the per-step kernels' arithmetic in the same order, so
+traces (CVs, model deviation), final positions and velocities are the same
+bits as through the per-step kernels: checked on the paper's small
+configuration's shape, with distance CVs, eight members, a 96-wide ensemble,
+step counts with and without a final trace slot, calls continued from a
+previous call, and a Maxwell-Boltzmann start.  Ineligible shapes (residual
+networks, energy traces) take the per-step path with the switch on."""
+import numpy as np
+import pytest
+
+from paper_2408_14070_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_2408_14070_gb300 import build, rid
+    build.build()
+    return rid
+
+
+def run(R, sp, ens, x0, n_steps, fused, calls=1, v0=None, res=False):
+    W, C = x0.shape[0], sp.n_cv
+    T = n_steps // sp.output_freq
+    out = []
+    with R.System(sp) as sysm:
+        sysm.set_ensemble(ens, precision=R.RID_PREC_FP32)
+        sysm.set_fused_steps(fused)
+        l0 = sysm.launch_count()
+        sysm.walkers_load(x0, v0)
+        for _ in range(calls):
+            cv = np.zeros((W, T, C), np.float32)
+            eps = np.zeros((W, T), np.float32)
+            sysm.walkers_advance(n_steps, cv_out=cv, eps_out=eps)
+            out += [cv, eps]
+        xo, vo = np.zeros_like(x0), np.zeros_like(x0)
+        sysm.walkers_read(x_out=xo, v_out=vo)
+        launches = sysm.launch_count() - l0
+    return out + [xo, vo], launches
+
+
+CASES = [
+    # n, C, nd, W, M, L, H, steps, of, calls, seed
+    (22, 2, 0, 16, 4, 3, 64, 200, 10, 1, 1),     # the paper's small configuration's shape
+    (22, 2, 0, 16, 4, 3, 64, 207, 10, 2, 2),     # no trace at the last step; a continued call
+    (61, 9, 3, 8, 8, 2, 32, 150, 7, 1, 3),       # distance CVs, eight members
+    (150, 12, 0, 5, 2, 2, 96, 60, 1, 1, 4),      # 96 wide, a trace every step
+    (40, 4, 0, 33, 2, 4, 48, 90, 9, 1, 5),       # four hidden layers, ragged widths
+]
+
+
+@pytest.mark.parametrize("n,C,nd,W,M,L,H,steps,of,calls,seed", CASES)
+def test_fused_steps_equal_per_step_kernels(R, n, C, nd, W, M, L, H, steps, of, calls, seed):
+    sp = I.make_system(n, C, seed, n_dist=nd, dist_span=5, output_freq=of)
+    x0 = I.make_chains(W, sp, seed)
+    ens = I.make_ensemble(M, 2 * C, L, H, seed)
+    a, la = run(R, sp, ens, x0, steps, True, calls)
+    b, lb = run(R, sp, ens, x0, steps, False, calls)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+    assert np.all(np.isfinite(a[-2]))
+    assert la < lb   # one launch per call instead of three per step
+
+
+def test_fused_with_maxwell_boltzmann_start_and_trust_band(R, orc):
+    sp = I.make_system(22, 2, 9, output_freq=5)
+    x0 = I.make_chains(16, sp, 9)
+    ens = I.make_ensemble(4, 4, 3, 64, 9)
+    eps0 = np.array([orc.ensemble(ens, orc.cvs(sp, x0[w].astype(np.float64))[0])["eps"] for w in range(16)])
+    ens.trust_lo, ens.trust_hi = float(np.percentile(eps0, 25)), float(np.percentile(eps0, 75))
+    a, _ = run(R, sp, ens, x0, 100, True)
+    b, _ = run(R, sp, ens, x0, 100, False)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+
+
+def test_ineligible_shapes_take_the_per_step_path(R):
+    sp = I.make_system(30, 3, 11, output_freq=5)
+    x0 = I.make_chains(8, sp, 11)
+    ens = I.make_ensemble(4, 6, 3, 64, 11, resnet=True)
+    a, la = run(R, sp, ens, x0, 50, True)
+    b, lb = run(R, sp, ens, x0, 50, False)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+    assert la == lb
+    with R.System(sp) as sysm:
+        with pytest.raises(R.RidError) as e:
+            R._check(R.lib().rid_set_fused_steps(sysm.h, 2))
+        assert e.value.code == R.RID_ERR_ARG

@@ -30,6 +30,7 @@ def test_replayed_run_equals_short_calls(R, prec, n_steps, of):
     T = n_steps // of
     with R.System(sp) as sysm:
         sysm.set_ensemble(ens, precision=p)
+        sysm.set_fused_steps(False)   # the per-step kernels (this FP32 shape would run fused)
         cv = np.zeros((W, T, 2), np.float32)
         eps = np.zeros((W, T), np.float32)
         xo, vo = np.zeros_like(x0), np.zeros_like(x0)
