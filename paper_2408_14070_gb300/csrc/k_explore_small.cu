@@ -22,7 +22,31 @@
 
 namespace {
 
-constexpr int XS_THREADS = 256;
+constexpr int XS_THREADS = 320;   // 64 force-field threads beside 256 for the ensemble
+// During a step's evaluation the force field (which needs only the new
+// positions) runs on the first XS_FF threads while the ensemble (which needs
+// only the CVs) runs on the rest, each group with its own named barrier.
+constexpr int XS_FF = 64;
+constexpr int XS_EN = XS_THREADS - XS_FF;
+
+// acc += sum_k a[k] b[k * sb], k = 0 .. K-1 in order, the loads of 8 terms
+// issued before their FMAs
+__device__ __forceinline__ float xs_dot(const float* a, const float* b, int sb, int K, float acc) {
+    int k = 0;
+    for (; k + 8 <= K; k += 8) {
+        float x[8], y[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            x[q] = a[k + q];
+            y[q] = b[(k + q) * sb];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc = fmaf(x[q], y[q], acc);
+    }
+    for (; k < K; ++k) acc = fmaf(a[k], b[k * sb], acc);
+    return acc;
+}
+__device__ __forceinline__ void xs_bar(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 struct XsArgs {
     SysDev S;
@@ -267,23 +291,23 @@ __global__ void __launch_bounds__(XS_THREADS, 1) k_explore_small(XsArgs A) {
         __syncthreads();
     };
 
-    // ---- every member (k_mlp_fp32_small's arithmetic): member values, CV gradients
+    // ---- every member (k_mlp_fp32_small's arithmetic): member values, CV gradients;
+    // threads XS_FF .. XS_THREADS-1
     auto ensemble = [&]() {
+        const int et = tid - XS_FF, ew = et >> 5;
         for (int l = 0; l < L; ++l) {
             const int K = l == 0 ? D : H;
-            for (int idx = tid; idx < M * H; idx += XS_THREADS) {
+            for (int idx = et; idx < M * H; idx += XS_EN) {
                 const int m = idx / H, n = idx - m * H;
                 const float* in = l == 0 ? us : ts + ((size_t)m * L + l - 1) * H;
                 const float* wr = Ws + (size_t)m * wm + xs_wlayer(D, H, l) + n * (K + 1);
-                float acc = 0.0f;
-#pragma unroll 8
-                for (int k = 0; k < K; ++k) acc = fmaf(in[k], wr[k], acc);   // loads run ahead of the chain
+                const float acc = xs_dot(in, wr, 1, K, 0.0f);
                 ts[((size_t)m * L + l) * H + n] = tanhf(acc + bs[((size_t)m * L + l) * H + n]);
             }
-            __syncthreads();
+            xs_bar(1, XS_EN);
         }
         // member value A = w_out . h_L + b_out: lane-strided partials, then the butterfly
-        for (int m = warp; m < M; m += XS_THREADS / 32) {
+        for (int m = ew; m < M; m += XS_EN / 32) {
             const float* hL = ts + ((size_t)m * L + L - 1) * H;
             float part = 0.0f;
             for (int n = lane; n < H; n += 32) part = fmaf(wo[m * H + n], hL[n], part);
@@ -292,31 +316,28 @@ __global__ void __launch_bounds__(XS_THREADS, 1) k_explore_small(XsArgs A) {
             if (lane == 0) Av[m] = part + __ldg(E.bout + m);
         }
         // input gradient: g_L = w_out, Delta_l = g_l (1 - t_l^2), g_{l-1} = Delta_l W_l
-        for (int idx = tid; idx < M * H; idx += XS_THREADS) {
+        for (int idx = et; idx < M * H; idx += XS_EN) {
             const int m = idx / H, o = idx - m * H;
             G[m * gw + o] = wo[m * H + o];
         }
-        __syncthreads();
+        xs_bar(1, XS_EN);
         for (int l = L - 1; l >= 0; --l) {
             const int Nout = l == 0 ? D : H;
-            for (int idx = tid; idx < M * H; idx += XS_THREADS) {
+            for (int idx = et; idx < M * H; idx += XS_EN) {
                 const int m = idx / H, o = idx - m * H;
                 const float t = ts[((size_t)m * L + l) * H + o];
                 Gn[m * gw + o] = G[m * gw + o] * (1.0f - t * t);
             }
-            __syncthreads();
-            for (int idx = tid; idx < M * Nout; idx += XS_THREADS) {
+            xs_bar(1, XS_EN);
+            for (int idx = et; idx < M * Nout; idx += XS_EN) {
                 const int m = idx / Nout, j = idx - m * Nout;
                 const float* Wl = Ws + (size_t)m * wm + xs_wlayer(D, H, l);
-                float acc = 0.0f;
-#pragma unroll 8
-                for (int k = 0; k < H; ++k) acc = fmaf(Gn[m * gw + k], Wl[k * (Nout + 1) + j], acc);
-                G[m * gw + j] = acc;
+                G[m * gw + j] = xs_dot(Gn + m * gw, Wl + j, Nout + 1, H, 0.0f);
             }
-            __syncthreads();
+            xs_bar(1, XS_EN);
         }
         // dA/ds_j = -sin s_j g0[2j] + cos s_j g0[2j+1] (torsion), g0[2j] (distance: input (s, 0))
-        for (int idx = tid; idx < M * C; idx += XS_THREADS) {
+        for (int idx = et; idx < M * C; idx += XS_EN) {
             const int m = idx / C, j = idx - m * C;
             const float cs = us[2 * j], sn = us[2 * j + 1];
             const float* g0 = G + m * gw;
@@ -325,16 +346,27 @@ __global__ void __launch_bounds__(XS_THREADS, 1) k_explore_small(XsArgs A) {
         }
     };
 
-    // ---- force field (k_ff's arithmetic; warps on the same 32-bead groups)
+    // ---- force field (k_ff's arithmetic; warps on the same 32-bead groups); threads 0 .. XS_FF-1
     auto forcefield = [&]() {
         const int nclus = Y.nclus, nwords = (nclus + 31) / 32;
-        lj_cluster_boxes(xs, N, cbox);
+        // cluster bounding boxes (lj_cluster_boxes over this group's threads)
+        for (int c = tid; c < nclus; c += XS_FF) {
+            const int j1 = min(LJ_CLUSTER * (c + 1), N);
+            float4 lo = xs[LJ_CLUSTER * c], hi = lo;
+            for (int j = LJ_CLUSTER * c + 1; j < j1; ++j) {
+                const float4 p = xs[j];
+                lo.x = fminf(lo.x, p.x); lo.y = fminf(lo.y, p.y); lo.z = fminf(lo.z, p.z);
+                hi.x = fmaxf(hi.x, p.x); hi.y = fmaxf(hi.y, p.y); hi.z = fmaxf(hi.z, p.z);
+            }
+            cbox[2 * c] = lo;
+            cbox[2 * c + 1] = hi;
+        }
         if (BSMEM)
-            for (int t = tid; t < N; t += XS_THREADS) bonded_terms_to_smem(S, xs, t, fB, fA, fD);
-        __syncthreads();
+            for (int t = tid; t < N; t += XS_FF) bonded_terms_to_smem(S, xs, t, fB, fA, fD);
+        xs_bar(2, XS_FF);
         const bool sig1 = S.sig2 == 1.0f;
-        for (int it = 0; it * XS_THREADS < N; ++it) {
-            const int i = it * XS_THREADS + tid;
+        for (int it = 0; it * XS_FF < N; ++it) {
+            const int i = it * XS_FF + tid;
             const int wlo = i - lane, whi = wlo + 31;
             if (wlo >= N) break;                                  // warp-uniform
             const bool act = i < N;
@@ -356,7 +388,6 @@ __global__ void __launch_bounds__(XS_THREADS, 1) k_explore_small(XsArgs A) {
                 ff[i] = make_float4(fmaf(sc, fx, fb.x), fmaf(sc, fy, fb.y), fmaf(sc, fz, fb.z), 0.0f);
             }
         }
-        __syncthreads();
     };
 
     // ---- the call: step t finishes step t-1 (t > 0), then opens and evaluates step t
@@ -366,8 +397,9 @@ __global__ void __launch_bounds__(XS_THREADS, 1) k_explore_small(XsArgs A) {
         if (t > 0) finish(slot_of(t - 1));
         beads(t > 0, true, A.step0 + (uint32_t)t);
         cvs();
-        ensemble();
-        forcefield();
+        if (tid < XS_FF) forcefield();   // beside the ensemble
+        else ensemble();
+        __syncthreads();
     }
     if (n > 0) {
         finish(slot_of(n - 1));
