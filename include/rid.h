@@ -540,9 +540,11 @@ RID_API int rid_get_ff_threads(rid_system* sys, int32_t* threads);
  * state fits the CTA's shared memory (a few dozen to a few hundred beads with
  * small ensembles), the walkers fit one wave of CTAs, and no energy trace is
  * asked for; otherwise, and with on = 0, the steps run as per-step kernels.
- * Each step is the per-step kernels' arithmetic in the same order, so the
- * results are the same bits either way; a fused call ends with its last step
- * closed.
+ * The switch also sends rid_label of chains below 768 beads through the
+ * persistent label kernel (every step of every run in one launch, one CTA per
+ * run).  Each step is the per-step kernels' arithmetic in the same order, so
+ * the results are the same bits either way; a fused call ends with its last
+ * step closed.
  * Errors: RID_ERR_ARG (on not 0 or 1).
  */
 RID_API int rid_set_fused_steps(rid_system* sys, int32_t on);

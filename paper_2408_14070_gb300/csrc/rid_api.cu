@@ -12,6 +12,7 @@
 #include <cudaTypedefs.h>
 #include <algorithm>
 
+#include "rid_batch.cuh"
 #include "rid_internal.cuh"
 #include "rid_tc.cuh"
 
@@ -126,6 +127,7 @@ struct rid_system {
     DevBuf x, v, f, fff, s, J, u, gradA, Aval, eps, hs, eff, flags;
     // label
     DevBuf lsum, lsum2, lbsum, ls0, lkap;
+    DevBuf lfused;   // rid_label through the persistent label kernel: its job, items and counter
     // staging for host I/O and traces
     DevBuf io0, io1, tr_cv, tr_eps, tr_en, tr_chunk, out_mf, out_se, out_sd;
     // resident walker session
@@ -1508,11 +1510,7 @@ extern "C" int rid_label(rid_system* sys, int32_t R, const float* x0, const floa
     StateDev sd = state_view(sys);
     TRY(load_xyz(sys, x0, sd.x, nb, mem, st));
     if (v0) TRY(load_xyz(sys, v0, sd.v, nb, mem, st));
-    else rid_launch_mb(sys->S, sd, R, (uint32_t)step0, st);
     CK(cudaMemsetAsync(sys->flags.p, 0, (size_t)R * sizeof(int), st));
-    TRY(evaluate_at_rest(sys, R, 2, &lab, st));
-    bool pend = false;
-    TRY(run_steps(sys, R, 2, &lab, n_steps, step0, nullptr, nullptr, nullptr, 0, pend, true, st));
     double *dmf = mf_out, *dse = se_out, *dsd = std_out;
     if (mem == RID_MEM_HOST) {
         TRY(sys->out_mf.ensure(nc * sizeof(double)));
@@ -1522,7 +1520,71 @@ extern "C" int rid_label(rid_system* sys, int32_t R, const float* x0, const floa
         dse = sys->out_se.as<double>();
         dsd = sys->out_sd.as<double>();
     }
-    rid_launch_label_final(lab, R, C, dmf, dse, dsd, st);
+    if (sys->fused_on && N < 768 && !sys->prof_on) {
+        // chains below 768 beads: every step of every run in one launch of the persistent
+        // label kernel, one CTA per run (the batch and the request loop's kernel: the same
+        // arithmetic as the per-step kernels, so the same bits)
+        FusedJob J{};
+        J.S = sys->S;
+        J.x = sd.x;
+        J.v = sd.v;
+        J.f = sd.f;
+        J.s0 = lab.s0;
+        J.kappa = lab.kappa;
+        J.sum = lab.sum;
+        J.sum2 = lab.sum2;
+        J.bsum = lab.bsum;
+        J.mf = dmf;
+        J.se = dse;
+        J.sd = dsd;
+        J.flags = sd.flags;
+        J.R = R;
+        J.B = n_blocks;
+        J.n_steps = n_steps;
+        J.n_equil = n_equil;
+        J.K = n_steps - n_equil;
+        J.t0 = 0;
+        J.t1 = n_steps;
+        J.step0 = (uint32_t)step0;
+        J.init = 1;
+        J.mb = v0 ? 0 : 1;
+        std::vector<FusedItem> items((size_t)R);
+        for (int r = 0; r < R; ++r) items[r] = {0, r};
+        const size_t o_items = (sizeof(FusedJob) + 255) / 256 * 256;
+        const size_t o_cnt = (o_items + sizeof(FusedItem) * (size_t)R + 255) / 256 * 256;
+        TRY(sys->lfused.ensure(o_cnt + 256));
+        std::vector<char> hb(o_cnt);
+        memcpy(hb.data(), &J, sizeof(FusedJob));
+        memcpy(hb.data() + o_items, items.data(), sizeof(FusedItem) * (size_t)R);
+        char* dm = sys->lfused.as<char>();
+        CK(cudaMemcpyAsync(dm, hb.data(), o_cnt, cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(dm + o_cnt, 0, 256, st));
+        FusedArgs A{};
+        A.jobs = reinterpret_cast<const FusedJob*>(dm);
+        A.items = reinterpret_cast<const FusedItem*>(dm + o_items);
+        A.n_items = R;
+        A.next = reinterpret_cast<int*>(dm + o_cnt);
+        const size_t smem = rid_label_fused_smem(N, C, 0);
+        int nt = N <= 128 ? 128 : (N <= 256 ? 256 : 512);
+        if (rid_label_fused_occupancy(nt, smem) < 1) nt = 128;
+        int occ = rid_label_fused_occupancy(nt, smem);
+        if (occ < 1) return fail(RID_ERR_ARG, "label runs of %d beads exceed shared memory", N);
+        int nsm = 1, dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const int grid = (int)std::min<long long>(R, (long long)occ * nsm);
+        cudaError_t le = cudaSuccess;
+        TRY(timed_launch(sys, "k_label_fused", st, [&] { le = rid_launch_label_fused(A, nt, grid, smem, st); }));
+        if (le != cudaSuccess) return fail(RID_ERR_CUDA, "k_label_fused launch: %s", cudaGetErrorString(le));
+        // the host staging vector must outlive the copy
+        CK(cudaStreamSynchronize(st));
+    } else {
+        if (!v0) rid_launch_mb(sys->S, sd, R, (uint32_t)step0, st);
+        TRY(evaluate_at_rest(sys, R, 2, &lab, st));
+        bool pend = false;
+        TRY(run_steps(sys, R, 2, &lab, n_steps, step0, nullptr, nullptr, nullptr, 0, pend, true, st));
+        rid_launch_label_final(lab, R, C, dmf, dse, dsd, st);
+    }
     CK(cudaGetLastError());
     TRY(store_xyz(sys, sd.x, x_out, nb, mem, st));
     TRY(store_xyz(sys, sd.v, v_out, nb, mem, st));

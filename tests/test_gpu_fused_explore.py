@@ -1,4 +1,4 @@
-"""Fused exploration steps (k_explore_small): for small systems with FP32
+"""Fused steps.  Exploration (k_explore_small): for small systems with FP32
 ensembles every step of a call runs in one persistent launch, one CTA per
 walker.  Each step is the per-step kernels' arithmetic in the same order, so
 traces (CVs, model deviation), final positions and velocities are the same
@@ -6,7 +6,9 @@ bits as through the per-step kernels: checked on the paper's small
 configuration's shape, with distance CVs, eight members, a 96-wide ensemble,
 step counts with and without a final trace slot, calls continued from a
 previous call, and a Maxwell-Boltzmann start.  Ineligible shapes (residual
-networks, energy traces) take the per-step path with the switch on."""
+networks, energy traces) take the per-step path with the switch on.  Labels:
+rid_label of chains below 768 beads runs in one launch of the persistent label
+kernel, with the same bits as through the per-step kernels."""
 import numpy as np
 import pytest
 
@@ -90,3 +92,34 @@ def test_ineligible_shapes_take_the_per_step_path(R):
         with pytest.raises(R.RidError) as e:
             R._check(R.lib().rid_set_fused_steps(sysm.h, 2))
         assert e.value.code == R.RID_ERR_ARG
+
+
+@pytest.mark.parametrize("n,C,R_,steps,seed", [(22, 2, 16, 300, 21), (200, 20, 3, 240, 22), (700, 9, 40, 120, 23)])
+def test_fused_labels_equal_per_step_kernels(R, n, C, R_, steps, seed):
+    """rid_label of chains below 768 beads runs in one launch of the persistent
+    label kernel; with the switch off, through the per-step kernels: the same
+    bits (mean force, standard error, std, final positions and velocities),
+    with a Maxwell-Boltzmann start and with given velocities."""
+    sp = I.make_system(n, C, seed)
+    x0 = I.make_chains(R_, sp, seed)
+    rng = np.random.default_rng(seed)
+    kap = rng.uniform(50.0, 500.0, size=(R_, C))
+    outs = []
+    for fused in (True, False):
+        with R.System(sp) as sysm:
+            sysm.set_fused_steps(fused)
+            s = np.zeros((R_, C), np.float32)
+            sysm.eval_forces(x0, R.RID_BIAS_NONE, s_out=s)
+            s0 = s.astype(np.float64) + np.random.default_rng(seed + 1).uniform(-0.3, 0.3, size=s.shape)
+            res = []
+            for v0 in (None, (0.5 * rng.standard_normal(x0.shape)).astype(np.float32)):
+                mf, se, sd = (np.zeros((R_, C)) for _ in range(3))
+                xo, vo = np.zeros_like(x0), np.zeros_like(x0)
+                sysm.label(x0, s0, kap, steps, steps // 5, 8, mf, se, sd, v0=v0, x_out=xo, v_out=vo)
+                res += [mf, se, sd, xo, vo]
+            outs.append(res)
+        rng = np.random.default_rng(seed)
+        kap = rng.uniform(50.0, 500.0, size=(R_, C))
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    assert np.all(np.isfinite(outs[0][0]))
