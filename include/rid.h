@@ -536,10 +536,10 @@ RID_API int rid_get_ff_threads(rid_system* sys, int32_t* threads);
  * = 1 (the default) runs every step of an exploration call (rid_explore,
  * rid_walkers_advance) in one persistent launch, one CTA per walker holding
  * its chain, CVs and the whole ensemble in shared memory, when the ensemble is
- * FP32 and non-residual with at most 8 members, the CVs number at most 32, the
- * state fits the CTA's shared memory (a few dozen to a few hundred beads with
- * small ensembles), the walkers fit one wave of CTAs, and no energy trace is
- * asked for; otherwise, and with on = 0, the steps run as per-step kernels.
+ * FP32 and non-residual with at most 8 members, the chain has at most 128
+ * beads, the CVs number at most 32, the state fits the CTA's shared memory,
+ * the walkers fit one wave of CTAs, and no energy trace is asked for;
+ * otherwise, and with on = 0, the steps run as per-step kernels.
  * The switch also sends rid_label of chains below 768 beads through the
  * persistent label kernel (every step of every run in one launch, one CTA per
  * run).  Each step is the per-step kernels' arithmetic in the same order, so

@@ -16,8 +16,9 @@
 // reduction and integrator, k_mlp_fp32_small's sequential dot products and
 // lane-strided member value, k_ff's cluster-culled pairs with the warps on
 // the same 32-bead groups), so a call gives the same bits as the per-step
-// path.  Used for FP32 non-residual ensembles of at most 8 members when the
-// whole state fits one CTA's shared memory and the walkers fit one wave.
+// path.  Used for chains of at most 128 beads with FP32 non-residual
+// ensembles of at most 8 members when the whole state fits one CTA's shared
+// memory and the walkers fit one wave.
 #include "rid_forces.cuh"
 
 namespace {
@@ -436,7 +437,9 @@ __global__ void __launch_bounds__(XS_THREADS, 1) k_explore_small(XsArgs A) {
 
 // Shared memory of k_explore_small, or 0 when the shape is not eligible.
 size_t rid_explore_small_smem(const SysDev& S, const EnsDev& E) {
-    if (E.resnet || E.M > 8 || E.M < 1 || S.C > 32 || E.D != 2 * S.C) return 0;
+    // (chains of at most 128 beads: the force field has 64 threads here, where the per-step
+    // kernel splits a longer chain over several CTAs)
+    if (S.N > 128 || E.resnet || E.M > 8 || E.M < 1 || S.C > 32 || E.D != 2 * S.C) return 0;
     const XsLayout Y = xs_layout(S.N, S.C, E.M, E.D, E.L, E.H, S.N <= RID_BONDED_SMEM_MAX);
     return Y.bytes <= 200 * 1024 ? Y.bytes : 0;
 }

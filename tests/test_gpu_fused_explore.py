@@ -49,7 +49,7 @@ CASES = [
     (22, 2, 0, 16, 4, 3, 64, 200, 10, 1, 1),     # the paper's small configuration's shape
     (22, 2, 0, 16, 4, 3, 64, 207, 10, 2, 2),     # no trace at the last step; a continued call
     (61, 9, 3, 8, 8, 2, 32, 150, 7, 1, 3),       # distance CVs, eight members
-    (150, 12, 0, 5, 2, 2, 96, 60, 1, 1, 4),      # 96 wide, a trace every step
+    (120, 12, 0, 5, 2, 2, 96, 60, 1, 1, 4),      # 96 wide, a trace every step
     (40, 4, 0, 33, 2, 4, 48, 90, 9, 1, 5),       # four hidden layers, ragged widths
 ]
 
@@ -79,10 +79,12 @@ def test_fused_with_maxwell_boltzmann_start_and_trust_band(R, orc):
         assert np.array_equal(u, v)
 
 
-def test_ineligible_shapes_take_the_per_step_path(R):
-    sp = I.make_system(30, 3, 11, output_freq=5)
+@pytest.mark.parametrize("n,resnet", [(30, True), (200, False)])
+def test_ineligible_shapes_take_the_per_step_path(R, n, resnet):
+    """A residual ensemble, a chain above 128 beads."""
+    sp = I.make_system(n, 3, 11, output_freq=5)
     x0 = I.make_chains(8, sp, 11)
-    ens = I.make_ensemble(4, 6, 3, 64, 11, resnet=True)
+    ens = I.make_ensemble(4, 6, 3, 64, 11, resnet=resnet)
     a, la = run(R, sp, ens, x0, 50, True)
     b, lb = run(R, sp, ens, x0, 50, False)
     for u, v in zip(a, b):
