@@ -274,6 +274,7 @@ def run_batching(rid, n_jobs, n_steps, plain_jobs, seed=3):
     for k in sample:
         j = jobs[k]
         C = j["system"].C
+        j["system"].set_fused_steps(False)   # the plain path: per-step kernels
         mf, se, sd = np.zeros((1, C)), np.zeros((1, C)), np.zeros((1, C))
         t1 = time.perf_counter()
         try:
@@ -526,8 +527,11 @@ def run_serving(rid, n_req, rate, plain_req, seed=5):
     for d in served:
         d["system"].close()
 
-    # plain FP32 per-job path on the first plain_req requests, in arrival order
+    # plain FP32 per-job path on the first plain_req requests, in arrival order (per-step
+    # kernels: the fused steps off)
     plain = [build_req(r, rid.RID_PREC_FP32) for r in reqs[:plain_req]]
+    for d in plain:
+        d["system"].set_fused_steps(False)
     lat_p = {"label": [], "explore": []}
     t0 = time.perf_counter()
     busy_until = 0.0
@@ -567,7 +571,8 @@ def run_serving(rid, n_req, rate, plain_req, seed=5):
             "mlp_precision": "bf16",
             "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
             "plain_per_job": {"requests": len(plain), "path": "rid_label / rid_explore per request in arrival "
-                                                              "order, FP32 ensembles, one at a time",
+                                                              "order, FP32 ensembles, per-step kernels, one at "
+                                                              "a time",
                               "label_latency_ms": {"p50": pct(lat_p["label"], 50), "p99": pct(lat_p["label"], 99)},
                               "explore_latency_ms": {"p50": pct(lat_p["explore"], 50),
                                                      "p99": pct(lat_p["explore"], 99)},
