@@ -545,7 +545,7 @@ RID_API int rid_get_ff_threads(rid_system* sys, int32_t* threads);
  * run).  Each step is the per-step kernels' arithmetic in the same order, so
  * the results are the same bits either way; a fused call ends with its last
  * step closed.
- * Errors: RID_ERR_ARG (on not 0 or 1).
+ * Errors: RID_ERR_ARG (sys NULL, or on not 0 or 1).
  */
 RID_API int rid_set_fused_steps(rid_system* sys, int32_t on);
 

@@ -156,6 +156,7 @@ def lib() -> C.CDLL:
     L.rid_get_mlp_cluster.argtypes = [vp, C.POINTER(i32)]
     L.rid_set_ff_threads.argtypes = [vp, i32]
     L.rid_get_ff_threads.argtypes = [vp, C.POINTER(i32)]
+    L.rid_set_fused_steps.argtypes = [vp, i32]
     L.rid_ensemble_grad_noalloc.argtypes = [i32, i32, vp, i32, i32, i32, i32, vp, vp, vp, vp]
     L.rid_server_create.argtypes = [u64, C.POINTER(vp)]
     L.rid_server_destroy.argtypes = [vp]
@@ -421,7 +422,9 @@ class System:
         _check(lib().rid_set_ff_threads(self.h, int(threads)))
 
     def set_fused_steps(self, on):
-        """Fused exploration steps (one persistent launch per call) on or off."""
+        """The persistent small-system kernels on or off: exploration calls of small
+        FP32 systems, and rid_label below 768 beads, in one launch per call.  The
+        results are the same bits either way."""
         _check(lib().rid_set_fused_steps(self.h, 1 if on else 0))
 
     def ff_threads(self):

@@ -59,6 +59,16 @@ def test_null_arguments_rejected_before_device_work(L):
     assert L.rid_explore(None, 1, None, None, 0, 1, None, None, None, None, None, 0, None) == rid.RID_ERR_ARG
     assert L.rid_philox(-1, None, 0, None, None, 0, None) == rid.RID_ERR_ARG
     assert L.rid_destroy_system(None) == rid.RID_OK
+    # the per-system switches and the request loop answer a NULL handle
+    i32 = C.c_int32()
+    for call in (lambda: L.rid_set_fused_steps(None, 1), lambda: L.rid_set_mlp_cluster(None, 0),
+                 lambda: L.rid_set_ff_threads(None, 0), lambda: L.rid_get_ff_threads(None, C.byref(i32)),
+                 lambda: L.rid_get_mlp_cluster(None, C.byref(i32)), lambda: L.rid_profile_enable(None, 1),
+                 lambda: L.rid_submit(None, None, None), lambda: L.rid_poll(None, 1, None),
+                 lambda: L.rid_server_load(None, None, None, None)):
+        assert call() == rid.RID_ERR_ARG
+        assert b"NULL" in L.rid_last_error()
+    assert L.rid_launch_count(None) == -1
 
 
 def test_ctypes_structures_match_the_header(tmp_path):
