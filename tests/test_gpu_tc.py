@@ -333,3 +333,46 @@ def test_cluster_size_argument_errors(R):
                 s2.set_mlp_cluster(cs)
                 s2.eval_forces(x3, R.RID_BIAS_ENSEMBLE, f_out=np.zeros((3, 140, 3), np.float32))
                 assert s2.mlp_cluster() == used, cs
+
+
+def test_full_size_as_benched(R, orc):
+    """The benchmark's workload and launch configuration: 1024 walkers of the
+    200-bead chain, 20 torsions, the BF16 ensemble 4 x 40->256x4->1 with the
+    default trust levels, inputs drawn as the benchmark draws them.  One force
+    evaluation, member gradients and eps checked against the oracle on a
+    sample of walkers one by one (tiles 0, 1, 3 and 7, first and last rows);
+    then 20 resident steps, the path the benchmark times, with the CV and eps
+    traces' last slot checked against the oracle at the final positions the
+    GPU reached."""
+    sp = I.make_system(200, 20, 1, output_freq=10)
+    W = 1024
+    x = I.make_chains(W, sp, 1)
+    ens = I.make_ensemble(4, 40, 4, 256, 1)
+    sample = [0, 1, 127, 128, 511, 777, 1000, 1023]
+    s = np.zeros((W, 20), np.float32)
+    f, eps, abar, g = (np.zeros((W, 200, 3), np.float32), np.zeros(W, np.float32), np.zeros(W, np.float32),
+                       np.zeros((4, W, 20), np.float32))
+    with R.System(sp) as sysm:
+        sysm.set_ensemble(ens, precision=R.RID_PREC_BF16)
+        sysm.eval_forces(x, R.RID_BIAS_ENSEMBLE, f_out=f, s_out=s, eps_out=eps, abar_out=abar, grad_out=g)
+        for w in sample:
+            sr, _ = orc.cvs(sp, x[w].astype(np.float64))
+            assert np.abs(np.angle(np.exp(1j * (s[w] - sr)))).max() < 1e-5
+            e = orc.ensemble(ens, sr)
+            for m in range(4):
+                assert normwise(g[m, w], e["gradA"][m]) < GRAD_TOL, (w, m)
+            assert normwise(g[:, w].mean(axis=0), e["gradA"].mean(axis=0)) < GRAD_TOL, w
+            assert abs(eps[w] - e["eps"]) <= EPS_TOL * abs(e["eps"]) + 1e-4, w
+        assert np.isfinite(f).all()
+        sysm.walkers_load(x)
+        cv = np.zeros((W, 2, 20), np.float32)
+        et = np.zeros((W, 2), np.float32)
+        sysm.walkers_advance(20, cv_out=cv, eps_out=et)
+        xo = np.zeros_like(x)
+        sysm.walkers_read(x_out=xo)
+    assert np.isfinite(xo).all() and np.isfinite(cv).all()
+    for w in sample:
+        sr, _ = orc.cvs(sp, xo[w].astype(np.float64))
+        assert np.abs(np.angle(np.exp(1j * (cv[w, -1] - sr)))).max() < 1e-4, w
+        e = orc.ensemble(ens, sr)
+        assert abs(et[w, -1] - e["eps"]) <= EPS_TOL * abs(e["eps"]) + 1e-4, w
