@@ -125,3 +125,40 @@ def test_fused_labels_equal_per_step_kernels(R, n, C, R_, steps, seed):
     for a, b in zip(*outs):
         assert np.array_equal(a, b)
     assert np.all(np.isfinite(outs[0][0]))
+
+
+def test_small_configuration_as_benched(R, orc):
+    """The paper's small configuration in the calls the benchmark times: 16
+    walkers x 2000 biased steps in one exploration call (the fused kernel) and
+    16 restrained runs (kappa 50, centres uniform on the torus) x 1000 steps in
+    one label call (the persistent label kernel).  The first trace slot
+    against the oracle's first 10 steps (1e-4), the last slot against the
+    oracle's CVs and model deviation at the final positions the GPU reached
+    (1e-5), labels within two combined standard errors of the oracle's."""
+    sp = I.make_system(22, 2, 1, output_freq=10)
+    W = 16
+    x0 = I.make_chains(W, sp, 1)
+    ens = I.make_ensemble(4, 4, 3, 64, 1)
+    cv = np.zeros((W, 200, 2), np.float32)
+    eps = np.zeros((W, 200), np.float32)
+    xo = np.zeros_like(x0)
+    s0 = I.make_label_targets(W, 2, 1)
+    kap = np.full((W, 2), 50.0)
+    mf, se, sd = (np.zeros((W, 2)) for _ in range(3))
+    with R.System(sp) as sysm:
+        sysm.set_ensemble(ens, precision=R.RID_PREC_FP32)
+        sysm.explore(x0, 2000, cv_out=cv, eps_out=eps, x_out=xo)
+        sysm.label(x0, s0, kap, 1000, 100, 20, mf, se, sd)
+    assert np.isfinite(xo).all() and np.isfinite(cv).all() and np.isfinite(eps).all()
+    first = orc.explore(sp, x0, 10, ens=ens)
+    assert np.abs(np.angle(np.exp(1j * (cv[:, 0] - first["cv"][:, 0])))).max() < 1e-4
+    assert np.allclose(eps[:, 0], first["eps"][:, 0], rtol=1e-4, atol=1e-5)
+    for w in range(W):
+        sr, _ = orc.cvs(sp, xo[w].astype(np.float64))
+        assert np.abs(np.angle(np.exp(1j * (cv[w, -1] - sr)))).max() < 1e-5, w
+        e = orc.ensemble(ens, sr)
+        assert abs(eps[w, -1] - e["eps"]) <= 1e-4 * e["eps"] + 1e-6, w
+    ref = orc.label(sp, x0, s0, kap, 1000, 100, 20)
+    z = (mf - ref["mf"]) / np.sqrt(se ** 2 + ref["se"] ** 2)
+    assert np.mean(np.abs(z) <= 2) >= 0.9 and np.all(np.abs(z) < 4), z
+    assert np.all(se > 0) and np.allclose(sd, ref["std"], rtol=0.3)
