@@ -679,6 +679,14 @@ RID_API int rid_submit(rid_server* srv, const rid_request* req, uint64_t* job_id
  * ...), after which the id is forgotten.  info (may be NULL) is filled in
  * either case.  Unknown id: RID_ERR_ARG. */
 RID_API int rid_poll(rid_server* srv, uint64_t job_id, rid_job_info* info);
+/* Withdraw a job that is still queued (not yet admitted; it holds no device
+ * memory and no device work of it has been issued): the job is dropped, its
+ * output arrays are not written, and rid_poll then reports RID_ERR_CANCELLED
+ * (t_start_ms stays -1).  A host-side operation: no device call.  Errors:
+ * RID_ERR_ARG (srv NULL, or an unknown or already polled id), RID_ERR_STATE
+ * (the job is running or final: it runs to its end and rid_poll reports its
+ * own status). */
+RID_API int rid_cancel(rid_server* srv, uint64_t job_id);
 /* Jobs queued and running, and device bytes granted to running jobs. */
 RID_API int rid_server_load(rid_server* srv, int32_t* queued, int32_t* running, uint64_t* bytes_in_use);
 

@@ -989,6 +989,25 @@ extern "C" int rid_poll(rid_server* srv, uint64_t job_id, rid_job_info* info) {
     return st;
 }
 
+extern "C" int rid_cancel(rid_server* srv, uint64_t job_id) {
+    if (!srv) return rid_fail(RID_ERR_ARG, "NULL server");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->jobs.find(job_id);
+    if (it == srv->jobs.end()) return rid_fail(RID_ERR_ARG, "unknown job id %llu", (unsigned long long)job_id);
+    SJob* j = it->second.get();
+    // only a job still waiting for admission holds nothing on the device; the
+    // worker reads the queue under the same lock
+    auto q = std::find(srv->queue.begin(), srv->queue.end(), j);
+    if (q == srv->queue.end())
+        return rid_fail(RID_ERR_STATE, "job %llu is %s", (unsigned long long)job_id,
+                        j->status == RID_NOT_READY ? "running" : "final");
+    srv->queue.erase(q);
+    j->status = RID_ERR_CANCELLED;
+    j->t_end = now_ms(srv);
+    srv->cv.notify_all();
+    return RID_OK;
+}
+
 extern "C" int rid_server_load(rid_server* srv, int32_t* queued, int32_t* running, uint64_t* bytes_in_use) {
     if (!srv) return rid_fail(RID_ERR_ARG, "NULL server");
     {

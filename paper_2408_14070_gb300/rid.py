@@ -35,7 +35,7 @@ EXPORTS = ("rid_version", "rid_status_string", "rid_last_error", "rid_create_sys
            "rid_set_ensemble", "rid_explore", "rid_label", "rid_eval_forces", "rid_pair_mask", "rid_philox",
            "rid_walkers_load", "rid_walkers_advance", "rid_walkers_read", "rid_profile_enable",
            "rid_profile_read", "rid_launch_count", "rid_ensemble_grad_noalloc", "rid_server_create",
-           "rid_server_destroy", "rid_label_batch", "rid_submit", "rid_poll", "rid_server_load",
+           "rid_server_destroy", "rid_label_batch", "rid_submit", "rid_poll", "rid_cancel", "rid_server_load",
            "rid_trainer_create", "rid_trainer_destroy", "rid_trainer_set_data", "rid_trainer_run",
            "rid_trainer_grad", "rid_trainer_weights", "rid_mcmc", "rid_select",
            "rid_label_constrained", "rid_mcmc_system", "rid_set_mlp_cluster",
@@ -163,6 +163,7 @@ def lib() -> C.CDLL:
     L.rid_label_batch.argtypes = [vp, C.POINTER(LabelJob), i32, i32, C.POINTER(i32), i32, vp]
     L.rid_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(u64)]
     L.rid_poll.argtypes = [vp, u64, C.POINTER(JobInfo)]
+    L.rid_cancel.argtypes = [vp, u64]
     L.rid_server_load.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(u64)]
     L.rid_launch_count.restype = i64
     L.rid_trainer_create.argtypes = [C.POINTER(TrainDesc), vp, C.POINTER(vp)]
@@ -572,6 +573,15 @@ class Server:
                     raise TimeoutError(f"{len(left)} jobs not final after {timeout} s")
                 time.sleep(sleep)
         return out
+
+    def cancel(self, job_id):
+        """Withdraw a job still queued: True (rid_poll then reports
+        RID_ERR_CANCELLED), False if it is running or final (it runs to its end)."""
+        rc = lib().rid_cancel(self.h, C.c_uint64(job_id))
+        if rc == RID_ERR_STATE:
+            return False
+        _check(rc)
+        return True
 
     def load(self):
         q, r, b = C.c_int32(), C.c_int32(), C.c_uint64()

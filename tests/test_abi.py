@@ -36,9 +36,7 @@ def test_library_exports_every_declared_symbol(L):
     from paper_2408_14070_gb300 import rid
     for n in declared_symbols():
         assert hasattr(L, n), n
-    assert set(declared_symbols()) <= set(rid.EXPORTS) | {"rid_server_create", "rid_server_destroy",
-                                                          "rid_submit", "rid_poll", "rid_cancel",
-                                                          "rid_server_stats"}
+    assert set(declared_symbols()) == set(rid.EXPORTS)
 
 
 def test_version_and_status_strings(L):
@@ -65,6 +63,7 @@ def test_null_arguments_rejected_before_device_work(L):
                  lambda: L.rid_set_ff_threads(None, 0), lambda: L.rid_get_ff_threads(None, C.byref(i32)),
                  lambda: L.rid_get_mlp_cluster(None, C.byref(i32)), lambda: L.rid_profile_enable(None, 1),
                  lambda: L.rid_submit(None, None, None), lambda: L.rid_poll(None, 1, None),
+                 lambda: L.rid_cancel(None, 1),
                  lambda: L.rid_server_load(None, None, None, None)):
         assert call() == rid.RID_ERR_ARG
         assert b"NULL" in L.rid_last_error()

@@ -167,6 +167,47 @@ def test_admission_by_footprint_keeps_within_the_budget(R):
         sp.sys.close()
 
 
+def test_cancel_withdraws_queued_jobs_only(R):
+    """A 1 MiB budget holds most of twelve label jobs back; the last four are
+    withdrawn right after submission, while the first ones still run (2000
+    steps each).  A withdrawn job's outputs stay untouched and it polls as
+    cancelled, never started; the others give the per-job results.  A job
+    that is final but not yet polled cannot be withdrawn; an id that was
+    polled or never given is unknown."""
+    specs = [Spec(R, "label", 200, 20, 8, 2000, 40 + k) for k in range(12)]
+    with R.Server(1 << 20) as srv:
+        ids = [sp.submit(srv) for sp in specs]
+        withdrawn = [jid for jid in ids[8:] if srv.cancel(jid)]
+        assert withdrawn                               # queued behind the budget
+        while srv.load()[:2] != (0, 0):
+            time.sleep(0.001)
+        assert not srv.cancel(ids[0])                  # final, not yet polled
+        res = srv.wait(ids)
+        with pytest.raises(R.RidError) as e:
+            srv.cancel(ids[0])                         # polled: forgotten
+        assert e.value.code == R.RID_ERR_ARG
+        with pytest.raises(R.RidError) as e:
+            srv.cancel(987654)
+        assert e.value.code == R.RID_ERR_ARG
+    for sp, jid in zip(specs, ids):
+        st, info = res[jid]
+        if jid in withdrawn:
+            assert st == R.RID_ERR_CANCELLED and info["t_start_ms"] == -1
+            assert all(not a.any() for a in sp.outputs())
+            continue
+        out = [a.copy() for a in sp.outputs()]
+        try:
+            ref, st_ref = sp.per_job(), R.RID_OK
+        except R.RidError as err:
+            ref, st_ref = None, err.code
+        assert st == st_ref
+        if ref is not None:
+            for a, b in zip(out, ref):
+                assert np.array_equal(a, b)
+    for sp in specs:
+        sp.sys.close()
+
+
 def test_request_errors(R):
     big = Spec(R, "label", 400, 20, 256, 40, 31)
     with R.Server(2 << 20) as srv:
