@@ -170,18 +170,22 @@ class ClockSampler:
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         lo, hi = getattr(self, "window", (-1e30, 1e30))
-        inside = [ln for t, ln in self.lines if lo - 0.1 <= t <= hi + 0.1]
-        if not inside and self.lines:       # region shorter than the sampling period
-            inside = [min(self.lines, key=lambda tl: abs(tl[0] - 0.5 * (lo + hi)))[1]]
-        for ln in inside:
+        def parsed(ln):
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 7:
-                continue
+                return None
             try:
-                sm.append(float(f[0]))
-                mx.append(float(f[1]))
+                return float(f[0]), float(f[1]), f
             except ValueError:
-                continue
+                return None
+        good = [(t, parsed(ln)) for t, ln in self.lines]
+        good = [(t, p) for t, p in good if p is not None]
+        inside = [p for t, p in good if lo - 0.1 <= t <= hi + 0.1]
+        if not inside and good:             # region shorter than the sampling period
+            inside = [min(good, key=lambda tp: abs(tp[0] - 0.5 * (lo + hi)))[1]]
+        for s_mhz, m_mhz, f in inside:
+            sm.append(s_mhz)
+            mx.append(m_mhz)
             for n, v in zip(names, f[3:7]):
                 if v.lower() == "active":
                     reasons.add(n)

@@ -81,6 +81,9 @@ def test_clock_record_keeps_samples_of_the_timed_region(B):
     # a region shorter than the sampling period takes the sample nearest its middle
     s = _sampler(B, lines, (2.8, 2.81)).summary()
     assert s["samples"] == 1 and s["sm_mhz"] == 500 and s["reasons"] == ["hw_slowdown"]
+    # ... the nearest sample that parses: not the unreadable one at 1.3
+    s = _sampler(B, lines, (1.6, 1.61)).summary()
+    assert s == {"sm_mhz": 2055, "sm_max_mhz": 2070, "reasons": [], "samples": 1}
     assert _sampler(B, [], (0, 1)).summary()["sm_mhz"] is None
 
 
