@@ -120,3 +120,22 @@ def test_rate_over_ranks_and_summary_of_the_line(B):
     assert s["serving"]["tput"] == 2046016 and s["serving"]["label_p99_ms"] == 676
     assert s["serving"]["plain_label_p99_ms"] is None and s["batching"] is None
     assert s["cpu"] == [11032, 16]
+
+
+def test_reference_arm_line_on_rank_zero(B, monkeypatch, capsys):
+    """The reference arm times the oracle on the host cores and prints one
+    JSON line with the primary arm's metric, unit and config."""
+    for k, v in (("RANK", "0"), ("WORLD_SIZE", "1"), ("LOCAL_RANK", "0")):
+        monkeypatch.setenv(k, v)
+
+    class A:
+        steps, warmup, gpus = 1, 0, 1
+    B.run_reference(A())
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == "biased MD walker-steps/s"
+    assert line["unit"] == "walker-steps/s" and line["higher_is_better"] is True
+    assert line["config"]["workload"] == B.WORKLOAD and line["dtype"] == "f64"
+    assert line["value"] > 0 and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": "walker-steps/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
